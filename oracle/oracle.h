@@ -1,0 +1,129 @@
+/*
+ * oracle.h - FP64 CPU oracle for the Whitted tracer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, plain reference the
+ * CUDA path is checked against.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the product path never does.
+ * It shares no code, header or constant with the CUDA sources.
+ *
+ * What it computes (paper: "Massively Parallel Ray Tracing Algorithm Using
+ * GPU", Qin, Lin, Huang):
+ *   - ray-sphere hits by the quadratic of Eq. 9-12 (textbook form, in FP64);
+ *   - ray-triangle hits (Moller-Trumbore 1997: the plain point-in-plane and
+ *     inside-triangle test written with barycentrics);
+ *   - local illumination with one shadow ray per point light, Alg. 1 (an
+ *     occluder anywhere on the segment blocks the light; otherwise its
+ *     irradiance is added once);
+ *   - Eq. 8 specialised to point lights and a Lambert + Phong BRDF, plus the
+ *     emission term L_e of Eq. 7;
+ *   - reflection and refraction rays traced to a fixed depth (Sec. IV.A,
+ *     Fig. 3), both recursively and as the paper's iteration-over-depth form.
+ *
+ * Input arrays use the binary layout of the C ABI structs (4-byte fields,
+ * no padding); the oracle promotes every value to double on entry.
+ */
+#ifndef RTB_ORACLE_H
+#define RTB_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_scene orc_scene;
+
+/* Copies and promotes the inputs; builds the oracle's own median-split BVH.
+ * background: 3 doubles.  eps_scale: offset scale (1e-4).  fragile_k: the
+ * multiplier K of the rounding model (decision margins below K x the
+ * modelled FP32 uncertainty are flagged).  Returns NULL on bad input. */
+orc_scene* orc_scene_create(const void* spheres, int64_t n_spheres,
+                            const void* triangles, int64_t n_triangles,
+                            const void* materials, int64_t n_materials,
+                            const void* lights, int64_t n_lights,
+                            const double* background, double eps_scale,
+                            double fragile_k);
+void orc_scene_free(orc_scene* s);
+int64_t orc_bvh_node_count(const orc_scene* s);
+
+/* Pinhole camera ray of pixel (x, y), row 0 at the top.  cam: rt_camera
+ * layout (10 floats).  Writes origin o[3] and unit direction d[3]. */
+void orc_camera_ray(const void* cam, int width, int height, int x, int y,
+                    double* o, double* d);
+
+/* Renders the pixels listed in `pixels` (n_pixels indices y*W+x; NULL =
+ * every pixel).  Outputs are indexed like `pixels` (or by pixel when NULL):
+ *   rgb[3*i]      radiance (FP64)
+ *   prim[i]       primary hit prim id (sphere j -> j, triangle k -> ns+k,
+ *                 miss -> -1)
+ *   t[i]          primary hit distance (inf on a miss)
+ *   robust[i]     smallest decision margin in the pixel's path tree in units
+ *                 of the modelled FP32 uncertainty (>= 1: no decision is
+ *                 within reach of FP32 rounding)
+ *   counts        [3 + 3*(max_depth+1)] ray counts: totals of primary,
+ *                 shadow and secondary rays, then per depth (closest-hit
+ *                 rays, shadow rays, unused) - may be NULL
+ * mode: 0 recursive brute force, 1 recursive with the oracle BVH,
+ *       2 iterative (explicit per-depth ray lists, brute force).
+ * nthreads <= 0 uses all OpenMP threads.  Returns 0 on success. */
+int orc_render(const orc_scene* s, const void* cam, int width, int height,
+               int max_depth, int mode, const int64_t* pixels,
+               int64_t n_pixels, double* rgb, int32_t* prim, double* t,
+               double* robust, uint64_t* counts, int nthreads);
+
+/* Closest hit for n given FP32 rays (promoted to double), t in (tmin, inf).
+ * prim/t as above; robust as above for this single query, with the rays
+ * treated as exact (intersection rounding only). */
+int orc_closest_hits(const orc_scene* s, int64_t n, const float* o,
+                     const float* d, double tmin, int use_bvh, int32_t* prim,
+                     double* t, double* robust, int nthreads);
+
+/* Any hit with t in (tmin, tmax[i]) for n given FP32 rays. */
+int orc_any_hits(const orc_scene* s, int64_t n, const float* o,
+                 const float* d, double tmin, const float* tmax, int use_bvh,
+                 uint8_t* occluded, double* robust, int nthreads);
+
+/* Ray-sphere roots of Eq. 11-12 for one sphere; returns the number of real
+ * roots (0, 1 or 2), roots ascending in t[0..1]. */
+int orc_sphere_roots(const double* o, const double* d, const double* c,
+                     double r, double* t);
+
+/* Moller-Trumbore for one triangle: returns 1 on a hit (t > 0) with t, u, v. */
+int orc_triangle_hit(const double* o, const double* d, const double* v0,
+                     const double* v1, const double* v2, double* t, double* u,
+                     double* v);
+
+/* Fresnel-Schlick reflectance and the refracted direction for a unit d
+ * meeting a surface with unit normal n facing the ray (d.n < 0).  Returns
+ * 1 and writes R and the refracted unit direction, or 0 on total internal
+ * reflection (R = 1). */
+int orc_refract(const double* d, const double* n, double n1, double n2,
+                double* R, double* dt);
+
+/* ---- neural radiance cache oracle (FP64) ---------------------------- */
+
+/* Frequency encoding of a hit: 3 normalised position values, normal (3),
+ * view direction (3) and sin/cos(2^k pi x_hat) for k = 0..11 (72), i.e.
+ * 81 features, zero-padded to 96.  in: n x 9 (p, n, v), bbox: lo[3], hi[3]. */
+void orc_nrc_encode(int64_t n, const double* in, const double* bbox_lo,
+                    const double* bbox_hi, double* out96);
+
+/* MLP 96 -> 64 -> 64 -> 64 -> 64 -> 3, ReLU hidden, exp output.
+ * W: layer weights row-major [out][in] concatenated; B: biases.
+ * Layer sizes are fixed by `dims` (6 entries: 96,64,64,64,64,3). */
+void orc_mlp_forward(int64_t n, const double* x, const double* W,
+                     const double* B, double* y);
+
+/* Mean relative-L2 loss mean((y - t)^2 / (sg(y)^2 + 0.01)) over n x 3 and
+ * its gradients dW, dB (same layout as W, B).  Returns the loss. */
+double orc_mlp_loss_grad(int64_t n, const double* x, const double* target,
+                         const double* W, const double* B, double* dW,
+                         double* dB);
+
+/* One Adam step (bias-corrected), in place, on n parameters.  step >= 1. */
+void orc_adam(int64_t n, double* w, const double* g, double* m, double* v,
+              int64_t step, double lr, double beta1, double beta2, double eps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
