@@ -1,0 +1,303 @@
+"""Benchmark: Mrays/s of the B300 Whitted tracer on the 1080p / 123,904-triangle
+terrain scene at depth 5 (4 point lights, 60/25/15 % diffuse / mirror /
+dielectric icospheres), synthetic and seeded.
+
+One step = one pass of the whole hot path over the scene, inputs resident
+in HBM: SoA repacking of the geometry (device-to-device), the BVH build
+(Morton codes, radix sort, LBVH, binned-SAH top levels, SAH leaf
+collapsing) and the frame (primary rays, closest hit + shading, shadow
+rays, reflection / refraction rays to depth 5).  Rays counted: primary +
+shadow + secondary.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation
+of this method here) on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank renders its own replica of the frame
+(replicas only: the path needs no collective); value = all ranks' rays /
+the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Mrays/s at 1080p 100k-tri depth 5, plain vs radiance cache at relMSE ≤ 0.01"
+UNIT = "Mrays/s"
+# algorithmic FP32 operations per unit of work (counted from the math)
+OPS_NODE = 28     # two slab tests: 12 FFMA + 12 min/max + 4 compares
+OPS_TRI = 30      # Moller-Trumbore
+BYTES_NODE = 64
+BYTES_TRI = 48
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return p, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(sc, seconds_hint=15.0):
+    """Times the FP64 oracle (brute force, as it stands) on a bounded pixel
+    sample of the frame; returns (Mrays/s, sample description, cores)."""
+    import oracle as O
+    orc = O.OracleScene.from_scene(sc)
+    W, H = sc.width, sc.height
+    stride = 1031            # prime: an even spread of ~2000 pixels over the frame
+    pix = np.arange(0, W * H, stride)
+    t0 = time.perf_counter()
+    r = orc.render(sc.camera, W, H, sc.max_depth, mode="brute", pixels=pix)
+    dt = time.perf_counter() - t0
+    c = r["counts"]
+    rays = c["primary"] + c["shadow"] + c["secondary"]
+    cores = os.cpu_count()
+    return rays / dt / 1e6, f"brute force, every {stride}th pixel of the frame ({len(pix)} px, {rays} rays, " \
+                            f"{dt:.1f} s)", cores
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle on the host cores."""
+    from paper_1504_03151_b300 import scenes as S
+    if rank != 0:
+        return
+    sc = S.scene_terrain()
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; keep the timed steps bounded instead
+    import oracle as O
+    orc = O.OracleScene.from_scene(sc)
+    W, H = sc.width, sc.height
+    stride = 4099
+    times, rays = [], 0
+    for k in range(args.steps):
+        pix = np.arange(k % stride, W * H, stride)
+        t0 = time.perf_counter()
+        r = orc.render(sc.camera, W, H, sc.max_depth, mode="brute", pixels=pix)
+        times.append(time.perf_counter() - t0)
+        c = r["counts"]
+        rays += c["primary"] + c["shadow"] + c["secondary"]
+    total = sum(times)
+    value = rays / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "terrain 1920x1080, 123904 triangles, depth 5, 4 lights",
+                   "sample": f"each step: every {stride}th pixel (offset by the step index)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"brute force, every {stride}th pixel per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_1504_03151_b300 as rtb
+    from paper_1504_03151_b300 import build as rtb_build
+    from paper_1504_03151_b300 import scenes as S
+
+    rtb_build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    sc = S.scene_terrain()
+    W, H, D = sc.width, sc.height, sc.max_depth
+    scene = rtb.Scene(sc)
+    h = scene.handle
+    tri_bytes = sc.triangles.view(np.uint8).reshape(-1)
+    tri_dev = torch.from_numpy(tri_bytes.copy()).to(dev)             # resident input
+    tri_pin = torch.from_numpy(tri_bytes.copy()).pin_memory()        # host input for e2e
+    out = torch.empty(H * W * 3, device=dev, dtype=torch.float32)
+    out_pin = torch.empty(H * W * 3, dtype=torch.float32).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)   # > L2 (126 MB)
+    opts = rtb.make_options(background=sc.background)
+    opts_t = rtb.make_options(background=sc.background, flags=rtb.RT_FLAG_STAGE_TIMING)
+
+    def step(o=None):
+        rtb.rt_scene_update(h, None, tri_dev)
+        rtb.rt_bvh_build(h)
+        rtb.rt_render_ex(h, sc.camera, W, H, D, out, o or opts)
+
+    # rays per frame and algorithmic work (outside the timed region)
+    step()
+    st = rtb.rt_render_ex(h, sc.camera, W, H, D, out, rtb.make_options(background=sc.background), stats=True)
+    rays = st["primary"] + st["shadow"] + st["secondary"]
+    work = rtb.rt_render_ex(h, sc.camera, W, H, D, out,
+                            rtb.make_options(background=sc.background, flags=rtb.RT_FLAG_COUNT_WORK), stats=True)
+    info = rtb.rt_bvh_get_info(h)
+    assert rtb.rt_scene_sync(h) == rtb.RT_OK
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    trace_ms, shadow_ms = [], []
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()                       # L2 flush between steps (not timed)
+            ev[k][0].record(stream)
+            step(opts_t)
+            ev[k][1].record(stream)
+            _, a, b = rtb.rt_render_stage_times(h)    # waits for this step's last kernel
+            trace_ms.append(a)
+            shadow_ms.append(b)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * rays / (ms * 1e3)        # Mrays/s over all ranks
+
+    # end to end through the public API: H2D of the geometry from pinned
+    # memory, build, render, D2H of the image into pinned memory
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rtb.rt_scene_update(h, None, tri_pin)
+        rtb.rt_bvh_build(h)
+        rtb.rt_render_host(h, sc.camera, W, H, D, out_pin, opts)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = sorted(e2e_ms)[len(e2e_ms) // 2]
+    e2e_value = world * rays / (e2e_ms * 1e3)
+
+    # roofline of the dominant kernel class
+    pk, pk_kind = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2032.0)
+    alu_peak = 148 * 128 * sm_mhz * 1e6 / 1e12       # FP32 lanes x clock: Tops/s (one op per lane per clock)
+    tr = sum(trace_ms) / len(trace_ms)
+    sh = sum(shadow_ms) / len(shadow_ms)
+    cls, kms = (0, tr) if tr >= sh else (1, sh)
+    ops = work["node_visits"][cls] * OPS_NODE + work["prim_tests"][cls] * OPS_TRI
+    achieved = ops / (kms * 1e-3) / 1e12
+    launches_per_step = info["build_launches"] + 1 + 2 + st["launches"] + 2
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, cores = cpu_oracle_sample(sc)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "terrain 1920x1080, 123904 triangles (fBm 256x192 + 20 L3 icospheres), "
+                                   "depth 5, 4 point lights, materials 60/25/15",
+                       "rays_per_step": rays, "primary": st["primary"], "shadow": st["shadow"],
+                       "secondary": st["secondary"], "l2": "flushed between steps (256 MB write)",
+                       "step": "repack + BVH build + render", "parallelism": f"replicas x{world}",
+                       "bvh": {k: info[k] for k in ("n_nodes", "max_depth", "sah_cost", "sah_cost_lbvh")}},
+            "roofline": {"bound": "alu", "kernel": "closest-hit+shade" if cls == 0 else "any-hit shadow",
+                         "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
+                         "traffic": None, "peak_source": f"148 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
+                                                         f"({pk_kind} clock)",
+                         "kernel_ms": kms, "alg_ops": ops},
+            "stage_ms": {"trace": tr, "shadow": sh, "step": ms},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tri_bytes.nbytes),
+                    "d2h_bytes_per_step": int(H * W * 3 * 4), "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    scene.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

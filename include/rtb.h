@@ -1,0 +1,222 @@
+/*
+ * rtb.h - C ABI of the B300 (sm_103a) Whitted ray tracer, librtb.so.
+ *
+ * The method is that of "Massively Parallel Ray Tracing Algorithm Using GPU"
+ * (Qin, Lin, Huang): one thread per ray, the recursion over reflection /
+ * refraction turned into an iteration whose trip count is the recursion
+ * depth (Sec. IV.A), one shadow ray per light at every hit (Alg. 1), the
+ * ray-sphere quadratic of Eq. 9-12 and shading from Eq. 6-8.  Triangles, the
+ * BVH and the wavefront queues extend it.
+ *
+ * Conventions shared by every call:
+ *   - Primitive ids: sphere i -> i, triangle j -> n_spheres + j; -1 = miss.
+ *   - Images are H x W x 3 float32, row-major, row 0 at the top.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Calls are stream-ordered.  Argument errors are returned at once.
+ *     Errors raised inside kernels (queue overflow, traversal limit) are
+ *     latched in the scene and returned by the next rt_scene_sync (or by
+ *     rt_render_ex when it is given a stats pointer, which syncs).
+ *   - rt_last_error() gives a message for the last non-OK status of the
+ *     calling thread.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  Device
+ *     buffers passed in (out_rgb, AOVs, ray arrays) are owned by the caller
+ *     and must stay alive until the stream reaches the call.
+ */
+#ifndef RTB_H
+#define RTB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTB_ABI_VERSION 1
+#define RT_MAX_DEPTH 16
+
+typedef enum rt_status {
+  RT_OK = 0,
+  RT_ERR_INVALID_ARG = 1,     /* bad pointer, size, NaN/Inf, radius <= 0, bad material index ... */
+  RT_ERR_OOM = 2,             /* a device or pinned allocation failed */
+  RT_ERR_CUDA = 3,            /* any other CUDA runtime error */
+  RT_ERR_NOT_BUILT = 4,       /* BVH traversal requested before rt_bvh_build */
+  RT_ERR_QUEUE_OVERFLOW = 5,  /* a ray queue was full: rays were dropped */
+  RT_ERR_TRAVERSAL_LIMIT = 6, /* a ray hit the traversal step cap or the stack depth */
+  RT_ERR_UNSUPPORTED = 7      /* a valid request this build does not handle */
+} rt_status;
+
+/* Sphere of Eq. 9: |p - center|^2 = radius^2.  radius > 0. */
+typedef struct rt_sphere {
+  float center[3];
+  float radius;
+  uint32_t material;          /* index into the material array */
+} rt_sphere;
+
+/* Triangle (v0, v1, v2); two-sided; its geometric normal is
+ * normalize((v1-v0) x (v2-v0)).  Degenerate triangles are never hit. */
+typedef struct rt_triangle {
+  float v0[3], v1[3], v2[3];
+  uint32_t material;
+} rt_triangle;
+
+enum { RT_MAT_DIFFUSE = 0, RT_MAT_MIRROR = 1, RT_MAT_DIELECTRIC = 2 };
+
+/* Surface model (the f_r and L_e of Eq. 7-8):
+ *   DIFFUSE    : Lambert (albedo) + Phong (ks, shininess); reflectivity ignored.
+ *   MIRROR     : (1 - reflectivity) x the DIFFUSE local term, plus a
+ *                reflection ray of weight reflectivity.
+ *   DIELECTRIC : no local term; Fresnel-Schlick reflection ray (weight R)
+ *                and Snell refraction ray (weight 1 - R; none on total
+ *                internal reflection); index of refraction `ior`.
+ *   emission   : L_e, added at every hit. */
+typedef struct rt_material {
+  uint32_t kind;
+  float albedo[3];
+  float ks;
+  float shininess;
+  float reflectivity;
+  float ior;
+  float emission[3];
+} rt_material;
+
+/* Point light: no distance fall-off; intensity per channel. */
+typedef struct rt_point_light {
+  float position[3];
+  float intensity[3];
+} rt_point_light;
+
+/* Pinhole camera, vertical field of view in degrees, aspect W/H,
+ * pixel centres at +0.5. */
+typedef struct rt_camera {
+  float eye[3], look_at[3], up[3];
+  float vfov_deg;
+} rt_camera;
+
+enum {
+  RT_FLAG_STAGE_TIMING = 1,   /* record per-stage CUDA events (stats.ms_*) */
+  RT_FLAG_COUNT_WORK = 2,     /* count node visits / primitive tests (slower kernels) */
+  RT_FLAG_NO_GRAPH = 4        /* launch the kernels directly, no CUDA graph */
+};
+
+typedef struct rt_render_options {
+  int32_t use_bvh;            /* 1: BVH traversal; 0: test every primitive (Alg. 1's loop) */
+  int32_t flags;              /* RT_FLAG_* */
+  float background[3];        /* radiance of a miss */
+  float eps_scale;            /* origin offset eps = eps_scale * max(1, |p|_inf) */
+  int64_t queue_capacity;     /* rays per secondary / shadow queue; 0 = default */
+  int64_t traversal_cap;      /* loop steps per ray before RT_ERR_TRAVERSAL_LIMIT; 0 = default */
+} rt_render_options;
+
+/* Defaults: use_bvh 1, flags 0, background 0.1, eps_scale 1e-4,
+ * queue_capacity max(2*W*H, 65536) closest-hit rays (shadow queue:
+ * n_lights x that), traversal_cap 4 * nodes + 64. */
+void rt_render_options_default(rt_render_options* opt);
+
+typedef struct rt_render_stats {
+  uint64_t primary, shadow, secondary;           /* rays traced per class */
+  uint64_t rays_per_depth[RT_MAX_DEPTH + 1];     /* closest-hit rays at depth d */
+  uint64_t shadow_per_depth[RT_MAX_DEPTH + 1];   /* shadow rays cast from depth-d hits */
+  uint64_t hits_per_depth[RT_MAX_DEPTH + 1];
+  uint64_t node_visits[2], prim_tests[2];        /* [closest, any]; RT_FLAG_COUNT_WORK only */
+  float ms_total;                                /* RT_FLAG_STAGE_TIMING only */
+  float ms_trace;                                /* closest-hit + shade kernels */
+  float ms_shadow;                               /* any-hit kernels */
+  int32_t launches;                              /* kernels this render launched */
+} rt_render_stats;
+
+typedef struct rt_bvh_info {
+  int64_t n_prims;
+  int64_t n_nodes;            /* internal nodes reachable from the root */
+  int64_t root;               /* index of the root node in the exported layout */
+  int32_t max_depth;          /* deepest leaf (root = 0) */
+  int32_t max_leaf_size;
+  double sah_cost;            /* SAH cost (C_trav = C_isect = 1) of the tree */
+  double sah_cost_lbvh;       /* same, of the plain LBVH before refinement */
+  float build_ms;             /* last build, when timed */
+  int32_t build_launches;     /* kernels (and memsets) the last build issued */
+} rt_bvh_info;
+
+typedef struct rt_scene rt_scene;
+
+int rt_abi_version(void);
+const char* rt_last_error(void);
+
+/* Copies the host arrays to the device and packs them into the device
+ * layout.  Spheres and triangles may be empty (not both NULL with n > 0).
+ * Validates every value: RT_ERR_INVALID_ARG on NaN/Inf, radius <= 0 or a
+ * material index >= n_materials.  Synchronous. */
+rt_status rt_scene_create(const rt_sphere* spheres, size_t n_spheres, const rt_triangle* triangles,
+                          size_t n_triangles, const rt_material* materials, size_t n_materials,
+                          const rt_point_light* lights, size_t n_lights, rt_scene** out);
+
+/* Replaces the geometry with new arrays of the same counts (a moving
+ * scene).  The arrays may live in host memory (pinned memory makes the
+ * copy asynchronous) or in device memory; the copy and the on-device
+ * repacking run on `stream`.  The BVH must be rebuilt afterwards.
+ * Values are not validated (use rt_scene_create for checked input). */
+rt_status rt_scene_update(rt_scene* s, const rt_sphere* spheres, const rt_triangle* triangles,
+                          void* stream);
+
+/* Builds the BVH on the device: 30-bit Morton codes, radix sort, LBVH
+ * hierarchy, bottom-up boxes, binned-SAH rebuild of the top levels and
+ * SAH leaf collapsing.  Stream-ordered; rebuild allowed at any time. */
+rt_status rt_bvh_build(rt_scene* s, void* stream);
+
+/* Fills *info (syncs the stream). */
+rt_status rt_bvh_get_info(rt_scene* s, rt_bvh_info* info, void* stream);
+
+/* Copies the traversal layout to host buffers (syncs), for inspection:
+ * nodes: n_nodes x 16 floats (two child boxes + two child links, see
+ * DESIGN), prim_order: n_prims int32 (leaf order -> primitive id),
+ * morton: n_prims uint32 sorted codes.  Any pointer may be NULL. */
+rt_status rt_bvh_export(rt_scene* s, float* nodes, int64_t nodes_capacity, int32_t* prim_order,
+                        uint32_t* morton, void* stream);
+
+/* Renders one frame into out_rgb_device (H*W*3 float32, overwritten). */
+rt_status rt_render(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
+                    float* out_rgb_device, void* stream);
+
+/* rt_render with options (NULL = defaults), optional primary-ray AOVs
+ * (device, H*W: hit primitive id / hit distance, inf on a miss) and
+ * optional stats (host; filled after a stream sync). */
+rt_status rt_render_ex(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
+                       float* out_rgb_device, const rt_render_options* opt, int32_t* aov_prim,
+                       float* aov_t, rt_render_stats* stats, void* stream);
+
+/* Stage times (ms) of the last frame rendered with RT_FLAG_STAGE_TIMING,
+ * from CUDA events recorded on its stream: the whole frame, the
+ * closest-hit + shade kernels and the shadow kernels.  Waits for that
+ * frame's last event only. */
+rt_status rt_render_stage_times(rt_scene* s, float* ms_total, float* ms_trace, float* ms_shadow);
+
+/* rt_render into a HOST buffer: renders into scene-owned device memory,
+ * copies back on `stream` and waits for it. */
+rt_status rt_render_host(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
+                         float* out_rgb_host, const rt_render_options* opt, void* stream);
+
+/* The primary rays rt_render traces (device arrays, H*W*3 float each,
+ * pixel-major): the same device function generates them. */
+rt_status rt_camera_rays(const rt_camera* cam, int width, int height, float* o_device,
+                         float* d_device, void* stream);
+
+/* Closest hit for n rays (device arrays n*3 float), t in (tmin, inf):
+ * prim id (or -1) and t (inf on a miss).  use_bvh as in the options. */
+rt_status rt_trace_closest(rt_scene* s, const float* o_device, const float* d_device, int64_t n,
+                           float tmin, int use_bvh, int32_t* prim_device, float* t_device,
+                           void* stream);
+
+/* Any hit with t in (tmin, tmax[i]) for n rays: occluded[i] = 0/1. */
+rt_status rt_trace_any(rt_scene* s, const float* o_device, const float* d_device,
+                       const float* tmax_device, int64_t n, float tmin, int use_bvh,
+                       uint8_t* occluded_device, void* stream);
+
+/* Waits for `stream` and returns (and clears) the latched kernel error. */
+rt_status rt_scene_sync(rt_scene* s, void* stream);
+
+rt_status rt_scene_destroy(rt_scene* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTB_H */

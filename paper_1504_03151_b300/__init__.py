@@ -1,0 +1,328 @@
+"""Python binding of librtb.so, the sm_103a Whitted ray tracer.
+
+Argument marshalling only: every step of the tracer runs in the library's
+CUDA kernels.  The functions carry the C ABI's names (include/rtb.h).
+Device buffers are torch CUDA tensors (or raw device pointers as ints);
+host arrays are numpy arrays in the ABI's struct layouts (see ``scenes``).
+There is no CPU fallback: if librtb.so is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "RtError", "lib", "rt_abi_version", "rt_last_error", "rt_render_options_default",
+    "rt_scene_create", "rt_scene_update", "rt_bvh_build", "rt_bvh_get_info", "rt_bvh_export",
+    "rt_render", "rt_render_ex", "rt_render_host", "rt_camera_rays", "rt_trace_closest",
+    "rt_trace_any", "rt_scene_sync", "rt_scene_destroy", "rt_render_stage_times", "Scene",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librtb.so")
+
+RT_OK = 0
+RT_ERR_INVALID_ARG = 1
+RT_ERR_OOM = 2
+RT_ERR_CUDA = 3
+RT_ERR_NOT_BUILT = 4
+RT_ERR_QUEUE_OVERFLOW = 5
+RT_ERR_TRAVERSAL_LIMIT = 6
+RT_ERR_UNSUPPORTED = 7
+STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_OOM", 3: "RT_ERR_CUDA", 4: "RT_ERR_NOT_BUILT",
+                5: "RT_ERR_QUEUE_OVERFLOW", 6: "RT_ERR_TRAVERSAL_LIMIT", 7: "RT_ERR_UNSUPPORTED"}
+
+RT_FLAG_STAGE_TIMING = 1
+RT_FLAG_COUNT_WORK = 2
+RT_FLAG_NO_GRAPH = 4
+RT_MAX_DEPTH = 16
+
+
+class RtError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class rt_camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("look_at", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("vfov_deg", ctypes.c_float)]
+
+
+class rt_render_options(ctypes.Structure):
+    _fields_ = [("use_bvh", ctypes.c_int32), ("flags", ctypes.c_int32), ("background", ctypes.c_float * 3),
+                ("eps_scale", ctypes.c_float), ("queue_capacity", ctypes.c_int64),
+                ("traversal_cap", ctypes.c_int64)]
+
+
+class rt_render_stats(ctypes.Structure):
+    _fields_ = [("primary", ctypes.c_uint64), ("shadow", ctypes.c_uint64), ("secondary", ctypes.c_uint64),
+                ("rays_per_depth", ctypes.c_uint64 * (RT_MAX_DEPTH + 1)),
+                ("shadow_per_depth", ctypes.c_uint64 * (RT_MAX_DEPTH + 1)),
+                ("hits_per_depth", ctypes.c_uint64 * (RT_MAX_DEPTH + 1)),
+                ("node_visits", ctypes.c_uint64 * 2), ("prim_tests", ctypes.c_uint64 * 2),
+                ("ms_total", ctypes.c_float), ("ms_trace", ctypes.c_float), ("ms_shadow", ctypes.c_float),
+                ("launches", ctypes.c_int32)]
+
+
+class rt_bvh_info(ctypes.Structure):
+    _fields_ = [("n_prims", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("root", ctypes.c_int64),
+                ("max_depth", ctypes.c_int32),
+                ("max_leaf_size", ctypes.c_int32), ("sah_cost", ctypes.c_double),
+                ("sah_cost_lbvh", ctypes.c_double), ("build_ms", ctypes.c_float),
+                ("build_launches", ctypes.c_int32)]
+
+
+_lib = None
+P = ctypes.c_void_p
+
+
+def lib():
+    """Loads librtb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1504_03151_b300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        I, I64, F, S = ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+        sigs = {
+            "rt_abi_version": (I, []),
+            "rt_last_error": (ctypes.c_char_p, []),
+            "rt_render_options_default": (None, [P]),
+            "rt_scene_create": (I, [P, S, P, S, P, S, P, S, P]),
+            "rt_scene_update": (I, [P, P, P, P]),
+            "rt_bvh_build": (I, [P, P]),
+            "rt_bvh_get_info": (I, [P, P, P]),
+            "rt_bvh_export": (I, [P, P, I64, P, P, P]),
+            "rt_render": (I, [P, P, I, I, I, P, P]),
+            "rt_render_ex": (I, [P, P, I, I, I, P, P, P, P, P, P]),
+            "rt_render_host": (I, [P, P, I, I, I, P, P, P]),
+            "rt_render_stage_times": (I, [P, P, P, P]),
+            "rt_camera_rays": (I, [P, I, I, P, P, P]),
+            "rt_trace_closest": (I, [P, P, P, I64, F, I, P, P, P]),
+            "rt_trace_any": (I, [P, P, P, P, I64, F, I, P, P]),
+            "rt_scene_sync": (I, [P, P]),
+            "rt_scene_destroy": (I, [P]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _check(status):
+    if status != RT_OK:
+        raise RtError(status, lib().rt_last_error().decode())
+    return status
+
+
+def _dptr(x):
+    """Device pointer of a torch CUDA tensor (or an int); None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("expected a C-contiguous array")
+        return a.ctypes.data
+    return a.data_ptr()   # a torch CPU tensor (pinned or not)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_camera(cam) -> rt_camera:
+    """rt_camera from a CAMERA_DTYPE record (or an rt_camera)."""
+    if isinstance(cam, rt_camera):
+        return cam
+    c = np.asarray(cam).reshape(-1)[0]
+    out = rt_camera()
+    out.eye[:] = [float(v) for v in c["eye"]]
+    out.look_at[:] = [float(v) for v in c["look_at"]]
+    out.up[:] = [float(v) for v in c["up"]]
+    out.vfov_deg = float(c["vfov_deg"])
+    return out
+
+
+def rt_render_options_default() -> rt_render_options:
+    o = rt_render_options()
+    lib().rt_render_options_default(ctypes.byref(o))
+    return o
+
+
+def make_options(use_bvh=True, flags=0, background=(0.1, 0.1, 0.1), eps_scale=1e-4, queue_capacity=0,
+                 traversal_cap=0) -> rt_render_options:
+    o = rt_render_options_default()
+    o.use_bvh = int(bool(use_bvh))
+    o.flags = int(flags)
+    o.background[:] = [float(v) for v in background]
+    o.eps_scale = float(eps_scale)
+    o.queue_capacity = int(queue_capacity)
+    o.traversal_cap = int(traversal_cap)
+    return o
+
+
+def stats_dict(s: rt_render_stats, max_depth: int) -> dict:
+    n = max_depth + 1
+    return {
+        "primary": s.primary, "shadow": s.shadow, "secondary": s.secondary,
+        "rays_per_depth": list(s.rays_per_depth[:n]), "shadow_per_depth": list(s.shadow_per_depth[:n]),
+        "hits_per_depth": list(s.hits_per_depth[:n]),
+        "node_visits": list(s.node_visits), "prim_tests": list(s.prim_tests),
+        "ms_total": s.ms_total, "ms_trace": s.ms_trace, "ms_shadow": s.ms_shadow, "launches": s.launches,
+    }
+
+
+# ---------------------------------------------------------------------------
+# the ABI, call by call
+# ---------------------------------------------------------------------------
+def rt_abi_version() -> int:
+    return lib().rt_abi_version()
+
+
+def rt_last_error() -> str:
+    return lib().rt_last_error().decode()
+
+
+def rt_scene_create(spheres, triangles, materials, lights) -> int:
+    h = P()
+    _check(lib().rt_scene_create(_hptr(spheres), len(spheres), _hptr(triangles), len(triangles),
+                                 _hptr(materials), len(materials), _hptr(lights), len(lights), ctypes.byref(h)))
+    return h.value
+
+
+def rt_scene_update(scene, spheres, triangles, stream=None):
+    """spheres / triangles: numpy arrays, torch CPU tensors or torch CUDA tensors (raw struct bytes)."""
+    def ptr(a):
+        if a is None:
+            return None
+        if hasattr(a, "is_cuda") and a.is_cuda:
+            return _dptr(a)
+        return _hptr(a)
+    _check(lib().rt_scene_update(scene, ptr(spheres), ptr(triangles), _stream(stream)))
+
+
+def rt_bvh_build(scene, stream=None):
+    _check(lib().rt_bvh_build(scene, _stream(stream)))
+
+
+def rt_bvh_get_info(scene, stream=None) -> dict:
+    info = rt_bvh_info()
+    _check(lib().rt_bvh_get_info(scene, ctypes.byref(info), _stream(stream)))
+    return {k: getattr(info, k) for k, _ in rt_bvh_info._fields_}
+
+
+def rt_bvh_export(scene, n_prims, n_node_slots, stream=None):
+    nodes = np.zeros((n_node_slots, 16), np.float32)
+    order = np.zeros(n_prims, np.int32)
+    morton = np.zeros(n_prims, np.uint32)
+    _check(lib().rt_bvh_export(scene, nodes.ctypes.data, n_node_slots, order.ctypes.data, morton.ctypes.data,
+                               _stream(stream)))
+    return nodes, order, morton
+
+
+def rt_render(scene, camera, width, height, max_depth, out_rgb, stream=None):
+    cam = make_camera(camera)
+    _check(lib().rt_render(scene, ctypes.byref(cam), width, height, max_depth, _dptr(out_rgb), _stream(stream)))
+
+
+def rt_render_ex(scene, camera, width, height, max_depth, out_rgb, options=None, aov_prim=None, aov_t=None,
+                 stats=False, stream=None):
+    cam = make_camera(camera)
+    st = rt_render_stats() if stats else None
+    _check(lib().rt_render_ex(scene, ctypes.byref(cam), width, height, max_depth, _dptr(out_rgb),
+                              ctypes.byref(options) if options is not None else None, _dptr(aov_prim),
+                              _dptr(aov_t), ctypes.byref(st) if st is not None else None, _stream(stream)))
+    return stats_dict(st, max_depth) if st is not None else None
+
+
+def rt_render_host(scene, camera, width, height, max_depth, out_host, options=None, stream=None):
+    cam = make_camera(camera)
+    _check(lib().rt_render_host(scene, ctypes.byref(cam), width, height, max_depth, _hptr(out_host),
+                                ctypes.byref(options) if options is not None else None, _stream(stream)))
+
+
+def rt_render_stage_times(scene):
+    """(ms_total, ms_trace, ms_shadow) of the last frame rendered with RT_FLAG_STAGE_TIMING."""
+    a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    _check(lib().rt_render_stage_times(scene, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def rt_camera_rays(camera, width, height, o_dev, d_dev, stream=None):
+    cam = make_camera(camera)
+    _check(lib().rt_camera_rays(ctypes.byref(cam), width, height, _dptr(o_dev), _dptr(d_dev), _stream(stream)))
+
+
+def rt_trace_closest(scene, o_dev, d_dev, n, tmin, use_bvh, prim_dev, t_dev, stream=None):
+    _check(lib().rt_trace_closest(scene, _dptr(o_dev), _dptr(d_dev), n, tmin, int(use_bvh), _dptr(prim_dev),
+                                  _dptr(t_dev), _stream(stream)))
+
+
+def rt_trace_any(scene, o_dev, d_dev, tmax_dev, n, tmin, use_bvh, occluded_dev, stream=None):
+    _check(lib().rt_trace_any(scene, _dptr(o_dev), _dptr(d_dev), _dptr(tmax_dev), n, tmin, int(use_bvh),
+                              _dptr(occluded_dev), _stream(stream)))
+
+
+def rt_scene_sync(scene, stream=None) -> int:
+    """Waits for the stream; returns the latched kernel status (does not raise)."""
+    return lib().rt_scene_sync(scene, _stream(stream))
+
+
+def rt_scene_destroy(scene):
+    _check(lib().rt_scene_destroy(scene))
+
+
+class Scene:
+    """Owns an rt_scene handle built from a scenes.Scene-like object."""
+
+    def __init__(self, sc):
+        self.sc = sc
+        self.handle = rt_scene_create(sc.spheres, sc.triangles, sc.materials, sc.lights)
+
+    def build(self, stream=None):
+        rt_bvh_build(self.handle, stream)
+        return self
+
+    def render(self, out_rgb, options=None, aov_prim=None, aov_t=None, stats=False, camera=None, width=None,
+               height=None, max_depth=None, stream=None):
+        sc = self.sc
+        return rt_render_ex(self.handle, sc.camera if camera is None else camera, width or sc.width,
+                            height or sc.height, sc.max_depth if max_depth is None else max_depth, out_rgb,
+                            options, aov_prim, aov_t, stats, stream)
+
+    def close(self):
+        if self.handle:
+            rt_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1127 @@
+// bvh.cu - on-device BVH build: Morton codes, radix sort, LBVH hierarchy,
+// bottom-up boxes with SAH costs, binned-SAH rebuild of the top levels over
+// Morton clusters, SAH leaf collapsing, traversal layout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+#include "rtb_internal.cuh"
+
+namespace rtb {
+
+constexpr int kSortTile = 4096;     // keys per radix-sort tile (256 threads x 16)
+constexpr int kScanBlock = 4096;    // elements per scan block (1024 threads x 4)
+constexpr int kTopBins = 16;        // SAH bins per axis for the top-level rebuild
+constexpr int kTopMaxLevels = 64;   // launches of the level kernel (empty ones return at once)
+constexpr int kTopForceMedian = 32; // from this level on, split segments at the middle: with at
+                                    // most 2^28 clusters every segment is done by level 60
+
+// Device-side build results, read by rt_bvh_get_info.
+struct BuildInfo {
+  int height;          // deepest internal-node chain (stack entries needed <= height)
+  float sah;           // SAH cost of the final tree
+  float sah_lbvh;      // SAH cost of the plain LBVH (single-primitive leaves)
+  int n_clusters;
+  int n_top;           // top nodes emitted by the SAH rebuild
+  int root;
+  int max_leaf;
+  int pad;
+};
+
+// Scratch carved out of one allocation.
+struct BuildScratch {
+  float4 *aabb_lo, *aabb_hi;     // per primitive (id order)
+  unsigned *keys0, *vals0, *keys1, *vals1;
+  unsigned* hist;                // 256 x tiles
+  unsigned* partials;            // scan partials
+  int *lch, *rch, *parent, *leaf_parent, *flags;
+  int2* range;
+  float4 *node_lo, *node_hi;     // LBVH internal boxes; lo.w = SAH cost, hi.w = meta bits
+  float* cost_lbvh;
+  int* cent_bounds;              // 6 ordered ints
+  // top-level rebuild
+  int *clu_a, *clu_b;            // cluster ids (ping-pong)
+  int* clu_link;                 // per cluster: its link (internal LBVH node or leaf link)
+  float4 *clu_lo, *clu_hi;       // per cluster box; lo.w = prim count; hi.w = height
+  int4 *seg_a, *seg_b;           // active segments: (begin, end, parent slot, node id)
+  int* seg_count;                // [kTopMaxLevels + 1]
+  int* top_count;
+  float4 *top_lo, *top_hi;       // boxes of top nodes (for their parent's child box)
+  int* top_height;
+  BuildInfo* info;
+};
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------------------
+// ordered-int encoding of floats for atomic min / max
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int f2o(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ float area(float4 lo, float4 hi) {
+  float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+  if (!(dx >= 0.f) || !(dy >= 0.f) || !(dz >= 0.f)) return 0.f;
+  return 2.f * (dx * dy + dy * dz + dz * dx);
+}
+
+// Grows a box by a few ulps so that the slab test never cuts off a
+// primitive that lies on its face.
+__device__ __forceinline__ float pad_lo(float x) { return x - fabsf(x) * 2.4e-7f - 1e-30f; }
+__device__ __forceinline__ float pad_hi(float x) { return x + fabsf(x) * 2.4e-7f + 1e-30f; }
+
+// ---------------------------------------------------------------------------
+// 1. primitive boxes and the centroid bounds
+// ---------------------------------------------------------------------------
+__global__ void k_init_bounds(int* cb) {
+  int t = threadIdx.x;
+  if (t < 3) cb[t] = f2o(INFINITY);
+  else if (t < 6) cb[t] = f2o(-INFINITY);
+}
+
+__global__ void k_prim_bounds(const float4* __restrict__ prims, int n, float4* __restrict__ lo_out,
+                              float4* __restrict__ hi_out, int* __restrict__ cb) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float cx = INFINITY, cy = INFINITY, cz = INFINITY, Cx = -INFINITY, Cy = -INFINITY, Cz = -INFINITY;
+  if (i < n) {
+    float4 r0 = prims[3 * (size_t)i], r1 = prims[3 * (size_t)i + 1], r2 = prims[3 * (size_t)i + 2];
+    float4 lo, hi;
+    if (__float_as_int(r0.w) == kKindSphere) {
+      float r = r1.x;
+      lo = make_float4(r0.x - r, r0.y - r, r0.z - r, 0.f);
+      hi = make_float4(r0.x + r, r0.y + r, r0.z + r, 0.f);
+    } else {
+      float ax = r0.x + r1.x, ay = r0.y + r1.y, az = r0.z + r1.z;
+      float bx = r0.x + r2.x, by = r0.y + r2.y, bz = r0.z + r2.z;
+      lo = make_float4(fminf(r0.x, fminf(ax, bx)), fminf(r0.y, fminf(ay, by)), fminf(r0.z, fminf(az, bz)), 0.f);
+      hi = make_float4(fmaxf(r0.x, fmaxf(ax, bx)), fmaxf(r0.y, fmaxf(ay, by)), fmaxf(r0.z, fmaxf(az, bz)), 0.f);
+    }
+    lo = make_float4(pad_lo(lo.x), pad_lo(lo.y), pad_lo(lo.z), 0.f);
+    hi = make_float4(pad_hi(hi.x), pad_hi(hi.y), pad_hi(hi.z), 0.f);
+    lo_out[i] = lo;
+    hi_out[i] = hi;
+    cx = Cx = 0.5f * (lo.x + hi.x);
+    cy = Cy = 0.5f * (lo.y + hi.y);
+    cz = Cz = 0.5f * (lo.z + hi.z);
+  }
+  // warp reduce, then one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) {
+    cx = fminf(cx, __shfl_xor_sync(0xffffffffu, cx, o));
+    cy = fminf(cy, __shfl_xor_sync(0xffffffffu, cy, o));
+    cz = fminf(cz, __shfl_xor_sync(0xffffffffu, cz, o));
+    Cx = fmaxf(Cx, __shfl_xor_sync(0xffffffffu, Cx, o));
+    Cy = fmaxf(Cy, __shfl_xor_sync(0xffffffffu, Cy, o));
+    Cz = fmaxf(Cz, __shfl_xor_sync(0xffffffffu, Cz, o));
+  }
+  if ((threadIdx.x & 31) == 0 && cx <= Cx) {
+    atomicMin(&cb[0], f2o(cx));
+    atomicMin(&cb[1], f2o(cy));
+    atomicMin(&cb[2], f2o(cz));
+    atomicMax(&cb[3], f2o(Cx));
+    atomicMax(&cb[4], f2o(Cy));
+    atomicMax(&cb[5], f2o(Cz));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. 30-bit Morton codes: 10 bits per axis of the centroid, normalised to
+//    the centroid bounds, bits interleaved x y z from the top.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned spread10(unsigned v) {
+  // places bit k of v at bit 3k
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__device__ __forceinline__ unsigned quantize10(float c, float lo, float hi) {
+  float ext = hi - lo;
+  float f = ext > 0.f ? (c - lo) / ext : 0.5f;
+  int q = (int)(f * 1024.0f);
+  return (unsigned)min(max(q, 0), 1023);
+}
+
+__global__ void k_morton(const float4* __restrict__ lo, const float4* __restrict__ hi, int n,
+                         const int* __restrict__ cb, unsigned* __restrict__ keys, unsigned* __restrict__ vals) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 a = lo[i], b = hi[i];
+  float cx = 0.5f * (a.x + b.x), cy = 0.5f * (a.y + b.y), cz = 0.5f * (a.z + b.z);
+  unsigned qx = quantize10(cx, o2f(cb[0]), o2f(cb[3]));
+  unsigned qy = quantize10(cy, o2f(cb[1]), o2f(cb[4]));
+  unsigned qz = quantize10(cz, o2f(cb[2]), o2f(cb[5]));
+  keys[i] = (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
+  vals[i] = (unsigned)i;
+}
+
+// ---------------------------------------------------------------------------
+// 3. LSD radix sort of (key, value) pairs, 8 bits a pass, stable.
+// ---------------------------------------------------------------------------
+__global__ void k_sort_hist(const unsigned* __restrict__ keys, int n, int shift, unsigned* __restrict__ hist,
+                            int tiles) {
+  __shared__ unsigned h[256];
+  int t = threadIdx.x;
+  h[t] = 0;
+  __syncthreads();
+  size_t base = (size_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int r = 0; r < kSortTile / 256; ++r) {
+    size_t idx = base + (size_t)r * 256 + t;
+    if (idx < (size_t)n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(size_t)t * tiles + blockIdx.x] = h[t];
+}
+
+// Exclusive scan, block level: 1024 threads x 4 elements.  Writes the block
+// total to partials[blockIdx.x].
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned v, int lane) {
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned x = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += x;
+  }
+  return v;
+}
+
+__device__ unsigned block_excl_scan_1024(unsigned v, unsigned* sw, unsigned& total) {
+  int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  unsigned inc = warp_incl_scan(v, lane);
+  if (lane == 31) sw[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned s = sw[lane];
+    unsigned si = warp_incl_scan(s, lane);
+    sw[lane] = si - s;
+    if (lane == 31) sw[32] = si;
+  }
+  __syncthreads();
+  unsigned r = inc - v + sw[w];
+  total = sw[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_block(unsigned* __restrict__ data, size_t m, unsigned* __restrict__ partials) {
+  __shared__ unsigned sw[33];
+  size_t base = (size_t)blockIdx.x * kScanBlock + (size_t)threadIdx.x * 4;
+  unsigned a[4], s = 0;
+  for (int k = 0; k < 4; ++k) {
+    a[k] = base + k < m ? data[base + k] : 0u;
+    s += a[k];
+  }
+  unsigned total;
+  unsigned ex = block_excl_scan_1024(s, sw, total);
+  for (int k = 0; k < 4; ++k) {
+    if (base + k < m) data[base + k] = ex;
+    ex += a[k];
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+__global__ void k_scan_partials(unsigned* __restrict__ partials, int np) {
+  __shared__ unsigned sw[33];
+  unsigned carry = 0;
+  for (int base = 0; base < np; base += 1024) {
+    int i = base + threadIdx.x;
+    unsigned v = i < np ? partials[i] : 0u;
+    unsigned total;
+    unsigned ex = block_excl_scan_1024(v, sw, total);
+    if (i < np) partials[i] = ex + carry;
+    carry += total;
+  }
+}
+
+__global__ void k_scan_add(unsigned* __restrict__ data, size_t m, const unsigned* __restrict__ partials) {
+  unsigned add = partials[blockIdx.x];
+  size_t base = (size_t)blockIdx.x * kScanBlock + (size_t)threadIdx.x * 4;
+  for (int k = 0; k < 4; ++k)
+    if (base + k < m) data[base + k] += add;
+}
+
+// Stable scatter: the tile's keys are ranked in index order, 256 at a time;
+// within a warp, keys with equal digits are found with match.any.
+__global__ void __launch_bounds__(256) k_sort_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
+                                                      unsigned* __restrict__ kout, unsigned* __restrict__ vout, int n,
+                                                      int shift, const unsigned* __restrict__ offs, int tiles) {
+  __shared__ unsigned base[256];
+  __shared__ unsigned wcnt[8][256];
+  int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  base[t] = offs[(size_t)t * tiles + blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) wcnt[k][t] = 0;
+  __syncthreads();
+  size_t tile0 = (size_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortTile / 256; ++r) {
+    size_t idx = tile0 + (size_t)r * 256 + t;
+    bool valid = idx < (size_t)n;
+    unsigned key = valid ? kin[idx] : 0u, val = valid ? vin[idx] : 0u;
+    unsigned digit = (key >> shift) & 255u;
+    unsigned peers = __match_any_sync(0xffffffffu, valid ? digit : 256u + (unsigned)lane);
+    int rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcnt[w][digit] = __popc(peers);
+    __syncthreads();
+    {
+      unsigned run = base[t];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        unsigned c = wcnt[k][t];
+        wcnt[k][t] = run;
+        run += c;
+      }
+      base[t] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      unsigned pos = wcnt[w][digit] + (unsigned)rank;
+      if (pos < (unsigned)n) {
+        kout[pos] = key;
+        vout[pos] = val;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) wcnt[k][t] = 0;
+    __syncthreads();
+  }
+}
+
+static int scan_exclusive(unsigned* data, size_t m, unsigned* partials, cudaStream_t st) {
+  int blocks = (int)((m + kScanBlock - 1) / kScanBlock);
+  k_scan_block<<<blocks, 1024, 0, st>>>(data, m, partials);
+  if (blocks > 1) {
+    k_scan_partials<<<1, 1024, 0, st>>>(partials, blocks);
+    k_scan_add<<<blocks, 1024, 0, st>>>(data, m, partials);
+    return 3;
+  }
+  return 1;
+}
+
+// Sorts (keys0, vals0) by the low `bits` bits; the result ends in
+// (keys0, vals0) (an even number of passes).
+static int radix_sort_pairs(BuildScratch& b, int n, int bits, cudaStream_t st) {
+  int launches = 0;
+  int tiles = (n + kSortTile - 1) / kSortTile;
+  int passes = (bits + 7) / 8;
+  if (passes & 1) passes++;
+  unsigned *ki = b.keys0, *vi = b.vals0, *ko = b.keys1, *vo = b.vals1;
+  for (int p = 0; p < passes; ++p) {
+    int shift = 8 * p;
+    k_sort_hist<<<tiles, 256, 0, st>>>(ki, n, shift, b.hist, tiles);
+    launches += 2 + scan_exclusive(b.hist, (size_t)256 * tiles, b.partials, st);
+    k_sort_scatter<<<tiles, 256, 0, st>>>(ki, vi, ko, vo, n, shift, b.hist, tiles);
+    std::swap(ki, ko);
+    std::swap(vi, vo);
+  }
+  return launches;
+}
+
+// ---------------------------------------------------------------------------
+// 4. LBVH hierarchy (Karras 2012): internal node i covers a key range with
+//    i at one end; its split is where the common prefix of the range ends.
+//    Equal codes are told apart by their index.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int prefix_len(const unsigned* __restrict__ keys, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  unsigned a = keys[i], b = keys[j];
+  if (a != b) return __clz(a ^ b);
+  return 32 + __clz((unsigned)i ^ (unsigned)j);
+}
+
+__global__ void k_hierarchy(const unsigned* __restrict__ keys, int n, int* __restrict__ lch, int* __restrict__ rch,
+                            int* __restrict__ parent, int* __restrict__ leaf_parent, int2* __restrict__ range) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int dl = prefix_len(keys, n, i, i - 1), dr = prefix_len(keys, n, i, i + 1);
+  int d = dr > dl ? 1 : -1;
+  int dmin = dr > dl ? dl : dr;
+  int lmax = 2;
+  while (prefix_len(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (prefix_len(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  int j = i + l * d;
+  int dnode = prefix_len(keys, n, i, j);
+  int s = 0, div = 2, t;
+  do {
+    t = (l + div - 1) / div;
+    if (prefix_len(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    div <<= 1;
+  } while (t > 1);
+  int gamma = i + s * d + (d < 0 ? -1 : 0);
+  int lo = min(i, j), hi = max(i, j);
+  int left = (lo == gamma) ? ~gamma : gamma;
+  int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+  lch[i] = left;
+  rch[i] = right;
+  range[i] = make_int2(lo, hi);
+  if (left < 0) leaf_parent[gamma] = i;
+  else parent[left] = i;
+  if (right < 0) leaf_parent[gamma + 1] = i;
+  else parent[right] = i;
+  if (i == 0) parent[0] = -1;
+}
+
+// ---------------------------------------------------------------------------
+// 5. bottom-up boxes, SAH costs and leaf collapsing.  The second thread to
+//    reach a node processes it.  meta (node_hi.w bits): height | collapse<<8
+// ---------------------------------------------------------------------------
+struct ChildInfo {
+  float4 lo, hi;
+  float cost, cost_lbvh;
+  int height;
+};
+
+__device__ __forceinline__ ChildInfo child_info(int c, const unsigned* __restrict__ vals, const float4* aabb_lo,
+                                                const float4* aabb_hi, const float4* node_lo, const float4* node_hi,
+                                                const float* cost_lbvh) {
+  ChildInfo r;
+  if (c < 0) {
+    unsigned pid = vals[~c];
+    r.lo = aabb_lo[pid];
+    r.hi = aabb_hi[pid];
+    r.cost = kCostIsect;
+    r.cost_lbvh = kCostIsect;
+    r.height = 0;
+  } else {
+    r.lo = __ldcg(&node_lo[c]);
+    r.hi = __ldcg(&node_hi[c]);
+    r.cost = r.lo.w;
+    r.cost_lbvh = __ldcg(&cost_lbvh[c]);
+    r.height = __float_as_int(r.hi.w) & 0xff;   // 0 for a collapsed node
+  }
+  return r;
+}
+
+__global__ void k_refit(int n, const unsigned* __restrict__ vals, const float4* __restrict__ aabb_lo,
+                        const float4* __restrict__ aabb_hi, const int* __restrict__ lch, const int* __restrict__ rch,
+                        const int* __restrict__ parent, const int* __restrict__ leaf_parent,
+                        const int2* __restrict__ range, float4* node_lo, float4* node_hi, float* cost_lbvh, int* flags) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int node = leaf_parent[p];
+  // a radix tree has at most n-1 ancestors above a leaf; the bound and the
+  // index check only guard against a malformed tree
+  for (int it = 0; node >= 0 && node < n - 1 && it < n; ++it) {
+    __threadfence();
+    if (atomicAdd(&flags[node], 1) == 0) return;
+    __threadfence();
+    ChildInfo a = child_info(lch[node], vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
+    ChildInfo b = child_info(rch[node], vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
+    float4 lo = make_float4(fminf(a.lo.x, b.lo.x), fminf(a.lo.y, b.lo.y), fminf(a.lo.z, b.lo.z), 0.f);
+    float4 hi = make_float4(fmaxf(a.hi.x, b.hi.x), fmaxf(a.hi.y, b.hi.y), fmaxf(a.hi.z, b.hi.z), 0.f);
+    float A = area(lo, hi), Aa = area(a.lo, a.hi), Ab = area(b.lo, b.hi);
+    float ci, cl;
+    if (A > 0.f) {
+      ci = kCostTrav + (Aa * a.cost + Ab * b.cost) / A;
+      cl = kCostTrav + (Aa * a.cost_lbvh + Ab * b.cost_lbvh) / A;
+    } else {
+      ci = kCostTrav + a.cost + b.cost;
+      cl = kCostTrav + a.cost_lbvh + b.cost_lbvh;
+    }
+    int2 rg = range[node];
+    int count = rg.y - rg.x + 1;
+    float leaf_cost = kCostIsect * (float)count;
+    int collapse = (count <= kMaxLeaf && leaf_cost <= ci) ? 1 : 0;
+    int height = collapse ? 0 : 1 + max(a.height, b.height);
+    lo.w = collapse ? leaf_cost : ci;
+    hi.w = __int_as_float(height | (collapse << 8));
+    node_lo[node] = lo;
+    node_hi[node] = hi;
+    cost_lbvh[node] = cl;
+    node = parent[node];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 6. binned-SAH rebuild of the top levels (HLBVH style): the LBVH nodes
+//    with at most `cluster_max` primitives whose parent has more become
+//    clusters; a new top tree is built over the clusters' boxes with 16
+//    bins per axis, level by level (one block per segment).
+// ---------------------------------------------------------------------------
+__global__ void k_find_clusters(int n, int cluster_max, const int* __restrict__ lch, const int* __restrict__ rch,
+                                const int2* __restrict__ range, const float4* __restrict__ node_lo,
+                                const float4* __restrict__ node_hi, const unsigned* __restrict__ vals,
+                                const float4* __restrict__ aabb_lo, const float4* __restrict__ aabb_hi,
+                                int* __restrict__ clu_count_out, int* __restrict__ clu_ids, int* __restrict__ clu_link,
+                                float4* __restrict__ clu_lo, float4* __restrict__ clu_hi) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int2 rg = range[i];
+  if (rg.y - rg.x + 1 <= cluster_max) return;     // a node above the cut only emits its children
+  int kids[2] = {lch[i], rch[i]};
+  for (int k = 0; k < 2; ++k) {
+    int c = kids[k];
+    int count;
+    float4 lo, hi;
+    int link, height;
+    if (c < 0) {
+      unsigned pid = vals[~c];
+      lo = aabb_lo[pid];
+      hi = aabb_hi[pid];
+      count = 1;
+      link = leaf_link(~c, 1);
+      height = 0;
+    } else {
+      int2 r2 = range[c];
+      count = r2.y - r2.x + 1;
+      if (count > cluster_max) continue;
+      lo = node_lo[c];
+      hi = node_hi[c];
+      int meta = __float_as_int(hi.w);
+      bool collapse = (meta >> 8) & 1;
+      link = collapse ? leaf_link(r2.x, count) : c;
+      height = collapse ? 0 : (meta & 0xff);
+    }
+    int slot = atomicAdd(clu_count_out, 1);
+    clu_ids[slot] = slot;
+    clu_link[slot] = link;
+    clu_lo[slot] = make_float4(lo.x, lo.y, lo.z, (float)count);
+    clu_hi[slot] = make_float4(hi.x, hi.y, hi.z, __int_as_float(height));
+  }
+}
+
+__global__ void k_top_init(int* seg_count, int4* seg0, const int* __restrict__ n_clusters, int* top_count,
+                           BuildInfo* info) {
+  // one segment covering every cluster; it becomes top node 0
+  if (threadIdx.x == 0) {
+    seg0[0] = make_int4(0, *n_clusters, -1, 0);
+    seg_count[0] = 1;
+    for (int l = 1; l <= kTopMaxLevels; ++l) seg_count[l] = 0;
+    top_count[0] = 1;
+    info->height = 1;
+  }
+}
+
+__global__ void k_iota(int* __restrict__ a, const int* __restrict__ n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < *n) a[i] = i;
+}
+
+// Writes child `side` (0/1) of a node in the traversal layout.
+__device__ __forceinline__ void write_child(float4* nodes, int node, int side, float4 lo, float4 hi, int link) {
+  float* n = (float*)(nodes + 4 * (size_t)node);
+  int o = side == 0 ? 0 : 4;
+  n[o + 0] = lo.x;
+  n[o + 1] = hi.x;
+  n[o + 2] = lo.y;
+  n[o + 3] = hi.y;
+  n[8 + 2 * side] = lo.z;
+  n[9 + 2 * side] = hi.z;
+  n[12 + side] = __int_as_float(link);
+}
+
+__device__ __forceinline__ int bin_of(float c, float lo, float ext) {
+  int bi = ext > 0.f ? (int)((c - lo) / ext * kTopBins) : 0;
+  return min(max(bi, 0), kTopBins - 1);
+}
+
+// One block (256 threads) per active segment of this level: binned SAH
+// split (16 bins per axis, cost A_L N_L + A_R N_R with N in primitives),
+// stable partition of the cluster ids, then the two children are emitted:
+// a single cluster becomes a direct link, anything larger a new top node
+// (and a segment of the next level).
+__global__ void __launch_bounds__(256) k_top_level(int level, int top_base, const int* __restrict__ seg_count,
+                                                   const int4* __restrict__ seg_in, int4* __restrict__ seg_out,
+                                                   int* __restrict__ seg_count_out, const int* __restrict__ ids_in,
+                                                   int* __restrict__ ids_out, const int* __restrict__ clu_link,
+                                                   const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
+                                                   int* __restrict__ top_count, float4* __restrict__ nodes,
+                                                   BuildInfo* __restrict__ info) {
+  __shared__ int s_cb[6];
+  __shared__ int bin_count[3][kTopBins];
+  __shared__ int bin_lo[3][kTopBins][3], bin_hi[3][kTopBins][3];
+  __shared__ float s_cost[3 * (kTopBins - 1)];
+  __shared__ int s_split_axis, s_split_bin;
+  __shared__ int s_wcount[8];
+  __shared__ int s_box[2][6];
+  int nseg = seg_count[level];
+  int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int sidx = blockIdx.x; sidx < nseg; sidx += gridDim.x) {
+    int4 sg = seg_in[sidx];
+    int b = sg.x, e = sg.y, node = sg.w;
+    int m = e - b;
+    if (t < 6) {
+      s_cb[t] = f2o(t < 3 ? INFINITY : -INFINITY);
+      s_box[0][t] = f2o(t < 3 ? INFINITY : -INFINITY);
+      s_box[1][t] = f2o(t < 3 ? INFINITY : -INFINITY);
+    }
+    if (t < 3 * kTopBins) {
+      int a = t / kTopBins, k = t % kTopBins;
+      bin_count[a][k] = 0;
+      for (int q = 0; q < 3; ++q) {
+        bin_lo[a][k][q] = f2o(INFINITY);
+        bin_hi[a][k][q] = f2o(-INFINITY);
+      }
+    }
+    __syncthreads();
+    // centroid bounds of the segment
+    float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int k = b + t; k < e; k += 256) {
+      int c = ids_in[k];
+      float4 lo = clu_lo[c], hi = clu_hi[c];
+      float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+      for (int a = 0; a < 3; ++a) {
+        cmin[a] = fminf(cmin[a], cc[a]);
+        cmax[a] = fmaxf(cmax[a], cc[a]);
+      }
+    }
+    for (int a = 0; a < 3; ++a) {
+      if (cmin[a] <= cmax[a]) {
+        atomicMin(&s_cb[a], f2o(cmin[a]));
+        atomicMax(&s_cb[a + 3], f2o(cmax[a]));
+      }
+    }
+    __syncthreads();
+    float clo[3] = {o2f(s_cb[0]), o2f(s_cb[1]), o2f(s_cb[2])};
+    float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
+    // bin every axis
+    for (int k = b + t; k < e; k += 256) {
+      int c = ids_in[k];
+      float4 lo = clu_lo[c], hi = clu_hi[c];
+      float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+      float lo3[3] = {lo.x, lo.y, lo.z}, hi3[3] = {hi.x, hi.y, hi.z};
+      for (int a = 0; a < 3; ++a) {
+        int bi = bin_of(cc[a], clo[a], cext[a]);
+        atomicAdd(&bin_count[a][bi], (int)lo.w);
+        for (int q = 0; q < 3; ++q) {
+          atomicMin(&bin_lo[a][bi][q], f2o(lo3[q]));
+          atomicMax(&bin_hi[a][bi][q], f2o(hi3[q]));
+        }
+      }
+    }
+    __syncthreads();
+    // SAH of every split plane (one thread per plane)
+    if (t < 3 * (kTopBins - 1)) {
+      int a = t / (kTopBins - 1), sp = t % (kTopBins - 1);
+      float l0[3] = {INFINITY, INFINITY, INFINITY}, l1[3] = {-INFINITY, -INFINITY, -INFINITY};
+      float r0[3] = {INFINITY, INFINITY, INFINITY}, r1[3] = {-INFINITY, -INFINITY, -INFINITY};
+      int nl = 0, nr = 0;
+      for (int k = 0; k < kTopBins; ++k) {
+        int cnt = bin_count[a][k];
+        if (cnt == 0) continue;
+        bool lft = k <= sp;
+        if (lft) nl += cnt;
+        else nr += cnt;
+        for (int q = 0; q < 3; ++q) {
+          float blo = o2f(bin_lo[a][k][q]), bhi = o2f(bin_hi[a][k][q]);
+          if (lft) {
+            l0[q] = fminf(l0[q], blo);
+            l1[q] = fmaxf(l1[q], bhi);
+          } else {
+            r0[q] = fminf(r0[q], blo);
+            r1[q] = fmaxf(r1[q], bhi);
+          }
+        }
+      }
+      float cost = INFINITY;
+      if (nl > 0 && nr > 0) {
+        float AL = area(make_float4(l0[0], l0[1], l0[2], 0), make_float4(l1[0], l1[1], l1[2], 0));
+        float AR = area(make_float4(r0[0], r0[1], r0[2], 0), make_float4(r1[0], r1[1], r1[2], 0));
+        cost = AL * (float)nl + AR * (float)nr;
+      }
+      s_cost[t] = cost;
+    }
+    __syncthreads();
+    if (t == 0) {
+      int best = -1;
+      float bc = INFINITY;
+      for (int k = 0; k < 3 * (kTopBins - 1); ++k)
+        if (s_cost[k] < bc) {
+          bc = s_cost[k];
+          best = k;
+        }
+      if (best < 0 || level >= kTopForceMedian) {
+        s_split_axis = -1;   // split the segment at its middle
+        s_split_bin = 0;
+      } else {
+        s_split_axis = best / (kTopBins - 1);
+        s_split_bin = best % (kTopBins - 1);
+      }
+    }
+    __syncthreads();
+    int ax = s_split_axis, sb = s_split_bin;
+    // stable partition into ids_out[b, e): left side ascending from b,
+    // right side descending from e-1, then the right side is reversed
+    int nleft = m / 2;
+    if (ax < 0) {
+      for (int k = b + t; k < e; k += 256) ids_out[k] = ids_in[k];
+    } else {
+      int run_l = 0, run_r = 0;
+      for (int k0 = b; k0 < e; k0 += 256) {
+        int k = k0 + t;
+        bool valid = k < e;
+        int c = valid ? ids_in[k] : 0;
+        bool left = false;
+        if (valid) {
+          float4 lo = clu_lo[c], hi = clu_hi[c];
+          float cl = ax == 0 ? lo.x : (ax == 1 ? lo.y : lo.z);
+          float ch = ax == 0 ? hi.x : (ax == 1 ? hi.y : hi.z);
+          left = bin_of(0.5f * (cl + ch), clo[ax], cext[ax]) <= sb;
+        }
+        unsigned bl = __ballot_sync(0xffffffffu, left);
+        unsigned br = __ballot_sync(0xffffffffu, valid && !left);
+        if (lane == 0) s_wcount[w] = __popc(bl) | (__popc(br) << 16);
+        __syncthreads();
+        int before_l = 0, before_r = 0, chunk_l = 0, chunk_r = 0;
+        for (int q = 0; q < 8; ++q) {
+          int v = s_wcount[q];
+          if (q < w) {
+            before_l += v & 0xffff;
+            before_r += v >> 16;
+          }
+          chunk_l += v & 0xffff;
+          chunk_r += v >> 16;
+        }
+        unsigned lt = (1u << lane) - 1u;
+        if (valid && left) ids_out[b + run_l + before_l + __popc(bl & lt)] = c;
+        if (valid && !left) ids_out[e - 1 - (run_r + before_r + __popc(br & lt))] = c;
+        run_l += chunk_l;
+        run_r += chunk_r;
+        __syncthreads();
+      }
+      nleft = run_l;
+      int nr = m - nleft;
+      for (int k = t; k < nr / 2; k += 256) {
+        int x = ids_out[b + nleft + k];
+        ids_out[b + nleft + k] = ids_out[e - 1 - k];
+        ids_out[e - 1 - k] = x;
+      }
+      if (nleft == 0 || nleft == m) {   // not reachable with a finite SAH cost; keep a valid split
+        __syncthreads();
+        for (int k = b + t; k < e; k += 256) ids_out[k] = ids_in[k];
+        nleft = m / 2;
+      }
+    }
+    __syncthreads();
+    // boxes of the two sides
+    {
+      float lo[2][3] = {{INFINITY, INFINITY, INFINITY}, {INFINITY, INFINITY, INFINITY}};
+      float hi[2][3] = {{-INFINITY, -INFINITY, -INFINITY}, {-INFINITY, -INFINITY, -INFINITY}};
+      for (int k = b + t; k < e; k += 256) {
+        int c = ids_out[k];
+        int side = k < b + nleft ? 0 : 1;
+        float4 a = clu_lo[c], h = clu_hi[c];
+        lo[side][0] = fminf(lo[side][0], a.x);
+        lo[side][1] = fminf(lo[side][1], a.y);
+        lo[side][2] = fminf(lo[side][2], a.z);
+        hi[side][0] = fmaxf(hi[side][0], h.x);
+        hi[side][1] = fmaxf(hi[side][1], h.y);
+        hi[side][2] = fmaxf(hi[side][2], h.z);
+      }
+      for (int side = 0; side < 2; ++side)
+        for (int q = 0; q < 3; ++q) {
+          if (lo[side][q] <= hi[side][q]) {
+            atomicMin(&s_box[side][q], f2o(lo[side][q]));
+            atomicMax(&s_box[side][q + 3], f2o(hi[side][q]));
+          }
+        }
+    }
+    __syncthreads();
+    if (t < 2) {
+      int cb = t == 0 ? b : b + nleft;
+      int ce = t == 0 ? b + nleft : e;
+      float4 lo = make_float4(o2f(s_box[t][0]), o2f(s_box[t][1]), o2f(s_box[t][2]), 0.f);
+      float4 hi = make_float4(o2f(s_box[t][3]), o2f(s_box[t][4]), o2f(s_box[t][5]), 0.f);
+      int link;
+      if (ce - cb == 1) {
+        int c = ids_out[cb];
+        link = clu_link[c];
+        // internal nodes on this path: the top levels 0..level, then the cluster's
+        atomicMax(&info->height, level + 1 + __float_as_int(clu_hi[c].w));
+      } else {
+        int child = atomicAdd(top_count, 1);
+        link = top_base + child;
+        int slot = atomicAdd(seg_count_out, 1);
+        seg_out[slot] = make_int4(cb, ce, node, child);
+        atomicMax(&info->height, level + 2);
+      }
+      write_child(nodes, top_base + node, t, lo, hi, link);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_top_done(const int* __restrict__ top_count, const int* __restrict__ n_clusters, BuildInfo* info,
+                           int top_base) {
+  info->n_top = *top_count;
+  info->n_clusters = *n_clusters;
+  info->root = top_base;
+}
+
+// ---------------------------------------------------------------------------
+// 7. traversal layout of the LBVH nodes
+// ---------------------------------------------------------------------------
+__global__ void k_layout(int n, const int* __restrict__ lch, const int* __restrict__ rch, const int2* __restrict__ range,
+                         const float4* __restrict__ node_lo, const float4* __restrict__ node_hi,
+                         const unsigned* __restrict__ vals, const float4* __restrict__ aabb_lo,
+                         const float4* __restrict__ aabb_hi, float4* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  float4 lo[2], hi[2];
+  int link[2];
+  int kids[2] = {lch[i], rch[i]};
+  for (int k = 0; k < 2; ++k) {
+    int c = kids[k];
+    if (c < 0) {
+      unsigned pid = vals[~c];
+      lo[k] = aabb_lo[pid];
+      hi[k] = aabb_hi[pid];
+      link[k] = leaf_link(~c, 1);
+    } else {
+      lo[k] = node_lo[c];
+      hi[k] = node_hi[c];
+      int meta = __float_as_int(hi[k].w);
+      if ((meta >> 8) & 1) {
+        int2 rg = range[c];
+        link[k] = leaf_link(rg.x, rg.y - rg.x + 1);
+      } else {
+        link[k] = c;
+      }
+    }
+  }
+  float4* o = out + 4 * (size_t)i;
+  o[0] = make_float4(lo[0].x, hi[0].x, lo[0].y, hi[0].y);
+  o[1] = make_float4(lo[1].x, hi[1].x, lo[1].y, hi[1].y);
+  o[2] = make_float4(lo[0].z, hi[0].z, lo[1].z, hi[1].z);
+  o[3] = make_float4(__int_as_float(link[0]), __int_as_float(link[1]), 0.f, 0.f);
+}
+
+// one primitive: a root whose second child box is empty
+__global__ void k_layout_single(const float4* __restrict__ aabb_lo, const float4* __restrict__ aabb_hi,
+                                float4* __restrict__ out, BuildInfo* info) {
+  float4 lo = aabb_lo[0], hi = aabb_hi[0];
+  out[0] = make_float4(lo.x, hi.x, lo.y, hi.y);
+  out[1] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+  out[2] = make_float4(lo.z, hi.z, INFINITY, -INFINITY);
+  out[3] = make_float4(__int_as_float(leaf_link(0, 1)), __int_as_float(leaf_link(0, 1)), 0.f, 0.f);
+  info->height = 1;
+  info->sah = kCostTrav + kCostIsect;
+  info->sah_lbvh = info->sah;
+  info->root = 0;
+  info->n_clusters = 0;
+  info->n_top = 0;
+  info->max_leaf = 1;
+}
+
+__global__ void k_gather_prims(const unsigned* __restrict__ vals, int n, const float4* __restrict__ in,
+                               float4* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * n) return;
+  int p = i / 3, r = i - 3 * p;
+  unsigned v = min(vals[p], (unsigned)(n - 1));
+  out[i] = in[3 * (size_t)v + r];
+}
+
+__global__ void k_info_lbvh(const float4* __restrict__ node_lo, const float4* __restrict__ node_hi,
+                            const float* __restrict__ cost_lbvh, BuildInfo* info, int root) {
+  info->height = __float_as_int(node_hi[0].w) & 0xff;
+  info->sah = node_lo[0].w;
+  info->sah_lbvh = cost_lbvh[0];
+  info->root = root;
+  info->n_clusters = 0;
+  info->n_top = 0;
+  info->max_leaf = kMaxLeaf;
+}
+
+}  // namespace rtb
+
+using namespace rtb;
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+namespace rtb {
+
+static rt_status carve(rt_scene* s, int n, BuildScratch& b) {
+  size_t tiles = (size_t)(n + kSortTile - 1) / kSortTile;
+  size_t hist_n = 256 * tiles;
+  size_t parts = (hist_n + kScanBlock - 1) / kScanBlock + 1;
+  size_t N = (size_t)std::max(n, 2);
+  size_t off = 0;
+  size_t sz[32];
+  int k = 0;
+  sz[k++] = N * 16;  // aabb_lo
+  sz[k++] = N * 16;  // aabb_hi
+  sz[k++] = N * 4;   // keys0
+  sz[k++] = N * 4;   // vals0
+  sz[k++] = N * 4;   // keys1
+  sz[k++] = N * 4;   // vals1
+  sz[k++] = hist_n * 4 + 16;
+  sz[k++] = parts * 4 + 16;
+  sz[k++] = N * 4;   // lch
+  sz[k++] = N * 4;   // rch
+  sz[k++] = N * 4;   // parent
+  sz[k++] = N * 4;   // leaf_parent
+  sz[k++] = N * 4;   // flags
+  sz[k++] = N * 8;   // range
+  sz[k++] = N * 16;  // node_lo
+  sz[k++] = N * 16;  // node_hi
+  sz[k++] = N * 4;   // cost_lbvh
+  sz[k++] = 64;      // cent_bounds
+  sz[k++] = N * 4;   // clu_a
+  sz[k++] = N * 4;   // clu_b
+  sz[k++] = N * 4;   // clu_link
+  sz[k++] = N * 16;  // clu_lo
+  sz[k++] = N * 16;  // clu_hi
+  sz[k++] = N * 16;  // seg_a
+  sz[k++] = N * 16;  // seg_b
+  sz[k++] = (kTopMaxLevels + 2) * 4;
+  sz[k++] = 16;      // top_count
+  sz[k++] = N * 16;  // top_lo (also SAH scratch)
+  sz[k++] = N * 16;  // top_hi
+  sz[k++] = N * 4;   // top_height
+  sz[k++] = sizeof(BuildInfo);
+  size_t total = 0;
+  for (int i = 0; i < k; ++i) total += align_up(sz[i]);
+  rt_status st = ensure(s->build_tmp, total);
+  if (st) return st;
+  char* base = (char*)s->build_tmp.p;
+  void* ptr[32];
+  for (int i = 0; i < k; ++i) {
+    ptr[i] = base + off;
+    off += align_up(sz[i]);
+  }
+  int q = 0;
+  b.aabb_lo = (float4*)ptr[q++];
+  b.aabb_hi = (float4*)ptr[q++];
+  b.keys0 = (unsigned*)ptr[q++];
+  b.vals0 = (unsigned*)ptr[q++];
+  b.keys1 = (unsigned*)ptr[q++];
+  b.vals1 = (unsigned*)ptr[q++];
+  b.hist = (unsigned*)ptr[q++];
+  b.partials = (unsigned*)ptr[q++];
+  b.lch = (int*)ptr[q++];
+  b.rch = (int*)ptr[q++];
+  b.parent = (int*)ptr[q++];
+  b.leaf_parent = (int*)ptr[q++];
+  b.flags = (int*)ptr[q++];
+  b.range = (int2*)ptr[q++];
+  b.node_lo = (float4*)ptr[q++];
+  b.node_hi = (float4*)ptr[q++];
+  b.cost_lbvh = (float*)ptr[q++];
+  b.cent_bounds = (int*)ptr[q++];
+  b.clu_a = (int*)ptr[q++];
+  b.clu_b = (int*)ptr[q++];
+  b.clu_link = (int*)ptr[q++];
+  b.clu_lo = (float4*)ptr[q++];
+  b.clu_hi = (float4*)ptr[q++];
+  b.seg_a = (int4*)ptr[q++];
+  b.seg_b = (int4*)ptr[q++];
+  b.seg_count = (int*)ptr[q++];
+  b.top_count = (int*)ptr[q++];
+  b.top_lo = (float4*)ptr[q++];
+  b.top_hi = (float4*)ptr[q++];
+  b.top_height = (int*)ptr[q++];
+  b.info = (BuildInfo*)ptr[q++];
+  return RT_OK;
+}
+
+// Cluster size of the top-level rebuild: aims at a few thousand clusters.
+static int cluster_max_for(int n) {
+  int c = 64;
+  while ((int64_t)n / c > 16384) c *= 2;
+  return c;
+}
+
+rt_status bvh_build(rt_scene* s, cudaStream_t st) {
+  int n = (int)s->n_prims;
+  if (n == 0) {
+    s->root = -1;
+    s->built = true;
+    return RT_OK;
+  }
+  BuildScratch b;
+  rt_status rs = carve(s, n, b);
+  if (rs) return rs;
+  // nodes: LBVH internal nodes [0, n-1) + top nodes [n-1, 2n-2)
+  size_t slots = (size_t)std::max(2 * n, 2);
+  if ((rs = ensure(s->nodes, slots * 64))) return rs;
+  s->n_nodes_total = (int64_t)slots;
+  float4* nodes = (float4*)s->nodes.p;
+  int tb = 256, grid = (n + tb - 1) / tb;
+  int L = 0;   // launches (kernels + memsets) of this build
+  k_init_bounds<<<1, 32, 0, st>>>(b.cent_bounds);
+  k_prim_bounds<<<grid, tb, 0, st>>>((const float4*)s->prims_id.p, n, b.aabb_lo, b.aabb_hi, b.cent_bounds);
+  L += 2;
+  if (n == 1) {
+    cudaMemsetAsync(b.vals0, 0, 4, st);
+    k_layout_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, nodes, b.info);
+    k_gather_prims<<<1, 32, 0, st>>>(b.vals0, 1, (const float4*)s->prims_id.p, (float4*)s->prims_leaf.p);
+    s->last_build_launches = L + 3;
+    s->root = 0;
+    s->built = true;
+    return cuda_error(cudaGetLastError(), "rt_bvh_build");
+  }
+  k_morton<<<grid, tb, 0, st>>>(b.aabb_lo, b.aabb_hi, n, b.cent_bounds, b.keys0, b.vals0);
+  L += 1 + radix_sort_pairs(b, n, 30, st);
+  cudaMemsetAsync(b.flags, 0, (size_t)n * 4, st);
+  cudaMemsetAsync(b.parent, 0xff, (size_t)n * 4, st);
+  cudaMemsetAsync(b.leaf_parent, 0xff, (size_t)n * 4, st);
+  k_hierarchy<<<grid, tb, 0, st>>>(b.keys0, n, b.lch, b.rch, b.parent, b.leaf_parent, b.range);
+  k_refit<<<grid, tb, 0, st>>>(n, b.vals0, b.aabb_lo, b.aabb_hi, b.lch, b.rch, b.parent, b.leaf_parent, b.range,
+                               b.node_lo, b.node_hi, b.cost_lbvh, b.flags);
+  k_layout<<<grid, tb, 0, st>>>(n, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo, b.aabb_hi,
+                                nodes);
+  k_gather_prims<<<(3 * n + 255) / 256, 256, 0, st>>>(b.vals0, n, (const float4*)s->prims_id.p,
+                                                      (float4*)s->prims_leaf.p);
+  k_info_lbvh<<<1, 1, 0, st>>>(b.node_lo, b.node_hi, b.cost_lbvh, b.info, 0);
+  L += 8;
+  s->root = 0;
+  int cmax = cluster_max_for(n);
+  if (n > 2 * cmax) {
+    // top levels: binned SAH over the Morton clusters
+    int top_base = n - 1;
+    int* n_clusters_dev = b.seg_count + kTopMaxLevels + 1;
+    cudaMemsetAsync(b.seg_count, 0, (kTopMaxLevels + 2) * 4, st);
+    // a zeroed top node is harmless to traverse (links to node 0, empty boxes)
+    cudaMemsetAsync(nodes + 4 * (size_t)top_base, 0, (size_t)(slots - top_base) * 64, st);
+    k_find_clusters<<<grid, tb, 0, st>>>(n, cmax, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo,
+                                         b.aabb_hi, n_clusters_dev, b.clu_a, b.clu_link, b.clu_lo, b.clu_hi);
+    k_top_init<<<1, 32, 0, st>>>(b.seg_count, b.seg_a, n_clusters_dev, b.top_count, b.info);
+    int top_grid = std::max(1, 2 * s->sm_count);
+    for (int level = 0; level < kTopMaxLevels; ++level) {
+      bool odd = level & 1;
+      k_top_level<<<top_grid, 256, 0, st>>>(level, top_base, b.seg_count, odd ? b.seg_b : b.seg_a,
+                                            odd ? b.seg_a : b.seg_b, b.seg_count + level + 1,
+                                            odd ? b.clu_b : b.clu_a, odd ? b.clu_a : b.clu_b, b.clu_link, b.clu_lo,
+                                            b.clu_hi, b.top_count, nodes, b.info);
+    }
+    k_top_done<<<1, 1, 0, st>>>(b.top_count, n_clusters_dev, b.info, top_base);
+    L += 5 + kTopMaxLevels;
+    s->root = top_base;
+  }
+  s->last_build_launches = L;
+  s->built = true;
+  return cuda_error(cudaGetLastError(), "rt_bvh_build");
+}
+
+}  // namespace rtb
+
+extern "C" {
+
+rt_status rt_bvh_build(rt_scene* s, void* stream) {
+  if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_bvh_build: scene is NULL");
+  return bvh_build(s, (cudaStream_t)stream);
+}
+
+rt_status rt_bvh_get_info(rt_scene* s, rt_bvh_info* info, void* stream) {
+  if (!s || !info) return set_error(RT_ERR_INVALID_ARG, "rt_bvh_get_info: NULL argument");
+  if (!s->built) return set_error(RT_ERR_NOT_BUILT, "rt_bvh_get_info: no BVH");
+  memset(info, 0, sizeof(*info));
+  info->n_prims = s->n_prims;
+  info->build_ms = s->last_build_ms;
+  info->build_launches = s->last_build_launches;
+  if (s->n_prims == 0) return RT_OK;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "rt_bvh_get_info");
+  BuildScratch b;
+  rt_status rs = carve(s, (int)s->n_prims, b);
+  if (rs) return rs;
+  BuildInfo bi;
+  e = cudaMemcpy(&bi, b.info, sizeof(bi), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "rt_bvh_get_info");
+  std::vector<float> nodes((size_t)s->n_nodes_total * 16);
+  e = cudaMemcpy(nodes.data(), s->nodes.p, nodes.size() * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "rt_bvh_get_info nodes");
+  // walk the traversal layout: reachable nodes, depth, leaf sizes, SAH cost
+  auto area3 = [](const float* lo, const float* hi) {
+    double dx = (double)hi[0] - lo[0], dy = (double)hi[1] - lo[1], dz = (double)hi[2] - lo[2];
+    if (!(dx >= 0) || !(dy >= 0) || !(dz >= 0)) return 0.0;
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+  };
+  auto child_box = [&](int node, int c, float* lo, float* hi) {
+    const float* n = &nodes[(size_t)node * 16];
+    if (c == 0) {
+      lo[0] = n[0]; hi[0] = n[1]; lo[1] = n[2]; hi[1] = n[3]; lo[2] = n[8]; hi[2] = n[9];
+    } else {
+      lo[0] = n[4]; hi[0] = n[5]; lo[1] = n[6]; hi[1] = n[7]; lo[2] = n[10]; hi[2] = n[11];
+    }
+  };
+  auto link_of = [&](int node, int c) {
+    int v;
+    memcpy(&v, &nodes[(size_t)node * 16 + 12 + c], 4);
+    return v;
+  };
+  float l0[3], h0[3], l1[3], h1[3];
+  child_box(s->root, 0, l0, h0);
+  child_box(s->root, 1, l1, h1);
+  float rlo[3], rhi[3];
+  for (int k = 0; k < 3; ++k) {
+    rlo[k] = std::min(l0[k], l1[k]);
+    rhi[k] = std::max(h0[k], h1[k]);
+  }
+  double a_root = area3(rlo, rhi);
+  double sum = kCostTrav * a_root;
+  int64_t reach = 0;
+  int max_depth = 0, max_leaf = 0;
+  std::vector<std::pair<int, int>> stack;
+  stack.push_back({s->root, 1});
+  while (!stack.empty()) {
+    auto [node, depth] = stack.back();
+    stack.pop_back();
+    if (node < 0 || node >= s->n_nodes_total || reach > s->n_nodes_total)
+      return set_error(RT_ERR_CUDA, "rt_bvh_get_info: malformed tree");
+    ++reach;
+    max_depth = std::max(max_depth, depth);
+    for (int c = 0; c < 2; ++c) {
+      float lo[3], hi[3];
+      child_box(node, c, lo, hi);
+      int link = link_of(node, c);
+      if (link < 0) {
+        int cnt = leaf_count(link);
+        if (s->n_prims == 1 && c == 1) continue;   // the single-primitive root's empty slot
+        max_leaf = std::max(max_leaf, cnt);
+        sum += kCostIsect * cnt * area3(lo, hi);
+      } else {
+        sum += kCostTrav * area3(lo, hi);
+        stack.push_back({link, depth + 1});
+      }
+    }
+  }
+  info->n_nodes = reach;
+  info->root = s->root;
+  info->max_depth = max_depth;
+  info->max_leaf_size = max_leaf;
+  info->sah_cost = a_root > 0 ? sum / a_root : 0.0;
+  info->sah_cost_lbvh = bi.sah_lbvh;
+  return RT_OK;
+}
+
+rt_status rt_bvh_export(rt_scene* s, float* nodes, int64_t nodes_capacity, int32_t* prim_order, uint32_t* morton,
+                        void* stream) {
+  if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_bvh_export: scene is NULL");
+  if (!s->built) return set_error(RT_ERR_NOT_BUILT, "rt_bvh_export: no BVH");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "rt_bvh_export");
+  int n = (int)s->n_prims;
+  if (n == 0) return RT_OK;
+  BuildScratch b;
+  rt_status rs = carve(s, n, b);
+  if (rs) return rs;
+  if (nodes) {
+    int64_t cnt = std::min<int64_t>(nodes_capacity, s->n_nodes_total);
+    e = cudaMemcpy(nodes, s->nodes.p, (size_t)cnt * 64, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "rt_bvh_export nodes");
+  }
+  if (prim_order) {
+    e = cudaMemcpy(prim_order, b.vals0, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "rt_bvh_export order");
+  }
+  if (morton) {
+    e = cudaMemcpy(morton, b.keys0, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "rt_bvh_export morton");
+  }
+  return RT_OK;
+}
+
+}  // extern "C"

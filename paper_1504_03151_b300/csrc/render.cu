@@ -1,0 +1,751 @@
+// render.cu - the wavefront Whitted pipeline: closest-hit + shade kernels
+// (the depth-0 one generates its primary rays itself), any-hit shadow
+// kernels, warp-aggregated queue pushes, and the ABI entry points.
+//
+// One frame, per Sec. IV.A of the paper (recursion turned into an
+// iteration whose trip count is the depth):
+//   depth 0 : camera rays -> closest hit -> shade: shadow rays (Alg. 1, one
+//             per point light) to the shadow queue, reflection/refraction
+//             rays to the next ray queue, misses / emission to the image
+//   shadow  : any hit on (0, dist - eps); unblocked -> add to the image
+//   depth d : the same on the queued rays, until max_depth
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "rtb_internal.cuh"
+
+namespace rtb {
+
+constexpr int kSentinelLink = INT_MIN;   // popped from an empty stack; never a valid link
+constexpr float kSlabUp = 1.0000005f;    // grows a slab's exit distance by > 2 ulps
+constexpr unsigned kFull = 0xffffffffu;
+
+// Device-side counters of one frame (reset at its start).
+struct Counters {
+  unsigned rays[RT_MAX_DEPTH + 2];        // rays queued for depth d (d >= 1)
+  unsigned shadow[RT_MAX_DEPTH + 1];      // shadow rays cast from depth-d hits
+  unsigned hits[RT_MAX_DEPTH + 1];
+  unsigned fetch_trace[RT_MAX_DEPTH + 1]; // dynamic work fetch
+  unsigned fetch_shadow[RT_MAX_DEPTH + 1];
+  unsigned long long visits[2], tests[2]; // [closest, any]
+};
+
+struct FrameParams {
+  CamBasis cam;
+  int W, H, tiles_x, tiles_y;
+  int max_depth;
+  float bg_r, bg_g, bg_b;
+  float eps_scale;
+  float* fb;
+  int32_t* aov_prim;
+  float* aov_t;
+  float4* rayq[2];
+  float4* shadowq;
+  unsigned ray_cap, shadow_cap;
+  Counters* ctr;
+};
+
+// ---------------------------------------------------------------------------
+// traversal
+// ---------------------------------------------------------------------------
+struct RayInv {
+  f3 o, d, idir, oid;
+};
+
+__device__ __forceinline__ RayInv make_ray(f3 o, f3 d) {
+  RayInv r;
+  r.o = o;
+  r.d = d;
+  const float tiny = 8.27e-25f;   // 2^-80: keeps 1/d finite
+  float dx = fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x);
+  float dy = fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y);
+  float dz = fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z);
+  r.idir = mk3(1.0f / dx, 1.0f / dy, 1.0f / dz);
+  r.oid = mk3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
+  return r;
+}
+
+struct WorkCount {
+  unsigned visits, tests;
+};
+
+// Tests the primitives [start, start+count) in `prims`.  Closest hit:
+// nearest t, ties to the lower primitive id; any hit: returns at the first.
+template <bool kAny, bool kCount>
+__device__ __forceinline__ bool leaf_hits(const float4* __restrict__ prims, int start, int count, const RayInv& r,
+                                          float tmin, float& tbest, int& best, int& best_id, WorkCount& wc) {
+  for (int k = start; k < start + count; ++k) {
+    float4 r0 = __ldg(&prims[3 * (size_t)k]);
+    float4 r1 = __ldg(&prims[3 * (size_t)k + 1]);
+    float t;
+    bool h;
+    if (kCount) wc.tests++;
+    if (__float_as_int(r0.w) == kKindSphere) {
+      h = hit_sphere<!kAny>(r.o, r.d, r0, r1, tmin, tbest, t);
+    } else {
+      float4 r2 = __ldg(&prims[3 * (size_t)k + 2]);
+      h = hit_triangle<!kAny>(r.o, r.d, r0, r1, r2, tmin, tbest, t);
+    }
+    if (h) {
+      if (kAny) {
+        best = k;
+        return true;
+      }
+      int id = __float_as_int(r1.w);
+      if (t < tbest || id < best_id) {
+        tbest = t;
+        best = k;
+        best_id = id;
+      }
+    }
+  }
+  return false;
+}
+
+// BVH traversal with a per-thread stack in shared memory (column
+// `stack[i * kTraceThreads]`).  Near child first; the far one is pushed.
+// Returns the hit record index (leaf order) or -1.  Sets *fail when the
+// step cap or the stack depth is exceeded (the ray then counts as a miss).
+template <bool kAny, bool kCount>
+__device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& tbest, int* stack, int cap,
+                        bool& fail, WorkCount& wc) {
+  int best = -1, best_id = INT_MAX;
+  if (sc.n_prims == 0) return -1;
+  if (!sc.use_bvh) {
+    leaf_hits<kAny, kCount>(sc.prims, 0, sc.n_prims, r, tmin, tbest, best, best_id, wc);
+    return best;
+  }
+  int sp = 0;
+  int node = sc.root;
+  int steps = 0;
+  const float4* __restrict__ nodes = sc.nodes;
+  for (;;) {
+    // inner nodes
+    while (node >= 0) {
+      if (++steps > cap) {
+        fail = true;
+        return kAny ? -1 : best;
+      }
+      if (node >= sc.n_nodes) {
+        atomicOr(sc.status, kErrBadTree);
+        fail = true;
+        return -1;
+      }
+      if (kCount) wc.visits++;
+      const float4* n = nodes + 4 * (size_t)node;
+      float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
+      float a0 = fmaf(n0.x, r.idir.x, -r.oid.x), b0 = fmaf(n0.y, r.idir.x, -r.oid.x);
+      float a1 = fmaf(n0.z, r.idir.y, -r.oid.y), b1 = fmaf(n0.w, r.idir.y, -r.oid.y);
+      float a2 = fmaf(n2.x, r.idir.z, -r.oid.z), b2 = fmaf(n2.y, r.idir.z, -r.oid.z);
+      float c0min = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), tmin));
+      float c0max = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tbest)) * kSlabUp;
+      float d0 = fmaf(n1.x, r.idir.x, -r.oid.x), e0 = fmaf(n1.y, r.idir.x, -r.oid.x);
+      float d1 = fmaf(n1.z, r.idir.y, -r.oid.y), e1 = fmaf(n1.w, r.idir.y, -r.oid.y);
+      float d2 = fmaf(n2.z, r.idir.z, -r.oid.z), e2 = fmaf(n2.w, r.idir.z, -r.oid.z);
+      float c1min = fmaxf(fmaxf(fminf(d0, e0), fminf(d1, e1)), fmaxf(fminf(d2, e2), tmin));
+      float c1max = fminf(fminf(fmaxf(d0, e0), fmaxf(d1, e1)), fminf(fmaxf(d2, e2), tbest)) * kSlabUp;
+      bool h0 = c0min <= c0max, h1 = c1min <= c1max;
+      int l0 = __float_as_int(n3.x), l1 = __float_as_int(n3.y);
+      if (h0 && h1) {
+        int nearc = c0min <= c1min ? l0 : l1;
+        int farc = c0min <= c1min ? l1 : l0;
+        if (sp >= kStackSize) {
+          fail = true;
+          return kAny ? -1 : best;
+        }
+        stack[sp * kTraceThreads] = farc;
+        ++sp;
+        node = nearc;
+      } else if (h0) {
+        node = l0;
+      } else if (h1) {
+        node = l1;
+      } else {
+        node = sp > 0 ? stack[--sp * kTraceThreads] : kSentinelLink;
+      }
+    }
+    if (node == kSentinelLink) break;
+    // leaves
+    while (node < 0 && node != kSentinelLink) {
+      int ls = leaf_start(node), lc = leaf_count(node);
+      if (ls + lc > sc.n_prims) {
+        atomicOr(sc.status, kErrBadTree);
+        fail = true;
+        return -1;
+      }
+      if (leaf_hits<kAny, kCount>(sc.prims, ls, lc, r, tmin, tbest, best, best_id, wc)) return best;
+      node = sp > 0 ? stack[--sp * kTraceThreads] : kSentinelLink;
+    }
+    if (node == kSentinelLink) break;
+  }
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// warp-aggregated queue push: one atomic per warp per call
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned warp_push(unsigned* counter, bool pred, unsigned cap, bool& ok,
+                                              unsigned* status) {
+  unsigned mask = __ballot_sync(kFull, pred);
+  int lane = threadIdx.x & 31;
+  unsigned base = 0;
+  if (mask) {
+    int leader = __ffs(mask) - 1;
+    if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(mask));
+    base = __shfl_sync(kFull, base, leader);
+  }
+  unsigned pos = base + (unsigned)__popc(mask & ((1u << lane) - 1u));
+  ok = pred && pos < cap;
+  if (pred && pos >= cap) atomicOr(status, kErrQueueOverflow);
+  return pos;
+}
+
+__device__ __forceinline__ void store_ray(float4* q, unsigned pos, f3 o, int pixel, f3 d, float tmax, f3 w) {
+  float4* p = q + 3 * (size_t)pos;
+  p[0] = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
+  p[1] = make_float4(d.x, d.y, d.z, tmax);
+  p[2] = make_float4(w.x, w.y, w.z, 0.f);
+}
+
+__device__ __forceinline__ void add_fb(float* fb, int pixel, f3 c) {
+  float* p = fb + 3 * (size_t)pixel;
+  atomicAdd(p, c.x);
+  atomicAdd(p + 1, c.y);
+  atomicAdd(p + 2, c.z);
+}
+
+template <bool kCount>
+__device__ __forceinline__ void flush_work(Counters* ctr, int cls, WorkCount wc) {
+  if (!kCount) return;
+  unsigned v = wc.visits, t = wc.tests;
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_xor_sync(kFull, v, o);
+    t += __shfl_xor_sync(kFull, t, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&ctr->visits[cls], (unsigned long long)v);
+    atomicAdd(&ctr->tests[cls], (unsigned long long)t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// closest hit + shade (+ primary ray generation at depth 0)
+// ---------------------------------------------------------------------------
+template <bool kPrimary, bool kCount>
+__global__ void __launch_bounds__(kTraceThreads) k_trace(DevScene sc, FrameParams fp, int depth, int cap) {
+  __shared__ int s_stack[kStackSize * kTraceThreads];
+  int* stack = s_stack + threadIdx.x;
+  int lane = threadIdx.x & 31;
+  Counters* ctr = fp.ctr;
+  unsigned n_items = kPrimary ? (unsigned)(fp.tiles_x * fp.tiles_y * 32) : min(ctr->rays[depth], fp.ray_cap);
+  const float4* __restrict__ qin = fp.rayq[depth & 1];
+  float4* qout = fp.rayq[(depth + 1) & 1];
+  bool spawn = depth < fp.max_depth;
+  WorkCount wc = {0u, 0u};
+  for (;;) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&ctr->fetch_trace[depth], 32u);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= n_items) break;
+    unsigned idx = base + lane;
+    bool active = idx < n_items;
+    f3 o, d, w;
+    int pixel = 0;
+    if (kPrimary) {
+      int tile = (int)(idx >> 5);
+      int x = (tile % fp.tiles_x) * 8 + (lane & 7);
+      int y = (tile / fp.tiles_x) * 4 + (lane >> 3);
+      active = active && x < fp.W && y < fp.H;
+      pixel = y * fp.W + x;
+      camera_ray(fp.cam, fp.W, fp.H, min(x, fp.W - 1), min(y, fp.H - 1), o, d);
+      w = mk3(1.f, 1.f, 1.f);
+    } else {
+      float4 q0 = make_float4(0, 0, 0, 0), q1 = make_float4(0, 0, 1, 0), q2 = make_float4(0, 0, 0, 0);
+      if (active) {
+        q0 = qin[3 * (size_t)idx];
+        q1 = qin[3 * (size_t)idx + 1];
+        q2 = qin[3 * (size_t)idx + 2];
+      }
+      o = xyz(q0);
+      pixel = __float_as_int(q0.w);
+      d = xyz(q1);
+      w = xyz(q2);
+    }
+    // closest hit
+    float t = INFINITY;
+    int hit = -1;
+    bool fail = false;
+    if (active) {
+      RayInv ri = make_ray(o, d);
+      hit = traverse<false, kCount>(sc, ri, 0.0f, t, stack, cap, fail, wc);
+      if (fail) atomicOr(sc.status, kErrTraversalLimit);
+    }
+    __syncwarp();
+    if (kPrimary && active) {
+      if (fp.aov_prim) fp.aov_prim[pixel] = hit >= 0 ? __float_as_int(__ldg(&sc.prims[3 * (size_t)hit + 1]).w) : -1;
+      if (fp.aov_t) fp.aov_t[pixel] = hit >= 0 ? t : INFINITY;
+    }
+    // shading
+    bool is_hit = active && hit >= 0;
+    if (active && hit < 0) add_fb(fp.fb, pixel, w * mk3(fp.bg_r, fp.bg_g, fp.bg_b));
+    unsigned hm = __ballot_sync(kFull, is_hit);
+    if (lane == 0 && hm) atomicAdd(&ctr->hits[depth], (unsigned)__popc(hm));
+    f3 p = mk3(0, 0, 0), n = mk3(0, 1, 0), albedo = mk3(0, 0, 0);
+    float ks = 0.f, shin = 1.f, refl = 0.f, ior = 1.f, eps = 0.f;
+    int kind = 0;
+    bool inside = false;
+    if (is_hit) {
+      float4 r0 = __ldg(&sc.prims[3 * (size_t)hit]);
+      float4 r1 = __ldg(&sc.prims[3 * (size_t)hit + 1]);
+      float4 r2 = __ldg(&sc.prims[3 * (size_t)hit + 2]);
+      int mat = __float_as_int(r2.w);
+      p = o + d * t;
+      f3 ng = geometric_normal(r0, r1, r2, p);
+      inside = dot(d, ng) > 0.f;
+      n = inside ? ng * -1.f : ng;
+      float4 m0 = __ldg(&sc.mats[3 * mat]), m1 = __ldg(&sc.mats[3 * mat + 1]), m2 = __ldg(&sc.mats[3 * mat + 2]);
+      albedo = xyz(m0);
+      ks = m0.w;
+      shin = m1.x;
+      refl = m1.y;
+      ior = m1.z;
+      kind = __float_as_int(m1.w);
+      if (m2.x != 0.f || m2.y != 0.f || m2.z != 0.f) add_fb(fp.fb, pixel, w * xyz(m2));   // L_e, Eq. 7
+      eps = fp.eps_scale * fmaxf(1.0f, maxabs(p));
+    }
+    f3 o_up = p + n * eps;
+    bool diel = kind == RT_MAT_DIELECTRIC;
+    float rho = kind == RT_MAT_MIRROR ? refl : 0.f;
+    // Alg. 1: one shadow ray per point light where n.l > 0 (Eq. 8 with point lights)
+    bool local = is_hit && !diel && (1.f - rho) > 0.f;
+    for (int li = 0; li < sc.n_lights; ++li) {
+      float4 L0 = __ldg(&sc.lights[2 * li]), L1 = __ldg(&sc.lights[2 * li + 1]);
+      f3 lp = xyz(L0);
+      bool valid = false;
+      f3 contrib = mk3(0, 0, 0), sd = mk3(0, 0, 1);
+      float tmax = 0.f;
+      if (local) {
+        f3 l = normalize(lp - p);
+        float nl = dot(n, l);
+        if (nl > 0.f) {
+          valid = true;
+          f3 rl = n * (2.f * nl) - l;                  // reflect(-l, n)
+          float rv = -dot(rl, d);
+          float spec = rv > 0.f ? powf(rv, shin) : 0.f;
+          f3 f = albedo * nl + mk3(ks * spec, ks * spec, ks * spec);
+          contrib = w * xyz(L1) * f * (1.f - rho);
+          f3 to_l = lp - o_up;
+          float dist = sqrtf(dot(to_l, to_l));
+          sd = to_l * (1.f / dist);
+          tmax = dist - eps;
+        }
+      }
+      bool ok;
+      unsigned pos = warp_push(&ctr->shadow[depth], valid, fp.shadow_cap, ok, sc.status);
+      if (ok) store_ray(fp.shadowq, pos, o_up, pixel, sd, tmax, contrib);
+    }
+    // reflection / refraction rays (Fig. 3), not past the last depth
+    bool want_r = false, want_t = false;
+    f3 dr = mk3(0, 0, 1), dt = mk3(0, 0, 1), wr = mk3(0, 0, 0), wt = mk3(0, 0, 0);
+    if (is_hit && spawn) {
+      float dn = dot(d, n);
+      if (!diel) {
+        if (rho > 0.f) {
+          want_r = true;
+          dr = normalize(d - n * (2.f * dn));
+          wr = w * rho;
+        }
+      } else {
+        float n1 = inside ? ior : 1.f, n2 = inside ? 1.f : ior;
+        float eta = n1 / n2;
+        float ci = -dn;
+        float k = 1.f - eta * eta * (1.f - ci * ci);
+        float R = 1.f;
+        if (k >= 0.f) {
+          float ct = sqrtf(k);
+          float r0 = (n1 - n2) / (n1 + n2);
+          r0 *= r0;
+          float c = n1 <= n2 ? ci : ct;
+          float x = 1.f - c;
+          R = r0 + (1.f - r0) * x * x * x * x * x;
+          want_t = true;
+          dt = normalize(d * eta + n * (eta * ci - ct));
+          wt = w * (1.f - R);
+        }
+        want_r = true;
+        dr = normalize(d - n * (2.f * dn));
+        wr = w * R;
+      }
+    }
+    {
+      bool ok;
+      unsigned pos = warp_push(&ctr->rays[depth + 1], want_r, fp.ray_cap, ok, sc.status);
+      if (ok) store_ray(qout, pos, o_up, pixel, dr, INFINITY, wr);
+      pos = warp_push(&ctr->rays[depth + 1], want_t, fp.ray_cap, ok, sc.status);
+      if (ok) store_ray(qout, pos, p - n * eps, pixel, dt, INFINITY, wt);
+    }
+  }
+  flush_work<kCount>(ctr, 0, wc);
+}
+
+// ---------------------------------------------------------------------------
+// shadow rays: any hit on (0, tmax); unblocked -> add the light's term
+// ---------------------------------------------------------------------------
+template <bool kCount>
+__global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FrameParams fp, int depth, int cap) {
+  __shared__ int s_stack[kStackSize * kTraceThreads];
+  int* stack = s_stack + threadIdx.x;
+  int lane = threadIdx.x & 31;
+  Counters* ctr = fp.ctr;
+  unsigned n_items = min(ctr->shadow[depth], fp.shadow_cap);
+  WorkCount wc = {0u, 0u};
+  for (;;) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&ctr->fetch_shadow[depth], 32u);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= n_items) break;
+    unsigned idx = base + lane;
+    if (idx < n_items) {
+      const float4* q = fp.shadowq + 3 * (size_t)idx;
+      float4 q0 = q[0], q1 = q[1], q2 = q[2];
+      RayInv ri = make_ray(xyz(q0), xyz(q1));
+      float tmax = q1.w;
+      bool fail = false;
+      int h = traverse<true, kCount>(sc, ri, 0.0f, tmax, stack, cap, fail, wc);
+      if (fail) atomicOr(sc.status, kErrTraversalLimit);
+      if (h < 0 && !fail) add_fb(fp.fb, __float_as_int(q0.w), xyz(q2));
+    }
+  }
+  flush_work<kCount>(ctr, 1, wc);
+}
+
+// ---------------------------------------------------------------------------
+// plain queries on caller rays
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTraceThreads) k_query(DevScene sc, const float* __restrict__ o,
+                                                         const float* __restrict__ d, const float* __restrict__ tmax_in,
+                                                         int64_t n, float tmin, int any, int cap,
+                                                         int32_t* __restrict__ prim_out, float* __restrict__ t_out,
+                                                         uint8_t* __restrict__ occ_out) {
+  __shared__ int s_stack[kStackSize * kTraceThreads];
+  int* stack = s_stack + threadIdx.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  RayInv ri = make_ray(mk3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
+  bool fail = false;
+  WorkCount wc = {0u, 0u};
+  if (any) {
+    float tm = tmax_in[i];
+    int h = traverse<true, false>(sc, ri, tmin, tm, stack, cap, fail, wc);
+    occ_out[i] = h >= 0 ? 1 : 0;
+  } else {
+    float t = INFINITY;
+    int h = traverse<false, false>(sc, ri, tmin, t, stack, cap, fail, wc);
+    prim_out[i] = h >= 0 ? __float_as_int(sc.prims[3 * (size_t)h + 1].w) : -1;
+    t_out[i] = h >= 0 ? t : INFINITY;
+  }
+  if (fail) atomicOr(sc.status, kErrTraversalLimit);
+}
+
+__global__ void k_camera_rays(CamBasis cb, int W, int H, float* __restrict__ o, float* __restrict__ d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= W * H) return;
+  f3 oo, dd;
+  camera_ray(cb, W, H, i % W, i / W, oo, dd);
+  o[3 * i] = oo.x;
+  o[3 * i + 1] = oo.y;
+  o[3 * i + 2] = oo.z;
+  d[3 * i] = dd.x;
+  d[3 * i + 1] = dd.y;
+  d[3 * i + 2] = dd.z;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static CamBasis camera_basis(const rt_camera* c, int W, int H) {
+  // host FP32 arithmetic, once per frame
+  CamBasis cb;
+  float fx = c->look_at[0] - c->eye[0], fy = c->look_at[1] - c->eye[1], fz = c->look_at[2] - c->eye[2];
+  float fl = 1.0f / std::sqrt(fx * fx + fy * fy + fz * fz);
+  fx *= fl;
+  fy *= fl;
+  fz *= fl;
+  float ux = c->up[0], uy = c->up[1], uz = c->up[2];
+  float rx = fy * uz - fz * uy, ry = fz * ux - fx * uz, rz = fx * uy - fy * ux;
+  float rl = 1.0f / std::sqrt(rx * rx + ry * ry + rz * rz);
+  rx *= rl;
+  ry *= rl;
+  rz *= rl;
+  cb.eye = {c->eye[0], c->eye[1], c->eye[2]};
+  cb.f = {fx, fy, fz};
+  cb.r = {rx, ry, rz};
+  cb.u = {ry * fz - rz * fy, rz * fx - rx * fz, rx * fy - ry * fx};
+  cb.h = std::tan(0.5f * c->vfov_deg * 3.14159265358979f / 180.0f);
+  cb.aspect = (float)W / (float)H;
+  return cb;
+}
+
+static int g_blocks_per_sm_trace = 0, g_blocks_per_sm_shadow = 0;
+
+static void occupancy(rt_scene* s) {
+  if (s->trace_blocks) return;
+  int a = 0, b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<false, false>, kTraceThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_shadow<false>, kTraceThreads, 0);
+  g_blocks_per_sm_trace = std::max(a, 1);
+  g_blocks_per_sm_shadow = std::max(b, 1);
+  s->trace_blocks = s->sm_count * g_blocks_per_sm_trace;
+  s->shadow_blocks = s->sm_count * g_blocks_per_sm_shadow;
+}
+
+static bool finite_cam(const rt_camera* c) {
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(c->eye[i]) || !std::isfinite(c->look_at[i]) || !std::isfinite(c->up[i])) return false;
+  if (!std::isfinite(c->vfov_deg) || !(c->vfov_deg > 0.f) || !(c->vfov_deg < 180.f)) return false;
+  float fx = c->look_at[0] - c->eye[0], fy = c->look_at[1] - c->eye[1], fz = c->look_at[2] - c->eye[2];
+  if (fx == 0.f && fy == 0.f && fz == 0.f) return false;
+  float rx = fy * c->up[2] - fz * c->up[1], ry = fz * c->up[0] - fx * c->up[2], rz = fx * c->up[1] - fy * c->up[0];
+  return rx != 0.f || ry != 0.f || rz != 0.f;
+}
+
+// Records a stage boundary of the frame on the scene's reusable events.
+static void mark_stage(rt_scene* s, int kind, cudaStream_t st) {
+  if ((size_t)s->tcount >= s->tev.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    s->tev.push_back(e);
+    s->tkind.push_back(0);
+  }
+  s->tkind[s->tcount] = kind;
+  cudaEventRecord(s->tev[s->tcount], st);
+  s->tcount++;
+}
+
+// Stage times of the last timed frame (waits for its last event).
+static rt_status stage_times(rt_scene* s, float* total, float* trace, float* shadow) {
+  *total = *trace = *shadow = 0.f;
+  if (s->tcount < 2) return set_error(RT_ERR_INVALID_ARG, "no frame was rendered with RT_FLAG_STAGE_TIMING");
+  cudaError_t e = cudaEventSynchronize(s->tev[s->tcount - 1]);
+  if (e != cudaSuccess) return cuda_error(e, "stage times");
+  cudaEventElapsedTime(total, s->tev[0], s->tev[s->tcount - 1]);
+  for (int i = 0; i + 1 < s->tcount; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->tev[i], s->tev[i + 1]);
+    if (s->tkind[i] == 0) *trace += ms;
+    else if (s->tkind[i] == 1) *shadow += ms;
+  }
+  return RT_OK;
+}
+
+static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, int D, float* out,
+                             const rt_render_options* opt_in, int32_t* aov_prim, float* aov_t, rt_render_stats* stats,
+                             cudaStream_t st) {
+  if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_render: scene is NULL");
+  if (!cam || !finite_cam(cam)) return set_error(RT_ERR_INVALID_ARG, "rt_render: invalid camera");
+  if (W < 1 || H < 1) return set_error(RT_ERR_INVALID_ARG, "rt_render: width and height must be >= 1");
+  if ((int64_t)W * H > (int64_t)1 << 30) return set_error(RT_ERR_UNSUPPORTED, "rt_render: image too large");
+  if (D < 0 || D > RT_MAX_DEPTH) return set_error(RT_ERR_INVALID_ARG, "rt_render: max_depth outside [0, 16]");
+  if (!out) return set_error(RT_ERR_INVALID_ARG, "rt_render: out_rgb is NULL");
+  rt_render_options opt;
+  rt_render_options_default(&opt);
+  if (opt_in) opt = *opt_in;
+  if (!std::isfinite(opt.background[0]) || !std::isfinite(opt.background[1]) || !std::isfinite(opt.background[2]) ||
+      !std::isfinite(opt.eps_scale) || opt.eps_scale < 0.f || opt.queue_capacity < 0 || opt.traversal_cap < 0)
+    return set_error(RT_ERR_INVALID_ARG, "rt_render: invalid options");
+  bool use_bvh = opt.use_bvh != 0;
+  if (use_bvh && !s->built) return set_error(RT_ERR_NOT_BUILT, "rt_render: BVH requested before rt_bvh_build");
+  occupancy(s);
+  int64_t qcap = opt.queue_capacity > 0 ? opt.queue_capacity : std::max<int64_t>(2 * (int64_t)W * H, 65536);
+  int64_t scap = qcap * std::max<int64_t>(s->n_lights, 1);
+  if (qcap > 0x7fffffffLL || scap > 0x7fffffffLL) return set_error(RT_ERR_UNSUPPORTED, "rt_render: queue too large");
+  int64_t pcap = std::max<int64_t>((int64_t)W * H * std::max<int64_t>(s->n_lights, 1), scap);
+  rt_status rs;
+  if ((rs = ensure(s->rayq[0], (size_t)qcap * 48)) || (rs = ensure(s->rayq[1], (size_t)qcap * 48)) ||
+      (rs = ensure(s->shadowq, (size_t)pcap * 48)) || (rs = ensure(s->counters, sizeof(Counters))))
+    return rs;
+  s->ray_cap = qcap;
+  s->shadow_cap = pcap;
+  DevScene sc = dev_scene(s, use_bvh);
+  int64_t tcap = opt.traversal_cap > 0 ? opt.traversal_cap : 4 * std::max<int64_t>(s->n_nodes_total, 1) + 64;
+  int cap = (int)std::min<int64_t>(tcap, 0x7fffffff);
+  FrameParams fp;
+  fp.cam = camera_basis(cam, W, H);
+  fp.W = W;
+  fp.H = H;
+  fp.tiles_x = (W + 7) / 8;
+  fp.tiles_y = (H + 3) / 4;
+  fp.max_depth = D;
+  fp.bg_r = opt.background[0];
+  fp.bg_g = opt.background[1];
+  fp.bg_b = opt.background[2];
+  fp.eps_scale = opt.eps_scale;
+  fp.fb = out;
+  fp.aov_prim = aov_prim;
+  fp.aov_t = aov_t;
+  fp.rayq[0] = (float4*)s->rayq[0].p;
+  fp.rayq[1] = (float4*)s->rayq[1].p;
+  fp.shadowq = (float4*)s->shadowq.p;
+  fp.ray_cap = (unsigned)qcap;
+  fp.shadow_cap = (unsigned)pcap;
+  fp.ctr = (Counters*)s->counters.p;
+  bool timing = (opt.flags & RT_FLAG_STAGE_TIMING) != 0;
+  bool count = (opt.flags & RT_FLAG_COUNT_WORK) != 0;
+  int launches = 0;
+  if (timing) {
+    s->tcount = 0;
+    mark_stage(s, 3, st);
+  }
+  auto mark = [&](int kind) {
+    if (timing) mark_stage(s, kind, st);
+  };
+  cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);
+  cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
+  for (int depth = 0; depth <= D; ++depth) {
+    mark(0);
+    if (depth == 0) {
+      if (count) k_trace<true, true><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, 0, cap);
+      else k_trace<true, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, 0, cap);
+    } else {
+      if (count) k_trace<false, true><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+      else k_trace<false, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+    }
+    mark(1);
+    if (count) k_shadow<true><<<s->shadow_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+    else k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+    launches += 2;
+  }
+  mark(2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "rt_render launch");
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    Counters c;
+    e = cudaMemcpyAsync(&c, fp.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "rt_render stats");
+    stats->primary = (uint64_t)W * H;
+    stats->rays_per_depth[0] = stats->primary;
+    for (int d = 0; d <= D; ++d) {
+      if (d > 0) {
+        stats->rays_per_depth[d] = std::min<uint64_t>(c.rays[d], (uint64_t)qcap);
+        stats->secondary += stats->rays_per_depth[d];
+      }
+      stats->shadow_per_depth[d] = std::min<uint64_t>(c.shadow[d], (uint64_t)pcap);
+      stats->shadow += stats->shadow_per_depth[d];
+      stats->hits_per_depth[d] = c.hits[d];
+    }
+    for (int k = 0; k < 2; ++k) {
+      stats->node_visits[k] = c.visits[k];
+      stats->prim_tests[k] = c.tests[k];
+    }
+    stats->launches = launches;
+    if (timing) stage_times(s, &stats->ms_total, &stats->ms_trace, &stats->ms_shadow);
+    rt_status sync_st = rt_scene_sync(s, st);
+    if (sync_st != RT_OK) return sync_st;
+  }
+  return RT_OK;
+}
+
+}  // namespace rtb
+
+using namespace rtb;
+
+extern "C" {
+
+rt_status rt_render(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth, float* out,
+                    void* stream) {
+  return render_impl(s, cam, width, height, max_depth, out, nullptr, nullptr, nullptr, nullptr,
+                     (cudaStream_t)stream);
+}
+
+rt_status rt_render_ex(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth, float* out,
+                       const rt_render_options* opt, int32_t* aov_prim, float* aov_t, rt_render_stats* stats,
+                       void* stream) {
+  return render_impl(s, cam, width, height, max_depth, out, opt, aov_prim, aov_t, stats, (cudaStream_t)stream);
+}
+
+rt_status rt_render_host(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth, float* out_host,
+                         const rt_render_options* opt, void* stream) {
+  if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_render_host: scene is NULL");
+  if (!out_host) return set_error(RT_ERR_INVALID_ARG, "rt_render_host: out_rgb_host is NULL");
+  if (width < 1 || height < 1) return set_error(RT_ERR_INVALID_ARG, "rt_render_host: bad size");
+  size_t bytes = (size_t)width * height * 3 * sizeof(float);
+  rt_status rs = ensure(s->fb_host_stage, bytes);
+  if (rs) return rs;
+  cudaStream_t st = (cudaStream_t)stream;
+  rs = render_impl(s, cam, width, height, max_depth, (float*)s->fb_host_stage.p, opt, nullptr, nullptr, nullptr, st);
+  if (rs) return rs;
+  cudaError_t e = cudaMemcpyAsync(out_host, s->fb_host_stage.p, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "rt_render_host");
+  return RT_OK;
+}
+
+rt_status rt_render_stage_times(rt_scene* s, float* ms_total, float* ms_trace, float* ms_shadow) {
+  if (!s || !ms_total || !ms_trace || !ms_shadow)
+    return set_error(RT_ERR_INVALID_ARG, "rt_render_stage_times: NULL argument");
+  return stage_times(s, ms_total, ms_trace, ms_shadow);
+}
+
+rt_status rt_camera_rays(const rt_camera* cam, int width, int height, float* o, float* d, void* stream) {
+  if (!cam || !finite_cam(cam)) return set_error(RT_ERR_INVALID_ARG, "rt_camera_rays: invalid camera");
+  if (width < 1 || height < 1 || !o || !d) return set_error(RT_ERR_INVALID_ARG, "rt_camera_rays: bad argument");
+  int n = width * height;
+  k_camera_rays<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(camera_basis(cam, width, height), width, height,
+                                                                    o, d);
+  return cuda_error(cudaGetLastError(), "rt_camera_rays");
+}
+
+static rt_status query(rt_scene* s, const float* o, const float* d, const float* tmax, int64_t n, float tmin,
+                       int use_bvh, int any, int32_t* prim, float* t, uint8_t* occ, cudaStream_t st) {
+  if (!s || !o || !d || n < 0) return set_error(RT_ERR_INVALID_ARG, "rt_trace: bad argument");
+  if (any ? (!tmax || !occ) : (!prim || !t)) return set_error(RT_ERR_INVALID_ARG, "rt_trace: NULL output");
+  if (use_bvh && !s->built) return set_error(RT_ERR_NOT_BUILT, "rt_trace: BVH requested before rt_bvh_build");
+  if (n == 0) return RT_OK;
+  DevScene sc = dev_scene(s, use_bvh != 0);
+  int cap = (int)std::min<int64_t>(4 * std::max<int64_t>(s->n_nodes_total, 1) + 64, 0x7fffffff);
+  int64_t blocks = (n + kTraceThreads - 1) / kTraceThreads;
+  k_query<<<(unsigned)blocks, kTraceThreads, 0, st>>>(sc, o, d, tmax, n, tmin, any, cap, prim, t, occ);
+  return cuda_error(cudaGetLastError(), "rt_trace");
+}
+
+rt_status rt_trace_closest(rt_scene* s, const float* o, const float* d, int64_t n, float tmin, int use_bvh,
+                           int32_t* prim, float* t, void* stream) {
+  return query(s, o, d, nullptr, n, tmin, use_bvh, 0, prim, t, nullptr, (cudaStream_t)stream);
+}
+
+rt_status rt_trace_any(rt_scene* s, const float* o, const float* d, const float* tmax, int64_t n, float tmin,
+                       int use_bvh, uint8_t* occ, void* stream) {
+  return query(s, o, d, tmax, n, tmin, use_bvh, 1, nullptr, nullptr, occ, (cudaStream_t)stream);
+}
+
+rt_status rt_scene_destroy(rt_scene* s) {
+  if (!s) return RT_OK;
+  cudaDeviceSynchronize();
+  release(s->raw_sph);
+  release(s->raw_tri);
+  release(s->prims_id);
+  release(s->prims_leaf);
+  release(s->mats);
+  release(s->lights);
+  release(s->nodes);
+  release(s->build_tmp);
+  release(s->build_info);
+  release(s->rayq[0]);
+  release(s->rayq[1]);
+  release(s->shadowq);
+  release(s->counters);
+  release(s->fb_host_stage);
+  for (auto e : s->tev) cudaEventDestroy(e);
+  if (s->status) cudaFree(s->status);
+  delete s;
+  return RT_OK;
+}
+
+}  // extern "C"

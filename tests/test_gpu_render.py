@@ -1,0 +1,402 @@
+"""GPU parity of the CUDA tracer against the FP64 oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1504_03151_b300 as rtb
+from paper_1504_03151_b300 import build as rtb_build
+from paper_1504_03151_b300 import scenes as S
+
+from gpu_helpers import COLOUR_TOL, compare, gpu_render, oracle_render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(gpu):
+    rtb_build.build()
+    torch.cuda.set_device(0)
+
+
+def small_terrain(w=96, h=64, depth=5, seed=7):
+    return S.scene_terrain(seed=seed, width=w, height=h, max_depth=depth, cells=(16, 12), n_ico=6, ico_level=2)
+
+
+# ---------------------------------------------------------------------------
+# closed forms on the GPU
+# ---------------------------------------------------------------------------
+def test_lambert_sphere_closed_form():
+    sc = S.single_sphere(width=65, height=65)
+    g = gpu_render(sc, use_bvh=True)
+    o, d = O.camera_rays(sc.camera, 65, 65)
+    tca = -(o * d).sum(1)
+    dist2 = (o * o).sum(1) - tca ** 2
+    hit = dist2 <= 1.0
+    p = o + (tca - np.sqrt(np.clip(1 - dist2, 0, None)))[:, None] * d
+    l = np.array([0, 0, 10.0]) - p
+    l /= np.linalg.norm(l, axis=1, keepdims=True)
+    exp = np.where(hit[:, None], np.array([0.7, 0.5, 0.3]) * np.clip((p * l).sum(1), 0, None)[:, None], 0.1)
+    edge = np.abs(dist2 - 1.0) < 1e-4          # silhouette pixels: hit/miss decided by rounding
+    err = np.abs(g["rgb"] - exp).max(axis=1)
+    assert err[~edge].max() < 1e-5
+    np.testing.assert_array_equal(g["prim"][~edge] >= 0, hit[~edge])
+
+
+def test_camera_rays_match_oracle():
+    for sc in (S.scene_spheres8(width=37, height=23), S.scene_terrain(width=64, height=36)):
+        W, H = sc.width, sc.height
+        o = torch.empty(W * H * 3, device="cuda")
+        d = torch.empty(W * H * 3, device="cuda")
+        rtb.rt_camera_rays(sc.camera, W, H, o, d)
+        torch.cuda.synchronize()
+        ro, rd = O.camera_rays(sc.camera, W, H)
+        np.testing.assert_allclose(o.view(-1, 3).cpu().numpy(), ro, atol=1e-6)
+        np.testing.assert_allclose(d.view(-1, 3).cpu().numpy(), rd, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# image parity
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("use_bvh", [False, True])
+def test_spheres8_parity(use_bvh):
+    sc = S.scene_spheres8()
+    ref = oracle_render(sc, mode="brute")
+    g = gpu_render(sc, use_bvh=use_bvh)
+    rep = compare(g, ref)
+    assert rep["max_err_robust"] < 1e-4, rep
+    st = g["stats"]
+    c = ref["counts"]
+    assert st["primary"] == c["primary"] == 256 * 256
+    for k in ("shadow", "secondary"):
+        assert abs(st[k] - c[k]) <= 1e-3 * c[k] + 4, (k, st[k], c[k])
+
+
+def test_terrain_small_parity_all_modes():
+    sc = small_terrain()
+    ref = oracle_render(sc, mode="brute")
+    gb = gpu_render(sc, use_bvh=False)
+    gv = gpu_render(sc, use_bvh=True)
+    compare(gb, ref)
+    compare(gv, ref)
+    # BVH and brute force on the GPU: same FP32 tests, same answer
+    np.testing.assert_array_equal(gb["prim"], gv["prim"])
+    np.testing.assert_allclose(gb["rgb"], gv["rgb"], atol=1e-5)
+
+
+@pytest.mark.parametrize("wh", [(1, 1), (7, 3), (37, 23), (8, 4), (129, 65)])
+def test_ragged_sizes(wh):
+    W, H = wh
+    sc = S.scene_spheres8(width=W, height=H)
+    ref = oracle_render(sc, mode="brute")
+    g = gpu_render(sc)
+    compare(g, ref, budget=1.0 if W * H < 1000 else 1e-3)
+
+
+def test_terrain_1080p_full_frame_parity():
+    sc = S.scene_terrain()
+    g = gpu_render(sc)
+    ref = oracle_render(sc, mode="bvh")
+    rep = compare(g, ref)
+    st = g["stats"]
+    c = ref["counts"]
+    assert st["primary"] == 1920 * 1080
+    for k in ("shadow", "secondary"):
+        assert abs(st[k] - c[k]) <= 1e-3 * c[k], (k, st[k], c[k])
+    for d in range(sc.max_depth + 1):
+        assert abs(st["rays_per_depth"][d] - c["rays_per_depth"][d]) <= 1e-3 * c["rays_per_depth"][d] + 16
+    print(rep)
+
+
+def test_depth_zero_and_max_depth():
+    sc = S.scene_spheres8(width=64, height=64)
+    for D in (0, 1, 16):
+        ref = oracle_render(sc, mode="brute", max_depth=D)
+        g = gpu_render(sc, max_depth=D)
+        compare(g, ref, budget=2e-3)
+        if D == 0:
+            assert g["stats"]["secondary"] == 0
+
+
+# ---------------------------------------------------------------------------
+# intersection parity on the GPU's own FP32 rays
+# ---------------------------------------------------------------------------
+def _gpu_closest(scene, o, d, use_bvh=True):
+    n = len(o)
+    od = torch.from_numpy(np.ascontiguousarray(o, np.float32)).cuda()
+    dd = torch.from_numpy(np.ascontiguousarray(d, np.float32)).cuda()
+    prim = torch.empty(n, dtype=torch.int32, device="cuda")
+    t = torch.empty(n, dtype=torch.float32, device="cuda")
+    rtb.rt_trace_closest(scene.handle, od, dd, n, 0.0, use_bvh, prim, t)
+    torch.cuda.synchronize()
+    return prim.cpu().numpy(), t.double().cpu().numpy()
+
+
+def test_intersection_parity_on_gpu_rays():
+    for sc in (S.scene_spheres8(), S.scene_terrain(width=480, height=270)):
+        W, H = sc.width, sc.height
+        o = torch.empty(W * H * 3, device="cuda")
+        d = torch.empty(W * H * 3, device="cuda")
+        rtb.rt_camera_rays(sc.camera, W, H, o, d)
+        o = o.view(-1, 3).cpu().numpy()
+        d = d.view(-1, 3).cpu().numpy()
+        scene = rtb.Scene(sc).build()
+        gp, gt = _gpu_closest(scene, o, d)
+        scene.close()
+        orc = O.OracleScene.from_scene(sc)
+        rp, rt, rb = orc.closest_hits(o, d, use_bvh=True)
+        robust = rb >= 1
+        assert not ((gp != rp) & robust).any()
+        assert (gp != rp).mean() <= 1e-3
+        m = (gp == rp) & (rp >= 0) & robust
+        assert (np.abs(gt[m] - rt[m]) / rt[m]).max() <= 1e-5
+
+
+def test_random_rays_bvh_equals_bruteforce_and_oracle():
+    sc = small_terrain()
+    rng = np.random.default_rng(5)
+    n = 20000
+    o = np.stack([rng.uniform(-34, 34, n), rng.uniform(-2, 12, n), rng.uniform(-26, 26, n)], 1).astype(np.float32)
+    tgt = np.stack([rng.uniform(-32, 32, n), rng.uniform(-3, 5, n), rng.uniform(-24, 24, n)], 1)
+    d = tgt - o
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    scene = rtb.Scene(sc).build()
+    p1, t1 = _gpu_closest(scene, o, d, True)
+    p0, t0 = _gpu_closest(scene, o, d, False)
+    np.testing.assert_array_equal(p1, p0)
+    orc = O.OracleScene.from_scene(sc)
+    rp, rt, rb = orc.closest_hits(o, d, use_bvh=True)
+    assert not ((p1 != rp) & (rb >= 1)).any()
+    # any hit on (0, tmax)
+    tmax = rng.uniform(1, 60, n).astype(np.float32)
+    occ = torch.empty(n, dtype=torch.uint8, device="cuda")
+    rtb.rt_trace_any(scene.handle, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(),
+                     torch.from_numpy(tmax).cuda(), n, 0.0, True, occ)
+    torch.cuda.synchronize()
+    g_occ = occ.cpu().numpy().astype(bool)
+    r_occ, r_rb = orc.any_hits(o, d, tmax, use_bvh=True)
+    assert not ((g_occ != r_occ) & (r_rb >= 1)).any()
+    assert (g_occ != r_occ).mean() <= 1e-3
+    scene.close()
+
+
+# ---------------------------------------------------------------------------
+# BVH structure
+# ---------------------------------------------------------------------------
+def _walk(nodes, root, n_prims):
+    """Visits the traversal layout from the root; returns leaf ranges and depth."""
+    seen = np.zeros(n_prims, np.int32)
+    max_depth = 0
+    stack = [(root, 1)]
+    internal = 0
+    links = nodes[:, 12:14].view(np.int32)
+    while stack:
+        node, depth = stack.pop()
+        internal += 1
+        max_depth = max(max_depth, depth)
+        for c in range(2):
+            link = int(links[node, c])
+            if link < 0:
+                v = ~link
+                start, cnt = v >> 3, (v & 7) + 1
+                seen[start:start + cnt] += 1
+            else:
+                stack.append((link, depth + 1))
+    return seen, max_depth, internal
+
+
+def _child_box(nodes, node, c):
+    n = nodes[node]
+    if c == 0:
+        return np.array([n[0], n[2], n[8]]), np.array([n[1], n[3], n[9]])
+    return np.array([n[4], n[6], n[10]]), np.array([n[5], n[7], n[11]])
+
+
+@pytest.mark.parametrize("which", ["spheres8", "terrain_small", "terrain"])
+def test_bvh_structure_invariants(which):
+    sc = {"spheres8": S.scene_spheres8, "terrain_small": small_terrain, "terrain": S.scene_terrain}[which]()
+    n = sc.n_prims
+    scene = rtb.Scene(sc).build()
+    info = rtb.rt_bvh_get_info(scene.handle)
+    nodes, order, morton = rtb.rt_bvh_export(scene.handle, n, 2 * max(n, 2))
+    scene.close()
+    # the sort: a permutation, codes ascending, equal codes keep index order
+    assert np.array_equal(np.sort(order), np.arange(n))
+    assert (np.diff(morton.astype(np.int64)) >= 0).all()
+    eq = np.diff(morton.astype(np.int64)) == 0
+    assert (np.diff(order)[eq] > 0).all()
+    # every primitive in exactly one leaf reachable from the root
+    root = info["root"]
+    seen, depth, internal = _walk(nodes, root, n)
+    assert (seen == 1).all()
+    assert depth == info["max_depth"] and internal == info["n_nodes"]
+    assert depth <= 64
+    # every child box holds its primitives (leaf boxes) / child's children
+    prim_lo = np.zeros((n, 3))
+    prim_hi = np.zeros((n, 3))
+    ns = len(sc.spheres)
+    if ns:
+        c, r = sc.spheres["center"].astype(np.float64), sc.spheres["radius"].astype(np.float64)
+        prim_lo[:ns], prim_hi[:ns] = c - r[:, None], c + r[:, None]
+    if len(sc.triangles):
+        V = np.stack([sc.triangles["v0"], sc.triangles["v1"], sc.triangles["v2"]], 1).astype(np.float64)
+        prim_lo[ns:], prim_hi[ns:] = V.min(1), V.max(1)
+    links = nodes[:, 12:14].view(np.int32)
+    stack = [root]
+    while stack:
+        node = stack.pop()
+        for c in range(2):
+            lo, hi = _child_box(nodes, node, c)
+            link = int(links[node, c])
+            if link < 0:
+                v = ~link
+                ids = order[(v >> 3):(v >> 3) + (v & 7) + 1]
+                tol = 1e-6 * (1 + np.abs(prim_lo[ids]).max())
+                assert (prim_lo[ids] >= lo - tol).all() and (prim_hi[ids] <= hi + tol).all()
+            else:
+                for cc in range(2):
+                    clo, chi = _child_box(nodes, link, cc)
+                    assert (clo >= lo).all() and (chi <= hi).all()
+                stack.append(link)
+    # refinement never makes the tree worse than the plain LBVH by SAH
+    assert info["sah_cost"] <= info["sah_cost_lbvh"] * 1.001 or which == "spheres8"
+
+
+def test_morton_codes_against_cpu_interleave():
+    sc = S.scene_terrain()
+    n = sc.n_prims
+    scene = rtb.Scene(sc).build()
+    _, order, morton = rtb.rt_bvh_export(scene.handle, n, 2 * n)
+    scene.close()
+    V = np.stack([sc.triangles["v0"], sc.triangles["v1"], sc.triangles["v2"]], 1).astype(np.float64)
+    c = 0.5 * (V.min(1) + V.max(1))
+    lo, hi = c.min(0), c.max(0)
+    q = np.clip(((c - lo) / (hi - lo) * 1024).astype(np.int64), 0, 1023)
+
+    def spread(v):
+        out = np.zeros_like(v)
+        for b in range(10):
+            out |= ((v >> b) & 1) << (3 * b)
+        return out
+
+    code = (spread(q[:, 0]) << 2) | (spread(q[:, 1]) << 1) | spread(q[:, 2])
+    got = morton.astype(np.int64)
+    exp = code[order]
+    # quantisation may differ by one cell where a centroid sits on a cell edge
+    assert (got == exp).mean() > 0.999
+
+    def unspread(v):
+        out = np.zeros_like(v)
+        for b in range(10):
+            out |= ((v >> (3 * b)) & 1) << b
+        return out
+
+    for shift in (2, 1, 0):
+        assert np.abs(unspread(got >> shift) - unspread(exp >> shift)).max() <= 1
+
+
+# ---------------------------------------------------------------------------
+# host API behaviour
+# ---------------------------------------------------------------------------
+def test_render_host_matches_device():
+    sc = S.scene_spheres8(width=64, height=48)
+    g = gpu_render(sc)
+    scene = rtb.Scene(sc).build()
+    host = np.zeros(64 * 48 * 3, np.float32)
+    rtb.rt_render_host(scene.handle, sc.camera, 64, 48, sc.max_depth, host,
+                       rtb.make_options(background=sc.background))
+    scene.close()
+    np.testing.assert_allclose(host.reshape(-1, 3), g["rgb"], atol=1e-6)
+
+
+def test_scene_update_then_rebuild():
+    a = small_terrain(seed=7)
+    b = small_terrain(seed=8)
+    assert len(a.triangles) == len(b.triangles)
+    scene = rtb.Scene(a).build()
+    rtb.rt_scene_update(scene.handle, b.spheres, b.triangles)
+    rtb.rt_bvh_build(scene.handle)
+    out = torch.empty(b.width * b.height * 3, device="cuda")
+    rtb.rt_render_ex(scene.handle, b.camera, b.width, b.height, b.max_depth, out,
+                     rtb.make_options(background=b.background))
+    torch.cuda.synchronize()
+    fresh = gpu_render(b)
+    np.testing.assert_allclose(out.view(-1, 3).double().cpu().numpy(), fresh["rgb"], atol=1e-5)
+    scene.close()
+
+
+def test_not_built_is_reported():
+    sc = S.scene_spheres8(width=8, height=8)
+    scene = rtb.Scene(sc)
+    out = torch.empty(8 * 8 * 3, device="cuda")
+    with pytest.raises(rtb.RtError) as ei:
+        rtb.rt_render(scene.handle, sc.camera, 8, 8, 3, out)
+    assert ei.value.status == rtb.RT_ERR_NOT_BUILT
+    # brute force needs no BVH
+    rtb.rt_render_ex(scene.handle, sc.camera, 8, 8, 3, out, rtb.make_options(use_bvh=False))
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    scene.close()
+
+
+def test_invalid_render_arguments():
+    sc = S.scene_spheres8(width=8, height=8)
+    scene = rtb.Scene(sc).build()
+    out = torch.empty(8 * 8 * 3, device="cuda")
+    for w, h, d in ((0, 8, 3), (8, -1, 3), (8, 8, -1), (8, 8, 17)):
+        with pytest.raises(rtb.RtError) as ei:
+            rtb.rt_render(scene.handle, sc.camera, w, h, d, out)
+        assert ei.value.status == rtb.RT_ERR_INVALID_ARG
+    scene.close()
+
+
+def test_queue_overflow_is_reported_not_hung():
+    sc = small_terrain()
+    scene = rtb.Scene(sc).build()
+    out = torch.empty(sc.width * sc.height * 3, device="cuda")
+    rtb.rt_render_ex(scene.handle, sc.camera, sc.width, sc.height, sc.max_depth, out,
+                     rtb.make_options(queue_capacity=8))
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_ERR_QUEUE_OVERFLOW
+    # the status is cleared once read; a normal render is fine afterwards
+    rtb.rt_render(scene.handle, sc.camera, sc.width, sc.height, sc.max_depth, out)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    scene.close()
+
+
+def test_traversal_limit_is_reported_not_hung():
+    sc = small_terrain()
+    scene = rtb.Scene(sc).build()
+    out = torch.empty(sc.width * sc.height * 3, device="cuda")
+    rtb.rt_render_ex(scene.handle, sc.camera, sc.width, sc.height, sc.max_depth, out,
+                     rtb.make_options(traversal_cap=1))
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_ERR_TRAVERSAL_LIMIT
+    scene.close()
+
+
+def test_empty_scene_and_single_primitive():
+    mats = S.material(S.MAT_DIFFUSE, (0.5, 0.5, 0.5))
+    li = S.lights([(0, 10, 0)], [(1, 1, 1)])
+    empty = S.Scene("empty", np.zeros(0, S.SPHERE_DTYPE), np.zeros(0, S.TRIANGLE_DTYPE), mats, li,
+                    S.camera((0, 0, 5), (0, 0, 0)), 16, 8, 2)
+    g = gpu_render(empty)
+    np.testing.assert_allclose(g["rgb"], 0.1, atol=0)
+    assert (g["prim"] == -1).all() and np.isinf(g["t"]).all()
+    one = S.single_sphere(width=33, height=33)
+    compare(gpu_render(one), oracle_render(one, mode="brute"))
+    tri = S.Scene("tri", np.zeros(0, S.SPHERE_DTYPE),
+                  S.triangles_from([(-1, -1, 0)], [(1, -1, 0)], [(0, 1, 0)], 0), mats, li,
+                  S.camera((0, 0, 5), (0, 0, 0)), 33, 33, 1)
+    compare(gpu_render(tri), oracle_render(tri, mode="brute"))
+
+
+def test_degenerate_triangles_never_hit():
+    mats = S.material(S.MAT_DIFFUSE, (0.5, 0.5, 0.5))
+    li = S.lights([(0, 10, 0)], [(1, 1, 1)])
+    tris = S.triangles_from([(-1, -1, 0), (-5, 0, 0), (0, 0, 0)], [(1, -1, 0), (5, 0, 0), (0, 0, 0)],
+                            [(0, 1, 0), (0, 0, 0), (0, 0, 0)], 0)   # a line and a point
+    sc = S.Scene("degenerate", np.zeros(0, S.SPHERE_DTYPE), tris, mats, li, S.camera((0, 0, 5), (0, 0, 0)), 33,
+                 33, 1)
+    g = gpu_render(sc)
+    assert set(np.unique(g["prim"])) <= {-1, 0}
+    compare(g, oracle_render(sc, mode="brute"))
