@@ -315,6 +315,9 @@ def test_scene_update_then_rebuild():
     a = small_terrain(seed=7)
     b = small_terrain(seed=8)
     assert len(a.triangles) == len(b.triangles)
+    # only the geometry is replaced: keep a's materials and lights
+    b.materials = a.materials.copy()
+    b.lights = a.lights.copy()
     scene = rtb.Scene(a).build()
     rtb.rt_scene_update(scene.handle, b.spheres, b.triangles)
     rtb.rt_bvh_build(scene.handle)
