@@ -211,6 +211,35 @@ rt_status rt_trace_any(rt_scene* s, const float* o_device, const float* d_device
                        const float* tmax_device, int64_t n, float tmin, int use_bvh,
                        uint8_t* occluded_device, void* stream);
 
+/* Limits of rt_render_noalloc's fixed scratch array. */
+#define RT_NOALLOC_MAX_PIXELS 16384
+#define RT_NOALLOC_MAX_LIGHTS 4
+
+/* rt_render without any device allocation, for callers that may not call
+ * cudaMalloc while they render (a host application or plug-in framework
+ * that owns the GPU memory budget and forbids allocation after start-up,
+ * or code confined to a pre-reserved pool).  The paper has no counterpart:
+ * this is a deployment variant of rt_render.
+ *   - Same frame as rt_render with default options (BVH traversal,
+ *     background 0.1, eps_scale 1e-4); the scene must be built.
+ *   - Ray queues and counters live in one file-scope device array of
+ *     about 9.4 MB (counters + 2 x 2*RT_NOALLOC_MAX_PIXELS ray records +
+ *     2*RT_NOALLOC_MAX_PIXELS*RT_NOALLOC_MAX_LIGHTS shadow records, 48 B
+ *     each) that every GPU loading the library holds until the process
+ *     exits.  width*height > RT_NOALLOC_MAX_PIXELS or more than
+ *     RT_NOALLOC_MAX_LIGHTS lights -> RT_ERR_UNSUPPORTED with a message.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first
+ *     call before any stream capture.
+ *   - All calls share the one array (the counters are cleared at the start
+ *     of each call): calls whose work overlaps on the GPU - on different
+ *     streams, or from different threads - race and corrupt each other.
+ *     Serialise them on one stream.
+ *   - Queue overflow (many dielectric bounces) is latched like rt_render's
+ *     and returned by rt_scene_sync. */
+rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
+                            float* out_rgb_device, void* stream);
+
 /* Waits for `stream` and returns (and clears) the latched kernel error. */
 rt_status rt_scene_sync(rt_scene* s, void* stream);
 

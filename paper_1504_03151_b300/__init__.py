@@ -104,6 +104,7 @@ def lib():
             "rt_camera_rays": (I, [P, I, I, P, P, P]),
             "rt_trace_closest": (I, [P, P, P, I64, F, I, P, P, P]),
             "rt_trace_any": (I, [P, P, P, P, I64, F, I, P, P]),
+            "rt_render_noalloc": (I, [P, P, I, I, I, P, P]),
             "rt_scene_sync": (I, [P, P]),
             "rt_scene_destroy": (I, [P]),
         }
@@ -287,6 +288,13 @@ def rt_trace_closest(scene, o_dev, d_dev, n, tmin, use_bvh, prim_dev, t_dev, str
 def rt_trace_any(scene, o_dev, d_dev, tmax_dev, n, tmin, use_bvh, occluded_dev, stream=None):
     _check(lib().rt_trace_any(scene, _dptr(o_dev), _dptr(d_dev), _dptr(tmax_dev), n, tmin, int(use_bvh),
                               _dptr(occluded_dev), _stream(stream)))
+
+
+def rt_render_noalloc(scene, camera, width, height, max_depth, out_rgb, stream=None):
+    """rt_render without device allocation (fixed scratch; see include/rtb.h for the limits)."""
+    cam = make_camera(camera)
+    _check(lib().rt_render_noalloc(scene, ctypes.byref(cam), width, height, max_depth, _dptr(out_rgb),
+                                   _stream(stream)))
 
 
 def rt_scene_sync(scene, stream=None) -> int:

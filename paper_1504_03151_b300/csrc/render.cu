@@ -749,3 +749,98 @@ rt_status rt_scene_destroy(rt_scene* s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// rt_render_noalloc: the rt_render frame with its ray queues and counters in
+// a fixed, file-scope device array instead of memory allocated on demand.
+//
+// Who needs it: callers that may not allocate device memory while they
+// render - a host application or plug-in framework that owns the GPU memory
+// budget and forbids cudaMalloc after start-up, or code that runs inside a
+// pre-reserved memory pool.  The scene (and its BVH) is still created and
+// built beforehand with the ordinary calls.
+// ---------------------------------------------------------------------------
+namespace rtb {
+
+constexpr int64_t kNoallocMaxPixels = RT_NOALLOC_MAX_PIXELS;
+constexpr int64_t kNoallocMaxLights = RT_NOALLOC_MAX_LIGHTS;
+constexpr int64_t kNoallocRayCap = 2 * kNoallocMaxPixels;                 // per ray queue
+constexpr int64_t kNoallocShadowCap = kNoallocRayCap * kNoallocMaxLights;  // shadow queue
+constexpr size_t kNoallocCounterBytes = (sizeof(Counters) + 255) & ~(size_t)255;
+constexpr size_t kNoallocBytes = kNoallocCounterBytes + (size_t)(2 * kNoallocRayCap + kNoallocShadowCap) * 48;
+
+// Shared by every call on a device; it keeps the last call's contents.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device.
+static void* g_noalloc_addr[64] = {nullptr};
+
+static rt_status noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "rt_render_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 64) return set_error(RT_ERR_UNSUPPORTED, "rt_render_noalloc: device index above 63");
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_error(e, "rt_render_noalloc: cudaGetSymbolAddress");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return RT_OK;
+}
+
+}  // namespace rtb
+
+extern "C" rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int W, int H, int D, float* out,
+                                       void* stream) {
+  using namespace rtb;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_render_noalloc: scene is NULL");
+  if (!cam || !finite_cam(cam)) return set_error(RT_ERR_INVALID_ARG, "rt_render_noalloc: invalid camera");
+  if (W < 1 || H < 1) return set_error(RT_ERR_INVALID_ARG, "rt_render_noalloc: width and height must be >= 1");
+  if (D < 0 || D > RT_MAX_DEPTH) return set_error(RT_ERR_INVALID_ARG, "rt_render_noalloc: max_depth outside [0, 16]");
+  if (!out) return set_error(RT_ERR_INVALID_ARG, "rt_render_noalloc: out_rgb is NULL");
+  if ((int64_t)W * H > kNoallocMaxPixels)
+    return set_error(RT_ERR_UNSUPPORTED, "rt_render_noalloc: width*height exceeds RT_NOALLOC_MAX_PIXELS (" +
+                                             std::to_string(kNoallocMaxPixels) + "); use rt_render");
+  if (s->n_lights > kNoallocMaxLights)
+    return set_error(RT_ERR_UNSUPPORTED, "rt_render_noalloc: more than RT_NOALLOC_MAX_LIGHTS (" +
+                                             std::to_string(kNoallocMaxLights) + ") lights; use rt_render");
+  if (!s->built) return set_error(RT_ERR_NOT_BUILT, "rt_render_noalloc: call rt_bvh_build first");
+  void* base = nullptr;
+  rt_status rs = noalloc_scratch(&base);
+  if (rs) return rs;
+  occupancy(s);
+  char* p = (char*)base;
+  FrameParams fp;
+  fp.cam = camera_basis(cam, W, H);
+  fp.W = W;
+  fp.H = H;
+  fp.tiles_x = (W + 7) / 8;
+  fp.tiles_y = (H + 3) / 4;
+  fp.max_depth = D;
+  fp.bg_r = fp.bg_g = fp.bg_b = 0.1f;
+  fp.eps_scale = 1e-4f;
+  fp.fb = out;
+  fp.aov_prim = nullptr;
+  fp.aov_t = nullptr;
+  fp.ctr = (Counters*)p;
+  fp.rayq[0] = (float4*)(p + kNoallocCounterBytes);
+  fp.rayq[1] = fp.rayq[0] + 3 * kNoallocRayCap;
+  fp.shadowq = fp.rayq[1] + 3 * kNoallocRayCap;
+  fp.ray_cap = (unsigned)kNoallocRayCap;
+  fp.shadow_cap = (unsigned)kNoallocShadowCap;
+  DevScene sc = dev_scene(s, true);
+  int cap = (int)std::min<int64_t>(4 * std::max<int64_t>(s->n_nodes_total, 1) + 64, 0x7fffffff);
+  // the counters must start at zero; the queues are written before they are read
+  cudaError_t e = cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);
+  if (e != cudaSuccess) return cuda_error(e, "rt_render_noalloc memset");
+  for (int depth = 0; depth <= D; ++depth) {
+    if (depth == 0) k_trace<true, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, 0, cap);
+    else k_trace<false, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+    k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+  }
+  return cuda_error(cudaGetLastError(), "rt_render_noalloc launch");
+}
