@@ -165,6 +165,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--per-depth", action="store_true", help="queue every depth (no depth-first secondary paths)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -197,8 +198,9 @@ def main():
     out = torch.empty(H * W * 3, device=dev, dtype=torch.float32)
     out_pin = torch.empty(H * W * 3, dtype=torch.float32).pin_memory()
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)   # > L2 (126 MB)
-    opts = rtb.make_options(background=sc.background)
-    opts_t = rtb.make_options(background=sc.background, flags=rtb.RT_FLAG_STAGE_TIMING)
+    mode = rtb.RT_FLAG_PER_DEPTH_WAVEFRONT if args.per_depth else 0
+    opts = rtb.make_options(background=sc.background, flags=mode)
+    opts_t = rtb.make_options(background=sc.background, flags=rtb.RT_FLAG_STAGE_TIMING | mode)
 
     def step(o=None):
         rtb.rt_scene_update(h, None, tri_dev)
@@ -207,10 +209,11 @@ def main():
 
     # rays per frame and algorithmic work (outside the timed region)
     step()
-    st = rtb.rt_render_ex(h, sc.camera, W, H, D, out, rtb.make_options(background=sc.background), stats=True)
+    st = rtb.rt_render_ex(h, sc.camera, W, H, D, out, opts, stats=True)
     rays = st["primary"] + st["shadow"] + st["secondary"]
     work = rtb.rt_render_ex(h, sc.camera, W, H, D, out,
-                            rtb.make_options(background=sc.background, flags=rtb.RT_FLAG_COUNT_WORK), stats=True)
+                            rtb.make_options(background=sc.background, flags=rtb.RT_FLAG_COUNT_WORK | mode),
+                            stats=True)
     info = rtb.rt_bvh_get_info(h)
     assert rtb.rt_scene_sync(h) == rtb.RT_OK
 
@@ -286,7 +289,11 @@ def main():
                          "traffic": None, "peak_source": f"148 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
                                                          f"({pk_kind} clock)",
                          "kernel_ms": kms, "alg_ops": ops},
-            "stage_ms": {"trace": tr, "shadow": sh, "step": ms},
+            "stage_ms": {"trace": tr, "shadow": sh, "step": ms,
+                         "note": "sums of per-kernel times; shadow kernels overlap the next depth's trace"},
+            "work": {"node_visits_per_depth": work["node_visits_per_depth"],
+                     "max_visits_per_ray_per_depth": work["max_visits_per_depth"],
+                     "rays_per_depth": st["rays_per_depth"], "shadow_per_depth": st["shadow_per_depth"]},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tri_bytes.nbytes),
                     "d2h_bytes_per_step": int(H * W * 3 * 4), "ms_per_step": e2e_ms},
             "gpu_launches": launches_per_step * args.steps,

@@ -96,7 +96,9 @@ typedef struct rt_camera {
 enum {
   RT_FLAG_STAGE_TIMING = 1,   /* record per-stage CUDA events (stats.ms_*) */
   RT_FLAG_COUNT_WORK = 2,     /* count node visits / primitive tests (slower kernels) */
-  RT_FLAG_NO_GRAPH = 4        /* launch the kernels directly, no CUDA graph */
+  RT_FLAG_NO_GRAPH = 4,       /* launch the kernels directly, no CUDA graph */
+  RT_FLAG_PER_DEPTH_WAVEFRONT = 8  /* queue every depth (default: depth 0 as a wavefront,
+                                      deeper rays depth-first, one thread per depth-1 subtree) */
 };
 
 typedef struct rt_render_options {
@@ -119,9 +121,11 @@ typedef struct rt_render_stats {
   uint64_t shadow_per_depth[RT_MAX_DEPTH + 1];   /* shadow rays cast from depth-d hits */
   uint64_t hits_per_depth[RT_MAX_DEPTH + 1];
   uint64_t node_visits[2], prim_tests[2];        /* [closest, any]; RT_FLAG_COUNT_WORK only */
+  uint64_t node_visits_per_depth[2][RT_MAX_DEPTH + 1];  /* same, per depth */
+  uint32_t max_visits_per_depth[2][RT_MAX_DEPTH + 1];   /* most node visits of one ray */
   float ms_total;                                /* RT_FLAG_STAGE_TIMING only */
-  float ms_trace;                                /* closest-hit + shade kernels */
-  float ms_shadow;                               /* any-hit kernels */
+  float ms_trace;                                /* closest-hit + shade kernels (sum of their times) */
+  float ms_shadow;                               /* any-hit kernels; they overlap the next depth's trace */
   int32_t launches;                              /* kernels this render launched */
 } rt_render_stats;
 

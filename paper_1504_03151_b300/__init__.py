@@ -38,6 +38,7 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_OOM", 3: "RT_ERR
 RT_FLAG_STAGE_TIMING = 1
 RT_FLAG_COUNT_WORK = 2
 RT_FLAG_NO_GRAPH = 4
+RT_FLAG_PER_DEPTH_WAVEFRONT = 8
 RT_MAX_DEPTH = 16
 
 
@@ -64,6 +65,8 @@ class rt_render_stats(ctypes.Structure):
                 ("shadow_per_depth", ctypes.c_uint64 * (RT_MAX_DEPTH + 1)),
                 ("hits_per_depth", ctypes.c_uint64 * (RT_MAX_DEPTH + 1)),
                 ("node_visits", ctypes.c_uint64 * 2), ("prim_tests", ctypes.c_uint64 * 2),
+                ("node_visits_per_depth", (ctypes.c_uint64 * (RT_MAX_DEPTH + 1)) * 2),
+                ("max_visits_per_depth", (ctypes.c_uint32 * (RT_MAX_DEPTH + 1)) * 2),
                 ("ms_total", ctypes.c_float), ("ms_trace", ctypes.c_float), ("ms_shadow", ctypes.c_float),
                 ("launches", ctypes.c_int32)]
 
@@ -195,6 +198,8 @@ def stats_dict(s: rt_render_stats, max_depth: int) -> dict:
         "rays_per_depth": list(s.rays_per_depth[:n]), "shadow_per_depth": list(s.shadow_per_depth[:n]),
         "hits_per_depth": list(s.hits_per_depth[:n]),
         "node_visits": list(s.node_visits), "prim_tests": list(s.prim_tests),
+        "node_visits_per_depth": [list(s.node_visits_per_depth[k][:n]) for k in range(2)],
+        "max_visits_per_depth": [list(s.max_visits_per_depth[k][:n]) for k in range(2)],
         "ms_total": s.ms_total, "ms_trace": s.ms_trace, "ms_shadow": s.ms_shadow, "launches": s.launches,
     }
 

@@ -32,7 +32,9 @@ struct Counters {
   unsigned hits[RT_MAX_DEPTH + 1];
   unsigned fetch_trace[RT_MAX_DEPTH + 1]; // dynamic work fetch
   unsigned fetch_shadow[RT_MAX_DEPTH + 1];
-  unsigned long long visits[2], tests[2]; // [closest, any]
+  unsigned max_visits[2][RT_MAX_DEPTH + 1];          // [closest, any][depth], counting runs only
+  unsigned long long visits[2][RT_MAX_DEPTH + 1];
+  unsigned long long tests[2][RT_MAX_DEPTH + 1];
 };
 
 struct FrameParams {
@@ -45,7 +47,7 @@ struct FrameParams {
   int32_t* aov_prim;
   float* aov_t;
   float4* rayq[2];
-  float4* shadowq;
+  float4* shadowq[2];                     // shadow queue of depth d: shadowq[d & 1]
   unsigned ray_cap, shadow_cap;
   Counters* ctr;
 };
@@ -71,38 +73,52 @@ __device__ __forceinline__ RayInv make_ray(f3 o, f3 d) {
 }
 
 struct WorkCount {
-  unsigned visits, tests;
+  unsigned visits, tests, vmax;   // vmax: most node visits of one ray
 };
+
+template <bool kAny>
+__device__ __forceinline__ bool test_prim(float4 r0, float4 r1, float4 r2, int k, const RayInv& r, float tmin,
+                                          float& tbest, int& best, int& best_id) {
+  float t;
+  bool h;
+  if (__float_as_int(r0.w) == kKindSphere) h = hit_sphere<!kAny>(r.o, r.d, r0, r1, tmin, tbest, t);
+  else h = hit_triangle<!kAny>(r.o, r.d, r0, r1, r2, tmin, tbest, t);
+  if (h) {
+    if (kAny) {
+      best = k;
+      return true;
+    }
+    int id = __float_as_int(r1.w);
+    if (t < tbest || id < best_id) {
+      tbest = t;
+      best = k;
+      best_id = id;
+    }
+  }
+  return false;
+}
 
 // Tests the primitives [start, start+count) in `prims`.  Closest hit:
 // nearest t, ties to the lower primitive id; any hit: returns at the first.
+// Two records are loaded before either is tested, so a leaf costs one
+// memory round trip per pair rather than per primitive.
 template <bool kAny, bool kCount>
 __device__ __forceinline__ bool leaf_hits(const float4* __restrict__ prims, int start, int count, const RayInv& r,
                                           float tmin, float& tbest, int& best, int& best_id, WorkCount& wc) {
-  for (int k = start; k < start + count; ++k) {
-    float4 r0 = __ldg(&prims[3 * (size_t)k]);
-    float4 r1 = __ldg(&prims[3 * (size_t)k + 1]);
-    float t;
-    bool h;
+  int k = start, end = start + count;
+  for (; k + 1 < end; k += 2) {
+    const float4* a = prims + 3 * (size_t)k;
+    float4 a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2);
+    float4 b0 = __ldg(a + 3), b1 = __ldg(a + 4), b2 = __ldg(a + 5);
+    if (kCount) wc.tests += 2;
+    if (test_prim<kAny>(a0, a1, a2, k, r, tmin, tbest, best, best_id)) return true;
+    if (test_prim<kAny>(b0, b1, b2, k + 1, r, tmin, tbest, best, best_id)) return true;
+  }
+  if (k < end) {
+    const float4* a = prims + 3 * (size_t)k;
+    float4 a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2);
     if (kCount) wc.tests++;
-    if (__float_as_int(r0.w) == kKindSphere) {
-      h = hit_sphere<!kAny>(r.o, r.d, r0, r1, tmin, tbest, t);
-    } else {
-      float4 r2 = __ldg(&prims[3 * (size_t)k + 2]);
-      h = hit_triangle<!kAny>(r.o, r.d, r0, r1, r2, tmin, tbest, t);
-    }
-    if (h) {
-      if (kAny) {
-        best = k;
-        return true;
-      }
-      int id = __float_as_int(r1.w);
-      if (t < tbest || id < best_id) {
-        tbest = t;
-        best = k;
-        best_id = id;
-      }
-    }
+    if (test_prim<kAny>(a0, a1, a2, k, r, tmin, tbest, best, best_id)) return true;
   }
   return false;
 }
@@ -220,24 +236,126 @@ __device__ __forceinline__ void add_fb(float* fb, int pixel, f3 c) {
 }
 
 template <bool kCount>
-__device__ __forceinline__ void flush_work(Counters* ctr, int cls, WorkCount wc) {
+__device__ __forceinline__ void flush_work(Counters* ctr, int cls, int depth, WorkCount wc) {
   if (!kCount) return;
-  unsigned v = wc.visits, t = wc.tests;
+  unsigned v = wc.visits, t = wc.tests, m = wc.vmax;
   for (int o = 16; o > 0; o >>= 1) {
     v += __shfl_xor_sync(kFull, v, o);
     t += __shfl_xor_sync(kFull, t, o);
+    m = max(m, __shfl_xor_sync(kFull, m, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&ctr->visits[cls], (unsigned long long)v);
-    atomicAdd(&ctr->tests[cls], (unsigned long long)t);
+    atomicAdd(&ctr->visits[cls][depth], (unsigned long long)v);
+    atomicAdd(&ctr->tests[cls][depth], (unsigned long long)t);
+    atomicMax(&ctr->max_visits[cls][depth], m);
   }
+}
+
+// ---------------------------------------------------------------------------
+// shading of one hit (shared by the wavefront and the per-path kernels)
+// ---------------------------------------------------------------------------
+struct Surface {
+  f3 p, n, albedo, emission;
+  float ks, shin, rho, ior, eps;
+  int kind;
+  bool inside;
+};
+
+__device__ __forceinline__ Surface surface_at(const DevScene& sc, int hit, f3 o, f3 d, float t, float eps_scale) {
+  Surface sf;
+  float4 r0 = __ldg(&sc.prims[3 * (size_t)hit]);
+  float4 r1 = __ldg(&sc.prims[3 * (size_t)hit + 1]);
+  float4 r2 = __ldg(&sc.prims[3 * (size_t)hit + 2]);
+  int mat = __float_as_int(r2.w);
+  sf.p = o + d * t;
+  f3 ng = geometric_normal(r0, r1, r2, sf.p);
+  sf.inside = dot(d, ng) > 0.f;
+  sf.n = sf.inside ? ng * -1.f : ng;
+  float4 m0 = __ldg(&sc.mats[3 * mat]), m1 = __ldg(&sc.mats[3 * mat + 1]), m2 = __ldg(&sc.mats[3 * mat + 2]);
+  sf.albedo = xyz(m0);
+  sf.ks = m0.w;
+  sf.shin = m1.x;
+  sf.ior = m1.z;
+  sf.kind = __float_as_int(m1.w);
+  sf.rho = sf.kind == RT_MAT_MIRROR ? m1.y : 0.f;
+  sf.emission = xyz(m2);
+  sf.eps = eps_scale * fmaxf(1.0f, maxabs(sf.p));
+  return sf;
+}
+
+// Alg. 1 for one point light (Eq. 8 with point lights): the term the light
+// adds if nothing blocks it, and the shadow ray that decides; false where
+// n.l <= 0 (no shadow ray is cast).
+__device__ __forceinline__ bool light_term(const Surface& sf, f3 d, f3 w, float4 L0, float4 L1, f3& contrib, f3& o_s,
+                                           f3& d_s, float& tmax) {
+  f3 lp = xyz(L0);
+  f3 l = normalize(lp - sf.p);
+  float nl = dot(sf.n, l);
+  if (!(nl > 0.f)) return false;
+  f3 rl = sf.n * (2.f * nl) - l;                  // reflect(-l, n)
+  float rv = -dot(rl, d);
+  float spec = rv > 0.f ? powf(rv, sf.shin) : 0.f;
+  f3 f = sf.albedo * nl + mk3(sf.ks * spec, sf.ks * spec, sf.ks * spec);
+  contrib = w * xyz(L1) * f * (1.f - sf.rho);
+  o_s = sf.p + sf.n * sf.eps;
+  f3 to_l = lp - o_s;
+  float dist = sqrtf(dot(to_l, to_l));
+  d_s = to_l * (1.f / dist);
+  tmax = dist - sf.eps;
+  return true;
+}
+
+// Reflection / refraction rays of a hit (Fig. 3): mirror rho -> reflection
+// of weight rho; dielectric -> Fresnel-Schlick R reflection and 1-R
+// refraction (none on total internal reflection).
+struct Children {
+  bool want_r, want_t;
+  f3 or_, dr, wr, ot, dt, wt;
+};
+
+__device__ __forceinline__ Children children_of(const Surface& sf, f3 d, f3 w) {
+  Children c;
+  c.want_r = c.want_t = false;
+  c.or_ = sf.p + sf.n * sf.eps;
+  c.ot = sf.p - sf.n * sf.eps;
+  c.dr = c.dt = mk3(0, 0, 1);
+  c.wr = c.wt = mk3(0, 0, 0);
+  float dn = dot(d, sf.n);
+  if (sf.kind != RT_MAT_DIELECTRIC) {
+    if (sf.rho > 0.f) {
+      c.want_r = true;
+      c.dr = normalize(d - sf.n * (2.f * dn));
+      c.wr = w * sf.rho;
+    }
+  } else {
+    float n1 = sf.inside ? sf.ior : 1.f, n2 = sf.inside ? 1.f : sf.ior;
+    float eta = n1 / n2;
+    float ci = -dn;
+    float k = 1.f - eta * eta * (1.f - ci * ci);
+    float R = 1.f;
+    if (k >= 0.f) {
+      float ct = sqrtf(k);
+      float r0 = (n1 - n2) / (n1 + n2);
+      r0 *= r0;
+      float cs = n1 <= n2 ? ci : ct;
+      float x = 1.f - cs;
+      R = r0 + (1.f - r0) * x * x * x * x * x;
+      c.want_t = true;
+      c.dt = normalize(d * eta + sf.n * (eta * ci - ct));
+      c.wt = w * (1.f - R);
+    }
+    c.want_r = true;
+    c.dr = normalize(d - sf.n * (2.f * dn));
+    c.wr = w * R;
+  }
+  return c;
 }
 
 // ---------------------------------------------------------------------------
 // closest hit + shade (+ primary ray generation at depth 0)
 // ---------------------------------------------------------------------------
 template <bool kPrimary, bool kCount>
-__global__ void __launch_bounds__(kTraceThreads) k_trace(DevScene sc, FrameParams fp, int depth, int cap) {
+__global__ void __launch_bounds__(kTraceThreads, 6) k_trace(DevScene sc, FrameParams fp, int depth, int cap) {
   __shared__ int s_stack[kStackSize * kTraceThreads];
   int* stack = s_stack + threadIdx.x;
   int lane = threadIdx.x & 31;
@@ -246,7 +364,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(DevScene sc, FrameParam
   const float4* __restrict__ qin = fp.rayq[depth & 1];
   float4* qout = fp.rayq[(depth + 1) & 1];
   bool spawn = depth < fp.max_depth;
-  WorkCount wc = {0u, 0u};
+  WorkCount wc = {0u, 0u, 0u};
   for (;;) {
     unsigned base = 0;
     if (lane == 0) base = atomicAdd(&ctr->fetch_trace[depth], 32u);
@@ -282,7 +400,9 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(DevScene sc, FrameParam
     bool fail = false;
     if (active) {
       RayInv ri = make_ray(o, d);
+      unsigned v0 = wc.visits;
       hit = traverse<false, kCount>(sc, ri, 0.0f, t, stack, cap, fail, wc);
+      if (kCount) wc.vmax = max(wc.vmax, wc.visits - v0);
       if (fail) atomicOr(sc.status, kErrTraversalLimit);
     }
     __syncwarp();
@@ -295,102 +415,37 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(DevScene sc, FrameParam
     if (active && hit < 0) add_fb(fp.fb, pixel, w * mk3(fp.bg_r, fp.bg_g, fp.bg_b));
     unsigned hm = __ballot_sync(kFull, is_hit);
     if (lane == 0 && hm) atomicAdd(&ctr->hits[depth], (unsigned)__popc(hm));
-    f3 p = mk3(0, 0, 0), n = mk3(0, 1, 0), albedo = mk3(0, 0, 0);
-    float ks = 0.f, shin = 1.f, refl = 0.f, ior = 1.f, eps = 0.f;
-    int kind = 0;
-    bool inside = false;
+    Surface sf;
+    sf.kind = RT_MAT_DIELECTRIC;   // no local term, no children unless a hit sets it
     if (is_hit) {
-      float4 r0 = __ldg(&sc.prims[3 * (size_t)hit]);
-      float4 r1 = __ldg(&sc.prims[3 * (size_t)hit + 1]);
-      float4 r2 = __ldg(&sc.prims[3 * (size_t)hit + 2]);
-      int mat = __float_as_int(r2.w);
-      p = o + d * t;
-      f3 ng = geometric_normal(r0, r1, r2, p);
-      inside = dot(d, ng) > 0.f;
-      n = inside ? ng * -1.f : ng;
-      float4 m0 = __ldg(&sc.mats[3 * mat]), m1 = __ldg(&sc.mats[3 * mat + 1]), m2 = __ldg(&sc.mats[3 * mat + 2]);
-      albedo = xyz(m0);
-      ks = m0.w;
-      shin = m1.x;
-      refl = m1.y;
-      ior = m1.z;
-      kind = __float_as_int(m1.w);
-      if (m2.x != 0.f || m2.y != 0.f || m2.z != 0.f) add_fb(fp.fb, pixel, w * xyz(m2));   // L_e, Eq. 7
-      eps = fp.eps_scale * fmaxf(1.0f, maxabs(p));
+      sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
+      if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f)
+        add_fb(fp.fb, pixel, w * sf.emission);   // L_e, Eq. 7
     }
-    f3 o_up = p + n * eps;
-    bool diel = kind == RT_MAT_DIELECTRIC;
-    float rho = kind == RT_MAT_MIRROR ? refl : 0.f;
-    // Alg. 1: one shadow ray per point light where n.l > 0 (Eq. 8 with point lights)
-    bool local = is_hit && !diel && (1.f - rho) > 0.f;
+    // Alg. 1: one shadow ray per point light where n.l > 0
+    bool local = is_hit && sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f;
     for (int li = 0; li < sc.n_lights; ++li) {
-      float4 L0 = __ldg(&sc.lights[2 * li]), L1 = __ldg(&sc.lights[2 * li + 1]);
-      f3 lp = xyz(L0);
-      bool valid = false;
-      f3 contrib = mk3(0, 0, 0), sd = mk3(0, 0, 1);
+      f3 contrib = mk3(0, 0, 0), os = mk3(0, 0, 0), sd = mk3(0, 0, 1);
       float tmax = 0.f;
-      if (local) {
-        f3 l = normalize(lp - p);
-        float nl = dot(n, l);
-        if (nl > 0.f) {
-          valid = true;
-          f3 rl = n * (2.f * nl) - l;                  // reflect(-l, n)
-          float rv = -dot(rl, d);
-          float spec = rv > 0.f ? powf(rv, shin) : 0.f;
-          f3 f = albedo * nl + mk3(ks * spec, ks * spec, ks * spec);
-          contrib = w * xyz(L1) * f * (1.f - rho);
-          f3 to_l = lp - o_up;
-          float dist = sqrtf(dot(to_l, to_l));
-          sd = to_l * (1.f / dist);
-          tmax = dist - eps;
-        }
-      }
+      bool valid = local && light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib,
+                                       os, sd, tmax);
       bool ok;
       unsigned pos = warp_push(&ctr->shadow[depth], valid, fp.shadow_cap, ok, sc.status);
-      if (ok) store_ray(fp.shadowq, pos, o_up, pixel, sd, tmax, contrib);
+      if (ok) store_ray(fp.shadowq[depth & 1], pos, os, pixel, sd, tmax, contrib);
     }
     // reflection / refraction rays (Fig. 3), not past the last depth
-    bool want_r = false, want_t = false;
-    f3 dr = mk3(0, 0, 1), dt = mk3(0, 0, 1), wr = mk3(0, 0, 0), wt = mk3(0, 0, 0);
-    if (is_hit && spawn) {
-      float dn = dot(d, n);
-      if (!diel) {
-        if (rho > 0.f) {
-          want_r = true;
-          dr = normalize(d - n * (2.f * dn));
-          wr = w * rho;
-        }
-      } else {
-        float n1 = inside ? ior : 1.f, n2 = inside ? 1.f : ior;
-        float eta = n1 / n2;
-        float ci = -dn;
-        float k = 1.f - eta * eta * (1.f - ci * ci);
-        float R = 1.f;
-        if (k >= 0.f) {
-          float ct = sqrtf(k);
-          float r0 = (n1 - n2) / (n1 + n2);
-          r0 *= r0;
-          float c = n1 <= n2 ? ci : ct;
-          float x = 1.f - c;
-          R = r0 + (1.f - r0) * x * x * x * x * x;
-          want_t = true;
-          dt = normalize(d * eta + n * (eta * ci - ct));
-          wt = w * (1.f - R);
-        }
-        want_r = true;
-        dr = normalize(d - n * (2.f * dn));
-        wr = w * R;
-      }
-    }
+    Children ch;
+    ch.want_r = ch.want_t = false;
+    if (is_hit && spawn) ch = children_of(sf, d, w);
     {
       bool ok;
-      unsigned pos = warp_push(&ctr->rays[depth + 1], want_r, fp.ray_cap, ok, sc.status);
-      if (ok) store_ray(qout, pos, o_up, pixel, dr, INFINITY, wr);
-      pos = warp_push(&ctr->rays[depth + 1], want_t, fp.ray_cap, ok, sc.status);
-      if (ok) store_ray(qout, pos, p - n * eps, pixel, dt, INFINITY, wt);
+      unsigned pos = warp_push(&ctr->rays[depth + 1], ch.want_r, fp.ray_cap, ok, sc.status);
+      if (ok) store_ray(qout, pos, ch.or_, pixel, ch.dr, INFINITY, ch.wr);
+      pos = warp_push(&ctr->rays[depth + 1], ch.want_t, fp.ray_cap, ok, sc.status);
+      if (ok) store_ray(qout, pos, ch.ot, pixel, ch.dt, INFINITY, ch.wt);
     }
   }
-  flush_work<kCount>(ctr, 0, wc);
+  flush_work<kCount>(ctr, 0, depth, wc);
 }
 
 // ---------------------------------------------------------------------------
@@ -403,7 +458,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FramePara
   int lane = threadIdx.x & 31;
   Counters* ctr = fp.ctr;
   unsigned n_items = min(ctr->shadow[depth], fp.shadow_cap);
-  WorkCount wc = {0u, 0u};
+  WorkCount wc = {0u, 0u, 0u};
   for (;;) {
     unsigned base = 0;
     if (lane == 0) base = atomicAdd(&ctr->fetch_shadow[depth], 32u);
@@ -411,17 +466,138 @@ __global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FramePara
     if (base >= n_items) break;
     unsigned idx = base + lane;
     if (idx < n_items) {
-      const float4* q = fp.shadowq + 3 * (size_t)idx;
+      const float4* q = fp.shadowq[depth & 1] + 3 * (size_t)idx;
       float4 q0 = q[0], q1 = q[1], q2 = q[2];
       RayInv ri = make_ray(xyz(q0), xyz(q1));
       float tmax = q1.w;
       bool fail = false;
+      unsigned v0 = wc.visits;
       int h = traverse<true, kCount>(sc, ri, 0.0f, tmax, stack, cap, fail, wc);
+      if (kCount) wc.vmax = max(wc.vmax, wc.visits - v0);
       if (fail) atomicOr(sc.status, kErrTraversalLimit);
       if (h < 0 && !fail) add_fb(fp.fb, __float_as_int(q0.w), xyz(q2));
     }
   }
-  flush_work<kCount>(ctr, 1, wc);
+  flush_work<kCount>(ctr, 1, depth, wc);
+}
+
+// ---------------------------------------------------------------------------
+// secondary rays, depth first: one thread carries a depth-1 ray's whole
+// subtree - the paper's recursion-as-iteration (Sec. IV.A) - tracing its
+// shadow rays inline.  One launch replaces the per-depth trace and shadow
+// launches of depths >= 1, whose few rays would otherwise make every depth
+// as slow as its slowest ray.
+// ---------------------------------------------------------------------------
+struct Pending {
+  f3 o, d, w;
+  int depth;
+};
+
+template <bool kCount>
+__device__ __forceinline__ void count_ray(Counters* ctr, int cls, int depth, unsigned v, unsigned t) {
+  if (!kCount) return;
+  atomicAdd(&ctr->visits[cls][depth], (unsigned long long)v);
+  atomicAdd(&ctr->tests[cls][depth], (unsigned long long)t);
+  atomicMax(&ctr->max_visits[cls][depth], v);
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParams fp, int cap) {
+  __shared__ int s_stack[kStackSize * kTraceThreads];
+  __shared__ unsigned s_cnt[3][RT_MAX_DEPTH + 2];   // rays spawned for / shadow rays cast at / hits at depth d
+  int* stack = s_stack + threadIdx.x;
+  for (int i = threadIdx.x; i < 3 * (RT_MAX_DEPTH + 2); i += blockDim.x) (&s_cnt[0][0])[i] = 0u;
+  __syncthreads();
+  Counters* ctr = fp.ctr;
+  unsigned n_items = min(ctr->rays[1], fp.ray_cap);
+  const float4* __restrict__ qin = fp.rayq[1];
+  const f3 bg = mk3(fp.bg_r, fp.bg_g, fp.bg_b);
+  Pending pend[RT_MAX_DEPTH];
+  int np = 0;
+  WorkCount wc = {0u, 0u, 0u};
+  f3 o = mk3(0, 0, 0), d = mk3(0, 0, 1), w = mk3(0, 0, 0);
+  int depth = 1, pixel = 0;
+  for (;;) {
+    if (np > 0) {
+      --np;
+      o = pend[np].o;
+      d = pend[np].d;
+      w = pend[np].w;
+      depth = pend[np].depth;
+    } else {
+      unsigned idx = atomicAdd(&ctr->fetch_trace[1], 1u);
+      if (idx >= n_items) break;
+      float4 q0 = qin[3 * (size_t)idx], q1 = qin[3 * (size_t)idx + 1], q2 = qin[3 * (size_t)idx + 2];
+      o = xyz(q0);
+      pixel = __float_as_int(q0.w);
+      d = xyz(q1);
+      w = xyz(q2);
+      depth = 1;
+    }
+    // follow this ray and, at each hit, one of its children; the other
+    // child waits on the thread's own stack
+    for (;;) {
+      float t = INFINITY;
+      bool fail = false;
+      unsigned v0 = wc.visits, t0 = wc.tests;
+      int hit = traverse<false, kCount>(sc, make_ray(o, d), 0.0f, t, stack, cap, fail, wc);
+      count_ray<kCount>(ctr, 0, depth, wc.visits - v0, wc.tests - t0);
+      if (fail) atomicOr(sc.status, kErrTraversalLimit);
+      if (hit < 0) {
+        add_fb(fp.fb, pixel, w * bg);
+        break;
+      }
+      atomicAdd(&s_cnt[2][depth], 1u);
+      Surface sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
+      if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp.fb, pixel, w * sf.emission);
+      if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
+        for (int li = 0; li < sc.n_lights; ++li) {
+          f3 contrib, os, sd;
+          float tmax;
+          if (!light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd, tmax))
+            continue;
+          atomicAdd(&s_cnt[1][depth], 1u);
+          bool sfail = false;
+          unsigned sv0 = wc.visits, st0 = wc.tests;
+          int h = traverse<true, kCount>(sc, make_ray(os, sd), 0.0f, tmax, stack, cap, sfail, wc);
+          count_ray<kCount>(ctr, 1, depth, wc.visits - sv0, wc.tests - st0);
+          if (sfail) atomicOr(sc.status, kErrTraversalLimit);
+          if (h < 0 && !sfail) add_fb(fp.fb, pixel, contrib);
+        }
+      }
+      if (depth >= fp.max_depth) break;
+      Children ch = children_of(sf, d, w);
+      if (!ch.want_r && !ch.want_t) break;
+      atomicAdd(&s_cnt[0][depth + 1], (unsigned)ch.want_r + (unsigned)ch.want_t);
+      if (ch.want_r && ch.want_t) {
+        if (np < RT_MAX_DEPTH) {
+          pend[np].o = ch.or_;
+          pend[np].d = ch.dr;
+          pend[np].w = ch.wr;
+          pend[np].depth = depth + 1;
+          ++np;
+        } else {
+          atomicOr(sc.status, kErrQueueOverflow);   // deeper than the stack holds: cannot happen for depth <= 16
+        }
+      }
+      if (ch.want_t) {
+        o = ch.ot;
+        d = ch.dt;
+        w = ch.wt;
+      } else {
+        o = ch.or_;
+        d = ch.dr;
+        w = ch.wr;
+      }
+      ++depth;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= RT_MAX_DEPTH; i += blockDim.x) {
+    if (s_cnt[0][i] && i >= 2) atomicAdd(&ctr->rays[i], s_cnt[0][i]);
+    if (s_cnt[1][i]) atomicAdd(&ctr->shadow[i], s_cnt[1][i]);
+    if (s_cnt[2][i]) atomicAdd(&ctr->hits[i], s_cnt[2][i]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -438,7 +614,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_query(DevScene sc, const floa
   if (i >= n) return;
   RayInv ri = make_ray(mk3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
   bool fail = false;
-  WorkCount wc = {0u, 0u};
+  WorkCount wc = {0u, 0u, 0u};
   if (any) {
     float tm = tmax_in[i];
     int h = traverse<true, false>(sc, ri, tmin, tm, stack, cap, fail, wc);
@@ -498,6 +674,9 @@ static void occupancy(rt_scene* s) {
   int a = 0, b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<false, false>, kTraceThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_shadow<false>, kTraceThreads, 0);
+  int c = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_paths<false>, kTraceThreads, 0);
+  s->paths_blocks = s->sm_count * std::max(c, 1);
   g_blocks_per_sm_trace = std::max(a, 1);
   g_blocks_per_sm_shadow = std::max(b, 1);
   s->trace_blocks = s->sm_count * g_blocks_per_sm_trace;
@@ -514,33 +693,51 @@ static bool finite_cam(const rt_camera* c) {
   return rx != 0.f || ry != 0.f || rz != 0.f;
 }
 
-// Records a stage boundary of the frame on the scene's reusable events.
-static void mark_stage(rt_scene* s, int kind, cudaStream_t st) {
-  if ((size_t)s->tcount >= s->tev.size()) {
+// Timing: event pairs (start, end) recorded around each kernel on the
+// stream it runs on; pair 0 brackets the whole frame.  The events are the
+// scene's and are reused frame after frame.
+static int timing_begin(rt_scene* s, int kind, cudaStream_t st) {
+  int slot = s->tcount++;
+  while ((size_t)(2 * s->tcount) > s->tev.size()) {
     cudaEvent_t e;
     cudaEventCreate(&e);
     s->tev.push_back(e);
-    s->tkind.push_back(0);
   }
-  s->tkind[s->tcount] = kind;
-  cudaEventRecord(s->tev[s->tcount], st);
-  s->tcount++;
+  if ((size_t)s->tcount > s->tkind.size()) s->tkind.resize(s->tcount);
+  s->tkind[slot] = kind;
+  cudaEventRecord(s->tev[2 * slot], st);
+  return slot;
 }
 
-// Stage times of the last timed frame (waits for its last event).
+static void timing_end(rt_scene* s, int slot, cudaStream_t st) { cudaEventRecord(s->tev[2 * slot + 1], st); }
+
+// Per-kernel times of the last timed frame, summed by kind (waits for the
+// frame's end event only).
 static rt_status stage_times(rt_scene* s, float* total, float* trace, float* shadow) {
   *total = *trace = *shadow = 0.f;
-  if (s->tcount < 2) return set_error(RT_ERR_INVALID_ARG, "no frame was rendered with RT_FLAG_STAGE_TIMING");
-  cudaError_t e = cudaEventSynchronize(s->tev[s->tcount - 1]);
+  if (s->tcount < 1) return set_error(RT_ERR_INVALID_ARG, "no frame was rendered with RT_FLAG_STAGE_TIMING");
+  cudaError_t e = cudaEventSynchronize(s->tev[1]);
   if (e != cudaSuccess) return cuda_error(e, "stage times");
-  cudaEventElapsedTime(total, s->tev[0], s->tev[s->tcount - 1]);
-  for (int i = 0; i + 1 < s->tcount; ++i) {
+  cudaEventElapsedTime(total, s->tev[0], s->tev[1]);
+  for (int i = 1; i < s->tcount; ++i) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, s->tev[i], s->tev[i + 1]);
+    cudaEventElapsedTime(&ms, s->tev[2 * i], s->tev[2 * i + 1]);
     if (s->tkind[i] == 0) *trace += ms;
     else if (s->tkind[i] == 1) *shadow += ms;
   }
   return RT_OK;
+}
+
+// The side stream that runs each depth's shadow kernel while the main
+// stream traces the next depth, and the events that order them.
+static rt_status ensure_side_stream(rt_scene* s) {
+  if (s->side) return RT_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+  for (int d = 0; e == cudaSuccess && d <= RT_MAX_DEPTH; ++d) {
+    e = cudaEventCreateWithFlags(&s->ev_traced[d], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_shadowed[d], cudaEventDisableTiming);
+  }
+  return cuda_error(e, "side stream");
 }
 
 static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, int D, float* out,
@@ -561,13 +758,19 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   bool use_bvh = opt.use_bvh != 0;
   if (use_bvh && !s->built) return set_error(RT_ERR_NOT_BUILT, "rt_render: BVH requested before rt_bvh_build");
   occupancy(s);
+  int64_t lights = std::max<int64_t>(s->n_lights, 1);
   int64_t qcap = opt.queue_capacity > 0 ? opt.queue_capacity : std::max<int64_t>(2 * (int64_t)W * H, 65536);
-  int64_t scap = qcap * std::max<int64_t>(s->n_lights, 1);
+  int64_t scap = qcap * lights;
   if (qcap > 0x7fffffffLL || scap > 0x7fffffffLL) return set_error(RT_ERR_UNSUPPORTED, "rt_render: queue too large");
-  int64_t pcap = std::max<int64_t>((int64_t)W * H * std::max<int64_t>(s->n_lights, 1), scap);
+  // depth 0 casts up to W*H*lights shadow rays, a deeper depth up to qcap*lights;
+  // shadowq[0] serves the even depths, shadowq[1] the odd ones
+  int64_t pcap = std::max<int64_t>((int64_t)W * H * lights, scap);
+  if (pcap > 0x7fffffffLL) return set_error(RT_ERR_UNSUPPORTED, "rt_render: shadow queue too large");
   rt_status rs;
   if ((rs = ensure(s->rayq[0], (size_t)qcap * 48)) || (rs = ensure(s->rayq[1], (size_t)qcap * 48)) ||
-      (rs = ensure(s->shadowq, (size_t)pcap * 48)) || (rs = ensure(s->counters, sizeof(Counters))))
+      (rs = ensure(s->shadowq[0], (size_t)pcap * 48)) ||
+      (rs = ensure(s->shadowq[1], D > 0 ? (size_t)pcap * 48 : 16)) || (rs = ensure(s->counters, sizeof(Counters))) ||
+      (rs = ensure_side_stream(s)))
     return rs;
   s->ray_cap = qcap;
   s->shadow_cap = pcap;
@@ -590,24 +793,27 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   fp.aov_t = aov_t;
   fp.rayq[0] = (float4*)s->rayq[0].p;
   fp.rayq[1] = (float4*)s->rayq[1].p;
-  fp.shadowq = (float4*)s->shadowq.p;
+  fp.shadowq[0] = (float4*)s->shadowq[0].p;
+  fp.shadowq[1] = (float4*)s->shadowq[1].p;
   fp.ray_cap = (unsigned)qcap;
   fp.shadow_cap = (unsigned)pcap;
   fp.ctr = (Counters*)s->counters.p;
   bool timing = (opt.flags & RT_FLAG_STAGE_TIMING) != 0;
   bool count = (opt.flags & RT_FLAG_COUNT_WORK) != 0;
   int launches = 0;
+  int frame_slot = -1;
   if (timing) {
     s->tcount = 0;
-    mark_stage(s, 3, st);
+    frame_slot = timing_begin(s, 3, st);
   }
-  auto mark = [&](int kind) {
-    if (timing) mark_stage(s, kind, st);
-  };
   cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);
   cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
-  for (int depth = 0; depth <= D; ++depth) {
-    mark(0);
+  bool per_depth = (opt.flags & RT_FLAG_PER_DEPTH_WAVEFRONT) != 0;
+  int last = per_depth ? D : 0;   // depths run as wavefronts; the rest run as paths
+  for (int depth = 0; depth <= last; ++depth) {
+    // trace(depth) fills the shadow buffer that shadow(depth - 2) reads
+    if (depth >= 2) cudaStreamWaitEvent(st, s->ev_shadowed[depth - 2], 0);
+    int slot = timing ? timing_begin(s, 0, st) : -1;
     if (depth == 0) {
       if (count) k_trace<true, true><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, 0, cap);
       else k_trace<true, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, 0, cap);
@@ -615,12 +821,26 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
       if (count) k_trace<false, true><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
       else k_trace<false, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
     }
-    mark(1);
-    if (count) k_shadow<true><<<s->shadow_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
-    else k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+    if (timing) timing_end(s, slot, st);
+    // shadow(depth) runs on the side stream, beside trace(depth + 1)
+    cudaEventRecord(s->ev_traced[depth], st);
+    cudaStreamWaitEvent(s->side, s->ev_traced[depth], 0);
+    slot = timing ? timing_begin(s, 1, s->side) : -1;
+    if (count) k_shadow<true><<<s->shadow_blocks, kTraceThreads, 0, s->side>>>(sc, fp, depth, cap);
+    else k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, s->side>>>(sc, fp, depth, cap);
+    if (timing) timing_end(s, slot, s->side);
+    cudaEventRecord(s->ev_shadowed[depth], s->side);
     launches += 2;
   }
-  mark(2);
+  if (!per_depth && D >= 1) {
+    int slot = timing ? timing_begin(s, 0, st) : -1;
+    if (count) k_paths<true><<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);
+    else k_paths<false><<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);
+    if (timing) timing_end(s, slot, st);
+    launches += 1;
+  }
+  cudaStreamWaitEvent(st, s->ev_shadowed[last], 0);
+  if (timing) timing_end(s, frame_slot, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "rt_render launch");
   if (stats) {
@@ -636,13 +856,15 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
         stats->rays_per_depth[d] = std::min<uint64_t>(c.rays[d], (uint64_t)qcap);
         stats->secondary += stats->rays_per_depth[d];
       }
-      stats->shadow_per_depth[d] = std::min<uint64_t>(c.shadow[d], (uint64_t)pcap);
+      stats->shadow_per_depth[d] = std::min<uint64_t>(c.shadow[d], (uint64_t)fp.shadow_cap);
       stats->shadow += stats->shadow_per_depth[d];
       stats->hits_per_depth[d] = c.hits[d];
-    }
-    for (int k = 0; k < 2; ++k) {
-      stats->node_visits[k] = c.visits[k];
-      stats->prim_tests[k] = c.tests[k];
+      for (int k = 0; k < 2; ++k) {
+        stats->node_visits[k] += c.visits[k][d];
+        stats->prim_tests[k] += c.tests[k][d];
+        stats->node_visits_per_depth[k][d] = c.visits[k][d];
+        stats->max_visits_per_depth[k][d] = c.max_visits[k][d];
+      }
     }
     stats->launches = launches;
     if (timing) stage_times(s, &stats->ms_total, &stats->ms_trace, &stats->ms_shadow);
@@ -739,7 +961,15 @@ rt_status rt_scene_destroy(rt_scene* s) {
   release(s->build_info);
   release(s->rayq[0]);
   release(s->rayq[1]);
-  release(s->shadowq);
+  release(s->shadowq[0]);
+  release(s->shadowq[1]);
+  if (s->side) {
+    cudaStreamDestroy(s->side);
+    for (int d = 0; d <= RT_MAX_DEPTH; ++d) {
+      cudaEventDestroy(s->ev_traced[d]);
+      cudaEventDestroy(s->ev_shadowed[d]);
+    }
+  }
   release(s->counters);
   release(s->fb_host_stage);
   for (auto e : s->tev) cudaEventDestroy(e);
@@ -828,7 +1058,8 @@ extern "C" rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int W,
   fp.ctr = (Counters*)p;
   fp.rayq[0] = (float4*)(p + kNoallocCounterBytes);
   fp.rayq[1] = fp.rayq[0] + 3 * kNoallocRayCap;
-  fp.shadowq = fp.rayq[1] + 3 * kNoallocRayCap;
+  fp.shadowq[0] = fp.rayq[1] + 3 * kNoallocRayCap;   // its depths run in order on one stream
+  fp.shadowq[1] = fp.shadowq[0];
   fp.ray_cap = (unsigned)kNoallocRayCap;
   fp.shadow_cap = (unsigned)kNoallocShadowCap;
   DevScene sc = dev_scene(s, true);

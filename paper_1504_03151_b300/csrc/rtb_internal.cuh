@@ -104,15 +104,17 @@ struct rt_scene {
   float last_build_ms = 0.f;
   int last_build_launches = 0;
   // render
-  rtb::Buf rayq[2], shadowq, counters, fb_host_stage;
+  rtb::Buf rayq[2], shadowq[2], counters, fb_host_stage;
+  cudaStream_t side = nullptr;   // runs each depth's shadow kernel beside the next depth's trace
+  cudaEvent_t ev_traced[RT_MAX_DEPTH + 1], ev_shadowed[RT_MAX_DEPTH + 1];
   int64_t ray_cap = 0, shadow_cap = 0;
   unsigned* status = nullptr;    // device status word
   int sm_count = 0;
-  int trace_blocks = 0, shadow_blocks = 0;
+  int trace_blocks = 0, shadow_blocks = 0, paths_blocks = 0;
   rtb::GraphCache* graphs = nullptr;
   // stage timing of the last frame rendered with RT_FLAG_STAGE_TIMING
   std::vector<cudaEvent_t> tev;  // reused across frames
-  std::vector<int> tkind;        // stage that starts at tev[i]: 0 trace, 1 shadow, 2 end
+  std::vector<int> tkind;        // kind of event pair i: 0 trace, 1 shadow, 3 whole frame
   int tcount = 0;
 };
 

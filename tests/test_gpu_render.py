@@ -403,3 +403,19 @@ def test_degenerate_triangles_never_hit():
     g = gpu_render(sc)
     assert set(np.unique(g["prim"])) <= {-1, 0}
     compare(g, oracle_render(sc, mode="brute"))
+
+
+@pytest.mark.parametrize("which", ["spheres8", "terrain_small_deep"])
+def test_pipeline_modes_agree(which):
+    """Depth-first secondary paths (default) and per-depth wavefronts trace
+    the same rays with the same FP32 functions: same counts, same image."""
+    sc = S.scene_spheres8(width=128, height=96) if which == "spheres8" else small_terrain(depth=8)
+    ref = oracle_render(sc, mode="brute")
+    g_paths = gpu_render(sc)
+    g_wave = gpu_render(sc, flags=rtb.RT_FLAG_PER_DEPTH_WAVEFRONT)
+    compare(g_paths, ref)
+    compare(g_wave, ref)
+    np.testing.assert_array_equal(g_paths["prim"], g_wave["prim"])
+    np.testing.assert_allclose(g_paths["rgb"], g_wave["rgb"], atol=1e-5)
+    for k in ("primary", "shadow", "secondary", "rays_per_depth", "shadow_per_depth", "hits_per_depth"):
+        assert g_paths["stats"][k] == g_wave["stats"][k], k
