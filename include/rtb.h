@@ -244,6 +244,51 @@ rt_status rt_trace_any(rt_scene* s, const float* o_device, const float* d_device
 rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
                             float* out_rgb_device, void* stream);
 
+/* ---- neural radiance cache (no counterpart in the paper) -------------
+ * A small MLP that stands in for the rest of a path after a fixed bounce:
+ * 81 features (normalised hit position, normal, view direction and sin/cos
+ * of 2^k pi x for k = 0..11) -> 64 -> 64 -> 64 -> 64 -> 3, ReLU hidden
+ * layers, exp output; BF16 weights and activations with FP32 accumulation
+ * on the tensor cores; trained online with Adam (FP32 master weights) on
+ * the relative-L2 loss mean((y - t)^2 / (y^2 + 0.01)) against the radiance
+ * the tracer computes for a seeded subset of the cached hits. */
+typedef struct rt_nrc rt_nrc;
+
+typedef struct rt_nrc_config {
+  int32_t train_batch;        /* training samples per frame (default 65536) */
+  int32_t terminate_depth;    /* depth whose hits read the cache (default 2) */
+  float lr, beta1, beta2, eps;/* Adam (1e-2, 0.9, 0.99, 1e-8) */
+  uint64_t seed;              /* weight initialisation and sample selection */
+} rt_nrc_config;
+
+#define RT_NRC_PARAMS 18883   /* W0[64][96] W1..W3[64][64] W4[3][64], b0..b3[64], b4[3] (FP32) */
+
+void rt_nrc_config_default(rt_nrc_config* cfg);
+/* He-uniform initial weights (seeded), zero biases; the encoding normalises
+ * positions by the scene's bounding box. */
+rt_status rt_nrc_create(rt_scene* s, const rt_nrc_config* cfg, rt_nrc** out);
+rt_status rt_nrc_destroy(rt_nrc* nrc);
+/* FP32 master parameters, RT_NRC_PARAMS floats (layout above); set also
+ * resets the Adam moments and step. */
+rt_status rt_nrc_get_params(rt_nrc* nrc, float* host_params, void* stream);
+rt_status rt_nrc_set_params(rt_nrc* nrc, const float* host_params, void* stream);
+/* Gradient of the last training step (RT_NRC_PARAMS floats) and its loss. */
+rt_status rt_nrc_get_grads(rt_nrc* nrc, float* host_grads, float* host_loss, void* stream);
+/* exp(MLP(encode(p, n, v))) for n hits given as n x 9 device floats (p, n, v);
+ * out: n x 3 device floats. */
+rt_status rt_nrc_infer(rt_nrc* nrc, rt_scene* s, const float* pnv_device, int64_t n, float* out_device,
+                       void* stream);
+/* One training step (gradient + Adam) on n samples: pnv n x 9, target n x 3. */
+rt_status rt_nrc_train_step(rt_nrc* nrc, rt_scene* s, const float* pnv_device, const float* target_device,
+                            int64_t n, void* stream);
+/* A frame whose hits at cfg.terminate_depth take their radiance from the
+ * cache (no shadow or secondary rays there); when `train` is set, a seeded
+ * subset of those hits (about train_batch) is also traced to max_depth with
+ * unit weight, the results become training targets and one Adam step runs
+ * after the frame.  Stats as in rt_render_ex (rays actually traced). */
+rt_status rt_render_nrc(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int width, int height, int max_depth,
+                        float* out_rgb_device, int train, rt_render_stats* stats, void* stream);
+
 /* Waits for `stream` and returns (and clears) the latched kernel error. */
 rt_status rt_scene_sync(rt_scene* s, void* stream);
 

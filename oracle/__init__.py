@@ -55,6 +55,9 @@ def lib():
         L.orc_mlp_forward.argtypes = [I64, P, P, P, P]
         L.orc_mlp_loss_grad.restype = D
         L.orc_mlp_loss_grad.argtypes = [I64, P, P, P, P, P, P]
+        L.orc_mlp_forward_ex.argtypes = [I64, P, P, P, P, I32]
+        L.orc_mlp_loss_grad_ex.restype = D
+        L.orc_mlp_loss_grad_ex.argtypes = [I64, P, P, P, P, P, P, I32]
         L.orc_adam.argtypes = [I64, P, P, P, P, I64, D, D, D, D]
         _lib = L
     return _lib
@@ -210,20 +213,21 @@ def nrc_encode(pnv, bbox_lo, bbox_hi):
     return out
 
 
-def mlp_forward(x, W, B):
+def mlp_forward(x, W, B, bf16_acts=False):
+    """bf16_acts: hidden activations rounded to BF16 after the ReLU."""
     x = _f64(x).reshape(-1, 96)
     y = np.zeros((len(x), 3))
-    lib().orc_mlp_forward(len(x), _ptr(x), _ptr(_f64(W)), _ptr(_f64(B)), _ptr(y))
+    lib().orc_mlp_forward_ex(len(x), _ptr(x), _ptr(_f64(W)), _ptr(_f64(B)), _ptr(y), int(bf16_acts))
     return y
 
 
-def mlp_loss_grad(x, target, W, B):
+def mlp_loss_grad(x, target, W, B, bf16_acts=False):
     x = _f64(x).reshape(-1, 96)
     tg = _f64(target).reshape(-1, 3)
     dW = np.zeros(N_W)
     dB = np.zeros(N_B)
-    loss = lib().orc_mlp_loss_grad(len(x), _ptr(x), _ptr(tg), _ptr(_f64(W)), _ptr(_f64(B)), _ptr(dW),
-                                   _ptr(dB))
+    loss = lib().orc_mlp_loss_grad_ex(len(x), _ptr(x), _ptr(tg), _ptr(_f64(W)), _ptr(_f64(B)), _ptr(dW),
+                                      _ptr(dB), int(bf16_acts))
     return loss, dW, dB
 
 

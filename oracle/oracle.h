@@ -119,6 +119,15 @@ double orc_mlp_loss_grad(int64_t n, const double* x, const double* target,
                          const double* W, const double* B, double* dW,
                          double* dB);
 
+/* As above with bf16 != 0: hidden activations rounded to BF16 after the
+ * ReLU, and the gradients w.r.t. pre-activations rounded to BF16 where
+ * they enter the weight and input gradients (bias gradients use the
+ * unrounded values); the network's activations are BF16 by design, the
+ * accumulation stays FP64. */
+void orc_mlp_forward_ex(int64_t n, const double* x, const double* W, const double* B, double* y, int bf16);
+double orc_mlp_loss_grad_ex(int64_t n, const double* x, const double* target, const double* W,
+                            const double* B, double* dW, double* dB, int bf16);
+
 /* One Adam step (bias-corrected), in place, on n parameters.  step >= 1. */
 void orc_adam(int64_t n, double* w, const double* g, double* m, double* v,
               int64_t step, double lr, double beta1, double beta2, double eps);

@@ -19,6 +19,8 @@ __all__ = [
     "rt_scene_create", "rt_scene_update", "rt_bvh_build", "rt_bvh_get_info", "rt_bvh_export",
     "rt_render", "rt_render_ex", "rt_render_host", "rt_camera_rays", "rt_trace_closest",
     "rt_trace_any", "rt_scene_sync", "rt_scene_destroy", "rt_render_stage_times", "Scene",
+    "rt_nrc_config_default", "rt_nrc_create", "rt_nrc_destroy", "rt_nrc_get_params", "rt_nrc_set_params",
+    "rt_nrc_get_grads", "rt_nrc_infer", "rt_nrc_train_step", "rt_render_nrc",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -71,6 +73,15 @@ class rt_render_stats(ctypes.Structure):
                 ("launches", ctypes.c_int32)]
 
 
+class rt_nrc_config(ctypes.Structure):
+    _fields_ = [("train_batch", ctypes.c_int32), ("terminate_depth", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+RT_NRC_PARAMS = 18883
+
+
 class rt_bvh_info(ctypes.Structure):
     _fields_ = [("n_prims", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("root", ctypes.c_int64),
                 ("max_depth", ctypes.c_int32),
@@ -109,6 +120,15 @@ def lib():
             "rt_trace_any": (I, [P, P, P, P, I64, F, I, P, P]),
             "rt_render_noalloc": (I, [P, P, I, I, I, P, P]),
             "rt_scene_sync": (I, [P, P]),
+            "rt_nrc_config_default": (None, [P]),
+            "rt_nrc_create": (I, [P, P, P]),
+            "rt_nrc_destroy": (I, [P]),
+            "rt_nrc_get_params": (I, [P, P, P]),
+            "rt_nrc_set_params": (I, [P, P, P]),
+            "rt_nrc_get_grads": (I, [P, P, P, P]),
+            "rt_nrc_infer": (I, [P, P, P, I64, P, P]),
+            "rt_nrc_train_step": (I, [P, P, P, P, I64, P]),
+            "rt_render_nrc": (I, [P, P, P, I, I, I, P, I, P, P]),
             "rt_scene_destroy": (I, [P]),
         }
         for name, (res, args) in sigs.items():
@@ -309,6 +329,60 @@ def rt_scene_sync(scene, stream=None) -> int:
 
 def rt_scene_destroy(scene):
     _check(lib().rt_scene_destroy(scene))
+
+
+# ---- radiance cache --------------------------------------------------------
+def rt_nrc_config_default(**kw) -> rt_nrc_config:
+    c = rt_nrc_config()
+    lib().rt_nrc_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def rt_nrc_create(scene, config=None) -> int:
+    h = P()
+    _check(lib().rt_nrc_create(scene, ctypes.byref(config) if config is not None else None, ctypes.byref(h)))
+    return h.value
+
+
+def rt_nrc_destroy(nrc):
+    _check(lib().rt_nrc_destroy(nrc))
+
+
+def rt_nrc_get_params(nrc, stream=None) -> np.ndarray:
+    out = np.zeros(RT_NRC_PARAMS, np.float32)
+    _check(lib().rt_nrc_get_params(nrc, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def rt_nrc_set_params(nrc, params, stream=None):
+    a = np.ascontiguousarray(params, np.float32)
+    assert a.size == RT_NRC_PARAMS
+    _check(lib().rt_nrc_set_params(nrc, a.ctypes.data, _stream(stream)))
+
+
+def rt_nrc_get_grads(nrc, stream=None):
+    g = np.zeros(RT_NRC_PARAMS, np.float32)
+    loss = ctypes.c_float()
+    _check(lib().rt_nrc_get_grads(nrc, g.ctypes.data, ctypes.byref(loss), _stream(stream)))
+    return g, loss.value
+
+
+def rt_nrc_infer(nrc, scene, pnv_dev, n, out_dev, stream=None):
+    _check(lib().rt_nrc_infer(nrc, scene, _dptr(pnv_dev), n, _dptr(out_dev), _stream(stream)))
+
+
+def rt_nrc_train_step(nrc, scene, pnv_dev, target_dev, n, stream=None):
+    _check(lib().rt_nrc_train_step(nrc, scene, _dptr(pnv_dev), _dptr(target_dev), n, _stream(stream)))
+
+
+def rt_render_nrc(scene, nrc, camera, width, height, max_depth, out_rgb, train=True, stats=False, stream=None):
+    cam = make_camera(camera)
+    st = rt_render_stats() if stats else None
+    _check(lib().rt_render_nrc(scene, nrc, ctypes.byref(cam), width, height, max_depth, _dptr(out_rgb), int(train),
+                               ctypes.byref(st) if st is not None else None, _stream(stream)))
+    return stats_dict(st, max_depth) if st is not None else None
 
 
 class Scene:

@@ -1,0 +1,806 @@
+// nrc.cu - neural radiance cache: frequency encoding, fused tcgen05 MLP
+// inference and training (forward, backward, weight gradients accumulated in
+// tensor memory), Adam on FP32 master weights.
+//
+// Network: 96 inputs (81 used) -> 64 -> 64 -> 64 -> 64 -> 3, ReLU hidden
+// layers, exp output; BF16 weights and activations, FP32 accumulation.
+// Loss: mean over samples and channels of (y - t)^2 / (sg(y)^2 + 0.01).
+// The paper has no learned component; this cache terminates paths after a
+// fixed bounce and is trained online on radiance the tracer itself produces.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "nrc_internal.cuh"
+#include "rtb_internal.cuh"
+#include "tc.cuh"
+
+namespace rtb {
+
+// ---------------------------------------------------------------------------
+// parameter layouts
+// ---------------------------------------------------------------------------
+// FP32 master parameters (oracle layout): W0[64][96] W1[64][64] W2 W3 W4[3][64],
+// then b0[64] b1 b2 b3 b4[3].
+__host__ __device__ constexpr int off_w(int l) { return l == 0 ? 0 : 6144 + 4096 * (l - 1); }
+__host__ __device__ constexpr int off_b(int l) { return kNW + 64 * l; }
+__host__ __device__ constexpr int d_in(int l) { return l == 0 ? 96 : 64; }
+__host__ __device__ constexpr int d_out(int l) { return l == 4 ? 3 : 64; }
+
+// Packed BF16 copies (row-major) read by the kernels, then FP32 biases.
+// forward W_l as [out][in] (W4 padded to 16 rows), backward W_l^T as
+// [in][out] (W4^T padded to 16 columns).
+constexpr int kPW0 = 0, kPW1 = 6144, kPW2 = 10240, kPW3 = 14336, kPW4 = 18432;   // W4: 16 x 64
+constexpr int kPT1 = 19456, kPT2 = 23552, kPT3 = 27648, kPT4 = 31744;             // T4: 64 x 16
+constexpr int kPackedBf16 = 32768;                                                 // 64 KB
+constexpr int kPackedBias = 4 * 64 + 16;
+constexpr size_t kPackedBytes = kPackedBf16 * 2 + kPackedBias * 4;
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_float(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+// ---------------------------------------------------------------------------
+// encoding: 3 normalised position values, normal (3), view direction (3),
+// sin and cos of 2^k pi x_hat_j for k = 0..11 -> 81 values, zero-padded to 96
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void encode81(const float* pnv, const float* lo, const float* inv_ext, float* f) {
+  float xh[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    xh[j] = (pnv[j] - lo[j]) * inv_ext[j];
+    f[j] = xh[j];
+    f[3 + j] = pnv[3 + j];
+    f[6 + j] = pnv[6 + j];
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    float sc = (float)(1 << k);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float s, c;
+      sincospif(sc * xh[j], &s, &c);
+      f[9 + 6 * k + j] = s;
+      f[9 + 6 * k + 3 + j] = c;
+    }
+  }
+#pragma unroll
+  for (int k = 81; k < 96; ++k) f[k] = 0.f;
+}
+
+// Writes 8 consecutive features (columns 8c..8c+7) of row r as one 16-byte
+// chunk of a K-major canonical tile.
+__device__ __forceinline__ void store_chunk(uint8_t* tile, int r, int c, int K, const float* v8) {
+  uint4 q;
+  q.x = (uint32_t)bf16_bits(v8[0]) | ((uint32_t)bf16_bits(v8[1]) << 16);
+  q.y = (uint32_t)bf16_bits(v8[2]) | ((uint32_t)bf16_bits(v8[3]) << 16);
+  q.z = (uint32_t)bf16_bits(v8[4]) | ((uint32_t)bf16_bits(v8[5]) << 16);
+  q.w = (uint32_t)bf16_bits(v8[6]) | ((uint32_t)bf16_bits(v8[7]) << 16);
+  *(uint4*)(tile + tc::core_off(r, 8 * c, K)) = q;
+}
+
+// Copies a row-major [R][K] bf16 matrix from global memory into a K-major
+// canonical tile (16-byte chunks).
+__device__ __forceinline__ void load_tile(uint8_t* tile, const uint16_t* __restrict__ g, int R, int K) {
+  int chunks = R * (K / 8);
+  for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+    int r = i / (K / 8), c = i % (K / 8);
+    uint4 q = *(const uint4*)(g + (size_t)r * K + 8 * c);
+    *(uint4*)(tile + tc::core_off(r, 8 * c, K)) = q;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// inference: records (p, n, v, weight, pixel) -> pixel += weight * exp(MLP)
+// 128 threads, one sample per thread, one 128-sample tile at a time.
+// ---------------------------------------------------------------------------
+constexpr int kInferThreads = 128;
+constexpr int kInferTmemCols = 64;
+// dynamic shared memory (bytes), 1 KB aligned sections
+constexpr int kSmW0 = 0, kSmW1 = 12288, kSmW2 = 20480, kSmW3 = 28672, kSmW4 = 36864;   // 2 KB
+constexpr int kSmBias = 38912;                                                         // 272 floats
+constexpr int kSmA = 40960;                                                            // 24 KB
+constexpr int kSmMisc = 65536;                                                         // mbarrier, tmem slot, flags
+constexpr int kInferSmem = kSmMisc + 64;
+
+__device__ __forceinline__ void fb_add(float* fb, float* target, int pixel, float r, float g, float b) {
+  float* p = pixel >= 0 ? fb + 3 * (size_t)pixel : target + 3 * (size_t)(~pixel);
+  atomicAdd(p, r);
+  atomicAdd(p + 1, g);
+  atomicAdd(p + 2, b);
+}
+
+__global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const float4* __restrict__ recs,
+                                                            const unsigned* __restrict__ count, unsigned cap,
+                                                            float* __restrict__ fb, float* __restrict__ out3,
+                                                            unsigned* status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* mbar = (uint64_t*)(sm + kSmMisc);
+  uint32_t* tslot = (uint32_t*)(sm + kSmMisc + 8);
+  int* abort_flag = (int*)(sm + kSmMisc + 16);
+  float* bias = (float*)(sm + kSmBias);
+  int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) tc::alloc(tc::smem_u32(tslot), kInferTmemCols);
+  const uint16_t* pw = (const uint16_t*)nd.packed;
+  load_tile(sm + kSmW0, pw + kPW0, 64, 96);
+  load_tile(sm + kSmW1, pw + kPW1, 64, 64);
+  load_tile(sm + kSmW2, pw + kPW2, 64, 64);
+  load_tile(sm + kSmW3, pw + kPW3, 64, 64);
+  load_tile(sm + kSmW4, pw + kPW4, 16, 64);
+  const float* gb = (const float*)(pw + kPackedBf16);
+  for (int i = tid; i < kPackedBias; i += blockDim.x) bias[i] = gb[i];
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_u32(mbar), 1);
+    *abort_flag = 0;
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  uint32_t tmem = *tslot;
+  uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+  uint32_t mb = tc::smem_u32(mbar);
+  uint32_t sA = tc::smem_u32(sm + kSmA);
+  const uint32_t sW[5] = {tc::smem_u32(sm + kSmW0), tc::smem_u32(sm + kSmW1), tc::smem_u32(sm + kSmW2),
+                          tc::smem_u32(sm + kSmW3), tc::smem_u32(sm + kSmW4)};
+  unsigned n = min(*count, cap);
+  unsigned tiles = (n + 127) / 128;
+  uint32_t phase = 0;
+  float lo[3] = {nd.lo[0], nd.lo[1], nd.lo[2]}, ie[3] = {nd.inv_ext[0], nd.inv_ext[1], nd.inv_ext[2]};
+  for (unsigned tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    unsigned row = tile * 128 + tid;
+    bool valid = row < n;
+    float f[96];
+    float wr = 0.f, wg = 0.f, wb = 0.f;
+    int pixel = 0;
+    if (valid) {
+      float4 q0 = recs[4 * (size_t)row], q1 = recs[4 * (size_t)row + 1], q2 = recs[4 * (size_t)row + 2],
+             q3 = recs[4 * (size_t)row + 3];
+      float pnv[9] = {q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z};
+      encode81(pnv, lo, ie, f);
+      pixel = __float_as_int(q0.w);
+      wr = q3.x;
+      wg = q3.y;
+      wb = q3.z;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 96; ++k) f[k] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 12; ++c) store_chunk(sm + kSmA, tid, c, 96, f + 8 * c);
+    tc::fence_proxy_async();
+    __syncthreads();
+    for (int l = 0; l < 5; ++l) {
+      int N = l < 4 ? 64 : 16;
+      if (tid == 0) {
+        tc::fence_after_sync();
+        tc::gemm(tmem, sA, sW[l], d_in(l), tc::idesc_bf16_f32(128, N), false);
+        tc::commit(mb);
+      }
+      bool ok = tc::mbar_wait(mb, phase);
+      phase ^= 1;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(status, kErrNrcTimeout);
+        goto done;
+      }
+      tc::fence_after_sync();
+      if (l < 4) {
+        float h[64];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tc::ld16(lane_addr + 16 * c, h + 16 * c);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) h[k] = fmaxf(h[k] + bias[64 * l + k], 0.f);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) store_chunk(sm + kSmA, tid, c, 64, h + 8 * c);
+        tc::fence_before_sync();
+        tc::fence_proxy_async();
+        __syncthreads();
+      } else {
+        float o[16];
+        tc::ld16(lane_addr, o);
+        float y0 = expf(o[0] + bias[256]), y1 = expf(o[1] + bias[257]), y2 = expf(o[2] + bias[258]);
+        if (valid) {
+          if (out3) {
+            out3[3 * (size_t)row] = y0;
+            out3[3 * (size_t)row + 1] = y1;
+            out3[3 * (size_t)row + 2] = y2;
+          }
+          if (fb) fb_add(fb, nd.target, pixel, wr * y0, wg * y1, wb * y2);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+      }
+    }
+  }
+done:
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::dealloc(tmem, kInferTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// training: forward (activations kept), loss gradient, backward; weight
+// gradients accumulate in tensor memory over the CTA's tiles, then go to
+// global memory with atomics.  One CTA per SM (512 tensor-memory columns).
+// ---------------------------------------------------------------------------
+constexpr int kTrainThreads = 128;
+constexpr int kTrainTmemCols = 512;
+// tensor-memory columns
+constexpr int kTcAcc = 0;      // 64: forward / backward accumulator (M = 128)
+constexpr int kTcDW0 = 64;     // 96: dW0 (M = 64, N = 96)
+constexpr int kTcDW1 = 160;    // 64 each: dW1, dW2, dW3
+constexpr int kTcDW4 = 352;    // 16: dW4^T (M = 64, N = 16)
+// shared memory (bytes)
+constexpr int kTsW0 = 0, kTsW1 = 12288, kTsW2 = 20480, kTsW3 = 28672, kTsW4 = 36864;   // forward, 38 KB
+constexpr int kTsT1 = 38912, kTsT2 = 47104, kTsT3 = 55296, kTsT4 = 63488;              // backward, 26 KB
+constexpr int kTsA = 65536;      // 24 KB: X (K = 96), then H (K = 64)
+constexpr int kTsXT = 90112;     // 24 KB: X^T [96][128]
+constexpr int kTsHT = 114688;    // 4 x 16 KB: H1^T .. H4^T [64][128]
+constexpr int kTsDZ = 180224;    // 16 KB: dZ [128][64] (dZ5: [128][16])
+constexpr int kTsDZT = 196608;   // 16 KB: dZ^T [64][128] (dZ5^T: [16][128])
+constexpr int kTsBias = 212992;  // 272 floats
+constexpr int kTsDB = 214528;    // 272 floats: bias gradients of this CTA
+constexpr int kTsMisc = 216064;  // mbarrier, tmem slot, flags, loss
+constexpr int kTrainSmem = kTsMisc + 64;
+
+// Lane of row m of an M = 64 accumulator: 16 rows in each 32-lane quarter.
+__device__ __forceinline__ int m64_row_of_lane(int lane) { return (lane & 31) < 16 ? (lane >> 5) * 16 + (lane & 31) : -1; }
+
+__device__ __forceinline__ void store_transposed(uint8_t* tileT, int col, int rows, const float* v) {
+  // element (k, col) of a [rows][128] K-major tile for k < rows
+  for (int k = 0; k < rows; ++k) *(uint16_t*)(tileT + tc::core_off(k, col, 128)) = bf16_bits(v[k]);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, const float4* __restrict__ recs,
+                                                                const float* __restrict__ targets,
+                                                                const unsigned* __restrict__ count, unsigned cap,
+                                                                float* __restrict__ grad, unsigned* status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* mbar = (uint64_t*)(sm + kTsMisc);
+  uint32_t* tslot = (uint32_t*)(sm + kTsMisc + 8);
+  float* s_loss = (float*)(sm + kTsMisc + 16);
+  float* bias = (float*)(sm + kTsBias);
+  float* db = (float*)(sm + kTsDB);
+  int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::alloc(tc::smem_u32(tslot), kTrainTmemCols);
+  const uint16_t* pw = (const uint16_t*)nd.packed;
+  load_tile(sm + kTsW0, pw + kPW0, 64, 96);
+  load_tile(sm + kTsW1, pw + kPW1, 64, 64);
+  load_tile(sm + kTsW2, pw + kPW2, 64, 64);
+  load_tile(sm + kTsW3, pw + kPW3, 64, 64);
+  load_tile(sm + kTsW4, pw + kPW4, 16, 64);
+  load_tile(sm + kTsT1, pw + kPT1, 64, 64);
+  load_tile(sm + kTsT2, pw + kPT2, 64, 64);
+  load_tile(sm + kTsT3, pw + kPT3, 64, 64);
+  load_tile(sm + kTsT4, pw + kPT4, 64, 16);
+  const float* gb = (const float*)(pw + kPackedBf16);
+  for (int i = tid; i < kPackedBias; i += blockDim.x) {
+    bias[i] = gb[i];
+    db[i] = 0.f;
+  }
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_u32(mbar), 1);
+    *s_loss = 0.f;
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  uint32_t tmem = *tslot;
+  uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+  uint32_t mb = tc::smem_u32(mbar);
+  const uint32_t sW[5] = {tc::smem_u32(sm + kTsW0), tc::smem_u32(sm + kTsW1), tc::smem_u32(sm + kTsW2),
+                          tc::smem_u32(sm + kTsW3), tc::smem_u32(sm + kTsW4)};
+  const uint32_t sT[5] = {0u, tc::smem_u32(sm + kTsT1), tc::smem_u32(sm + kTsT2), tc::smem_u32(sm + kTsT3),
+                          tc::smem_u32(sm + kTsT4)};
+  const uint32_t sA = tc::smem_u32(sm + kTsA), sXT = tc::smem_u32(sm + kTsXT), sDZ = tc::smem_u32(sm + kTsDZ),
+                 sDZT = tc::smem_u32(sm + kTsDZT);
+  uint32_t sHT[5];
+  sHT[0] = sXT;
+  for (int l = 1; l <= 4; ++l) sHT[l] = tc::smem_u32(sm + kTsHT + (l - 1) * 16384);
+  unsigned n = min(*count, cap);
+  unsigned tiles = (n + 127) / 128;
+  float inv_n3 = n > 0 ? 1.0f / (3.0f * (float)n) : 0.f;
+  uint32_t phase = 0;
+  bool first = true;
+  float loss_acc = 0.f;
+  bool aborted = false;
+  float lo[3] = {nd.lo[0], nd.lo[1], nd.lo[2]}, ie[3] = {nd.inv_ext[0], nd.inv_ext[1], nd.inv_ext[2]};
+
+#define RTB_WAIT()                                   \
+  {                                                  \
+    bool ok_ = tc::mbar_wait(mb, phase);             \
+    phase ^= 1;                                      \
+    if (__syncthreads_or(!ok_)) {                    \
+      if (tid == 0) atomicOr(status, kErrNrcTimeout); \
+      aborted = true;                                \
+      goto done;                                     \
+    }                                                \
+    tc::fence_after_sync();                          \
+  }
+
+  for (unsigned tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    unsigned row = tile * 128 + tid;
+    bool valid = row < n;
+    uint32_t mask[4][2];   // ReLU masks of the 4 hidden layers (64 bits each)
+    float f[96];
+    float tr = 0.f, tg = 0.f, tb = 0.f;
+    if (valid) {
+      float4 q0 = recs[3 * (size_t)row], q1 = recs[3 * (size_t)row + 1], q2 = recs[3 * (size_t)row + 2];
+      float pnv[9] = {q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z};
+      encode81(pnv, lo, ie, f);
+      int slot = __float_as_int(q0.w);
+      tr = targets[3 * (size_t)slot];
+      tg = targets[3 * (size_t)slot + 1];
+      tb = targets[3 * (size_t)slot + 2];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 96; ++k) f[k] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 12; ++c) store_chunk(sm + kTsA, tid, c, 96, f + 8 * c);
+    store_transposed(sm + kTsXT, tid, 96, f);
+    tc::fence_proxy_async();
+    __syncthreads();
+    // forward
+    float o[16];
+    for (int l = 0; l < 5; ++l) {
+      int N = l < 4 ? 64 : 16;
+      if (tid == 0) {
+        tc::fence_after_sync();
+        tc::gemm(tmem + kTcAcc, sA, sW[l], d_in(l), tc::idesc_bf16_f32(128, N), false);
+        tc::commit(mb);
+      }
+      RTB_WAIT();
+      if (l < 4) {
+        float h[64];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tc::ld16(lane_addr + kTcAcc + 16 * c, h + 16 * c);
+        mask[l][0] = mask[l][1] = 0u;
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+          float z = h[k] + bias[64 * l + k];
+          bool pos = valid && z > 0.f;
+          mask[l][k >> 5] |= (pos ? 1u : 0u) << (k & 31);
+          h[k] = pos ? z : 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) store_chunk(sm + kTsA, tid, c, 64, h + 8 * c);
+        store_transposed(sm + kTsHT + l * 16384, tid, 64, h);
+        tc::fence_before_sync();
+        tc::fence_proxy_async();
+        __syncthreads();
+      } else {
+        tc::ld16(lane_addr + kTcAcc, o);
+        tc::fence_before_sync();
+      }
+    }
+    // loss gradient at the exp output: dL/dz5 = 2 (y - t) / (y^2 + 0.01) / (3n) * y
+    {
+      float g[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) g[k] = 0.f;
+      if (valid) {
+        float t3[3] = {tr, tg, tb};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float y = expf(o[c] + bias[256 + c]);
+          float den = y * y + 0.01f;
+          float dy = y - t3[c];
+          loss_acc += dy * dy / den * inv_n3;
+          g[c] = 2.f * dy / den * inv_n3 * y;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float s = warp_sum(g[c]);
+        if (lane == 0) atomicAdd(&db[256 + c], s);
+      }
+      store_chunk(sm + kTsDZ, tid, 0, 16, g);
+      store_chunk(sm + kTsDZ, tid, 1, 16, g + 8);
+      store_transposed(sm + kTsDZT, tid, 16, g);
+      tc::fence_proxy_async();
+      __syncthreads();
+    }
+    // backward: layer 4 -> 0
+    for (int l = 4; l >= 0; --l) {
+      if (tid == 0) {
+        tc::fence_after_sync();
+        if (l == 4) {
+          // dW4^T [64 in][16 out] += H4^T . dZ5 (K = batch)
+          tc::gemm(tmem + kTcDW4, sHT[4], sDZT, 128, tc::idesc_bf16_f32(64, 16), !first);
+          // dH4 = dZ5 . W4  (A: dZ5 [128][16], B: W4^T [64][16])
+          tc::gemm(tmem + kTcAcc, sDZ, sT[4], 16, tc::idesc_bf16_f32(128, 64), false);
+        } else {
+          // dW_l [64 out][in] += dZ_{l+1}^T . H_l (K = batch); H_0 = X
+          uint32_t col = l == 0 ? kTcDW0 : kTcDW1 + 64 * (l - 1);
+          tc::gemm(tmem + col, sDZT, sHT[l], 128, tc::idesc_bf16_f32(64, d_in(l)), !first);
+          if (l > 0) tc::gemm(tmem + kTcAcc, sDZ, sT[l], 64, tc::idesc_bf16_f32(128, 64), false);
+        }
+        tc::commit(mb);
+      }
+      RTB_WAIT();
+      if (l == 0) break;
+      // dZ_l = dH_l * relu'(z_l)
+      float g[64];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tc::ld16(lane_addr + kTcAcc + 16 * c, g + 16 * c);
+#pragma unroll
+      for (int k = 0; k < 64; ++k) g[k] = ((mask[l - 1][k >> 5] >> (k & 31)) & 1u) ? g[k] : 0.f;
+#pragma unroll
+      for (int k = 0; k < 64; ++k) {
+        float s = warp_sum(g[k]);
+        if (lane == 0) atomicAdd(&db[64 * (l - 1) + k], s);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) store_chunk(sm + kTsDZ, tid, c, 64, g + 8 * c);
+      store_transposed(sm + kTsDZT, tid, 64, g);
+      tc::fence_before_sync();
+      tc::fence_proxy_async();
+      __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    first = false;
+  }
+done:
+  // weight gradients of this CTA: tensor memory -> global (atomics)
+  if (!aborted && !first) {
+    tc::fence_after_sync();
+    int m = m64_row_of_lane(tid);
+    float v[16];
+    // dW0 (M = 64 x N = 96)
+    for (int c = 0; c < 6; ++c) {
+      tc::ld16(lane_addr + kTcDW0 + 16 * c, v);
+      if (m >= 0)
+        for (int k = 0; k < 16; ++k) atomicAdd(&grad[off_w(0) + m * 96 + 16 * c + k], v[k]);
+    }
+    for (int l = 1; l <= 3; ++l)
+      for (int c = 0; c < 4; ++c) {
+        tc::ld16(lane_addr + kTcDW1 + 64 * (l - 1) + 16 * c, v);
+        if (m >= 0)
+          for (int k = 0; k < 16; ++k) atomicAdd(&grad[off_w(l) + m * 64 + 16 * c + k], v[k]);
+      }
+    // dW4^T [64 in][16 out] -> dW4 [3][64]
+    tc::ld16(lane_addr + kTcDW4, v);
+    if (m >= 0)
+      for (int k = 0; k < 3; ++k) atomicAdd(&grad[off_w(4) + k * 64 + m], v[k]);
+  }
+  __syncthreads();
+  if (!first) {
+    for (int i = tid; i < 4 * 64; i += blockDim.x) atomicAdd(&grad[off_b(0) + i], db[i]);
+    if (tid < 3) atomicAdd(&grad[off_b(4) + tid], db[256 + tid]);
+    float ls = warp_sum(loss_acc);
+    if (lane == 0) atomicAdd(s_loss, ls);
+    __syncthreads();
+    if (tid == 0) atomicAdd(&grad[kNP], *s_loss);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::dealloc(tmem, kTrainTmemCols);
+#undef RTB_WAIT
+}
+
+// ---------------------------------------------------------------------------
+// Adam on the FP32 master parameters, then the BF16 copies; clears the
+// gradient for the next step.
+// ---------------------------------------------------------------------------
+__global__ void k_nrc_adam(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                           float lr, float b1, float b2, float eps, float c1, float c2, int apply) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNP) return;
+  if (apply) {
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.f - b1) * gi;
+    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+__global__ void k_nrc_pack(const float* __restrict__ w, uint16_t* __restrict__ packed) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float* pb = (float*)(packed + kPackedBf16);
+  if (i < kPackedBf16) {
+    float x = 0.f;
+    if (i < kPW4) {   // W0..W3 [out][in]
+      x = w[i];
+    } else if (i < kPT1) {   // W4 padded to 16 rows
+      int r = (i - kPW4) / 64, c = (i - kPW4) % 64;
+      x = r < 3 ? w[off_w(4) + r * 64 + c] : 0.f;
+    } else if (i < kPT4) {   // W1^T .. W3^T [in][out]
+      int l = 1 + (i - kPT1) / 4096, j = (i - kPT1) % 4096;
+      int in = j / 64, out = j % 64;
+      x = w[off_w(l) + out * 64 + in];
+    } else {   // W4^T [64 in][16 out]
+      int in = (i - kPT4) / 16, out = (i - kPT4) % 16;
+      x = out < 3 ? w[off_w(4) + out * 64 + in] : 0.f;
+    }
+    packed[i] = bf16_bits(x);
+  } else if (i < kPackedBf16 + kPackedBias) {
+    int j = i - kPackedBf16;
+    pb[j] = j < 256 ? w[kNW + j] : (j < 259 ? w[kNW + j] : 0.f);
+  }
+}
+
+__global__ void k_make_records(const float* __restrict__ pnv, int64_t n, float4* __restrict__ recs, int stride) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* q = pnv + 9 * i;
+  float4* r = recs + stride * i;
+  r[0] = make_float4(q[0], q[1], q[2], __int_as_float((int)i));
+  r[1] = make_float4(q[3], q[4], q[5], 0.f);
+  r[2] = make_float4(q[6], q[7], q[8], 0.f);
+  if (stride == 4) r[3] = make_float4(1.f, 1.f, 1.f, 0.f);
+}
+
+void nrc_make_records(const float* pnv, const float* targets, int64_t n, float4* recs, int stride, cudaStream_t st) {
+  (void)targets;
+  k_make_records<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pnv, n, recs, stride);
+}
+
+__global__ void k_zero(float* p, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = 0.f;
+}
+
+}  // namespace rtb
+
+// ---------------------------------------------------------------------------
+// host API
+// ---------------------------------------------------------------------------
+using namespace rtb;
+
+struct rt_nrc {
+  rt_nrc_config cfg;
+  NrcDevice nd;
+  Buf params, m, v, grad, packed;
+  Buf infer_q, train_q, train_target, counters;   // frame queues (render integration)
+  int64_t infer_cap = 0, train_cap = 0;
+  int64_t step = 0;
+  uint64_t frame = 0;
+  int sm_count = 0, infer_blocks = 0;
+  float last_loss = 0.f;
+};
+
+namespace rtb {
+
+static uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static bool g_smem_attr_set = false;
+
+static rt_status nrc_setup_kernels() {
+  if (g_smem_attr_set) return RT_OK;
+  cudaError_t e = cudaFuncSetAttribute(k_nrc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_nrc_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem);
+  if (e != cudaSuccess) return cuda_error(e, "nrc kernel attributes");
+  g_smem_attr_set = true;
+  return RT_OK;
+}
+
+static rt_status nrc_pack(rt_nrc* r, cudaStream_t st) {
+  int n = kPackedBf16 + kPackedBias;
+  k_nrc_pack<<<(n + 255) / 256, 256, 0, st>>>((const float*)r->params.p, (uint16_t*)r->packed.p);
+  return cuda_error(cudaGetLastError(), "nrc pack");
+}
+
+rt_status nrc_infer_launch(rt_nrc* r, const float4* recs, const unsigned* count, unsigned cap, float* fb,
+                           float* out3, unsigned* status, cudaStream_t st) {
+  rt_status rs = nrc_setup_kernels();
+  if (rs) return rs;
+  int blocks = r->infer_blocks;
+  k_nrc_infer<<<blocks, kInferThreads, kInferSmem, st>>>(r->nd, recs, count, cap, fb, out3, status);
+  return cuda_error(cudaGetLastError(), "nrc infer");
+}
+
+rt_status nrc_train_launch(rt_nrc* r, const float4* recs, const float* targets, const unsigned* count, unsigned cap,
+                           unsigned* status, cudaStream_t st) {
+  rt_status rs = nrc_setup_kernels();
+  if (rs) return rs;
+  k_zero<<<(kNP + 1 + 255) / 256, 256, 0, st>>>((float*)r->grad.p, kNP + 1);
+  k_nrc_train<<<r->sm_count, kTrainThreads, kTrainSmem, st>>>(r->nd, recs, targets, count, cap, (float*)r->grad.p,
+                                                               status);
+  r->step++;
+  float c1 = 1.f - powf(r->cfg.beta1, (float)r->step), c2 = 1.f - powf(r->cfg.beta2, (float)r->step);
+  k_nrc_adam<<<(kNP + 255) / 256, 256, 0, st>>>((float*)r->params.p, (float*)r->grad.p, (float*)r->m.p,
+                                                 (float*)r->v.p, r->cfg.lr, r->cfg.beta1, r->cfg.beta2, r->cfg.eps, c1,
+                                                 c2, 1);
+  rs = nrc_pack(r, st);
+  if (rs) return rs;
+  return cuda_error(cudaGetLastError(), "nrc train");
+}
+
+NrcDevice* nrc_device(rt_nrc* r) { return &r->nd; }
+
+rt_status nrc_frame_buffers(rt_nrc* r, int64_t ray_cap, bool train, NrcFrame* out) {
+  int64_t icap = std::max<int64_t>(ray_cap, 65536);
+  int64_t tcap = r->cfg.train_batch;
+  rt_status rs;
+  if ((rs = ensure(r->infer_q, (size_t)icap * 64)) || (rs = ensure(r->train_q, (size_t)tcap * 48)) ||
+      (rs = ensure(r->train_target, (size_t)tcap * 12)))
+    return rs;
+  r->frame++;
+  uint64_t sd = r->cfg.seed ^ (r->frame * 0x9E3779B97F4A7C15ull);
+  out->depth = r->cfg.terminate_depth;
+  out->target = (float*)r->train_target.p;
+  out->infer_q = (float4*)r->infer_q.p;
+  out->train_q = (float4*)r->train_q.p;
+  out->infer_cap = (unsigned)icap;
+  out->train_cap = (unsigned)tcap;
+  out->train_batch = (unsigned)tcap;
+  out->seed = (uint32_t)(splitmix64(sd) >> 32);
+  r->nd.target = out->target;
+  (void)train;
+  return RT_OK;
+}
+
+}  // namespace rtb
+
+extern "C" {
+
+void rt_nrc_config_default(rt_nrc_config* c) {
+  if (!c) return;
+  c->train_batch = 65536;
+  c->terminate_depth = 2;
+  c->lr = 1e-2f;
+  c->beta1 = 0.9f;
+  c->beta2 = 0.99f;
+  c->eps = 1e-8f;
+  c->seed = 1;
+}
+
+rt_status rt_nrc_create(rt_scene* s, const rt_nrc_config* cfg_in, rt_nrc** out) {
+  if (!s || !out) return set_error(RT_ERR_INVALID_ARG, "rt_nrc_create: NULL argument");
+  *out = nullptr;
+  rt_nrc_config cfg;
+  rt_nrc_config_default(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.train_batch < 128 || cfg.train_batch > (1 << 22) || cfg.terminate_depth < 1 ||
+      cfg.terminate_depth > RT_MAX_DEPTH || !(cfg.lr > 0.f) || !(cfg.beta1 >= 0.f && cfg.beta1 < 1.f) ||
+      !(cfg.beta2 >= 0.f && cfg.beta2 < 1.f) || !(cfg.eps > 0.f))
+    return set_error(RT_ERR_INVALID_ARG, "rt_nrc_create: invalid configuration");
+  rt_nrc* r = new rt_nrc();
+  r->cfg = cfg;
+  cudaDeviceGetAttribute(&r->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  r->infer_blocks = r->sm_count * 2;
+  for (int j = 0; j < 3; ++j) {
+    float lo = s->bbox_lo[j], hi = s->bbox_hi[j];
+    if (!(hi > lo)) hi = lo + 1.f;
+    r->nd.lo[j] = lo;
+    r->nd.inv_ext[j] = 1.f / (hi - lo);
+  }
+  rt_status rs;
+  if ((rs = ensure(r->params, kNP * 4)) || (rs = ensure(r->m, kNP * 4)) || (rs = ensure(r->v, kNP * 4)) ||
+      (rs = ensure(r->grad, (kNP + 16) * 4)) || (rs = ensure(r->packed, kPackedBytes))) {
+    rt_nrc_destroy(r);
+    return rs;
+  }
+  // He-uniform initialisation, seeded; biases zero
+  std::vector<float> w(kNP, 0.f);
+  uint64_t st = cfg.seed * 0x2545F4914F6CDD1Dull + 12345;
+  for (int l = 0; l < 5; ++l) {
+    int fan_in = l == 0 ? kFeatures : 64;
+    float a = std::sqrt(6.0f / (float)fan_in);
+    for (int o = 0; o < d_out(l); ++o)
+      for (int i = 0; i < d_in(l); ++i) {
+        float u = (float)((splitmix64(st) >> 11) * (1.0 / 9007199254740992.0));
+        w[off_w(l) + o * d_in(l) + i] = (l == 0 && i >= kFeatures) ? 0.f : (2.f * u - 1.f) * a;
+      }
+  }
+  cudaError_t e = cudaMemcpy(r->params.p, w.data(), kNP * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(r->m.p, 0, kNP * 4);
+  if (e == cudaSuccess) e = cudaMemset(r->v.p, 0, kNP * 4);
+  if (e != cudaSuccess) {
+    rt_nrc_destroy(r);
+    return cuda_error(e, "rt_nrc_create");
+  }
+  r->nd.packed = r->packed.p;
+  r->nd.target = nullptr;
+  if ((rs = nrc_pack(r, 0)) || (rs = nrc_setup_kernels())) {
+    rt_nrc_destroy(r);
+    return rs;
+  }
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    rt_nrc_destroy(r);
+    return cuda_error(e, "rt_nrc_create");
+  }
+  *out = r;
+  return RT_OK;
+}
+
+rt_status rt_nrc_destroy(rt_nrc* r) {
+  if (!r) return RT_OK;
+  cudaDeviceSynchronize();
+  release(r->params);
+  release(r->m);
+  release(r->v);
+  release(r->grad);
+  release(r->packed);
+  release(r->infer_q);
+  release(r->train_q);
+  release(r->train_target);
+  release(r->counters);
+  delete r;
+  return RT_OK;
+}
+
+rt_status rt_nrc_get_params(rt_nrc* r, float* host, void* stream) {
+  if (!r || !host) return set_error(RT_ERR_INVALID_ARG, "rt_nrc_get_params: NULL argument");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(host, r->params.p, kNP * 4, cudaMemcpyDeviceToHost);
+  return cuda_error(e, "rt_nrc_get_params");
+}
+
+rt_status rt_nrc_set_params(rt_nrc* r, const float* host, void* stream) {
+  if (!r || !host) return set_error(RT_ERR_INVALID_ARG, "rt_nrc_set_params: NULL argument");
+  for (int i = 0; i < kNP; ++i)
+    if (!std::isfinite(host[i])) return set_error(RT_ERR_INVALID_ARG, "rt_nrc_set_params: non-finite value");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(r->params.p, host, kNP * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(r->m.p, 0, kNP * 4);
+  if (e == cudaSuccess) e = cudaMemset(r->v.p, 0, kNP * 4);
+  if (e != cudaSuccess) return cuda_error(e, "rt_nrc_set_params");
+  r->step = 0;
+  return nrc_pack(r, st);
+}
+
+rt_status rt_nrc_get_grads(rt_nrc* r, float* host, float* loss, void* stream) {
+  if (!r || !host) return set_error(RT_ERR_INVALID_ARG, "rt_nrc_get_grads: NULL argument");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(host, r->grad.p, kNP * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && loss) e = cudaMemcpy(loss, (float*)r->grad.p + kNP, 4, cudaMemcpyDeviceToHost);
+  return cuda_error(e, "rt_nrc_get_grads");
+}
+
+// Plain queries (tests, tools): n hits (p, n, v) -> radiance exp(MLP).
+rt_status rt_nrc_infer(rt_nrc* r, rt_scene* s, const float* pnv_dev, int64_t n, float* out_dev, void* stream) {
+  if (!r || !s || (n > 0 && (!pnv_dev || !out_dev)) || n < 0 || n > (1 << 26))
+    return set_error(RT_ERR_INVALID_ARG, "rt_nrc_infer: bad argument");
+  if (n == 0) return RT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  rt_status rs;
+  if ((rs = ensure(r->infer_q, (size_t)n * 64)) || (rs = ensure(r->counters, 64))) return rs;
+  cudaError_t e = cudaMemcpyAsync(r->counters.p, &n, 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "rt_nrc_infer");
+  nrc_make_records(pnv_dev, nullptr, n, (float4*)r->infer_q.p, 4, st);
+  return nrc_infer_launch(r, (const float4*)r->infer_q.p, (const unsigned*)r->counters.p, (unsigned)n, nullptr,
+                          out_dev, s->status, st);
+}
+
+// One training step on n given samples (p, n, v) with targets (n x 3):
+// gradients (rt_nrc_get_grads), then Adam.
+rt_status rt_nrc_train_step(rt_nrc* r, rt_scene* s, const float* pnv_dev, const float* target_dev, int64_t n,
+                            void* stream) {
+  if (!r || !s || n <= 0 || n > (1 << 26) || !pnv_dev || !target_dev)
+    return set_error(RT_ERR_INVALID_ARG, "rt_nrc_train_step: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  rt_status rs;
+  if ((rs = ensure(r->train_q, (size_t)n * 48)) || (rs = ensure(r->counters, 64))) return rs;
+  cudaError_t e = cudaMemcpyAsync((unsigned*)r->counters.p + 1, &n, 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "rt_nrc_train_step");
+  nrc_make_records(pnv_dev, target_dev, n, (float4*)r->train_q.p, 3, st);
+  return nrc_train_launch(r, (const float4*)r->train_q.p, target_dev, (const unsigned*)r->counters.p + 1,
+                          (unsigned)n, s->status, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+// nrc_internal.cuh - shared declarations of the radiance-cache code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rtb.h"
+
+namespace rtb {
+
+constexpr int kFeatures = 81;                          // encoded features (padded to 96)
+constexpr int kNW = 64 * 96 + 3 * 64 * 64 + 3 * 64;    // weights, oracle layout
+constexpr int kNB = 4 * 64 + 3;                        // biases
+constexpr int kNP = kNW + kNB;                         // 18,883 parameters
+constexpr unsigned kErrNrcTimeout = 8u;                // a tensor-core wait timed out
+
+// What the cache kernels read, by value.
+struct NrcDevice {
+  const void* packed;     // BF16 weights (forward + transposed) then FP32 biases
+  float* target;          // training targets of the current frame (3 per slot)
+  float lo[3], inv_ext[3];
+};
+
+rt_status nrc_infer_launch(rt_nrc* r, const float4* recs, const unsigned* count, unsigned cap, float* fb, float* out3,
+                           unsigned* status, cudaStream_t st);
+rt_status nrc_train_launch(rt_nrc* r, const float4* recs, const float* targets, const unsigned* count, unsigned cap,
+                           unsigned* status, cudaStream_t st);
+// Records from caller arrays: pnv n x 9 -> stride-4 (inference, weight 1)
+// or stride-3 (training, slot = index) float4 records.
+void nrc_make_records(const float* pnv, const float* targets, int64_t n, float4* recs, int stride, cudaStream_t st);
+NrcDevice* nrc_device(rt_nrc* r);
+
+// Per-frame buffers of a cached render.
+struct NrcFrame {
+  int depth;
+  float* target;
+  float4 *infer_q, *train_q;
+  unsigned infer_cap, train_cap, train_batch;
+  uint32_t seed;
+};
+rt_status nrc_frame_buffers(rt_nrc* r, int64_t ray_cap, bool train, NrcFrame* out);
+
+}  // namespace rtb

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <vector>
 
+#include "nrc_internal.cuh"
 #include "rtb_internal.cuh"
 
 namespace rtb {
@@ -33,6 +34,7 @@ struct Counters {
   unsigned fetch_trace[RT_MAX_DEPTH + 1]; // dynamic work fetch
   unsigned fetch_shadow[RT_MAX_DEPTH + 1];
   unsigned max_visits[2][RT_MAX_DEPTH + 1];          // [closest, any][depth], counting runs only
+  unsigned infer_count, train_count;                 // radiance-cache records of the frame
   unsigned long long visits[2][RT_MAX_DEPTH + 1];
   unsigned long long tests[2][RT_MAX_DEPTH + 1];
 };
@@ -50,6 +52,15 @@ struct FrameParams {
   float4* shadowq[2];                     // shadow queue of depth d: shadowq[d & 1]
   unsigned ray_cap, shadow_cap;
   Counters* ctr;
+  int path_depth0;          // first depth of the depth-first secondary kernel
+  // radiance cache (nrc_depth < 0: off)
+  int nrc_depth;
+  float* target;            // training targets: pixel ids < 0 route here (slot ~pixel)
+  float4* infer_q;          // 4 float4 per record: (p, pixel) (n) (v) (weight)
+  float4* train_q;          // 3 float4 per record: (p, slot) (n) (v)
+  unsigned infer_cap, train_cap;
+  unsigned train_batch;     // wanted training samples; selection probability = batch / rays
+  uint32_t seed;
 };
 
 // ---------------------------------------------------------------------------
@@ -217,7 +228,7 @@ __device__ __forceinline__ unsigned warp_push(unsigned* counter, bool pred, unsi
   }
   unsigned pos = base + (unsigned)__popc(mask & ((1u << lane) - 1u));
   ok = pred && pos < cap;
-  if (pred && pos >= cap) atomicOr(status, kErrQueueOverflow);
+  if (pred && pos >= cap && status) atomicOr(status, kErrQueueOverflow);
   return pos;
 }
 
@@ -228,11 +239,22 @@ __device__ __forceinline__ void store_ray(float4* q, unsigned pos, f3 o, int pix
   p[2] = make_float4(w.x, w.y, w.z, 0.f);
 }
 
-__device__ __forceinline__ void add_fb(float* fb, int pixel, f3 c) {
-  float* p = fb + 3 * (size_t)pixel;
+// Adds radiance to a pixel, or to a training target when the ray belongs to
+// the radiance cache's training subset (pixel id < 0 -> slot ~pixel).
+__device__ __forceinline__ void add_fb(const FrameParams& fp, int pixel, f3 c) {
+  float* p = pixel >= 0 ? fp.fb + 3 * (size_t)pixel : fp.target + 3 * (size_t)(~pixel);
   atomicAdd(p, c.x);
   atomicAdd(p + 1, c.y);
   atomicAdd(p + 2, c.z);
+}
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
 }
 
 template <bool kCount>
@@ -412,16 +434,42 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(DevScene sc, FramePa
     }
     // shading
     bool is_hit = active && hit >= 0;
-    if (active && hit < 0) add_fb(fp.fb, pixel, w * mk3(fp.bg_r, fp.bg_g, fp.bg_b));
+    if (active && hit < 0) add_fb(fp, pixel, w * mk3(fp.bg_r, fp.bg_g, fp.bg_b));
     unsigned hm = __ballot_sync(kFull, is_hit);
     if (lane == 0 && hm) atomicAdd(&ctr->hits[depth], (unsigned)__popc(hm));
     Surface sf;
     sf.kind = RT_MAT_DIELECTRIC;   // no local term, no children unless a hit sets it
-    if (is_hit) {
-      sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
-      if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f)
-        add_fb(fp.fb, pixel, w * sf.emission);   // L_e, Eq. 7
+    if (is_hit) sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
+    if (depth == fp.nrc_depth) {
+      // radiance cache: every hit here takes the rest of its path from the
+      // cache; a seeded subset is also traced on, with unit weight, into a
+      // training target
+      bool ok;
+      unsigned pos = warp_push(&ctr->infer_count, is_hit, fp.infer_cap, ok, sc.status);
+      if (ok) {
+        float4* q = fp.infer_q + 4 * (size_t)pos;
+        q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float(pixel));
+        q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
+        q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
+        q[3] = make_float4(w.x, w.y, w.z, 0.f);
+      }
+      float u = (float)(hash32(fp.seed ^ hash32((uint32_t)pixel * 0x9E3779B9u ^ __float_as_uint(d.x))) >> 8) *
+                (1.0f / 16777216.0f);
+      bool sel = is_hit && (float)fp.train_batch > u * (float)n_items;
+      unsigned slot = warp_push(&ctr->train_count, sel, fp.train_cap, ok, nullptr);   // a full batch is no error
+      sel = sel && slot < fp.train_cap;
+      if (sel) {
+        float4* q = fp.train_q + 3 * (size_t)slot;
+        q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float((int)slot));
+        q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
+        q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
+        w = mk3(1.f, 1.f, 1.f);
+        pixel = ~(int)slot;
+      }
+      is_hit = sel;
     }
+    if (is_hit && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f))
+      add_fb(fp, pixel, w * sf.emission);   // L_e, Eq. 7
     // Alg. 1: one shadow ray per point light where n.l > 0
     bool local = is_hit && sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f;
     for (int li = 0; li < sc.n_lights; ++li) {
@@ -475,7 +523,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FramePara
       int h = traverse<true, kCount>(sc, ri, 0.0f, tmax, stack, cap, fail, wc);
       if (kCount) wc.vmax = max(wc.vmax, wc.visits - v0);
       if (fail) atomicOr(sc.status, kErrTraversalLimit);
-      if (h < 0 && !fail) add_fb(fp.fb, __float_as_int(q0.w), xyz(q2));
+      if (h < 0 && !fail) add_fb(fp, __float_as_int(q0.w), xyz(q2));
     }
   }
   flush_work<kCount>(ctr, 1, depth, wc);
@@ -509,14 +557,15 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
   for (int i = threadIdx.x; i < 3 * (RT_MAX_DEPTH + 2); i += blockDim.x) (&s_cnt[0][0])[i] = 0u;
   __syncthreads();
   Counters* ctr = fp.ctr;
-  unsigned n_items = min(ctr->rays[1], fp.ray_cap);
-  const float4* __restrict__ qin = fp.rayq[1];
+  const int d0 = fp.path_depth0;
+  unsigned n_items = min(ctr->rays[d0], fp.ray_cap);
+  const float4* __restrict__ qin = fp.rayq[d0 & 1];
   const f3 bg = mk3(fp.bg_r, fp.bg_g, fp.bg_b);
   Pending pend[RT_MAX_DEPTH];
   int np = 0;
   WorkCount wc = {0u, 0u, 0u};
   f3 o = mk3(0, 0, 0), d = mk3(0, 0, 1), w = mk3(0, 0, 0);
-  int depth = 1, pixel = 0;
+  int depth = d0, pixel = 0;
   for (;;) {
     if (np > 0) {
       --np;
@@ -525,14 +574,14 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
       w = pend[np].w;
       depth = pend[np].depth;
     } else {
-      unsigned idx = atomicAdd(&ctr->fetch_trace[1], 1u);
+      unsigned idx = atomicAdd(&ctr->fetch_trace[d0], 1u);
       if (idx >= n_items) break;
       float4 q0 = qin[3 * (size_t)idx], q1 = qin[3 * (size_t)idx + 1], q2 = qin[3 * (size_t)idx + 2];
       o = xyz(q0);
       pixel = __float_as_int(q0.w);
       d = xyz(q1);
       w = xyz(q2);
-      depth = 1;
+      depth = d0;
     }
     // follow this ray and, at each hit, one of its children; the other
     // child waits on the thread's own stack
@@ -544,12 +593,12 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
       count_ray<kCount>(ctr, 0, depth, wc.visits - v0, wc.tests - t0);
       if (fail) atomicOr(sc.status, kErrTraversalLimit);
       if (hit < 0) {
-        add_fb(fp.fb, pixel, w * bg);
+        add_fb(fp, pixel, w * bg);
         break;
       }
       atomicAdd(&s_cnt[2][depth], 1u);
       Surface sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
-      if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp.fb, pixel, w * sf.emission);
+      if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
       if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
         for (int li = 0; li < sc.n_lights; ++li) {
           f3 contrib, os, sd;
@@ -562,7 +611,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
           int h = traverse<true, kCount>(sc, make_ray(os, sd), 0.0f, tmax, stack, cap, sfail, wc);
           count_ray<kCount>(ctr, 1, depth, wc.visits - sv0, wc.tests - st0);
           if (sfail) atomicOr(sc.status, kErrTraversalLimit);
-          if (h < 0 && !sfail) add_fb(fp.fb, pixel, contrib);
+          if (h < 0 && !sfail) add_fb(fp, pixel, contrib);
         }
       }
       if (depth >= fp.max_depth) break;
@@ -594,7 +643,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
   }
   __syncthreads();
   for (int i = threadIdx.x; i <= RT_MAX_DEPTH; i += blockDim.x) {
-    if (s_cnt[0][i] && i >= 2) atomicAdd(&ctr->rays[i], s_cnt[0][i]);
+    if (s_cnt[0][i]) atomicAdd(&ctr->rays[i], s_cnt[0][i]);
     if (s_cnt[1][i]) atomicAdd(&ctr->shadow[i], s_cnt[1][i]);
     if (s_cnt[2][i]) atomicAdd(&ctr->hits[i], s_cnt[2][i]);
   }
@@ -742,7 +791,7 @@ static rt_status ensure_side_stream(rt_scene* s) {
 
 static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, int D, float* out,
                              const rt_render_options* opt_in, int32_t* aov_prim, float* aov_t, rt_render_stats* stats,
-                             cudaStream_t st) {
+                             cudaStream_t st, rt_nrc* nrc = nullptr, int train = 0) {
   if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_render: scene is NULL");
   if (!cam || !finite_cam(cam)) return set_error(RT_ERR_INVALID_ARG, "rt_render: invalid camera");
   if (W < 1 || H < 1) return set_error(RT_ERR_INVALID_ARG, "rt_render: width and height must be >= 1");
@@ -798,6 +847,29 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   fp.ray_cap = (unsigned)qcap;
   fp.shadow_cap = (unsigned)pcap;
   fp.ctr = (Counters*)s->counters.p;
+  fp.path_depth0 = 1;
+  fp.nrc_depth = -1;
+  fp.target = nullptr;
+  fp.infer_q = fp.train_q = nullptr;
+  fp.infer_cap = fp.train_cap = fp.train_batch = 0;
+  fp.seed = 0;
+  int T = -1;   // radiance-cache depth of this frame
+  if (nrc) {
+    NrcFrame nf;
+    rs = nrc_frame_buffers(nrc, qcap, train != 0, &nf);
+    if (rs) return rs;
+    T = nf.depth <= D ? nf.depth : -1;
+    fp.nrc_depth = T;
+    fp.target = nf.target;
+    fp.infer_q = nf.infer_q;
+    fp.train_q = nf.train_q;
+    fp.infer_cap = nf.infer_cap;
+    fp.train_cap = nf.train_cap;
+    fp.train_batch = train ? nf.train_batch : 0u;
+    fp.seed = nf.seed;
+    fp.path_depth0 = T + 1;
+    if (T >= 0 && train) cudaMemsetAsync(fp.target, 0, (size_t)nf.train_cap * 12, st);
+  }
   bool timing = (opt.flags & RT_FLAG_STAGE_TIMING) != 0;
   bool count = (opt.flags & RT_FLAG_COUNT_WORK) != 0;
   int launches = 0;
@@ -809,7 +881,9 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);
   cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
   bool per_depth = (opt.flags & RT_FLAG_PER_DEPTH_WAVEFRONT) != 0;
-  int last = per_depth ? D : 0;   // depths run as wavefronts; the rest run as paths
+  // depths 0..last run as wavefronts; the rest run as depth-first paths
+  // (with the cache: up to its depth, then only the training rays go on)
+  int last = per_depth ? D : (T >= 0 ? T : 0);
   for (int depth = 0; depth <= last; ++depth) {
     // trace(depth) fills the shadow buffer that shadow(depth - 2) reads
     if (depth >= 2) cudaStreamWaitEvent(st, s->ev_shadowed[depth - 2], 0);
@@ -832,7 +906,17 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     cudaEventRecord(s->ev_shadowed[depth], s->side);
     launches += 2;
   }
-  if (!per_depth && D >= 1) {
+  if (T >= 0) {
+    // cache lookups of the depth-T hits, beside the training rays' paths
+    int slot = timing ? timing_begin(s, 2, s->side) : -1;
+    rs = nrc_infer_launch(nrc, fp.infer_q, &fp.ctr->infer_count, fp.infer_cap, out, nullptr, s->status, s->side);
+    if (rs) return rs;
+    if (timing) timing_end(s, slot, s->side);
+    cudaEventRecord(s->ev_shadowed[last], s->side);
+    launches += 1;
+  }
+  bool run_paths = !per_depth && D > last && (T < 0 || train);
+  if (run_paths) {
     int slot = timing ? timing_begin(s, 0, st) : -1;
     if (count) k_paths<true><<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);
     else k_paths<false><<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);
@@ -840,6 +924,14 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     launches += 1;
   }
   cudaStreamWaitEvent(st, s->ev_shadowed[last], 0);
+  if (T >= 0 && train) {
+    // one Adam step on this frame's targets (complete once both streams joined)
+    int slot = timing ? timing_begin(s, 2, st) : -1;
+    rs = nrc_train_launch(nrc, fp.train_q, fp.target, &fp.ctr->train_count, fp.train_cap, s->status, st);
+    if (rs) return rs;
+    if (timing) timing_end(s, slot, st);
+    launches += 4;
+  }
   if (timing) timing_end(s, frame_slot, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "rt_render launch");
@@ -907,6 +999,15 @@ rt_status rt_render_host(rt_scene* s, const rt_camera* cam, int width, int heigh
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_error(e, "rt_render_host");
   return RT_OK;
+}
+
+rt_status rt_render_nrc(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int width, int height, int max_depth,
+                        float* out, int train, rt_render_stats* stats, void* stream) {
+  if (!nrc) return set_error(RT_ERR_INVALID_ARG, "rt_render_nrc: cache is NULL");
+  rt_render_options opt;
+  rt_render_options_default(&opt);
+  return render_impl(s, cam, width, height, max_depth, out, &opt, nullptr, nullptr, stats, (cudaStream_t)stream, nrc,
+                     train);
 }
 
 rt_status rt_render_stage_times(rt_scene* s, float* ms_total, float* ms_trace, float* ms_shadow) {

@@ -88,6 +88,7 @@ struct GraphCache;
 struct rt_scene {
   int device = 0;
   int64_t n_spheres = 0, n_tris = 0, n_prims = 0, n_mats = 0, n_lights = 0;
+  float bbox_lo[3] = {0.f, 0.f, 0.f}, bbox_hi[3] = {1.f, 1.f, 1.f};   // of the input geometry
   // geometry
   rtb::Buf raw_sph, raw_tri;     // raw ABI structs on the device (for repacking)
   rtb::Buf prims_id;             // packed records, primitive-id order

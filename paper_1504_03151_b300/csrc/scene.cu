@@ -2,6 +2,7 @@
 // error reporting of the C ABI.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -159,6 +160,25 @@ rt_status rt_scene_create(const rt_sphere* spheres, size_t n_spheres, const rt_t
       return set_error(RT_ERR_INVALID_ARG, "light " + std::to_string(i) + ": non-finite value");
 
   rt_scene* s = new rt_scene();
+  {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (size_t i = 0; i < n_spheres; ++i)
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], spheres[i].center[k] - spheres[i].radius);
+        hi[k] = std::max(hi[k], spheres[i].center[k] + spheres[i].radius);
+      }
+    for (size_t i = 0; i < n_triangles; ++i)
+      for (int k = 0; k < 3; ++k) {
+        const rt_triangle& t = triangles[i];
+        lo[k] = std::min(lo[k], std::min(t.v0[k], std::min(t.v1[k], t.v2[k])));
+        hi[k] = std::max(hi[k], std::max(t.v0[k], std::max(t.v1[k], t.v2[k])));
+      }
+    for (int k = 0; k < 3; ++k)
+      if (lo[k] <= hi[k]) {
+        s->bbox_lo[k] = lo[k];
+        s->bbox_hi[k] = hi[k];
+      }
+  }
   cudaGetDevice(&s->device);
   cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
   s->n_spheres = (int64_t)n_spheres;

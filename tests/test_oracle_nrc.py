@@ -118,3 +118,17 @@ def test_training_reduces_loss():
         O.adam(p, np.concatenate([dW, dB]), m, v, step, lr=1e-2)
     last, _, _ = O.mlp_loss_grad(x, t, p[:O.N_W], p[O.N_W:])
     assert last < 0.2 * first
+
+
+def test_bf16_activation_rounding_option():
+    # one path x0 -> h -> ... -> out with all weights 1: h = x0 rounded to BF16
+    W = np.zeros(O.N_W)
+    offs = np.cumsum([0, 96 * 64, 64 * 64, 64 * 64, 64 * 64])
+    for o in offs:
+        W[o] = 1.0
+    x = np.zeros((1, 96))
+    x[0, 0] = 1.0 + 2.0 ** -10          # not representable in BF16 (8 bits of mantissa): rounds to 1
+    y = O.mlp_forward(x, W, np.zeros(O.N_B), bf16_acts=True)
+    assert y[0, 0] == pytest.approx(math.exp(1.0), rel=1e-15)
+    y = O.mlp_forward(x, W, np.zeros(O.N_B), bf16_acts=False)
+    assert y[0, 0] == pytest.approx(math.exp(1.0 + 2.0 ** -10), rel=1e-15)
