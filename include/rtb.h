@@ -285,9 +285,11 @@ rt_status rt_nrc_train_step(rt_nrc* nrc, rt_scene* s, const float* pnv_device, c
  * cache (no shadow or secondary rays there); when `train` is set, a seeded
  * subset of those hits (about train_batch) is also traced to max_depth with
  * unit weight, the results become training targets and one Adam step runs
- * after the frame.  Stats as in rt_render_ex (rays actually traced). */
+ * after the frame.  Options (NULL = defaults) and stats as in rt_render_ex
+ * (rays actually traced). */
 rt_status rt_render_nrc(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int width, int height, int max_depth,
-                        float* out_rgb_device, int train, rt_render_stats* stats, void* stream);
+                        float* out_rgb_device, int train, const rt_render_options* opt, rt_render_stats* stats,
+                        void* stream);
 
 /* Waits for `stream` and returns (and clears) the latched kernel error. */
 rt_status rt_scene_sync(rt_scene* s, void* stream);

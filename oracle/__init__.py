@@ -59,6 +59,9 @@ def lib():
         L.orc_mlp_loss_grad_ex.restype = D
         L.orc_mlp_loss_grad_ex.argtypes = [I64, P, P, P, P, P, P, I32]
         L.orc_adam.argtypes = [I64, P, P, P, P, I64, D, D, D, D]
+        L.orc_set_cache.argtypes = [P, I32, P, P, I32, P, P]
+        L.orc_round_bf16.restype = D
+        L.orc_round_bf16.argtypes = [D]
         _lib = L
     return _lib
 
@@ -100,6 +103,21 @@ class OracleScene:
         if h:
             lib().orc_scene_free(h)
             self._h = None
+
+    def set_cache(self, depth, params, lo, inv_ext, bf16=True):
+        """Terminates hits at `depth` with the radiance cache (params: the
+        18,883 FP32 parameters; weights rounded to BF16 when bf16)."""
+        params = np.asarray(params, np.float64)
+        W = params[:N_W].copy()
+        if bf16:
+            W = round_bf16(W)
+        B = np.ascontiguousarray(params[N_W:N_W + N_B])
+        self._cache = (np.ascontiguousarray(W), B, _f64(lo), _f64(inv_ext))
+        lib().orc_set_cache(self._h, int(depth), _ptr(self._cache[0]), _ptr(self._cache[1]), int(bf16),
+                            _ptr(self._cache[2]), _ptr(self._cache[3]))
+
+    def clear_cache(self):
+        lib().orc_set_cache(self._h, -1, None, None, 0, None, None)
 
     @property
     def bvh_nodes(self) -> int:
@@ -201,6 +219,14 @@ def refract(d, n, n1, n2):
 
 
 # ---- radiance cache network ------------------------------------------------
+def round_bf16(x):
+    """Nearest BF16 value (ties to even), through FP32, as float64."""
+    a = np.ascontiguousarray(x, np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 MLP_DIMS = (96, 64, 64, 64, 64, 3)
 N_W = sum(MLP_DIMS[i] * MLP_DIMS[i + 1] for i in range(5))
 N_B = sum(MLP_DIMS[1:])

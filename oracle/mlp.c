@@ -44,7 +44,7 @@ void orc_nrc_encode(int64_t n, const double* in, const double* lo, const double*
 
 /* Round to the nearest BF16 value (ties to even), through FP32.  Used when
  * the network's activations are stored in BF16 between layers. */
-static double round_bf16(double x) {
+double orc_round_bf16(double x) {
   float f = (float)x;
   uint32_t u;
   memcpy(&u, &f, 4);
@@ -76,7 +76,7 @@ static void fwd1(const double* x, const double* W, const double* B, double a[6][
       for (int k = 0; k < DIMS[l]; ++k) s += Wl[(int64_t)o * DIMS[l] + k] * a[l][k];
       z[l + 1][o] = s;
       double h = (l < 4) ? (s > 0 ? s : 0) : exp(s);
-      a[l + 1][o] = (bf16 && l < 4) ? round_bf16(h) : h;
+      a[l + 1][o] = (bf16 && l < 4) ? orc_round_bf16(h) : h;
     }
   }
 }
@@ -114,7 +114,7 @@ double orc_mlp_loss_grad_ex(int64_t n, const double* x, const double* target, co
       double* dWl = dW + w_off(l);
       double* dBl = dB + b_off(l);
       double gr[96];   /* the gradient the weight and input gradients use */
-      for (int o = 0; o < DIMS[l + 1]; ++o) gr[o] = bf16 ? round_bf16(g[l + 1][o]) : g[l + 1][o];
+      for (int o = 0; o < DIMS[l + 1]; ++o) gr[o] = bf16 ? orc_round_bf16(g[l + 1][o]) : g[l + 1][o];
       for (int o = 0; o < DIMS[l + 1]; ++o) {
         dBl[o] += g[l + 1][o];
         for (int k = 0; k < DIMS[l]; ++k) dWl[(int64_t)o * DIMS[l] + k] += gr[o] * a[l][k];

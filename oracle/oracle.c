@@ -108,6 +108,11 @@ struct orc_scene {
   double l_max;        /* bound on the radiance any subtree returns */
   v3 scene_lo, scene_hi;
   int64_t n_nodes; node_t* nodes; int64_t* order;
+  /* radiance cache (nrc_depth < 0: none): network parameters and box */
+  int nrc_depth, nrc_bf16;
+  double* nrc_W;
+  double* nrc_B;
+  double nrc_lo[3], nrc_inv_ext[3];
 };
 
 /* A ray with the modelled FP32 uncertainty of its origin (absolute, eo),
@@ -638,6 +643,27 @@ typedef struct {
   double robust;
 } trace_ctx;
 
+/* The radiance cache's answer for a hit: exp(MLP(encode(p, n, -d))), with
+ * n the normal facing the ray; it replaces the hit's local term and all of
+ * its children. */
+static v3 cache_radiance(const orc_scene* s, const ray_t* r, hit_t h) {
+  const prim_t* p = &s->prims[h.prim];
+  v3 ph = add(r->o, scl(r->d, h.t));
+  v3 ng = geometric_normal(p, ph);
+  v3 n = dot(r->d, ng) > 0.0 ? scl(ng, -1.0) : ng;
+  double pnv[9] = {0, 0, 0, n.x, n.y, n.z, -r->d.x, -r->d.y, -r->d.z};
+  double pc[3] = {ph.x, ph.y, ph.z};
+  /* normalised position first, then the encoding of an identity box */
+  for (int j = 0; j < 3; ++j) pnv[j] = (pc[j] - s->nrc_lo[j]) * s->nrc_inv_ext[j];
+  double f[96], y[3];
+  double zero[3] = {0, 0, 0}, one[3] = {1, 1, 1};
+  orc_nrc_encode(1, pnv, zero, one, f);
+  if (s->nrc_bf16)
+    for (int k = 0; k < 96; ++k) f[k] = orc_round_bf16(f[k]);
+  orc_mlp_forward_ex(1, f, s->nrc_W, s->nrc_B, y, s->nrc_bf16);
+  return mk(y[0], y[1], y[2]);
+}
+
 /* Radiance arriving along r at depth `depth`, times the ray weight w. */
 static v3 trace_rec(trace_ctx* cx, const ray_t* r, int depth, v3 w, int32_t* prim0, double* t0) {
   const orc_scene* s = cx->s;
@@ -649,6 +675,7 @@ static v3 trace_rec(trace_ctx* cx, const ray_t* r, int depth, v3 w, int32_t* pri
   if (prim0) { *prim0 = h.prim; *t0 = h.t; }
   if (h.prim < 0) return mul(w, s->bg);
   cx->counts[3 + 3 * depth + 2]++;
+  if (depth == s->nrc_depth) return mul(w, cache_radiance(s, r, h));
   shade_t sh = shade_hit(s, r, w, h.prim, h.t, h.cosn, depth < cx->max_depth, cx->use_bvh, 1);
   if (sh.robust < cx->robust) cx->robust = sh.robust;
   cx->counts[1] += (uint64_t)sh.n_shadow;
@@ -680,6 +707,7 @@ static v3 trace_iter(trace_ctx* cx, const ray_t* r0, int32_t* prim0, double* t0)
       if (depth == 0 && prim0) { *prim0 = h.prim; *t0 = h.t; }
       if (h.prim < 0) { pix = add(pix, mul(cur[i].w, s->bg)); continue; }
       cx->counts[3 + 3 * depth + 2]++;
+      if (depth == s->nrc_depth) { pix = add(pix, mul(cur[i].w, cache_radiance(s, &cur[i].r, h))); continue; }
       shade_t sh = shade_hit(s, &cur[i].r, cur[i].w, h.prim, h.t, h.cosn, depth < cx->max_depth, 0, 0);
       cx->counts[1] += (uint64_t)sh.n_shadow;
       cx->counts[3 + 3 * depth + 1] += (uint64_t)sh.n_shadow;
@@ -742,6 +770,7 @@ orc_scene* orc_scene_create(const void* spheres, int64_t ns, const void* triangl
   s->bg = mk(background[0], background[1], background[2]);
   s->eps_scale = eps_scale;
   s->K = fragile_k;
+  s->nrc_depth = -1;
   const in_mat* im = (const in_mat*)materials;
   double ks_max = 0, em_max = 0;
   for (int64_t i = 0; i < nm; ++i) {
@@ -822,10 +851,29 @@ bad:
 void orc_scene_free(orc_scene* s) {
   if (!s) return;
   free(s->prims); free(s->mats); free(s->lights); free(s->nodes); free(s->order);
+  free(s->nrc_W); free(s->nrc_B);
   free(s);
 }
 
 int64_t orc_bvh_node_count(const orc_scene* s) { return s->n_nodes; }
+
+void orc_set_cache(orc_scene* s, int depth, const double* W, const double* B, int bf16, const double* lo,
+                   const double* inv_ext) {
+  free(s->nrc_W);
+  free(s->nrc_B);
+  s->nrc_W = s->nrc_B = NULL;
+  s->nrc_depth = depth;
+  if (depth < 0) return;
+  s->nrc_W = (double*)malloc(sizeof(double) * ORC_NRC_NW);
+  s->nrc_B = (double*)malloc(sizeof(double) * ORC_NRC_NB);
+  memcpy(s->nrc_W, W, sizeof(double) * ORC_NRC_NW);
+  memcpy(s->nrc_B, B, sizeof(double) * ORC_NRC_NB);
+  s->nrc_bf16 = bf16;
+  for (int j = 0; j < 3; ++j) {
+    s->nrc_lo[j] = lo[j];
+    s->nrc_inv_ext[j] = inv_ext[j];
+  }
+}
 
 /* ------------------------------------------------------------------ */
 /* entry points                                                         */

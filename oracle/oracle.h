@@ -101,6 +101,19 @@ int orc_refract(const double* d, const double* n, double n1, double n2,
 
 /* ---- neural radiance cache oracle (FP64) ---------------------------- */
 
+#define ORC_NRC_NW 18624   /* W0[64][96] W1..W3[64][64] W4[3][64] */
+#define ORC_NRC_NB 259     /* b0..b3[64] b4[3] */
+
+/* Renders that follow terminate every hit at depth `depth` (-1: off) with
+ * the cache: radiance exp(MLP(encode(p, n, -d))) replaces that hit's local
+ * term and children.  Positions are normalised as (p - lo) * inv_ext.
+ * bf16 != 0: features and hidden activations rounded to BF16. */
+void orc_set_cache(orc_scene* s, int depth, const double* W, const double* B, int bf16, const double* lo,
+                   const double* inv_ext);
+
+/* Round to the nearest BF16 value (ties to even), through FP32. */
+double orc_round_bf16(double x);
+
 /* Frequency encoding of a hit: 3 normalised position values, normal (3),
  * view direction (3) and sin/cos(2^k pi x_hat) for k = 0..11 (72), i.e.
  * 81 features, zero-padded to 96.  in: n x 9 (p, n, v), bbox: lo[3], hi[3]. */

@@ -128,7 +128,7 @@ def lib():
             "rt_nrc_get_grads": (I, [P, P, P, P]),
             "rt_nrc_infer": (I, [P, P, P, I64, P, P]),
             "rt_nrc_train_step": (I, [P, P, P, P, I64, P]),
-            "rt_render_nrc": (I, [P, P, P, I, I, I, P, I, P, P]),
+            "rt_render_nrc": (I, [P, P, P, I, I, I, P, I, P, P, P]),
             "rt_scene_destroy": (I, [P]),
         }
         for name, (res, args) in sigs.items():
@@ -377,10 +377,12 @@ def rt_nrc_train_step(nrc, scene, pnv_dev, target_dev, n, stream=None):
     _check(lib().rt_nrc_train_step(nrc, scene, _dptr(pnv_dev), _dptr(target_dev), n, _stream(stream)))
 
 
-def rt_render_nrc(scene, nrc, camera, width, height, max_depth, out_rgb, train=True, stats=False, stream=None):
+def rt_render_nrc(scene, nrc, camera, width, height, max_depth, out_rgb, train=True, options=None, stats=False,
+                  stream=None):
     cam = make_camera(camera)
     st = rt_render_stats() if stats else None
     _check(lib().rt_render_nrc(scene, nrc, ctypes.byref(cam), width, height, max_depth, _dptr(out_rgb), int(train),
+                               ctypes.byref(options) if options is not None else None,
                                ctypes.byref(st) if st is not None else None, _stream(stream)))
     return stats_dict(st, max_depth) if st is not None else None
 

@@ -630,13 +630,21 @@ rt_status nrc_train_launch(rt_nrc* r, const float4* recs, const float* targets, 
 
 NrcDevice* nrc_device(rt_nrc* r) { return &r->nd; }
 
+const unsigned* nrc_prev_hits(rt_nrc* r) { return (const unsigned*)r->counters.p + 4; }
+
+void nrc_keep_hits(rt_nrc* r, const unsigned* hits, cudaStream_t st) {
+  cudaMemcpyAsync((unsigned*)r->counters.p + 4, hits, 4, cudaMemcpyDeviceToDevice, st);
+}
+
 rt_status nrc_frame_buffers(rt_nrc* r, int64_t ray_cap, bool train, NrcFrame* out) {
   int64_t icap = std::max<int64_t>(ray_cap, 65536);
   int64_t tcap = r->cfg.train_batch;
   rt_status rs;
+  bool fresh = !r->counters.p;
   if ((rs = ensure(r->infer_q, (size_t)icap * 64)) || (rs = ensure(r->train_q, (size_t)tcap * 48)) ||
-      (rs = ensure(r->train_target, (size_t)tcap * 12)))
+      (rs = ensure(r->train_target, (size_t)tcap * 12)) || (rs = ensure(r->counters, 64)))
     return rs;
+  if (fresh) cudaMemset(r->counters.p, 0, 64);
   r->frame++;
   uint64_t sd = r->cfg.seed ^ (r->frame * 0x9E3779B97F4A7C15ull);
   out->depth = r->cfg.terminate_depth;
@@ -711,6 +719,10 @@ rt_status rt_nrc_create(rt_scene* s, const rt_nrc_config* cfg_in, rt_nrc** out) 
   if (e != cudaSuccess) {
     rt_nrc_destroy(r);
     return cuda_error(e, "rt_nrc_create");
+  }
+  if ((rs = ensure(r->counters, 64)) != RT_OK || cudaMemset(r->counters.p, 0, 64) != cudaSuccess) {
+    rt_nrc_destroy(r);
+    return rs ? rs : set_error(RT_ERR_CUDA, "rt_nrc_create: memset");
   }
   r->nd.packed = r->packed.p;
   r->nd.target = nullptr;

@@ -39,5 +39,8 @@ struct NrcFrame {
   uint32_t seed;
 };
 rt_status nrc_frame_buffers(rt_nrc* r, int64_t ray_cap, bool train, NrcFrame* out);
+// Cache hits of the previous frame (device), and the copy that keeps this frame's.
+const unsigned* nrc_prev_hits(rt_nrc* r);
+void nrc_keep_hits(rt_nrc* r, const unsigned* hits, cudaStream_t st);
 
 }  // namespace rtb

@@ -35,6 +35,7 @@ struct Counters {
   unsigned fetch_shadow[RT_MAX_DEPTH + 1];
   unsigned max_visits[2][RT_MAX_DEPTH + 1];          // [closest, any][depth], counting runs only
   unsigned infer_count, train_count;                 // radiance-cache records of the frame
+  unsigned cache_hits;                               // hits at the cache depth (depth-first frames)
   unsigned long long visits[2][RT_MAX_DEPTH + 1];
   unsigned long long tests[2][RT_MAX_DEPTH + 1];
 };
@@ -61,6 +62,7 @@ struct FrameParams {
   unsigned infer_cap, train_cap;
   unsigned train_batch;     // wanted training samples; selection probability = batch / rays
   uint32_t seed;
+  const unsigned* prev_hits;   // depth-first frames: cache hits of the previous frame (0: take all)
 };
 
 // ---------------------------------------------------------------------------
@@ -598,6 +600,33 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
       }
       atomicAdd(&s_cnt[2][depth], 1u);
       Surface sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
+      if (depth == fp.nrc_depth) {
+        // radiance cache (as in k_trace); the selection probability comes
+        // from the previous frame's number of cache hits
+        atomicAdd(&ctr->cache_hits, 1u);
+        unsigned pos = atomicAdd(&ctr->infer_count, 1u);
+        if (pos < fp.infer_cap) {
+          float4* q = fp.infer_q + 4 * (size_t)pos;
+          q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float(pixel));
+          q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
+          q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
+          q[3] = make_float4(w.x, w.y, w.z, 0.f);
+        } else {
+          atomicOr(sc.status, kErrQueueOverflow);
+        }
+        unsigned prev = fp.prev_hits ? *fp.prev_hits : 0u;
+        float u = (float)(hash32(fp.seed ^ hash32((uint32_t)pixel * 0x9E3779B9u ^ __float_as_uint(d.x))) >> 8) *
+                  (1.0f / 16777216.0f);
+        bool sel = fp.train_batch > 0 && (prev == 0u || (float)fp.train_batch > u * (float)prev);
+        unsigned slot = sel ? atomicAdd(&ctr->train_count, 1u) : 0u;
+        if (!sel || slot >= fp.train_cap) break;   // this path ends in the cache
+        float4* q = fp.train_q + 3 * (size_t)slot;
+        q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float((int)slot));
+        q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
+        q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
+        w = mk3(1.f, 1.f, 1.f);
+        pixel = ~(int)slot;   // traced on, with unit weight, into the training target
+      }
       if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
       if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
         for (int li = 0; li < sc.n_lights; ++li) {
@@ -693,6 +722,18 @@ __global__ void k_camera_rays(CamBasis cb, int W, int H, float* __restrict__ o, 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// Every field of a frame's parameters, with the radiance cache off.
+static FrameParams frame_defaults() {
+  FrameParams fp;
+  memset(&fp, 0, sizeof(fp));
+  fp.path_depth0 = 1;
+  fp.nrc_depth = -1;
+  fp.target = nullptr;
+  fp.infer_q = fp.train_q = nullptr;
+  fp.prev_hits = nullptr;
+  return fp;
+}
+
 static CamBasis camera_basis(const rt_camera* c, int W, int H) {
   // host FP32 arithmetic, once per frame
   CamBasis cb;
@@ -826,7 +867,7 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   DevScene sc = dev_scene(s, use_bvh);
   int64_t tcap = opt.traversal_cap > 0 ? opt.traversal_cap : 4 * std::max<int64_t>(s->n_nodes_total, 1) + 64;
   int cap = (int)std::min<int64_t>(tcap, 0x7fffffff);
-  FrameParams fp;
+  FrameParams fp = frame_defaults();
   fp.cam = camera_basis(cam, W, H);
   fp.W = W;
   fp.H = H;
@@ -847,12 +888,6 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   fp.ray_cap = (unsigned)qcap;
   fp.shadow_cap = (unsigned)pcap;
   fp.ctr = (Counters*)s->counters.p;
-  fp.path_depth0 = 1;
-  fp.nrc_depth = -1;
-  fp.target = nullptr;
-  fp.infer_q = fp.train_q = nullptr;
-  fp.infer_cap = fp.train_cap = fp.train_batch = 0;
-  fp.seed = 0;
   int T = -1;   // radiance-cache depth of this frame
   if (nrc) {
     NrcFrame nf;
@@ -881,9 +916,13 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);
   cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
   bool per_depth = (opt.flags & RT_FLAG_PER_DEPTH_WAVEFRONT) != 0;
-  // depths 0..last run as wavefronts; the rest run as depth-first paths
-  // (with the cache: up to its depth, then only the training rays go on)
-  int last = per_depth ? D : (T >= 0 ? T : 0);
+  // depths 0..last run as wavefronts; the rest run as depth-first paths,
+  // which meet the cache at depth T themselves unless it is depth 0
+  int last = per_depth ? D : (T == 0 ? 0 : 0);
+  bool cache_in_paths = !per_depth && T >= 1;
+  if (per_depth || T == 0) fp.path_depth0 = T >= 0 ? T + 1 : 1;
+  else fp.path_depth0 = 1;
+  if (cache_in_paths && fp.nrc_depth >= 0) fp.prev_hits = nrc_prev_hits(nrc);
   for (int depth = 0; depth <= last; ++depth) {
     // trace(depth) fills the shadow buffer that shadow(depth - 2) reads
     if (depth >= 2) cudaStreamWaitEvent(st, s->ev_shadowed[depth - 2], 0);
@@ -906,7 +945,7 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     cudaEventRecord(s->ev_shadowed[depth], s->side);
     launches += 2;
   }
-  if (T >= 0) {
+  if (T >= 0 && !cache_in_paths) {
     // cache lookups of the depth-T hits, beside the training rays' paths
     int slot = timing ? timing_begin(s, 2, s->side) : -1;
     rs = nrc_infer_launch(nrc, fp.infer_q, &fp.ctr->infer_count, fp.infer_cap, out, nullptr, s->status, s->side);
@@ -915,13 +954,21 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     cudaEventRecord(s->ev_shadowed[last], s->side);
     launches += 1;
   }
-  bool run_paths = !per_depth && D > last && (T < 0 || train);
+  bool run_paths = !per_depth && D >= fp.path_depth0 && (T < 0 || cache_in_paths || train);
   if (run_paths) {
     int slot = timing ? timing_begin(s, 0, st) : -1;
     if (count) k_paths<true><<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);
     else k_paths<false><<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);
     if (timing) timing_end(s, slot, st);
     launches += 1;
+  }
+  if (cache_in_paths) {
+    int slot = timing ? timing_begin(s, 2, st) : -1;
+    rs = nrc_infer_launch(nrc, fp.infer_q, &fp.ctr->infer_count, fp.infer_cap, out, nullptr, s->status, st);
+    if (rs) return rs;
+    if (timing) timing_end(s, slot, st);
+    nrc_keep_hits(nrc, &fp.ctr->cache_hits, st);
+    launches += 2;
   }
   cudaStreamWaitEvent(st, s->ev_shadowed[last], 0);
   if (T >= 0 && train) {
@@ -1002,11 +1049,9 @@ rt_status rt_render_host(rt_scene* s, const rt_camera* cam, int width, int heigh
 }
 
 rt_status rt_render_nrc(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int width, int height, int max_depth,
-                        float* out, int train, rt_render_stats* stats, void* stream) {
+                        float* out, int train, const rt_render_options* opt, rt_render_stats* stats, void* stream) {
   if (!nrc) return set_error(RT_ERR_INVALID_ARG, "rt_render_nrc: cache is NULL");
-  rt_render_options opt;
-  rt_render_options_default(&opt);
-  return render_impl(s, cam, width, height, max_depth, out, &opt, nullptr, nullptr, stats, (cudaStream_t)stream, nrc,
+  return render_impl(s, cam, width, height, max_depth, out, opt, nullptr, nullptr, stats, (cudaStream_t)stream, nrc,
                      train);
 }
 
@@ -1144,7 +1189,7 @@ extern "C" rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int W,
   if (rs) return rs;
   occupancy(s);
   char* p = (char*)base;
-  FrameParams fp;
+  FrameParams fp = frame_defaults();
   fp.cam = camera_basis(cam, W, H);
   fp.W = W;
   fp.H = H;

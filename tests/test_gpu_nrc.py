@@ -145,3 +145,98 @@ def test_nrc_training_reduces_loss():
     assert losses[-1] < 0.2 * losses[0], losses[::10]
     rtb.rt_nrc_destroy(nrc)
     scene.close()
+
+
+def _gpu_bbox32(sc):
+    lo, hi = _bbox(sc)
+    lo32, hi32 = lo.astype(np.float32), hi.astype(np.float32)
+    return lo32.astype(np.float64), (np.float32(1.0) / (hi32 - lo32)).astype(np.float64)
+
+
+def _render_nrc(scene, nrc, sc, train, flags=0):
+    W, H = sc.width, sc.height
+    out = torch.full((W * H * 3,), float("nan"), device="cuda")
+    st = rtb.rt_render_nrc(scene.handle, nrc, sc.camera, W, H, sc.max_depth, out, train=train,
+                           options=rtb.make_options(background=sc.background, flags=flags), stats=True)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    return out.view(-1, 3).double().cpu().numpy(), st
+
+
+@pytest.mark.parametrize("flags", [0, rtb.RT_FLAG_PER_DEPTH_WAVEFRONT])
+def test_cached_frame_matches_oracle(flags):
+    """rt_render_nrc without training: hits at depth 2 read the cache; the
+    oracle terminates the same hits with the same (BF16) network.  Both
+    pipeline modes (depth-first paths, per-depth wavefronts)."""
+    from gpu_helpers import compare
+    sc, scene = _scene()
+    sc.background = (0.1, 0.1, 0.1)
+    nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=11))
+    # a few training steps so that the cache's answers vary over the scene
+    rng = np.random.default_rng(4)
+    pnv = _samples(sc, 2048, rng)
+    tgt = (0.2 + 0.1 * np.cos(pnv[:, :3])).astype(np.float32)
+    for _ in range(5):
+        rtb.rt_nrc_train_step(nrc, scene.handle, torch.from_numpy(pnv).cuda(), torch.from_numpy(tgt).cuda(), 2048)
+    params = rtb.rt_nrc_get_params(nrc)
+    img, st = _render_nrc(scene, nrc, sc, train=False, flags=flags)
+    orc = O.OracleScene.from_scene(sc)
+    lo, inv = _gpu_bbox32(sc)
+    orc.set_cache(2, params, lo, inv, bf16=True)
+    ref = orc.render(sc.camera, sc.width, sc.height, sc.max_depth, mode="brute")
+    g = {"rgb": img, "prim": ref["prim"], "t": ref["t"]}   # primary AOVs are checked elsewhere
+    compare(g, ref, budget=5e-3)
+    c = ref["counts"]
+    assert st["primary"] == c["primary"]
+    assert abs(st["shadow"] - c["shadow"]) <= 1e-3 * c["shadow"] + 4
+    assert st["rays_per_depth"][:3] == c["rays_per_depth"][:3] or \
+        np.abs(np.array(st["rays_per_depth"][:3]) - np.array(c["rays_per_depth"][:3])).max() <= 4
+    assert sum(st["rays_per_depth"][3:]) == 0            # nothing is traced past the cache
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()
+
+
+def _relmse(x, r):
+    return float(np.mean((x - r) ** 2 / (r ** 2 + 0.01)))
+
+
+def test_trained_cache_beats_truncation():
+    """Online training on the tracer's own depth-2 radiance: after a few
+    dozen frames the cached image is closer to the full-depth trace than
+    the trace truncated at depth 2 is."""
+    sc = S.scene_terrain(seed=2, width=192, height=108, max_depth=5)
+    scene = rtb.Scene(sc).build()
+    W, H = sc.width, sc.height
+    full = torch.empty(W * H * 3, device="cuda")
+    rtb.rt_render(scene.handle, sc.camera, W, H, 5, full)
+    trunc = torch.empty(W * H * 3, device="cuda")
+    rtb.rt_render(scene.handle, sc.camera, W, H, 2, trunc)
+    full = full.view(-1, 3).double().cpu().numpy()
+    trunc = trunc.view(-1, 3).double().cpu().numpy()
+    nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=1))
+    for _ in range(64):
+        _render_nrc(scene, nrc, sc, train=True)
+    img, st = _render_nrc(scene, nrc, sc, train=False)
+    e_cache, e_trunc = _relmse(img, full), _relmse(trunc, full)
+    print(f"relMSE cache {e_cache:.3e}, truncated {e_trunc:.3e}")
+    assert np.isfinite(img).all()
+    assert e_cache < e_trunc
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()
+
+
+@pytest.mark.parametrize("flags", [0, rtb.RT_FLAG_PER_DEPTH_WAVEFRONT])
+def test_training_frame_image_and_rays(flags):
+    """A training frame shows the same cached image as an inference-only
+    frame (training rays write targets, not pixels) and traces the
+    training rays to full depth."""
+    sc, scene = _scene()
+    nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=13))
+    a, sa = _render_nrc(scene, nrc, sc, train=False, flags=flags)
+    b, sb = _render_nrc(scene, nrc, sc, train=True, flags=flags)
+    np.testing.assert_allclose(a, b, atol=1e-5)
+    assert sum(sa["rays_per_depth"][3:]) == 0
+    assert sum(sb["rays_per_depth"][3:]) > 0 or sb["hits_per_depth"][2] == 0
+    p1 = rtb.rt_nrc_get_params(nrc)
+    assert np.isfinite(p1).all()
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()

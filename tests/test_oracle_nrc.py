@@ -132,3 +132,34 @@ def test_bf16_activation_rounding_option():
     assert y[0, 0] == pytest.approx(math.exp(1.0), rel=1e-15)
     y = O.mlp_forward(x, W, np.zeros(O.N_B), bf16_acts=False)
     assert y[0, 0] == pytest.approx(math.exp(1.0 + 2.0 ** -10), rel=1e-15)
+
+
+def test_cached_frame_closed_form():
+    # A constant cache (all weights 0, output bias log c) at depth 1: a
+    # primary hit on a rho = 1 mirror with no lights is exactly c wherever
+    # its reflection meets a surface, and the background where it does not.
+    from paper_1504_03151_b300 import scenes as S
+    big = 50.0
+    plane = S.triangles_from([(-big, 0, -big), (-big, 0, -big)], [(-big, 0, big), (big, 0, big)],
+                             [(big, 0, big), (big, 0, -big)], 0)
+    sph = S.spheres_from([(0.0, 1.5, -1.0)], [1.0], [1])
+    mats = np.concatenate([S.material(S.MAT_MIRROR, (0.5, 0.5, 0.5), reflectivity=1.0),
+                           S.material(S.MAT_DIFFUSE, (0.8, 0.3, 0.2))])
+    cam = S.camera((0, 4, 6), (0, 0, -2))
+    orc = O.OracleScene(sph, plane, mats, np.zeros(0, S.LIGHT_DTYPE), background=(0.1, 0.2, 0.3))
+    c = np.array([0.25, 0.5, 2.0])
+    params = np.zeros(O.N_W + O.N_B)
+    params[O.N_W + O.N_B - 3:] = np.log(c)
+    plain = orc.render(cam, 40, 30, 3, mode="brute")
+    orc.set_cache(1, params, lo=np.zeros(3), inv_ext=np.ones(3), bf16=False)
+    cached = orc.render(cam, 40, 30, 3, mode="brute")
+    it = orc.render(cam, 40, 30, 3, mode="iterative")
+    np.testing.assert_allclose(cached["rgb"], it["rgb"], atol=1e-14)
+    on_mirror = plain["prim"] >= 1
+    # the reflected ray's fate: hit -> c, miss -> background
+    reflected_hit = on_mirror & (np.abs(plain["rgb"] - np.array([0.1, 0.2, 0.3])).max(1) > 1e-12)
+    np.testing.assert_allclose(cached["rgb"][reflected_hit], np.tile(c, (reflected_hit.sum(), 1)), atol=1e-14)
+    assert reflected_hit.sum() > 20
+    assert cached["counts"]["shadow"] == 0
+    orc.clear_cache()
+    np.testing.assert_array_equal(orc.render(cam, 40, 30, 3, mode="brute")["rgb"], plain["rgb"])
