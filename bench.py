@@ -166,6 +166,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--per-depth", action="store_true", help="queue every depth (no depth-first secondary paths)")
+    ap.add_argument("--no-nrc", action="store_true", help="skip the radiance-cache leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -268,6 +269,52 @@ def main():
     achieved = ops / (kms * 1e-3) / 1e12
     launches_per_step = info["build_launches"] + 1 + 2 + st["launches"] + 2
 
+    # radiance cache: online training frames, then timed training frames;
+    # its Mrays-equivalent = rays the full-depth frame traces / cached step time
+    nrc_line = None
+    if not args.no_nrc:
+        full = torch.empty_like(out)
+        rtb.rt_render_ex(h, sc.camera, W, H, D, full, opts)
+        nrc = rtb.rt_nrc_create(h, rtb.rt_nrc_config_default(seed=1))
+        nrc_out = torch.empty_like(out)
+
+        def nrc_step(stats=False):
+            rtb.rt_scene_update(h, None, tri_dev)
+            rtb.rt_bvh_build(h)
+            return rtb.rt_render_nrc(h, nrc, sc.camera, W, H, D, nrc_out, train=True, options=opts, stats=stats)
+
+        for _ in range(64):
+            nrc_step()
+        nst = nrc_step(stats=True)
+        torch.cuda.synchronize()
+        nev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            nev[k][0].record(stream)
+            nrc_step()
+            nev[k][1].record(stream)
+        torch.cuda.synchronize()
+        nrc_ms = sum(a.elapsed_time(b) for a, b in nev) / args.steps
+        if dist:
+            t = torch.tensor([nrc_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            nrc_ms = float(t.item())
+        x, r = nrc_out.double(), full.double()
+        relmse = float(((x - r) ** 2 / (r ** 2 + 0.01)).mean())
+        mse01 = float(((x.clamp(0, 1) - r.clamp(0, 1)) ** 2).mean())
+        nrc_value = world * rays / (nrc_ms * 1e3)
+        nrc_line = {
+            "metric": "Mrays-equivalent/s (full-depth rays per cached step)", "value": nrc_value,
+            "ms_per_step": nrc_ms, "vs_plain": nrc_value / value, "relmse_vs_full_depth": relmse,
+            "psnr_db": 10 * np.log10(1.0 / max(mse01, 1e-30)), "warmup_frames": 64,
+            "train_batch": 65536, "cache_depth": 2,
+            "rays_traced_per_step": nst["primary"] + nst["shadow"] + nst["secondary"],
+            "cache_hits": nst["hits_per_depth"][2],
+            "step": "repack + BVH build + cached frame (inference) + training rays + one Adam step",
+        }
+        rtb.rt_nrc_destroy(nrc)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, cores = cpu_oracle_sample(sc)
@@ -301,6 +348,8 @@ def main():
         }
         if cpu:
             line["cpu_baseline"] = cpu
+        if nrc_line:
+            line["radiance_cache"] = nrc_line
         print(json.dumps(line), flush=True)
     scene.close()
     if dist:
