@@ -1,6 +1,7 @@
 // bvh.cu - on-device BVH build: Morton codes, radix sort, LBVH hierarchy,
 // bottom-up boxes with SAH costs, binned-SAH rebuild of the top levels over
 // Morton clusters, SAH leaf collapsing, traversal layout.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,6 +11,8 @@
 #include <vector>
 
 #include "rtb_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rtb {
 
@@ -530,13 +533,13 @@ __device__ __forceinline__ int bin_of(float c, float lo, float ext) {
 // stable partition of the cluster ids, then the two children are emitted:
 // a single cluster becomes a direct link, anything larger a new top node
 // (and a segment of the next level).
-__global__ void __launch_bounds__(256) k_top_level(int level, int top_base, const int* __restrict__ seg_count,
-                                                   const int4* __restrict__ seg_in, int4* __restrict__ seg_out,
-                                                   int* __restrict__ seg_count_out, const int* __restrict__ ids_in,
-                                                   int* __restrict__ ids_out, const int* __restrict__ clu_link,
-                                                   const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
-                                                   int* __restrict__ top_count, float4* __restrict__ nodes,
-                                                   BuildInfo* __restrict__ info) {
+// seg_in / ids_in were written by the previous level (possibly by other
+// blocks of the same launch): they are read through L2 (__ldcg).
+__device__ __forceinline__ void top_level_body(int level, int top_base, const int* seg_count, const int4* seg_in,
+                                               int4* seg_out, int* seg_count_out, const int* ids_in, int* ids_out,
+                                               const int* __restrict__ clu_link, const float4* __restrict__ clu_lo,
+                                               const float4* __restrict__ clu_hi, int* top_count, float4* nodes,
+                                               BuildInfo* info) {
   __shared__ int s_cb[6];
   __shared__ int bin_count[3][kTopBins];
   __shared__ int bin_lo[3][kTopBins][3], bin_hi[3][kTopBins][3];
@@ -544,10 +547,10 @@ __global__ void __launch_bounds__(256) k_top_level(int level, int top_base, cons
   __shared__ int s_split_axis, s_split_bin;
   __shared__ int s_wcount[8];
   __shared__ int s_box[2][6];
-  int nseg = seg_count[level];
+  int nseg = __ldcg(&seg_count[level]);
   int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (int sidx = blockIdx.x; sidx < nseg; sidx += gridDim.x) {
-    int4 sg = seg_in[sidx];
+    int4 sg = __ldcg(&seg_in[sidx]);
     int b = sg.x, e = sg.y, node = sg.w;
     int m = e - b;
     if (t < 6) {
@@ -567,7 +570,7 @@ __global__ void __launch_bounds__(256) k_top_level(int level, int top_base, cons
     // centroid bounds of the segment
     float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int k = b + t; k < e; k += 256) {
-      int c = ids_in[k];
+      int c = __ldcg(&ids_in[k]);
       float4 lo = clu_lo[c], hi = clu_hi[c];
       float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
       for (int a = 0; a < 3; ++a) {
@@ -586,7 +589,7 @@ __global__ void __launch_bounds__(256) k_top_level(int level, int top_base, cons
     float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
     // bin every axis
     for (int k = b + t; k < e; k += 256) {
-      int c = ids_in[k];
+      int c = __ldcg(&ids_in[k]);
       float4 lo = clu_lo[c], hi = clu_hi[c];
       float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
       float lo3[3] = {lo.x, lo.y, lo.z}, hi3[3] = {hi.x, hi.y, hi.z};
@@ -654,13 +657,13 @@ __global__ void __launch_bounds__(256) k_top_level(int level, int top_base, cons
     // right side descending from e-1, then the right side is reversed
     int nleft = m / 2;
     if (ax < 0) {
-      for (int k = b + t; k < e; k += 256) ids_out[k] = ids_in[k];
+      for (int k = b + t; k < e; k += 256) ids_out[k] = __ldcg(&ids_in[k]);
     } else {
       int run_l = 0, run_r = 0;
       for (int k0 = b; k0 < e; k0 += 256) {
         int k = k0 + t;
         bool valid = k < e;
-        int c = valid ? ids_in[k] : 0;
+        int c = valid ? __ldcg(&ids_in[k]) : 0;
         bool left = false;
         if (valid) {
           float4 lo = clu_lo[c], hi = clu_hi[c];
@@ -698,7 +701,7 @@ __global__ void __launch_bounds__(256) k_top_level(int level, int top_base, cons
       }
       if (nleft == 0 || nleft == m) {   // not reachable with a finite SAH cost; keep a valid split
         __syncthreads();
-        for (int k = b + t; k < e; k += 256) ids_out[k] = ids_in[k];
+        for (int k = b + t; k < e; k += 256) ids_out[k] = __ldcg(&ids_in[k]);
         nleft = m / 2;
       }
     }
@@ -748,6 +751,32 @@ __global__ void __launch_bounds__(256) k_top_level(int level, int top_base, cons
       write_child(nodes, top_base + node, t, lo, hi, link);
     }
     __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_top_level(int level, int top_base, const int* seg_count, const int4* seg_in,
+                                                   int4* seg_out, int* seg_count_out, const int* ids_in, int* ids_out,
+                                                   const int* __restrict__ clu_link,
+                                                   const float4* __restrict__ clu_lo,
+                                                   const float4* __restrict__ clu_hi, int* top_count, float4* nodes,
+                                                   BuildInfo* info) {
+  top_level_body(level, top_base, seg_count, seg_in, seg_out, seg_count_out, ids_in, ids_out, clu_link, clu_lo, clu_hi,
+                 top_count, nodes, info);
+}
+
+// Every level in one cooperative launch: the blocks meet at a grid-wide
+// barrier between levels and stop at the first level without segments.
+__global__ void __launch_bounds__(256) k_top_all(int top_base, int* seg_count, int4* seg_a, int4* seg_b, int* clu_a,
+                                                 int* clu_b, const int* __restrict__ clu_link,
+                                                 const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
+                                                 int* top_count, float4* nodes, BuildInfo* info) {
+  cg::grid_group grid = cg::this_grid();
+  for (int level = 0; level < kTopMaxLevels; ++level) {
+    if (__ldcg(&seg_count[level]) == 0) break;   // the same value in every block after the barrier
+    bool odd = level & 1;
+    top_level_body(level, top_base, seg_count, odd ? seg_b : seg_a, odd ? seg_a : seg_b, seg_count + level + 1,
+                   odd ? clu_b : clu_a, odd ? clu_a : clu_b, clu_link, clu_lo, clu_hi, top_count, nodes, info);
+    grid.sync();
   }
 }
 
@@ -989,7 +1018,23 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
                                          b.aabb_hi, n_clusters_dev, b.clu_a, b.clu_link, b.clu_lo, b.clu_hi);
     k_top_init<<<1, 32, 0, st>>>(b.seg_count, b.seg_a, n_clusters_dev, b.top_count, b.info);
     int top_grid = std::max(1, 2 * s->sm_count);
-    for (int level = 0; level < kTopMaxLevels; ++level) {
+    static int coop_blocks = -1;
+    if (coop_blocks < 0) {
+      int coop = 0, per_sm = 0;
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_top_all, 256, 0);
+      coop_blocks = coop ? std::min(per_sm, 2) * s->sm_count : 0;
+    }
+    bool launched = false;
+    if (coop_blocks > 0) {
+      int tb_ = top_base;
+      void* args[] = {&tb_, &b.seg_count, &b.seg_a, &b.seg_b, &b.clu_a, &b.clu_b, &b.clu_link,
+                      &b.clu_lo, &b.clu_hi, &b.top_count, &nodes, &b.info};
+      launched = cudaLaunchCooperativeKernel((void*)k_top_all, coop_blocks, 256, args, 0, st) == cudaSuccess;
+      if (!launched) cudaGetLastError();
+      L += launched ? 1 - kTopMaxLevels : 0;
+    }
+    for (int level = 0; !launched && level < kTopMaxLevels; ++level) {
       bool odd = level & 1;
       k_top_level<<<top_grid, 256, 0, st>>>(level, top_base, b.seg_count, odd ? b.seg_b : b.seg_a,
                                             odd ? b.seg_a : b.seg_b, b.seg_count + level + 1,

@@ -538,11 +538,6 @@ __global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FramePara
 // launches of depths >= 1, whose few rays would otherwise make every depth
 // as slow as its slowest ray.
 // ---------------------------------------------------------------------------
-struct Pending {
-  f3 o, d, w;
-  int depth;
-};
-
 template <bool kCount>
 __device__ __forceinline__ void count_ray(Counters* ctr, int cls, int depth, unsigned v, unsigned t) {
   if (!kCount) return;
@@ -551,123 +546,195 @@ __device__ __forceinline__ void count_ray(Counters* ctr, int cls, int depth, uns
   atomicMax(&ctr->max_visits[cls][depth], v);
 }
 
+constexpr int kWarpPending = 64;   // pending children per warp (shared memory, 12 KB a block)
+
 template <bool kCount>
 __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParams fp, int cap) {
   __shared__ int s_stack[kStackSize * kTraceThreads];
   __shared__ unsigned s_cnt[3][RT_MAX_DEPTH + 2];   // rays spawned for / shadow rays cast at / hits at depth d
+  __shared__ float4 s_pend[kTraceThreads / 32][kWarpPending][3];   // (o, pixel) (d, depth) (w, -)
+  __shared__ int s_np[kTraceThreads / 32];
   int* stack = s_stack + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   for (int i = threadIdx.x; i < 3 * (RT_MAX_DEPTH + 2); i += blockDim.x) (&s_cnt[0][0])[i] = 0u;
+  if (lane == 0) s_np[warp] = 0;
   __syncthreads();
   Counters* ctr = fp.ctr;
   const int d0 = fp.path_depth0;
-  unsigned n_items = min(ctr->rays[d0], fp.ray_cap);
+  const unsigned n_items = min(ctr->rays[d0], fp.ray_cap);
   const float4* __restrict__ qin = fp.rayq[d0 & 1];
   const f3 bg = mk3(fp.bg_r, fp.bg_g, fp.bg_b);
-  Pending pend[RT_MAX_DEPTH];
-  int np = 0;
+  // overflow of this lane when the warp's pending stack is full (depth first: <= max depth entries)
+  float4 local[RT_MAX_DEPTH][3];
+  int nl = 0;
+  bool queue_done = false;
+  bool have = false;
   WorkCount wc = {0u, 0u, 0u};
   f3 o = mk3(0, 0, 0), d = mk3(0, 0, 1), w = mk3(0, 0, 0);
   int depth = d0, pixel = 0;
   for (;;) {
-    if (np > 0) {
-      --np;
-      o = pend[np].o;
-      d = pend[np].d;
-      w = pend[np].w;
-      depth = pend[np].depth;
-    } else {
-      unsigned idx = atomicAdd(&ctr->fetch_trace[d0], 1u);
-      if (idx >= n_items) break;
-      float4 q0 = qin[3 * (size_t)idx], q1 = qin[3 * (size_t)idx + 1], q2 = qin[3 * (size_t)idx + 2];
-      o = xyz(q0);
-      pixel = __float_as_int(q0.w);
-      d = xyz(q1);
-      w = xyz(q2);
-      depth = d0;
+    // --- refill lanes without a ray: own overflow, warp stack, global queue
+    if (!have && nl > 0) {
+      --nl;
+      o = xyz(local[nl][0]);
+      pixel = __float_as_int(local[nl][0].w);
+      d = xyz(local[nl][1]);
+      depth = __float_as_int(local[nl][1].w);
+      w = xyz(local[nl][2]);
+      have = true;
     }
-    // follow this ray and, at each hit, one of its children; the other
-    // child waits on the thread's own stack
-    for (;;) {
+    unsigned need = __ballot_sync(kFull, !have);
+    int np = s_np[warp];
+    if (need && np > 0) {
+      int take = min(__popc(need), np);
+      int rank = __popc(need & lt);
+      if (!have && rank < take) {
+        const float4* r = s_pend[warp][np - 1 - rank];
+        o = xyz(r[0]);
+        pixel = __float_as_int(r[0].w);
+        d = xyz(r[1]);
+        depth = __float_as_int(r[1].w);
+        w = xyz(r[2]);
+        have = true;
+      }
+      __syncwarp();
+      if (lane == 0) s_np[warp] = np - take;
+      __syncwarp();
+      need = __ballot_sync(kFull, !have);
+    }
+    if (need && !queue_done) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(&ctr->fetch_trace[d0], (unsigned)__popc(need));
+      base = __shfl_sync(kFull, base, 0);
+      unsigned idx = base + (unsigned)__popc(need & lt);
+      if (base + (unsigned)__popc(need) >= n_items) queue_done = true;
+      if (!have && idx < n_items) {
+        float4 q0 = qin[3 * (size_t)idx], q1 = qin[3 * (size_t)idx + 1], q2 = qin[3 * (size_t)idx + 2];
+        o = xyz(q0);
+        pixel = __float_as_int(q0.w);
+        d = xyz(q1);
+        w = xyz(q2);
+        depth = d0;
+        have = true;
+      }
+    }
+    if (!__any_sync(kFull, have)) break;   // nothing left for this warp
+    // --- one segment per lane: closest hit, shading, shadow rays, children
+    Children ch;
+    ch.want_r = ch.want_t = false;
+    if (have) {
       float t = INFINITY;
       bool fail = false;
       unsigned v0 = wc.visits, t0 = wc.tests;
       int hit = traverse<false, kCount>(sc, make_ray(o, d), 0.0f, t, stack, cap, fail, wc);
       count_ray<kCount>(ctr, 0, depth, wc.visits - v0, wc.tests - t0);
       if (fail) atomicOr(sc.status, kErrTraversalLimit);
-      if (hit < 0) {
-        add_fb(fp, pixel, w * bg);
-        break;
+      bool live = hit >= 0;
+      if (!live) add_fb(fp, pixel, w * bg);
+      Surface sf;
+      if (live) {
+        atomicAdd(&s_cnt[2][depth], 1u);
+        sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
+        if (depth == fp.nrc_depth) {
+          // radiance cache (as in k_trace); the selection probability comes
+          // from the previous frame's number of cache hits
+          atomicAdd(&ctr->cache_hits, 1u);
+          unsigned pos = atomicAdd(&ctr->infer_count, 1u);
+          if (pos < fp.infer_cap) {
+            float4* q = fp.infer_q + 4 * (size_t)pos;
+            q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float(pixel));
+            q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
+            q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
+            q[3] = make_float4(w.x, w.y, w.z, 0.f);
+          } else {
+            atomicOr(sc.status, kErrQueueOverflow);
+          }
+          unsigned prev = fp.prev_hits ? *fp.prev_hits : 0u;
+          float u = (float)(hash32(fp.seed ^ hash32((uint32_t)pixel * 0x9E3779B9u ^ __float_as_uint(d.x))) >> 8) *
+                    (1.0f / 16777216.0f);
+          bool sel = fp.train_batch > 0 && (prev == 0u || (float)fp.train_batch > u * (float)prev);
+          unsigned slot = sel ? atomicAdd(&ctr->train_count, 1u) : 0u;
+          if (sel && slot < fp.train_cap) {
+            float4* q = fp.train_q + 3 * (size_t)slot;
+            q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float((int)slot));
+            q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
+            q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
+            w = mk3(1.f, 1.f, 1.f);
+            pixel = ~(int)slot;   // traced on, with unit weight, into the training target
+          } else {
+            live = false;          // this path ends in the cache
+          }
+        }
       }
-      atomicAdd(&s_cnt[2][depth], 1u);
-      Surface sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
-      if (depth == fp.nrc_depth) {
-        // radiance cache (as in k_trace); the selection probability comes
-        // from the previous frame's number of cache hits
-        atomicAdd(&ctr->cache_hits, 1u);
-        unsigned pos = atomicAdd(&ctr->infer_count, 1u);
-        if (pos < fp.infer_cap) {
-          float4* q = fp.infer_q + 4 * (size_t)pos;
-          q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float(pixel));
-          q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
-          q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
-          q[3] = make_float4(w.x, w.y, w.z, 0.f);
+      if (live) {
+        if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
+        if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
+          for (int li = 0; li < sc.n_lights; ++li) {
+            f3 contrib, os, sd;
+            float tmax;
+            if (!light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd,
+                            tmax))
+              continue;
+            atomicAdd(&s_cnt[1][depth], 1u);
+            bool sfail = false;
+            unsigned sv0 = wc.visits, st0 = wc.tests;
+            int h = traverse<true, kCount>(sc, make_ray(os, sd), 0.0f, tmax, stack, cap, sfail, wc);
+            count_ray<kCount>(ctr, 1, depth, wc.visits - sv0, wc.tests - st0);
+            if (sfail) atomicOr(sc.status, kErrTraversalLimit);
+            if (h < 0 && !sfail) add_fb(fp, pixel, contrib);
+          }
+        }
+        if (depth < fp.max_depth) {
+          ch = children_of(sf, d, w);
+          if (ch.want_r || ch.want_t) atomicAdd(&s_cnt[0][depth + 1], (unsigned)ch.want_r + (unsigned)ch.want_t);
+        }
+      }
+    }
+    // --- a second child goes to the warp's stack (or this lane's overflow)
+    bool two = have && ch.want_r && ch.want_t;
+    unsigned m2 = __ballot_sync(kFull, two);
+    if (m2) {
+      int np2 = s_np[warp];
+      int room = kWarpPending - np2;
+      int rank = __popc(m2 & lt);
+      float4 r0 = make_float4(ch.or_.x, ch.or_.y, ch.or_.z, __int_as_float(pixel));
+      float4 r1 = make_float4(ch.dr.x, ch.dr.y, ch.dr.z, __int_as_float(depth + 1));
+      float4 r2 = make_float4(ch.wr.x, ch.wr.y, ch.wr.z, 0.f);
+      if (two) {
+        if (rank < room) {
+          float4* r = s_pend[warp][np2 + rank];
+          r[0] = r0;
+          r[1] = r1;
+          r[2] = r2;
+        } else if (nl < RT_MAX_DEPTH) {
+          local[nl][0] = r0;
+          local[nl][1] = r1;
+          local[nl][2] = r2;
+          ++nl;
         } else {
-          atomicOr(sc.status, kErrQueueOverflow);
-        }
-        unsigned prev = fp.prev_hits ? *fp.prev_hits : 0u;
-        float u = (float)(hash32(fp.seed ^ hash32((uint32_t)pixel * 0x9E3779B9u ^ __float_as_uint(d.x))) >> 8) *
-                  (1.0f / 16777216.0f);
-        bool sel = fp.train_batch > 0 && (prev == 0u || (float)fp.train_batch > u * (float)prev);
-        unsigned slot = sel ? atomicAdd(&ctr->train_count, 1u) : 0u;
-        if (!sel || slot >= fp.train_cap) break;   // this path ends in the cache
-        float4* q = fp.train_q + 3 * (size_t)slot;
-        q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float((int)slot));
-        q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
-        q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
-        w = mk3(1.f, 1.f, 1.f);
-        pixel = ~(int)slot;   // traced on, with unit weight, into the training target
-      }
-      if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
-      if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
-        for (int li = 0; li < sc.n_lights; ++li) {
-          f3 contrib, os, sd;
-          float tmax;
-          if (!light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd, tmax))
-            continue;
-          atomicAdd(&s_cnt[1][depth], 1u);
-          bool sfail = false;
-          unsigned sv0 = wc.visits, st0 = wc.tests;
-          int h = traverse<true, kCount>(sc, make_ray(os, sd), 0.0f, tmax, stack, cap, sfail, wc);
-          count_ray<kCount>(ctr, 1, depth, wc.visits - sv0, wc.tests - st0);
-          if (sfail) atomicOr(sc.status, kErrTraversalLimit);
-          if (h < 0 && !sfail) add_fb(fp, pixel, contrib);
+          atomicOr(sc.status, kErrQueueOverflow);   // not reachable for depth <= 16
         }
       }
-      if (depth >= fp.max_depth) break;
-      Children ch = children_of(sf, d, w);
-      if (!ch.want_r && !ch.want_t) break;
-      atomicAdd(&s_cnt[0][depth + 1], (unsigned)ch.want_r + (unsigned)ch.want_t);
-      if (ch.want_r && ch.want_t) {
-        if (np < RT_MAX_DEPTH) {
-          pend[np].o = ch.or_;
-          pend[np].d = ch.dr;
-          pend[np].w = ch.wr;
-          pend[np].depth = depth + 1;
-          ++np;
-        } else {
-          atomicOr(sc.status, kErrQueueOverflow);   // deeper than the stack holds: cannot happen for depth <= 16
-        }
-      }
+      __syncwarp();
+      if (lane == 0) s_np[warp] = np2 + min(__popc(m2), room);
+      __syncwarp();
+    }
+    // --- this lane follows its (other) child, or is free for new work
+    if (have) {
       if (ch.want_t) {
         o = ch.ot;
         d = ch.dt;
         w = ch.wt;
-      } else {
+        ++depth;
+      } else if (ch.want_r) {
         o = ch.or_;
         d = ch.dr;
         w = ch.wr;
+        ++depth;
+      } else {
+        have = false;
       }
-      ++depth;
     }
   }
   __syncthreads();

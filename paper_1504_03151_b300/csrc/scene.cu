@@ -8,6 +8,7 @@
 #include <cstring>
 #include <string>
 
+#include "nrc_internal.cuh"
 #include "rtb_internal.cuh"
 
 namespace rtb {
@@ -261,6 +262,7 @@ rt_status rt_scene_sync(rt_scene* s, void* stream) {
     if (flags & kErrQueueOverflow)
       return set_error(RT_ERR_QUEUE_OVERFLOW, "a ray queue overflowed; rays were dropped (raise queue_capacity)");
     if (flags & kErrBadTree) return set_error(RT_ERR_CUDA, "traversal met a link outside the BVH arrays");
+    if (flags & kErrNrcTimeout) return set_error(RT_ERR_CUDA, "a radiance-cache tensor-core wait timed out");
     if (flags & kErrTraversalLimit)
       return set_error(RT_ERR_TRAVERSAL_LIMIT, "a ray reached the traversal step cap or the stack depth");
   }
