@@ -136,8 +136,16 @@ __device__ __forceinline__ bool leaf_hits(const float4* __restrict__ prims, int 
   return false;
 }
 
-// BVH traversal with a per-thread stack in shared memory (column
-// `stack[i * kTraceThreads]`).  Near child first; the far one is pushed.
+__device__ __forceinline__ int pop_stack(const int* stack, const int* deep, int& sp) {
+  if (sp == 0) return kSentinelLink;
+  --sp;
+  return sp < kStackShared ? stack[sp * kTraceThreads] : deep[sp - kStackShared];
+}
+
+// BVH traversal with a per-thread stack: its first kStackShared entries
+// live in shared memory (column `stack[i * kTraceThreads]`), deeper ones in
+// local memory, which leaves most of L1 to nodes and primitives.  Near
+// child first; the far one is pushed.
 // Returns the hit record index (leaf order) or -1.  Sets *fail when the
 // step cap or the stack depth is exceeded (the ray then counts as a miss).
 template <bool kAny, bool kCount>
@@ -153,6 +161,7 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
   int node = sc.root;
   int steps = 0;
   const float4* __restrict__ nodes = sc.nodes;
+  int deep[kStackSize - kStackShared > 0 ? kStackSize - kStackShared : 1];   // entries below the shared part
   for (;;) {
     // inner nodes
     while (node >= 0) {
@@ -187,7 +196,8 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
           fail = true;
           return kAny ? -1 : best;
         }
-        stack[sp * kTraceThreads] = farc;
+        if (sp < kStackShared) stack[sp * kTraceThreads] = farc;
+        else deep[sp - kStackShared] = farc;
         ++sp;
         node = nearc;
       } else if (h0) {
@@ -195,7 +205,7 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
       } else if (h1) {
         node = l1;
       } else {
-        node = sp > 0 ? stack[--sp * kTraceThreads] : kSentinelLink;
+        node = pop_stack(stack, deep, sp);
       }
     }
     if (node == kSentinelLink) break;
@@ -208,7 +218,7 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
         return -1;
       }
       if (leaf_hits<kAny, kCount>(sc.prims, ls, lc, r, tmin, tbest, best, best_id, wc)) return best;
-      node = sp > 0 ? stack[--sp * kTraceThreads] : kSentinelLink;
+      node = pop_stack(stack, deep, sp);
     }
     if (node == kSentinelLink) break;
   }
@@ -380,7 +390,7 @@ __device__ __forceinline__ Children children_of(const Surface& sf, f3 d, f3 w) {
 // ---------------------------------------------------------------------------
 template <bool kPrimary, bool kCount>
 __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(DevScene sc, FrameParams fp, int depth, int cap) {
-  __shared__ int s_stack[kStackSize * kTraceThreads];
+  __shared__ int s_stack[kStackShared * kTraceThreads];
   int* stack = s_stack + threadIdx.x;
   int lane = threadIdx.x & 31;
   Counters* ctr = fp.ctr;
@@ -503,7 +513,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(DevScene sc, FramePa
 // ---------------------------------------------------------------------------
 template <bool kCount>
 __global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FrameParams fp, int depth, int cap) {
-  __shared__ int s_stack[kStackSize * kTraceThreads];
+  __shared__ int s_stack[kStackShared * kTraceThreads];
   int* stack = s_stack + threadIdx.x;
   int lane = threadIdx.x & 31;
   Counters* ctr = fp.ctr;
@@ -550,7 +560,7 @@ constexpr int kWarpPending = 64;   // pending children per warp (shared memory, 
 
 template <bool kCount>
 __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParams fp, int cap) {
-  __shared__ int s_stack[kStackSize * kTraceThreads];
+  __shared__ int s_stack[kStackShared * kTraceThreads];
   __shared__ unsigned s_cnt[3][RT_MAX_DEPTH + 2];   // rays spawned for / shadow rays cast at / hits at depth d
   __shared__ float4 s_pend[kTraceThreads / 32][kWarpPending][3];   // (o, pixel) (d, depth) (w, -)
   __shared__ int s_np[kTraceThreads / 32];
@@ -753,7 +763,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_query(DevScene sc, const floa
                                                          int64_t n, float tmin, int any, int cap,
                                                          int32_t* __restrict__ prim_out, float* __restrict__ t_out,
                                                          uint8_t* __restrict__ occ_out) {
-  __shared__ int s_stack[kStackSize * kTraceThreads];
+  __shared__ int s_stack[kStackShared * kTraceThreads];
   int* stack = s_stack + threadIdx.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;

@@ -15,7 +15,11 @@ namespace rtb {
 // ---------------------------------------------------------------------------
 // Tunables
 // ---------------------------------------------------------------------------
-constexpr int kStackSize = 64;       // traversal stack entries per thread (shared memory)
+constexpr int kStackSize = 64;       // traversal stack entries per thread
+#ifndef RTB_STACK_SHARED
+#define RTB_STACK_SHARED 16
+#endif
+constexpr int kStackShared = RTB_STACK_SHARED;   // of which the top ones live in shared memory; deeper ones in local memory
 constexpr int kTraceThreads = 128;   // threads per block of the traversal kernels
 constexpr int kMaxLeaf = 8;          // primitives per leaf after SAH collapsing
 constexpr float kCostTrav = 1.0f;    // SAH constants
