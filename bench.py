@@ -34,9 +34,9 @@ import numpy as np  # noqa: E402
 METRIC = "Mrays/s at 1080p 100k-tri depth 5, plain vs radiance cache at relMSE ≤ 0.01"
 UNIT = "Mrays/s"
 # algorithmic FP32 operations per unit of work (counted from the math)
-OPS_NODE = 28     # two slab tests: 12 FFMA + 12 min/max + 4 compares
+OPS_BOX = 14      # ordered slab test of one child box: 6 FFMA + 6 min/max + 1 widening FMUL + 1 compare
 OPS_TRI = 30      # Moller-Trumbore
-BYTES_NODE = 64
+BYTES_NODE = 128
 BYTES_TRI = 48
 
 
@@ -265,7 +265,7 @@ def main():
     tr = sum(trace_ms) / len(trace_ms)
     sh = sum(shadow_ms) / len(shadow_ms)
     cls, kms = (0, tr) if tr >= sh else (1, sh)
-    ops = work["node_visits"][cls] * OPS_NODE + work["prim_tests"][cls] * OPS_TRI
+    ops = work["box_tests"][cls] * OPS_BOX + work["prim_tests"][cls] * OPS_TRI
     achieved = ops / (kms * 1e-3) / 1e12
     launches_per_step = info["build_launches"] + 1 + 2 + st["launches"] + 2
 

@@ -127,6 +127,8 @@ typedef struct rt_render_stats {
   float ms_trace;                                /* closest-hit + shade kernels (sum of their times) */
   float ms_shadow;                               /* any-hit kernels; they overlap the next depth's trace */
   int32_t launches;                              /* kernels this render launched */
+  uint64_t box_tests[2];                         /* child boxes tested ([closest, any]; RT_FLAG_COUNT_WORK only);
+                                                    node_visits counts 4-wide nodes, each testing 2 to 4 boxes */
 } rt_render_stats;
 
 typedef struct rt_bvh_info {
@@ -176,6 +178,17 @@ rt_status rt_bvh_get_info(rt_scene* s, rt_bvh_info* info, void* stream);
  * morton: n_prims uint32 sorted codes.  Any pointer may be NULL. */
 rt_status rt_bvh_export(rt_scene* s, float* nodes, int64_t nodes_capacity, int32_t* prim_order,
                         uint32_t* morton, void* stream);
+
+/* Copies the 4-wide tree that the traversal kernels walk to a host buffer
+ * (syncs), for inspection.  Node i is 32 floats: lo.x[4], hi.x[4], lo.y[4],
+ * hi.y[4], lo.z[4], hi.z[4], then four int32 child links (>= 0: node
+ * index; < 0 and not INT32_MIN: leaf ~(start << 3 | count - 1) over
+ * prim_order positions; INT32_MIN: unused slot, box lo = +inf, hi = -inf),
+ * then the number of used slots and three unused words.  The root is node
+ * 0.  Writes min(capacity, nodes built) nodes; *n_nodes (if not NULL)
+ * receives the number built.  The 4-wide nodes are a device layout of this
+ * library: the paper's tree is binary (rt_bvh_export). */
+rt_status rt_bvh_export_wide(rt_scene* s, float* nodes, int64_t nodes_capacity, int64_t* n_nodes, void* stream);
 
 /* Renders one frame into out_rgb_device (H*W*3 float32, overwritten). */
 rt_status rt_render(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,

@@ -16,7 +16,7 @@ import numpy as np
 
 __all__ = [
     "RtError", "lib", "rt_abi_version", "rt_last_error", "rt_render_options_default",
-    "rt_scene_create", "rt_scene_update", "rt_bvh_build", "rt_bvh_get_info", "rt_bvh_export",
+    "rt_scene_create", "rt_scene_update", "rt_bvh_build", "rt_bvh_get_info", "rt_bvh_export", "rt_bvh_export_wide",
     "rt_render", "rt_render_ex", "rt_render_host", "rt_camera_rays", "rt_trace_closest",
     "rt_trace_any", "rt_scene_sync", "rt_scene_destroy", "rt_render_stage_times", "Scene",
     "rt_nrc_config_default", "rt_nrc_create", "rt_nrc_destroy", "rt_nrc_get_params", "rt_nrc_set_params",
@@ -70,7 +70,7 @@ class rt_render_stats(ctypes.Structure):
                 ("node_visits_per_depth", (ctypes.c_uint64 * (RT_MAX_DEPTH + 1)) * 2),
                 ("max_visits_per_depth", (ctypes.c_uint32 * (RT_MAX_DEPTH + 1)) * 2),
                 ("ms_total", ctypes.c_float), ("ms_trace", ctypes.c_float), ("ms_shadow", ctypes.c_float),
-                ("launches", ctypes.c_int32)]
+                ("launches", ctypes.c_int32), ("box_tests", ctypes.c_uint64 * 2)]
 
 
 class rt_nrc_config(ctypes.Structure):
@@ -111,6 +111,7 @@ def lib():
             "rt_bvh_build": (I, [P, P]),
             "rt_bvh_get_info": (I, [P, P, P]),
             "rt_bvh_export": (I, [P, P, I64, P, P, P]),
+            "rt_bvh_export_wide": (I, [P, P, I64, P, P]),
             "rt_render": (I, [P, P, I, I, I, P, P]),
             "rt_render_ex": (I, [P, P, I, I, I, P, P, P, P, P, P]),
             "rt_render_host": (I, [P, P, I, I, I, P, P, P]),
@@ -217,7 +218,7 @@ def stats_dict(s: rt_render_stats, max_depth: int) -> dict:
         "primary": s.primary, "shadow": s.shadow, "secondary": s.secondary,
         "rays_per_depth": list(s.rays_per_depth[:n]), "shadow_per_depth": list(s.shadow_per_depth[:n]),
         "hits_per_depth": list(s.hits_per_depth[:n]),
-        "node_visits": list(s.node_visits), "prim_tests": list(s.prim_tests),
+        "node_visits": list(s.node_visits), "prim_tests": list(s.prim_tests), "box_tests": list(s.box_tests),
         "node_visits_per_depth": [list(s.node_visits_per_depth[k][:n]) for k in range(2)],
         "max_visits_per_depth": [list(s.max_visits_per_depth[k][:n]) for k in range(2)],
         "ms_total": s.ms_total, "ms_trace": s.ms_trace, "ms_shadow": s.ms_shadow, "launches": s.launches,
@@ -270,6 +271,16 @@ def rt_bvh_export(scene, n_prims, n_node_slots, stream=None):
     _check(lib().rt_bvh_export(scene, nodes.ctypes.data, n_node_slots, order.ctypes.data, morton.ctypes.data,
                                _stream(stream)))
     return nodes, order, morton
+
+
+def rt_bvh_export_wide(scene, stream=None):
+    """The 4-wide traversal tree: (n, 32) float32 rows (boxes as floats,
+    the last 8 words reinterpreted as int32 links / slot count)."""
+    n = ctypes.c_int64(0)
+    _check(lib().rt_bvh_export_wide(scene, None, 0, ctypes.byref(n), _stream(stream)))
+    nodes = np.zeros((max(n.value, 1), 32), np.float32)
+    _check(lib().rt_bvh_export_wide(scene, nodes.ctypes.data, n.value, None, _stream(stream)))
+    return nodes[:n.value]
 
 
 def rt_render(scene, camera, width, height, max_depth, out_rgb, stream=None):

@@ -22,7 +22,7 @@
 
 namespace rtb {
 
-constexpr int kSentinelLink = INT_MIN;   // popped from an empty stack; never a valid link
+constexpr int kSentinelLink = kEmptyLink;   // popped from an empty stack; never a valid link
 constexpr float kSlabUp = 1.0000005f;    // grows a slab's exit distance by > 2 ulps
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -38,6 +38,7 @@ struct Counters {
   unsigned cache_hits;                               // hits at the cache depth (depth-first frames)
   unsigned long long visits[2][RT_MAX_DEPTH + 1];
   unsigned long long tests[2][RT_MAX_DEPTH + 1];
+  unsigned long long boxes[2][RT_MAX_DEPTH + 1];
 };
 
 struct FrameParams {
@@ -87,6 +88,7 @@ __device__ __forceinline__ RayInv make_ray(f3 o, f3 d) {
 
 struct WorkCount {
   unsigned visits, tests, vmax;   // vmax: most node visits of one ray
+  unsigned boxes;                 // child boxes tested (non-empty slots of the visited nodes)
 };
 
 template <bool kAny>
@@ -142,10 +144,41 @@ __device__ __forceinline__ int pop_stack(const int* stack, const int* deep, int&
   return sp < kStackShared ? stack[sp * kTraceThreads] : deep[sp - kStackShared];
 }
 
-// BVH traversal with a per-thread stack: its first kStackShared entries
-// live in shared memory (column `stack[i * kTraceThreads]`), deeper ones in
-// local memory, which leaves most of L1 to nodes and primitives.  Near
-// child first; the far one is pushed.
+// Entry time of the ray into one child box of a 4-wide node, or +inf when
+// it misses: the ordered slab test over the near and far planes (picked by
+// the direction's signs), far distance widened by kSlabUp.  A slot with an
+// inverted box (lo = +inf, hi = -inf) always misses.
+__device__ __forceinline__ float child_entry(float nx, float ny, float nz, float fx, float fy, float fz,
+                                             const RayInv& r, float tmin, float tbest) {
+  float tn = fmaxf(fmaxf(fmaf(nx, r.idir.x, -r.oid.x), fmaf(ny, r.idir.y, -r.oid.y)),
+                   fmaxf(fmaf(nz, r.idir.z, -r.oid.z), tmin));
+  float tf = fminf(fminf(fmaf(fx, r.idir.x, -r.oid.x), fmaf(fy, r.idir.y, -r.oid.y)),
+                   fminf(fmaf(fz, r.idir.z, -r.oid.z), tbest)) * kSlabUp;
+  return tn <= tf ? tn : INFINITY;
+}
+
+__device__ __forceinline__ void order2(float& da, int& la, float& db, int& lb) {
+  bool sw = db < da;
+  float d = sw ? db : da;
+  int l = sw ? lb : la;
+  db = sw ? da : db;
+  lb = sw ? la : lb;
+  da = d;
+  la = l;
+}
+
+__device__ __forceinline__ void push_stack(int* stack, int* deep, int& sp, int v) {
+  if (sp < kStackShared) stack[sp * kTraceThreads] = v;
+  else deep[sp - kStackShared] = v;
+  ++sp;
+}
+
+// BVH traversal over the 4-wide tree with a per-thread stack: its first
+// kStackShared entries live in shared memory (column `stack[i *
+// kTraceThreads]`), deeper ones in local memory, which leaves most of L1 to
+// nodes and primitives.  The children a ray enters are sorted by entry
+// distance; the walk continues into the nearest and pushes the others,
+// farthest first.
 // Returns the hit record index (leaf order) or -1.  Sets *fail when the
 // step cap or the stack depth is exceeded (the ray then counts as a miss).
 template <bool kAny, bool kCount>
@@ -162,6 +195,8 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
   int steps = 0;
   const float4* __restrict__ nodes = sc.nodes;
   int deep[kStackSize - kStackShared > 0 ? kStackSize - kStackShared : 1];   // entries below the shared part
+  // rows of the near planes: lo when the direction is positive, else hi
+  const int sx = r.idir.x < 0.f, sy = r.idir.y < 0.f, sz = r.idir.z < 0.f;
   for (;;) {
     // inner nodes
     while (node >= 0) {
@@ -174,38 +209,40 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
         fail = true;
         return -1;
       }
-      if (kCount) wc.visits++;
-      const float4* n = nodes + 4 * (size_t)node;
-      float4 n0 = __ldg(n), n1 = __ldg(n + 1), n2 = __ldg(n + 2), n3 = __ldg(n + 3);
-      float a0 = fmaf(n0.x, r.idir.x, -r.oid.x), b0 = fmaf(n0.y, r.idir.x, -r.oid.x);
-      float a1 = fmaf(n0.z, r.idir.y, -r.oid.y), b1 = fmaf(n0.w, r.idir.y, -r.oid.y);
-      float a2 = fmaf(n2.x, r.idir.z, -r.oid.z), b2 = fmaf(n2.y, r.idir.z, -r.oid.z);
-      float c0min = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), tmin));
-      float c0max = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), tbest)) * kSlabUp;
-      float d0 = fmaf(n1.x, r.idir.x, -r.oid.x), e0 = fmaf(n1.y, r.idir.x, -r.oid.x);
-      float d1 = fmaf(n1.z, r.idir.y, -r.oid.y), e1 = fmaf(n1.w, r.idir.y, -r.oid.y);
-      float d2 = fmaf(n2.z, r.idir.z, -r.oid.z), e2 = fmaf(n2.w, r.idir.z, -r.oid.z);
-      float c1min = fmaxf(fmaxf(fminf(d0, e0), fminf(d1, e1)), fmaxf(fminf(d2, e2), tmin));
-      float c1max = fminf(fminf(fmaxf(d0, e0), fmaxf(d1, e1)), fminf(fmaxf(d2, e2), tbest)) * kSlabUp;
-      bool h0 = c0min <= c0max, h1 = c1min <= c1max;
-      int l0 = __float_as_int(n3.x), l1 = __float_as_int(n3.y);
-      if (h0 && h1) {
-        int nearc = c0min <= c1min ? l0 : l1;
-        int farc = c0min <= c1min ? l1 : l0;
-        if (sp >= kStackSize) {
+      const float4* n = nodes + 8 * (size_t)node;
+      float4 nx = __ldg(n + sx), fx = __ldg(n + 1 - sx);
+      float4 ny = __ldg(n + 2 + sy), fy = __ldg(n + 3 - sy);
+      float4 nz = __ldg(n + 4 + sz), fz = __ldg(n + 5 - sz);
+      float4 lk = __ldg(n + 6);
+      float d0 = child_entry(nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, r, tmin, tbest);
+      float d1 = child_entry(nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, r, tmin, tbest);
+      float d2 = child_entry(nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, r, tmin, tbest);
+      float d3 = child_entry(nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, r, tmin, tbest);
+      int l0 = __float_as_int(lk.x), l1 = __float_as_int(lk.y), l2 = __float_as_int(lk.z), l3 = __float_as_int(lk.w);
+      if (kCount) {
+        wc.visits++;
+        wc.boxes += (l0 != kEmptyLink) + (l1 != kEmptyLink) + (l2 != kEmptyLink) + (l3 != kEmptyLink);
+      }
+      int cnt = (d0 < INFINITY) + (d1 < INFINITY) + (d2 < INFINITY) + (d3 < INFINITY);
+      if (cnt == 0) {
+        node = pop_stack(stack, deep, sp);
+      } else if (cnt == 1) {
+        node = d0 < INFINITY ? l0 : d1 < INFINITY ? l1 : d2 < INFINITY ? l2 : l3;
+      } else {
+        // five compare-exchanges sort four (distance, link) pairs; misses (+inf) go last
+        order2(d0, l0, d1, l1);
+        order2(d2, l2, d3, l3);
+        order2(d0, l0, d2, l2);
+        order2(d1, l1, d3, l3);
+        order2(d1, l1, d2, l2);
+        if (sp + cnt - 1 > kStackSize) {
           fail = true;
           return kAny ? -1 : best;
         }
-        if (sp < kStackShared) stack[sp * kTraceThreads] = farc;
-        else deep[sp - kStackShared] = farc;
-        ++sp;
-        node = nearc;
-      } else if (h0) {
+        if (cnt == 4) push_stack(stack, deep, sp, l3);
+        if (cnt >= 3) push_stack(stack, deep, sp, l2);
+        push_stack(stack, deep, sp, l1);
         node = l0;
-      } else if (h1) {
-        node = l1;
-      } else {
-        node = pop_stack(stack, deep, sp);
       }
     }
     if (node == kSentinelLink) break;
@@ -272,15 +309,17 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
 template <bool kCount>
 __device__ __forceinline__ void flush_work(Counters* ctr, int cls, int depth, WorkCount wc) {
   if (!kCount) return;
-  unsigned v = wc.visits, t = wc.tests, m = wc.vmax;
+  unsigned v = wc.visits, t = wc.tests, m = wc.vmax, b = wc.boxes;
   for (int o = 16; o > 0; o >>= 1) {
     v += __shfl_xor_sync(kFull, v, o);
     t += __shfl_xor_sync(kFull, t, o);
+    b += __shfl_xor_sync(kFull, b, o);
     m = max(m, __shfl_xor_sync(kFull, m, o));
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&ctr->visits[cls][depth], (unsigned long long)v);
     atomicAdd(&ctr->tests[cls][depth], (unsigned long long)t);
+    atomicAdd(&ctr->boxes[cls][depth], (unsigned long long)b);
     atomicMax(&ctr->max_visits[cls][depth], m);
   }
 }
@@ -398,7 +437,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6) k_trace(DevScene sc, FramePa
   const float4* __restrict__ qin = fp.rayq[depth & 1];
   float4* qout = fp.rayq[(depth + 1) & 1];
   bool spawn = depth < fp.max_depth;
-  WorkCount wc = {0u, 0u, 0u};
+  WorkCount wc = {0u, 0u, 0u, 0u};
   for (;;) {
     unsigned base = 0;
     if (lane == 0) base = atomicAdd(&ctr->fetch_trace[depth], 32u);
@@ -518,7 +557,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FramePara
   int lane = threadIdx.x & 31;
   Counters* ctr = fp.ctr;
   unsigned n_items = min(ctr->shadow[depth], fp.shadow_cap);
-  WorkCount wc = {0u, 0u, 0u};
+  WorkCount wc = {0u, 0u, 0u, 0u};
   for (;;) {
     unsigned base = 0;
     if (lane == 0) base = atomicAdd(&ctr->fetch_shadow[depth], 32u);
@@ -549,10 +588,11 @@ __global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FramePara
 // as slow as its slowest ray.
 // ---------------------------------------------------------------------------
 template <bool kCount>
-__device__ __forceinline__ void count_ray(Counters* ctr, int cls, int depth, unsigned v, unsigned t) {
+__device__ __forceinline__ void count_ray(Counters* ctr, int cls, int depth, unsigned v, unsigned t, unsigned b) {
   if (!kCount) return;
   atomicAdd(&ctr->visits[cls][depth], (unsigned long long)v);
   atomicAdd(&ctr->tests[cls][depth], (unsigned long long)t);
+  atomicAdd(&ctr->boxes[cls][depth], (unsigned long long)b);
   atomicMax(&ctr->max_visits[cls][depth], v);
 }
 
@@ -580,7 +620,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
   int nl = 0;
   bool queue_done = false;
   bool have = false;
-  WorkCount wc = {0u, 0u, 0u};
+  WorkCount wc = {0u, 0u, 0u, 0u};
   f3 o = mk3(0, 0, 0), d = mk3(0, 0, 1), w = mk3(0, 0, 0);
   int depth = d0, pixel = 0;
   for (;;) {
@@ -636,9 +676,9 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
     if (have) {
       float t = INFINITY;
       bool fail = false;
-      unsigned v0 = wc.visits, t0 = wc.tests;
+      unsigned v0 = wc.visits, t0 = wc.tests, b0 = wc.boxes;
       int hit = traverse<false, kCount>(sc, make_ray(o, d), 0.0f, t, stack, cap, fail, wc);
-      count_ray<kCount>(ctr, 0, depth, wc.visits - v0, wc.tests - t0);
+      count_ray<kCount>(ctr, 0, depth, wc.visits - v0, wc.tests - t0, wc.boxes - b0);
       if (fail) atomicOr(sc.status, kErrTraversalLimit);
       bool live = hit >= 0;
       if (!live) add_fb(fp, pixel, w * bg);
@@ -688,9 +728,9 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
               continue;
             atomicAdd(&s_cnt[1][depth], 1u);
             bool sfail = false;
-            unsigned sv0 = wc.visits, st0 = wc.tests;
+            unsigned sv0 = wc.visits, st0 = wc.tests, sb0 = wc.boxes;
             int h = traverse<true, kCount>(sc, make_ray(os, sd), 0.0f, tmax, stack, cap, sfail, wc);
-            count_ray<kCount>(ctr, 1, depth, wc.visits - sv0, wc.tests - st0);
+            count_ray<kCount>(ctr, 1, depth, wc.visits - sv0, wc.tests - st0, wc.boxes - sb0);
             if (sfail) atomicOr(sc.status, kErrTraversalLimit);
             if (h < 0 && !sfail) add_fb(fp, pixel, contrib);
           }
@@ -769,7 +809,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_query(DevScene sc, const floa
   if (i >= n) return;
   RayInv ri = make_ray(mk3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
   bool fail = false;
-  WorkCount wc = {0u, 0u, 0u};
+  WorkCount wc = {0u, 0u, 0u, 0u};
   if (any) {
     float tm = tmax_in[i];
     int h = traverse<true, false>(sc, ri, tmin, tm, stack, cap, fail, wc);
@@ -942,7 +982,7 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   s->ray_cap = qcap;
   s->shadow_cap = pcap;
   DevScene sc = dev_scene(s, use_bvh);
-  int64_t tcap = opt.traversal_cap > 0 ? opt.traversal_cap : 4 * std::max<int64_t>(s->n_nodes_total, 1) + 64;
+  int64_t tcap = opt.traversal_cap > 0 ? opt.traversal_cap : 4 * std::max<int64_t>(s->n_nodes4, 1) + 64;
   int cap = (int)std::min<int64_t>(tcap, 0x7fffffff);
   FrameParams fp = frame_defaults();
   fp.cam = camera_basis(cam, W, H);
@@ -1078,6 +1118,7 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
       for (int k = 0; k < 2; ++k) {
         stats->node_visits[k] += c.visits[k][d];
         stats->prim_tests[k] += c.tests[k][d];
+        stats->box_tests[k] += c.boxes[k][d];
         stats->node_visits_per_depth[k][d] = c.visits[k][d];
         stats->max_visits_per_depth[k][d] = c.max_visits[k][d];
       }
@@ -1154,7 +1195,7 @@ static rt_status query(rt_scene* s, const float* o, const float* d, const float*
   if (use_bvh && !s->built) return set_error(RT_ERR_NOT_BUILT, "rt_trace: BVH requested before rt_bvh_build");
   if (n == 0) return RT_OK;
   DevScene sc = dev_scene(s, use_bvh != 0);
-  int cap = (int)std::min<int64_t>(4 * std::max<int64_t>(s->n_nodes_total, 1) + 64, 0x7fffffff);
+  int cap = (int)std::min<int64_t>(4 * std::max<int64_t>(s->n_nodes4, 1) + 64, 0x7fffffff);
   int64_t blocks = (n + kTraceThreads - 1) / kTraceThreads;
   k_query<<<(unsigned)blocks, kTraceThreads, 0, st>>>(sc, o, d, tmax, n, tmin, any, cap, prim, t, occ);
   return cuda_error(cudaGetLastError(), "rt_trace");
@@ -1180,6 +1221,7 @@ rt_status rt_scene_destroy(rt_scene* s) {
   release(s->mats);
   release(s->lights);
   release(s->nodes);
+  release(s->nodes4);
   release(s->build_tmp);
   release(s->build_info);
   release(s->rayq[0]);
@@ -1286,7 +1328,7 @@ extern "C" rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int W,
   fp.ray_cap = (unsigned)kNoallocRayCap;
   fp.shadow_cap = (unsigned)kNoallocShadowCap;
   DevScene sc = dev_scene(s, true);
-  int cap = (int)std::min<int64_t>(4 * std::max<int64_t>(s->n_nodes_total, 1) + 64, 0x7fffffff);
+  int cap = (int)std::min<int64_t>(4 * std::max<int64_t>(s->n_nodes4, 1) + 64, 0x7fffffff);
   // the counters must start at zero; the queues are written before they are read
   cudaError_t e = cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);

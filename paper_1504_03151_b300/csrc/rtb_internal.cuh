@@ -15,7 +15,7 @@ namespace rtb {
 // ---------------------------------------------------------------------------
 // Tunables
 // ---------------------------------------------------------------------------
-constexpr int kStackSize = 64;       // traversal stack entries per thread
+constexpr int kStackSize = 96;       // traversal stack entries per thread (up to 3 pushes per 4-wide node)
 #ifndef RTB_STACK_SHARED
 #define RTB_STACK_SHARED 16
 #endif
@@ -36,6 +36,10 @@ constexpr int kKindSphere = 1;
 
 // Traversal-stack sentinel: popped from an empty stack.
 constexpr int kSentinel = 0x7fffffff;
+// Link of an unused slot of a 4-wide node; its box is inverted (lo = +inf,
+// hi = -inf), which the ordered slab test never hits.  Equal to the
+// traversal's empty-stack value, so that following it can only end a walk.
+constexpr int kEmptyLink = (int)0x80000000;
 
 // ---------------------------------------------------------------------------
 // Device layouts
@@ -44,14 +48,21 @@ constexpr int kSentinel = 0x7fffffff;
 //   triangle: (v0.xyz, kind) (e1.xyz, prim id) (e2.xyz, material)
 //   sphere  : (c.xyz,  kind) (r, r*r, 0, prim id) (0, 0, 0, material)
 //   (integers stored with __int_as_float)
-// BVH node, 4 x float4 = 64 B, 64-B aligned; the two child boxes are stored
-// by axis so that one float4 holds an axis slab pair of both children:
+// Binary BVH node (build output and export format), 4 x float4 = 64 B; the
+// two child boxes are stored by axis so that one float4 holds an axis slab
+// pair of both children:
 //   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
 //   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
 //   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
 //   n3 = (link0, link1, -, -)
+// 4-wide traversal node, 8 x float4 = 128 B (one cache line), one float4 per
+// box plane over the four children, so that a ray picks its near and far
+// planes by the sign of its direction alone:
+//   m0 = lo.x[0..3]  m1 = hi.x[0..3]  m2 = lo.y  m3 = hi.y  m4 = lo.z  m5 = hi.z
+//   m6 = (link0..link3)  m7 = unused
 // link >= 0: internal node index; link < 0: leaf = ~(start << 3 | count-1)
-// over primitive records [start, start+count) in leaf order.
+// over primitive records [start, start+count) in leaf order; kEmptyLink:
+// an unused slot.
 // Material, 3 x float4: (albedo.rgb, ks) (shininess, reflectivity, ior, kind)
 //   (emission.rgb, 0).
 // Light, 2 x float4: (position, 0) (intensity, 0).
@@ -65,7 +76,7 @@ __host__ __device__ inline int leaf_count(int link) { return ((~link) & 7) + 1; 
 // Everything a traversal kernel needs, by value.
 struct DevScene {
   const float4* prims;      // 3 per primitive, leaf order (BVH) or id order
-  const float4* nodes;      // 4 per node
+  const float4* nodes;      // 4-wide nodes, 8 float4 each; the root is node 0
   const float4* mats;       // 3 per material
   const float4* lights;     // 2 per light
   int n_prims;
@@ -103,6 +114,8 @@ struct rt_scene {
   int root = -1;
   int64_t n_nodes_total = 0;     // slots in `nodes` (LBVH internal + top nodes)
   rtb::Buf nodes;
+  rtb::Buf nodes4;               // 4-wide traversal layout (root 0)
+  int64_t n_nodes4 = 0;
   rtb::Buf build_tmp;            // scratch for the build, carved below
   size_t build_tmp_n = 0;
   rtb::Buf build_info;           // device-side build results (BuildInfo)

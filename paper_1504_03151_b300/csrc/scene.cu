@@ -90,13 +90,13 @@ static bool finite3(const float* p) { return std::isfinite(p[0]) && std::isfinit
 DevScene dev_scene(const rt_scene* s, bool use_bvh) {
   DevScene d;
   d.prims = (const float4*)(use_bvh ? s->prims_leaf.p : s->prims_id.p);
-  d.nodes = (const float4*)s->nodes.p;
+  d.nodes = (const float4*)s->nodes4.p;
   d.mats = (const float4*)s->mats.p;
   d.lights = (const float4*)s->lights.p;
   d.n_prims = (int)s->n_prims;
   d.n_lights = (int)s->n_lights;
-  d.n_nodes = (int)s->n_nodes_total;
-  d.root = use_bvh ? s->root : -1;
+  d.n_nodes = (int)s->n_nodes4;
+  d.root = use_bvh && s->root >= 0 ? 0 : -1;
   d.use_bvh = use_bvh ? 1 : 0;
   d.traversal_cap = 0;
   d.status = s->status;

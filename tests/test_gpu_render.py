@@ -264,6 +264,83 @@ def test_bvh_structure_invariants(which):
     assert info["sah_cost"] <= info["sah_cost_lbvh"] * 1.001 or which == "spheres8"
 
 
+def _prim_boxes(sc):
+    n = sc.n_prims
+    lo, hi = np.zeros((n, 3)), np.zeros((n, 3))
+    ns = len(sc.spheres)
+    if ns:
+        c, r = sc.spheres["center"].astype(np.float64), sc.spheres["radius"].astype(np.float64)
+        lo[:ns], hi[:ns] = c - r[:, None], c + r[:, None]
+    if len(sc.triangles):
+        V = np.stack([sc.triangles["v0"], sc.triangles["v1"], sc.triangles["v2"]], 1).astype(np.float64)
+        lo[ns:], hi[ns:] = V.min(1), V.max(1)
+    return lo, hi
+
+
+def _binary_leaves(nodes, root):
+    links = nodes[:, 12:14].view(np.int32)
+    leaves, stack = set(), [root]
+    while stack:
+        node = stack.pop()
+        for c in range(2):
+            link = int(links[node, c])
+            if link < 0:
+                leaves.add(link)
+            else:
+                stack.append(link)
+    return leaves
+
+
+@pytest.mark.parametrize("which", ["single", "spheres8", "terrain_small", "terrain"])
+def test_wide_bvh_structure(which):
+    """The 4-wide tree the kernels walk: a tree over the binary tree's leaves
+    (same leaves, each reached once), 2-4 used slots a node (one for a
+    single primitive), unused slots
+    empty, every box holding what lies below it."""
+    sc = {"single": lambda: S.single_sphere(width=8, height=8), "spheres8": S.scene_spheres8,
+          "terrain_small": small_terrain, "terrain": S.scene_terrain}[which]()
+    n = sc.n_prims
+    scene = rtb.Scene(sc).build()
+    info = rtb.rt_bvh_get_info(scene.handle)
+    bnodes, order, _ = rtb.rt_bvh_export(scene.handle, n, 2 * max(n, 2))
+    wide = rtb.rt_bvh_export_wide(scene.handle)
+    scene.close()
+    assert 1 <= len(wide) <= max(info["n_nodes"], 1)
+    box_lo = np.stack([wide[:, 0:4], wide[:, 8:12], wide[:, 16:20]], 2).astype(np.float64)    # (node, slot, axis)
+    box_hi = np.stack([wide[:, 4:8], wide[:, 12:16], wide[:, 20:24]], 2).astype(np.float64)
+    links = wide[:, 24:28].view(np.int32)
+    used = wide[:, 28:29].view(np.int32)[:, 0]
+    assert ((used >= (1 if n == 1 else 2)) & (used <= 4)).all()
+    empty = np.arange(4)[None, :] >= used[:, None]
+    assert (links[empty] == np.iinfo(np.int32).min).all()
+    assert np.isposinf(box_lo[empty]).all() and np.isneginf(box_hi[empty]).all()
+    assert (links[~empty] != np.iinfo(np.int32).min).all()
+    plo, phi = _prim_boxes(sc)
+    visited = np.zeros(len(wide), np.int64)
+    leaves = []
+    stack, depth = [(0, 0)], 0
+    while stack:
+        node, d = stack.pop()
+        visited[node] += 1
+        depth = max(depth, d)
+        for c in range(int(used[node])):
+            link, lo_c, hi_c = int(links[node, c]), box_lo[node, c], box_hi[node, c]
+            if link < 0:
+                leaves.append(link)
+                v = ~link
+                ids = order[(v >> 3):(v >> 3) + (v & 7) + 1]
+                tol = 1e-6 * (1 + np.abs(plo[ids]).max())
+                assert (plo[ids] >= lo_c - tol).all() and (phi[ids] <= hi_c + tol).all()
+            else:
+                k = int(used[link])
+                assert (box_lo[link, :k] >= lo_c).all() and (box_hi[link, :k] <= hi_c).all()
+                stack.append((link, d + 1))
+    assert (visited == 1).all()
+    assert len(leaves) == len(set(leaves))
+    assert set(leaves) == _binary_leaves(bnodes, info["root"])
+    assert depth <= info["max_depth"]
+
+
 def test_morton_codes_against_cpu_interleave():
     sc = S.scene_terrain()
     n = sc.n_prims
