@@ -427,8 +427,15 @@ __device__ __forceinline__ Children children_of(const Surface& sf, f3 d, f3 w) {
 // ---------------------------------------------------------------------------
 // closest hit + shade (+ primary ray generation at depth 0)
 // ---------------------------------------------------------------------------
+#ifndef RTB_TRACE_MIN_BLOCKS
+#define RTB_TRACE_MIN_BLOCKS 6
+#endif
+#ifndef RTB_PATHS_MIN_BLOCKS
+#define RTB_PATHS_MIN_BLOCKS 5
+#endif
+
 template <bool kPrimary, bool kCount>
-__global__ void __launch_bounds__(kTraceThreads, 6) k_trace(DevScene sc, FrameParams fp, int depth, int cap) {
+__global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(DevScene sc, FrameParams fp, int depth, int cap) {
   __shared__ int s_stack[kStackShared * kTraceThreads];
   int* stack = s_stack + threadIdx.x;
   int lane = threadIdx.x & 31;
@@ -598,8 +605,9 @@ __device__ __forceinline__ void count_ray(Counters* ctr, int cls, int depth, uns
 
 constexpr int kWarpPending = 64;   // pending children per warp (shared memory, 12 KB a block)
 
+
 template <bool kCount>
-__global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParams fp, int cap) {
+__global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(DevScene sc, FrameParams fp, int cap) {
   __shared__ int s_stack[kStackShared * kTraceThreads];
   __shared__ unsigned s_cnt[3][RT_MAX_DEPTH + 2];   // rays spawned for / shadow rays cast at / hits at depth d
   __shared__ float4 s_pend[kTraceThreads / 32][kWarpPending][3];   // (o, pixel) (d, depth) (w, -)
@@ -621,8 +629,17 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
   bool queue_done = false;
   bool have = false;
   WorkCount wc = {0u, 0u, 0u, 0u};
+  // A lane's item is a path segment (depth >= 0) or a shadow ray cast from
+  // a depth-(~depth) hit (depth < 0; w holds its contribution, tmax its
+  // length), so that lanes without a path of their own trace the shadow
+  // rays of the others.
   f3 o = mk3(0, 0, 0), d = mk3(0, 0, 1), w = mk3(0, 0, 0);
   int depth = d0, pixel = 0;
+  float tmax_item = 0.f;
+  // queue rays a warp takes at a time: spread over all warps, so that every
+  // warp starts with free lanes for the children and shadow rays it makes
+  const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
+  const unsigned chunk = max(1u, min(32u, (n_items + n_warps - 1) / n_warps));
   for (;;) {
     // --- refill lanes without a ray: own overflow, warp stack, global queue
     if (!have && nl > 0) {
@@ -634,6 +651,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
       w = xyz(local[nl][2]);
       have = true;
     }
+    __syncwarp();   // shadow rays pushed by this warp's lanes are visible
     unsigned need = __ballot_sync(kFull, !have);
     int np = s_np[warp];
     if (need && np > 0) {
@@ -646,6 +664,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
         d = xyz(r[1]);
         depth = __float_as_int(r[1].w);
         w = xyz(r[2]);
+        tmax_item = r[2].w;
         have = true;
       }
       __syncwarp();
@@ -654,12 +673,14 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
       need = __ballot_sync(kFull, !have);
     }
     if (need && !queue_done) {
+      unsigned want = min((unsigned)__popc(need), chunk);
       unsigned base = 0;
-      if (lane == 0) base = atomicAdd(&ctr->fetch_trace[d0], (unsigned)__popc(need));
+      if (lane == 0) base = atomicAdd(&ctr->fetch_trace[d0], want);
       base = __shfl_sync(kFull, base, 0);
-      unsigned idx = base + (unsigned)__popc(need & lt);
-      if (base + (unsigned)__popc(need) >= n_items) queue_done = true;
-      if (!have && idx < n_items) {
+      unsigned rank = (unsigned)__popc(need & lt);
+      unsigned idx = base + rank;
+      if (base + want >= n_items) queue_done = true;
+      if (!have && rank < want && idx < n_items) {
         float4 q0 = qin[3 * (size_t)idx], q1 = qin[3 * (size_t)idx + 1], q2 = qin[3 * (size_t)idx + 2];
         o = xyz(q0);
         pixel = __float_as_int(q0.w);
@@ -673,7 +694,15 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
     // --- one segment per lane: closest hit, shading, shadow rays, children
     Children ch;
     ch.want_r = ch.want_t = false;
-    if (have) {
+    if (have && depth < 0) {
+      bool sfail = false;
+      float tm = tmax_item;
+      unsigned sv0 = wc.visits, st0 = wc.tests, sb0 = wc.boxes;
+      int h = traverse<true, kCount>(sc, make_ray(o, d), 0.0f, tm, stack, cap, sfail, wc);
+      count_ray<kCount>(ctr, 1, ~depth, wc.visits - sv0, wc.tests - st0, wc.boxes - sb0);
+      if (sfail) atomicOr(sc.status, kErrTraversalLimit);
+      if (h < 0 && !sfail) add_fb(fp, pixel, w);
+    } else if (have) {
       float t = INFINITY;
       bool fail = false;
       unsigned v0 = wc.visits, t0 = wc.tests, b0 = wc.boxes;
@@ -727,6 +756,16 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
                             tmax))
               continue;
             atomicAdd(&s_cnt[1][depth], 1u);
+            // to the warp's pending stack for a free lane; traced here when it is full
+            int pos = atomicAdd(&s_np[warp], 1);
+            if (pos < kWarpPending) {
+              float4* r = s_pend[warp][pos];
+              r[0] = make_float4(os.x, os.y, os.z, __int_as_float(pixel));
+              r[1] = make_float4(sd.x, sd.y, sd.z, __int_as_float(~depth));
+              r[2] = make_float4(contrib.x, contrib.y, contrib.z, tmax);
+              continue;
+            }
+            atomicSub(&s_np[warp], 1);
             bool sfail = false;
             unsigned sv0 = wc.visits, st0 = wc.tests, sb0 = wc.boxes;
             int h = traverse<true, kCount>(sc, make_ray(os, sd), 0.0f, tmax, stack, cap, sfail, wc);
@@ -745,6 +784,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_paths(DevScene sc, FrameParam
     bool two = have && ch.want_r && ch.want_t;
     unsigned m2 = __ballot_sync(kFull, two);
     if (m2) {
+      __syncwarp();
       int np2 = s_np[warp];
       int room = kWarpPending - np2;
       int rank = __popc(m2 & lt);

@@ -22,7 +22,10 @@ constexpr int kStackSize = 96;       // traversal stack entries per thread (up t
 constexpr int kStackShared = RTB_STACK_SHARED;   // of which the top ones live in shared memory; deeper ones in local memory
 constexpr int kTraceThreads = 128;   // threads per block of the traversal kernels
 constexpr int kMaxLeaf = 8;          // primitives per leaf after SAH collapsing
-constexpr float kCostTrav = 1.0f;    // SAH constants
+#ifndef RTB_COST_TRAV
+#define RTB_COST_TRAV 1.0f
+#endif
+constexpr float kCostTrav = RTB_COST_TRAV;   // SAH constants: one node step vs one primitive test
 constexpr float kCostIsect = 1.0f;
 
 // Bits of the device status word.
