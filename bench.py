@@ -219,7 +219,8 @@ def main():
     assert rtb.rt_scene_sync(h) == rtb.RT_OK
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        step(opts_t)                            # the timed step's options: its timing events exist from here on
+        rtb.rt_render_stage_times(h)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
