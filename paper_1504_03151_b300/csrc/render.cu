@@ -173,12 +173,54 @@ __device__ __forceinline__ void push_stack(int* stack, int* deep, int& sp, int v
   ++sp;
 }
 
+// One step of the walk at an inner node of the 4-wide tree: tests the four
+// child boxes, sorts the children the ray enters by entry distance,
+// continues into the nearest and pushes the others (farthest first); pops
+// when the ray enters none.  Returns false when the stack would overflow.
+template <bool kCount>
+__device__ __forceinline__ bool visit_inner(const float4* __restrict__ nodes, int& node, const RayInv& r, int sx,
+                                            int sy, int sz, float tmin, float tbest, int* stack, int* deep, int& sp,
+                                            WorkCount& wc) {
+  const float4* n = nodes + 8 * (size_t)node;
+  float4 nx = __ldg(n + sx), fx = __ldg(n + 1 - sx);
+  float4 ny = __ldg(n + 2 + sy), fy = __ldg(n + 3 - sy);
+  float4 nz = __ldg(n + 4 + sz), fz = __ldg(n + 5 - sz);
+  float4 lk = __ldg(n + 6);
+  float d0 = child_entry(nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, r, tmin, tbest);
+  float d1 = child_entry(nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, r, tmin, tbest);
+  float d2 = child_entry(nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, r, tmin, tbest);
+  float d3 = child_entry(nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, r, tmin, tbest);
+  int l0 = __float_as_int(lk.x), l1 = __float_as_int(lk.y), l2 = __float_as_int(lk.z), l3 = __float_as_int(lk.w);
+  if (kCount) {
+    wc.visits++;
+    wc.boxes += (l0 != kEmptyLink) + (l1 != kEmptyLink) + (l2 != kEmptyLink) + (l3 != kEmptyLink);
+  }
+  int cnt = (d0 < INFINITY) + (d1 < INFINITY) + (d2 < INFINITY) + (d3 < INFINITY);
+  if (cnt == 0) {
+    node = pop_stack(stack, deep, sp);
+  } else if (cnt == 1) {
+    node = d0 < INFINITY ? l0 : d1 < INFINITY ? l1 : d2 < INFINITY ? l2 : l3;
+  } else {
+    // five compare-exchanges sort four (distance, link) pairs; misses (+inf) go last
+    order2(d0, l0, d1, l1);
+    order2(d2, l2, d3, l3);
+    order2(d0, l0, d2, l2);
+    order2(d1, l1, d3, l3);
+    order2(d1, l1, d2, l2);
+    if (sp + cnt - 1 > kStackSize) return false;
+    if (cnt == 4) push_stack(stack, deep, sp, l3);
+    if (cnt >= 3) push_stack(stack, deep, sp, l2);
+    push_stack(stack, deep, sp, l1);
+    node = l0;
+  }
+  return true;
+}
+
 // BVH traversal over the 4-wide tree with a per-thread stack: its first
 // kStackShared entries live in shared memory (column `stack[i *
 // kTraceThreads]`), deeper ones in local memory, which leaves most of L1 to
-// nodes and primitives.  The children a ray enters are sorted by entry
-// distance; the walk continues into the nearest and pushes the others,
-// farthest first.
+// nodes and primitives.  For lanes that walk on their own (the depth-first
+// path kernel); traverse_warp below is the form for whole warps.
 // Returns the hit record index (leaf order) or -1.  Sets *fail when the
 // step cap or the stack depth is exceeded (the ray then counts as a miss).
 template <bool kAny, bool kCount>
@@ -193,7 +235,6 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
   int sp = 0;
   int node = sc.root;
   int steps = 0;
-  const float4* __restrict__ nodes = sc.nodes;
   int deep[kStackSize - kStackShared > 0 ? kStackSize - kStackShared : 1];   // entries below the shared part
   // rows of the near planes: lo when the direction is positive, else hi
   const int sx = r.idir.x < 0.f, sy = r.idir.y < 0.f, sz = r.idir.z < 0.f;
@@ -209,40 +250,9 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
         fail = true;
         return -1;
       }
-      const float4* n = nodes + 8 * (size_t)node;
-      float4 nx = __ldg(n + sx), fx = __ldg(n + 1 - sx);
-      float4 ny = __ldg(n + 2 + sy), fy = __ldg(n + 3 - sy);
-      float4 nz = __ldg(n + 4 + sz), fz = __ldg(n + 5 - sz);
-      float4 lk = __ldg(n + 6);
-      float d0 = child_entry(nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, r, tmin, tbest);
-      float d1 = child_entry(nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, r, tmin, tbest);
-      float d2 = child_entry(nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, r, tmin, tbest);
-      float d3 = child_entry(nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, r, tmin, tbest);
-      int l0 = __float_as_int(lk.x), l1 = __float_as_int(lk.y), l2 = __float_as_int(lk.z), l3 = __float_as_int(lk.w);
-      if (kCount) {
-        wc.visits++;
-        wc.boxes += (l0 != kEmptyLink) + (l1 != kEmptyLink) + (l2 != kEmptyLink) + (l3 != kEmptyLink);
-      }
-      int cnt = (d0 < INFINITY) + (d1 < INFINITY) + (d2 < INFINITY) + (d3 < INFINITY);
-      if (cnt == 0) {
-        node = pop_stack(stack, deep, sp);
-      } else if (cnt == 1) {
-        node = d0 < INFINITY ? l0 : d1 < INFINITY ? l1 : d2 < INFINITY ? l2 : l3;
-      } else {
-        // five compare-exchanges sort four (distance, link) pairs; misses (+inf) go last
-        order2(d0, l0, d1, l1);
-        order2(d2, l2, d3, l3);
-        order2(d0, l0, d2, l2);
-        order2(d1, l1, d3, l3);
-        order2(d1, l1, d2, l2);
-        if (sp + cnt - 1 > kStackSize) {
-          fail = true;
-          return kAny ? -1 : best;
-        }
-        if (cnt == 4) push_stack(stack, deep, sp, l3);
-        if (cnt >= 3) push_stack(stack, deep, sp, l2);
-        push_stack(stack, deep, sp, l1);
-        node = l0;
+      if (!visit_inner<kCount>(sc.nodes, node, r, sx, sy, sz, tmin, tbest, stack, deep, sp, wc)) {
+        fail = true;
+        return kAny ? -1 : best;
       }
     }
     if (node == kSentinelLink) break;
@@ -258,6 +268,64 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
       node = pop_stack(stack, deep, sp);
     }
     if (node == kSentinelLink) break;
+  }
+  return best;
+}
+
+// The same walk for a whole warp: all 32 lanes call it together, lanes with
+// `part` false take no step.  The inner-node and leaf loops run while any
+// lane has work of their kind and end in a warp vote, so the warp
+// reconverges at every switch between the two instead of running its lanes'
+// phases one after another.  Same results and errors as traverse().
+template <bool kAny, bool kCount>
+__device__ int traverse_warp(const DevScene& sc, const RayInv& r, bool part, float tmin, float& tbest, int* stack,
+                             int cap, bool& fail, WorkCount& wc) {
+  int best = -1, best_id = INT_MAX;
+  if (sc.n_prims == 0) return -1;
+  if (!sc.use_bvh) {
+    if (part) leaf_hits<kAny, kCount>(sc.prims, 0, sc.n_prims, r, tmin, tbest, best, best_id, wc);
+    return best;
+  }
+  int sp = 0;
+  int node = part ? sc.root : kSentinelLink;
+  int steps = 0;
+  int deep[kStackSize - kStackShared > 0 ? kStackSize - kStackShared : 1];
+  const int sx = r.idir.x < 0.f, sy = r.idir.y < 0.f, sz = r.idir.z < 0.f;
+  for (;;) {
+    while (__any_sync(kFull, node >= 0)) {
+      if (node >= 0) {
+        if (++steps > cap) {
+          fail = true;
+          if (kAny) best = -1;
+          node = kSentinelLink;
+        } else if (node >= sc.n_nodes) {
+          atomicOr(sc.status, kErrBadTree);
+          fail = true;
+          best = -1;
+          node = kSentinelLink;
+        } else if (!visit_inner<kCount>(sc.nodes, node, r, sx, sy, sz, tmin, tbest, stack, deep, sp, wc)) {
+          fail = true;
+          if (kAny) best = -1;
+          node = kSentinelLink;
+        }
+      }
+    }
+    if (!__any_sync(kFull, node != kSentinelLink)) break;
+    while (__any_sync(kFull, node < 0 && node != kSentinelLink)) {
+      if (node < 0 && node != kSentinelLink) {
+        int ls = leaf_start(node), lc = leaf_count(node);
+        if (ls + lc > sc.n_prims) {
+          atomicOr(sc.status, kErrBadTree);
+          fail = true;
+          best = -1;
+          node = kSentinelLink;
+        } else if (leaf_hits<kAny, kCount>(sc.prims, ls, lc, r, tmin, tbest, best, best_id, wc)) {
+          node = kSentinelLink;   // any hit: done
+        } else {
+          node = pop_stack(stack, deep, sp);
+        }
+      }
+    }
   }
   return best;
 }
@@ -476,16 +544,11 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
     }
     // closest hit
     float t = INFINITY;
-    int hit = -1;
     bool fail = false;
-    if (active) {
-      RayInv ri = make_ray(o, d);
-      unsigned v0 = wc.visits;
-      hit = traverse<false, kCount>(sc, ri, 0.0f, t, stack, cap, fail, wc);
-      if (kCount) wc.vmax = max(wc.vmax, wc.visits - v0);
-      if (fail) atomicOr(sc.status, kErrTraversalLimit);
-    }
-    __syncwarp();
+    unsigned v0 = wc.visits;
+    int hit = traverse_warp<false, kCount>(sc, make_ray(o, d), active, 0.0f, t, stack, cap, fail, wc);
+    if (kCount) wc.vmax = max(wc.vmax, wc.visits - v0);
+    if (fail) atomicOr(sc.status, kErrTraversalLimit);
     if (kPrimary && active) {
       if (fp.aov_prim) fp.aov_prim[pixel] = hit >= 0 ? __float_as_int(__ldg(&sc.prims[3 * (size_t)hit + 1]).w) : -1;
       if (fp.aov_t) fp.aov_t[pixel] = hit >= 0 ? t : INFINITY;
@@ -571,18 +634,22 @@ __global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FramePara
     base = __shfl_sync(kFull, base, 0);
     if (base >= n_items) break;
     unsigned idx = base + lane;
-    if (idx < n_items) {
+    bool part = idx < n_items;
+    float4 q0 = make_float4(0, 0, 0, 0), q1 = make_float4(0, 0, 1, 0), q2 = make_float4(0, 0, 0, 0);
+    if (part) {
       const float4* q = fp.shadowq[depth & 1] + 3 * (size_t)idx;
-      float4 q0 = q[0], q1 = q[1], q2 = q[2];
-      RayInv ri = make_ray(xyz(q0), xyz(q1));
-      float tmax = q1.w;
-      bool fail = false;
-      unsigned v0 = wc.visits;
-      int h = traverse<true, kCount>(sc, ri, 0.0f, tmax, stack, cap, fail, wc);
-      if (kCount) wc.vmax = max(wc.vmax, wc.visits - v0);
-      if (fail) atomicOr(sc.status, kErrTraversalLimit);
-      if (h < 0 && !fail) add_fb(fp, __float_as_int(q0.w), xyz(q2));
+      q0 = q[0];
+      q1 = q[1];
+      q2 = q[2];
     }
+    float tmax = q1.w;
+    bool fail = false;
+    unsigned v0 = wc.visits;
+    int h = -1;
+    if (part) h = traverse<true, kCount>(sc, make_ray(xyz(q0), xyz(q1)), 0.0f, tmax, stack, cap, fail, wc);
+    if (kCount) wc.vmax = max(wc.vmax, wc.visits - v0);
+    if (fail) atomicOr(sc.status, kErrTraversalLimit);
+    if (part && h < 0 && !fail) add_fb(fp, __float_as_int(q0.w), xyz(q2));
   }
   flush_work<kCount>(ctr, 1, depth, wc);
 }
@@ -846,19 +913,23 @@ __global__ void __launch_bounds__(kTraceThreads) k_query(DevScene sc, const floa
   __shared__ int s_stack[kStackShared * kTraceThreads];
   int* stack = s_stack + threadIdx.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  RayInv ri = make_ray(mk3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
+  bool part = i < n;   // every lane of the warp walks together (traverse_warp)
+  int64_t k = part ? i : 0;
+  RayInv ri = make_ray(part ? mk3(o[3 * k], o[3 * k + 1], o[3 * k + 2]) : mk3(0, 0, 0),
+                       part ? mk3(d[3 * k], d[3 * k + 1], d[3 * k + 2]) : mk3(0, 0, 1));
   bool fail = false;
   WorkCount wc = {0u, 0u, 0u, 0u};
   if (any) {
-    float tm = tmax_in[i];
-    int h = traverse<true, false>(sc, ri, tmin, tm, stack, cap, fail, wc);
-    occ_out[i] = h >= 0 ? 1 : 0;
+    float tm = part ? tmax_in[k] : 0.f;
+    int h = traverse_warp<true, false>(sc, ri, part, tmin, tm, stack, cap, fail, wc);
+    if (part) occ_out[i] = h >= 0 ? 1 : 0;
   } else {
     float t = INFINITY;
-    int h = traverse<false, false>(sc, ri, tmin, t, stack, cap, fail, wc);
-    prim_out[i] = h >= 0 ? __float_as_int(sc.prims[3 * (size_t)h + 1].w) : -1;
-    t_out[i] = h >= 0 ? t : INFINITY;
+    int h = traverse_warp<false, false>(sc, ri, part, tmin, t, stack, cap, fail, wc);
+    if (part) {
+      prim_out[i] = h >= 0 ? __float_as_int(sc.prims[3 * (size_t)h + 1].w) : -1;
+      t_out[i] = h >= 0 ? t : INFINITY;
+    }
   }
   if (fail) atomicOr(sc.status, kErrTraversalLimit);
 }
