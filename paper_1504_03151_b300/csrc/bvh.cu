@@ -18,6 +18,8 @@ namespace rtb {
 
 constexpr int kSortTile = 4096;     // keys per radix-sort tile (256 threads x 16)
 constexpr int kScanBlock = 4096;    // elements per scan block (1024 threads x 4)
+constexpr int kSortCoopMaxBlocks = 1024;   // grid of the single-launch sort (co-resident blocks)
+constexpr int kSortCoopMaxKeys = 1 << 22;  // larger inputs take the multi-launch sort
 constexpr int kTopBins = 16;        // SAH bins per axis for the top-level rebuild
 constexpr int kMaxLevels4 = 256;    // levels of the 4-wide tree (at most the binary tree's height)
 constexpr int kTopMaxLevels = 64;   // launches of the level kernel (empty ones return at once)
@@ -300,6 +302,124 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const unsigned* __restrict
   }
 }
 
+// Exclusive scan over a 256-thread block.
+__device__ unsigned block_excl_scan_256(unsigned v, unsigned* sw, unsigned& total) {
+  int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  unsigned inc = warp_incl_scan(v, lane);
+  if (lane == 31) sw[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned x = lane < 8 ? sw[lane] : 0u;
+    unsigned xi = warp_incl_scan(x, lane);
+    if (lane < 8) sw[lane] = xi - x;
+    if (lane == 7) sw[8] = xi;
+  }
+  __syncthreads();
+  unsigned r = inc - v + sw[w];
+  total = sw[8];
+  __syncthreads();
+  return r;
+}
+
+// The whole LSD radix sort in one cooperative launch (inputs up to
+// kSortCoopMaxKeys): block b owns one contiguous tile of the keys.  Each
+// 8-bit pass counts the tile's digits, scans every digit's counts over the
+// tiles (one block per digit), and scatters the tile stably, with grid
+// barriers between the three steps.  Keys written by other blocks are read
+// through L2 (__ldcg).
+__global__ void __launch_bounds__(256) k_sort_coop(unsigned* k0, unsigned* v0, unsigned* k1, unsigned* v1, int n,
+                                                   int passes, unsigned* __restrict__ hist,
+                                                   unsigned* __restrict__ totals) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ unsigned h[256];
+  __shared__ unsigned base[256];
+  __shared__ unsigned wcnt[8][256];
+  __shared__ unsigned sw[9];
+  const int G = (int)gridDim.x, b = (int)blockIdx.x, t = (int)threadIdx.x, lane = t & 31, w = t >> 5;
+  const int T = (n + G - 1) / G;
+  const int beg = min(n, b * T), end = min(n, beg + T);
+  unsigned *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    // 1. digit counts of this tile
+    h[t] = 0;
+    __syncthreads();
+    for (int i = beg + t; i < end; i += 256) atomicAdd(&h[(__ldcg(&ki[i]) >> shift) & 255u], 1u);
+    __syncthreads();
+    hist[(size_t)t * G + b] = h[t];
+    grid.sync();
+    // 2. per digit: exclusive scan of its counts over the tiles, and its total
+    for (int d = b; d < 256; d += G) {
+      unsigned* row = hist + (size_t)d * G;
+      const int per = (G + 255) / 256, i0 = t * per;
+      unsigned sum = 0;
+      for (int k = 0; k < per; ++k)
+        if (i0 + k < G) sum += __ldcg(&row[i0 + k]);
+      unsigned tot;
+      unsigned ex = block_excl_scan_256(sum, sw, tot);
+      for (int k = 0; k < per; ++k) {
+        if (i0 + k < G) {
+          unsigned x = __ldcg(&row[i0 + k]);
+          row[i0 + k] = ex;
+          ex += x;
+        }
+      }
+      if (t == 0) totals[d] = tot;
+    }
+    grid.sync();
+    // 3. where this tile's keys of each digit start
+    {
+      unsigned tot_d = __ldcg(&totals[t]), all;
+      unsigned digit_base = block_excl_scan_256(tot_d, sw, all);
+      base[t] = digit_base + __ldcg(&hist[(size_t)t * G + b]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) wcnt[k][t] = 0;
+    }
+    __syncthreads();
+    // 4. stable scatter, 256 keys at a time in index order; equal digits
+    //    within a warp are ranked with match.any
+    for (int r0 = beg; r0 < end; r0 += 256) {
+      const int idx = r0 + t;
+      const bool valid = idx < end;
+      unsigned key = valid ? __ldcg(&ki[idx]) : 0u, val = valid ? __ldcg(&vi[idx]) : 0u;
+      unsigned digit = (key >> shift) & 255u;
+      unsigned peers = __match_any_sync(0xffffffffu, valid ? digit : 256u + (unsigned)lane);
+      int rank = __popc(peers & ((1u << lane) - 1u));
+      if (valid && rank == 0) wcnt[w][digit] = __popc(peers);
+      __syncthreads();
+      {
+        unsigned run = base[t];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          unsigned c = wcnt[k][t];
+          wcnt[k][t] = run;
+          run += c;
+        }
+        base[t] = run;
+      }
+      __syncthreads();
+      if (valid) {
+        unsigned pos = wcnt[w][digit] + (unsigned)rank;
+        if (pos < (unsigned)n) {
+          ko[pos] = key;
+          vo[pos] = val;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 8; ++k) wcnt[k][t] = 0;
+      __syncthreads();
+    }
+    grid.sync();
+    unsigned* tk = ki;
+    ki = ko;
+    ko = tk;
+    unsigned* tv = vi;
+    vi = vo;
+    vo = tv;
+  }
+}
+
 static int scan_exclusive(unsigned* data, size_t m, unsigned* partials, cudaStream_t st) {
   int blocks = (int)((m + kScanBlock - 1) / kScanBlock);
   k_scan_block<<<blocks, 1024, 0, st>>>(data, m, partials);
@@ -313,11 +433,23 @@ static int scan_exclusive(unsigned* data, size_t m, unsigned* partials, cudaStre
 
 // Sorts (keys0, vals0) by the low `bits` bits; the result ends in
 // (keys0, vals0) (an even number of passes).
-static int radix_sort_pairs(BuildScratch& b, int n, int bits, cudaStream_t st) {
+static int radix_sort_pairs(rt_scene* s, BuildScratch& b, int n, int bits, cudaStream_t st) {
   int launches = 0;
   int tiles = (n + kSortTile - 1) / kSortTile;
   int passes = (bits + 7) / 8;
   if (passes & 1) passes++;
+  static int coop_blocks = -1;
+  if (coop_blocks < 0) {
+    int coop = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_coop, 256, 0);
+    coop_blocks = coop ? std::min(std::min(per_sm, 2) * s->sm_count, kSortCoopMaxBlocks) : 0;
+  }
+  if (coop_blocks > 0 && n <= kSortCoopMaxKeys) {
+    void* args[] = {&b.keys0, &b.vals0, &b.keys1, &b.vals1, &n, &passes, &b.hist, &b.partials};
+    if (cudaLaunchCooperativeKernel((void*)k_sort_coop, coop_blocks, 256, args, 0, st) == cudaSuccess) return 1;
+    cudaGetLastError();
+  }
   unsigned *ki = b.keys0, *vi = b.vals0, *ko = b.keys1, *vo = b.vals1;
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
@@ -996,8 +1128,8 @@ namespace rtb {
 
 static rt_status carve(rt_scene* s, int n, BuildScratch& b) {
   size_t tiles = (size_t)(n + kSortTile - 1) / kSortTile;
-  size_t hist_n = 256 * tiles;
-  size_t parts = (hist_n + kScanBlock - 1) / kScanBlock + 1;
+  size_t hist_n = 256 * std::max(tiles, (size_t)kSortCoopMaxBlocks);   // per-tile or per-block digit counts
+  size_t parts = std::max((hist_n + kScanBlock - 1) / kScanBlock + 1, (size_t)256);   // scan partials / digit totals
   size_t N = (size_t)std::max(n, 2);
   size_t off = 0;
   size_t sz[32];
@@ -1149,7 +1281,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     return cuda_error(cudaGetLastError(), "rt_bvh_build");
   }
   k_morton<<<grid, tb, 0, st>>>(b.aabb_lo, b.aabb_hi, n, b.cent_bounds, b.keys0, b.vals0);
-  L += 1 + radix_sort_pairs(b, n, 30, st);
+  L += 1 + radix_sort_pairs(s, b, n, 30, st);
   cudaMemsetAsync(b.flags, 0, (size_t)n * 4, st);
   cudaMemsetAsync(b.parent, 0xff, (size_t)n * 4, st);
   cudaMemsetAsync(b.leaf_parent, 0xff, (size_t)n * 4, st);
