@@ -184,10 +184,13 @@ rt_status rt_bvh_export(rt_scene* s, float* nodes, int64_t nodes_capacity, int32
  * hi.y[4], lo.z[4], hi.z[4], then four int32 child links (>= 0: node
  * index; < 0 and not INT32_MIN: leaf ~(start << 3 | count - 1) over
  * prim_order positions; INT32_MIN: unused slot, box lo = +inf, hi = -inf),
- * then the number of used slots and three unused words.  The root is node
- * 0.  Writes min(capacity, nodes built) nodes; *n_nodes (if not NULL)
- * receives the number built.  The 4-wide nodes are a device layout of this
- * library: the paper's tree is binary (rt_bvh_export). */
+ * then the number of used slots and three unused words.  There is one
+ * node per binary node slot, at the binary node's index; the root is the
+ * root that rt_bvh_get_info reports, and nodes that cannot be reached from
+ * it hold data that is never read.  Writes min(capacity, slots) nodes;
+ * *n_nodes (if not NULL) receives the number of slots.  The 4-wide nodes
+ * are a device layout of this library: the paper's tree is binary
+ * (rt_bvh_export). */
 rt_status rt_bvh_export_wide(rt_scene* s, float* nodes, int64_t nodes_capacity, int64_t* n_nodes, void* stream);
 
 /* Renders one frame into out_rgb_device (H*W*3 float32, overwritten). */

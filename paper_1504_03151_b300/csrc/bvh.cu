@@ -21,7 +21,6 @@ constexpr int kScanBlock = 4096;    // elements per scan block (1024 threads x 4
 constexpr int kSortCoopMaxBlocks = 1024;   // grid of the single-launch sort (co-resident blocks)
 constexpr int kSortCoopMaxKeys = 1 << 22;  // larger inputs take the multi-launch sort
 constexpr int kTopBins = 16;        // SAH bins per axis for the top-level rebuild
-constexpr int kMaxLevels4 = 256;    // levels of the 4-wide tree (at most the binary tree's height)
 constexpr int kTopMaxLevels = 64;   // launches of the level kernel (empty ones return at once)
 constexpr int kTopForceMedian = 32; // from this level on, split segments at the middle: with at
                                     // most 2^28 clusters every segment is done by level 60
@@ -58,7 +57,6 @@ struct BuildScratch {
   int* top_count;
   float4 *top_lo, *top_hi;       // boxes of top nodes (for their parent's child box)
   int* top_height;
-  int* c4;                       // collapse: [0] BVH4 nodes, [1 + level] queue sizes
   BuildInfo* info;
 };
 
@@ -922,16 +920,20 @@ __global__ void k_top_done(const int* __restrict__ top_count, const int* __restr
 }
 
 // ---------------------------------------------------------------------------
-// 8. 4-wide traversal tree.  Each 4-wide node stands for one internal node
-//    of the binary tree and takes its children; while fewer than four, the
-//    internal child with the largest surface area is replaced by its own two
-//    children.  Built top-down, one level of the 4-wide tree per step of a
-//    cooperative launch; a queue entry is (binary node, 4-wide slot).
+// 8. 4-wide traversal tree.  A 4-wide node stands for one internal node of
+//    the binary tree and takes its children; while it has fewer than four,
+//    the internal child with the largest surface area is replaced by its
+//    own two children.  What a 4-wide node holds depends on its binary
+//    node's subtree alone, so every binary node gets its 4-wide node at its
+//    own index, in parallel: a child slot that is an internal binary node
+//    links to that node's 4-wide node.  Walking from the root reaches
+//    exactly the nodes a top-down collapse would make; the others are never
+//    visited.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void bin_child(const float4* __restrict__ bin, int node, int c, float* lo, float* hi,
                                           int& link) {
   const float4* n = bin + 4 * (size_t)node;
-  float4 xy = __ldcg(n + c), z = __ldcg(n + 2), l = __ldcg(n + 3);
+  float4 xy = __ldg(n + c), z = __ldg(n + 2), l = __ldg(n + 3);
   lo[0] = xy.x;
   hi[0] = xy.y;
   lo[1] = xy.z;
@@ -946,84 +948,47 @@ __device__ __forceinline__ float half_area(const float* lo, const float* hi) {
   return dx * dy + dy * dz + dz * dx;
 }
 
-__global__ void __launch_bounds__(256) k_collapse4(const float4* __restrict__ bin, int bin_root, int n_bin,
-                                                   float4* __restrict__ out, int cap4, int* c4, int2* qa, int2* qb,
-                                                   int qcap, unsigned* status) {
-  cg::grid_group grid = cg::this_grid();
-  if (grid.thread_rank() == 0) {
-    qa[0] = make_int2(bin_root, 0);
-    c4[0] = 1;   // 4-wide nodes handed out
-    c4[1] = 1;   // queue size of level 0
-    for (int l = 2; l < kMaxLevels4 + 2; ++l) c4[l] = 0;
-  }
-  grid.sync();
-  int level = 0;
-  for (; level < kMaxLevels4; ++level) {
-    int nq = __ldcg(&c4[1 + level]);
-    if (nq == 0) break;
-    nq = min(nq, qcap);
-    const int2* qin = (level & 1) ? qb : qa;
-    int2* qout = (level & 1) ? qa : qb;
-    for (int i = (int)grid.thread_rank(); i < nq; i += (int)grid.size()) {
-      int2 it = __ldcg(&qin[i]);
-      float lo[4][3], hi[4][3];
-      int link[4];
-      int ns = 2;
-      bin_child(bin, it.x, 0, lo[0], hi[0], link[0]);
-      bin_child(bin, it.x, 1, lo[1], hi[1], link[1]);
-      while (ns < 4) {
-        int best = -1;
-        float ba = -1.f;
-        for (int k = 0; k < ns; ++k) {
-          if (link[k] < 0 || link[k] >= n_bin) continue;   // a leaf stays a leaf
-          float a = half_area(lo[k], hi[k]);
-          if (a > ba) {
-            ba = a;
-            best = k;
-          }
-        }
-        if (best < 0) break;
-        int x = link[best];
-        bin_child(bin, x, 1, lo[ns], hi[ns], link[ns]);
-        bin_child(bin, x, 0, lo[best], hi[best], link[best]);
-        ++ns;
+__global__ void __launch_bounds__(256) k_collapse4(const float4* __restrict__ bin, int n_bin,
+                                                   float4* __restrict__ out) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n_bin) return;
+  float lo[4][3], hi[4][3];
+  int link[4];
+  int ns = 2;
+  bin_child(bin, x, 0, lo[0], hi[0], link[0]);
+  bin_child(bin, x, 1, lo[1], hi[1], link[1]);
+  while (ns < 4) {
+    int best = -1;
+    float ba = -1.f;
+    for (int k = 0; k < ns; ++k) {
+      if (link[k] < 0 || link[k] >= n_bin) continue;   // a leaf stays a leaf
+      float a = half_area(lo[k], hi[k]);
+      if (a > ba) {
+        ba = a;
+        best = k;
       }
-      int out_link[4];
-      for (int k = 0; k < 4; ++k) {
-        if (k >= ns) {
-          out_link[k] = kEmptyLink;
-        } else if (link[k] >= 0) {
-          // an internal child becomes a 4-wide node of the next level
-          int j = link[k] < n_bin ? atomicAdd(&c4[0], 1) : cap4;
-          int pos = j < cap4 ? atomicAdd(&c4[2 + level], 1) : qcap;
-          if (pos < qcap) {
-            qout[pos] = make_int2(link[k], j);
-            out_link[k] = j;
-          } else {
-            atomicOr(status, kErrBadTree);
-            out_link[k] = kEmptyLink;
-          }
-        } else {
-          out_link[k] = link[k];
-        }
-      }
-      float r[6][4];
-      for (int k = 0; k < 4; ++k) {
-        bool used = k < ns && out_link[k] != kEmptyLink;
-        for (int a = 0; a < 3; ++a) {
-          r[2 * a][k] = used ? lo[k][a] : INFINITY;
-          r[2 * a + 1][k] = used ? hi[k][a] : -INFINITY;
-        }
-      }
-      float4* o = out + 8 * (size_t)it.y;
-      for (int q = 0; q < 6; ++q) o[q] = make_float4(r[q][0], r[q][1], r[q][2], r[q][3]);
-      o[6] = make_float4(__int_as_float(out_link[0]), __int_as_float(out_link[1]), __int_as_float(out_link[2]),
-                         __int_as_float(out_link[3]));
-      o[7] = make_float4(__int_as_float(ns), 0.f, 0.f, 0.f);
     }
-    grid.sync();
+    if (best < 0) break;
+    int c = link[best];
+    bin_child(bin, c, 1, lo[ns], hi[ns], link[ns]);
+    bin_child(bin, c, 0, lo[best], hi[best], link[best]);
+    ++ns;
   }
-  if (grid.thread_rank() == 0 && level == kMaxLevels4 && __ldcg(&c4[1 + level]) != 0) atomicOr(status, kErrBadTree);
+  float r[6][4];
+  int out_link[4];
+  for (int k = 0; k < 4; ++k) {
+    bool used = k < ns;
+    out_link[k] = used ? link[k] : kEmptyLink;
+    for (int a = 0; a < 3; ++a) {
+      r[2 * a][k] = used ? lo[k][a] : INFINITY;
+      r[2 * a + 1][k] = used ? hi[k][a] : -INFINITY;
+    }
+  }
+  float4* o = out + 8 * (size_t)x;
+  for (int q = 0; q < 6; ++q) o[q] = make_float4(r[q][0], r[q][1], r[q][2], r[q][3]);
+  o[6] = make_float4(__int_as_float(out_link[0]), __int_as_float(out_link[1]), __int_as_float(out_link[2]),
+                     __int_as_float(out_link[3]));
+  o[7] = make_float4(__int_as_float(ns), 0.f, 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -1066,7 +1031,7 @@ __global__ void k_layout(int n, const int* __restrict__ lch, const int* __restri
 
 // one primitive, 4-wide: a root with one used slot
 __global__ void k_wide_single(const float4* __restrict__ aabb_lo, const float4* __restrict__ aabb_hi,
-                              float4* __restrict__ out, int* c4) {
+                              float4* __restrict__ out) {
   float4 lo = aabb_lo[0], hi = aabb_hi[0];
   out[0] = make_float4(lo.x, INFINITY, INFINITY, INFINITY);
   out[1] = make_float4(hi.x, -INFINITY, -INFINITY, -INFINITY);
@@ -1077,7 +1042,6 @@ __global__ void k_wide_single(const float4* __restrict__ aabb_lo, const float4* 
   out[6] = make_float4(__int_as_float(leaf_link(0, 1)), __int_as_float(kEmptyLink), __int_as_float(kEmptyLink),
                        __int_as_float(kEmptyLink));
   out[7] = make_float4(__int_as_float(1), 0.f, 0.f, 0.f);
-  c4[0] = 1;
 }
 
 // one primitive: a root whose second child box is empty
@@ -1132,7 +1096,7 @@ static rt_status carve(rt_scene* s, int n, BuildScratch& b) {
   size_t parts = std::max((hist_n + kScanBlock - 1) / kScanBlock + 1, (size_t)256);   // scan partials / digit totals
   size_t N = (size_t)std::max(n, 2);
   size_t off = 0;
-  size_t sz[32];
+  size_t sz[48];
   int k = 0;
   sz[k++] = N * 16;  // aabb_lo
   sz[k++] = N * 16;  // aabb_hi
@@ -1164,14 +1128,14 @@ static rt_status carve(rt_scene* s, int n, BuildScratch& b) {
   sz[k++] = N * 16;  // top_lo (also SAH scratch)
   sz[k++] = N * 16;  // top_hi
   sz[k++] = N * 4;   // top_height
-  sz[k++] = (kMaxLevels4 + 4) * 4;   // c4
   sz[k++] = sizeof(BuildInfo);
+  static_assert(sizeof(sz) / sizeof(sz[0]) >= 34, "scratch region table too small");
   size_t total = 0;
   for (int i = 0; i < k; ++i) total += align_up(sz[i]);
   rt_status st = ensure(s->build_tmp, total);
   if (st) return st;
   char* base = (char*)s->build_tmp.p;
-  void* ptr[32];
+  void* ptr[48];
   for (int i = 0; i < k; ++i) {
     ptr[i] = base + off;
     off += align_up(sz[i]);
@@ -1207,7 +1171,6 @@ static rt_status carve(rt_scene* s, int n, BuildScratch& b) {
   b.top_lo = (float4*)ptr[q++];
   b.top_hi = (float4*)ptr[q++];
   b.top_height = (int*)ptr[q++];
-  b.c4 = (int*)ptr[q++];
   b.info = (BuildInfo*)ptr[q++];
   return RT_OK;
 }
@@ -1219,35 +1182,18 @@ static int cluster_max_for(int n) {
   return c;
 }
 
-// Collapses the binary tree rooted at s->root into the 4-wide traversal
-// tree (s->nodes4, root 0) with one cooperative launch.
+// The 4-wide traversal tree: one 4-wide node per binary node slot, at the
+// same index (the root is the binary root).
 static rt_status collapse4(rt_scene* s, const BuildScratch& b, const float4* nodes, int n_bin, cudaStream_t st) {
-  int n = (int)s->n_prims;
-  int cap4 = std::max(n, 2);   // one 4-wide node per binary internal node at most
-  rt_status rs = ensure(s->nodes4, (size_t)cap4 * 128);
+  rt_status rs = ensure(s->nodes4, (size_t)n_bin * 128);
   if (rs) return rs;
-  s->n_nodes4 = cap4;
-  static int coop_blocks = -1;
-  if (coop_blocks < 0) {
-    int coop = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collapse4, 256, 0);
-    coop_blocks = coop ? std::min(per_sm, 2) * s->sm_count : 0;
+  s->n_nodes4 = n_bin;
+  if (s->n_prims == 1) {
+    k_wide_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, (float4*)s->nodes4.p);
+  } else {
+    k_collapse4<<<(n_bin + 255) / 256, 256, 0, st>>>(nodes, n_bin, (float4*)s->nodes4.p);
   }
-  if (coop_blocks <= 0) return set_error(RT_ERR_CUDA, "rt_bvh_build: the device has no cooperative launch");
-  if (n == 1) {
-    k_wide_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, (float4*)s->nodes4.p, b.c4);
-    return cuda_error(cudaGetLastError(), "rt_bvh_build: 4-wide root");
-  }
-  int root = s->root, qcap = 2 * std::max(n, 1);   // int2 entries in seg_a / seg_b
-  float4* out = (float4*)s->nodes4.p;
-  int2* qa = (int2*)b.seg_a;
-  int2* qb = (int2*)b.seg_b;
-  int* c4 = b.c4;
-  unsigned* status = s->status;
-  void* args[] = {(void*)&nodes, &root, &n_bin, &out, &cap4, &c4, &qa, &qb, &qcap, &status};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_collapse4, coop_blocks, 256, args, 0, st);
-  return e == cudaSuccess ? RT_OK : cuda_error(e, "rt_bvh_build: 4-wide collapse");
+  return cuda_error(cudaGetLastError(), "rt_bvh_build: 4-wide tree");
 }
 
 rt_status bvh_build(rt_scene* s, cudaStream_t st) {
@@ -1466,19 +1412,10 @@ rt_status rt_bvh_export_wide(rt_scene* s, float* nodes, int64_t nodes_capacity, 
   if (nodes_capacity < 0) return set_error(RT_ERR_INVALID_ARG, "rt_bvh_export_wide: negative capacity");
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_error(e, "rt_bvh_export_wide");
-  if (n_nodes) *n_nodes = 0;
-  int n = (int)s->n_prims;
-  if (n == 0) return RT_OK;
-  BuildScratch b;
-  rt_status rs = carve(s, n, b);
-  if (rs) return rs;
-  int built = 0;
-  e = cudaMemcpy(&built, b.c4, 4, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_error(e, "rt_bvh_export_wide count");
-  built = std::min<int>(built, (int)s->n_nodes4);
-  if (n_nodes) *n_nodes = built;
-  if (nodes) {
-    int64_t cnt = std::min<int64_t>(nodes_capacity, built);
+  int64_t slots = s->n_prims > 0 ? s->n_nodes4 : 0;
+  if (n_nodes) *n_nodes = slots;
+  if (nodes && slots > 0) {
+    int64_t cnt = std::min<int64_t>(nodes_capacity, slots);
     e = cudaMemcpy(nodes, s->nodes4.p, (size_t)cnt * 128, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "rt_bvh_export_wide nodes");
   }

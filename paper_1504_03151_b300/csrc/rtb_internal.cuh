@@ -79,7 +79,7 @@ __host__ __device__ inline int leaf_count(int link) { return ((~link) & 7) + 1; 
 // Everything a traversal kernel needs, by value.
 struct DevScene {
   const float4* prims;      // 3 per primitive, leaf order (BVH) or id order
-  const float4* nodes;      // 4-wide nodes, 8 float4 each; the root is node 0
+  const float4* nodes;      // 4-wide nodes, 8 float4 each, one per binary node slot
   const float4* mats;       // 3 per material
   const float4* lights;     // 2 per light
   int n_prims;
@@ -117,7 +117,7 @@ struct rt_scene {
   int root = -1;
   int64_t n_nodes_total = 0;     // slots in `nodes` (LBVH internal + top nodes)
   rtb::Buf nodes;
-  rtb::Buf nodes4;               // 4-wide traversal layout (root 0)
+  rtb::Buf nodes4;               // 4-wide traversal layout, indexed like the binary nodes
   int64_t n_nodes4 = 0;
   rtb::Buf build_tmp;            // scratch for the build, carved below
   size_t build_tmp_n = 0;

@@ -96,7 +96,7 @@ DevScene dev_scene(const rt_scene* s, bool use_bvh) {
   d.n_prims = (int)s->n_prims;
   d.n_lights = (int)s->n_lights;
   d.n_nodes = (int)s->n_nodes4;
-  d.root = use_bvh && s->root >= 0 ? 0 : -1;
+  d.root = use_bvh ? s->root : -1;
   d.use_bvh = use_bvh ? 1 : 0;
   d.traversal_cap = 0;
   d.status = s->status;

@@ -293,9 +293,9 @@ def _binary_leaves(nodes, root):
 
 @pytest.mark.parametrize("which", ["single", "spheres8", "terrain_small", "terrain"])
 def test_wide_bvh_structure(which):
-    """The 4-wide tree the kernels walk: a tree over the binary tree's leaves
-    (same leaves, each reached once), 2-4 used slots a node (one for a
-    single primitive), unused slots
+    """The 4-wide tree the kernels walk, from the binary root: a tree over
+    the binary tree's leaves (same leaves, each reached once), 2-4 used
+    slots a node (one for a single primitive), unused slots
     empty, every box holding what lies below it."""
     sc = {"single": lambda: S.single_sphere(width=8, height=8), "spheres8": S.scene_spheres8,
           "terrain_small": small_terrain, "terrain": S.scene_terrain}[which]()
@@ -305,20 +305,15 @@ def test_wide_bvh_structure(which):
     bnodes, order, _ = rtb.rt_bvh_export(scene.handle, n, 2 * max(n, 2))
     wide = rtb.rt_bvh_export_wide(scene.handle)
     scene.close()
-    assert 1 <= len(wide) <= max(info["n_nodes"], 1)
+    assert len(wide) >= max(info["n_nodes"], 1)
     box_lo = np.stack([wide[:, 0:4], wide[:, 8:12], wide[:, 16:20]], 2).astype(np.float64)    # (node, slot, axis)
     box_hi = np.stack([wide[:, 4:8], wide[:, 12:16], wide[:, 20:24]], 2).astype(np.float64)
     links = wide[:, 24:28].view(np.int32)
     used = wide[:, 28:29].view(np.int32)[:, 0]
-    assert ((used >= (1 if n == 1 else 2)) & (used <= 4)).all()
-    empty = np.arange(4)[None, :] >= used[:, None]
-    assert (links[empty] == np.iinfo(np.int32).min).all()
-    assert np.isposinf(box_lo[empty]).all() and np.isneginf(box_hi[empty]).all()
-    assert (links[~empty] != np.iinfo(np.int32).min).all()
     plo, phi = _prim_boxes(sc)
     visited = np.zeros(len(wide), np.int64)
     leaves = []
-    stack, depth = [(0, 0)], 0
+    stack, depth = [(info["root"], 0)], 0
     while stack:
         node, d = stack.pop()
         visited[node] += 1
@@ -335,7 +330,14 @@ def test_wide_bvh_structure(which):
                 k = int(used[link])
                 assert (box_lo[link, :k] >= lo_c).all() and (box_hi[link, :k] <= hi_c).all()
                 stack.append((link, d + 1))
-    assert (visited == 1).all()
+    assert visited.max() == 1 and 1 <= visited.sum() <= max(info["n_nodes"], 1)
+    r = visited == 1   # the reachable nodes
+    assert ((used[r] >= (1 if n == 1 else 2)) & (used[r] <= 4)).all()
+    empty = (np.arange(4)[None, :] >= used[:, None]) & r[:, None]
+    full = (np.arange(4)[None, :] < used[:, None]) & r[:, None]
+    assert (links[empty] == np.iinfo(np.int32).min).all()
+    assert np.isposinf(box_lo[empty]).all() and np.isneginf(box_hi[empty]).all()
+    assert (links[full] != np.iinfo(np.int32).min).all()
     assert len(leaves) == len(set(leaves))
     assert set(leaves) == _binary_leaves(bnodes, info["root"])
     assert depth <= info["max_depth"]
