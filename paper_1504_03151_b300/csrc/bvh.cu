@@ -660,6 +660,189 @@ __device__ __forceinline__ int bin_of(float c, float lo, float ext) {
   return min(max(bi, 0), kTopBins - 1);
 }
 
+// Split of a segment of at most 256 clusters, one cluster per thread, held
+// in registers from one load: the same bins, SAH costs, choice and stable
+// partition as the general path below, with fewer passes and barriers.
+// Returns the number of clusters on the left side.
+__device__ __forceinline__ int split_small(int level, int b, int e, const int* ids_in, int* ids_out,
+                                           const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
+                                           float4 side_lo[2], float4 side_hi[2]) {
+  __shared__ int s_cb[6];
+  __shared__ int s_cnt[3][kTopBins];
+  __shared__ int s_blo[3][kTopBins][3], s_bhi[3][kTopBins][3];
+  __shared__ float s_cost[3 * (kTopBins - 1)];
+  __shared__ int s_best;
+  __shared__ int s_wl[8], s_wr[8];
+  __shared__ int s_box[2][6];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, m = e - b;
+  const bool mine = t < m;
+  int c = 0;
+  float4 lo = make_float4(0, 0, 0, 0), hi = make_float4(0, 0, 0, 0);
+  if (mine) {
+    c = __ldcg(&ids_in[b + t]);
+    lo = clu_lo[c];
+    hi = clu_hi[c];
+  }
+  float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+  if (t < 6) {
+    s_cb[t] = f2o(t < 3 ? INFINITY : -INFINITY);
+    s_box[0][t] = f2o(t < 3 ? INFINITY : -INFINITY);
+    s_box[1][t] = f2o(t < 3 ? INFINITY : -INFINITY);
+  }
+  if (t < 3 * kTopBins) {
+    int a = t / kTopBins, k = t % kTopBins;
+    s_cnt[a][k] = 0;
+    for (int q = 0; q < 3; ++q) {
+      s_blo[a][k][q] = f2o(INFINITY);
+      s_bhi[a][k][q] = f2o(-INFINITY);
+    }
+  }
+  // centroid bounds: warp reduction, one atomic per warp and axis
+  float cmin[3], cmax[3];
+  for (int a = 0; a < 3; ++a) {
+    cmin[a] = mine ? cc[a] : INFINITY;
+    cmax[a] = mine ? cc[a] : -INFINITY;
+    for (int o = 16; o > 0; o >>= 1) {
+      cmin[a] = fminf(cmin[a], __shfl_xor_sync(0xffffffffu, cmin[a], o));
+      cmax[a] = fmaxf(cmax[a], __shfl_xor_sync(0xffffffffu, cmax[a], o));
+    }
+  }
+  __syncthreads();
+  if (lane == 0 && cmin[0] <= cmax[0]) {
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(&s_cb[a], f2o(cmin[a]));
+      atomicMax(&s_cb[a + 3], f2o(cmax[a]));
+    }
+  }
+  __syncthreads();
+  const float clo[3] = {o2f(s_cb[0]), o2f(s_cb[1]), o2f(s_cb[2])};
+  const float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
+  int bin[3];
+  const float lo3[3] = {lo.x, lo.y, lo.z}, hi3[3] = {hi.x, hi.y, hi.z};
+  for (int a = 0; a < 3; ++a) {
+    bin[a] = bin_of(cc[a], clo[a], cext[a]);
+    if (mine) {
+      atomicAdd(&s_cnt[a][bin[a]], (int)lo.w);
+      for (int q = 0; q < 3; ++q) {
+        atomicMin(&s_blo[a][bin[a]][q], f2o(lo3[q]));
+        atomicMax(&s_bhi[a][bin[a]][q], f2o(hi3[q]));
+      }
+    }
+  }
+  __syncthreads();
+  if (t < 3 * (kTopBins - 1)) {
+    int a = t / (kTopBins - 1), sp = t % (kTopBins - 1);
+    float l0[3] = {INFINITY, INFINITY, INFINITY}, l1[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float r0[3] = {INFINITY, INFINITY, INFINITY}, r1[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int nl = 0, nr = 0;
+    for (int k = 0; k < kTopBins; ++k) {
+      int cnt = s_cnt[a][k];
+      if (cnt == 0) continue;
+      bool lft = k <= sp;
+      if (lft) nl += cnt;
+      else nr += cnt;
+      for (int q = 0; q < 3; ++q) {
+        float blo = o2f(s_blo[a][k][q]), bhi = o2f(s_bhi[a][k][q]);
+        if (lft) {
+          l0[q] = fminf(l0[q], blo);
+          l1[q] = fmaxf(l1[q], bhi);
+        } else {
+          r0[q] = fminf(r0[q], blo);
+          r1[q] = fmaxf(r1[q], bhi);
+        }
+      }
+    }
+    float cost = INFINITY;
+    if (nl > 0 && nr > 0) {
+      float AL = area(make_float4(l0[0], l0[1], l0[2], 0), make_float4(l1[0], l1[1], l1[2], 0));
+      float AR = area(make_float4(r0[0], r0[1], r0[2], 0), make_float4(r1[0], r1[1], r1[2], 0));
+      cost = AL * (float)nl + AR * (float)nr;
+    }
+    s_cost[t] = cost;
+  }
+  __syncthreads();
+  if (w == 0) {
+    // the cheapest plane, ties to the lower index (as a serial scan would pick)
+    float bc = INFINITY;
+    int bk = -1;
+    for (int k = lane; k < 3 * (kTopBins - 1); k += 32) {
+      if (s_cost[k] < bc) {
+        bc = s_cost[k];
+        bk = k;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      float oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      if (oc < bc || (oc == bc && ok >= 0 && (bk < 0 || ok < bk))) {
+        bc = oc;
+        bk = ok;
+      }
+    }
+    if (lane == 0) s_best = (bk < 0 || level >= kTopForceMedian) ? -1 : bk;
+  }
+  __syncthreads();
+  const int best = s_best;
+  bool left;
+  if (best < 0) {
+    left = t < m / 2;   // split at the middle, order kept
+  } else {
+    const int ax = best / (kTopBins - 1), sb = best % (kTopBins - 1);
+    left = bin[ax] <= sb;
+  }
+  const unsigned bl = __ballot_sync(0xffffffffu, mine && left), br = __ballot_sync(0xffffffffu, mine && !left);
+  if (lane == 0) {
+    s_wl[w] = __popc(bl);
+    s_wr[w] = __popc(br);
+  }
+  __syncthreads();
+  int before_l = 0, before_r = 0, nleft = 0;
+  for (int q = 0; q < 8; ++q) {
+    if (q < w) {
+      before_l += s_wl[q];
+      before_r += s_wr[q];
+    }
+    nleft += s_wl[q];
+  }
+  if (nleft == 0 || nleft == m) {
+    // not reachable with a finite SAH cost; keep a valid split at the middle
+    nleft = m / 2;
+    left = t < nleft;
+    before_l = min(w * 32, nleft);
+    before_r = max(w * 32 - nleft, 0);
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  {
+    const unsigned bl2 = __ballot_sync(0xffffffffu, mine && left), br2 = __ballot_sync(0xffffffffu, mine && !left);
+    if (mine) {
+      int pos = left ? b + before_l + __popc(bl2 & lt) : b + nleft + before_r + __popc(br2 & lt);
+      ids_out[pos] = c;
+    }
+  }
+  // the two sides' boxes
+  for (int side = 0; side < 2; ++side) {
+    bool in = mine && (left == (side == 0));
+    float v[6] = {in ? lo.x : INFINITY, in ? lo.y : INFINITY, in ? lo.z : INFINITY,
+                  in ? hi.x : -INFINITY, in ? hi.y : -INFINITY, in ? hi.z : -INFINITY};
+    for (int o = 16; o > 0; o >>= 1) {
+      for (int q = 0; q < 3; ++q) v[q] = fminf(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+      for (int q = 3; q < 6; ++q) v[q] = fmaxf(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+    }
+    if (lane == 0 && v[0] <= v[3]) {
+      for (int q = 0; q < 3; ++q) {
+        atomicMin(&s_box[side][q], f2o(v[q]));
+        atomicMax(&s_box[side][q + 3], f2o(v[q + 3]));
+      }
+    }
+  }
+  __syncthreads();
+  for (int side = 0; side < 2; ++side) {
+    side_lo[side] = make_float4(o2f(s_box[side][0]), o2f(s_box[side][1]), o2f(s_box[side][2]), 0.f);
+    side_hi[side] = make_float4(o2f(s_box[side][3]), o2f(s_box[side][4]), o2f(s_box[side][5]), 0.f);
+  }
+  return nleft;
+}
+
 // One block (256 threads) per active segment of this level: binned SAH
 // split (16 bins per axis, cost A_L N_L + A_R N_R with N in primitives),
 // stable partition of the cluster ids, then the two children are emitted:
@@ -685,188 +868,197 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
     int4 sg = __ldcg(&seg_in[sidx]);
     int b = sg.x, e = sg.y, node = sg.w;
     int m = e - b;
-    if (t < 6) {
-      s_cb[t] = f2o(t < 3 ? INFINITY : -INFINITY);
-      s_box[0][t] = f2o(t < 3 ? INFINITY : -INFINITY);
-      s_box[1][t] = f2o(t < 3 ? INFINITY : -INFINITY);
-    }
-    if (t < 3 * kTopBins) {
-      int a = t / kTopBins, k = t % kTopBins;
-      bin_count[a][k] = 0;
-      for (int q = 0; q < 3; ++q) {
-        bin_lo[a][k][q] = f2o(INFINITY);
-        bin_hi[a][k][q] = f2o(-INFINITY);
-      }
-    }
-    __syncthreads();
-    // centroid bounds of the segment
-    float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int k = b + t; k < e; k += 256) {
-      int c = __ldcg(&ids_in[k]);
-      float4 lo = clu_lo[c], hi = clu_hi[c];
-      float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
-      for (int a = 0; a < 3; ++a) {
-        cmin[a] = fminf(cmin[a], cc[a]);
-        cmax[a] = fmaxf(cmax[a], cc[a]);
-      }
-    }
-    for (int a = 0; a < 3; ++a) {
-      if (cmin[a] <= cmax[a]) {
-        atomicMin(&s_cb[a], f2o(cmin[a]));
-        atomicMax(&s_cb[a + 3], f2o(cmax[a]));
-      }
-    }
-    __syncthreads();
-    float clo[3] = {o2f(s_cb[0]), o2f(s_cb[1]), o2f(s_cb[2])};
-    float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
-    // bin every axis
-    for (int k = b + t; k < e; k += 256) {
-      int c = __ldcg(&ids_in[k]);
-      float4 lo = clu_lo[c], hi = clu_hi[c];
-      float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
-      float lo3[3] = {lo.x, lo.y, lo.z}, hi3[3] = {hi.x, hi.y, hi.z};
-      for (int a = 0; a < 3; ++a) {
-        int bi = bin_of(cc[a], clo[a], cext[a]);
-        atomicAdd(&bin_count[a][bi], (int)lo.w);
-        for (int q = 0; q < 3; ++q) {
-          atomicMin(&bin_lo[a][bi][q], f2o(lo3[q]));
-          atomicMax(&bin_hi[a][bi][q], f2o(hi3[q]));
-        }
-      }
-    }
-    __syncthreads();
-    // SAH of every split plane (one thread per plane)
-    if (t < 3 * (kTopBins - 1)) {
-      int a = t / (kTopBins - 1), sp = t % (kTopBins - 1);
-      float l0[3] = {INFINITY, INFINITY, INFINITY}, l1[3] = {-INFINITY, -INFINITY, -INFINITY};
-      float r0[3] = {INFINITY, INFINITY, INFINITY}, r1[3] = {-INFINITY, -INFINITY, -INFINITY};
-      int nl = 0, nr = 0;
-      for (int k = 0; k < kTopBins; ++k) {
-        int cnt = bin_count[a][k];
-        if (cnt == 0) continue;
-        bool lft = k <= sp;
-        if (lft) nl += cnt;
-        else nr += cnt;
-        for (int q = 0; q < 3; ++q) {
-          float blo = o2f(bin_lo[a][k][q]), bhi = o2f(bin_hi[a][k][q]);
-          if (lft) {
-            l0[q] = fminf(l0[q], blo);
-            l1[q] = fmaxf(l1[q], bhi);
-          } else {
-            r0[q] = fminf(r0[q], blo);
-            r1[q] = fmaxf(r1[q], bhi);
-          }
-        }
-      }
-      float cost = INFINITY;
-      if (nl > 0 && nr > 0) {
-        float AL = area(make_float4(l0[0], l0[1], l0[2], 0), make_float4(l1[0], l1[1], l1[2], 0));
-        float AR = area(make_float4(r0[0], r0[1], r0[2], 0), make_float4(r1[0], r1[1], r1[2], 0));
-        cost = AL * (float)nl + AR * (float)nr;
-      }
-      s_cost[t] = cost;
-    }
-    __syncthreads();
-    if (t == 0) {
-      int best = -1;
-      float bc = INFINITY;
-      for (int k = 0; k < 3 * (kTopBins - 1); ++k)
-        if (s_cost[k] < bc) {
-          bc = s_cost[k];
-          best = k;
-        }
-      if (best < 0 || level >= kTopForceMedian) {
-        s_split_axis = -1;   // split the segment at its middle
-        s_split_bin = 0;
-      } else {
-        s_split_axis = best / (kTopBins - 1);
-        s_split_bin = best % (kTopBins - 1);
-      }
-    }
-    __syncthreads();
-    int ax = s_split_axis, sb = s_split_bin;
-    // stable partition into ids_out[b, e): left side ascending from b,
-    // right side descending from e-1, then the right side is reversed
-    int nleft = m / 2;
-    if (ax < 0) {
-      for (int k = b + t; k < e; k += 256) ids_out[k] = __ldcg(&ids_in[k]);
+    float4 slo[2], shi[2];
+    int nleft;
+    if (m <= 256) {
+      nleft = split_small(level, b, e, ids_in, ids_out, clu_lo, clu_hi, slo, shi);
     } else {
-      int run_l = 0, run_r = 0;
-      for (int k0 = b; k0 < e; k0 += 256) {
-        int k = k0 + t;
-        bool valid = k < e;
-        int c = valid ? __ldcg(&ids_in[k]) : 0;
-        bool left = false;
-        if (valid) {
-          float4 lo = clu_lo[c], hi = clu_hi[c];
-          float cl = ax == 0 ? lo.x : (ax == 1 ? lo.y : lo.z);
-          float ch = ax == 0 ? hi.x : (ax == 1 ? hi.y : hi.z);
-          left = bin_of(0.5f * (cl + ch), clo[ax], cext[ax]) <= sb;
-        }
-        unsigned bl = __ballot_sync(0xffffffffu, left);
-        unsigned br = __ballot_sync(0xffffffffu, valid && !left);
-        if (lane == 0) s_wcount[w] = __popc(bl) | (__popc(br) << 16);
-        __syncthreads();
-        int before_l = 0, before_r = 0, chunk_l = 0, chunk_r = 0;
-        for (int q = 0; q < 8; ++q) {
-          int v = s_wcount[q];
-          if (q < w) {
-            before_l += v & 0xffff;
-            before_r += v >> 16;
-          }
-          chunk_l += v & 0xffff;
-          chunk_r += v >> 16;
-        }
-        unsigned lt = (1u << lane) - 1u;
-        if (valid && left) ids_out[b + run_l + before_l + __popc(bl & lt)] = c;
-        if (valid && !left) ids_out[e - 1 - (run_r + before_r + __popc(br & lt))] = c;
-        run_l += chunk_l;
-        run_r += chunk_r;
-        __syncthreads();
+      if (t < 6) {
+        s_cb[t] = f2o(t < 3 ? INFINITY : -INFINITY);
+        s_box[0][t] = f2o(t < 3 ? INFINITY : -INFINITY);
+        s_box[1][t] = f2o(t < 3 ? INFINITY : -INFINITY);
       }
-      nleft = run_l;
-      int nr = m - nleft;
-      for (int k = t; k < nr / 2; k += 256) {
-        int x = ids_out[b + nleft + k];
-        ids_out[b + nleft + k] = ids_out[e - 1 - k];
-        ids_out[e - 1 - k] = x;
-      }
-      if (nleft == 0 || nleft == m) {   // not reachable with a finite SAH cost; keep a valid split
-        __syncthreads();
-        for (int k = b + t; k < e; k += 256) ids_out[k] = __ldcg(&ids_in[k]);
-        nleft = m / 2;
-      }
-    }
-    __syncthreads();
-    // boxes of the two sides
-    {
-      float lo[2][3] = {{INFINITY, INFINITY, INFINITY}, {INFINITY, INFINITY, INFINITY}};
-      float hi[2][3] = {{-INFINITY, -INFINITY, -INFINITY}, {-INFINITY, -INFINITY, -INFINITY}};
-      for (int k = b + t; k < e; k += 256) {
-        int c = ids_out[k];
-        int side = k < b + nleft ? 0 : 1;
-        float4 a = clu_lo[c], h = clu_hi[c];
-        lo[side][0] = fminf(lo[side][0], a.x);
-        lo[side][1] = fminf(lo[side][1], a.y);
-        lo[side][2] = fminf(lo[side][2], a.z);
-        hi[side][0] = fmaxf(hi[side][0], h.x);
-        hi[side][1] = fmaxf(hi[side][1], h.y);
-        hi[side][2] = fmaxf(hi[side][2], h.z);
-      }
-      for (int side = 0; side < 2; ++side)
+      if (t < 3 * kTopBins) {
+        int a = t / kTopBins, k = t % kTopBins;
+        bin_count[a][k] = 0;
         for (int q = 0; q < 3; ++q) {
-          if (lo[side][q] <= hi[side][q]) {
-            atomicMin(&s_box[side][q], f2o(lo[side][q]));
-            atomicMax(&s_box[side][q + 3], f2o(hi[side][q]));
+          bin_lo[a][k][q] = f2o(INFINITY);
+          bin_hi[a][k][q] = f2o(-INFINITY);
+        }
+      }
+      __syncthreads();
+      // centroid bounds of the segment
+      float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int k = b + t; k < e; k += 256) {
+        int c = __ldcg(&ids_in[k]);
+        float4 lo = clu_lo[c], hi = clu_hi[c];
+        float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+        for (int a = 0; a < 3; ++a) {
+          cmin[a] = fminf(cmin[a], cc[a]);
+          cmax[a] = fmaxf(cmax[a], cc[a]);
+        }
+      }
+      for (int a = 0; a < 3; ++a) {
+        if (cmin[a] <= cmax[a]) {
+          atomicMin(&s_cb[a], f2o(cmin[a]));
+          atomicMax(&s_cb[a + 3], f2o(cmax[a]));
+        }
+      }
+      __syncthreads();
+      float clo[3] = {o2f(s_cb[0]), o2f(s_cb[1]), o2f(s_cb[2])};
+      float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
+      // bin every axis
+      for (int k = b + t; k < e; k += 256) {
+        int c = __ldcg(&ids_in[k]);
+        float4 lo = clu_lo[c], hi = clu_hi[c];
+        float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+        float lo3[3] = {lo.x, lo.y, lo.z}, hi3[3] = {hi.x, hi.y, hi.z};
+        for (int a = 0; a < 3; ++a) {
+          int bi = bin_of(cc[a], clo[a], cext[a]);
+          atomicAdd(&bin_count[a][bi], (int)lo.w);
+          for (int q = 0; q < 3; ++q) {
+            atomicMin(&bin_lo[a][bi][q], f2o(lo3[q]));
+            atomicMax(&bin_hi[a][bi][q], f2o(hi3[q]));
           }
         }
+      }
+      __syncthreads();
+      // SAH of every split plane (one thread per plane)
+      if (t < 3 * (kTopBins - 1)) {
+        int a = t / (kTopBins - 1), sp = t % (kTopBins - 1);
+        float l0[3] = {INFINITY, INFINITY, INFINITY}, l1[3] = {-INFINITY, -INFINITY, -INFINITY};
+        float r0[3] = {INFINITY, INFINITY, INFINITY}, r1[3] = {-INFINITY, -INFINITY, -INFINITY};
+        int nl = 0, nr = 0;
+        for (int k = 0; k < kTopBins; ++k) {
+          int cnt = bin_count[a][k];
+          if (cnt == 0) continue;
+          bool lft = k <= sp;
+          if (lft) nl += cnt;
+          else nr += cnt;
+          for (int q = 0; q < 3; ++q) {
+            float blo = o2f(bin_lo[a][k][q]), bhi = o2f(bin_hi[a][k][q]);
+            if (lft) {
+              l0[q] = fminf(l0[q], blo);
+              l1[q] = fmaxf(l1[q], bhi);
+            } else {
+              r0[q] = fminf(r0[q], blo);
+              r1[q] = fmaxf(r1[q], bhi);
+            }
+          }
+        }
+        float cost = INFINITY;
+        if (nl > 0 && nr > 0) {
+          float AL = area(make_float4(l0[0], l0[1], l0[2], 0), make_float4(l1[0], l1[1], l1[2], 0));
+          float AR = area(make_float4(r0[0], r0[1], r0[2], 0), make_float4(r1[0], r1[1], r1[2], 0));
+          cost = AL * (float)nl + AR * (float)nr;
+        }
+        s_cost[t] = cost;
+      }
+      __syncthreads();
+      if (t == 0) {
+        int best = -1;
+        float bc = INFINITY;
+        for (int k = 0; k < 3 * (kTopBins - 1); ++k)
+          if (s_cost[k] < bc) {
+            bc = s_cost[k];
+            best = k;
+          }
+        if (best < 0 || level >= kTopForceMedian) {
+          s_split_axis = -1;   // split the segment at its middle
+          s_split_bin = 0;
+        } else {
+          s_split_axis = best / (kTopBins - 1);
+          s_split_bin = best % (kTopBins - 1);
+        }
+      }
+      __syncthreads();
+      int ax = s_split_axis, sb = s_split_bin;
+      // stable partition into ids_out[b, e): left side ascending from b,
+      // right side descending from e-1, then the right side is reversed
+      nleft = m / 2;
+      if (ax < 0) {
+        for (int k = b + t; k < e; k += 256) ids_out[k] = __ldcg(&ids_in[k]);
+      } else {
+        int run_l = 0, run_r = 0;
+        for (int k0 = b; k0 < e; k0 += 256) {
+          int k = k0 + t;
+          bool valid = k < e;
+          int c = valid ? __ldcg(&ids_in[k]) : 0;
+          bool left = false;
+          if (valid) {
+            float4 lo = clu_lo[c], hi = clu_hi[c];
+            float cl = ax == 0 ? lo.x : (ax == 1 ? lo.y : lo.z);
+            float ch = ax == 0 ? hi.x : (ax == 1 ? hi.y : hi.z);
+            left = bin_of(0.5f * (cl + ch), clo[ax], cext[ax]) <= sb;
+          }
+          unsigned bl = __ballot_sync(0xffffffffu, left);
+          unsigned br = __ballot_sync(0xffffffffu, valid && !left);
+          if (lane == 0) s_wcount[w] = __popc(bl) | (__popc(br) << 16);
+          __syncthreads();
+          int before_l = 0, before_r = 0, chunk_l = 0, chunk_r = 0;
+          for (int q = 0; q < 8; ++q) {
+            int v = s_wcount[q];
+            if (q < w) {
+              before_l += v & 0xffff;
+              before_r += v >> 16;
+            }
+            chunk_l += v & 0xffff;
+            chunk_r += v >> 16;
+          }
+          unsigned lt = (1u << lane) - 1u;
+          if (valid && left) ids_out[b + run_l + before_l + __popc(bl & lt)] = c;
+          if (valid && !left) ids_out[e - 1 - (run_r + before_r + __popc(br & lt))] = c;
+          run_l += chunk_l;
+          run_r += chunk_r;
+          __syncthreads();
+        }
+        nleft = run_l;
+        int nr = m - nleft;
+        for (int k = t; k < nr / 2; k += 256) {
+          int x = ids_out[b + nleft + k];
+          ids_out[b + nleft + k] = ids_out[e - 1 - k];
+          ids_out[e - 1 - k] = x;
+        }
+        if (nleft == 0 || nleft == m) {   // not reachable with a finite SAH cost; keep a valid split
+          __syncthreads();
+          for (int k = b + t; k < e; k += 256) ids_out[k] = __ldcg(&ids_in[k]);
+          nleft = m / 2;
+        }
+      }
+      __syncthreads();
+      // boxes of the two sides
+      {
+        float lo[2][3] = {{INFINITY, INFINITY, INFINITY}, {INFINITY, INFINITY, INFINITY}};
+        float hi[2][3] = {{-INFINITY, -INFINITY, -INFINITY}, {-INFINITY, -INFINITY, -INFINITY}};
+        for (int k = b + t; k < e; k += 256) {
+          int c = ids_out[k];
+          int side = k < b + nleft ? 0 : 1;
+          float4 a = clu_lo[c], h = clu_hi[c];
+          lo[side][0] = fminf(lo[side][0], a.x);
+          lo[side][1] = fminf(lo[side][1], a.y);
+          lo[side][2] = fminf(lo[side][2], a.z);
+          hi[side][0] = fmaxf(hi[side][0], h.x);
+          hi[side][1] = fmaxf(hi[side][1], h.y);
+          hi[side][2] = fmaxf(hi[side][2], h.z);
+        }
+        for (int side = 0; side < 2; ++side)
+          for (int q = 0; q < 3; ++q) {
+            if (lo[side][q] <= hi[side][q]) {
+              atomicMin(&s_box[side][q], f2o(lo[side][q]));
+              atomicMax(&s_box[side][q + 3], f2o(hi[side][q]));
+            }
+          }
+      }
+      __syncthreads();
+      for (int side = 0; side < 2; ++side) {
+        slo[side] = make_float4(o2f(s_box[side][0]), o2f(s_box[side][1]), o2f(s_box[side][2]), 0.f);
+        shi[side] = make_float4(o2f(s_box[side][3]), o2f(s_box[side][4]), o2f(s_box[side][5]), 0.f);
+      }
     }
-    __syncthreads();
     if (t < 2) {
       int cb = t == 0 ? b : b + nleft;
       int ce = t == 0 ? b + nleft : e;
-      float4 lo = make_float4(o2f(s_box[t][0]), o2f(s_box[t][1]), o2f(s_box[t][2]), 0.f);
-      float4 hi = make_float4(o2f(s_box[t][3]), o2f(s_box[t][4]), o2f(s_box[t][5]), 0.f);
+      float4 lo = slo[t], hi = shi[t];
       int link;
       if (ce - cb == 1) {
         int c = ids_out[cb];
