@@ -22,6 +22,8 @@ constexpr int kSortCoopMaxBlocks = 1024;   // grid of the single-launch sort (co
 constexpr int kSortCoopMaxKeys = 1 << 22;  // larger inputs take the multi-launch sort
 constexpr int kTopBins = 16;        // SAH bins per axis for the top-level rebuild
 constexpr int kTopMaxLevels = 64;   // launches of the level kernel (empty ones return at once)
+constexpr int kTopCache = 4096;     // clusters of one segment held in shared memory (36 B each)
+constexpr int kTopWarpSeg = 32;     // segments of at most this many clusters are finished by one warp
 constexpr int kTopForceMedian = 32; // from this level on, split segments at the middle: with at
                                     // most 2^28 clusters every segment is done by level 60
 
@@ -53,10 +55,9 @@ struct BuildScratch {
   int* clu_link;                 // per cluster: its link (internal LBVH node or leaf link)
   float4 *clu_lo, *clu_hi;       // per cluster box; lo.w = prim count; hi.w = height
   int4 *seg_a, *seg_b;           // active segments: (begin, end, parent slot, node id)
-  int* seg_count;                // [kTopMaxLevels + 1]
+  int* seg_count;                // [level] segments; [kTopMaxLevels + 1] clusters; [kTopMaxLevels + 2] small segments
   int* top_count;
-  float4 *top_lo, *top_hi;       // boxes of top nodes (for their parent's child box)
-  int* top_height;
+  int4* small_seg;               // segments of <= kTopWarpSeg clusters: (begin, end, top node, level)
   BuildInfo* info;
 };
 
@@ -854,7 +855,7 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
                                                int4* seg_out, int* seg_count_out, const int* ids_in, int* ids_out,
                                                const int* __restrict__ clu_link, const float4* __restrict__ clu_lo,
                                                const float4* __restrict__ clu_hi, int* top_count, float4* nodes,
-                                               BuildInfo* info) {
+                                               BuildInfo* info, int4* small_seg, int* small_count, int cache_cap) {
   __shared__ int s_cb[6];
   __shared__ int bin_count[3][kTopBins];
   __shared__ int bin_lo[3][kTopBins][3], bin_hi[3][kTopBins][3];
@@ -873,6 +874,32 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
     if (m <= 256) {
       nleft = split_small(level, b, e, ids_in, ids_out, clu_lo, clu_hi, slo, shi);
     } else {
+      // a segment of up to cache_cap clusters is read once into shared memory
+      extern __shared__ float4 s_dyn[];
+      float4* c_lo = s_dyn;
+      float4* c_hi = s_dyn + cache_cap;
+      int* c_id = (int*)(s_dyn + 2 * (size_t)cache_cap);
+      const bool cached = m <= cache_cap;
+      if (cached) {
+        for (int k = t; k < m; k += 256) c_id[k] = __ldcg(&ids_in[b + k]);
+        __syncthreads();
+        for (int k = t; k < m; k += 256) {
+          int c = c_id[k];
+          c_lo[k] = clu_lo[c];
+          c_hi[k] = clu_hi[c];
+        }
+      }
+      auto fetch = [&](int k, int& c, float4& lo, float4& hi) {
+        if (cached) {
+          c = c_id[k - b];
+          lo = c_lo[k - b];
+          hi = c_hi[k - b];
+        } else {
+          c = __ldcg(&ids_in[k]);
+          lo = clu_lo[c];
+          hi = clu_hi[c];
+        }
+      };
       if (t < 6) {
         s_cb[t] = f2o(t < 3 ? INFINITY : -INFINITY);
         s_box[0][t] = f2o(t < 3 ? INFINITY : -INFINITY);
@@ -890,8 +917,9 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
       // centroid bounds of the segment
       float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
       for (int k = b + t; k < e; k += 256) {
-        int c = __ldcg(&ids_in[k]);
-        float4 lo = clu_lo[c], hi = clu_hi[c];
+        int c;
+        float4 lo, hi;
+        fetch(k, c, lo, hi);
         float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
         for (int a = 0; a < 3; ++a) {
           cmin[a] = fminf(cmin[a], cc[a]);
@@ -909,8 +937,9 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
       float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
       // bin every axis
       for (int k = b + t; k < e; k += 256) {
-        int c = __ldcg(&ids_in[k]);
-        float4 lo = clu_lo[c], hi = clu_hi[c];
+        int c;
+        float4 lo, hi;
+        fetch(k, c, lo, hi);
         float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
         float lo3[3] = {lo.x, lo.y, lo.z}, hi3[3] = {hi.x, hi.y, hi.z};
         for (int a = 0; a < 3; ++a) {
@@ -976,17 +1005,24 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
       // stable partition into ids_out[b, e): left side ascending from b,
       // right side descending from e-1, then the right side is reversed
       nleft = m / 2;
+      bool by_position = ax < 0;   // sides by position (a split at the middle)
       if (ax < 0) {
-        for (int k = b + t; k < e; k += 256) ids_out[k] = __ldcg(&ids_in[k]);
+        for (int k = b + t; k < e; k += 256) {
+          int c;
+          float4 lo, hi;
+          fetch(k, c, lo, hi);
+          ids_out[k] = c;
+        }
       } else {
         int run_l = 0, run_r = 0;
         for (int k0 = b; k0 < e; k0 += 256) {
           int k = k0 + t;
           bool valid = k < e;
-          int c = valid ? __ldcg(&ids_in[k]) : 0;
+          int c = 0;
           bool left = false;
           if (valid) {
-            float4 lo = clu_lo[c], hi = clu_hi[c];
+            float4 lo, hi;
+            fetch(k, c, lo, hi);
             float cl = ax == 0 ? lo.x : (ax == 1 ? lo.y : lo.z);
             float ch = ax == 0 ? hi.x : (ax == 1 ? hi.y : hi.z);
             left = bin_of(0.5f * (cl + ch), clo[ax], cext[ax]) <= sb;
@@ -1021,8 +1057,14 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
         }
         if (nleft == 0 || nleft == m) {   // not reachable with a finite SAH cost; keep a valid split
           __syncthreads();
-          for (int k = b + t; k < e; k += 256) ids_out[k] = __ldcg(&ids_in[k]);
+          for (int k = b + t; k < e; k += 256) {
+            int c;
+            float4 lo, hi;
+            fetch(k, c, lo, hi);
+            ids_out[k] = c;
+          }
           nleft = m / 2;
+          by_position = true;
         }
       }
       __syncthreads();
@@ -1031,9 +1073,17 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
         float lo[2][3] = {{INFINITY, INFINITY, INFINITY}, {INFINITY, INFINITY, INFINITY}};
         float hi[2][3] = {{-INFINITY, -INFINITY, -INFINITY}, {-INFINITY, -INFINITY, -INFINITY}};
         for (int k = b + t; k < e; k += 256) {
-          int c = ids_out[k];
-          int side = k < b + nleft ? 0 : 1;
-          float4 a = clu_lo[c], h = clu_hi[c];
+          int c;
+          float4 a, h;
+          fetch(k, c, a, h);
+          int side;
+          if (by_position) {
+            side = k < b + nleft ? 0 : 1;
+          } else {
+            float cl = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
+            float ch = ax == 0 ? h.x : (ax == 1 ? h.y : h.z);
+            side = bin_of(0.5f * (cl + ch), clo[ax], cext[ax]) <= sb ? 0 : 1;
+          }
           lo[side][0] = fminf(lo[side][0], a.x);
           lo[side][1] = fminf(lo[side][1], a.y);
           lo[side][2] = fminf(lo[side][2], a.z);
@@ -1068,8 +1118,13 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
       } else {
         int child = atomicAdd(top_count, 1);
         link = top_base + child;
-        int slot = atomicAdd(seg_count_out, 1);
-        seg_out[slot] = make_int4(cb, ce, node, child);
+        if (ce - cb <= kTopWarpSeg) {
+          int slot = atomicAdd(small_count, 1);
+          small_seg[slot] = make_int4(cb, ce, child, level + 1);
+        } else {
+          int slot = atomicAdd(seg_count_out, 1);
+          seg_out[slot] = make_int4(cb, ce, node, child);
+        }
         atomicMax(&info->height, level + 2);
       }
       write_child(nodes, top_base + node, t, lo, hi, link);
@@ -1078,14 +1133,193 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
   }
 }
 
+// One warp finishes the subtree of a segment of 2..32 clusters, one cluster
+// a lane, all in registers.  Every round splits all unfinished segments of
+// the warp at once (their lanes are contiguous): per axis, the clusters are
+// ranked by centroid inside their segment, prefix and suffix boxes and
+// primitive counts of that order are scanned, and the cheapest split (SAH:
+// A_L N_L + A_R N_R over every position, not binned; ties to the lower axis
+// and position) is taken; then the lanes are permuted into the two halves.
+__device__ __forceinline__ float box_area7(const float* v) {
+  float dx = v[3] - v[0], dy = v[4] - v[1], dz = v[5] - v[2];
+  if (!(dx >= 0.f) || !(dy >= 0.f) || !(dz >= 0.f)) return 0.f;
+  return 2.f * (dx * dy + dy * dz + dz * dx);
+}
+
+__device__ __forceinline__ float combine7(int q, float a, float b) {
+  return q < 3 ? fminf(a, b) : (q < 6 ? fmaxf(a, b) : a + b);
+}
+
+__device__ void build_small_subtree(int4 item, int top_base, const int* ids, const int* __restrict__ clu_link,
+                                    const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
+                                    int* top_count, float4* nodes, BuildInfo* info, int* s_idx, int* s_c,
+                                    float4* s_lo, float4* s_hi) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int m = item.y - item.x;
+  const bool own = lane < m;
+  int c = own ? __ldcg(&ids[item.x + lane]) : 0;
+  float4 lo = own ? clu_lo[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 hi = own ? clu_hi[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+  // this lane's segment [sb, se) of lanes; lanes without a cluster are finished singletons
+  int sb = own ? 0 : lane, se = own ? m : lane + 1;
+  int node = item.z, level = item.w;
+  for (int round = 0; round < 32; ++round) {
+    const bool act = se - sb >= 2;
+    if (!__any_sync(FULL, act)) break;
+    const float cen[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+    float best = INFINITY;
+    int best_ax = 0, best_k = -1;
+    int rank_ax[3];
+    float bl[7], br[7];
+    for (int a = 0; a < 3; ++a) {
+      int rank = 0;
+      for (int j = 0; j < 32; ++j) {
+        float cj = __shfl_sync(FULL, cen[a], j);
+        rank += (j >= sb && j < se && (cj < cen[a] || (cj == cen[a] && j < lane))) ? 1 : 0;
+      }
+      rank_ax[a] = rank;
+      s_idx[sb + rank] = lane;
+      __syncwarp();
+      const int src = s_idx[lane];
+      __syncwarp();
+      float v[7] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, lo.w};
+      float pre[7], suf[7];
+      for (int q = 0; q < 7; ++q) pre[q] = suf[q] = __shfl_sync(FULL, v[q], src);
+      for (int o = 1; o < 32; o <<= 1) {
+        for (int q = 0; q < 7; ++q) {
+          float x = __shfl_up_sync(FULL, pre[q], o);
+          float y = __shfl_down_sync(FULL, suf[q], o);
+          if (lane - o >= sb) pre[q] = combine7(q, pre[q], x);
+          if (lane + o < se) suf[q] = combine7(q, suf[q], y);
+        }
+      }
+      float right[7];
+      for (int q = 0; q < 7; ++q) right[q] = __shfl_down_sync(FULL, suf[q], 1);   // suffix from the next position
+      const bool valid = act && lane + 1 < se;
+      float cost = valid ? box_area7(pre) * pre[6] + box_area7(right) * right[6] : INFINITY;
+      int pos = lane;
+      for (int o = 1; o < 32; o <<= 1) {
+        float oc = __shfl_up_sync(FULL, cost, o);
+        int op = __shfl_up_sync(FULL, pos, o);
+        if (lane - o >= sb && (oc < cost || (oc == cost && op < pos))) {
+          cost = oc;
+          pos = op;
+        }
+      }
+      const float seg_cost = __shfl_sync(FULL, cost, se - 1);
+      const int seg_pos = __shfl_sync(FULL, pos, se - 1);
+      float cl[7], cr[7];
+      for (int q = 0; q < 7; ++q) {
+        cl[q] = __shfl_sync(FULL, pre[q], seg_pos);
+        cr[q] = __shfl_sync(FULL, right[q], seg_pos);
+      }
+      if (seg_cost < best) {
+        best = seg_cost;
+        best_ax = a;
+        best_k = seg_pos;
+        for (int q = 0; q < 7; ++q) {
+          bl[q] = cl[q];
+          br[q] = cr[q];
+        }
+      }
+    }
+    if (act && best_k < 0) {
+      // no finite cost (not reachable for finite boxes): halves of the x
+      // order under boxes that every ray enters
+      best_ax = 0;
+      best_k = sb + (se - sb) / 2 - 1;
+      for (int q = 0; q < 7; ++q) bl[q] = br[q] = q < 3 ? -INFINITY : INFINITY;
+    }
+    // the lanes in the chosen order: left child [sb, best_k], right child [best_k + 1, se)
+    const int dst = act ? sb + rank_ax[best_ax] : lane;
+    s_c[dst] = c;
+    s_lo[dst] = lo;
+    s_hi[dst] = hi;
+    __syncwarp();
+    c = s_c[lane];
+    lo = s_lo[lane];
+    hi = s_hi[lane];
+    __syncwarp();
+    const int k = act ? best_k : lane;
+    const int c_right = __shfl_sync(FULL, c, min(k + 1, 31));
+    int cnode_l = -1, cnode_r = -1;
+    if (act && lane == sb) {
+      const int nl = k + 1 - sb, nr = se - (k + 1);
+      int link_l, link_r;
+      if (nl == 1) {
+        link_l = clu_link[c];
+        atomicMax(&info->height, level + 1 + __float_as_int(hi.w));
+      } else {
+        cnode_l = atomicAdd(top_count, 1);
+        link_l = top_base + cnode_l;
+        atomicMax(&info->height, level + 2);
+      }
+      if (nr == 1) {
+        link_r = clu_link[c_right];
+        atomicMax(&info->height, level + 1 + __float_as_int(clu_hi[c_right].w));
+      } else {
+        cnode_r = atomicAdd(top_count, 1);
+        link_r = top_base + cnode_r;
+        atomicMax(&info->height, level + 2);
+      }
+      write_child(nodes, top_base + node, 0, make_float4(bl[0], bl[1], bl[2], 0.f),
+                  make_float4(bl[3], bl[4], bl[5], 0.f), link_l);
+      write_child(nodes, top_base + node, 1, make_float4(br[0], br[1], br[2], 0.f),
+                  make_float4(br[3], br[4], br[5], 0.f), link_r);
+    }
+    cnode_l = __shfl_sync(FULL, cnode_l, sb);
+    cnode_r = __shfl_sync(FULL, cnode_r, sb);
+    if (act) {
+      if (lane <= k) {
+        se = k + 1;
+        node = cnode_l;
+      } else {
+        sb = k + 1;
+        node = cnode_r;
+      }
+      ++level;
+    }
+  }
+}
+
+// Every small segment of the top-level rebuild, one warp each.
+__device__ __forceinline__ void top_small_body(const int* seg_count, const int4* small_seg, int top_base,
+                                               const int* clu_a, const int* clu_b, const int* __restrict__ clu_link,
+                                               const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
+                                               int* top_count, float4* nodes, BuildInfo* info) {
+  __shared__ int s_idx[8][32], s_c[8][32];
+  __shared__ float4 s_lo[8][32], s_hi[8][32];
+  const int w = threadIdx.x >> 5;
+  const int n_small = __ldcg(&seg_count[kTopMaxLevels + 2]);
+  const int warps = (int)(gridDim.x * (blockDim.x >> 5));
+  for (int i = (int)(blockIdx.x * (blockDim.x >> 5)) + w; i < n_small; i += warps) {
+    int4 item = __ldcg(&small_seg[i]);
+    // the cluster ids of a level-L segment are in the buffer its parent's split wrote
+    const int* ids = (item.w & 1) ? clu_b : clu_a;
+    build_small_subtree(item, top_base, ids, clu_link, clu_lo, clu_hi, top_count, nodes, info, s_idx[w], s_c[w],
+                        s_lo[w], s_hi[w]);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_top_small(const int* seg_count, const int4* small_seg, int top_base,
+                                                   const int* clu_a, const int* clu_b,
+                                                   const int* __restrict__ clu_link,
+                                                   const float4* __restrict__ clu_lo,
+                                                   const float4* __restrict__ clu_hi, int* top_count, float4* nodes,
+                                                   BuildInfo* info) {
+  top_small_body(seg_count, small_seg, top_base, clu_a, clu_b, clu_link, clu_lo, clu_hi, top_count, nodes, info);
+}
+
 __global__ void __launch_bounds__(256) k_top_level(int level, int top_base, const int* seg_count, const int4* seg_in,
                                                    int4* seg_out, int* seg_count_out, const int* ids_in, int* ids_out,
                                                    const int* __restrict__ clu_link,
                                                    const float4* __restrict__ clu_lo,
                                                    const float4* __restrict__ clu_hi, int* top_count, float4* nodes,
-                                                   BuildInfo* info) {
+                                                   BuildInfo* info, int4* small_seg, int* small_count,
+                                                   int cache_cap) {
   top_level_body(level, top_base, seg_count, seg_in, seg_out, seg_count_out, ids_in, ids_out, clu_link, clu_lo, clu_hi,
-                 top_count, nodes, info);
+                 top_count, nodes, info, small_seg, small_count, cache_cap);
 }
 
 // Every level in one cooperative launch: the blocks meet at a grid-wide
@@ -1093,15 +1327,19 @@ __global__ void __launch_bounds__(256) k_top_level(int level, int top_base, cons
 __global__ void __launch_bounds__(256) k_top_all(int top_base, int* seg_count, int4* seg_a, int4* seg_b, int* clu_a,
                                                  int* clu_b, const int* __restrict__ clu_link,
                                                  const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
-                                                 int* top_count, float4* nodes, BuildInfo* info) {
+                                                 int* top_count, float4* nodes, BuildInfo* info, int4* small_seg,
+                                                 int cache_cap) {
   cg::grid_group grid = cg::this_grid();
   for (int level = 0; level < kTopMaxLevels; ++level) {
     if (__ldcg(&seg_count[level]) == 0) break;   // the same value in every block after the barrier
     bool odd = level & 1;
     top_level_body(level, top_base, seg_count, odd ? seg_b : seg_a, odd ? seg_a : seg_b, seg_count + level + 1,
-                   odd ? clu_b : clu_a, odd ? clu_a : clu_b, clu_link, clu_lo, clu_hi, top_count, nodes, info);
+                   odd ? clu_b : clu_a, odd ? clu_a : clu_b, clu_link, clu_lo, clu_hi, top_count, nodes, info,
+                   small_seg, seg_count + kTopMaxLevels + 2, cache_cap);
     grid.sync();
   }
+  // the small segments, one warp each, with no more barriers
+  top_small_body(seg_count, small_seg, top_base, clu_a, clu_b, clu_link, clu_lo, clu_hi, top_count, nodes, info);
 }
 
 __global__ void k_top_done(const int* __restrict__ top_count, const int* __restrict__ n_clusters, BuildInfo* info,
@@ -1315,11 +1553,9 @@ static rt_status carve(rt_scene* s, int n, BuildScratch& b) {
   sz[k++] = N * 16;  // clu_hi
   sz[k++] = N * 16;  // seg_a
   sz[k++] = N * 16;  // seg_b
-  sz[k++] = (kTopMaxLevels + 2) * 4;
+  sz[k++] = (kTopMaxLevels + 3) * 4;   // seg_count: levels, n_clusters, small segments
   sz[k++] = 16;      // top_count
-  sz[k++] = N * 16;  // top_lo (also SAH scratch)
-  sz[k++] = N * 16;  // top_hi
-  sz[k++] = N * 4;   // top_height
+  sz[k++] = N * 16;  // small_seg
   sz[k++] = sizeof(BuildInfo);
   static_assert(sizeof(sz) / sizeof(sz[0]) >= 34, "scratch region table too small");
   size_t total = 0;
@@ -1360,9 +1596,7 @@ static rt_status carve(rt_scene* s, int n, BuildScratch& b) {
   b.seg_b = (int4*)ptr[q++];
   b.seg_count = (int*)ptr[q++];
   b.top_count = (int*)ptr[q++];
-  b.top_lo = (float4*)ptr[q++];
-  b.top_hi = (float4*)ptr[q++];
-  b.top_height = (int*)ptr[q++];
+  b.small_seg = (int4*)ptr[q++];
   b.info = (BuildInfo*)ptr[q++];
   return RT_OK;
 }
@@ -1438,35 +1672,46 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     // top levels: binned SAH over the Morton clusters
     int top_base = n - 1;
     int* n_clusters_dev = b.seg_count + kTopMaxLevels + 1;
-    cudaMemsetAsync(b.seg_count, 0, (kTopMaxLevels + 2) * 4, st);
+    cudaMemsetAsync(b.seg_count, 0, (kTopMaxLevels + 3) * 4, st);
     // a zeroed top node is harmless to traverse (links to node 0, empty boxes)
     cudaMemsetAsync(nodes + 4 * (size_t)top_base, 0, (size_t)(slots - top_base) * 64, st);
     k_find_clusters<<<grid, tb, 0, st>>>(n, cmax, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo,
                                          b.aabb_hi, n_clusters_dev, b.clu_a, b.clu_link, b.clu_lo, b.clu_hi);
     k_top_init<<<1, 32, 0, st>>>(b.seg_count, b.seg_a, n_clusters_dev, b.top_count, b.info);
     int top_grid = std::max(1, 2 * s->sm_count);
+    // dynamic shared memory: the cluster cache of one segment
+    int cache_cap = kTopCache;
+    const size_t dyn = (size_t)cache_cap * 36;
     static int coop_blocks = -1;
     if (coop_blocks < 0) {
       int coop = 0, per_sm = 0;
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_top_all, 256, 0);
+      cudaFuncSetAttribute(k_top_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      cudaFuncSetAttribute(k_top_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_top_all, 256, dyn);
       coop_blocks = coop ? std::min(per_sm, 2) * s->sm_count : 0;
     }
     bool launched = false;
     if (coop_blocks > 0) {
       int tb_ = top_base;
       void* args[] = {&tb_, &b.seg_count, &b.seg_a, &b.seg_b, &b.clu_a, &b.clu_b, &b.clu_link,
-                      &b.clu_lo, &b.clu_hi, &b.top_count, &nodes, &b.info};
-      launched = cudaLaunchCooperativeKernel((void*)k_top_all, coop_blocks, 256, args, 0, st) == cudaSuccess;
+                      &b.clu_lo, &b.clu_hi, &b.top_count, &nodes, &b.info, &b.small_seg, &cache_cap};
+      launched = cudaLaunchCooperativeKernel((void*)k_top_all, coop_blocks, 256, args, dyn, st) == cudaSuccess;
       if (!launched) cudaGetLastError();
       L += launched ? 1 - kTopMaxLevels : 0;
     }
     for (int level = 0; !launched && level < kTopMaxLevels; ++level) {
       bool odd = level & 1;
-      k_top_level<<<top_grid, 256, 0, st>>>(level, top_base, b.seg_count, odd ? b.seg_b : b.seg_a,
-                                            odd ? b.seg_a : b.seg_b, b.seg_count + level + 1,
-                                            odd ? b.clu_b : b.clu_a, odd ? b.clu_a : b.clu_b, b.clu_link, b.clu_lo,
-                                            b.clu_hi, b.top_count, nodes, b.info);
+      k_top_level<<<top_grid, 256, dyn, st>>>(level, top_base, b.seg_count, odd ? b.seg_b : b.seg_a,
+                                              odd ? b.seg_a : b.seg_b, b.seg_count + level + 1,
+                                              odd ? b.clu_b : b.clu_a, odd ? b.clu_a : b.clu_b, b.clu_link, b.clu_lo,
+                                              b.clu_hi, b.top_count, nodes, b.info, b.small_seg,
+                                              b.seg_count + kTopMaxLevels + 2, cache_cap);
+    }
+    if (!launched) {
+      k_top_small<<<top_grid, 256, 0, st>>>(b.seg_count, b.small_seg, top_base, b.clu_a, b.clu_b, b.clu_link,
+                                            b.clu_lo, b.clu_hi, b.top_count, nodes, b.info);
+      L += 1;
     }
     k_top_done<<<1, 1, 0, st>>>(b.top_count, n_clusters_dev, b.info, top_base);
     L += 5 + kTopMaxLevels;
