@@ -307,6 +307,48 @@ rt_status rt_render_nrc(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int widt
                         float* out_rgb_device, int train, const rt_render_options* opt, rt_render_stats* stats,
                         void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched rendering.  The paper renders one scene at a time; this renders
+ * many scenes of uneven size and resolution in one persistent launch
+ * (replayed from a CUDA graph), each with its own BVH, camera and image.
+ * A warp takes a tile of 32 pixels of one scene and carries every ray it
+ * spawns (shadow rays, reflections, refractions; Sec. IV.A, Alg. 1) to
+ * max_depth depth first, sharing pending rays among its lanes; then it
+ * takes the next tile of any scene.  The image is the one rt_render makes.
+ * ------------------------------------------------------------------------- */
+typedef struct rt_tune {
+  int32_t tile_w, tile_h;   /* pixels of a warp's tile; tile_w * tile_h == 32 */
+  int32_t block_threads;    /* threads a block: 64, 128 or 256 */
+  int32_t blocks_per_sm;    /* persistent grid, blocks per SM; 0 = as many as fit */
+} rt_tune;
+
+typedef struct rt_batch rt_batch;
+
+/* A batch of n >= 1 frames: frame i renders scenes[i] (the same scene may
+ * appear more than once, e.g. several views) seen by cameras[i] at
+ * widths[i] x heights[i] into out_rgb[i] (caller-owned device buffers,
+ * H*W*3 float32, overwritten).  Copies the arrays (host); the scenes must
+ * outlive the batch and have a BVH when it renders.  options: NULL =
+ * defaults; use_bvh must be set.  RT_ERR_INVALID_ARG on a NULL argument,
+ * n < 1, a size < 1, an invalid camera or max_depth outside
+ * [0, RT_MAX_DEPTH]. */
+rt_status rt_batch_create(rt_scene* const* scenes, int32_t n, const rt_camera* cameras, const int32_t* widths,
+                          const int32_t* heights, int32_t max_depth, float* const* out_rgb,
+                          const rt_render_options* options, rt_batch** out);
+/* n cameras (host array), used from the next rt_batch_render on. */
+rt_status rt_batch_set_cameras(rt_batch* b, const rt_camera* cameras);
+/* Renders every frame of the batch on `stream` (one kernel, from a CUDA
+ * graph that is captured once per tune).  tune: NULL = the last autotuned
+ * choice, else a default.  stats (nullable): summed over the frames; asking
+ * for them syncs the stream and returns the scenes' latched errors. */
+rt_status rt_batch_render(rt_batch* b, const rt_tune* tune, rt_render_stats* stats, void* stream);
+/* Times candidate tunes on this batch (each rendered 3 times, CUDA events
+ * on `stream`) and keeps the fastest for rt_batch_render(b, NULL, ...).
+ * best and best_ms are nullable.  Renders the batch (the images are left
+ * valid). */
+rt_status rt_batch_autotune(rt_batch* b, rt_tune* best, float* best_ms, void* stream);
+rt_status rt_batch_destroy(rt_batch* b);
+
 /* Waits for `stream` and returns (and clears) the latched kernel error. */
 rt_status rt_scene_sync(rt_scene* s, void* stream);
 

@@ -21,6 +21,8 @@ __all__ = [
     "rt_trace_any", "rt_scene_sync", "rt_scene_destroy", "rt_render_stage_times", "Scene",
     "rt_nrc_config_default", "rt_nrc_create", "rt_nrc_destroy", "rt_nrc_get_params", "rt_nrc_set_params",
     "rt_nrc_get_grads", "rt_nrc_infer", "rt_nrc_train_step", "rt_render_nrc",
+    "rt_tune", "rt_batch_create", "rt_batch_set_cameras", "rt_batch_render", "rt_batch_autotune",
+    "rt_batch_destroy", "Batch",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -82,6 +84,20 @@ class rt_nrc_config(ctypes.Structure):
 RT_NRC_PARAMS = 18883
 
 
+class rt_tune(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
+def make_tune(tile_w=8, tile_h=4, block_threads=128, blocks_per_sm=0) -> rt_tune:
+    return rt_tune(tile_w, tile_h, block_threads, blocks_per_sm)
+
+
+def tune_dict(t: rt_tune) -> dict:
+    return {"tile_w": t.tile_w, "tile_h": t.tile_h, "block_threads": t.block_threads,
+            "blocks_per_sm": t.blocks_per_sm}
+
+
 class rt_bvh_info(ctypes.Structure):
     _fields_ = [("n_prims", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("root", ctypes.c_int64),
                 ("max_depth", ctypes.c_int32),
@@ -130,6 +146,11 @@ def lib():
             "rt_nrc_infer": (I, [P, P, P, I64, P, P]),
             "rt_nrc_train_step": (I, [P, P, P, P, I64, P]),
             "rt_render_nrc": (I, [P, P, P, I, I, I, P, I, P, P, P]),
+            "rt_batch_create": (I, [P, I, P, P, P, I, P, P, P]),
+            "rt_batch_set_cameras": (I, [P, P]),
+            "rt_batch_render": (I, [P, P, P, P]),
+            "rt_batch_autotune": (I, [P, P, P, P]),
+            "rt_batch_destroy": (I, [P]),
             "rt_scene_destroy": (I, [P]),
         }
         for name, (res, args) in sigs.items():
@@ -396,6 +417,76 @@ def rt_render_nrc(scene, nrc, camera, width, height, max_depth, out_rgb, train=T
                                ctypes.byref(options) if options is not None else None,
                                ctypes.byref(st) if st is not None else None, _stream(stream)))
     return stats_dict(st, max_depth) if st is not None else None
+
+
+def rt_batch_create(scenes, cameras, widths, heights, max_depth, outs, options=None):
+    """scenes: rt_scene handles; cameras: camera tuples or rt_camera; outs: device tensors."""
+    n = len(scenes)
+    sc_arr = (ctypes.c_void_p * n)(*[ctypes.c_void_p(h) if isinstance(h, int) else h for h in scenes])
+    cam_arr = (rt_camera * n)(*[make_camera(c) for c in cameras])
+    w_arr = (ctypes.c_int32 * n)(*[int(x) for x in widths])
+    h_arr = (ctypes.c_int32 * n)(*[int(x) for x in heights])
+    o_arr = (ctypes.c_void_p * n)(*[_dptr(o) for o in outs])
+    out = ctypes.c_void_p()
+    _check(lib().rt_batch_create(sc_arr, n, cam_arr, w_arr, h_arr, int(max_depth), o_arr,
+                                 ctypes.byref(options) if options is not None else None, ctypes.byref(out)))
+    return out.value
+
+
+def rt_batch_set_cameras(batch, cameras):
+    n = len(cameras)
+    cam_arr = (rt_camera * n)(*[make_camera(c) for c in cameras])
+    _check(lib().rt_batch_set_cameras(batch, cam_arr))
+
+
+def rt_batch_render(batch, tune=None, stats=False, max_depth=RT_MAX_DEPTH, stream=None):
+    st = rt_render_stats() if stats else None
+    _check(lib().rt_batch_render(batch, ctypes.byref(tune) if tune is not None else None,
+                                 ctypes.byref(st) if st is not None else None, _stream(stream)))
+    return stats_dict(st, max_depth) if st is not None else None
+
+
+def rt_batch_autotune(batch, stream=None):
+    """Returns (best rt_tune, its ms)."""
+    t = rt_tune()
+    ms = ctypes.c_float()
+    _check(lib().rt_batch_autotune(batch, ctypes.byref(t), ctypes.byref(ms), _stream(stream)))
+    return t, ms.value
+
+
+def rt_batch_destroy(batch):
+    _check(lib().rt_batch_destroy(batch))
+
+
+class Batch:
+    """Owns an rt_batch over Scene objects (each frame: scene, camera, size, device image)."""
+
+    def __init__(self, scenes, cameras, widths, heights, max_depth, outs, options=None):
+        self.scenes = list(scenes)   # keeps the scenes alive
+        self.outs = list(outs)
+        self.max_depth = max_depth
+        self.handle = rt_batch_create([s.handle for s in self.scenes], cameras, widths, heights, max_depth,
+                                      self.outs, options)
+
+    def render(self, tune=None, stats=False, stream=None):
+        return rt_batch_render(self.handle, tune, stats, self.max_depth, stream)
+
+    def autotune(self, stream=None):
+        return rt_batch_autotune(self.handle, stream)
+
+    def set_cameras(self, cameras):
+        rt_batch_set_cameras(self.handle, cameras)
+
+    def close(self):
+        if self.handle:
+            rt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Scene:

@@ -7,8 +7,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librtb.so")
-SOURCES = ["scene.cu", "bvh.cu", "render.cu", "nrc.cu"]
-HEADERS = ["rtb_internal.cuh", "nrc_internal.cuh", "tc.cuh"]
+SOURCES = ["scene.cu", "bvh.cu", "render.cu", "nrc.cu", "batch.cu"]
+HEADERS = ["rtb_internal.cuh", "nrc_internal.cuh", "tc.cuh", "trace_device.cuh"]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include", "rtb.h")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

@@ -1,0 +1,580 @@
+// batch.cu - many scenes in one persistent launch (rt_batch_*).
+//
+// The paper renders one scene per run; a renderer that serves many scenes
+// of uneven size and resolution wants them in one launch, so that small
+// frames do not leave the GPU idle and large ones do not serialise the
+// rest.  One kernel walks a global list of 32-pixel tiles of every frame
+// (per-frame tile offsets, per-scene BVH and primitive pointers in a device
+// table).  A warp takes a tile, traces its camera rays and then every ray
+// they spawn - shadow rays to each point light (Alg. 1), reflection and
+// refraction rays to max_depth (Sec. IV.A, Eq. 6-12) - depth first, with
+// the extra rays of a hit shared among the warp's lanes through a pending
+// stack in shared memory; then it takes the next tile, of any frame.  The
+// launch (counter reset, image clears, kernel) is captured in a CUDA graph
+// once per tune and replayed; an autotuner picks the tile shape, block size
+// and grid size by timing them on the batch itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "rtb_internal.cuh"
+#include "trace_device.cuh"
+
+namespace rtb {
+
+// Pending rays a warp can share (48 B each; 6 KB a warp below 256-thread
+// blocks, 3 KB in them, which keeps a block's static shared memory < 48 KB).
+template <int kThreads>
+__host__ __device__ constexpr int batch_pending() {
+  return kThreads >= 256 ? 64 : 128;
+}
+// Blocks per SM the register budget is cut for (about 100 registers a thread).
+template <int kThreads>
+__host__ __device__ constexpr int batch_min_blocks() {
+  return kThreads >= 256 ? 2 : 640 / kThreads;
+}
+
+struct BatchScene {
+  DevScene sc;
+  CamBasis cam;
+  float* fb;
+  int W, H, tiles_x;
+  unsigned tile0;   // first tile of this frame in the global tile list
+  int cap;          // traversal step cap
+};
+
+struct BatchCounts {
+  unsigned rays[RT_MAX_DEPTH + 1];     // closest-hit rays traced at depth d
+  unsigned shadow[RT_MAX_DEPTH + 1];   // shadow rays cast from depth-d hits
+  unsigned hits[RT_MAX_DEPTH + 1];
+  unsigned fetch;                      // next tile
+};
+
+struct BatchParams {
+  const BatchScene* scenes;
+  int n;
+  unsigned n_tiles;
+  int max_depth;
+  int tile_w, tile_h;
+  float bg_r, bg_g, bg_b, eps_scale;
+  BatchCounts* cnt;
+};
+
+__device__ __forceinline__ void add_rgb(float* fb, int pixel, f3 c) {
+  float* p = fb + 3 * (size_t)pixel;
+  atomicAdd(p, c.x);
+  atomicAdd(p + 1, c.y);
+  atomicAdd(p + 2, c.z);
+}
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batch(BatchParams bp) {
+  constexpr int kBatchPending = batch_pending<kThreads>();
+  __shared__ int s_stack[kStackShared * kThreads];
+  __shared__ float4 s_pend[kThreads / 32][kBatchPending][3];   // (o, pixel) (d, depth) (w, tmax)
+  __shared__ int s_np[kThreads / 32];
+  __shared__ unsigned s_cnt[3][RT_MAX_DEPTH + 1];
+  int* stack = s_stack + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int i = threadIdx.x; i < 3 * (RT_MAX_DEPTH + 1); i += blockDim.x) (&s_cnt[0][0])[i] = 0u;
+  if (lane == 0) s_np[warp] = 0;
+  __syncthreads();
+  const f3 bg = mk3(bp.bg_r, bp.bg_g, bp.bg_b);
+  // second children this lane could not share (depth first: <= max_depth entries)
+  float4 local[RT_MAX_DEPTH][3];
+  int nl = 0;
+  // A lane's item is a path segment (depth >= 0) or a shadow ray cast from a
+  // depth-(~depth) hit (depth < 0; w is its contribution, tmax_item its length).
+  bool have = false;
+  f3 o = mk3(0, 0, 0), d = mk3(0, 0, 1), w = mk3(0, 0, 0);
+  int depth = 0, pixel = 0;
+  float tmax_item = 0.f;
+  // the frame of the warp's current tile: every item of the warp belongs to it
+  DevScene sc;
+  sc.n_prims = 0;
+  float* fb = nullptr;
+  int cap = 0;
+  WorkCount wc = {0u, 0u, 0u, 0u};
+  for (;;) {
+    // --- refill lanes without an item: own overflow, then the warp's stack
+    if (!have && nl > 0) {
+      --nl;
+      o = xyz(local[nl][0]);
+      pixel = __float_as_int(local[nl][0].w);
+      d = xyz(local[nl][1]);
+      depth = __float_as_int(local[nl][1].w);
+      w = xyz(local[nl][2]);
+      have = true;
+    }
+    __syncwarp();   // rays pushed by this warp's lanes are visible
+    unsigned need = __ballot_sync(kFull, !have);
+    int np = s_np[warp];
+    if (need && np > 0) {
+      int take = min(__popc(need), np);
+      int rank = __popc(need & lt);
+      if (!have && rank < take) {
+        const float4* r = s_pend[warp][np - 1 - rank];
+        o = xyz(r[0]);
+        pixel = __float_as_int(r[0].w);
+        d = xyz(r[1]);
+        depth = __float_as_int(r[1].w);
+        w = xyz(r[2]);
+        tmax_item = r[2].w;
+        have = true;
+      }
+      __syncwarp();
+      if (lane == 0) s_np[warp] = np - take;
+      __syncwarp();
+    }
+    if (!__any_sync(kFull, have)) {
+      // --- the warp is idle (no item, nothing pending): the next tile
+      unsigned t = 0;
+      if (lane == 0) t = atomicAdd(&bp.cnt->fetch, 1u);
+      t = __shfl_sync(kFull, t, 0);
+      if (t >= bp.n_tiles) break;
+      int lo = 0, hi = bp.n - 1;   // the frame whose tiles start last at or before t
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&bp.scenes[mid].tile0) <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      const BatchScene* bs = bp.scenes + lo;
+      sc = bs->sc;
+      fb = bs->fb;
+      cap = bs->cap;
+      const int W = bs->W, H = bs->H;
+      const unsigned k = t - bs->tile0;
+      const int x = (int)(k % (unsigned)bs->tiles_x) * bp.tile_w + lane % bp.tile_w;
+      const int y = (int)(k / (unsigned)bs->tiles_x) * bp.tile_h + lane / bp.tile_w;
+      if (x < W && y < H) {
+        const CamBasis cb = bs->cam;
+        camera_ray(cb, W, H, x, y, o, d);
+        pixel = y * W + x;
+        w = mk3(1.f, 1.f, 1.f);
+        depth = 0;
+        have = true;
+      }
+      continue;   // to the top: a tile cut by the image edge still has lanes with work
+    }
+    // --- one item per lane
+    Children ch;
+    ch.want_r = ch.want_t = false;
+    if (have && depth < 0) {
+      bool sfail = false;
+      float tm = tmax_item;
+      int h = traverse<true, false, kThreads>(sc, make_ray(o, d), 0.0f, tm, stack, cap, sfail, wc);
+      if (sfail) atomicOr(sc.status, kErrTraversalLimit);
+      if (h < 0 && !sfail) add_rgb(fb, pixel, w);
+    } else if (have) {
+      float t = INFINITY;
+      bool fail = false;
+      int hit = traverse<false, false, kThreads>(sc, make_ray(o, d), 0.0f, t, stack, cap, fail, wc);
+      if (fail) atomicOr(sc.status, kErrTraversalLimit);
+      atomicAdd(&s_cnt[0][depth], 1u);
+      if (hit < 0) {
+        add_rgb(fb, pixel, w * bg);
+      } else {
+        atomicAdd(&s_cnt[2][depth], 1u);
+        Surface sf = surface_at(sc, hit, o, d, t, bp.eps_scale);
+        if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_rgb(fb, pixel, w * sf.emission);
+        if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
+          for (int li = 0; li < sc.n_lights; ++li) {
+            f3 contrib, os, sd;
+            float tmax;
+            if (!light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd,
+                            tmax))
+              continue;
+            atomicAdd(&s_cnt[1][depth], 1u);
+            // to the warp's pending stack for a free lane; traced here when it is full
+            int pos = atomicAdd(&s_np[warp], 1);
+            if (pos < kBatchPending) {
+              float4* r = s_pend[warp][pos];
+              r[0] = make_float4(os.x, os.y, os.z, __int_as_float(pixel));
+              r[1] = make_float4(sd.x, sd.y, sd.z, __int_as_float(~depth));
+              r[2] = make_float4(contrib.x, contrib.y, contrib.z, tmax);
+              continue;
+            }
+            atomicSub(&s_np[warp], 1);
+            bool sfail = false;
+            int h = traverse<true, false, kThreads>(sc, make_ray(os, sd), 0.0f, tmax, stack, cap, sfail, wc);
+            if (sfail) atomicOr(sc.status, kErrTraversalLimit);
+            if (h < 0 && !sfail) add_rgb(fb, pixel, contrib);
+          }
+        }
+        if (depth < bp.max_depth) ch = children_of(sf, d, w);
+      }
+    }
+    // --- a second child goes to the warp's stack (or this lane's overflow)
+    bool two = have && ch.want_r && ch.want_t;
+    unsigned m2 = __ballot_sync(kFull, two);
+    if (m2) {
+      __syncwarp();
+      int np2 = s_np[warp];
+      int room = kBatchPending - np2;
+      int rank = __popc(m2 & lt);
+      float4 r0 = make_float4(ch.or_.x, ch.or_.y, ch.or_.z, __int_as_float(pixel));
+      float4 r1 = make_float4(ch.dr.x, ch.dr.y, ch.dr.z, __int_as_float(depth + 1));
+      float4 r2 = make_float4(ch.wr.x, ch.wr.y, ch.wr.z, 0.f);
+      if (two) {
+        if (rank < room) {
+          float4* r = s_pend[warp][np2 + rank];
+          r[0] = r0;
+          r[1] = r1;
+          r[2] = r2;
+        } else if (nl < RT_MAX_DEPTH) {
+          local[nl][0] = r0;
+          local[nl][1] = r1;
+          local[nl][2] = r2;
+          ++nl;
+        } else {
+          atomicOr(sc.status, kErrQueueOverflow);   // not reachable for depth <= 16
+        }
+      }
+      __syncwarp();
+      if (lane == 0) s_np[warp] = np2 + min(__popc(m2), room);
+      __syncwarp();
+    }
+    // --- this lane follows its (other) child, or is free for new work
+    if (have) {
+      if (ch.want_t) {
+        o = ch.ot;
+        d = ch.dt;
+        w = ch.wt;
+        ++depth;
+      } else if (ch.want_r) {
+        o = ch.or_;
+        d = ch.dr;
+        w = ch.wr;
+        ++depth;
+      } else {
+        have = false;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= RT_MAX_DEPTH; i += blockDim.x) {
+    if (s_cnt[0][i]) atomicAdd(&bp.cnt->rays[i], s_cnt[0][i]);
+    if (s_cnt[1][i]) atomicAdd(&bp.cnt->shadow[i], s_cnt[1][i]);
+    if (s_cnt[2][i]) atomicAdd(&bp.cnt->hits[i], s_cnt[2][i]);
+  }
+}
+
+using BatchKernel = void (*)(BatchParams);
+
+static BatchKernel batch_kernel(int threads) {
+  switch (threads) {
+    case 64:
+      return k_batch<64>;
+    case 128:
+      return k_batch<128>;
+    case 256:
+      return k_batch<256>;
+    default:
+      return nullptr;
+  }
+}
+
+static bool valid_tune(const rt_tune& t) {
+  return t.tile_w > 0 && t.tile_h > 0 && t.tile_w * t.tile_h == 32 && batch_kernel(t.block_threads) &&
+         t.blocks_per_sm >= 0;
+}
+
+static bool same_tune(const rt_tune& a, const rt_tune& b) {
+  return a.tile_w == b.tile_w && a.tile_h == b.tile_h && a.block_threads == b.block_threads &&
+         a.blocks_per_sm == b.blocks_per_sm;
+}
+
+static rt_tune default_tune() {
+  rt_tune t;
+  t.tile_w = 8;
+  t.tile_h = 4;
+  t.block_threads = 128;
+  t.blocks_per_sm = 0;
+  return t;
+}
+
+}  // namespace rtb
+
+using namespace rtb;
+
+struct rt_batch {
+  std::vector<rt_scene*> scenes;
+  std::vector<rt_camera> cams;
+  std::vector<int> W, H;
+  std::vector<float*> outs;
+  int n = 0, max_depth = 0;
+  rt_render_options opt;
+  int device = 0, sm_count = 0;
+  Buf table, counts;
+  BatchScene* host_table = nullptr;   // pinned staging of the device table
+  cudaStream_t cap_stream = nullptr;  // graphs are captured here (never the caller's stream)
+  struct Graph {
+    rt_tune tune;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  rt_tune best;
+  bool tuned = false;
+};
+
+namespace rtb {
+
+// Fills the device table for `tune` (through the pinned staging copy) and
+// returns the number of tiles; the copy is ordered on `st`.
+static rt_status batch_table(rt_batch* b, const rt_tune& tune, unsigned* n_tiles, cudaStream_t st) {
+  uint64_t tile0 = 0;
+  for (int i = 0; i < b->n; ++i) {
+    rt_scene* s = b->scenes[i];
+    if (!s->built) return set_error(RT_ERR_NOT_BUILT, "rt_batch_render: a scene of the batch has no BVH");
+    BatchScene& e = b->host_table[i];
+    e.sc = dev_scene(s, true);
+    e.cam = camera_basis(&b->cams[i], b->W[i], b->H[i]);
+    e.fb = b->outs[i];
+    e.W = b->W[i];
+    e.H = b->H[i];
+    e.tiles_x = (e.W + tune.tile_w - 1) / tune.tile_w;
+    const int tiles_y = (e.H + tune.tile_h - 1) / tune.tile_h;
+    e.tile0 = (unsigned)tile0;
+    int64_t tcap = b->opt.traversal_cap > 0 ? b->opt.traversal_cap : 4 * std::max<int64_t>(s->n_nodes4, 1) + 64;
+    e.cap = (int)std::min<int64_t>(tcap, 0x7fffffff);
+    tile0 += (uint64_t)e.tiles_x * tiles_y;
+  }
+  if (tile0 > 0xffffffffull) return set_error(RT_ERR_UNSUPPORTED, "rt_batch_render: more than 2^32 tiles");
+  *n_tiles = (unsigned)tile0;
+  return cuda_error(cudaMemcpyAsync(b->table.p, b->host_table, sizeof(BatchScene) * b->n, cudaMemcpyHostToDevice, st),
+                    "rt_batch_render: table");
+}
+
+// The launch of one tune: counters, image clears and the kernel, captured
+// on the batch's own stream into a graph (once per tune).
+static rt_status batch_graph(rt_batch* b, const rt_tune& tune, unsigned n_tiles, cudaGraphExec_t* exec) {
+  for (auto& g : b->graphs)
+    if (same_tune(g.tune, tune)) {
+      *exec = g.exec;
+      return RT_OK;
+    }
+  BatchKernel kern = batch_kernel(tune.block_threads);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tune.block_threads, 0);
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: occupancy");
+  if (per_sm < 1) return set_error(RT_ERR_UNSUPPORTED, "rt_batch_render: the kernel does not fit on an SM");
+  if (tune.blocks_per_sm > 0) per_sm = std::min(per_sm, tune.blocks_per_sm);
+  BatchParams bp;
+  bp.scenes = (const BatchScene*)b->table.p;
+  bp.n = b->n;
+  bp.n_tiles = n_tiles;
+  bp.max_depth = b->max_depth;
+  bp.tile_w = tune.tile_w;
+  bp.tile_h = tune.tile_h;
+  bp.bg_r = b->opt.background[0];
+  bp.bg_g = b->opt.background[1];
+  bp.bg_b = b->opt.background[2];
+  bp.eps_scale = b->opt.eps_scale;
+  bp.cnt = (BatchCounts*)b->counts.p;
+  cudaStream_t cs = b->cap_stream;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: begin capture");
+  cudaMemsetAsync(b->counts.p, 0, sizeof(BatchCounts), cs);
+  for (int i = 0; i < b->n; ++i) cudaMemsetAsync(b->outs[i], 0, (size_t)b->W[i] * b->H[i] * 3 * sizeof(float), cs);
+  kern<<<b->sm_count * per_sm, tune.block_threads, 0, cs>>>(bp);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  e = cudaGetLastError();
+  if (e2 != cudaSuccess || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_error(e2 != cudaSuccess ? e2 : e, "rt_batch_render: capture");
+  }
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: instantiate");
+  b->graphs.push_back({tune, x});
+  *exec = x;
+  return RT_OK;
+}
+
+static rt_status batch_render(rt_batch* b, const rt_tune& tune, cudaStream_t st) {
+  if (!valid_tune(tune))
+    return set_error(RT_ERR_INVALID_ARG, "rt_batch_render: tune needs tile_w * tile_h == 32, block_threads 64, "
+                                         "128 or 256 and blocks_per_sm >= 0");
+  unsigned n_tiles = 0;
+  rt_status rs = batch_table(b, tune, &n_tiles, st);
+  if (rs) return rs;
+  cudaGraphExec_t exec = nullptr;
+  if ((rs = batch_graph(b, tune, n_tiles, &exec))) return rs;
+  // the tile count depends only on the sizes and the tile shape, both fixed per graph
+  return cuda_error(cudaGraphLaunch(exec, st), "rt_batch_render: launch");
+}
+
+}  // namespace rtb
+
+extern "C" {
+
+rt_status rt_batch_create(rt_scene* const* scenes, int32_t n, const rt_camera* cameras, const int32_t* widths,
+                          const int32_t* heights, int32_t max_depth, float* const* out_rgb,
+                          const rt_render_options* options, rt_batch** out) {
+  if (!scenes || !cameras || !widths || !heights || !out_rgb || !out)
+    return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: NULL argument");
+  *out = nullptr;
+  if (n < 1) return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: n < 1");
+  if (max_depth < 0 || max_depth > RT_MAX_DEPTH)
+    return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: max_depth outside [0, 16]");
+  rt_render_options opt;
+  rt_render_options_default(&opt);
+  if (options) opt = *options;
+  if (!opt.use_bvh) return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: batches trace with the BVH (use_bvh)");
+  if (!std::isfinite(opt.background[0]) || !std::isfinite(opt.background[1]) || !std::isfinite(opt.background[2]) ||
+      !std::isfinite(opt.eps_scale) || opt.eps_scale < 0.f || opt.traversal_cap < 0)
+    return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: invalid options");
+  for (int i = 0; i < n; ++i) {
+    if (!scenes[i] || !out_rgb[i]) return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: NULL scene or image");
+    if (widths[i] < 1 || heights[i] < 1) return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: size < 1");
+    if ((int64_t)widths[i] * heights[i] > (int64_t)1 << 30)
+      return set_error(RT_ERR_UNSUPPORTED, "rt_batch_create: image too large");
+    if (!finite_cam(&cameras[i])) return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: invalid camera");
+    if (scenes[i]->device != scenes[0]->device)
+      return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: scenes on different devices");
+  }
+  rt_batch* b = new rt_batch();
+  b->scenes.assign(scenes, scenes + n);
+  b->cams.assign(cameras, cameras + n);
+  b->W.assign(widths, widths + n);
+  b->H.assign(heights, heights + n);
+  b->outs.assign(out_rgb, out_rgb + n);
+  b->n = n;
+  b->max_depth = max_depth;
+  b->opt = opt;
+  b->device = scenes[0]->device;
+  b->sm_count = scenes[0]->sm_count;
+  b->best = default_tune();
+  rt_status rs = RT_OK;
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->host_table, sizeof(BatchScene) * n);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) rs = cuda_error(e, "rt_batch_create");
+  if (!rs) rs = ensure(b->table, sizeof(BatchScene) * n);
+  if (!rs) rs = ensure(b->counts, sizeof(BatchCounts));
+  if (rs) {
+    rt_batch_destroy(b);
+    return rs;
+  }
+  *out = b;
+  return RT_OK;
+}
+
+rt_status rt_batch_set_cameras(rt_batch* b, const rt_camera* cameras) {
+  if (!b || !cameras) return set_error(RT_ERR_INVALID_ARG, "rt_batch_set_cameras: NULL argument");
+  for (int i = 0; i < b->n; ++i)
+    if (!finite_cam(&cameras[i])) return set_error(RT_ERR_INVALID_ARG, "rt_batch_set_cameras: invalid camera");
+  b->cams.assign(cameras, cameras + b->n);
+  return RT_OK;
+}
+
+rt_status rt_batch_render(rt_batch* b, const rt_tune* tune, rt_render_stats* stats, void* stream) {
+  if (!b) return set_error(RT_ERR_INVALID_ARG, "rt_batch_render: batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  // the staging copy of the previous render may still be in flight
+  cudaError_t e = cudaStreamSynchronize(b->cap_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render");
+  rt_status rs = batch_render(b, tune ? *tune : b->best, st);
+  if (rs) return rs;
+  if (!stats) return RT_OK;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render");
+  BatchCounts c;
+  e = cudaMemcpy(&c, b->counts.p, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: stats");
+  memset(stats, 0, sizeof(*stats));
+  for (int d = 0; d <= RT_MAX_DEPTH; ++d) {
+    stats->rays_per_depth[d] = c.rays[d];
+    stats->shadow_per_depth[d] = c.shadow[d];
+    stats->hits_per_depth[d] = c.hits[d];
+    stats->shadow += c.shadow[d];
+    if (d == 0) stats->primary = c.rays[0];
+    else stats->secondary += c.rays[d];
+  }
+  stats->launches = 1;
+  for (int i = 0; i < b->n; ++i) {
+    rs = rt_scene_sync(b->scenes[i], stream);
+    if (rs) return rs;
+  }
+  return RT_OK;
+}
+
+rt_status rt_batch_autotune(rt_batch* b, rt_tune* best, float* best_ms, void* stream) {
+  if (!b) return set_error(RT_ERR_INVALID_ARG, "rt_batch_autotune: batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int tiles[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
+  const int threads[3] = {64, 128, 256};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_autotune");
+  rt_status rs = RT_OK;
+  float best_t = INFINITY;
+  rt_tune choice = default_tune();
+  for (int ti = 0; ti < 4 && !rs; ++ti) {
+    for (int bi = 0; bi < 3 && !rs; ++bi) {
+      rt_tune t;
+      t.tile_w = tiles[ti][0];
+      t.tile_h = tiles[ti][1];
+      t.block_threads = threads[bi];
+      t.blocks_per_sm = 0;
+      float ms = 0.f;
+      for (int rep = 0; rep < 3 && !rs; ++rep) {   // the first is a warm-up (and the graph's capture)
+        e = cudaStreamSynchronize(b->cap_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+          rs = cuda_error(e, "rt_batch_autotune");
+          break;
+        }
+        cudaEventRecord(e0, st);
+        rs = batch_render(b, t, st);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (!rs && e != cudaSuccess) rs = cuda_error(e, "rt_batch_autotune");
+        float x = 0.f;
+        if (!rs) cudaEventElapsedTime(&x, e0, e1);
+        if (rep > 0) ms += x;
+      }
+      if (!rs && ms / 2 < best_t) {
+        best_t = ms / 2;
+        choice = t;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rs) return rs;
+  b->best = choice;
+  b->tuned = true;
+  if (best) *best = choice;
+  if (best_ms) *best_ms = best_t;
+  // the images of the chosen tune
+  rs = batch_render(b, choice, st);
+  if (rs) return rs;
+  for (int i = 0; i < b->n; ++i) {
+    rs = rt_scene_sync(b->scenes[i], stream);
+    if (rs) return rs;
+  }
+  return RT_OK;
+}
+
+rt_status rt_batch_destroy(rt_batch* b) {
+  if (!b) return RT_OK;
+  if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  release(b->table);
+  release(b->counts);
+  if (b->host_table) cudaFreeHost(b->host_table);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+  return RT_OK;
+}
+
+}  // extern "C"

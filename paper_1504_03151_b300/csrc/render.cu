@@ -19,12 +19,9 @@
 
 #include "nrc_internal.cuh"
 #include "rtb_internal.cuh"
+#include "trace_device.cuh"
 
 namespace rtb {
-
-constexpr int kSentinelLink = kEmptyLink;   // popped from an empty stack; never a valid link
-constexpr float kSlabUp = 1.0000005f;    // grows a slab's exit distance by > 2 ulps
-constexpr unsigned kFull = 0xffffffffu;
 
 // Device-side counters of one frame (reset at its start).
 struct Counters {
@@ -66,296 +63,6 @@ struct FrameParams {
   const unsigned* prev_hits;   // depth-first frames: cache hits of the previous frame (0: take all)
 };
 
-// ---------------------------------------------------------------------------
-// traversal
-// ---------------------------------------------------------------------------
-struct RayInv {
-  f3 o, d, idir, oid;
-};
-
-__device__ __forceinline__ RayInv make_ray(f3 o, f3 d) {
-  RayInv r;
-  r.o = o;
-  r.d = d;
-  const float tiny = 8.27e-25f;   // 2^-80: keeps 1/d finite
-  float dx = fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x);
-  float dy = fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y);
-  float dz = fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z);
-  r.idir = mk3(1.0f / dx, 1.0f / dy, 1.0f / dz);
-  r.oid = mk3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
-  return r;
-}
-
-struct WorkCount {
-  unsigned visits, tests, vmax;   // vmax: most node visits of one ray
-  unsigned boxes;                 // child boxes tested (non-empty slots of the visited nodes)
-};
-
-template <bool kAny>
-__device__ __forceinline__ bool test_prim(float4 r0, float4 r1, float4 r2, int k, const RayInv& r, float tmin,
-                                          float& tbest, int& best, int& best_id) {
-  float t;
-  bool h;
-  if (__float_as_int(r0.w) == kKindSphere) h = hit_sphere<!kAny>(r.o, r.d, r0, r1, tmin, tbest, t);
-  else h = hit_triangle<!kAny>(r.o, r.d, r0, r1, r2, tmin, tbest, t);
-  if (h) {
-    if (kAny) {
-      best = k;
-      return true;
-    }
-    int id = __float_as_int(r1.w);
-    if (t < tbest || id < best_id) {
-      tbest = t;
-      best = k;
-      best_id = id;
-    }
-  }
-  return false;
-}
-
-// Tests the primitives [start, start+count) in `prims`.  Closest hit:
-// nearest t, ties to the lower primitive id; any hit: returns at the first.
-// Two records are loaded before either is tested, so a leaf costs one
-// memory round trip per pair rather than per primitive.
-template <bool kAny, bool kCount>
-__device__ __forceinline__ bool leaf_hits(const float4* __restrict__ prims, int start, int count, const RayInv& r,
-                                          float tmin, float& tbest, int& best, int& best_id, WorkCount& wc) {
-  int k = start, end = start + count;
-  for (; k + 1 < end; k += 2) {
-    const float4* a = prims + 3 * (size_t)k;
-    float4 a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2);
-    float4 b0 = __ldg(a + 3), b1 = __ldg(a + 4), b2 = __ldg(a + 5);
-    if (kCount) wc.tests += 2;
-    if (test_prim<kAny>(a0, a1, a2, k, r, tmin, tbest, best, best_id)) return true;
-    if (test_prim<kAny>(b0, b1, b2, k + 1, r, tmin, tbest, best, best_id)) return true;
-  }
-  if (k < end) {
-    const float4* a = prims + 3 * (size_t)k;
-    float4 a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2);
-    if (kCount) wc.tests++;
-    if (test_prim<kAny>(a0, a1, a2, k, r, tmin, tbest, best, best_id)) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ int pop_stack(const int* stack, const int* deep, int& sp) {
-  if (sp == 0) return kSentinelLink;
-  --sp;
-  return sp < kStackShared ? stack[sp * kTraceThreads] : deep[sp - kStackShared];
-}
-
-// Entry time of the ray into one child box of a 4-wide node, or +inf when
-// it misses: the ordered slab test over the near and far planes (picked by
-// the direction's signs), far distance widened by kSlabUp.  A slot with an
-// inverted box (lo = +inf, hi = -inf) always misses.
-__device__ __forceinline__ float child_entry(float nx, float ny, float nz, float fx, float fy, float fz,
-                                             const RayInv& r, float tmin, float tbest) {
-  float tn = fmaxf(fmaxf(fmaf(nx, r.idir.x, -r.oid.x), fmaf(ny, r.idir.y, -r.oid.y)),
-                   fmaxf(fmaf(nz, r.idir.z, -r.oid.z), tmin));
-  float tf = fminf(fminf(fmaf(fx, r.idir.x, -r.oid.x), fmaf(fy, r.idir.y, -r.oid.y)),
-                   fminf(fmaf(fz, r.idir.z, -r.oid.z), tbest)) * kSlabUp;
-  return tn <= tf ? tn : INFINITY;
-}
-
-__device__ __forceinline__ void order2(float& da, int& la, float& db, int& lb) {
-  bool sw = db < da;
-  float d = sw ? db : da;
-  int l = sw ? lb : la;
-  db = sw ? da : db;
-  lb = sw ? la : lb;
-  da = d;
-  la = l;
-}
-
-__device__ __forceinline__ void push_stack(int* stack, int* deep, int& sp, int v) {
-  if (sp < kStackShared) stack[sp * kTraceThreads] = v;
-  else deep[sp - kStackShared] = v;
-  ++sp;
-}
-
-// One step of the walk at an inner node of the 4-wide tree: tests the four
-// child boxes, sorts the children the ray enters by entry distance,
-// continues into the nearest and pushes the others (farthest first); pops
-// when the ray enters none.  Returns false when the stack would overflow.
-template <bool kCount>
-__device__ __forceinline__ bool visit_inner(const float4* __restrict__ nodes, int& node, const RayInv& r, int sx,
-                                            int sy, int sz, float tmin, float tbest, int* stack, int* deep, int& sp,
-                                            WorkCount& wc) {
-  const float4* n = nodes + 8 * (size_t)node;
-  float4 nx = __ldg(n + sx), fx = __ldg(n + 1 - sx);
-  float4 ny = __ldg(n + 2 + sy), fy = __ldg(n + 3 - sy);
-  float4 nz = __ldg(n + 4 + sz), fz = __ldg(n + 5 - sz);
-  float4 lk = __ldg(n + 6);
-  float d0 = child_entry(nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, r, tmin, tbest);
-  float d1 = child_entry(nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, r, tmin, tbest);
-  float d2 = child_entry(nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, r, tmin, tbest);
-  float d3 = child_entry(nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, r, tmin, tbest);
-  int l0 = __float_as_int(lk.x), l1 = __float_as_int(lk.y), l2 = __float_as_int(lk.z), l3 = __float_as_int(lk.w);
-  if (kCount) {
-    wc.visits++;
-    wc.boxes += (l0 != kEmptyLink) + (l1 != kEmptyLink) + (l2 != kEmptyLink) + (l3 != kEmptyLink);
-  }
-  int cnt = (d0 < INFINITY) + (d1 < INFINITY) + (d2 < INFINITY) + (d3 < INFINITY);
-  if (cnt == 0) {
-    node = pop_stack(stack, deep, sp);
-  } else if (cnt == 1) {
-    node = d0 < INFINITY ? l0 : d1 < INFINITY ? l1 : d2 < INFINITY ? l2 : l3;
-  } else {
-    // five compare-exchanges sort four (distance, link) pairs; misses (+inf) go last
-    order2(d0, l0, d1, l1);
-    order2(d2, l2, d3, l3);
-    order2(d0, l0, d2, l2);
-    order2(d1, l1, d3, l3);
-    order2(d1, l1, d2, l2);
-    if (sp + cnt - 1 > kStackSize) return false;
-    if (cnt == 4) push_stack(stack, deep, sp, l3);
-    if (cnt >= 3) push_stack(stack, deep, sp, l2);
-    push_stack(stack, deep, sp, l1);
-    node = l0;
-  }
-  return true;
-}
-
-// BVH traversal over the 4-wide tree with a per-thread stack: its first
-// kStackShared entries live in shared memory (column `stack[i *
-// kTraceThreads]`), deeper ones in local memory, which leaves most of L1 to
-// nodes and primitives.  For lanes that walk on their own (the depth-first
-// path kernel); traverse_warp below is the form for whole warps.
-// Returns the hit record index (leaf order) or -1.  Sets *fail when the
-// step cap or the stack depth is exceeded (the ray then counts as a miss).
-template <bool kAny, bool kCount>
-__device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& tbest, int* stack, int cap,
-                        bool& fail, WorkCount& wc) {
-  int best = -1, best_id = INT_MAX;
-  if (sc.n_prims == 0) return -1;
-  if (!sc.use_bvh) {
-    leaf_hits<kAny, kCount>(sc.prims, 0, sc.n_prims, r, tmin, tbest, best, best_id, wc);
-    return best;
-  }
-  int sp = 0;
-  int node = sc.root;
-  int steps = 0;
-  int deep[kStackSize - kStackShared > 0 ? kStackSize - kStackShared : 1];   // entries below the shared part
-  // rows of the near planes: lo when the direction is positive, else hi
-  const int sx = r.idir.x < 0.f, sy = r.idir.y < 0.f, sz = r.idir.z < 0.f;
-  for (;;) {
-    // inner nodes
-    while (node >= 0) {
-      if (++steps > cap) {
-        fail = true;
-        return kAny ? -1 : best;
-      }
-      if (node >= sc.n_nodes) {
-        atomicOr(sc.status, kErrBadTree);
-        fail = true;
-        return -1;
-      }
-      if (!visit_inner<kCount>(sc.nodes, node, r, sx, sy, sz, tmin, tbest, stack, deep, sp, wc)) {
-        fail = true;
-        return kAny ? -1 : best;
-      }
-    }
-    if (node == kSentinelLink) break;
-    // leaves
-    while (node < 0 && node != kSentinelLink) {
-      int ls = leaf_start(node), lc = leaf_count(node);
-      if (ls + lc > sc.n_prims) {
-        atomicOr(sc.status, kErrBadTree);
-        fail = true;
-        return -1;
-      }
-      if (leaf_hits<kAny, kCount>(sc.prims, ls, lc, r, tmin, tbest, best, best_id, wc)) return best;
-      node = pop_stack(stack, deep, sp);
-    }
-    if (node == kSentinelLink) break;
-  }
-  return best;
-}
-
-// The same walk for a whole warp: all 32 lanes call it together, lanes with
-// `part` false take no step.  The inner-node and leaf loops run while any
-// lane has work of their kind and end in a warp vote, so the warp
-// reconverges at every switch between the two instead of running its lanes'
-// phases one after another.  Same results and errors as traverse().
-template <bool kAny, bool kCount>
-__device__ int traverse_warp(const DevScene& sc, const RayInv& r, bool part, float tmin, float& tbest, int* stack,
-                             int cap, bool& fail, WorkCount& wc) {
-  int best = -1, best_id = INT_MAX;
-  if (sc.n_prims == 0) return -1;
-  if (!sc.use_bvh) {
-    if (part) leaf_hits<kAny, kCount>(sc.prims, 0, sc.n_prims, r, tmin, tbest, best, best_id, wc);
-    return best;
-  }
-  int sp = 0;
-  int node = part ? sc.root : kSentinelLink;
-  int steps = 0;
-  int deep[kStackSize - kStackShared > 0 ? kStackSize - kStackShared : 1];
-  const int sx = r.idir.x < 0.f, sy = r.idir.y < 0.f, sz = r.idir.z < 0.f;
-  for (;;) {
-    while (__any_sync(kFull, node >= 0)) {
-      if (node >= 0) {
-        if (++steps > cap) {
-          fail = true;
-          if (kAny) best = -1;
-          node = kSentinelLink;
-        } else if (node >= sc.n_nodes) {
-          atomicOr(sc.status, kErrBadTree);
-          fail = true;
-          best = -1;
-          node = kSentinelLink;
-        } else if (!visit_inner<kCount>(sc.nodes, node, r, sx, sy, sz, tmin, tbest, stack, deep, sp, wc)) {
-          fail = true;
-          if (kAny) best = -1;
-          node = kSentinelLink;
-        }
-      }
-    }
-    if (!__any_sync(kFull, node != kSentinelLink)) break;
-    while (__any_sync(kFull, node < 0 && node != kSentinelLink)) {
-      if (node < 0 && node != kSentinelLink) {
-        int ls = leaf_start(node), lc = leaf_count(node);
-        if (ls + lc > sc.n_prims) {
-          atomicOr(sc.status, kErrBadTree);
-          fail = true;
-          best = -1;
-          node = kSentinelLink;
-        } else if (leaf_hits<kAny, kCount>(sc.prims, ls, lc, r, tmin, tbest, best, best_id, wc)) {
-          node = kSentinelLink;   // any hit: done
-        } else {
-          node = pop_stack(stack, deep, sp);
-        }
-      }
-    }
-  }
-  return best;
-}
-
-// ---------------------------------------------------------------------------
-// warp-aggregated queue push: one atomic per warp per call
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned warp_push(unsigned* counter, bool pred, unsigned cap, bool& ok,
-                                              unsigned* status) {
-  unsigned mask = __ballot_sync(kFull, pred);
-  int lane = threadIdx.x & 31;
-  unsigned base = 0;
-  if (mask) {
-    int leader = __ffs(mask) - 1;
-    if (lane == leader) base = atomicAdd(counter, (unsigned)__popc(mask));
-    base = __shfl_sync(kFull, base, leader);
-  }
-  unsigned pos = base + (unsigned)__popc(mask & ((1u << lane) - 1u));
-  ok = pred && pos < cap;
-  if (pred && pos >= cap && status) atomicOr(status, kErrQueueOverflow);
-  return pos;
-}
-
-__device__ __forceinline__ void store_ray(float4* q, unsigned pos, f3 o, int pixel, f3 d, float tmax, f3 w) {
-  float4* p = q + 3 * (size_t)pos;
-  p[0] = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
-  p[1] = make_float4(d.x, d.y, d.z, tmax);
-  p[2] = make_float4(w.x, w.y, w.z, 0.f);
-}
-
 // Adds radiance to a pixel, or to a training target when the ray belongs to
 // the radiance cache's training subset (pixel id < 0 -> slot ~pixel).
 __device__ __forceinline__ void add_fb(const FrameParams& fp, int pixel, f3 c) {
@@ -365,14 +72,6 @@ __device__ __forceinline__ void add_fb(const FrameParams& fp, int pixel, f3 c) {
   atomicAdd(p + 2, c.z);
 }
 
-__device__ __forceinline__ uint32_t hash32(uint32_t x) {
-  x ^= x >> 16;
-  x *= 0x7feb352du;
-  x ^= x >> 15;
-  x *= 0x846ca68bu;
-  x ^= x >> 16;
-  return x;
-}
 
 template <bool kCount>
 __device__ __forceinline__ void flush_work(Counters* ctr, int cls, int depth, WorkCount wc) {
@@ -390,106 +89,6 @@ __device__ __forceinline__ void flush_work(Counters* ctr, int cls, int depth, Wo
     atomicAdd(&ctr->boxes[cls][depth], (unsigned long long)b);
     atomicMax(&ctr->max_visits[cls][depth], m);
   }
-}
-
-// ---------------------------------------------------------------------------
-// shading of one hit (shared by the wavefront and the per-path kernels)
-// ---------------------------------------------------------------------------
-struct Surface {
-  f3 p, n, albedo, emission;
-  float ks, shin, rho, ior, eps;
-  int kind;
-  bool inside;
-};
-
-__device__ __forceinline__ Surface surface_at(const DevScene& sc, int hit, f3 o, f3 d, float t, float eps_scale) {
-  Surface sf;
-  float4 r0 = __ldg(&sc.prims[3 * (size_t)hit]);
-  float4 r1 = __ldg(&sc.prims[3 * (size_t)hit + 1]);
-  float4 r2 = __ldg(&sc.prims[3 * (size_t)hit + 2]);
-  int mat = __float_as_int(r2.w);
-  sf.p = o + d * t;
-  f3 ng = geometric_normal(r0, r1, r2, sf.p);
-  sf.inside = dot(d, ng) > 0.f;
-  sf.n = sf.inside ? ng * -1.f : ng;
-  float4 m0 = __ldg(&sc.mats[3 * mat]), m1 = __ldg(&sc.mats[3 * mat + 1]), m2 = __ldg(&sc.mats[3 * mat + 2]);
-  sf.albedo = xyz(m0);
-  sf.ks = m0.w;
-  sf.shin = m1.x;
-  sf.ior = m1.z;
-  sf.kind = __float_as_int(m1.w);
-  sf.rho = sf.kind == RT_MAT_MIRROR ? m1.y : 0.f;
-  sf.emission = xyz(m2);
-  sf.eps = eps_scale * fmaxf(1.0f, maxabs(sf.p));
-  return sf;
-}
-
-// Alg. 1 for one point light (Eq. 8 with point lights): the term the light
-// adds if nothing blocks it, and the shadow ray that decides; false where
-// n.l <= 0 (no shadow ray is cast).
-__device__ __forceinline__ bool light_term(const Surface& sf, f3 d, f3 w, float4 L0, float4 L1, f3& contrib, f3& o_s,
-                                           f3& d_s, float& tmax) {
-  f3 lp = xyz(L0);
-  f3 l = normalize(lp - sf.p);
-  float nl = dot(sf.n, l);
-  if (!(nl > 0.f)) return false;
-  f3 rl = sf.n * (2.f * nl) - l;                  // reflect(-l, n)
-  float rv = -dot(rl, d);
-  float spec = rv > 0.f ? powf(rv, sf.shin) : 0.f;
-  f3 f = sf.albedo * nl + mk3(sf.ks * spec, sf.ks * spec, sf.ks * spec);
-  contrib = w * xyz(L1) * f * (1.f - sf.rho);
-  o_s = sf.p + sf.n * sf.eps;
-  f3 to_l = lp - o_s;
-  float dist = sqrtf(dot(to_l, to_l));
-  d_s = to_l * (1.f / dist);
-  tmax = dist - sf.eps;
-  return true;
-}
-
-// Reflection / refraction rays of a hit (Fig. 3): mirror rho -> reflection
-// of weight rho; dielectric -> Fresnel-Schlick R reflection and 1-R
-// refraction (none on total internal reflection).
-struct Children {
-  bool want_r, want_t;
-  f3 or_, dr, wr, ot, dt, wt;
-};
-
-__device__ __forceinline__ Children children_of(const Surface& sf, f3 d, f3 w) {
-  Children c;
-  c.want_r = c.want_t = false;
-  c.or_ = sf.p + sf.n * sf.eps;
-  c.ot = sf.p - sf.n * sf.eps;
-  c.dr = c.dt = mk3(0, 0, 1);
-  c.wr = c.wt = mk3(0, 0, 0);
-  float dn = dot(d, sf.n);
-  if (sf.kind != RT_MAT_DIELECTRIC) {
-    if (sf.rho > 0.f) {
-      c.want_r = true;
-      c.dr = normalize(d - sf.n * (2.f * dn));
-      c.wr = w * sf.rho;
-    }
-  } else {
-    float n1 = sf.inside ? sf.ior : 1.f, n2 = sf.inside ? 1.f : sf.ior;
-    float eta = n1 / n2;
-    float ci = -dn;
-    float k = 1.f - eta * eta * (1.f - ci * ci);
-    float R = 1.f;
-    if (k >= 0.f) {
-      float ct = sqrtf(k);
-      float r0 = (n1 - n2) / (n1 + n2);
-      r0 *= r0;
-      float cs = n1 <= n2 ? ci : ct;
-      float x = 1.f - cs;
-      R = r0 + (1.f - r0) * x * x * x * x * x;
-      c.want_t = true;
-      c.dt = normalize(d * eta + sf.n * (eta * ci - ct));
-      c.wt = w * (1.f - R);
-    }
-    c.want_r = true;
-    c.dr = normalize(d - sf.n * (2.f * dn));
-    c.wr = w * R;
-  }
-  return c;
 }
 
 // ---------------------------------------------------------------------------
@@ -962,7 +561,7 @@ static FrameParams frame_defaults() {
   return fp;
 }
 
-static CamBasis camera_basis(const rt_camera* c, int W, int H) {
+CamBasis camera_basis(const rt_camera* c, int W, int H) {
   // host FP32 arithmetic, once per frame
   CamBasis cb;
   float fx = c->look_at[0] - c->eye[0], fy = c->look_at[1] - c->eye[1], fz = c->look_at[2] - c->eye[2];
@@ -1001,7 +600,7 @@ static void occupancy(rt_scene* s) {
   s->shadow_blocks = s->sm_count * g_blocks_per_sm_shadow;
 }
 
-static bool finite_cam(const rt_camera* c) {
+bool finite_cam(const rt_camera* c) {
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(c->eye[i]) || !std::isfinite(c->look_at[i]) || !std::isfinite(c->up[i])) return false;
   if (!std::isfinite(c->vfov_deg) || !(c->vfov_deg > 0.f) || !(c->vfov_deg < 180.f)) return false;

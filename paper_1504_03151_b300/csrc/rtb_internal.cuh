@@ -152,6 +152,10 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st);
 
 // Kernel launch helpers shared by render.cu.
 DevScene dev_scene(const rt_scene* s, bool use_bvh);
+struct CamBasis;
+// Pinhole camera basis of a frame (host FP32 arithmetic) and its validation.
+CamBasis camera_basis(const rt_camera* c, int W, int H);
+bool finite_cam(const rt_camera* c);
 
 // ---------------------------------------------------------------------------
 // Device math

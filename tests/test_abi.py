@@ -47,6 +47,7 @@ def test_struct_sizes_match_header_layout():
     import ctypes
     assert ctypes.sizeof(rtb.rt_camera) == S.CAMERA_DTYPE.itemsize == 40
     assert ctypes.sizeof(rtb.rt_render_options) == 40
+    assert ctypes.sizeof(rtb.rt_tune) == 16
 
 
 def _base():

@@ -1,0 +1,190 @@
+"""Batched rendering (rt_batch_*): many frames of uneven scenes and sizes in
+one persistent launch must give the images that rendering each frame alone
+gives, and the oracle's, for every tune."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1504_03151_b300 as rtb
+from paper_1504_03151_b300 import build as rtb_build
+from paper_1504_03151_b300 import scenes as S
+
+from gpu_helpers import COLOUR_TOL, BUDGET, oracle_render
+
+pytestmark = pytest.mark.gpu
+
+SAME_TOL = 1e-5   # the same hits and terms, summed by float atomics in another order
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(gpu):
+    rtb_build.build()
+    torch.cuda.set_device(0)
+
+
+def small_terrain(w=72, h=40, depth=3, seed=7):
+    return S.scene_terrain(seed=seed, width=w, height=h, max_depth=depth, cells=(16, 12), n_ico=6, ico_level=2)
+
+
+def single_frame(scene, cam, w, h, depth, background):
+    out = torch.empty(w * h * 3, device="cuda")
+    rtb.rt_render_ex(scene.handle, cam, w, h, depth, out, rtb.make_options(background=background))
+    torch.cuda.synchronize()
+    return out.view(h * w, 3).double().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def frames():
+    """Four frames: three scenes, one of them twice with another camera and
+    size; sizes that do not divide into tiles."""
+    a = S.scene_spheres8(width=64, height=48, max_depth=3)
+    b = small_terrain()
+    c = S.single_sphere(width=33, height=17)
+    sa, sb, sc_ = rtb.Scene(a).build(), rtb.Scene(b).build(), rtb.Scene(c).build()
+    fr = [(sa, a, a.camera, 64, 48), (sb, b, b.camera, 72, 40), (sc_, c, c.camera, 33, 17),
+          (sb, b, S.camera((10.0, 8.0, 20.0), (0.0, 0.0, 0.0)), 40, 72)]
+    yield fr
+    for s in (sa, sb, sc_):
+        s.close()
+
+
+def make_batch(fr, depth=3, background=(0.1, 0.1, 0.1)):
+    outs = [torch.full((w * h * 3,), float("nan"), device="cuda") for _, _, _, w, h in fr]
+    b = rtb.Batch([f[0] for f in fr], [f[2] for f in fr], [f[3] for f in fr], [f[4] for f in fr], depth, outs,
+                  rtb.make_options(background=background))
+    return b, outs
+
+
+def images(outs, fr):
+    torch.cuda.synchronize()
+    return [o.view(h * w, 3).double().cpu().numpy() for o, (_, _, _, w, h) in zip(outs, fr)]
+
+
+def test_batch_matches_single_frames(frames):
+    b, outs = make_batch(frames)
+    b.render()
+    for img, (scene, sc, cam, w, h) in zip(images(outs, frames), frames):
+        ref = single_frame(scene, cam, w, h, 3, sc.background)
+        assert np.isfinite(img).all()
+        np.testing.assert_allclose(img, ref, atol=SAME_TOL, rtol=0)
+    b.close()
+
+
+def test_batch_matches_oracle():
+    """Colour parity with the FP64 oracle (the batch has no hit outputs)."""
+    a = S.scene_spheres8(width=48, height=40, max_depth=3)
+    c = S.single_sphere(width=33, height=17)
+    sa, sc_ = rtb.Scene(a).build(), rtb.Scene(c).build()
+    fr = [(sa, a, a.camera, 48, 40), (sc_, c, c.camera, 33, 17)]
+    b, outs = make_batch(fr)
+    b.render()
+    for img, (_, sc, _, w, h) in zip(images(outs, fr), fr):
+        ref = oracle_render(sc, mode="brute", width=w, height=h)
+        robust = ref["robust"] >= 1.0
+        err = np.abs(img - ref["rgb"]).max(axis=1)
+        assert not ((err > COLOUR_TOL) & robust).any()
+        assert (err > COLOUR_TOL).mean() <= BUDGET
+    b.close()
+    sa.close()
+    sc_.close()
+
+
+@pytest.mark.parametrize("tune", [(8, 4, 128, 0), (4, 8, 64, 0), (16, 2, 256, 0), (32, 1, 128, 2), (1, 32, 64, 1)])
+def test_every_tune_gives_the_same_image(frames, tune):
+    b, outs = make_batch(frames)
+    b.render(rtb.make_tune(*tune))
+    for img, (scene, sc, cam, w, h) in zip(images(outs, frames), frames):
+        np.testing.assert_allclose(img, single_frame(scene, cam, w, h, 3, sc.background), atol=SAME_TOL, rtol=0)
+    b.close()
+
+
+def test_batch_stats_are_the_frames_sums(frames):
+    b, outs = make_batch(frames)
+    st = b.render(stats=True)
+    prim = sec = shadow = 0
+    for scene, sc, cam, w, h in frames:
+        s1 = rtb.rt_render_ex(scene.handle, cam, w, h, 3, torch.empty(w * h * 3, device="cuda"),
+                              rtb.make_options(background=sc.background), stats=True)
+        prim += s1["primary"]
+        sec += s1["secondary"]
+        shadow += s1["shadow"]
+    assert st["primary"] == prim == sum(w * h for *_, w, h in frames)
+    assert st["secondary"] == sec
+    assert st["shadow"] == shadow
+    b.close()
+
+
+def test_many_tiny_frames():
+    """40 frames of random sizes (1x1 up to 50x50) over two scenes: the tile
+    list, its search and the image edges."""
+    rng = np.random.default_rng(5)
+    a = S.scene_spheres8(width=8, height=8, max_depth=2)
+    c = S.single_sphere(width=8, height=8)
+    sa, sc_ = rtb.Scene(a).build(), rtb.Scene(c).build()
+    fr = []
+    for i in range(40):
+        s, sc = (sa, a) if i % 3 else (sc_, c)
+        w, h = int(rng.integers(1, 51)), int(rng.integers(1, 51))
+        fr.append((s, sc, sc.camera, w, h))
+    b, outs = make_batch(fr, depth=2)
+    b.render(rtb.make_tune(16, 2, 64, 0))
+    for img, (scene, sc, cam, w, h) in zip(images(outs, fr), fr):
+        np.testing.assert_allclose(img, single_frame(scene, cam, w, h, 2, sc.background), atol=SAME_TOL, rtol=0)
+    b.close()
+    sa.close()
+    sc_.close()
+
+
+def test_autotune_graph_replay_and_new_cameras(frames):
+    b, outs = make_batch(frames)
+    tune, ms = b.autotune()
+    assert tune.tile_w * tune.tile_h == 32 and tune.block_threads in (64, 128, 256) and ms > 0
+    first = images(outs, frames)
+    b.render()   # the graph of the chosen tune, replayed
+    for x, y in zip(first, images(outs, frames)):
+        np.testing.assert_allclose(x, y, atol=SAME_TOL, rtol=0)
+    cams = [f[2] for f in frames]
+    cams[0] = S.camera((3.0, 4.0, 9.0), (0.0, 1.0, 0.0))
+    b.set_cameras(cams)
+    b.render()
+    scene, sc, _, w, h = frames[0]
+    np.testing.assert_allclose(images(outs, frames)[0], single_frame(scene, cams[0], w, h, 3, sc.background),
+                               atol=SAME_TOL, rtol=0)
+    b.close()
+
+
+def test_depth_zero_batch(frames):
+    b, outs = make_batch(frames, depth=0)
+    st = b.render(stats=True)
+    assert st["secondary"] == 0
+    for img, (scene, sc, cam, w, h) in zip(images(outs, frames), frames):
+        np.testing.assert_allclose(img, single_frame(scene, cam, w, h, 0, sc.background), atol=SAME_TOL, rtol=0)
+    b.close()
+
+
+def test_batch_argument_errors(frames):
+    scene, sc, cam, w, h = frames[0]
+    out = torch.empty(w * h * 3, device="cuda")
+    with pytest.raises(rtb.RtError):
+        rtb.rt_batch_create([], [], [], [], 3, [])
+    with pytest.raises(rtb.RtError):
+        rtb.rt_batch_create([scene.handle], [cam], [0], [h], 3, [out])
+    with pytest.raises(rtb.RtError):
+        rtb.rt_batch_create([scene.handle], [cam], [w], [h], 17, [out])
+    with pytest.raises(rtb.RtError):
+        rtb.rt_batch_create([scene.handle], [S.camera((0, 0, 0), (0, 0, 0))], [w], [h], 3, [out])
+    b = rtb.Batch([scene], [cam], [w], [h], 3, [out])
+    for bad in [(5, 6, 128, 0), (8, 4, 96, 0), (8, 4, 128, -1)]:
+        with pytest.raises(rtb.RtError):
+            b.render(rtb.make_tune(*bad))
+    b.close()
+    # a scene without a BVH
+    c = S.single_sphere(width=8, height=8)
+    raw = rtb.Scene(c)
+    o2 = torch.empty(8 * 8 * 3, device="cuda")
+    b2 = rtb.Batch([raw], [c.camera], [8], [8], 1, [o2])
+    with pytest.raises(rtb.RtError) as ei:
+        b2.render()
+    assert ei.value.status == rtb.RT_ERR_NOT_BUILT
+    b2.close()
+    raw.close()
