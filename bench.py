@@ -157,6 +157,63 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batch_leg(rtb, S, torch, dev, stream, flush, steps):
+    """64 scenes of uneven size (log-uniform 1e3-2e6 triangles, 16.6 M in all)
+    and resolution (256^2 .. 1280x720, 36.8 Mpixel), depth 4, in one
+    persistent launch; beside it, the same frames as one rt_render_ex each."""
+    scs = S.scene_batch()
+    D = 4
+    scenes = [rtb.Scene(x) for x in scs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for x in scenes:            # first builds allocate the scratch
+        x.build()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for x in scenes:
+        x.build()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    outs = [torch.empty(x.width * x.height * 3, device=dev) for x in scs]
+    opts = rtb.make_options(background=scs[0].background)
+    b = rtb.Batch(scenes, [x.camera for x in scs], [x.width for x in scs], [x.height for x in scs], D, outs, opts)
+    tune, tune_ms = b.autotune()
+    st = b.render(stats=True)
+    rays = st["primary"] + st["shadow"] + st["secondary"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        b.render()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(c) for a, c in ev) / steps
+    # the same frames, one launch sequence per frame (warm-up pass allocates their queues)
+    for x, sc_, o in zip(scenes, scs, outs):
+        rtb.rt_render_ex(x.handle, sc_.camera, sc_.width, sc_.height, D, o, opts)
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0.record(stream)
+    for x, sc_, o in zip(scenes, scs, outs):
+        rtb.rt_render_ex(x.handle, sc_.camera, sc_.width, sc_.height, D, o, opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_frame_ms = e0.elapsed_time(e1)
+    b.close()
+    for x in scenes:
+        x.close()
+    return {
+        "metric": "Mrays/s, 64 scenes in one persistent launch (CUDA graph)", "value": rays / (ms * 1e3),
+        "unit": UNIT, "ms_per_render": ms, "rays_per_render": rays, "primary": st["primary"],
+        "shadow": st["shadow"], "secondary": st["secondary"],
+        "workload": f"{len(scs)} scenes, {sum(x.n_prims for x in scs)} triangles (log-uniform 1e3-2e6), "
+                    f"{sum(x.width * x.height for x in scs)} pixels, depth 4, 4 lights",
+        "tune": rtb.tune_dict(tune), "autotune_best_ms": tune_ms,
+        "per_frame_launches_ms": per_frame_ms, "speedup_vs_per_frame_launches": per_frame_ms / ms,
+        "build_all_ms": build_ms, "l2": "flushed between renders",
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,6 +224,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--per-depth", action="store_true", help="queue every depth (no depth-first secondary paths)")
     ap.add_argument("--no-nrc", action="store_true", help="skip the radiance-cache leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-scene batch leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -316,6 +374,10 @@ def main():
         }
         rtb.rt_nrc_destroy(nrc)
 
+    batch_line = None
+    if world == 1 and not args.no_batch:
+        batch_line = batch_leg(rtb, S, torch, dev, stream, flush, max(args.steps // 2, 3))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, cores = cpu_oracle_sample(sc)
@@ -351,6 +413,8 @@ def main():
             line["cpu_baseline"] = cpu
         if nrc_line:
             line["radiance_cache"] = nrc_line
+        if batch_line:
+            line["batch"] = batch_line
         print(json.dumps(line), flush=True)
     scene.close()
     if dist:
