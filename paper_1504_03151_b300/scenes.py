@@ -264,16 +264,17 @@ def scene_spheres8(seed: int = 1, width: int = 256, height: int = 256, max_depth
 
 
 def _terrain_icospheres(rng, cells_x, cells_z, half_x, half_z, n_ico, ico_level,
-                        n_lights, ior_range=(1.5, 1.5), amplitude=3.0):
+                        n_lights, ior_range=(1.5, 1.5), amplitude=3.0, radius_range=(0.5, 2.0),
+                        base_freq=1.0 / 16.0, light_y=(20.0, 30.0)):
     xs = np.linspace(-half_x, half_x, cells_x + 1)
     zs = np.linspace(-half_z, half_z, cells_z + 1)
-    H = fbm_heights(rng, xs, zs, amplitude=amplitude)
+    H = fbm_heights(rng, xs, zs, amplitude=amplitude, base_freq=base_freq)
     tv0, tv1, tv2 = heightfield_triangles(xs, zs, H)
     mats = [material(MAT_DIFFUSE, (0.8, 0.8, 0.8))]
     v0s, v1s, v2s, ms = [tv0], [tv1], [tv2], [np.zeros(len(tv0), np.int64)]
     V, F = icosphere(ico_level)
     for i in range(n_ico):
-        r = rng.uniform(0.5, 2.0)
+        r = rng.uniform(*radius_range)
         cx = rng.uniform(-half_x + r, half_x - r)
         cz = rng.uniform(-half_z + r, half_z - r)
         cy = _bilinear_height(xs, zs, H, cx, cz) + r + rng.uniform(0.0, 2.0)
@@ -293,7 +294,7 @@ def _terrain_icospheres(rng, cells_x, cells_z, half_x, half_z, n_ico, ico_level,
         ms.append(np.full(len(F), len(mats) - 1, np.int64))
     tris = triangles_from(np.concatenate(v0s), np.concatenate(v1s), np.concatenate(v2s),
                           np.concatenate(ms))
-    lp = np.stack([rng.uniform(-half_x, half_x, n_lights), rng.uniform(20, 30, n_lights),
+    lp = np.stack([rng.uniform(-half_x, half_x, n_lights), rng.uniform(*light_y, n_lights),
                    rng.uniform(-half_z, half_z, n_lights)], axis=1)
     li = lights(lp, np.full((n_lights, 3), 1.0 / n_lights))
     return tris, np.concatenate(mats), li
@@ -333,6 +334,27 @@ def scene_batch(seed: int = 3, n_scenes: int = 64, max_depth: int = 4):
         w, h = res[int(rng.integers(0, 4))]
         out.append(scene_batch_member(int(rng.integers(0, 2**31)), n, w, h, max_depth))
     return out
+
+
+def scene_scaleup(seed: int = 5, width: int = 3840, height: int = 2160, max_depth: int = 8, cells: int = 2048,
+                  n_ico: int = 500, ico_level: int = 4):
+    """The scale-up workload: a 2048x2048-cell fBm terrain (8,388,608
+    triangles) over [-256, 256]^2 plus 500 level-4 icospheres (5,120
+    triangles each), 10,948,608 triangles; 8 lights; mirrors and dielectrics
+    with IOR U[1.3, 1.7]; depth 8.  Its four views (views_scaleup) look at
+    the centre from the compass points."""
+    rng = np.random.default_rng(seed)
+    tris, mats, li = _terrain_icospheres(rng, cells, cells, 256.0, 256.0, n_ico, ico_level, 8,
+                                         ior_range=(1.3, 1.7), amplitude=24.0, radius_range=(2.0, 8.0),
+                                         base_freq=1.0 / 128.0, light_y=(160.0, 240.0))
+    return Scene(f"scaleup{len(tris)}_{width}x{height}", np.zeros(0, SPHERE_DTYPE), tris, mats, li,
+                 views_scaleup()[0], width, height, max_depth)
+
+
+def views_scaleup():
+    """Four cameras on a circle of radius 300 at height 90, looking at the centre."""
+    return [camera((300.0 * sx, 90.0, 300.0 * sz), (0.0, 0.0, 0.0))
+            for sx, sz in ((0.0, 1.0), (1.0, 0.0), (0.0, -1.0), (-1.0, 0.0))]
 
 
 def single_sphere(width=65, height=65, albedo=(0.7, 0.5, 0.3), light=(0.0, 0.0, 10.0),
