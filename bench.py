@@ -214,6 +214,78 @@ def batch_leg(rtb, S, torch, dev, stream, flush, steps):
     }
 
 
+def scaleup_leg(rtb, S, torch, dev, stream, flush, steps, with_nrc):
+    """The scale-up workload: 10,948,608 triangles, four 3840x2160 views,
+    depth 8, 8 lights, as one batched launch; then the radiance cache on the
+    same views (one network, trained frame after frame) against the plain
+    full-depth frames."""
+    sc = S.scene_scaleup()
+    W, H, D = sc.width, sc.height, sc.max_depth
+    scene = rtb.Scene(sc).build()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    scene.build()
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    scene.build()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    views = S.views_scaleup()
+    outs = [torch.empty(W * H * 3, device=dev) for _ in views]
+    opts = rtb.make_options(background=sc.background)
+    b = rtb.Batch([scene] * 4, views, [W] * 4, [H] * 4, D, outs, opts)
+    tune, _ = b.autotune()
+    st = b.render(stats=True)
+    rays = st["primary"] + st["shadow"] + st["secondary"]
+    ts = []
+    for k in range(steps):
+        flush.zero_()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        b.render()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = sum(ts) / len(ts)
+    line = {
+        "metric": "Mrays/s, 4 views in one persistent launch", "value": rays / (ms * 1e3), "unit": UNIT,
+        "ms_per_render": ms, "rays_per_render": rays, "primary": st["primary"], "shadow": st["shadow"],
+        "secondary": st["secondary"], "build_ms": build_ms, "tune": rtb.tune_dict(tune),
+        "workload": f"{sc.n_prims} triangles (2048x2048-cell terrain + 500 L4 icospheres), 4 views "
+                    f"{W}x{H}, depth {D}, {len(sc.lights)} lights",
+    }
+    if with_nrc:
+        nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=1))
+        cached = torch.empty(W * H * 3, device=dev)
+        for k in range(32):                      # online training, the views in turn
+            rtb.rt_render_nrc(scene.handle, nrc, views[k % 4], W, H, D, cached, train=True, options=opts)
+        nrays = 0
+        nms, rel = [], []
+        for k, v in enumerate(views):
+            nst = rtb.rt_render_nrc(scene.handle, nrc, v, W, H, D, cached, train=True, options=opts, stats=True)
+            nrays += nst["primary"] + nst["shadow"] + nst["secondary"]
+            flush.zero_()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            rtb.rt_render_nrc(scene.handle, nrc, v, W, H, D, cached, train=True, options=opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            nms.append(e0.elapsed_time(e1))
+            x, r = cached.double(), outs[k].double()
+            rel.append(float(((x - r) ** 2 / (r ** 2 + 0.01)).mean()))
+        nrc_ms = sum(nms)
+        line["radiance_cache"] = {
+            "metric": "Mrays-equivalent/s (full-depth rays per cached frame, 4 views)",
+            "value": rays / (nrc_ms * 1e3), "ms_4_views": nrc_ms, "vs_plain_batch": ms / nrc_ms,
+            "relmse_vs_full_depth": rel, "rays_traced_4_views": nrays, "warmup_frames": 32,
+        }
+        rtb.rt_nrc_destroy(nrc)
+    b.close()
+    scene.close()
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,6 +297,7 @@ def main():
     ap.add_argument("--per-depth", action="store_true", help="queue every depth (no depth-first secondary paths)")
     ap.add_argument("--no-nrc", action="store_true", help="skip the radiance-cache leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-scene batch leg")
+    ap.add_argument("--no-scaleup", action="store_true", help="skip the 10.9M-triangle 4K leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -377,6 +450,9 @@ def main():
     batch_line = None
     if world == 1 and not args.no_batch:
         batch_line = batch_leg(rtb, S, torch, dev, stream, flush, max(args.steps // 2, 3))
+    scaleup_line = None
+    if world == 1 and not args.no_scaleup:
+        scaleup_line = scaleup_leg(rtb, S, torch, dev, stream, flush, 3, not args.no_nrc)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -415,6 +491,8 @@ def main():
             line["radiance_cache"] = nrc_line
         if batch_line:
             line["batch"] = batch_line
+        if scaleup_line:
+            line["scaleup"] = scaleup_line
         print(json.dumps(line), flush=True)
     scene.close()
     if dist:
