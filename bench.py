@@ -432,6 +432,40 @@ def main():
             t = torch.tensor([nrc_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             nrc_ms = float(t.item())
+        # the network's kernels alone, against the tensor-core peak: one training
+        # step on 65,536 samples and inference on 2^20 queries (random hits in
+        # the scene box; algorithmic FLOPs of the unpadded 96-64-64-64-64-3 MLP)
+        gen = torch.Generator(device=dev).manual_seed(5)
+        lo_b = torch.tensor(sc.triangles["v0"].min(0), device=dev, dtype=torch.float32)
+        hi_b = torch.tensor(sc.triangles["v0"].max(0), device=dev, dtype=torch.float32)
+
+        def random_hits(m):
+            p = lo_b + (hi_b - lo_b) * torch.rand(m, 3, device=dev, generator=gen)
+            nv = torch.nn.functional.normalize(torch.randn(m, 6, device=dev, generator=gen).view(m, 2, 3), dim=2)
+            return torch.cat([p, nv.view(m, 6)], 1).contiguous()
+
+        n_tr, n_inf = 65536, 1 << 20
+        pnv_tr, tgt = random_hits(n_tr), torch.rand(n_tr, 3, device=dev, generator=gen) + 0.05
+        pnv_inf, inf_out = random_hits(n_inf), torch.empty(n_inf, 3, device=dev)
+        kflops = {"train": n_tr * 99456, "infer": n_inf * 37248}   # 2*(fwd 18,624 + dX 12,480 + dW 18,624); 2*18,624
+        kms = {}
+        for name, fn in (("train", lambda: rtb.rt_nrc_train_step(nrc, h, pnv_tr, tgt, n_tr)),
+                         ("infer", lambda: rtb.rt_nrc_infer(nrc, h, pnv_inf, n_inf, inf_out))):
+            for _ in range(3):
+                fn()
+            kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+            for a_, b_ in kev:
+                a_.record(stream)
+                fn()
+                b_.record(stream)
+            torch.cuda.synchronize()
+            kms[name] = sum(a_.elapsed_time(b_) for a_, b_ in kev) / len(kev)
+        pk_n, pk_kind_n = peaks()
+        nrc_roof = {name: {"bound": "tensor", "achieved": kflops[name] / (kms[name] * 1e-3) / 1e12,
+                           "peak": pk_n["bf16_tflops"], "unit": "TFLOP/s",
+                           "frac": kflops[name] / (kms[name] * 1e-3) / 1e12 / pk_n["bf16_tflops"],
+                           "ms": kms[name], "flops": kflops[name], "peak_source": f"bf16 burst ({pk_kind_n})"}
+                    for name in kms}
         x, r = nrc_out.double(), full.double()
         relmse = float(((x - r) ** 2 / (r ** 2 + 0.01)).mean())
         mse01 = float(((x.clamp(0, 1) - r.clamp(0, 1)) ** 2).mean())
@@ -444,6 +478,7 @@ def main():
             "rays_traced_per_step": nst["primary"] + nst["shadow"] + nst["secondary"],
             "cache_hits": nst["hits_per_depth"][2],
             "step": "repack + BVH build + cached frame (inference) + training rays + one Adam step",
+            "kernel_roofline": nrc_roof,
         }
         rtb.rt_nrc_destroy(nrc)
 
