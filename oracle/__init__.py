@@ -62,6 +62,10 @@ def lib():
         L.orc_set_cache.argtypes = [P, I32, P, P, I32, P, P]
         L.orc_round_bf16.restype = D
         L.orc_round_bf16.argtypes = [D]
+        L.orc_set_area_lights.restype = I32
+        L.orc_set_area_lights.argtypes = [P, P, I64]
+        L.orc_set_pass.argtypes = [P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.orc_philox4x32.argtypes = [P, P, P]
         _lib = L
     return _lib
 
@@ -96,7 +100,21 @@ class OracleScene:
 
     @classmethod
     def from_scene(cls, sc, **kw):
-        return cls(sc.spheres, sc.triangles, sc.materials, sc.lights, sc.background, **kw)
+        o = cls(sc.spheres, sc.triangles, sc.materials, sc.lights, sc.background, **kw)
+        al = getattr(sc, "area_lights", None)
+        if al is not None and len(al):
+            o.set_area_lights(al)
+        return o
+
+    def set_area_lights(self, lights):
+        """Parallelogram lights in the rt_area_light layout (12 floats each)."""
+        self._alights = np.ascontiguousarray(lights)
+        if lib().orc_set_area_lights(self._h, _ptr(self._alights), len(self._alights)) != 0:
+            raise ValueError("oracle rejected the area lights (non-finite or degenerate)")
+
+    def set_pass(self, seed=0, index=0, strata=1, jitter=False):
+        """The pass later renders use (see orc_set_pass)."""
+        lib().orc_set_pass(self._h, int(seed), int(index), int(strata), int(bool(jitter)))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -176,6 +194,15 @@ class OracleScene:
         lib().orc_any_hits(self._h, n, _ptr(o), _ptr(d), tmin, _ptr(tmax), int(use_bvh), _ptr(occ),
                            _ptr(rb), nthreads)
         return occ.astype(bool), rb
+
+
+def philox4x32(ctr, key):
+    """Philox4x32-10 of a 4-word counter under a 2-word key (the oracle's)."""
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32(_ptr(c), _ptr(k), _ptr(out))
+    return out
 
 
 def camera_rays(camera, width, height, pixels=None):

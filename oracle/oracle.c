@@ -21,6 +21,15 @@
  * The readings of what the paper leaves open (camera model, offsets,
  * Fresnel-Schlick, background, constants) are stated at each function.
  *
+ * Area lights and passes (Sec. IV.A, Alg. 1: the paper samples one point
+ * of each light per pass and lets the image converge over passes): a pass
+ * k draws, for every path vertex, one stratified point on each
+ * parallelogram light and, optionally, a jittered point inside the pixel.
+ * The random numbers come from Philox4x32-10 (Salmon et al., "Parallel
+ * random numbers: as easy as 1, 2, 3", SC 2011), written here from that
+ * definition, keyed by the seed and counted by (pixel, pass, path vertex,
+ * slot); the progressive image is the mean of the passes.
+ *
  * Besides radiance the oracle reports, per pixel, how close any decision in
  * the pixel's path tree (which primitive is hit, whether a light is blocked,
  * front/back side, n.l > 0, total internal reflection) comes to flipping,
@@ -96,6 +105,10 @@ typedef struct {
 
 typedef struct { uint32_t kind; v3 albedo; double ks, shin, refl, ior; v3 emis; } mat_t;
 typedef struct { v3 pos, inten; } light_t;
+/* parallelogram light corner + a eu + b ev (a, b in [0, 1]); emits L on the
+ * side of nl = unit(eu x ev) */
+typedef struct { v3 corner, eu, ev, L, nl; double area; } alight_t;
+typedef struct { float corner[3], edge_u[3], edge_v[3], radiance[3]; } in_alight;
 typedef struct { v3 lo, hi; int64_t left, right, start, count; } node_t;
 
 struct orc_scene {
@@ -103,6 +116,11 @@ struct orc_scene {
   prim_t* prims;
   int64_t n_mats; mat_t* mats;
   int64_t n_lights; light_t* lights;
+  int64_t n_alights; alight_t* alights;
+  /* the pass being rendered: Philox key, pass index, strata per axis, and
+   * whether the camera ray is jittered inside its pixel */
+  uint32_t seed_lo, seed_hi;
+  int32_t pass, strata, jitter;
   v3 bg;
   double eps_scale, K;
   double l_max;        /* bound on the radiance any subtree returns */
@@ -504,7 +522,47 @@ static int refract_schlick(v3 d, v3 n, double n1, double n2, double* R, v3* dt, 
 /* ------------------------------------------------------------------ */
 /* shading: one hit                                                     */
 /* ------------------------------------------------------------------ */
-typedef struct { v3 o, d; v3 w; ray_t r; } child_t;
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10: ten rounds of two 32x32 -> 64-bit products whose high   */
+/* halves are mixed with the other counter words and the round key; the  */
+/* key grows by the Weyl constants after every round.                    */
+/* ------------------------------------------------------------------ */
+void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* uniform in [0, 1) from the top 24 bits (exact in FP32 and FP64) */
+static inline double unit24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+#define SLOT_PIXEL 0xFFFFFFFFu
+
+/* A stratified 2-D sample of pass k for (pixel, path vertex `code`, slot):
+ * over S x S consecutive passes each cell of an S x S grid is visited once,
+ * starting from a cell chosen per pixel and vertex; the point is uniform in
+ * its cell. */
+static void pass_sample(const orc_scene* s, int64_t pixel, uint32_t code, uint32_t slot, double* a, double* b) {
+  uint32_t key[2] = {s->seed_lo, s->seed_hi}, r[4], q[4];
+  uint32_t ctr[4] = {(uint32_t)pixel, (uint32_t)s->pass, code, slot};
+  orc_philox4x32(ctr, key, r);
+  /* the first cell of this (pixel, vertex, slot): the same in every pass */
+  uint32_t ctr0[4] = {(uint32_t)pixel, 0xFFFFFFFFu, code, slot};
+  orc_philox4x32(ctr0, key, q);
+  uint32_t S = (uint32_t)(s->strata > 0 ? s->strata : 1), cells = S * S;
+  uint32_t cell = ((uint32_t)s->pass % cells + q[0] % cells) % cells;
+  *a = ((double)(cell % S) + unit24(r[0])) / (double)S;
+  *b = ((double)(cell / S) + unit24(r[1])) / (double)S;
+}
+
+typedef struct { v3 o, d; v3 w; ray_t r; uint32_t code; } child_t;
 
 typedef struct {
   v3 local;            /* emission + (1 - rho) * sum over unblocked lights */
@@ -518,7 +576,7 @@ typedef struct {
  * returned local term is already weighted by w; children carry their own
  * absolute weights.  spawn = 0 at the last depth. */
 static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, double t, double hit_cos,
-                         int spawn, int use_bvh, int want_robust) {
+                         int spawn, int use_bvh, int want_robust, int64_t pixel, uint32_t code) {
   shade_t out;
   memset(&out, 0, sizeof out);
   out.robust = ROBUST_CAP;
@@ -591,6 +649,49 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
         if (relevant && maxc(contrib) >= 1e-3 && rb < out.robust) out.robust = rb;
         if (!occ) out.local = add(out.local, contrib);
       }
+      /* area lights: one stratified point on each per pass, the same term
+       * as a point light times A cos(theta_y) / r^2 (Eq. 8 over the light's
+       * area, sampled with density 1 / A) */
+      for (int64_t li = 0; li < s->n_alights; ++li) {
+        const alight_t* A = &s->alights[li];
+        double a, b;
+        pass_sample(s, pixel, code, (uint32_t)li, &a, &b);
+        v3 y = add(A->corner, add(scl(A->eu, a), scl(A->ev, b)));
+        v3 to = sub(y, ph);
+        double dist_c = len(to);
+        v3 l = scl(to, 1.0 / dist_c);
+        double nl = dot(n, l);
+        double cos_y = -dot(l, A->nl);
+        v3 vdir = scl(r->d, -1.0);
+        v3 rl = sub(scl(n, 2.0 * nl), l);                  /* reflect(-l, n) */
+        double rv = dot(rl, vdir);
+        double spec = rv > 0.0 ? pow(rv, m->shin) : 0.0;
+        v3 f = add(scl(m->albedo, nl), mk(m->ks * spec, m->ks * spec, m->ks * spec));
+        double G = A->area * cos_y / (dist_c * dist_c);
+        v3 contrib = scl(mul(mul(w, A->L), f), G * (1.0 - rho));
+        double uy = (Up + s->K * 3 * GAMMA32 * maxabs(y)) / dist_c;   /* direction to the sample */
+        int relevant = count_robust && maxc(scl(mul(w, A->L), (1.0 - rho) * fabs(G))) * (2.0 + m->ks) >= 1e-3;
+        if (relevant) {
+          double rb = fabs(nl) / (An + r->ed + uy);
+          if (rb < out.robust) out.robust = rb;
+          rb = fabs(cos_y) / (uy + s->K * 8 * GAMMA32);
+          if (rb < out.robust) out.robust = rb;
+        }
+        if (!(nl > 0.0) || !(cos_y > 0.0)) continue;
+        ray_t sr;
+        sr.o = o_up;
+        v3 to_y = sub(y, o_up);
+        double dist = len(to_y);
+        sr.d = scl(to_y, 1.0 / dist);
+        sr.eo = eo_child;
+        sr.en = en_child;
+        sr.ed = (eo_child + s->K * 3 * GAMMA32 * maxabs(y)) / dist + s->K * 4 * GAMMA32;
+        out.n_shadow++;
+        double rb = ROBUST_CAP;
+        int occ = any_hit(s, &sr, 0.0, dist - eps, use_bvh, relevant && maxc(contrib) >= 1e-3 ? &rb : NULL);
+        if (relevant && maxc(contrib) >= 1e-3 && rb < out.robust) out.robust = rb;
+        if (!occ) out.local = add(out.local, contrib);
+      }
     }
     if (spawn && rho > 0.0) {
       child_t* c = &out.child[out.n_children++];
@@ -600,6 +701,7 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
       c->r.en = en_child;
       c->r.ed = r->ed + 2.0 * An + s->K * 8 * GAMMA32;
       c->w = scl(w, rho);
+      c->code = code << 1;
     }
   } else {
     double n1 = inside ? m->ior : 1.0, n2 = inside ? 1.0 : m->ior;
@@ -619,6 +721,7 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
       c->r.en = en_child;
       c->r.ed = r->ed + 2.0 * An + s->K * 8 * GAMMA32;
       c->w = scl(w, R);
+      c->code = code << 1;
       if (has_t) {
         child_t* c2 = &out.child[out.n_children++];
         c2->r.o = sub(ph, scl(n, eps));
@@ -627,6 +730,7 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
         c2->r.en = en_child;
         c2->r.ed = r->ed + 3.0 * An + s->K * 8 * GAMMA32;
         c2->w = scl(w, 1.0 - R);
+        c2->code = (code << 1) | 1u;
       }
     }
   }
@@ -664,8 +768,11 @@ static v3 cache_radiance(const orc_scene* s, const ray_t* r, hit_t h) {
   return mk(y[0], y[1], y[2]);
 }
 
-/* Radiance arriving along r at depth `depth`, times the ray weight w. */
-static v3 trace_rec(trace_ctx* cx, const ray_t* r, int depth, v3 w, int32_t* prim0, double* t0) {
+/* Radiance arriving along r at depth `depth`, times the ray weight w.  The
+ * path vertex the ray leads to is `code`: 1 for the camera ray, then
+ * 2c (reflection) and 2c + 1 (refraction) for the children of vertex c. */
+static v3 trace_rec(trace_ctx* cx, const ray_t* r, int depth, v3 w, int64_t pixel, uint32_t code, int32_t* prim0,
+                    double* t0) {
   const orc_scene* s = cx->s;
   cx->counts[depth == 0 ? 0 : 2]++;
   cx->counts[3 + 3 * depth + 0]++;
@@ -676,27 +783,27 @@ static v3 trace_rec(trace_ctx* cx, const ray_t* r, int depth, v3 w, int32_t* pri
   if (h.prim < 0) return mul(w, s->bg);
   cx->counts[3 + 3 * depth + 2]++;
   if (depth == s->nrc_depth) return mul(w, cache_radiance(s, r, h));
-  shade_t sh = shade_hit(s, r, w, h.prim, h.t, h.cosn, depth < cx->max_depth, cx->use_bvh, 1);
+  shade_t sh = shade_hit(s, r, w, h.prim, h.t, h.cosn, depth < cx->max_depth, cx->use_bvh, 1, pixel, code);
   if (sh.robust < cx->robust) cx->robust = sh.robust;
   cx->counts[1] += (uint64_t)sh.n_shadow;
   cx->counts[3 + 3 * depth + 1] += (uint64_t)sh.n_shadow;
   v3 c = sh.local;
   for (int k = 0; k < sh.n_children; ++k)
-    c = add(c, trace_rec(cx, &sh.child[k].r, depth + 1, sh.child[k].w, NULL, NULL));
+    c = add(c, trace_rec(cx, &sh.child[k].r, depth + 1, sh.child[k].w, pixel, sh.child[k].code, NULL, NULL));
   return c;
 }
 
 /* The iteration-over-depth form (Sec. IV.A): all rays of one depth are
  * processed before the next; every contribution carries its explicit
  * weight.  Same arithmetic as trace_rec, accumulated in another order. */
-typedef struct { ray_t r; v3 w; } qray;
-static v3 trace_iter(trace_ctx* cx, const ray_t* r0, int32_t* prim0, double* t0) {
+typedef struct { ray_t r; v3 w; uint32_t code; } qray;
+static v3 trace_iter(trace_ctx* cx, const ray_t* r0, int64_t pixel, int32_t* prim0, double* t0) {
   const orc_scene* s = cx->s;
   int cap = 1 << (cx->max_depth + 2);
   qray* cur = (qray*)malloc(sizeof(qray) * (size_t)cap);
   qray* nxt = (qray*)malloc(sizeof(qray) * (size_t)cap);
   int ncur = 1, nnxt;
-  cur[0].r = *r0; cur[0].w = mk(1, 1, 1);
+  cur[0].r = *r0; cur[0].w = mk(1, 1, 1); cur[0].code = 1u;
   v3 pix = mk(0, 0, 0);
   for (int depth = 0; depth <= cx->max_depth && ncur > 0; ++depth) {
     nnxt = 0;
@@ -708,13 +815,15 @@ static v3 trace_iter(trace_ctx* cx, const ray_t* r0, int32_t* prim0, double* t0)
       if (h.prim < 0) { pix = add(pix, mul(cur[i].w, s->bg)); continue; }
       cx->counts[3 + 3 * depth + 2]++;
       if (depth == s->nrc_depth) { pix = add(pix, mul(cur[i].w, cache_radiance(s, &cur[i].r, h))); continue; }
-      shade_t sh = shade_hit(s, &cur[i].r, cur[i].w, h.prim, h.t, h.cosn, depth < cx->max_depth, 0, 0);
+      shade_t sh = shade_hit(s, &cur[i].r, cur[i].w, h.prim, h.t, h.cosn, depth < cx->max_depth, 0, 0, pixel,
+                             cur[i].code);
       cx->counts[1] += (uint64_t)sh.n_shadow;
       cx->counts[3 + 3 * depth + 1] += (uint64_t)sh.n_shadow;
       pix = add(pix, sh.local);
       for (int k = 0; k < sh.n_children; ++k) {
         nxt[nnxt].r = sh.child[k].r;
         nxt[nnxt].w = sh.child[k].w;
+        nxt[nnxt].code = sh.child[k].code;
         nnxt++;
       }
     }
@@ -730,17 +839,23 @@ static v3 trace_iter(trace_ctx* cx, const ray_t* r0, int32_t* prim0, double* t0)
 /* camera (the paper gives none): pinhole, vertical field of view,       */
 /* pixel centres at +0.5, row 0 at the top.                              */
 /* ------------------------------------------------------------------ */
-static void camera_ray(const in_cam* cam, int W, int H, int x, int y, v3* o, v3* d) {
+/* The ray through image point (px, py) in pixel units (the centre of pixel
+ * (x, y) is (x + 0.5, y + 0.5)). */
+static void camera_ray_at(const in_cam* cam, int W, int H, double px, double py, v3* o, v3* d) {
   v3 eye = f3(cam->eye), at = f3(cam->look_at), up = f3(cam->up);
   v3 f = unit(sub(at, eye));
   v3 r = unit(cross(f, up));
   v3 u = cross(r, f);
   double h = tan(0.5 * (double)cam->vfov_deg * M_PI / 180.0);
   double a = (double)W / (double)H;
-  double sx = (2.0 * (x + 0.5) / W - 1.0) * h * a;
-  double ty = (1.0 - 2.0 * (y + 0.5) / H) * h;
+  double sx = (2.0 * px / W - 1.0) * h * a;
+  double ty = (1.0 - 2.0 * py / H) * h;
   *o = eye;
   *d = unit(add(f, add(scl(r, sx), scl(u, ty))));
+}
+
+static void camera_ray(const in_cam* cam, int W, int H, int x, int y, v3* o, v3* d) {
+  camera_ray_at(cam, W, H, x + 0.5, y + 0.5, o, d);
 }
 
 void orc_camera_ray(const void* cam, int width, int height, int x, int y, double* o, double* d) {
@@ -771,6 +886,7 @@ orc_scene* orc_scene_create(const void* spheres, int64_t ns, const void* triangl
   s->eps_scale = eps_scale;
   s->K = fragile_k;
   s->nrc_depth = -1;
+  s->strata = 1;
   const in_mat* im = (const in_mat*)materials;
   double ks_max = 0, em_max = 0;
   for (int64_t i = 0; i < nm; ++i) {
@@ -850,12 +966,49 @@ bad:
 
 void orc_scene_free(orc_scene* s) {
   if (!s) return;
-  free(s->prims); free(s->mats); free(s->lights); free(s->nodes); free(s->order);
+  free(s->prims); free(s->mats); free(s->lights); free(s->alights); free(s->nodes); free(s->order);
   free(s->nrc_W); free(s->nrc_B);
   free(s);
 }
 
 int64_t orc_bvh_node_count(const orc_scene* s) { return s->n_nodes; }
+
+int orc_set_area_lights(orc_scene* s, const void* lights, int64_t n) {
+  if (!s || n < 0 || (n > 0 && !lights)) return 1;
+  const in_alight* il = (const in_alight*)lights;
+  alight_t* a = (alight_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(alight_t));
+  for (int64_t i = 0; i < n; ++i) {
+    if (!finite3(il[i].corner) || !finite3(il[i].edge_u) || !finite3(il[i].edge_v) || !finite3(il[i].radiance)) {
+      free(a);
+      return 1;
+    }
+    a[i].corner = f3(il[i].corner);
+    a[i].eu = f3(il[i].edge_u);
+    a[i].ev = f3(il[i].edge_v);
+    a[i].L = f3(il[i].radiance);
+    v3 c = cross(a[i].eu, a[i].ev);
+    a[i].area = len(c);
+    if (!(a[i].area > 0.0)) {
+      free(a);
+      return 1;
+    }
+    a[i].nl = scl(c, 1.0 / a[i].area);
+  }
+  free(s->alights);
+  s->alights = a;
+  s->n_alights = n;
+  /* a sampled area light has no small bound: track every decision */
+  if (n > 0) s->l_max = INFINITY;
+  return 0;
+}
+
+void orc_set_pass(orc_scene* s, uint64_t seed, int32_t pass, int32_t strata, int32_t jitter) {
+  s->seed_lo = (uint32_t)seed;
+  s->seed_hi = (uint32_t)(seed >> 32);
+  s->pass = pass;
+  s->strata = strata > 0 ? strata : 1;
+  s->jitter = jitter != 0;
+}
 
 void orc_set_cache(orc_scene* s, int depth, const double* W, const double* B, int bf16, const double* lo,
                    const double* inv_ext) {
@@ -898,7 +1051,9 @@ int orc_render(const orc_scene* s, const void* cam, int W, int H, int max_depth,
       int64_t pix = pixels ? pixels[i] : i;
       int x = (int)(pix % W), y = (int)(pix / W);
       ray_t r;
-      camera_ray((const in_cam*)cam, W, H, x, y, &r.o, &r.d);
+      double jx = 0.5, jy = 0.5;   /* the pixel centre, or the pass's point inside the pixel */
+      if (s->jitter) pass_sample(s, pix, 0u, SLOT_PIXEL, &jx, &jy);
+      camera_ray_at((const in_cam*)cam, W, H, x + jx, y + jy, &r.o, &r.d);
       r.eo = 0.0;
       r.en = 0.0;
       r.ed = s->K * 4 * GAMMA32;
@@ -908,8 +1063,8 @@ int orc_render(const orc_scene* s, const void* cam, int W, int H, int max_depth,
       int32_t p0 = -1;
       double t0 = INFINITY;
       v3 c;
-      if (mode == 2) c = trace_iter(&cx, &r, &p0, &t0);
-      else c = trace_rec(&cx, &r, 0, mk(1, 1, 1), &p0, &t0);
+      if (mode == 2) c = trace_iter(&cx, &r, pix, &p0, &t0);
+      else c = trace_rec(&cx, &r, 0, mk(1, 1, 1), pix, 1u, &p0, &t0);
       if (rgb) { rgb[3 * i] = c.x; rgb[3 * i + 1] = c.y; rgb[3 * i + 2] = c.z; }
       if (prim) prim[i] = p0;
       if (t) t[i] = p0 >= 0 ? t0 : INFINITY;

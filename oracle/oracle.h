@@ -45,6 +45,21 @@ orc_scene* orc_scene_create(const void* spheres, int64_t n_spheres,
 void orc_scene_free(orc_scene* s);
 int64_t orc_bvh_node_count(const orc_scene* s);
 
+/* Parallelogram area lights (rt_area_light layout: corner, edge_u, edge_v,
+ * radiance; 12 floats each), replacing earlier ones; they emit on the side
+ * of edge_u x edge_v.  Returns non-zero on a non-finite value or a
+ * degenerate parallelogram. */
+int orc_set_area_lights(orc_scene* s, const void* lights, int64_t n);
+
+/* The pass that orc_render renders: Philox key `seed`, pass index, strata
+ * per axis (S: stratified over S x S passes), and jitter != 0 to move the
+ * camera ray to a sampled point of its pixel.  Defaults: seed 0, pass 0,
+ * strata 1, no jitter. */
+void orc_set_pass(orc_scene* s, uint64_t seed, int32_t pass, int32_t strata, int32_t jitter);
+
+/* Philox4x32-10 of counter ctr[4] under key key[2] (exposed for tests). */
+void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
 /* Pinhole camera ray of pixel (x, y), row 0 at the top.  cam: rt_camera
  * layout (10 floats).  Writes origin o[3] and unit direction d[3]. */
 void orc_camera_ray(const void* cam, int width, int height, int x, int y,

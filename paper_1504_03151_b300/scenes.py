@@ -41,12 +41,15 @@ MATERIAL_DTYPE = np.dtype([
     ("reflectivity", "<f4"), ("ior", "<f4"), ("emission", "<f4", 3)])
 LIGHT_DTYPE = np.dtype([("position", "<f4", 3), ("intensity", "<f4", 3)])
 CAMERA_DTYPE = np.dtype([("eye", "<f4", 3), ("look_at", "<f4", 3), ("up", "<f4", 3), ("vfov_deg", "<f4")])
+AREA_LIGHT_DTYPE = np.dtype([("corner", "<f4", 3), ("edge_u", "<f4", 3), ("edge_v", "<f4", 3),
+                             ("radiance", "<f4", 3)])
 
 assert SPHERE_DTYPE.itemsize == 20
 assert TRIANGLE_DTYPE.itemsize == 40
 assert MATERIAL_DTYPE.itemsize == 44
 assert LIGHT_DTYPE.itemsize == 24
 assert CAMERA_DTYPE.itemsize == 40
+assert AREA_LIGHT_DTYPE.itemsize == 48
 
 MAT_DIFFUSE, MAT_MIRROR, MAT_DIELECTRIC = 0, 1, 2
 
@@ -66,6 +69,7 @@ class Scene:
     height: int
     max_depth: int
     background: tuple = BACKGROUND
+    area_lights: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, AREA_LIGHT_DTYPE))
 
     @property
     def n_prims(self) -> int:
@@ -78,6 +82,8 @@ class Scene:
             h.update(np.ascontiguousarray(a).tobytes())
         h.update(np.array([self.width, self.height, self.max_depth], np.int64).tobytes())
         h.update(np.array(self.background, np.float64).tobytes())
+        if len(self.area_lights):
+            h.update(np.ascontiguousarray(self.area_lights).tobytes())
         return h.hexdigest()
 
 
@@ -106,6 +112,17 @@ def lights(positions, intensities):
     a = np.zeros(len(positions), LIGHT_DTYPE)
     a["position"] = positions
     a["intensity"] = intensities
+    return a
+
+
+def area_lights(corners, edges_u, edges_v, radiances):
+    """Parallelogram lights corner + a edge_u + b edge_v (a, b in [0, 1]),
+    emitting `radiance` on the side of edge_u x edge_v."""
+    a = np.zeros(len(corners), AREA_LIGHT_DTYPE)
+    a["corner"] = corners
+    a["edge_u"] = edges_u
+    a["edge_v"] = edges_v
+    a["radiance"] = radiances
     return a
 
 
@@ -355,6 +372,15 @@ def views_scaleup():
     """Four cameras on a circle of radius 300 at height 90, looking at the centre."""
     return [camera((300.0 * sx, 90.0, 300.0 * sz), (0.0, 0.0, 0.0))
             for sx, sz in ((0.0, 1.0), (1.0, 0.0), (0.0, -1.0), (-1.0, 0.0))]
+
+
+def scene_spheres8_area(seed: int = 1, width: int = 256, height: int = 256, max_depth: int = 3) -> Scene:
+    """spheres8 lit by a 4 x 4 square area light at height 8 facing down
+    (radiance 2), besides its point light."""
+    sc = scene_spheres8(seed, width, height, max_depth)
+    sc.area_lights = area_lights([(-2.0, 8.0, -2.0)], [(4.0, 0.0, 0.0)], [(0.0, 0.0, 4.0)], [(2.0, 2.0, 2.0)])
+    sc.name = sc.name + "_area"
+    return sc
 
 
 def single_sphere(width=65, height=65, albedo=(0.7, 0.5, 0.3), light=(0.0, 0.0, 10.0),
