@@ -148,6 +148,31 @@ typedef struct rt_scene rt_scene;
 int rt_abi_version(void);
 const char* rt_last_error(void);
 
+/* A parallelogram light: the points corner + a edge_u + b edge_v, a and b
+ * in [0, 1].  It emits `radiance` (per channel, >= 0) on the side of
+ * edge_u x edge_v only, and is not geometry: rays do not hit it.  Each
+ * pass samples one point of it per shaded vertex (see rt_render_pass). */
+typedef struct rt_area_light {
+  float corner[3], edge_u[3], edge_v[3];
+  float radiance[3];
+} rt_area_light;
+
+/* One pass of a progressive render (Sec. IV.A: the paper samples each light
+ * once per pass and lets the image converge over passes).  The random
+ * numbers of pass `index` come from Philox4x32-10 keyed by `seed` and
+ * counted by (pixel, index, path vertex, slot); a sample is stratified over
+ * strata x strata consecutive passes.  jitter != 0 moves each camera ray to
+ * a sampled point inside its pixel (anti-aliasing); otherwise it goes
+ * through the pixel centre.  rt_render and rt_render_ex render pass
+ * {seed 0, index 0, strata 1, no jitter}. */
+typedef struct rt_pass {
+  uint64_t seed;
+  int32_t index;    /* >= 0 */
+  int32_t strata;   /* >= 1 */
+  int32_t jitter;
+  int32_t reserved; /* 0 */
+} rt_pass;
+
 /* Copies the host arrays to the device and packs them into the device
  * layout.  Spheres and triangles may be empty (not both NULL with n > 0).
  * Validates every value: RT_ERR_INVALID_ARG on NaN/Inf, radius <= 0 or a
@@ -155,6 +180,11 @@ const char* rt_last_error(void);
 rt_status rt_scene_create(const rt_sphere* spheres, size_t n_spheres, const rt_triangle* triangles,
                           size_t n_triangles, const rt_material* materials, size_t n_materials,
                           const rt_point_light* lights, size_t n_lights, rt_scene** out);
+
+/* Replaces the scene's area lights (n may be 0).  RT_ERR_INVALID_ARG on a
+ * non-finite value, a negative radiance or a degenerate parallelogram.
+ * Synchronous: waits for the device. */
+rt_status rt_scene_set_area_lights(rt_scene* s, const rt_area_light* lights, size_t n);
 
 /* Replaces the geometry with new arrays of the same counts (a moving
  * scene).  The arrays may live in host memory (pinned memory makes the
@@ -192,6 +222,15 @@ rt_status rt_bvh_export(rt_scene* s, float* nodes, int64_t nodes_capacity, int32
  * are a device layout of this library: the paper's tree is binary
  * (rt_bvh_export). */
 rt_status rt_bvh_export_wide(rt_scene* s, float* nodes, int64_t nodes_capacity, int64_t* n_nodes, void* stream);
+
+/* One pass of a progressive render: renders pass `pass->index` (with the
+ * options and limits of rt_render_ex) and folds it into accum_rgb_device
+ * (H*W*3 float32), the running mean of passes 0..index: pass 0 overwrites
+ * it, pass k adds (image - accum) / (k + 1).  Passes of one image must run
+ * in order on one stream. */
+rt_status rt_render_pass(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
+                         const rt_pass* pass, float* accum_rgb_device, const rt_render_options* options,
+                         void* stream);
 
 /* Renders one frame into out_rgb_device (H*W*3 float32, overwritten). */
 rt_status rt_render(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,

@@ -22,7 +22,7 @@ __all__ = [
     "rt_nrc_config_default", "rt_nrc_create", "rt_nrc_destroy", "rt_nrc_get_params", "rt_nrc_set_params",
     "rt_nrc_get_grads", "rt_nrc_infer", "rt_nrc_train_step", "rt_render_nrc",
     "rt_tune", "rt_batch_create", "rt_batch_set_cameras", "rt_batch_render", "rt_batch_autotune",
-    "rt_batch_destroy", "Batch",
+    "rt_batch_destroy", "Batch", "rt_pass", "rt_scene_set_area_lights", "rt_render_pass",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -98,6 +98,15 @@ def tune_dict(t: rt_tune) -> dict:
             "blocks_per_sm": t.blocks_per_sm}
 
 
+class rt_pass(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("index", ctypes.c_int32), ("strata", ctypes.c_int32),
+                ("jitter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def make_pass(index=0, seed=0, strata=1, jitter=False) -> rt_pass:
+    return rt_pass(int(seed), int(index), int(strata), int(bool(jitter)), 0)
+
+
 class rt_bvh_info(ctypes.Structure):
     _fields_ = [("n_prims", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("root", ctypes.c_int64),
                 ("max_depth", ctypes.c_int32),
@@ -151,6 +160,8 @@ def lib():
             "rt_batch_render": (I, [P, P, P, P]),
             "rt_batch_autotune": (I, [P, P, P, P]),
             "rt_batch_destroy": (I, [P]),
+            "rt_scene_set_area_lights": (I, [P, P, S]),
+            "rt_render_pass": (I, [P, P, I, I, I, P, P, P, P]),
             "rt_scene_destroy": (I, [P]),
         }
         for name, (res, args) in sigs.items():
@@ -419,6 +430,20 @@ def rt_render_nrc(scene, nrc, camera, width, height, max_depth, out_rgb, train=T
     return stats_dict(st, max_depth) if st is not None else None
 
 
+def rt_scene_set_area_lights(scene, lights):
+    """lights: numpy array in the rt_area_light layout (scenes.AREA_LIGHT_DTYPE)."""
+    a = np.ascontiguousarray(lights)
+    _check(lib().rt_scene_set_area_lights(scene, a.ctypes.data if len(a) else None, len(a)))
+
+
+def rt_render_pass(scene, camera, width, height, max_depth, pass_, accum_rgb, options=None, stream=None):
+    """Renders pass `pass_` (an rt_pass) and folds it into the running mean accum_rgb."""
+    cam = make_camera(camera)
+    _check(lib().rt_render_pass(scene, ctypes.byref(cam), width, height, max_depth, ctypes.byref(pass_),
+                                _dptr(accum_rgb), ctypes.byref(options) if options is not None else None,
+                                _stream(stream)))
+
+
 def rt_batch_create(scenes, cameras, widths, heights, max_depth, outs, options=None):
     """scenes: rt_scene handles; cameras: camera tuples or rt_camera; outs: device tensors."""
     n = len(scenes)
@@ -495,6 +520,9 @@ class Scene:
     def __init__(self, sc):
         self.sc = sc
         self.handle = rt_scene_create(sc.spheres, sc.triangles, sc.materials, sc.lights)
+        al = getattr(sc, "area_lights", None)
+        if al is not None and len(al):
+            rt_scene_set_area_lights(self.handle, al)
 
     def build(self, stream=None):
         rt_bvh_build(self.handle, stream)

@@ -61,6 +61,7 @@ struct BatchParams {
   int tile_w, tile_h;
   float bg_r, bg_g, bg_b, eps_scale;
   BatchCounts* cnt;
+  PassInfo ps;   // area-light samples and camera jitter: pass 0 of seed 0, no jitter
 };
 
 __device__ __forceinline__ void add_rgb(float* fb, int pixel, f3 c) {
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
   f3 o = mk3(0, 0, 0), d = mk3(0, 0, 1), w = mk3(0, 0, 0);
   int depth = 0, pixel = 0;
   float tmax_item = 0.f;
+  uint32_t code = 1u;   // path vertex of a segment's hit (keys the pass's samples)
   // the frame of the warp's current tile: every item of the warp belongs to it
   DevScene sc;
   sc.n_prims = 0;
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
       d = xyz(local[nl][1]);
       depth = __float_as_int(local[nl][1].w);
       w = xyz(local[nl][2]);
+      code = __float_as_uint(local[nl][2].w);
       have = true;
     }
     __syncwarp();   // rays pushed by this warp's lanes are visible
@@ -123,7 +126,8 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
         d = xyz(r[1]);
         depth = __float_as_int(r[1].w);
         w = xyz(r[2]);
-        tmax_item = r[2].w;
+        tmax_item = r[2].w;              // a shadow ray's length,
+        code = __float_as_uint(r[2].w);  // or a segment's path vertex
         have = true;
       }
       __syncwarp();
@@ -152,10 +156,13 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
       const int y = (int)(k / (unsigned)bs->tiles_x) * bp.tile_h + lane / bp.tile_w;
       if (x < W && y < H) {
         const CamBasis cb = bs->cam;
-        camera_ray(cb, W, H, x, y, o, d);
         pixel = y * W + x;
+        float px, py;
+        pass_pixel_point(bp.ps, pixel, x, y, px, py);
+        camera_ray_at(cb, W, H, px, py, o, d);
         w = mk3(1.f, 1.f, 1.f);
         depth = 0;
+        code = 1u;
         have = true;
       }
       continue;   // to the top: a tile cut by the image edge still has lanes with work
@@ -182,12 +189,20 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
         Surface sf = surface_at(sc, hit, o, d, t, bp.eps_scale);
         if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_rgb(fb, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
-          for (int li = 0; li < sc.n_lights; ++li) {
+          // point lights, then one sampled point of each area light
+          for (int li = 0; li < sc.n_lights + sc.n_alights; ++li) {
             f3 contrib, os, sd;
             float tmax;
-            if (!light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd,
-                            tmax))
-              continue;
+            bool lit;
+            if (li < sc.n_lights) {
+              lit = light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd,
+                               tmax);
+            } else {
+              float a, b;
+              pass_sample(bp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
+              lit = area_term(sf, d, w, sc.alights + 4 * (li - sc.n_lights), a, b, contrib, os, sd, tmax);
+            }
+            if (!lit) continue;
             atomicAdd(&s_cnt[1][depth], 1u);
             // to the warp's pending stack for a free lane; traced here when it is full
             int pos = atomicAdd(&s_np[warp], 1);
@@ -218,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
       int rank = __popc(m2 & lt);
       float4 r0 = make_float4(ch.or_.x, ch.or_.y, ch.or_.z, __int_as_float(pixel));
       float4 r1 = make_float4(ch.dr.x, ch.dr.y, ch.dr.z, __int_as_float(depth + 1));
-      float4 r2 = make_float4(ch.wr.x, ch.wr.y, ch.wr.z, 0.f);
+      float4 r2 = make_float4(ch.wr.x, ch.wr.y, ch.wr.z, __uint_as_float(code << 1));
       if (two) {
         if (rank < room) {
           float4* r = s_pend[warp][np2 + rank];
@@ -244,11 +259,13 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
         o = ch.ot;
         d = ch.dt;
         w = ch.wt;
+        code = (code << 1) | 1u;
         ++depth;
       } else if (ch.want_r) {
         o = ch.or_;
         d = ch.dr;
         w = ch.wr;
+        code <<= 1;
         ++depth;
       } else {
         have = false;
@@ -375,6 +392,8 @@ static rt_status batch_graph(rt_batch* b, const rt_tune& tune, unsigned n_tiles,
   bp.bg_b = b->opt.background[2];
   bp.eps_scale = b->opt.eps_scale;
   bp.cnt = (BatchCounts*)b->counts.p;
+  memset(&bp.ps, 0, sizeof(bp.ps));
+  bp.ps.strata = 1;
   cudaStream_t cs = b->cap_stream;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: begin capture");

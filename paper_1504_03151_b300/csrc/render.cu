@@ -61,6 +61,7 @@ struct FrameParams {
   unsigned train_batch;     // wanted training samples; selection probability = batch / rays
   uint32_t seed;
   const unsigned* prev_hits;   // depth-first frames: cache hits of the previous frame (0: take all)
+  PassInfo ps;                 // the pass: camera jitter and area-light samples
 };
 
 // Adds radiance to a pixel, or to a training target when the ray belongs to
@@ -121,13 +122,18 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
     bool active = idx < n_items;
     f3 o, d, w;
     int pixel = 0;
+    uint32_t code = 1u;   // path vertex of the ray's hit
     if (kPrimary) {
       int tile = (int)(idx >> 5);
       int x = (tile % fp.tiles_x) * 8 + (lane & 7);
       int y = (tile / fp.tiles_x) * 4 + (lane >> 3);
       active = active && x < fp.W && y < fp.H;
+      x = min(x, fp.W - 1);
+      y = min(y, fp.H - 1);
       pixel = y * fp.W + x;
-      camera_ray(fp.cam, fp.W, fp.H, min(x, fp.W - 1), min(y, fp.H - 1), o, d);
+      float px, py;
+      pass_pixel_point(fp.ps, pixel, x, y, px, py);
+      camera_ray_at(fp.cam, fp.W, fp.H, px, py, o, d);
       w = mk3(1.f, 1.f, 1.f);
     } else {
       float4 q0 = make_float4(0, 0, 0, 0), q1 = make_float4(0, 0, 1, 0), q2 = make_float4(0, 0, 0, 0);
@@ -140,6 +146,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
       pixel = __float_as_int(q0.w);
       d = xyz(q1);
       w = xyz(q2);
+      code = __float_as_uint(q2.w);
     }
     // closest hit
     float t = INFINITY;
@@ -201,6 +208,20 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
       unsigned pos = warp_push(&ctr->shadow[depth], valid, fp.shadow_cap, ok, sc.status);
       if (ok) store_ray(fp.shadowq[depth & 1], pos, os, pixel, sd, tmax, contrib);
     }
+    // area lights: one sampled point of each per pass
+    for (int li = 0; li < sc.n_alights; ++li) {
+      f3 contrib = mk3(0, 0, 0), os = mk3(0, 0, 0), sd = mk3(0, 0, 1);
+      float tmax = 0.f;
+      bool valid = false;
+      if (local) {
+        float a, b;
+        pass_sample(fp.ps, pixel, code, (uint32_t)li, a, b);
+        valid = area_term(sf, d, w, sc.alights + 4 * li, a, b, contrib, os, sd, tmax);
+      }
+      bool ok;
+      unsigned pos = warp_push(&ctr->shadow[depth], valid, fp.shadow_cap, ok, sc.status);
+      if (ok) store_ray(fp.shadowq[depth & 1], pos, os, pixel, sd, tmax, contrib);
+    }
     // reflection / refraction rays (Fig. 3), not past the last depth
     Children ch;
     ch.want_r = ch.want_t = false;
@@ -208,9 +229,9 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
     {
       bool ok;
       unsigned pos = warp_push(&ctr->rays[depth + 1], ch.want_r, fp.ray_cap, ok, sc.status);
-      if (ok) store_ray(qout, pos, ch.or_, pixel, ch.dr, INFINITY, ch.wr);
+      if (ok) store_ray(qout, pos, ch.or_, pixel, ch.dr, INFINITY, ch.wr, code << 1);
       pos = warp_push(&ctr->rays[depth + 1], ch.want_t, fp.ray_cap, ok, sc.status);
-      if (ok) store_ray(qout, pos, ch.ot, pixel, ch.dt, INFINITY, ch.wt);
+      if (ok) store_ray(qout, pos, ch.ot, pixel, ch.dt, INFINITY, ch.wt, (code << 1) | 1u);
     }
   }
   flush_work<kCount>(ctr, 0, depth, wc);
@@ -302,6 +323,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
   f3 o = mk3(0, 0, 0), d = mk3(0, 0, 1), w = mk3(0, 0, 0);
   int depth = d0, pixel = 0;
   float tmax_item = 0.f;
+  uint32_t code = 1u;   // path vertex of a segment's hit (keys the pass's samples)
   // queue rays a warp takes at a time: spread over all warps, so that every
   // warp starts with free lanes for the children and shadow rays it makes
   const unsigned n_warps = gridDim.x * (blockDim.x >> 5);
@@ -315,6 +337,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
       d = xyz(local[nl][1]);
       depth = __float_as_int(local[nl][1].w);
       w = xyz(local[nl][2]);
+      code = __float_as_uint(local[nl][2].w);
       have = true;
     }
     __syncwarp();   // shadow rays pushed by this warp's lanes are visible
@@ -330,7 +353,8 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
         d = xyz(r[1]);
         depth = __float_as_int(r[1].w);
         w = xyz(r[2]);
-        tmax_item = r[2].w;
+        tmax_item = r[2].w;              // a shadow ray's length,
+        code = __float_as_uint(r[2].w);  // or a segment's path vertex
         have = true;
       }
       __syncwarp();
@@ -352,6 +376,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
         pixel = __float_as_int(q0.w);
         d = xyz(q1);
         w = xyz(q2);
+        code = __float_as_uint(q2.w);
         depth = d0;
         have = true;
       }
@@ -415,12 +440,20 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
       if (live) {
         if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
-          for (int li = 0; li < sc.n_lights; ++li) {
+          // point lights, then one sampled point of each area light
+          for (int li = 0; li < sc.n_lights + sc.n_alights; ++li) {
             f3 contrib, os, sd;
             float tmax;
-            if (!light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd,
-                            tmax))
-              continue;
+            bool lit;
+            if (li < sc.n_lights) {
+              lit = light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd,
+                               tmax);
+            } else {
+              float a, b;
+              pass_sample(fp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
+              lit = area_term(sf, d, w, sc.alights + 4 * (li - sc.n_lights), a, b, contrib, os, sd, tmax);
+            }
+            if (!lit) continue;
             atomicAdd(&s_cnt[1][depth], 1u);
             // to the warp's pending stack for a free lane; traced here when it is full
             int pos = atomicAdd(&s_np[warp], 1);
@@ -456,7 +489,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
       int rank = __popc(m2 & lt);
       float4 r0 = make_float4(ch.or_.x, ch.or_.y, ch.or_.z, __int_as_float(pixel));
       float4 r1 = make_float4(ch.dr.x, ch.dr.y, ch.dr.z, __int_as_float(depth + 1));
-      float4 r2 = make_float4(ch.wr.x, ch.wr.y, ch.wr.z, 0.f);
+      float4 r2 = make_float4(ch.wr.x, ch.wr.y, ch.wr.z, __uint_as_float(code << 1));
       if (two) {
         if (rank < room) {
           float4* r = s_pend[warp][np2 + rank];
@@ -482,11 +515,13 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
         o = ch.ot;
         d = ch.dt;
         w = ch.wt;
+        code = (code << 1) | 1u;
         ++depth;
       } else if (ch.want_r) {
         o = ch.or_;
         d = ch.dr;
         w = ch.wr;
+        code <<= 1;
         ++depth;
       } else {
         have = false;
@@ -558,6 +593,7 @@ static FrameParams frame_defaults() {
   fp.target = nullptr;
   fp.infer_q = fp.train_q = nullptr;
   fp.prev_hits = nullptr;
+  fp.ps.strata = 1;   // pass 0 of seed 0, no jitter
   return fp;
 }
 
@@ -659,7 +695,7 @@ static rt_status ensure_side_stream(rt_scene* s) {
 
 static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, int D, float* out,
                              const rt_render_options* opt_in, int32_t* aov_prim, float* aov_t, rt_render_stats* stats,
-                             cudaStream_t st, rt_nrc* nrc = nullptr, int train = 0) {
+                             cudaStream_t st, rt_nrc* nrc = nullptr, int train = 0, const rt_pass* pass = nullptr) {
   if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_render: scene is NULL");
   if (!cam || !finite_cam(cam)) return set_error(RT_ERR_INVALID_ARG, "rt_render: invalid camera");
   if (W < 1 || H < 1) return set_error(RT_ERR_INVALID_ARG, "rt_render: width and height must be >= 1");
@@ -695,6 +731,13 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   int64_t tcap = opt.traversal_cap > 0 ? opt.traversal_cap : 4 * std::max<int64_t>(s->n_nodes4, 1) + 64;
   int cap = (int)std::min<int64_t>(tcap, 0x7fffffff);
   FrameParams fp = frame_defaults();
+  if (pass) {
+    fp.ps.seed_lo = (uint32_t)pass->seed;
+    fp.ps.seed_hi = (uint32_t)(pass->seed >> 32);
+    fp.ps.pass = pass->index;
+    fp.ps.strata = pass->strata;
+    fp.ps.jitter = pass->jitter != 0;
+  }
   fp.cam = camera_basis(cam, W, H);
   fp.W = W;
   fp.H = H;
@@ -876,6 +919,31 @@ rt_status rt_render_host(rt_scene* s, const rt_camera* cam, int width, int heigh
   return RT_OK;
 }
 
+// pass k folded into the running mean: accum += (image - accum) / (k + 1)
+__global__ void k_accumulate(float* __restrict__ accum, const float* __restrict__ img, size_t n, int k) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  accum[i] = k == 0 ? img[i] : accum[i] + (img[i] - accum[i]) / (float)(k + 1);
+}
+
+rt_status rt_render_pass(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth, const rt_pass* pass,
+                         float* accum, const rt_render_options* opt, void* stream) {
+  if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_render_pass: scene is NULL");
+  if (!pass || !accum) return set_error(RT_ERR_INVALID_ARG, "rt_render_pass: NULL pass or image");
+  if (pass->index < 0 || pass->strata < 1 || pass->reserved != 0)
+    return set_error(RT_ERR_INVALID_ARG, "rt_render_pass: index < 0, strata < 1 or reserved != 0");
+  if (width < 1 || height < 1) return set_error(RT_ERR_INVALID_ARG, "rt_render_pass: bad size");
+  size_t n = (size_t)width * height * 3;
+  rt_status rs = ensure(s->pass_img, n * sizeof(float));
+  if (rs) return rs;
+  cudaStream_t st = (cudaStream_t)stream;
+  rs = render_impl(s, cam, width, height, max_depth, (float*)s->pass_img.p, opt, nullptr, nullptr, nullptr, st,
+                   nullptr, 0, pass);
+  if (rs) return rs;
+  k_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(accum, (const float*)s->pass_img.p, n, pass->index);
+  return cuda_error(cudaGetLastError(), "rt_render_pass");
+}
+
 rt_status rt_render_nrc(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int width, int height, int max_depth,
                         float* out, int train, const rt_render_options* opt, rt_render_stats* stats, void* stream) {
   if (!nrc) return set_error(RT_ERR_INVALID_ARG, "rt_render_nrc: cache is NULL");
@@ -930,6 +998,8 @@ rt_status rt_scene_destroy(rt_scene* s) {
   release(s->prims_leaf);
   release(s->mats);
   release(s->lights);
+  release(s->alights);
+  release(s->pass_img);
   release(s->nodes);
   release(s->nodes4);
   release(s->build_tmp);

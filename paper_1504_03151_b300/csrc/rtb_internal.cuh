@@ -82,8 +82,10 @@ struct DevScene {
   const float4* nodes;      // 4-wide nodes, 8 float4 each, one per binary node slot
   const float4* mats;       // 3 per material
   const float4* lights;     // 2 per light
+  const float4* alights;    // 4 per area light: (corner, area) (edge_u, n.x) (edge_v, n.y) (radiance, n.z)
   int n_prims;
   int n_lights;
+  int n_alights;
   int n_nodes;              // node slots (links are checked against it)
   int root;                 // root node index (-1: no node)
   int use_bvh;
@@ -112,6 +114,9 @@ struct rt_scene {
   rtb::Buf prims_id;             // packed records, primitive-id order
   rtb::Buf prims_leaf;           // packed records, BVH leaf order
   rtb::Buf mats, lights;
+  rtb::Buf alights;              // area lights, 4 float4 each
+  rtb::Buf pass_img;             // one pass of a progressive render
+  int64_t n_alights = 0;
   // BVH
   bool built = false;
   int root = -1;
@@ -186,11 +191,17 @@ struct CamBasis {
   float h, aspect;
 };
 
-__device__ __forceinline__ void camera_ray(const CamBasis& cb, int W, int H, int x, int y, f3& o, f3& d) {
-  float sx = (2.0f * ((float)x + 0.5f) / (float)W - 1.0f) * cb.h * cb.aspect;
-  float ty = (1.0f - 2.0f * ((float)y + 0.5f) / (float)H) * cb.h;
+// The ray through image point (px, py) in pixel units; the centre of
+// pixel (x, y) is (x + 0.5, y + 0.5).
+__device__ __forceinline__ void camera_ray_at(const CamBasis& cb, int W, int H, float px, float py, f3& o, f3& d) {
+  float sx = (2.0f * px / (float)W - 1.0f) * cb.h * cb.aspect;
+  float ty = (1.0f - 2.0f * py / (float)H) * cb.h;
   o = cb.eye;
   d = normalize(cb.f + cb.r * sx + cb.u * ty);
+}
+
+__device__ __forceinline__ void camera_ray(const CamBasis& cb, int W, int H, int x, int y, f3& o, f3& d) {
+  camera_ray_at(cb, W, H, (float)x + 0.5f, (float)y + 0.5f, o, d);
 }
 
 // ---------------------------------------------------------------------------

@@ -95,6 +95,8 @@ DevScene dev_scene(const rt_scene* s, bool use_bvh) {
   d.lights = (const float4*)s->lights.p;
   d.n_prims = (int)s->n_prims;
   d.n_lights = (int)s->n_lights;
+  d.alights = (const float4*)s->alights.p;
+  d.n_alights = (int)s->n_alights;
   d.n_nodes = (int)s->n_nodes4;
   d.root = use_bvh ? s->root : -1;
   d.use_bvh = use_bvh ? 1 : 0;
@@ -230,6 +232,40 @@ rt_status rt_scene_create(const rt_sphere* spheres, size_t n_spheres, const rt_t
     return cuda_error(e, "rt_scene_create");
   }
   *out = s;
+  return RT_OK;
+}
+
+rt_status rt_scene_set_area_lights(rt_scene* s, const rt_area_light* lights, size_t n) {
+  if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_scene_set_area_lights: scene is NULL");
+  if (n && !lights) return set_error(RT_ERR_INVALID_ARG, "rt_scene_set_area_lights: NULL array with n > 0");
+  if (n > (1u << 20)) return set_error(RT_ERR_UNSUPPORTED, "rt_scene_set_area_lights: more than 2^20 lights");
+  std::vector<float4> rec(4 * (n ? n : 1));
+  for (size_t i = 0; i < n; ++i) {
+    const rt_area_light& a = lights[i];
+    if (!finite3(a.corner) || !finite3(a.edge_u) || !finite3(a.edge_v) || !finite3(a.radiance) ||
+        a.radiance[0] < 0.f || a.radiance[1] < 0.f || a.radiance[2] < 0.f)
+      return set_error(RT_ERR_INVALID_ARG, "rt_scene_set_area_lights: non-finite value or negative radiance");
+    // normal and area from edge_u x edge_v (host FP64, stored in FP32)
+    double cx = (double)a.edge_u[1] * a.edge_v[2] - (double)a.edge_u[2] * a.edge_v[1];
+    double cy = (double)a.edge_u[2] * a.edge_v[0] - (double)a.edge_u[0] * a.edge_v[2];
+    double cz = (double)a.edge_u[0] * a.edge_v[1] - (double)a.edge_u[1] * a.edge_v[0];
+    double area = std::sqrt(cx * cx + cy * cy + cz * cz);
+    if (!(area > 0.0) || !std::isfinite(area))
+      return set_error(RT_ERR_INVALID_ARG, "rt_scene_set_area_lights: degenerate parallelogram");
+    rec[4 * i + 0] = make_float4(a.corner[0], a.corner[1], a.corner[2], (float)area);
+    rec[4 * i + 1] = make_float4(a.edge_u[0], a.edge_u[1], a.edge_u[2], (float)(cx / area));
+    rec[4 * i + 2] = make_float4(a.edge_v[0], a.edge_v[1], a.edge_v[2], (float)(cy / area));
+    rec[4 * i + 3] = make_float4(a.radiance[0], a.radiance[1], a.radiance[2], (float)(cz / area));
+  }
+  cudaError_t e = cudaSetDevice(s->device);
+  if (e != cudaSuccess) return cuda_error(e, "rt_scene_set_area_lights");
+  rt_status st = ensure(s->alights, rec.size() * 16);
+  if (st) return st;
+  // the frames already queued on any stream may still read the old lights
+  e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(s->alights.p, rec.data(), rec.size() * 16, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "rt_scene_set_area_lights");
+  s->n_alights = (int64_t)n;
   return RT_OK;
 }
 

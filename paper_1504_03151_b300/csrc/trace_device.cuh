@@ -302,11 +302,15 @@ __device__ __forceinline__ unsigned warp_push(unsigned* counter, bool pred, unsi
   return pos;
 }
 
-__device__ __forceinline__ void store_ray(float4* q, unsigned pos, f3 o, int pixel, f3 d, float tmax, f3 w) {
+// A ray record; `code` is the path vertex the ray leads to (camera ray 1,
+// children of vertex c: 2c reflection, 2c + 1 refraction), which keys the
+// pass's random numbers there.
+__device__ __forceinline__ void store_ray(float4* q, unsigned pos, f3 o, int pixel, f3 d, float tmax, f3 w,
+                                          uint32_t code = 0u) {
   float4* p = q + 3 * (size_t)pos;
   p[0] = make_float4(o.x, o.y, o.z, __int_as_float(pixel));
   p[1] = make_float4(d.x, d.y, d.z, tmax);
-  p[2] = make_float4(w.x, w.y, w.z, 0.f);
+  p[2] = make_float4(w.x, w.y, w.z, __uint_as_float(code));
 }
 
 
@@ -317,6 +321,56 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
   x *= 0x846ca68bu;
   x ^= x >> 16;
   return x;
+}
+
+// ---------------------------------------------------------------------------
+// passes of a progressive render: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC 2011), counted by
+// (pixel, pass, path vertex, slot) and keyed by the seed
+// ---------------------------------------------------------------------------
+struct PassInfo {
+  uint32_t seed_lo, seed_hi;
+  int pass, strata, jitter;
+};
+
+constexpr uint32_t kSlotPixel = 0xFFFFFFFFu;   // the camera jitter's slot (area light i uses slot i)
+
+__device__ __forceinline__ uint4 philox4x32(uint4 c, uint2 k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// uniform in [0, 1) from the top 24 bits (exact in FP32)
+__device__ __forceinline__ float unit24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// A stratified 2-D sample of the pass for (pixel, path vertex `code`,
+// slot): over S x S consecutive passes each cell of an S x S grid is
+// visited once, from a first cell fixed per pixel, vertex and slot; the
+// point is uniform in its cell.
+__device__ __forceinline__ void pass_sample(const PassInfo& ps, int pixel, uint32_t code, uint32_t slot, float& a,
+                                            float& b) {
+  const uint2 key = make_uint2(ps.seed_lo, ps.seed_hi);
+  const uint4 r = philox4x32(make_uint4((uint32_t)pixel, (uint32_t)ps.pass, code, slot), key);
+  const uint4 q = philox4x32(make_uint4((uint32_t)pixel, 0xFFFFFFFFu, code, slot), key);
+  const uint32_t S = ps.strata > 0 ? (uint32_t)ps.strata : 1u, cells = S * S;
+  const uint32_t cell = ((uint32_t)ps.pass % cells + q.x % cells) % cells;
+  a = ((float)(cell % S) + unit24(r.x)) / (float)S;
+  b = ((float)(cell / S) + unit24(r.y)) / (float)S;
+}
+
+// The image point a pass traces pixel (x, y) through.
+__device__ __forceinline__ void pass_pixel_point(const PassInfo& ps, int pixel, int x, int y, float& px, float& py) {
+  float jx = 0.5f, jy = 0.5f;
+  if (ps.jitter) pass_sample(ps, pixel, 0u, kSlotPixel, jx, jy);
+  px = (float)x + jx;
+  py = (float)y + jy;
 }
 
 // ---------------------------------------------------------------------------
@@ -367,6 +421,35 @@ __device__ __forceinline__ bool light_term(const Surface& sf, f3 d, f3 w, float4
   contrib = w * xyz(L1) * f * (1.f - sf.rho);
   o_s = sf.p + sf.n * sf.eps;
   f3 to_l = lp - o_s;
+  float dist = sqrtf(dot(to_l, to_l));
+  d_s = to_l * (1.f / dist);
+  tmax = dist - sf.eps;
+  return true;
+}
+
+// One area light at a hit, at its sample point (a, b) of this pass: the
+// point-light term of light_term times A cos(theta_y) / r^2 (Eq. 8 over
+// the light's area, sampled with density 1 / A), and the shadow ray to the
+// point; false where n.l <= 0 or the light faces away (no shadow ray).
+__device__ __forceinline__ bool area_term(const Surface& sf, f3 d, f3 w, const float4* __restrict__ rec, float a,
+                                          float b, f3& contrib, f3& o_s, f3& d_s, float& tmax) {
+  const float4 A0 = __ldg(rec), A1 = __ldg(rec + 1), A2 = __ldg(rec + 2), A3 = __ldg(rec + 3);
+  const f3 nl = mk3(A1.w, A2.w, A3.w);
+  const f3 y = xyz(A0) + xyz(A1) * a + xyz(A2) * b;
+  const f3 to = y - sf.p;
+  const float dist_c = sqrtf(dot(to, to));
+  const f3 l = to * (1.f / dist_c);
+  const float nll = dot(sf.n, l);
+  const float cos_y = -dot(l, nl);
+  if (!(nll > 0.f) || !(cos_y > 0.f)) return false;
+  f3 rl = sf.n * (2.f * nll) - l;                 // reflect(-l, n)
+  float rv = -dot(rl, d);
+  float spec = rv > 0.f ? powf(rv, sf.shin) : 0.f;
+  f3 f = sf.albedo * nll + mk3(sf.ks * spec, sf.ks * spec, sf.ks * spec);
+  const float G = A0.w * cos_y / (dist_c * dist_c);
+  contrib = w * xyz(A3) * f * (G * (1.f - sf.rho));
+  o_s = sf.p + sf.n * sf.eps;
+  f3 to_l = y - o_s;
   float dist = sqrtf(dot(to_l, to_l));
   d_s = to_l * (1.f / dist);
   tmax = dist - sf.eps;

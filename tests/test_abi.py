@@ -48,6 +48,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(rtb.rt_camera) == S.CAMERA_DTYPE.itemsize == 40
     assert ctypes.sizeof(rtb.rt_render_options) == 40
     assert ctypes.sizeof(rtb.rt_tune) == 16
+    assert ctypes.sizeof(rtb.rt_pass) == 24
 
 
 def _base():
