@@ -71,7 +71,9 @@ __device__ __forceinline__ void add_rgb(float* fb, int pixel, f3 c) {
   atomicAdd(p + 2, c.z);
 }
 
-template <int kThreads>
+// kPass: some frame has area lights (their sampling code is compiled only
+// into these instances)
+template <int kThreads, bool kPass>
 __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batch(BatchParams bp) {
   constexpr int kBatchPending = batch_pending<kThreads>();
   __shared__ int s_stack[kStackShared * kThreads];
@@ -157,9 +159,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
       if (x < W && y < H) {
         const CamBasis cb = bs->cam;
         pixel = y * W + x;
-        float px, py;
-        pass_pixel_point(bp.ps, pixel, x, y, px, py);
-        camera_ray_at(cb, W, H, px, py, o, d);
+        camera_ray(cb, W, H, x, y, o, d);   // pixel centres (the batch renders pass 0 without jitter)
         w = mk3(1.f, 1.f, 1.f);
         depth = 0;
         code = 1u;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
         if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_rgb(fb, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
           // point lights, then one sampled point of each area light
-          for (int li = 0; li < sc.n_lights + sc.n_alights; ++li) {
+          for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights : 0); ++li) {
             f3 contrib, os, sd;
             float tmax;
             bool lit;
@@ -198,9 +198,12 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
               lit = light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd,
                                tmax);
             } else {
-              float a, b;
-              pass_sample(bp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
-              lit = area_term(sf, d, w, sc.alights + 4 * (li - sc.n_lights), a, b, contrib, os, sd, tmax);
+              lit = false;
+              if constexpr (kPass) {
+                float a, b;
+                pass_sample(bp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
+                lit = area_term(sf, d, w, sc.alights + 4 * (li - sc.n_lights), a, b, contrib, os, sd, tmax);
+              }
             }
             if (!lit) continue;
             atomicAdd(&s_cnt[1][depth], 1u);
@@ -282,14 +285,14 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
 
 using BatchKernel = void (*)(BatchParams);
 
-static BatchKernel batch_kernel(int threads) {
+static BatchKernel batch_kernel(int threads, bool pass = false) {
   switch (threads) {
     case 64:
-      return k_batch<64>;
+      return pass ? k_batch<64, true> : k_batch<64, false>;
     case 128:
-      return k_batch<128>;
+      return pass ? k_batch<128, true> : k_batch<128, false>;
     case 256:
-      return k_batch<256>;
+      return pass ? k_batch<256, true> : k_batch<256, false>;
     default:
       return nullptr;
   }
@@ -331,6 +334,7 @@ struct rt_batch {
   cudaStream_t cap_stream = nullptr;  // graphs are captured here (never the caller's stream)
   struct Graph {
     rt_tune tune;
+    bool pass;   // the kernel with area-light sampling
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;
@@ -368,13 +372,13 @@ static rt_status batch_table(rt_batch* b, const rt_tune& tune, unsigned* n_tiles
 
 // The launch of one tune: counters, image clears and the kernel, captured
 // on the batch's own stream into a graph (once per tune).
-static rt_status batch_graph(rt_batch* b, const rt_tune& tune, unsigned n_tiles, cudaGraphExec_t* exec) {
+static rt_status batch_graph(rt_batch* b, const rt_tune& tune, bool pass, unsigned n_tiles, cudaGraphExec_t* exec) {
   for (auto& g : b->graphs)
-    if (same_tune(g.tune, tune)) {
+    if (same_tune(g.tune, tune) && g.pass == pass) {
       *exec = g.exec;
       return RT_OK;
     }
-  BatchKernel kern = batch_kernel(tune.block_threads);
+  BatchKernel kern = batch_kernel(tune.block_threads, pass);
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tune.block_threads, 0);
   if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: occupancy");
@@ -411,7 +415,7 @@ static rt_status batch_graph(rt_batch* b, const rt_tune& tune, unsigned n_tiles,
   e = cudaGraphInstantiate(&x, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: instantiate");
-  b->graphs.push_back({tune, x});
+  b->graphs.push_back({tune, pass, x});
   *exec = x;
   return RT_OK;
 }
@@ -423,8 +427,10 @@ static rt_status batch_render(rt_batch* b, const rt_tune& tune, cudaStream_t st)
   unsigned n_tiles = 0;
   rt_status rs = batch_table(b, tune, &n_tiles, st);
   if (rs) return rs;
+  bool pass = false;
+  for (rt_scene* s : b->scenes) pass = pass || s->n_alights > 0;
   cudaGraphExec_t exec = nullptr;
-  if ((rs = batch_graph(b, tune, n_tiles, &exec))) return rs;
+  if ((rs = batch_graph(b, tune, pass, n_tiles, &exec))) return rs;
   // the tile count depends only on the sizes and the tile shape, both fixed per graph
   return cuda_error(cudaGraphLaunch(exec, st), "rt_batch_render: launch");
 }

@@ -102,7 +102,10 @@ __device__ __forceinline__ void flush_work(Counters* ctr, int cls, int depth, Wo
 #define RTB_PATHS_MIN_BLOCKS 5
 #endif
 
-template <bool kPrimary, bool kCount>
+// kPass: the frame has area lights or jittered camera rays (the sampling
+// code is compiled only into these instances, which keeps it out of the
+// plain kernels' instruction stream).
+template <bool kPrimary, bool kCount, bool kPass>
 __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(DevScene sc, FrameParams fp, int depth, int cap) {
   __shared__ int s_stack[kStackShared * kTraceThreads];
   int* stack = s_stack + threadIdx.x;
@@ -131,9 +134,13 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
       x = min(x, fp.W - 1);
       y = min(y, fp.H - 1);
       pixel = y * fp.W + x;
-      float px, py;
-      pass_pixel_point(fp.ps, pixel, x, y, px, py);
-      camera_ray_at(fp.cam, fp.W, fp.H, px, py, o, d);
+      if (kPass) {
+        float px, py;
+        pass_pixel_point(fp.ps, pixel, x, y, px, py);
+        camera_ray_at(fp.cam, fp.W, fp.H, px, py, o, d);
+      } else {
+        camera_ray(fp.cam, fp.W, fp.H, x, y, o, d);
+      }
       w = mk3(1.f, 1.f, 1.f);
     } else {
       float4 q0 = make_float4(0, 0, 0, 0), q1 = make_float4(0, 0, 1, 0), q2 = make_float4(0, 0, 0, 0);
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
       if (ok) store_ray(fp.shadowq[depth & 1], pos, os, pixel, sd, tmax, contrib);
     }
     // area lights: one sampled point of each per pass
-    for (int li = 0; li < sc.n_alights; ++li) {
+    for (int li = 0; kPass && li < sc.n_alights; ++li) {
       f3 contrib = mk3(0, 0, 0), os = mk3(0, 0, 0), sd = mk3(0, 0, 1);
       float tmax = 0.f;
       bool valid = false;
@@ -293,7 +300,7 @@ __device__ __forceinline__ void count_ray(Counters* ctr, int cls, int depth, uns
 constexpr int kWarpPending = 64;   // pending children per warp (shared memory, 12 KB a block)
 
 
-template <bool kCount>
+template <bool kCount, bool kPass>
 __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(DevScene sc, FrameParams fp, int cap) {
   __shared__ int s_stack[kStackShared * kTraceThreads];
   __shared__ unsigned s_cnt[3][RT_MAX_DEPTH + 2];   // rays spawned for / shadow rays cast at / hits at depth d
@@ -441,7 +448,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
         if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
           // point lights, then one sampled point of each area light
-          for (int li = 0; li < sc.n_lights + sc.n_alights; ++li) {
+          for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights : 0); ++li) {
             f3 contrib, os, sd;
             float tmax;
             bool lit;
@@ -449,9 +456,12 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
               lit = light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd,
                                tmax);
             } else {
-              float a, b;
-              pass_sample(fp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
-              lit = area_term(sf, d, w, sc.alights + 4 * (li - sc.n_lights), a, b, contrib, os, sd, tmax);
+              lit = false;
+              if constexpr (kPass) {
+                float a, b;
+                pass_sample(fp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
+                lit = area_term(sf, d, w, sc.alights + 4 * (li - sc.n_lights), a, b, contrib, os, sd, tmax);
+              }
             }
             if (!lit) continue;
             atomicAdd(&s_cnt[1][depth], 1u);
@@ -622,13 +632,30 @@ CamBasis camera_basis(const rt_camera* c, int W, int H) {
 
 static int g_blocks_per_sm_trace = 0, g_blocks_per_sm_shadow = 0;
 
+using TraceKernel = void (*)(DevScene, FrameParams, int, int);
+using PathsKernel = void (*)(DevScene, FrameParams, int);
+
+static TraceKernel trace_kernel(bool primary, bool count, bool pass) {
+  if (primary) {
+    if (count) return pass ? k_trace<true, true, true> : k_trace<true, true, false>;
+    return pass ? k_trace<true, false, true> : k_trace<true, false, false>;
+  }
+  if (count) return pass ? k_trace<false, true, true> : k_trace<false, true, false>;
+  return pass ? k_trace<false, false, true> : k_trace<false, false, false>;
+}
+
+static PathsKernel paths_kernel(bool count, bool pass) {
+  if (count) return pass ? k_paths<true, true> : k_paths<true, false>;
+  return pass ? k_paths<false, true> : k_paths<false, false>;
+}
+
 static void occupancy(rt_scene* s) {
   if (s->trace_blocks) return;
   int a = 0, b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<false, false>, kTraceThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<false, false, false>, kTraceThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_shadow<false>, kTraceThreads, 0);
   int c = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_paths<false>, kTraceThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_paths<false, false>, kTraceThreads, 0);
   s->paths_blocks = s->sm_count * std::max(c, 1);
   g_blocks_per_sm_trace = std::max(a, 1);
   g_blocks_per_sm_shadow = std::max(b, 1);
@@ -738,6 +765,7 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     fp.ps.strata = pass->strata;
     fp.ps.jitter = pass->jitter != 0;
   }
+  const bool pass_k = s->n_alights > 0 || fp.ps.jitter;   // kernels with the sampling code
   fp.cam = camera_basis(cam, W, H);
   fp.W = W;
   fp.H = H;
@@ -798,11 +826,9 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     if (depth >= 2) cudaStreamWaitEvent(st, s->ev_shadowed[depth - 2], 0);
     int slot = timing ? timing_begin(s, 0, st) : -1;
     if (depth == 0) {
-      if (count) k_trace<true, true><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, 0, cap);
-      else k_trace<true, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, 0, cap);
+      trace_kernel(true, count, pass_k)<<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, 0, cap);
     } else {
-      if (count) k_trace<false, true><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
-      else k_trace<false, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+      trace_kernel(false, count, pass_k)<<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
     }
     if (timing) timing_end(s, slot, st);
     // shadow(depth) runs on the side stream, beside trace(depth + 1)
@@ -827,8 +853,7 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   bool run_paths = !per_depth && D >= fp.path_depth0 && (T < 0 || cache_in_paths || train);
   if (run_paths) {
     int slot = timing ? timing_begin(s, 0, st) : -1;
-    if (count) k_paths<true><<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);
-    else k_paths<false><<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);
+    paths_kernel(count, pass_k)<<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);
     if (timing) timing_end(s, slot, st);
     launches += 1;
   }
@@ -1114,8 +1139,7 @@ extern "C" rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int W,
   if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);
   if (e != cudaSuccess) return cuda_error(e, "rt_render_noalloc memset");
   for (int depth = 0; depth <= D; ++depth) {
-    if (depth == 0) k_trace<true, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, 0, cap);
-    else k_trace<false, false><<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+    trace_kernel(depth == 0, false, sc.n_alights > 0)<<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
     k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
   }
   return cuda_error(cudaGetLastError(), "rt_render_noalloc launch");
