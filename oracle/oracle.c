@@ -117,6 +117,7 @@ struct orc_scene {
   int64_t n_mats; mat_t* mats;
   int64_t n_lights; light_t* lights;
   int64_t n_alights; alight_t* alights;
+  int64_t n_emitters; int64_t* emitters;   /* primitives whose material emits (Eq. 7), sampled as lights */
   /* the pass being rendered: Philox key, pass index, strata per axis, and
    * whether the camera ray is jittered inside its pixel */
   uint32_t seed_lo, seed_hi;
@@ -649,28 +650,56 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
         if (relevant && maxc(contrib) >= 1e-3 && rb < out.robust) out.robust = rb;
         if (!occ) out.local = add(out.local, contrib);
       }
-      /* area lights: one stratified point on each per pass, the same term
-       * as a point light times A cos(theta_y) / r^2 (Eq. 8 over the light's
-       * area, sampled with density 1 / A) */
-      for (int64_t li = 0; li < s->n_alights; ++li) {
-        const alight_t* A = &s->alights[li];
+      /* area lights, then emissive primitives (Eq. 7's L_e as a light): one
+       * stratified point on each per pass, the same term as a point light
+       * times A cos(theta_y) / r^2 (Eq. 8 over the light's area, sampled
+       * with density 1 / A) */
+      for (int64_t li = 0; li < s->n_alights + s->n_emitters; ++li) {
         double a, b;
         pass_sample(s, pixel, code, (uint32_t)li, &a, &b);
-        v3 y = add(A->corner, add(scl(A->eu, a), scl(A->ev, b)));
+        v3 y, ny, Lrad;
+        double area;
+        int two_sided = 0;
+        if (li < s->n_alights) {
+          const alight_t* A = &s->alights[li];
+          y = add(A->corner, add(scl(A->eu, a), scl(A->ev, b)));
+          ny = A->nl;
+          Lrad = A->L;
+          area = A->area;
+        } else {
+          const prim_t* E = &s->prims[s->emitters[li - s->n_alights]];
+          Lrad = s->mats[E->mat].emis;
+          if (E->is_sphere) {
+            /* uniform on the sphere: z = 1 - 2a, azimuth 2 pi b */
+            double z = 1.0 - 2.0 * a, rho_xy = sqrt(fmax(0.0, 1.0 - z * z)), phi = 2.0 * M_PI * b;
+            ny = mk(rho_xy * cos(phi), rho_xy * sin(phi), z);
+            y = add(E->c, scl(ny, E->r));
+            area = 4.0 * M_PI * E->r * E->r;
+          } else {
+            /* uniform on the triangle: fold (a, b) into a + b <= 1 */
+            if (a + b > 1.0) { a = 1.0 - a; b = 1.0 - b; }
+            v3 e1 = sub(E->v1, E->v0), e2 = sub(E->v2, E->v0), c = cross(e1, e2);
+            y = add(E->v0, add(scl(e1, a), scl(e2, b)));
+            area = 0.5 * len(c);
+            ny = unit(c);
+            two_sided = 1;   /* triangles emit (and are hit) on both sides */
+          }
+        }
         v3 to = sub(y, ph);
         double dist_c = len(to);
         v3 l = scl(to, 1.0 / dist_c);
         double nl = dot(n, l);
-        double cos_y = -dot(l, A->nl);
+        double cos_y = -dot(l, ny);
+        if (two_sided) cos_y = fabs(cos_y);
         v3 vdir = scl(r->d, -1.0);
         v3 rl = sub(scl(n, 2.0 * nl), l);                  /* reflect(-l, n) */
         double rv = dot(rl, vdir);
         double spec = rv > 0.0 ? pow(rv, m->shin) : 0.0;
         v3 f = add(scl(m->albedo, nl), mk(m->ks * spec, m->ks * spec, m->ks * spec));
-        double G = A->area * cos_y / (dist_c * dist_c);
-        v3 contrib = scl(mul(mul(w, A->L), f), G * (1.0 - rho));
+        double G = area * cos_y / (dist_c * dist_c);
+        v3 contrib = scl(mul(mul(w, Lrad), f), G * (1.0 - rho));
         double uy = (Up + s->K * 3 * GAMMA32 * maxabs(y)) / dist_c;   /* direction to the sample */
-        int relevant = count_robust && maxc(scl(mul(w, A->L), (1.0 - rho) * fabs(G))) * (2.0 + m->ks) >= 1e-3;
+        int relevant = count_robust && maxc(scl(mul(w, Lrad), (1.0 - rho) * fabs(G))) * (2.0 + m->ks) >= 1e-3;
         if (relevant) {
           double rb = fabs(nl) / (An + r->ed + uy);
           if (rb < out.robust) out.robust = rb;
@@ -944,6 +973,12 @@ orc_scene* orc_scene_create(const void* spheres, int64_t ns, const void* triangl
     p->bc = p->centroid;
     p->brad = fmax(len(sub(p->v0, p->bc)), fmax(len(sub(p->v1, p->bc)), len(sub(p->v2, p->bc))));
   }
+  /* emissive primitives, in id order */
+  s->emitters = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s->n_prims > 0 ? s->n_prims : 1));
+  s->n_emitters = 0;
+  for (int64_t i = 0; i < s->n_prims; ++i)
+    if (maxc(s->mats[s->prims[i].mat].emis) > 0.0) s->emitters[s->n_emitters++] = i;
+  if (s->n_emitters > 0) s->l_max = INFINITY;
   for (int64_t i = 0; i < s->n_prims; ++i) {
     slo = vmin(slo, s->prims[i].lo);
     shi = vmax(shi, s->prims[i].hi);
@@ -966,7 +1001,8 @@ bad:
 
 void orc_scene_free(orc_scene* s) {
   if (!s) return;
-  free(s->prims); free(s->mats); free(s->lights); free(s->alights); free(s->nodes); free(s->order);
+  free(s->prims); free(s->mats); free(s->lights); free(s->alights); free(s->emitters); free(s->nodes);
+  free(s->order);
   free(s->nrc_W); free(s->nrc_B);
   free(s);
 }

@@ -175,3 +175,51 @@ def test_passes_change_nothing_without_area_lights_and_jitter():
     ref = orc.render(sc.camera, sc.width, sc.height, 2, mode="brute")["rgb"]
     orc.set_pass(123, 17, 5, False)
     np.testing.assert_array_equal(orc.render(sc.camera, sc.width, sc.height, 2, mode="brute")["rgb"], ref)
+
+
+def floor_with_emitters(spheres=None, tris=None, L=(1.0, 1.0, 1.0), albedo=(0.5, 0.5, 0.5), W=9, H=9):
+    """The floor scene of plane_under_light with emissive primitives (material
+    1, emission L) instead of an area light; the centre pixel sees the floor
+    at the origin (the camera is above the emitters' reach)."""
+    mats = np.concatenate([S.material(S.MAT_DIFFUSE, albedo, ks=0.0),
+                           S.material(S.MAT_DIFFUSE, (0.0, 0.0, 0.0), ks=0.0, emission=L)])
+    floor = S.triangles_from([(-50, 0, -50), (-50, 0, -50)], [(-50, 0, 50), (50, 0, 50)],
+                             [(50, 0, 50), (50, 0, -50)], 0)
+    tri = floor if tris is None else np.concatenate([floor, tris])
+    sph = np.zeros(0, S.SPHERE_DTYPE) if spheres is None else spheres
+    cam = S.camera((0.0, 20.0, 0.0), (0.0, 0.0, 0.0), up=(0.0, 0.0, -1.0), vfov_deg=10.0)
+    return S.Scene("floor_emit", sph, tri, mats, np.zeros(0, S.LIGHT_DTYPE), cam, W, H, 0)
+
+
+def test_emissive_quad_converges_to_lambert():
+    """Two emissive triangles forming the tilted parallelogram of the area
+    light test light the floor as Lambert's formula says (they emit on both
+    sides; the camera looks past them at the floor below)."""
+    c = np.array((1.0, 2.0, -1.5))
+    eu, ev = np.array((2.0, 0.5, 0.0)), np.array((0.0, 0.0, 3.0))
+    quad = S.triangles_from([c, c], [c + eu, c + eu + ev], [c + eu + ev, c + ev], 1)
+    sc = floor_with_emitters(tris=quad, L=(2.0, 1.0, 0.5))
+    orc = O.OracleScene.from_scene(sc)
+    E = polygon_irradiance(np.zeros(3), np.array([0.0, 1.0, 0.0]), [c, c + eu, c + eu + ev, c + ev])
+    centre = np.array([(sc.height // 2) * sc.width + sc.width // 2])
+    got = progressive(orc, sc, passes=1024, strata=32, pixels=centre)[0]
+    np.testing.assert_allclose(got, 0.5 * np.array([2.0, 1.0, 0.5]) * E, rtol=3e-3)
+
+
+def test_emissive_sphere_converges_to_its_solid_angle():
+    """A uniformly emitting sphere of radius r at height d straight above
+    the point: the cosine-weighted solid angle is pi (r / d)^2."""
+    r, d = 0.6, 3.0
+    sph = S.spheres_from([(0.0, d, 0.0)], [r], [1])
+    sc = floor_with_emitters(spheres=sph, L=(1.0, 0.5, 0.25))
+    sc.camera = S.camera((0.0, 1.0, 0.0), (0.0, 0.0, 0.0), up=(0.0, 0.0, -1.0), vfov_deg=10.0)
+    orc = O.OracleScene.from_scene(sc)
+    centre = np.array([(sc.height // 2) * sc.width + sc.width // 2])
+    got = progressive(orc, sc, passes=1024, strata=32, pixels=centre)[0]
+    want = 0.5 * np.array([1.0, 0.5, 0.25]) * np.pi * (r / d) ** 2
+    np.testing.assert_allclose(got, want, rtol=5e-3)
+    # seen directly, the sphere shows its own emission (Eq. 7)
+    sc2 = floor_with_emitters(spheres=sph, L=(1.0, 0.5, 0.25))
+    sc2.camera = S.camera((0.0, 10.0, 0.0), (0.0, 0.0, 0.0), up=(0.0, 0.0, -1.0), vfov_deg=2.0)
+    top = O.OracleScene.from_scene(sc2).render(sc2.camera, 9, 9, 0, mode="brute", pixels=centre)["rgb"][0]
+    np.testing.assert_allclose(top, (1.0, 0.5, 0.25), atol=1e-12)
