@@ -69,7 +69,10 @@ enum { RT_MAT_DIFFUSE = 0, RT_MAT_MIRROR = 1, RT_MAT_DIELECTRIC = 2 };
  *   DIELECTRIC : no local term; Fresnel-Schlick reflection ray (weight R)
  *                and Snell refraction ray (weight 1 - R; none on total
  *                internal reflection); index of refraction `ior`.
- *   emission   : L_e, added at every hit. */
+ *   emission   : L_e, added at every hit.  A primitive whose material
+ *                emits (some channel > 0) is also a light: each pass
+ *                samples one point of it per shaded vertex, like an area
+ *                light (triangles emit on both faces). */
 typedef struct rt_material {
   uint32_t kind;
   float albedo[3];
@@ -190,7 +193,11 @@ rt_status rt_scene_set_area_lights(rt_scene* s, const rt_area_light* lights, siz
  * scene).  The arrays may live in host memory (pinned memory makes the
  * copy asynchronous) or in device memory; the copy and the on-device
  * repacking run on `stream`.  The BVH must be rebuilt afterwards.
- * Values are not validated (use rt_scene_create for checked input). */
+ * Values are not validated (use rt_scene_create for checked input),
+ * except material indices: one out of range is replaced by material 0 and
+ * reported by the next rt_scene_sync (RT_ERR_INVALID_ARG).  The emissive
+ * primitives sampled as lights are those that rt_scene_create found: an
+ * update that changes a primitive's material changes its shading only. */
 rt_status rt_scene_update(rt_scene* s, const rt_sphere* spheres, const rt_triangle* triangles,
                           void* stream);
 
@@ -202,10 +209,13 @@ rt_status rt_bvh_build(rt_scene* s, void* stream);
 /* Fills *info (syncs the stream). */
 rt_status rt_bvh_get_info(rt_scene* s, rt_bvh_info* info, void* stream);
 
-/* Copies the traversal layout to host buffers (syncs), for inspection:
- * nodes: n_nodes x 16 floats (two child boxes + two child links, see
- * DESIGN), prim_order: n_prims int32 (leaf order -> primitive id),
- * morton: n_prims uint32 sorted codes.  Any pointer may be NULL. */
+/* Copies the binary BVH to host buffers (syncs), for inspection.
+ * nodes: n_nodes x 16 floats per node: child 0's lo.x, hi.x, lo.y, hi.y;
+ * child 1's lo.x, hi.x, lo.y, hi.y; lo.z, hi.z of child 0 then of child 1;
+ * two int32 child links (>= 0: node index; < 0: leaf ~(start << 3 |
+ * count - 1) over prim_order positions); two unused words.  prim_order:
+ * n_prims int32 (leaf order -> primitive id); morton: n_prims uint32
+ * sorted codes.  Any pointer may be NULL. */
 rt_status rt_bvh_export(rt_scene* s, float* nodes, int64_t nodes_capacity, int32_t* prim_order,
                         uint32_t* morton, void* stream);
 
@@ -286,7 +296,8 @@ rt_status rt_trace_any(rt_scene* s, const float* o_device, const float* d_device
  *     2*RT_NOALLOC_MAX_PIXELS*RT_NOALLOC_MAX_LIGHTS shadow records, 48 B
  *     each) that every GPU loading the library holds until the process
  *     exits.  width*height > RT_NOALLOC_MAX_PIXELS or more than
- *     RT_NOALLOC_MAX_LIGHTS lights -> RT_ERR_UNSUPPORTED with a message.
+ *     RT_NOALLOC_MAX_LIGHTS lights (point lights, area lights and
+ *     emissive primitives together) -> RT_ERR_UNSUPPORTED with a message.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first
  *     call before any stream capture.

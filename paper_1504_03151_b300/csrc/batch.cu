@@ -71,8 +71,8 @@ __device__ __forceinline__ void add_rgb(float* fb, int pixel, f3 c) {
   atomicAdd(p + 2, c.z);
 }
 
-// kPass: some frame has area lights (their sampling code is compiled only
-// into these instances)
+// kPass: some frame has area lights or emissive primitives (their sampling
+// code is compiled only into these instances)
 template <int kThreads, bool kPass>
 __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batch(BatchParams bp) {
   constexpr int kBatchPending = batch_pending<kThreads>();
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
         Surface sf = surface_at(sc, hit, o, d, t, bp.eps_scale);
         if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_rgb(fb, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
-          // point lights, then one sampled point of each area light
-          for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights : 0); ++li) {
+          // point lights, then one sampled point of each area light and emitter
+          for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights + sc.n_emitters : 0); ++li) {
             f3 contrib, os, sd;
             float tmax;
             bool lit;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
               if constexpr (kPass) {
                 float a, b;
                 pass_sample(bp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
-                lit = area_term(sf, d, w, sc.alights + 4 * (li - sc.n_lights), a, b, contrib, os, sd, tmax);
+                lit = area_term(sf, d, w, area_point(sc, li - sc.n_lights, a, b), contrib, os, sd, tmax);
               }
             }
             if (!lit) continue;
@@ -428,7 +428,7 @@ static rt_status batch_render(rt_batch* b, const rt_tune& tune, cudaStream_t st)
   rt_status rs = batch_table(b, tune, &n_tiles, st);
   if (rs) return rs;
   bool pass = false;
-  for (rt_scene* s : b->scenes) pass = pass || s->n_alights > 0;
+  for (rt_scene* s : b->scenes) pass = pass || s->n_alights > 0 || s->n_emitters > 0;
   cudaGraphExec_t exec = nullptr;
   if ((rs = batch_graph(b, tune, pass, n_tiles, &exec))) return rs;
   // the tile count depends only on the sizes and the tile shape, both fixed per graph

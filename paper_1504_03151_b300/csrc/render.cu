@@ -102,9 +102,9 @@ __device__ __forceinline__ void flush_work(Counters* ctr, int cls, int depth, Wo
 #define RTB_PATHS_MIN_BLOCKS 5
 #endif
 
-// kPass: the frame has area lights or jittered camera rays (the sampling
-// code is compiled only into these instances, which keeps it out of the
-// plain kernels' instruction stream).
+// kPass: the frame has area lights, emissive primitives or jittered camera
+// rays (the sampling code is compiled only into these instances, which
+// keeps it out of the plain kernels' instruction stream).
 template <bool kPrimary, bool kCount, bool kPass>
 __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(DevScene sc, FrameParams fp, int depth, int cap) {
   __shared__ int s_stack[kStackShared * kTraceThreads];
@@ -215,15 +215,15 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
       unsigned pos = warp_push(&ctr->shadow[depth], valid, fp.shadow_cap, ok, sc.status);
       if (ok) store_ray(fp.shadowq[depth & 1], pos, os, pixel, sd, tmax, contrib);
     }
-    // area lights: one sampled point of each per pass
-    for (int li = 0; kPass && li < sc.n_alights; ++li) {
+    // area lights, then emissive primitives: one sampled point of each per pass
+    for (int li = 0; kPass && li < sc.n_alights + sc.n_emitters; ++li) {
       f3 contrib = mk3(0, 0, 0), os = mk3(0, 0, 0), sd = mk3(0, 0, 1);
       float tmax = 0.f;
       bool valid = false;
       if (local) {
         float a, b;
         pass_sample(fp.ps, pixel, code, (uint32_t)li, a, b);
-        valid = area_term(sf, d, w, sc.alights + 4 * li, a, b, contrib, os, sd, tmax);
+        valid = area_term(sf, d, w, area_point(sc, li, a, b), contrib, os, sd, tmax);
       }
       bool ok;
       unsigned pos = warp_push(&ctr->shadow[depth], valid, fp.shadow_cap, ok, sc.status);
@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
       if (live) {
         if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
-          // point lights, then one sampled point of each area light
-          for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights : 0); ++li) {
+          // point lights, then one sampled point of each area light and emitter
+          for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights + sc.n_emitters : 0); ++li) {
             f3 contrib, os, sd;
             float tmax;
             bool lit;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
               if constexpr (kPass) {
                 float a, b;
                 pass_sample(fp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
-                lit = area_term(sf, d, w, sc.alights + 4 * (li - sc.n_lights), a, b, contrib, os, sd, tmax);
+                lit = area_term(sf, d, w, area_point(sc, li - sc.n_lights, a, b), contrib, os, sd, tmax);
               }
             }
             if (!lit) continue;
@@ -765,7 +765,7 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     fp.ps.strata = pass->strata;
     fp.ps.jitter = pass->jitter != 0;
   }
-  const bool pass_k = s->n_alights > 0 || fp.ps.jitter;   // kernels with the sampling code
+  const bool pass_k = s->n_alights > 0 || s->n_emitters > 0 || fp.ps.jitter;   // kernels with the sampling code
   fp.cam = camera_basis(cam, W, H);
   fp.W = W;
   fp.H = H;
@@ -1024,6 +1024,7 @@ rt_status rt_scene_destroy(rt_scene* s) {
   release(s->mats);
   release(s->lights);
   release(s->alights);
+  release(s->emitters);
   release(s->pass_img);
   release(s->nodes);
   release(s->nodes4);
@@ -1104,9 +1105,11 @@ extern "C" rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int W,
   if ((int64_t)W * H > kNoallocMaxPixels)
     return set_error(RT_ERR_UNSUPPORTED, "rt_render_noalloc: width*height exceeds RT_NOALLOC_MAX_PIXELS (" +
                                              std::to_string(kNoallocMaxPixels) + "); use rt_render");
-  if (s->n_lights > kNoallocMaxLights)
+  // the shadow queue holds one record per ray and light of any kind
+  if (s->n_lights + s->n_alights + s->n_emitters > kNoallocMaxLights)
     return set_error(RT_ERR_UNSUPPORTED, "rt_render_noalloc: more than RT_NOALLOC_MAX_LIGHTS (" +
-                                             std::to_string(kNoallocMaxLights) + ") lights; use rt_render");
+                                             std::to_string(kNoallocMaxLights) +
+                                             ") point, area and emissive lights together; use rt_render");
   if (!s->built) return set_error(RT_ERR_NOT_BUILT, "rt_render_noalloc: call rt_bvh_build first");
   void* base = nullptr;
   rt_status rs = noalloc_scratch(&base);
@@ -1139,7 +1142,8 @@ extern "C" rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int W,
   if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);
   if (e != cudaSuccess) return cuda_error(e, "rt_render_noalloc memset");
   for (int depth = 0; depth <= D; ++depth) {
-    trace_kernel(depth == 0, false, sc.n_alights > 0)<<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
+    const bool pass_k = sc.n_alights + sc.n_emitters > 0;
+    trace_kernel(depth == 0, false, pass_k)<<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
     k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
   }
   return cuda_error(cudaGetLastError(), "rt_render_noalloc launch");

@@ -32,6 +32,7 @@ constexpr float kCostIsect = 1.0f;
 constexpr unsigned kErrQueueOverflow = 1u;
 constexpr unsigned kErrTraversalLimit = 2u;
 constexpr unsigned kErrBadTree = 4u;      // a link outside the node / primitive arrays
+constexpr unsigned kErrBadMaterial = 16u; // rt_scene_update met a material index out of range
 
 // Primitive kinds (row0.w of a primitive record).
 constexpr int kKindTriangle = 0;
@@ -83,9 +84,12 @@ struct DevScene {
   const float4* mats;       // 3 per material
   const float4* lights;     // 2 per light
   const float4* alights;    // 4 per area light: (corner, area) (edge_u, n.x) (edge_v, n.y) (radiance, n.z)
+  const float4* prims_id;   // 3 per primitive, id order (emitters are looked up here)
+  const int* emitters;      // ids of the primitives whose material emits, ascending
   int n_prims;
   int n_lights;
   int n_alights;
+  int n_emitters;
   int n_nodes;              // node slots (links are checked against it)
   int root;                 // root node index (-1: no node)
   int use_bvh;
@@ -117,6 +121,8 @@ struct rt_scene {
   rtb::Buf alights;              // area lights, 4 float4 each
   rtb::Buf pass_img;             // one pass of a progressive render
   int64_t n_alights = 0;
+  rtb::Buf emitters;             // int ids of the emissive primitives, ascending
+  int64_t n_emitters = 0;
   // BVH
   bool built = false;
   int root = -1;

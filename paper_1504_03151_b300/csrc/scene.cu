@@ -46,25 +46,34 @@ void release(Buf& b) {
 }
 
 // One thread per primitive: ABI structs -> 48-byte records (primitive-id
-// order).  Edges are formed once here, in FP32.
+// order).  Edges are formed once here, in FP32.  A material index out of
+// range (possible only through rt_scene_update) becomes 0 and is reported.
 __global__ void k_pack(const rt_sphere* __restrict__ sph, int ns, const rt_triangle* __restrict__ tri, int nt,
-                       float4* __restrict__ out) {
+                       uint32_t n_mats, float4* __restrict__ out, unsigned* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ns + nt) return;
   float4 r0, r1, r2;
+  uint32_t mat;
   if (i < ns) {
     const rt_sphere& s = sph[i];
     float r = s.radius;
+    mat = s.material;
     r0 = make_float4(s.center[0], s.center[1], s.center[2], __int_as_float(kKindSphere));
     r1 = make_float4(r, r * r, 0.f, __int_as_float(i));
-    r2 = make_float4(0.f, 0.f, 0.f, __int_as_float((int)s.material));
+    r2 = make_float4(0.f, 0.f, 0.f, 0.f);
   } else {
     const rt_triangle& t = tri[i - ns];
     float v0x = t.v0[0], v0y = t.v0[1], v0z = t.v0[2];
+    mat = t.material;
     r0 = make_float4(v0x, v0y, v0z, __int_as_float(kKindTriangle));
     r1 = make_float4(t.v1[0] - v0x, t.v1[1] - v0y, t.v1[2] - v0z, __int_as_float(i));
-    r2 = make_float4(t.v2[0] - v0x, t.v2[1] - v0y, t.v2[2] - v0z, __int_as_float((int)t.material));
+    r2 = make_float4(t.v2[0] - v0x, t.v2[1] - v0y, t.v2[2] - v0z, 0.f);
   }
+  if (mat >= n_mats) {
+    atomicOr(status, kErrBadMaterial);
+    mat = 0;
+  }
+  r2.w = __int_as_float((int)mat);
   out[3 * (size_t)i + 0] = r0;
   out[3 * (size_t)i + 1] = r1;
   out[3 * (size_t)i + 2] = r2;
@@ -75,7 +84,7 @@ static rt_status pack(rt_scene* s, cudaStream_t st) {
   if (n == 0) return RT_OK;
   k_pack<<<(n + 255) / 256, 256, 0, st>>>((const rt_sphere*)s->raw_sph.p, (int)s->n_spheres,
                                           (const rt_triangle*)s->raw_tri.p, (int)s->n_tris,
-                                          (float4*)s->prims_id.p);
+                                          (uint32_t)s->n_mats, (float4*)s->prims_id.p, s->status);
   return cuda_error(cudaGetLastError(), "k_pack");
 }
 
@@ -97,6 +106,9 @@ DevScene dev_scene(const rt_scene* s, bool use_bvh) {
   d.n_lights = (int)s->n_lights;
   d.alights = (const float4*)s->alights.p;
   d.n_alights = (int)s->n_alights;
+  d.prims_id = (const float4*)s->prims_id.p;
+  d.emitters = (const int*)s->emitters.p;
+  d.n_emitters = (int)s->n_emitters;
   d.n_nodes = (int)s->n_nodes4;
   d.root = use_bvh ? s->root : -1;
   d.use_bvh = use_bvh ? 1 : 0;
@@ -202,8 +214,20 @@ rt_status rt_scene_create(const rt_sphere* spheres, size_t n_spheres, const rt_t
     lts[2 * i + 0] = make_float4(l.position[0], l.position[1], l.position[2], 0.f);
     lts[2 * i + 1] = make_float4(l.intensity[0], l.intensity[1], l.intensity[2], 0.f);
   }
+  // primitives whose material emits (Eq. 7's L_e), sampled as lights, in id order
+  std::vector<int> emit;
+  auto emits = [&](uint32_t m) {
+    const float* e = materials[m].emission;
+    return std::max(e[0], std::max(e[1], e[2])) > 0.f;
+  };
+  for (size_t i = 0; i < n_spheres; ++i)
+    if (emits(spheres[i].material)) emit.push_back((int)i);
+  for (size_t i = 0; i < n_triangles; ++i)
+    if (emits(triangles[i].material)) emit.push_back((int)(n_spheres + i));
+  s->n_emitters = (int64_t)emit.size();
   size_t np = (size_t)s->n_prims;
   if ((st = ensure(s->raw_sph, n_spheres * sizeof(rt_sphere))) ||
+      (st = ensure(s->emitters, std::max<size_t>(emit.size(), 1) * sizeof(int))) ||
       (st = ensure(s->raw_tri, n_triangles * sizeof(rt_triangle))) ||
       (st = ensure(s->prims_id, np * 48)) || (st = ensure(s->prims_leaf, np * 48)) ||
       (st = ensure(s->mats, mats.size() * 16)) || (st = ensure(s->lights, lts.size() * 16))) {
@@ -218,6 +242,8 @@ rt_status rt_scene_create(const rt_sphere* spheres, size_t n_spheres, const rt_t
     e = cudaMemcpy(s->raw_tri.p, triangles, n_triangles * sizeof(rt_triangle), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->mats.p, mats.data(), mats.size() * 16, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->lights.p, lts.data(), lts.size() * 16, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !emit.empty())
+    e = cudaMemcpy(s->emitters.p, emit.data(), emit.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     rt_scene_destroy(s);
     return cuda_error(e, "rt_scene_create upload");
@@ -298,6 +324,8 @@ rt_status rt_scene_sync(rt_scene* s, void* stream) {
     if (flags & kErrQueueOverflow)
       return set_error(RT_ERR_QUEUE_OVERFLOW, "a ray queue overflowed; rays were dropped (raise queue_capacity)");
     if (flags & kErrBadTree) return set_error(RT_ERR_CUDA, "traversal met a link outside the BVH arrays");
+    if (flags & kErrBadMaterial)
+      return set_error(RT_ERR_INVALID_ARG, "rt_scene_update: a material index out of range (material 0 used)");
     if (flags & kErrNrcTimeout) return set_error(RT_ERR_CUDA, "a radiance-cache tensor-core wait timed out");
     if (flags & kErrTraversalLimit)
       return set_error(RT_ERR_TRAVERSAL_LIMIT, "a ray reached the traversal step cap or the stack depth");

@@ -427,29 +427,83 @@ __device__ __forceinline__ bool light_term(const Surface& sf, f3 d, f3 w, float4
   return true;
 }
 
-// One area light at a hit, at its sample point (a, b) of this pass: the
-// point-light term of light_term times A cos(theta_y) / r^2 (Eq. 8 over
-// the light's area, sampled with density 1 / A), and the shadow ray to the
-// point; false where n.l <= 0 or the light faces away (no shadow ray).
-__device__ __forceinline__ bool area_term(const Surface& sf, f3 d, f3 w, const float4* __restrict__ rec, float a,
-                                          float b, f3& contrib, f3& o_s, f3& d_s, float& tmax) {
-  const float4 A0 = __ldg(rec), A1 = __ldg(rec + 1), A2 = __ldg(rec + 2), A3 = __ldg(rec + 3);
-  const f3 nl = mk3(A1.w, A2.w, A3.w);
-  const f3 y = xyz(A0) + xyz(A1) * a + xyz(A2) * b;
-  const f3 to = y - sf.p;
+constexpr float kPi = 3.14159265358979f;
+
+// A sampled point y of an area light or of an emissive primitive, with the
+// light's normal there, its radiance and area (the sampling density is
+// 1 / area).
+struct AreaPoint {
+  f3 y, ny, L;
+  float area;
+  bool two_sided;   // triangles emit on both faces
+};
+
+// Light slot li (area lights first, then the emissive primitives in id
+// order) at the pass's sample (a, b) in [0, 1)^2: a parallelogram at
+// corner + a edge_u + b edge_v; a sphere uniformly over its surface
+// (z = 1 - 2a, azimuth 2 pi b); a triangle uniformly, (a, b) folded into
+// a + b <= 1.
+__device__ __forceinline__ AreaPoint area_point(const DevScene& sc, int li, float a, float b) {
+  AreaPoint q;
+  if (li < sc.n_alights) {
+    const float4* rec = sc.alights + 4 * li;
+    const float4 A0 = __ldg(rec), A1 = __ldg(rec + 1), A2 = __ldg(rec + 2), A3 = __ldg(rec + 3);
+    q.ny = mk3(A1.w, A2.w, A3.w);
+    q.y = xyz(A0) + xyz(A1) * a + xyz(A2) * b;
+    q.L = xyz(A3);
+    q.area = A0.w;
+    q.two_sided = false;
+    return q;
+  }
+  const int id = __ldg(&sc.emitters[li - sc.n_alights]);
+  const float4 r0 = __ldg(&sc.prims_id[3 * (size_t)id]);
+  const float4 r1 = __ldg(&sc.prims_id[3 * (size_t)id + 1]);
+  const float4 r2 = __ldg(&sc.prims_id[3 * (size_t)id + 2]);
+  q.L = xyz(__ldg(&sc.mats[3 * __float_as_int(r2.w) + 2]));
+  if (__float_as_int(r0.w) == kKindSphere) {
+    const float z = 1.f - 2.f * a, rxy = sqrtf(fmaxf(0.f, 1.f - z * z));
+    float sn, cs;
+    sincospif(2.f * b, &sn, &cs);
+    q.ny = mk3(rxy * cs, rxy * sn, z);
+    q.y = xyz(r0) + q.ny * r1.x;
+    q.area = 4.f * kPi * r1.y;
+    q.two_sided = false;
+  } else {
+    if (a + b > 1.f) {
+      a = 1.f - a;
+      b = 1.f - b;
+    }
+    const f3 e1 = xyz(r1), e2 = xyz(r2), c = cross(e1, e2);
+    const float len = sqrtf(dot(c, c));
+    q.y = xyz(r0) + e1 * a + e2 * b;
+    q.ny = c * (1.f / len);   // NaN for a degenerate triangle: its term is dropped below
+    q.area = 0.5f * len;
+    q.two_sided = true;
+  }
+  return q;
+}
+
+// One sampled light point at a hit: the point-light term of light_term
+// times A cos(theta_y) / r^2 (Eq. 8 over the light's area, sampled with
+// density 1 / A), and the shadow ray to the point; false where n.l <= 0
+// or the light faces away (no shadow ray).
+__device__ __forceinline__ bool area_term(const Surface& sf, f3 d, f3 w, const AreaPoint& q, f3& contrib, f3& o_s,
+                                          f3& d_s, float& tmax) {
+  const f3 to = q.y - sf.p;
   const float dist_c = sqrtf(dot(to, to));
   const f3 l = to * (1.f / dist_c);
   const float nll = dot(sf.n, l);
-  const float cos_y = -dot(l, nl);
+  float cos_y = -dot(l, q.ny);
+  if (q.two_sided) cos_y = fabsf(cos_y);
   if (!(nll > 0.f) || !(cos_y > 0.f)) return false;
   f3 rl = sf.n * (2.f * nll) - l;                 // reflect(-l, n)
   float rv = -dot(rl, d);
   float spec = rv > 0.f ? powf(rv, sf.shin) : 0.f;
   f3 f = sf.albedo * nll + mk3(sf.ks * spec, sf.ks * spec, sf.ks * spec);
-  const float G = A0.w * cos_y / (dist_c * dist_c);
-  contrib = w * xyz(A3) * f * (G * (1.f - sf.rho));
+  const float G = q.area * cos_y / (dist_c * dist_c);
+  contrib = w * q.L * f * (G * (1.f - sf.rho));
   o_s = sf.p + sf.n * sf.eps;
-  f3 to_l = y - o_s;
+  f3 to_l = q.y - o_s;
   float dist = sqrtf(dot(to_l, to_l));
   d_s = to_l * (1.f / dist);
   tmax = dist - sf.eps;

@@ -383,6 +383,25 @@ def scene_spheres8_area(seed: int = 1, width: int = 256, height: int = 256, max_
     return sc
 
 
+def scene_spheres8_emitters(seed: int = 1, width: int = 256, height: int = 256, max_depth: int = 3) -> Scene:
+    """spheres8 with emissive primitives as lights besides its point light
+    (Eq. 7's L_e): sphere 2 glows (emission (2, 1.5, 1)), sphere 5 is glass
+    (IOR 1.5), and a tilted 2 x 2 quad of two triangles at height 6 emits
+    (1, 1, 2) from both faces."""
+    sc = scene_spheres8(seed, width, height, max_depth)
+    mats = sc.materials.copy()
+    mats["emission"][3] = (2.0, 1.5, 1.0)
+    mats[6] = material(MAT_DIELECTRIC, (1.0, 1.0, 1.0), ks=0.0, ior=1.5)[0]
+    mats = np.concatenate([mats, material(MAT_DIFFUSE, (0.0, 0.0, 0.0), ks=0.0, emission=(1.0, 1.0, 2.0))])
+    c = np.array((-1.0, 6.0, -1.0))
+    eu, ev = np.array((2.0, 0.4, 0.0)), np.array((0.0, -0.3, 2.0))
+    quad = triangles_from([c, c], [c + eu, c + eu + ev], [c + eu + ev, c + ev], len(mats) - 1)
+    sc.materials = mats
+    sc.triangles = np.concatenate([sc.triangles, quad])
+    sc.name = sc.name + "_emit"
+    return sc
+
+
 def single_sphere(width=65, height=65, albedo=(0.7, 0.5, 0.3), light=(0.0, 0.0, 10.0),
                   eye=(0.0, 0.0, 5.0), radius=1.0, ks=0.0) -> Scene:
     """One unit sphere at the origin, one light, no ground: a closed-form Lambert image."""

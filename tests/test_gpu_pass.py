@@ -1,6 +1,7 @@
-"""Progressive passes on the GPU: area lights sampled once per pass and
-pixel jitter (Alg. 1, Sec. IV.A), against the oracle's passes (same
-Philox4x32-10 samples) and against closed forms."""
+"""Progressive passes on the GPU: area lights and emissive primitives
+sampled once per pass and pixel jitter (Alg. 1, Sec. IV.A, Eq. 7-8),
+against the oracle's passes (same Philox4x32-10 samples) and against
+closed forms."""
 import numpy as np
 import pytest
 import torch
@@ -112,6 +113,74 @@ def test_terrain_with_area_lights_pass_parity():
 
 def test_batch_with_area_lights_matches_single_frames():
     sc = S.scene_spheres8_area(width=40, height=32, max_depth=3)
+    scene = rtb.Scene(sc).build()
+    out = torch.empty(40 * 32 * 3, device="cuda")
+    ref = torch.empty(40 * 32 * 3, device="cuda")
+    b = rtb.Batch([scene], [sc.camera], [40], [32], 3, [out], rtb.make_options(background=sc.background))
+    b.render()
+    rtb.rt_render_ex(scene.handle, sc.camera, 40, 32, 3, ref, rtb.make_options(background=sc.background))
+    torch.cuda.synchronize()
+    err = (out - ref).abs().view(-1, 3).max(dim=1).values
+    assert (err > 1e-5).float().mean().item() <= 1e-3
+    b.close()
+    scene.close()
+
+
+def test_emissive_quad_converges_to_lambert_on_gpu():
+    c = np.array((1.0, 2.0, -1.5))
+    eu, ev = np.array((2.0, 0.5, 0.0)), np.array((0.0, 0.0, 3.0))
+    quad = S.triangles_from([c, c], [c + eu, c + eu + ev], [c + eu + ev, c + ev], 1)
+    sc = P.floor_with_emitters(tris=quad, L=(2.0, 1.0, 0.5))
+    E = P.polygon_irradiance(np.zeros(3), np.array([0.0, 1.0, 0.0]), [c, c + eu, c + eu + ev, c + ev])
+    img = gpu_passes(sc, 1024, 32, depth=0)
+    centre = (sc.height // 2) * sc.width + sc.width // 2
+    np.testing.assert_allclose(img[centre], 0.5 * np.array([2.0, 1.0, 0.5]) * E, rtol=3e-3)
+
+
+def test_emissive_sphere_converges_to_its_solid_angle_on_gpu():
+    r, d = 0.6, 3.0
+    sph = S.spheres_from([(0.0, d, 0.0)], [r], [1])
+    sc = P.floor_with_emitters(spheres=sph, L=(1.0, 0.5, 0.25))
+    sc.camera = S.camera((0.0, 1.0, 0.0), (0.0, 0.0, 0.0), up=(0.0, 0.0, -1.0), vfov_deg=10.0)
+    img = gpu_passes(sc, 1024, 32, depth=0)
+    centre = (sc.height // 2) * sc.width + sc.width // 2
+    np.testing.assert_allclose(img[centre], 0.5 * np.array([1.0, 0.5, 0.25]) * np.pi * (r / d) ** 2, rtol=5e-3)
+    # seen directly, the sphere shows its own emission (Eq. 7); it does not light itself
+    sc.camera = S.camera((0.0, 10.0, 0.0), (0.0, 0.0, 0.0), up=(0.0, 0.0, -1.0), vfov_deg=2.0)
+    top = gpu_render(sc, max_depth=0)["rgb"][centre]
+    np.testing.assert_allclose(top, (1.0, 0.5, 0.25), atol=1e-6)
+
+
+def test_first_pass_with_emitters_matches_oracle():
+    """Pass 0 of seed 0 with an emissive sphere, an emissive quad and a
+    glass sphere: hits, depths and emitter samples as the oracle's."""
+    sc = S.scene_spheres8_emitters(width=64, height=48, max_depth=3)
+    orc = O.OracleScene.from_scene(sc)
+    orc.set_pass(0, 0, 1, False)
+    ref = orc.render(sc.camera, sc.width, sc.height, sc.max_depth, mode="bvh")
+    compare(gpu_render(sc), ref)
+
+
+@pytest.mark.parametrize("flags", [0, rtb.RT_FLAG_PER_DEPTH_WAVEFRONT])
+def test_emitter_passes_match_oracle(flags):
+    sc = S.scene_spheres8_emitters(width=48, height=40, max_depth=3)
+    img = gpu_passes(sc, 8, 2, seed=11, jitter=True, flags=flags)
+    ref, robust = oracle_passes(sc, 8, 2, seed=11, jitter=True)
+    check_colour(img, ref, robust)
+
+
+def test_emitters_with_area_lights_pass_parity():
+    """Area lights take the first sample slots, emitters the next: both kinds
+    in one scene."""
+    sc = S.scene_spheres8_emitters(width=40, height=32, max_depth=2)
+    sc.area_lights = S.area_lights([(-2.0, 8.0, -2.0)], [(4.0, 0.0, 0.0)], [(0.0, 0.0, 4.0)], [(2.0, 2.0, 2.0)])
+    img = gpu_passes(sc, 4, 2, seed=2)
+    ref, robust = oracle_passes(sc, 4, 2, seed=2)
+    check_colour(img, ref, robust)
+
+
+def test_batch_with_emitters_matches_single_frames():
+    sc = S.scene_spheres8_emitters(width=40, height=32, max_depth=3)
     scene = rtb.Scene(sc).build()
     out = torch.empty(40 * 32 * 3, device="cuda")
     ref = torch.empty(40 * 32 * 3, device="cuda")

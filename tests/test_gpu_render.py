@@ -1,4 +1,5 @@
 """GPU parity of the CUDA tracer against the FP64 oracle, through the C ABI."""
+import dataclasses
 import math
 
 import numpy as np
@@ -406,6 +407,28 @@ def test_scene_update_then_rebuild():
     torch.cuda.synchronize()
     fresh = gpu_render(b)
     np.testing.assert_allclose(out.view(-1, 3).double().cpu().numpy(), fresh["rgb"], atol=1e-5)
+    scene.close()
+
+
+def test_scene_update_with_a_bad_material_is_reported():
+    """rt_scene_update does not validate; a material index out of range is
+    replaced by material 0 on the device and reported by the next sync."""
+    a = small_terrain(seed=7)
+    scene = rtb.Scene(a).build()
+    tris = a.triangles.copy()
+    tris["material"][5] = len(a.materials) + 3
+    rtb.rt_scene_update(scene.handle, a.spheres, tris)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_ERR_INVALID_ARG
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK          # the flag is cleared once read
+    rtb.rt_bvh_build(scene.handle)
+    out = torch.empty(a.width * a.height * 3, device="cuda")
+    rtb.rt_render_ex(scene.handle, a.camera, a.width, a.height, a.max_depth, out,
+                     rtb.make_options(background=a.background))
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    fixed = a.triangles.copy()
+    fixed["material"][5] = 0
+    b = dataclasses.replace(a, triangles=fixed)
+    np.testing.assert_allclose(out.view(-1, 3).double().cpu().numpy(), gpu_render(b)["rgb"], atol=1e-5)
     scene.close()
 
 

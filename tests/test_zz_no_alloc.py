@@ -44,6 +44,7 @@ def _render_both(sc):
 @pytest.mark.parametrize("make", [
     lambda: S.scene_spheres8(width=128, height=128),
     lambda: S.scene_terrain(seed=7, width=96, height=64, max_depth=5, cells=(16, 12), n_ico=6, ico_level=2),
+    lambda: S.scene_spheres8_emitters(width=96, height=96),   # 1 point light + 3 emissive primitives
 ])
 def test_noalloc_matches_rt_render_twice(make):
     ref, outs = _render_both(make())
@@ -61,4 +62,18 @@ def test_noalloc_rejects_oversize_frames():
         rtb.rt_render_noalloc(scene.handle, sc.camera, 256, 128, 3, out)   # 32768 > 16384 pixels
     assert ei.value.status == rtb.RT_ERR_UNSUPPORTED
     assert "RT_NOALLOC_MAX_PIXELS" in str(ei.value)
+    scene.close()
+
+
+def test_noalloc_counts_every_kind_of_light():
+    """The shadow queue holds a record per light of any kind: a point light,
+    an area light and three emissive primitives are five."""
+    sc = S.scene_spheres8_emitters(width=8, height=8)
+    sc.area_lights = S.area_lights([(-2.0, 8.0, -2.0)], [(4.0, 0.0, 0.0)], [(0.0, 0.0, 4.0)], [(2.0, 2.0, 2.0)])
+    scene = rtb.Scene(sc).build()
+    out = torch.empty(8 * 8 * 3, device="cuda")
+    with pytest.raises(rtb.RtError) as ei:
+        rtb.rt_render_noalloc(scene.handle, sc.camera, 8, 8, 3, out)
+    assert ei.value.status == rtb.RT_ERR_UNSUPPORTED
+    assert "RT_NOALLOC_MAX_LIGHTS" in str(ei.value)
     scene.close()
