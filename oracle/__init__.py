@@ -65,6 +65,7 @@ def lib():
         L.orc_set_area_lights.restype = I32
         L.orc_set_area_lights.argtypes = [P, P, I64]
         L.orc_set_pass.argtypes = [P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.orc_set_diffuse_bounce.argtypes = [P, ctypes.c_int32]
         L.orc_philox4x32.argtypes = [P, P, P]
         _lib = L
     return _lib
@@ -115,6 +116,10 @@ class OracleScene:
     def set_pass(self, seed=0, index=0, strata=1, jitter=False):
         """The pass later renders use (see orc_set_pass)."""
         lib().orc_set_pass(self._h, int(seed), int(index), int(strata), int(bool(jitter)))
+
+    def set_diffuse_bounce(self, on=True):
+        """Monte-Carlo GI for later renders (see orc_set_diffuse_bounce)."""
+        lib().orc_set_diffuse_bounce(self._h, int(bool(on)))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -30,6 +30,11 @@
  * definition, keyed by the seed and counted by (pixel, pass, path vertex,
  * slot); the progressive image is the mean of the passes.
  *
+ * Monte-Carlo GI (Eq. 8 in full, as an option): besides its light samples a
+ * diffuse vertex sends one cosine-weighted ray over its hemisphere, so light
+ * that other surfaces reflect reaches it too; the ray it makes adds no L_e
+ * where it hits, because the emitters were already sampled as lights.
+ *
  * Besides radiance the oracle reports, per pixel, how close any decision in
  * the pixel's path tree (which primitive is hit, whether a light is blocked,
  * front/back side, n.l > 0, total internal reflection) comes to flipping,
@@ -122,6 +127,7 @@ struct orc_scene {
    * whether the camera ray is jittered inside its pixel */
   uint32_t seed_lo, seed_hi;
   int32_t pass, strata, jitter;
+  int32_t bounce;      /* Monte-Carlo GI: one cosine-weighted diffuse bounce per vertex */
   v3 bg;
   double eps_scale, K;
   double l_max;        /* bound on the radiance any subtree returns */
@@ -545,6 +551,11 @@ void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4
 static inline double unit24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
 #define SLOT_PIXEL 0xFFFFFFFFu
+#define SLOT_BOUNCE 0xFFFFFFFEu
+/* bit 31 of a path-vertex code marks a ray made by a diffuse bounce; the
+ * other bits number the vertex (1 for the camera ray, 2c and 2c + 1 for
+ * the children of vertex c) */
+#define CODE_BOUNCE 0x80000000u
 
 /* A stratified 2-D sample of pass k for (pixel, path vertex `code`, slot):
  * over S x S consecutive passes each cell of an S x S grid is visited once,
@@ -564,6 +575,21 @@ static void pass_sample(const orc_scene* s, int64_t pixel, uint32_t code, uint32
 }
 
 typedef struct { v3 o, d; v3 w; ray_t r; uint32_t code; } child_t;
+
+/* A cosine-weighted direction about the unit normal n for (a, b) in
+ * [0, 1)^2 (Malley's method: the point (sqrt(a), 2 pi b) of the unit disk in
+ * polar form, lifted onto the hemisphere), expressed in the branch-free
+ * orthonormal basis of Duff et al., "Building an Orthonormal Basis,
+ * Revisited" (JCGT 2017), with the sign taken as n.z >= 0. */
+static v3 cosine_dir(v3 n, double a, double b) {
+  double sg = n.z >= 0.0 ? 1.0 : -1.0;
+  double k = -1.0 / (sg + n.z);
+  double m = n.x * n.y * k;
+  v3 t1 = mk(1.0 + sg * n.x * n.x * k, sg * m, -sg * n.x);
+  v3 t2 = mk(m, sg + n.y * n.y * k, -n.y);
+  double r = sqrt(a), phi = 2.0 * M_PI * b;
+  return unit(add(add(scl(t1, r * cos(phi)), scl(t2, r * sin(phi))), scl(n, sqrt(fmax(0.0, 1.0 - a)))));
+}
 
 typedef struct {
   v3 local;            /* emission + (1 - rho) * sum over unblocked lights */
@@ -604,8 +630,11 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
     if (rb < out.robust) out.robust = rb;
   }
 
-  /* L_e of Eq. 7 */
-  out.local = mul(w, m->emis);
+  /* L_e of Eq. 7, except on a ray made by a diffuse bounce: the vertex
+   * that bounced sampled every emitter as a light already */
+  const int via_bounce = (code & CODE_BOUNCE) != 0;
+  code &= ~CODE_BOUNCE;
+  out.local = via_bounce ? mk(0.0, 0.0, 0.0) : mul(w, m->emis);
 
   double eps = offset_eps(s, ph);
   v3 o_up = add(ph, scl(n, eps));
@@ -732,6 +761,27 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
       c->w = scl(w, rho);
       c->code = code << 1;
     }
+    /* Monte-Carlo GI (Eq. 8's hemisphere integral): one cosine-weighted
+     * diffuse bounce; with f_r = albedo (the albedo convention of the light
+     * terms) and density cos / pi its weight is pi (1 - rho) albedo.  Only
+     * the Lambert lobe is integrated: the Phong lobe stays a light term. */
+    if (spawn && s->bounce && 1.0 - rho > 0.0 && maxc(m->albedo) > 0.0) {
+      double a, b;
+      pass_sample(s, pixel, code, SLOT_BOUNCE, &a, &b);
+      child_t* c = &out.child[out.n_children++];
+      c->r.o = o_up;
+      c->r.d = cosine_dir(n, a, b);
+      c->r.eo = eo_child;
+      c->r.en = en_child;
+      c->r.ed = 3.0 * An + s->K * 16 * GAMMA32;
+      c->w = scl(mul(w, m->albedo), M_PI * (1.0 - rho));
+      c->code = ((code << 1) | 1u) | CODE_BOUNCE;
+      if (count_robust) {
+        /* the basis changes branch where n.z changes sign */
+        double rb = fabs(n.z) / (An + s->K * 4 * GAMMA32);
+        if (rb < out.robust) out.robust = rb;
+      }
+    }
   } else {
     double n1 = inside ? m->ior : 1.0, n2 = inside ? 1.0 : m->ior;
     double R, kk;
@@ -799,7 +849,8 @@ static v3 cache_radiance(const orc_scene* s, const ray_t* r, hit_t h) {
 
 /* Radiance arriving along r at depth `depth`, times the ray weight w.  The
  * path vertex the ray leads to is `code`: 1 for the camera ray, then
- * 2c (reflection) and 2c + 1 (refraction) for the children of vertex c. */
+ * 2c (reflection) and 2c + 1 (refraction or diffuse bounce) for the
+ * children of vertex c, with CODE_BOUNCE set on a diffuse bounce. */
 static v3 trace_rec(trace_ctx* cx, const ray_t* r, int depth, v3 w, int64_t pixel, uint32_t code, int32_t* prim0,
                     double* t0) {
   const orc_scene* s = cx->s;
@@ -1045,6 +1096,8 @@ void orc_set_pass(orc_scene* s, uint64_t seed, int32_t pass, int32_t strata, int
   s->strata = strata > 0 ? strata : 1;
   s->jitter = jitter != 0;
 }
+
+void orc_set_diffuse_bounce(orc_scene* s, int32_t on) { s->bounce = on != 0; }
 
 void orc_set_cache(orc_scene* s, int depth, const double* W, const double* B, int bf16, const double* lo,
                    const double* inv_ext) {

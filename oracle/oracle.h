@@ -57,6 +57,12 @@ int orc_set_area_lights(orc_scene* s, const void* lights, int64_t n);
  * strata 1, no jitter. */
 void orc_set_pass(orc_scene* s, uint64_t seed, int32_t pass, int32_t strata, int32_t jitter);
 
+/* Monte-Carlo GI (on != 0): every non-dielectric hit with 1 - rho > 0 and
+ * some albedo > 0 spawns, below the last depth, one cosine-weighted diffuse
+ * ray of weight pi (1 - rho) albedo (sample slot 2^32 - 2 of its vertex);
+ * the ray it makes adds no L_e where it hits.  Default off. */
+void orc_set_diffuse_bounce(orc_scene* s, int32_t on);
+
 /* Philox4x32-10 of counter ctr[4] under key key[2] (exposed for tests). */
 void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
