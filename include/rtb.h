@@ -100,8 +100,16 @@ enum {
   RT_FLAG_STAGE_TIMING = 1,   /* record per-stage CUDA events (stats.ms_*) */
   RT_FLAG_COUNT_WORK = 2,     /* count node visits / primitive tests (slower kernels) */
   RT_FLAG_NO_GRAPH = 4,       /* launch the kernels directly, no CUDA graph */
-  RT_FLAG_PER_DEPTH_WAVEFRONT = 8  /* queue every depth (default: depth 0 as a wavefront,
+  RT_FLAG_PER_DEPTH_WAVEFRONT = 8, /* queue every depth (default: depth 0 as a wavefront,
                                       deeper rays depth-first, one thread per depth-1 subtree) */
+  RT_FLAG_DIFFUSE_BOUNCE = 16      /* Monte-Carlo GI (Eq. 8's hemisphere integral): below the
+                                      last depth, every non-dielectric hit with reflectivity < 1
+                                      and some albedo > 0 also sends one cosine-weighted ray of
+                                      weight pi (1 - reflectivity) albedo (f_r = albedo, as in the
+                                      light terms), drawn from the pass (rt_pass).  That ray adds
+                                      no emission where it hits: emitters are sampled as lights.
+                                      Only the Lambert lobe is integrated.  Not with the radiance
+                                      cache (RT_ERR_UNSUPPORTED). */
 };
 
 typedef struct rt_render_options {

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
     }
     // --- one item per lane
     Children ch;
-    ch.want_r = ch.want_t = false;
+    ch.want_r = ch.want_t = ch.bounce = false;
     if (have && depth < 0) {
       bool sfail = false;
       float tm = tmax_item;
@@ -187,7 +187,11 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
       } else {
         atomicAdd(&s_cnt[2][depth], 1u);
         Surface sf = surface_at(sc, hit, o, d, t, bp.eps_scale);
-        if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_rgb(fb, pixel, w * sf.emission);
+        // L_e (not on a diffuse bounce: its parent sampled the emitters)
+        const bool via_bounce = kPass && (code & kCodeBounce) != 0u;
+        const uint32_t vcode = kPass ? (code & ~kCodeBounce) : code;
+        if (!via_bounce && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f))
+          add_rgb(fb, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
           // point lights, then one sampled point of each area light and emitter
           for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights + sc.n_emitters : 0); ++li) {
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
               lit = false;
               if constexpr (kPass) {
                 float a, b;
-                pass_sample(bp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
+                pass_sample(bp.ps, pixel, vcode, (uint32_t)(li - sc.n_lights), a, b);
                 lit = area_term(sf, d, w, area_point(sc, li - sc.n_lights, a, b), contrib, os, sd, tmax);
               }
             }
@@ -223,7 +227,10 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
             if (h < 0 && !sfail) add_rgb(fb, pixel, contrib);
           }
         }
-        if (depth < bp.max_depth) ch = children_of(sf, d, w);
+        if (depth < bp.max_depth) {
+          ch = children_of(sf, d, w);
+          if (kPass && bp.ps.bounce) add_bounce(ch, sf, w, bp.ps, pixel, vcode);
+        }
       }
     }
     // --- a second child goes to the warp's stack (or this lane's overflow)
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
         o = ch.ot;
         d = ch.dt;
         w = ch.wt;
-        code = (code << 1) | 1u;
+        code = (code << 1) | 1u | (ch.bounce ? kCodeBounce : 0u);
         ++depth;
       } else if (ch.want_r) {
         o = ch.or_;
@@ -398,6 +405,7 @@ static rt_status batch_graph(rt_batch* b, const rt_tune& tune, bool pass, unsign
   bp.cnt = (BatchCounts*)b->counts.p;
   memset(&bp.ps, 0, sizeof(bp.ps));
   bp.ps.strata = 1;
+  bp.ps.bounce = (b->opt.flags & RT_FLAG_DIFFUSE_BOUNCE) != 0;
   cudaStream_t cs = b->cap_stream;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: begin capture");
@@ -427,7 +435,7 @@ static rt_status batch_render(rt_batch* b, const rt_tune& tune, cudaStream_t st)
   unsigned n_tiles = 0;
   rt_status rs = batch_table(b, tune, &n_tiles, st);
   if (rs) return rs;
-  bool pass = false;
+  bool pass = (b->opt.flags & RT_FLAG_DIFFUSE_BOUNCE) != 0;
   for (rt_scene* s : b->scenes) pass = pass || s->n_alights > 0 || s->n_emitters > 0;
   cudaGraphExec_t exec = nullptr;
   if ((rs = batch_graph(b, tune, pass, n_tiles, &exec))) return rs;

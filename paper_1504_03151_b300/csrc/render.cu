@@ -202,8 +202,11 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
       }
       is_hit = sel;
     }
-    if (is_hit && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f))
-      add_fb(fp, pixel, w * sf.emission);   // L_e, Eq. 7
+    // L_e, Eq. 7 (not on a diffuse bounce: its parent sampled the emitters)
+    const bool via_bounce = kPass && (code & kCodeBounce) != 0u;
+    const uint32_t vcode = kPass ? (code & ~kCodeBounce) : code;
+    if (is_hit && !via_bounce && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f))
+      add_fb(fp, pixel, w * sf.emission);
     // Alg. 1: one shadow ray per point light where n.l > 0
     bool local = is_hit && sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f;
     for (int li = 0; li < sc.n_lights; ++li) {
@@ -222,23 +225,27 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
       bool valid = false;
       if (local) {
         float a, b;
-        pass_sample(fp.ps, pixel, code, (uint32_t)li, a, b);
+        pass_sample(fp.ps, pixel, vcode, (uint32_t)li, a, b);
         valid = area_term(sf, d, w, area_point(sc, li, a, b), contrib, os, sd, tmax);
       }
       bool ok;
       unsigned pos = warp_push(&ctr->shadow[depth], valid, fp.shadow_cap, ok, sc.status);
       if (ok) store_ray(fp.shadowq[depth & 1], pos, os, pixel, sd, tmax, contrib);
     }
-    // reflection / refraction rays (Fig. 3), not past the last depth
+    // reflection / refraction rays (Fig. 3) or a diffuse bounce, not past the last depth
     Children ch;
-    ch.want_r = ch.want_t = false;
-    if (is_hit && spawn) ch = children_of(sf, d, w);
+    ch.want_r = ch.want_t = ch.bounce = false;
+    if (is_hit && spawn) {
+      ch = children_of(sf, d, w);
+      if (kPass && fp.ps.bounce) add_bounce(ch, sf, w, fp.ps, pixel, vcode);
+    }
     {
       bool ok;
       unsigned pos = warp_push(&ctr->rays[depth + 1], ch.want_r, fp.ray_cap, ok, sc.status);
-      if (ok) store_ray(qout, pos, ch.or_, pixel, ch.dr, INFINITY, ch.wr, code << 1);
+      if (ok) store_ray(qout, pos, ch.or_, pixel, ch.dr, INFINITY, ch.wr, vcode << 1);
       pos = warp_push(&ctr->rays[depth + 1], ch.want_t, fp.ray_cap, ok, sc.status);
-      if (ok) store_ray(qout, pos, ch.ot, pixel, ch.dt, INFINITY, ch.wt, (code << 1) | 1u);
+      const uint32_t code_t = (vcode << 1) | 1u | (ch.bounce ? kCodeBounce : 0u);
+      if (ok) store_ray(qout, pos, ch.ot, pixel, ch.dt, INFINITY, ch.wt, code_t);
     }
   }
   flush_work<kCount>(ctr, 0, depth, wc);
@@ -391,7 +398,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
     if (!__any_sync(kFull, have)) break;   // nothing left for this warp
     // --- one segment per lane: closest hit, shading, shadow rays, children
     Children ch;
-    ch.want_r = ch.want_t = false;
+    ch.want_r = ch.want_t = ch.bounce = false;
     if (have && depth < 0) {
       bool sfail = false;
       float tm = tmax_item;
@@ -444,8 +451,12 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
           }
         }
       }
+      // L_e (not on a diffuse bounce: its parent sampled the emitters)
+      const bool via_bounce = kPass && (code & kCodeBounce) != 0u;
+      const uint32_t vcode = kPass ? (code & ~kCodeBounce) : code;
       if (live) {
-        if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
+        if (!via_bounce && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f))
+          add_fb(fp, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
           // point lights, then one sampled point of each area light and emitter
           for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights + sc.n_emitters : 0); ++li) {
@@ -459,7 +470,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
               lit = false;
               if constexpr (kPass) {
                 float a, b;
-                pass_sample(fp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
+                pass_sample(fp.ps, pixel, vcode, (uint32_t)(li - sc.n_lights), a, b);
                 lit = area_term(sf, d, w, area_point(sc, li - sc.n_lights, a, b), contrib, os, sd, tmax);
               }
             }
@@ -485,6 +496,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
         }
         if (depth < fp.max_depth) {
           ch = children_of(sf, d, w);
+          if (kPass && fp.ps.bounce) add_bounce(ch, sf, w, fp.ps, pixel, vcode);
           if (ch.want_r || ch.want_t) atomicAdd(&s_cnt[0][depth + 1], (unsigned)ch.want_r + (unsigned)ch.want_t);
         }
       }
@@ -525,7 +537,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
         o = ch.ot;
         d = ch.dt;
         w = ch.wt;
-        code = (code << 1) | 1u;
+        code = (code << 1) | 1u | (ch.bounce ? kCodeBounce : 0u);
         ++depth;
       } else if (ch.want_r) {
         o = ch.or_;
@@ -735,10 +747,13 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   if (!std::isfinite(opt.background[0]) || !std::isfinite(opt.background[1]) || !std::isfinite(opt.background[2]) ||
       !std::isfinite(opt.eps_scale) || opt.eps_scale < 0.f || opt.queue_capacity < 0 || opt.traversal_cap < 0)
     return set_error(RT_ERR_INVALID_ARG, "rt_render: invalid options");
+  if (nrc && (opt.flags & RT_FLAG_DIFFUSE_BOUNCE))
+    return set_error(RT_ERR_UNSUPPORTED, "rt_render_nrc: the radiance cache does not take RT_FLAG_DIFFUSE_BOUNCE");
   bool use_bvh = opt.use_bvh != 0;
   if (use_bvh && !s->built) return set_error(RT_ERR_NOT_BUILT, "rt_render: BVH requested before rt_bvh_build");
   occupancy(s);
-  int64_t lights = std::max<int64_t>(s->n_lights, 1);
+  // shadow rays per hit: one per point light, area light and emissive primitive
+  int64_t lights = std::max<int64_t>(s->n_lights + s->n_alights + s->n_emitters, 1);
   int64_t qcap = opt.queue_capacity > 0 ? opt.queue_capacity : std::max<int64_t>(2 * (int64_t)W * H, 65536);
   int64_t scap = qcap * lights;
   if (qcap > 0x7fffffffLL || scap > 0x7fffffffLL) return set_error(RT_ERR_UNSUPPORTED, "rt_render: queue too large");
@@ -765,7 +780,9 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     fp.ps.strata = pass->strata;
     fp.ps.jitter = pass->jitter != 0;
   }
-  const bool pass_k = s->n_alights > 0 || s->n_emitters > 0 || fp.ps.jitter;   // kernels with the sampling code
+  fp.ps.bounce = (opt.flags & RT_FLAG_DIFFUSE_BOUNCE) != 0;
+  // kernels with the sampling code
+  const bool pass_k = s->n_alights > 0 || s->n_emitters > 0 || fp.ps.jitter || fp.ps.bounce;
   fp.cam = camera_basis(cam, W, H);
   fp.W = W;
   fp.H = H;

@@ -331,9 +331,16 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
 struct PassInfo {
   uint32_t seed_lo, seed_hi;
   int pass, strata, jitter;
+  int bounce;   // Monte-Carlo GI: one cosine-weighted diffuse bounce per vertex
 };
 
-constexpr uint32_t kSlotPixel = 0xFFFFFFFFu;   // the camera jitter's slot (area light i uses slot i)
+constexpr uint32_t kSlotPixel = 0xFFFFFFFFu;    // the camera jitter's slot (light i uses slot i)
+constexpr uint32_t kSlotBounce = 0xFFFFFFFEu;   // the diffuse bounce's slot
+// bit 31 of a path-vertex code marks a ray made by a diffuse bounce; the
+// other bits number the vertex (1 for the camera ray, 2c and 2c + 1 for the
+// children of vertex c; vertex numbers stay below 2^18, so shifting a code
+// left drops the mark)
+constexpr uint32_t kCodeBounce = 0x80000000u;
 
 __device__ __forceinline__ uint4 philox4x32(uint4 c, uint2 k) {
 #pragma unroll
@@ -515,12 +522,13 @@ __device__ __forceinline__ bool area_term(const Surface& sf, f3 d, f3 w, const A
 // refraction (none on total internal reflection).
 struct Children {
   bool want_r, want_t;
+  bool bounce;   // the second child is a diffuse bounce, not a refraction
   f3 or_, dr, wr, ot, dt, wt;
 };
 
 __device__ __forceinline__ Children children_of(const Surface& sf, f3 d, f3 w) {
   Children c;
-  c.want_r = c.want_t = false;
+  c.want_r = c.want_t = c.bounce = false;
   c.or_ = sf.p + sf.n * sf.eps;
   c.ot = sf.p - sf.n * sf.eps;
   c.dr = c.dt = mk3(0, 0, 1);
@@ -554,6 +562,43 @@ __device__ __forceinline__ Children children_of(const Surface& sf, f3 d, f3 w) {
     c.wr = w * R;
   }
   return c;
+}
+
+// A cosine-weighted direction about the unit normal n for (a, b) in
+// [0, 1)^2: Malley's method (the point (sqrt(a), 2 pi b) of the unit disk in
+// polar form, lifted onto the hemisphere), in the branch-free orthonormal
+// basis of Duff et al., "Building an Orthonormal Basis, Revisited" (JCGT
+// 2017), with the sign taken as n.z >= 0.
+__device__ __forceinline__ f3 cosine_dir(f3 n, float a, float b) {
+  const float sg = n.z >= 0.f ? 1.f : -1.f;
+  const float k = -1.f / (sg + n.z);
+  const float m = n.x * n.y * k;
+  const f3 t1 = mk3(1.f + sg * n.x * n.x * k, sg * m, -sg * n.x);
+  const f3 t2 = mk3(m, sg + n.y * n.y * k, -n.y);
+  const float r = sqrtf(a);
+  float sn, cs;
+  sincospif(2.f * b, &sn, &cs);
+  return normalize(t1 * (r * cs) + t2 * (r * sn) + n * sqrtf(fmaxf(0.f, 1.f - a)));
+}
+
+// Monte-Carlo GI (Eq. 8's hemisphere integral over the Lambert lobe): a
+// non-dielectric hit with 1 - rho > 0 and some albedo > 0 sends one
+// cosine-weighted ray from the offset point above it, of weight
+// pi (1 - rho) albedo (f_r = albedo, as in the light terms, over the
+// density cos / pi).  It takes the second child's place, which only a
+// dielectric uses otherwise.  vcode: the hit's vertex (without the mark).
+__device__ __forceinline__ void add_bounce(Children& c, const Surface& sf, f3 w, const PassInfo& ps, int pixel,
+                                           uint32_t vcode) {
+  if (sf.kind == RT_MAT_DIELECTRIC || !((1.f - sf.rho) > 0.f) ||
+      !(fmaxf(fmaxf(sf.albedo.x, sf.albedo.y), sf.albedo.z) > 0.f))
+    return;
+  float a, b;
+  pass_sample(ps, pixel, vcode, kSlotBounce, a, b);
+  c.want_t = true;
+  c.bounce = true;
+  c.ot = c.or_;
+  c.dt = cosine_dir(sf.n, a, b);
+  c.wt = w * sf.albedo * (kPi * (1.f - sf.rho));
 }
 
 }  // namespace rtb

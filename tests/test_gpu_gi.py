@@ -1,0 +1,115 @@
+"""Monte-Carlo GI on the GPU (RT_FLAG_DIFFUSE_BOUNCE: Eq. 8's hemisphere
+integral by one cosine-weighted diffuse bounce per vertex), against the
+closed forms that pin the oracle's GI and against the oracle's GI passes
+(the same Philox4x32-10 samples)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1504_03151_b300 as rtb
+from paper_1504_03151_b300 import build as rtb_build
+from paper_1504_03151_b300 import scenes as S
+
+import test_oracle_gi as G
+from test_gpu_pass import check_colour, gpu_passes
+
+pytestmark = pytest.mark.gpu
+
+GI = rtb.RT_FLAG_DIFFUSE_BOUNCE
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(gpu):
+    rtb_build.build()
+    torch.cuda.set_device(0)
+
+
+def oracle_gi_passes(sc, passes, strata, seed, jitter=False, depth=None):
+    orc = O.OracleScene.from_scene(sc)
+    orc.set_diffuse_bounce(True)
+    D = sc.max_depth if depth is None else depth
+    acc, robust = None, None
+    for k in range(passes):
+        orc.set_pass(seed, k, strata, jitter)
+        r = orc.render(sc.camera, sc.width, sc.height, D, mode="bvh")
+        acc = r["rgb"] if acc is None else acc + (r["rgb"] - acc) / (k + 1)
+        robust = r["robust"] if robust is None else np.minimum(robust, r["robust"])
+    return acc, robust
+
+
+@pytest.mark.parametrize("depth,passes,rtol", [(0, 256, 4e-3), (1, 256, 5e-3), (3, 1024, 1e-2)])
+def test_furnace_closed_form_on_gpu(depth, passes, rtol):
+    a, Le = 0.25, (1.0, 0.5, 2.0)
+    sc = G.furnace(a, Le)
+    got = gpu_passes(sc, passes, 8, depth=depth, flags=GI)
+    want = G.furnace_value(a, Le, depth)
+    np.testing.assert_allclose(got.mean(axis=0), want, rtol=rtol)
+    assert np.median(np.abs(got / want - 1)) < 0.05
+
+
+@pytest.mark.parametrize("R", [np.eye(3), G.rotation((1.0, 0.3, 0.2), 50.0), G.rotation((1.0, -0.4, 0.1), -70.0)],
+                         ids=["upright", "normal_z_pos", "normal_z_neg"])
+def test_open_sky_with_a_wall_on_gpu(R):
+    sc = G.rotated(G.floor_and_wall(), R)
+    want = G.wall_expected(sc, R)
+    got = gpu_passes(sc, 1024, 32, depth=2, flags=GI)
+    np.testing.assert_allclose(got.mean(axis=0), want.mean(axis=0), rtol=3e-3)
+    np.testing.assert_allclose(got, want, rtol=0.05)
+
+
+@pytest.mark.parametrize("flags", [GI, GI | rtb.RT_FLAG_PER_DEPTH_WAVEFRONT])
+def test_gi_passes_match_oracle(flags):
+    """Emitters, a glass sphere and mirrors with the diffuse bounce, in both
+    pipeline forms."""
+    sc = S.scene_spheres8_emitters(width=48, height=40, max_depth=3)
+    img = gpu_passes(sc, 8, 2, seed=11, jitter=True, flags=flags)
+    ref, robust = oracle_gi_passes(sc, 8, 2, seed=11, jitter=True)
+    check_colour(img, ref, robust)
+
+
+def test_terrain_gi_pass_parity():
+    """The bench terrain (small) with point lights, an area light and the
+    bounce: its diffuse terrain sends a bounce from nearly every hit."""
+    sc = S.scene_terrain(seed=7, width=64, height=40, max_depth=3, cells=(16, 12), n_ico=6, ico_level=2)
+    sc.area_lights = S.area_lights([(-20.0, 15.0, -10.0)], [(8.0, 0.0, 0.0)], [(0.0, 0.0, 8.0)], [(1.5, 1.5, 1.2)])
+    img = gpu_passes(sc, 4, 2, seed=5, jitter=True, flags=GI)
+    ref, robust = oracle_gi_passes(sc, 4, 2, seed=5, jitter=True)
+    check_colour(img, ref, robust)
+
+
+def test_gi_is_off_at_depth_zero_and_without_the_flag():
+    sc = S.scene_spheres8_emitters(width=40, height=32, max_depth=2)
+    np.testing.assert_allclose(gpu_passes(sc, 2, 2, seed=4, depth=0, flags=GI),
+                               gpu_passes(sc, 2, 2, seed=4, depth=0), atol=1e-6)
+    assert not np.allclose(gpu_passes(sc, 2, 2, seed=4, flags=GI), gpu_passes(sc, 2, 2, seed=4), atol=1e-3)
+
+
+def test_batch_with_gi_matches_single_frames():
+    sc = S.scene_spheres8_emitters(width=40, height=32, max_depth=3)
+    scene = rtb.Scene(sc).build()
+    out = torch.empty(40 * 32 * 3, device="cuda")
+    ref = torch.empty(40 * 32 * 3, device="cuda")
+    opts = rtb.make_options(background=sc.background, flags=GI)
+    b = rtb.Batch([scene], [sc.camera], [40], [32], 3, [out], opts)
+    b.render()
+    rtb.rt_render_ex(scene.handle, sc.camera, 40, 32, 3, ref, opts)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    torch.cuda.synchronize()
+    err = (out - ref).abs().view(-1, 3).max(dim=1).values
+    assert (err > 1e-5).float().mean().item() <= 1e-3
+    b.close()
+    scene.close()
+
+
+def test_gi_with_the_radiance_cache_is_refused():
+    sc = S.scene_spheres8(width=16, height=16, max_depth=3)
+    scene = rtb.Scene(sc).build()
+    nrc = rtb.rt_nrc_create(scene.handle)
+    out = torch.empty(16 * 16 * 3, device="cuda")
+    with pytest.raises(rtb.RtError) as ei:
+        rtb.rt_render_nrc(scene.handle, nrc, sc.camera, 16, 16, 3, out, train=False,
+                          options=rtb.make_options(background=sc.background, flags=GI))
+    assert ei.value.status == rtb.RT_ERR_UNSUPPORTED
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()
