@@ -286,6 +286,40 @@ def scaleup_leg(rtb, S, torch, dev, stream, flush, steps, with_nrc):
     return line
 
 
+def passes_leg(rtb, S, torch, dev, stream, flush, steps):
+    """Progressive passes of the headline terrain with sampled lights (two
+    area lights and a glowing sphere besides the 4 point lights), jittered
+    camera rays over 4 x 4 strata, depth 5; once with light sampling alone
+    and once with the diffuse bounce (Monte-Carlo GI).  Rays per pass are the
+    mean of four counted passes."""
+    sc = S.scene_terrain_lit()
+    W, H, D = sc.width, sc.height, sc.max_depth
+    scene = rtb.Scene(sc).build()
+    acc = torch.empty(W * H * 3, device=dev)
+    out = {"metric": "Mrays/s per progressive pass", "unit": UNIT,
+           "workload": f"terrain {W}x{H}, {sc.n_prims} primitives, depth {D}, {len(sc.lights)} point lights + "
+                       f"{len(sc.area_lights)} area lights + 1 emissive sphere, jittered passes (4x4 strata)",
+           "l2": "flushed between passes"}
+    for name, flags in (("direct", 0), ("gi", rtb.RT_FLAG_DIFFUSE_BOUNCE)):
+        opts = rtb.make_options(background=sc.background, flags=flags)
+        counted = [rtb.rt_render_pass(scene.handle, sc.camera, W, H, D, rtb.make_pass(k, 7, 4, True), acc, opts,
+                                      stats=True) for k in range(4)]
+        rays = sum(c["primary"] + c["shadow"] + c["secondary"] for c in counted) / len(counted)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            rtb.rt_render_pass(scene.handle, sc.camera, W, H, D, rtb.make_pass(4 + k, 7, 4, True), acc, opts)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(c) for a, c in ev) / steps
+        out[name] = {"value": rays / (ms * 1e3), "ms_per_pass": ms, "rays_per_pass": rays,
+                     "shadow_per_pass": sum(c["shadow"] for c in counted) / len(counted),
+                     "secondary_per_pass": sum(c["secondary"] for c in counted) / len(counted)}
+    scene.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,6 +332,7 @@ def main():
     ap.add_argument("--no-nrc", action="store_true", help="skip the radiance-cache leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-scene batch leg")
     ap.add_argument("--no-scaleup", action="store_true", help="skip the 10.9M-triangle 4K leg")
+    ap.add_argument("--no-passes", action="store_true", help="skip the progressive-pass (sampled lights, GI) leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -485,6 +520,9 @@ def main():
     batch_line = None
     if world == 1 and not args.no_batch:
         batch_line = batch_leg(rtb, S, torch, dev, stream, flush, max(args.steps // 2, 3))
+    passes_line = None
+    if world == 1 and not args.no_passes:
+        passes_line = passes_leg(rtb, S, torch, dev, stream, flush, max(args.steps // 2, 3))
     scaleup_line = None
     if world == 1 and not args.no_scaleup:
         scaleup_line = scaleup_leg(rtb, S, torch, dev, stream, flush, 3, not args.no_nrc)
@@ -526,6 +564,8 @@ def main():
             line["radiance_cache"] = nrc_line
         if batch_line:
             line["batch"] = batch_line
+        if passes_line:
+            line["passes"] = passes_line
         if scaleup_line:
             line["scaleup"] = scaleup_line
         print(json.dumps(line), flush=True)

@@ -108,8 +108,9 @@ enum {
                                       weight pi (1 - reflectivity) albedo (f_r = albedo, as in the
                                       light terms), drawn from the pass (rt_pass).  That ray adds
                                       no emission where it hits: emitters are sampled as lights.
-                                      Only the Lambert lobe is integrated.  Not with the radiance
-                                      cache (RT_ERR_UNSUPPORTED). */
+                                      Only the Lambert lobe is integrated.  Such a frame runs
+                                      every depth as a wavefront (as RT_FLAG_PER_DEPTH_WAVEFRONT).
+                                      Not with the radiance cache (RT_ERR_UNSUPPORTED). */
 };
 
 typedef struct rt_render_options {
@@ -245,10 +246,11 @@ rt_status rt_bvh_export_wide(rt_scene* s, float* nodes, int64_t nodes_capacity, 
  * options and limits of rt_render_ex) and folds it into accum_rgb_device
  * (H*W*3 float32), the running mean of passes 0..index: pass 0 overwrites
  * it, pass k adds (image - accum) / (k + 1).  Passes of one image must run
- * in order on one stream. */
+ * in order on one stream.  stats (nullable) receives the pass's ray counts
+ * as rt_render_ex's do (syncs the stream). */
 rt_status rt_render_pass(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
                          const rt_pass* pass, float* accum_rgb_device, const rt_render_options* options,
-                         void* stream);
+                         rt_render_stats* stats, void* stream);
 
 /* Renders one frame into out_rgb_device (H*W*3 float32, overwritten). */
 rt_status rt_render(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,

@@ -162,7 +162,7 @@ def lib():
             "rt_batch_autotune": (I, [P, P, P, P]),
             "rt_batch_destroy": (I, [P]),
             "rt_scene_set_area_lights": (I, [P, P, S]),
-            "rt_render_pass": (I, [P, P, I, I, I, P, P, P, P]),
+            "rt_render_pass": (I, [P, P, I, I, I, P, P, P, P, P]),
             "rt_scene_destroy": (I, [P]),
         }
         for name, (res, args) in sigs.items():
@@ -437,12 +437,16 @@ def rt_scene_set_area_lights(scene, lights):
     _check(lib().rt_scene_set_area_lights(scene, a.ctypes.data if len(a) else None, len(a)))
 
 
-def rt_render_pass(scene, camera, width, height, max_depth, pass_, accum_rgb, options=None, stream=None):
-    """Renders pass `pass_` (an rt_pass) and folds it into the running mean accum_rgb."""
+def rt_render_pass(scene, camera, width, height, max_depth, pass_, accum_rgb, options=None, stats=False,
+                   stream=None):
+    """Renders pass `pass_` (an rt_pass) and folds it into the running mean accum_rgb;
+    with stats, returns the pass's ray counts (syncs)."""
     cam = make_camera(camera)
+    st = rt_render_stats() if stats else None
     _check(lib().rt_render_pass(scene, ctypes.byref(cam), width, height, max_depth, ctypes.byref(pass_),
                                 _dptr(accum_rgb), ctypes.byref(options) if options is not None else None,
-                                _stream(stream)))
+                                ctypes.byref(st) if st is not None else None, _stream(stream)))
+    return stats_dict(st, max_depth) if st is not None else None
 
 
 def rt_batch_create(scenes, cameras, widths, heights, max_depth, outs, options=None):

@@ -451,12 +451,10 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
           }
         }
       }
-      // L_e (not on a diffuse bounce: its parent sampled the emitters)
-      const bool via_bounce = kPass && (code & kCodeBounce) != 0u;
-      const uint32_t vcode = kPass ? (code & ~kCodeBounce) : code;
+      // (frames with the diffuse bounce run every depth as a wavefront, so
+      // no path here is a bounce and every hit adds its L_e)
       if (live) {
-        if (!via_bounce && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f))
-          add_fb(fp, pixel, w * sf.emission);
+        if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
           // point lights, then one sampled point of each area light and emitter
           for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights + sc.n_emitters : 0); ++li) {
@@ -470,7 +468,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
               lit = false;
               if constexpr (kPass) {
                 float a, b;
-                pass_sample(fp.ps, pixel, vcode, (uint32_t)(li - sc.n_lights), a, b);
+                pass_sample(fp.ps, pixel, code, (uint32_t)(li - sc.n_lights), a, b);
                 lit = area_term(sf, d, w, area_point(sc, li - sc.n_lights, a, b), contrib, os, sd, tmax);
               }
             }
@@ -496,7 +494,6 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
         }
         if (depth < fp.max_depth) {
           ch = children_of(sf, d, w);
-          if (kPass && fp.ps.bounce) add_bounce(ch, sf, w, fp.ps, pixel, vcode);
           if (ch.want_r || ch.want_t) atomicAdd(&s_cnt[0][depth + 1], (unsigned)ch.want_r + (unsigned)ch.want_t);
         }
       }
@@ -537,7 +534,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
         o = ch.ot;
         d = ch.dt;
         w = ch.wt;
-        code = (code << 1) | 1u | (ch.bounce ? kCodeBounce : 0u);
+        code = (code << 1) | 1u;
         ++depth;
       } else if (ch.want_r) {
         o = ch.or_;
@@ -832,8 +829,12 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
   bool per_depth = (opt.flags & RT_FLAG_PER_DEPTH_WAVEFRONT) != 0;
   // depths 0..last run as wavefronts; the rest run as depth-first paths,
-  // which meet the cache at depth T themselves unless it is depth 0
-  int last = per_depth ? D : (T == 0 ? 0 : 0);
+  // which meet the cache at depth T themselves unless it is depth 0.  With
+  // the diffuse bounce nearly every hit has a child, every depth is wide,
+  // and wavefronts are faster at each of them (measured on the 1080p terrain:
+  // 2.2 ms a pass against 3.5 ms depth first); the radiance cache never bounces.
+  if (fp.ps.bounce) per_depth = true;
+  int last = per_depth ? D : 0;
   bool cache_in_paths = !per_depth && T >= 1;
   if (per_depth || T == 0) fp.path_depth0 = T >= 0 ? T + 1 : 1;
   else fp.path_depth0 = 1;
@@ -969,7 +970,7 @@ __global__ void k_accumulate(float* __restrict__ accum, const float* __restrict_
 }
 
 rt_status rt_render_pass(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth, const rt_pass* pass,
-                         float* accum, const rt_render_options* opt, void* stream) {
+                         float* accum, const rt_render_options* opt, rt_render_stats* stats, void* stream) {
   if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_render_pass: scene is NULL");
   if (!pass || !accum) return set_error(RT_ERR_INVALID_ARG, "rt_render_pass: NULL pass or image");
   if (pass->index < 0 || pass->strata < 1 || pass->reserved != 0)
@@ -979,7 +980,7 @@ rt_status rt_render_pass(rt_scene* s, const rt_camera* cam, int width, int heigh
   rt_status rs = ensure(s->pass_img, n * sizeof(float));
   if (rs) return rs;
   cudaStream_t st = (cudaStream_t)stream;
-  rs = render_impl(s, cam, width, height, max_depth, (float*)s->pass_img.p, opt, nullptr, nullptr, nullptr, st,
+  rs = render_impl(s, cam, width, height, max_depth, (float*)s->pass_img.p, opt, nullptr, nullptr, stats, st,
                    nullptr, 0, pass);
   if (rs) return rs;
   k_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(accum, (const float*)s->pass_img.p, n, pass->index);

@@ -326,6 +326,21 @@ def scene_terrain(seed: int = 2, width: int = 1920, height: int = 1080, max_dept
                  camera((0, 12, 38), (0, 0, 0)), width, height, max_depth)
 
 
+def scene_terrain_lit(seed: int = 2, width: int = 1920, height: int = 1080, max_depth: int = 5, **kw) -> Scene:
+    """The terrain with sampled lights besides its 4 point lights: two
+    parallelogram area lights (8 x 8 at height 18 facing down, radiance 0.6;
+    6 x 4 tilted at height 14, radiance 0.4 x (1, 0.8, 0.6)) and a glowing
+    sphere of radius 1.5 at (6, 9, -4) (emission (2, 1.6, 1.2), no albedo)."""
+    sc = scene_terrain(seed, width, height, max_depth, **kw)
+    mats = np.concatenate([sc.materials, material(MAT_DIFFUSE, (0.0, 0.0, 0.0), ks=0.0, emission=(2.0, 1.6, 1.2))])
+    sc.materials = mats
+    sc.spheres = spheres_from([(6.0, 9.0, -4.0)], [1.5], [len(mats) - 1])
+    sc.area_lights = area_lights([(-12.0, 18.0, -8.0), (4.0, 14.0, 2.0)], [(8.0, 0.0, 0.0), (6.0, -1.0, 0.0)],
+                                 [(0.0, 0.0, 8.0), (0.0, 0.0, 4.0)], [(0.6, 0.6, 0.6), (0.4, 0.32, 0.24)])
+    sc.name = sc.name + "_lit"
+    return sc
+
+
 def scene_batch_member(seed: int, n_tris_target: int, width: int, height: int, max_depth: int = 4) -> Scene:
     """One scene of a batch: ~80 % terrain / ~20 % across 20 icospheres, sized to
     roughly n_tris_target triangles."""

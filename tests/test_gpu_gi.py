@@ -58,12 +58,11 @@ def test_open_sky_with_a_wall_on_gpu(R):
     np.testing.assert_allclose(got, want, rtol=0.05)
 
 
-@pytest.mark.parametrize("flags", [GI, GI | rtb.RT_FLAG_PER_DEPTH_WAVEFRONT])
-def test_gi_passes_match_oracle(flags):
-    """Emitters, a glass sphere and mirrors with the diffuse bounce, in both
-    pipeline forms."""
+def test_gi_passes_match_oracle():
+    """Emitters, a glass sphere and mirrors with the diffuse bounce (a frame
+    with the bounce runs every depth as a wavefront)."""
     sc = S.scene_spheres8_emitters(width=48, height=40, max_depth=3)
-    img = gpu_passes(sc, 8, 2, seed=11, jitter=True, flags=flags)
+    img = gpu_passes(sc, 8, 2, seed=11, jitter=True, flags=GI)
     ref, robust = oracle_gi_passes(sc, 8, 2, seed=11, jitter=True)
     check_colour(img, ref, robust)
 
@@ -113,3 +112,29 @@ def test_gi_with_the_radiance_cache_is_refused():
     assert ei.value.status == rtb.RT_ERR_UNSUPPORTED
     rtb.rt_nrc_destroy(nrc)
     scene.close()
+
+
+@pytest.mark.parametrize("flags", [0, GI], ids=["direct", "gi"])
+def test_full_size_lit_terrain_sampled_parity(flags):
+    """The benchmark's progressive-pass workload at full size (1920x1080,
+    depth 5, 4 point + 2 area lights + a glowing sphere, jittered 4x4
+    strata), one pass, checked on sampled pixels against the oracle's same
+    pass (its samples are keyed by the pixel, so any pixel can be rendered
+    alone)."""
+    sc = S.scene_terrain_lit()
+    W, H, D = sc.width, sc.height, sc.max_depth
+    scene = rtb.Scene(sc).build()
+    acc = torch.empty(W * H * 3, device="cuda")
+    # pass 0 overwrites the running mean (a later pass would blend into it)
+    st = rtb.rt_render_pass(scene.handle, sc.camera, W, H, D, rtb.make_pass(0, 7, 4, True), acc,
+                            rtb.make_options(background=sc.background, flags=flags), stats=True)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    assert st["primary"] == W * H and st["secondary"] > 0
+    img = acc.view(-1, 3).double().cpu().numpy()
+    scene.close()
+    orc = O.OracleScene.from_scene(sc)
+    orc.set_diffuse_bounce(flags != 0)
+    orc.set_pass(7, 0, 4, True)
+    px = np.sort(np.random.default_rng(21).choice(W * H, 400, replace=False))
+    ref = orc.render(sc.camera, W, H, D, mode="bvh", pixels=px)
+    check_colour(img[px], ref["rgb"], ref["robust"])
