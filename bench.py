@@ -37,6 +37,31 @@ UNIT = "Mrays/s"
 OPS_BOX = 14      # ordered slab test of one child box: 6 FFMA + 6 min/max + 1 widening FMUL + 1 compare
 OPS_TRI = 30      # Moller-Trumbore
 BYTES_NODE = 128
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one frame's
+# launches of each kernel class, from one ncu capture of the bench workload
+# (the summaries are in profiles/).  They stand only for the kernel sources
+# they were taken on: any change to those files reports null instead.
+PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
+                    "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
+PROFILED_SHA = "b66b503b74243e90"
+PROFILED_TRAFFIC = {
+    0: (24_632_576 + 124_867_584 + 10_513_152,
+        "k_trace<1,0,0> + k_paths<0,0>: profiles/k_trace_primary_terrain1080p.md, profiles/k_paths_terrain1080p.md"),
+    1: (179_974_400 + 7_628_288, "k_shadow<0>: profiles/k_shadow_terrain1080p.md"),
+}
+
+
+def profiled_traffic(cls):
+    """(bytes per frame, source) of a kernel class while its sources match the capture, else (None, why)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in PROFILED_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != PROFILED_SHA:
+        return None, "kernel sources changed since the ncu capture"
+    return PROFILED_TRAFFIC[cls]
 BYTES_TRI = 48
 
 
@@ -422,8 +447,8 @@ def main():
         rtb.rt_bvh_build(h)
         rtb.rt_render_host(h, sc.camera, W, H, D, out_pin, opts)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_ms = sorted(e2e_ms)[len(e2e_ms) // 2] if e2e_ms else float("nan")
-    e2e_value = world * rays / (e2e_ms * 1e3)
+    e2e_ms = sorted(e2e_ms)[len(e2e_ms) // 2] if e2e_ms else None
+    e2e_value = world * rays / (e2e_ms * 1e3) if e2e_ms else None
 
     # roofline of the dominant kernel class
     pk, pk_kind = peaks()
@@ -434,6 +459,7 @@ def main():
     cls, kms = (0, tr) if tr >= sh else (1, sh)
     ops = work["box_tests"][cls] * OPS_BOX + work["prim_tests"][cls] * OPS_TRI
     achieved = ops / (kms * 1e-3) / 1e12
+    traffic, traffic_src = profiled_traffic(cls)
     launches_per_step = info["build_launches"] + 1 + 2 + st["launches"] + 2
 
     # radiance cache: online training frames, then timed training frames;
@@ -545,8 +571,8 @@ def main():
                        "bvh": {k: info[k] for k in ("n_nodes", "max_depth", "sah_cost", "sah_cost_lbvh")}},
             "roofline": {"bound": "alu", "kernel": "closest-hit+shade" if cls == 0 else "any-hit shadow",
                          "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
-                         "traffic": None, "peak_source": f"148 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
-                                                         f"({pk_kind} clock)",
+                         "traffic": traffic, "traffic_unit": "bytes per frame", "traffic_source": traffic_src,
+                         "peak_source": f"148 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} clock)",
                          "kernel_ms": kms, "alg_ops": ops},
             "stage_ms": {"trace": tr, "shadow": sh, "step": ms,
                          "note": "sums of per-kernel times; shadow kernels overlap the next depth's trace"},
