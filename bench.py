@@ -74,34 +74,53 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region:
+    the sampler runs every 20 ms and is running (its first sample is in)
+    before the region starts; samples that arrive while the region runs are
+    its record.  A region shorter than one interval is represented by the
+    first sample after it (then "samples" is 0)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, gpu_index=0):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.lock = threading.Lock()
+        self.window = (0, 0)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.005)
         except (FileNotFoundError, OSError):
             self.proc = None
+        with self.lock:
+            self.window = (len(self.lines), len(self.lines))
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            with self.lock:
+                self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        with self.lock:
+            self.window = (self.window[0], len(self.lines))
         if self.proc:
+            if self.window[1] == self.window[0]:      # none inside: wait for the next one
+                t0 = time.perf_counter()
+                while len(self.lines) == self.window[1] and time.perf_counter() - t0 < 1.0:
+                    time.sleep(0.002)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -109,9 +128,12 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        a, b = self.window
+        inside = self.lines[a:b]
+        lines = inside if inside else self.lines[b:b + 1]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -124,9 +146,9 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(name)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(inside), "interval_ms": self.INTERVAL_MS}
 
 
 def cpu_oracle_sample(sc, seconds_hint=15.0):
@@ -416,17 +438,30 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # per-kernel stage times, on steps of their own: reading a step's stage
+    # events waits for it, which would leave the device idle while the host
+    # enqueues the next step
     trace_ms, shadow_ms = [], []
+    for k in range(args.steps):
+        flush.zero_()
+        step(opts_t)
+        _, a, b = rtb.rt_render_stage_times(h)
+        trace_ms.append(a)
+        shadow_ms.append(b)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    # the timed steps: enqueued back to back, so that the host stays ahead of
+    # the device; each is bracketed by its own event pair on the stream, and
+    # the L2 flush between steps lies outside the pairs
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.zero_()                       # L2 flush between steps (not timed)
             ev[k][0].record(stream)
-            step(opts_t)
+            step()
             ev[k][1].record(stream)
-            _, a, b = rtb.rt_render_stage_times(h)    # waits for this step's last kernel
-            trace_ms.append(a)
-            shadow_ms.append(b)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
