@@ -44,7 +44,7 @@ BYTES_NODE = 128
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "b66b503b74243e90"
+PROFILED_SHA = "7100f47b85aef08c"
 PROFILED_TRAFFIC = {
     0: (24_632_576 + 124_867_584 + 10_513_152,
         "k_trace<1,0,0> + k_paths<0,0>: profiles/k_trace_primary_terrain1080p.md, profiles/k_paths_terrain1080p.md"),

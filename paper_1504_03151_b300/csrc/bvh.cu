@@ -538,7 +538,41 @@ __device__ __forceinline__ ChildInfo child_info(int c, const unsigned* __restric
   return r;
 }
 
-__global__ void k_refit(int n, const unsigned* __restrict__ vals, const float4* __restrict__ aabb_lo,
+// The box, SAH costs and collapse decision of internal node `node`, from
+// its two children (both done).
+__device__ __forceinline__ void refit_node(int node, const unsigned* __restrict__ vals,
+                                           const float4* __restrict__ aabb_lo, const float4* __restrict__ aabb_hi,
+                                           const int* __restrict__ lch, const int* __restrict__ rch, int2 rg,
+                                           float4* node_lo, float4* node_hi, float* cost_lbvh) {
+  ChildInfo a = child_info(lch[node], vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
+  ChildInfo b = child_info(rch[node], vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
+  float4 lo = make_float4(fminf(a.lo.x, b.lo.x), fminf(a.lo.y, b.lo.y), fminf(a.lo.z, b.lo.z), 0.f);
+  float4 hi = make_float4(fmaxf(a.hi.x, b.hi.x), fmaxf(a.hi.y, b.hi.y), fmaxf(a.hi.z, b.hi.z), 0.f);
+  float A = area(lo, hi), Aa = area(a.lo, a.hi), Ab = area(b.lo, b.hi);
+  float ci, cl;
+  if (A > 0.f) {
+    ci = kCostTrav + (Aa * a.cost + Ab * b.cost) / A;
+    cl = kCostTrav + (Aa * a.cost_lbvh + Ab * b.cost_lbvh) / A;
+  } else {
+    ci = kCostTrav + a.cost + b.cost;
+    cl = kCostTrav + a.cost_lbvh + b.cost_lbvh;
+  }
+  int count = rg.y - rg.x + 1;
+  float leaf_cost = kCostIsect * (float)count;
+  int collapse = (count <= kMaxLeaf && leaf_cost <= ci) ? 1 : 0;
+  int height = collapse ? 0 : 1 + max(a.height, b.height);
+  lo.w = collapse ? leaf_cost : ci;
+  hi.w = __int_as_float(height | (collapse << 8));
+  node_lo[node] = lo;
+  node_hi[node] = hi;
+  cost_lbvh[node] = cl;
+}
+
+// Bottom-up from every leaf; the second thread to reach a node refits it
+// and climbs on.  A node over `cut` primitives is left alone (and its flag
+// untouched): the top rebuild replaces those nodes, and k_refit_upper
+// finishes them off the critical path for the plain LBVH's cost.
+__global__ void k_refit(int n, int cut, const unsigned* __restrict__ vals, const float4* __restrict__ aabb_lo,
                         const float4* __restrict__ aabb_hi, const int* __restrict__ lch, const int* __restrict__ rch,
                         const int* __restrict__ parent, const int* __restrict__ leaf_parent,
                         const int2* __restrict__ range, float4* node_lo, float4* node_hi, float* cost_lbvh, int* flags) {
@@ -548,34 +582,49 @@ __global__ void k_refit(int n, const unsigned* __restrict__ vals, const float4* 
   // a radix tree has at most n-1 ancestors above a leaf; the bound and the
   // index check only guard against a malformed tree
   for (int it = 0; node >= 0 && node < n - 1 && it < n; ++it) {
+    const int2 rg = range[node];
+    if (rg.y - rg.x + 1 > cut) return;
     __threadfence();
     if (atomicAdd(&flags[node], 1) == 0) return;
     __threadfence();
-    ChildInfo a = child_info(lch[node], vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
-    ChildInfo b = child_info(rch[node], vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
-    float4 lo = make_float4(fminf(a.lo.x, b.lo.x), fminf(a.lo.y, b.lo.y), fminf(a.lo.z, b.lo.z), 0.f);
-    float4 hi = make_float4(fmaxf(a.hi.x, b.hi.x), fmaxf(a.hi.y, b.hi.y), fmaxf(a.hi.z, b.hi.z), 0.f);
-    float A = area(lo, hi), Aa = area(a.lo, a.hi), Ab = area(b.lo, b.hi);
-    float ci, cl;
-    if (A > 0.f) {
-      ci = kCostTrav + (Aa * a.cost + Ab * b.cost) / A;
-      cl = kCostTrav + (Aa * a.cost_lbvh + Ab * b.cost_lbvh) / A;
-    } else {
-      ci = kCostTrav + a.cost + b.cost;
-      cl = kCostTrav + a.cost_lbvh + b.cost_lbvh;
-    }
-    int2 rg = range[node];
-    int count = rg.y - rg.x + 1;
-    float leaf_cost = kCostIsect * (float)count;
-    int collapse = (count <= kMaxLeaf && leaf_cost <= ci) ? 1 : 0;
-    int height = collapse ? 0 : 1 + max(a.height, b.height);
-    lo.w = collapse ? leaf_cost : ci;
-    hi.w = __int_as_float(height | (collapse << 8));
-    node_lo[node] = lo;
-    node_hi[node] = hi;
-    cost_lbvh[node] = cl;
+    refit_node(node, vals, aabb_lo, aabb_hi, lch, rch, rg, node_lo, node_hi, cost_lbvh);
     node = parent[node];
   }
+}
+
+// The nodes over `cut` primitives, after k_refit: a node with both children
+// at or under the cut is refitted by its own thread, one with a single such
+// child counts that child's arrival; then the climb goes on as in k_refit.
+__global__ void k_refit_upper(int n, int cut, const unsigned* __restrict__ vals, const float4* __restrict__ aabb_lo,
+                              const float4* __restrict__ aabb_hi, const int* __restrict__ lch,
+                              const int* __restrict__ rch, const int* __restrict__ parent,
+                              const int2* __restrict__ range, float4* node_lo, float4* node_hi, float* cost_lbvh,
+                              int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int2 rg = range[i];
+  if (rg.y - rg.x + 1 <= cut) return;
+  const int l = lch[i], r = rch[i];
+  const bool bl = l < 0 || range[l].y - range[l].x + 1 <= cut;
+  const bool br = r < 0 || range[r].y - range[r].x + 1 <= cut;
+  if (!bl && !br) return;                                   // both children arrive by climbing
+  if (bl != br && atomicAdd(&flags[i], 1) == 0) return;     // the other one will
+  __threadfence();
+  int node = i;
+  for (int it = 0; it < n; ++it) {
+    refit_node(node, vals, aabb_lo, aabb_hi, lch, rch, rg, node_lo, node_hi, cost_lbvh);
+    node = parent[node];
+    if (node < 0 || node >= n - 1) return;
+    rg = range[node];
+    __threadfence();
+    if (atomicAdd(&flags[node], 1) == 0) return;
+    __threadfence();
+  }
+}
+
+// The plain LBVH's SAH cost, once its root is refitted.
+__global__ void k_info_sah_lbvh(const float* __restrict__ cost_lbvh, BuildInfo* info) {
+  info->sah_lbvh = cost_lbvh[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -1632,6 +1681,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
   BuildScratch b;
   rt_status rs = carve(s, n, b);
   if (rs) return rs;
+  s->lbvh_cut = 0;
   // nodes: LBVH internal nodes [0, n-1) + top nodes [n-1, 2n-2)
   size_t slots = (size_t)std::max(2 * n, 2);
   if ((rs = ensure(s->nodes, slots * 64))) return rs;
@@ -1658,17 +1708,21 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
   cudaMemsetAsync(b.parent, 0xff, (size_t)n * 4, st);
   cudaMemsetAsync(b.leaf_parent, 0xff, (size_t)n * 4, st);
   k_hierarchy<<<grid, tb, 0, st>>>(b.keys0, n, b.lch, b.rch, b.parent, b.leaf_parent, b.range);
-  k_refit<<<grid, tb, 0, st>>>(n, b.vals0, b.aabb_lo, b.aabb_hi, b.lch, b.rch, b.parent, b.leaf_parent, b.range,
-                               b.node_lo, b.node_hi, b.cost_lbvh, b.flags);
+  int cmax = cluster_max_for(n);
+  const bool top = n > 2 * cmax;   // the top levels are rebuilt over clusters of <= cmax primitives
+  k_refit<<<grid, tb, 0, st>>>(n, top ? cmax : n, b.vals0, b.aabb_lo, b.aabb_hi, b.lch, b.rch, b.parent,
+                               b.leaf_parent, b.range, b.node_lo, b.node_hi, b.cost_lbvh, b.flags);
+  // the LBVH above the clusters only feeds the plain LBVH's cost, which
+  // rt_bvh_get_info computes when asked (upper_refit)
+  s->lbvh_cut = top ? cmax : 0;
   k_layout<<<grid, tb, 0, st>>>(n, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo, b.aabb_hi,
                                 nodes);
   k_gather_prims<<<(3 * n + 255) / 256, 256, 0, st>>>(b.vals0, n, (const float4*)s->prims_id.p,
                                                       (float4*)s->prims_leaf.p);
-  k_info_lbvh<<<1, 1, 0, st>>>(b.node_lo, b.node_hi, b.cost_lbvh, b.info, 0);
-  L += 8;
+  if (!top) k_info_lbvh<<<1, 1, 0, st>>>(b.node_lo, b.node_hi, b.cost_lbvh, b.info, 0);
+  L += top ? 7 : 8;
   s->root = 0;
-  int cmax = cluster_max_for(n);
-  if (n > 2 * cmax) {
+  if (top) {
     // top levels: binned SAH over the Morton clusters
     int top_base = n - 1;
     int* n_clusters_dev = b.seg_count + kTopMaxLevels + 1;
@@ -1746,6 +1800,19 @@ rt_status rt_bvh_get_info(rt_scene* s, rt_bvh_info* info, void* stream) {
   BuildScratch b;
   rt_status rs = carve(s, (int)s->n_prims, b);
   if (rs) return rs;
+  if (s->lbvh_cut > 0) {
+    // the plain LBVH's cost: refit its nodes above the clusters (once per build;
+    // the build's scratch is intact until the next build)
+    const int n = (int)s->n_prims;
+    k_refit_upper<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, s->lbvh_cut, b.vals0, b.aabb_lo, b.aabb_hi,
+                                                                      b.lch, b.rch, b.parent, b.range, b.node_lo,
+                                                                      b.node_hi, b.cost_lbvh, b.flags);
+    k_info_sah_lbvh<<<1, 1, 0, (cudaStream_t)stream>>>(b.cost_lbvh, b.info);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_error(e, "rt_bvh_get_info: LBVH cost");
+    s->lbvh_cut = 0;
+  }
   BuildInfo bi;
   e = cudaMemcpy(&bi, b.info, sizeof(bi), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_error(e, "rt_bvh_get_info");

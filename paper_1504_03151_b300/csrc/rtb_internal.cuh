@@ -135,6 +135,7 @@ struct rt_scene {
   rtb::Buf build_info;           // device-side build results (BuildInfo)
   float last_build_ms = 0.f;
   int last_build_launches = 0;
+  int lbvh_cut = 0;              // > 0: the LBVH nodes over this many primitives still await their refit
   // render
   rtb::Buf rayq[2], shadowq[2], counters, fb_host_stage;
   cudaStream_t side = nullptr;   // runs each depth's shadow kernel beside the next depth's trace
