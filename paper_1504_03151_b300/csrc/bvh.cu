@@ -1427,10 +1427,13 @@ __device__ __forceinline__ float half_area(const float* lo, const float* hi) {
   return dx * dy + dy * dz + dz * dx;
 }
 
-__global__ void __launch_bounds__(256) k_collapse4(const float4* __restrict__ bin, int n_bin,
-                                                   float4* __restrict__ out) {
+// Slots past the LBVH's n_lbvh internal nodes are top nodes; only the first
+// *top_count of them exist (none without a top rebuild: top_count NULL).
+__global__ void __launch_bounds__(256) k_collapse4(const float4* __restrict__ bin, int n_bin, int n_lbvh,
+                                                   const int* __restrict__ top_count, float4* __restrict__ out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= n_bin) return;
+  if (x >= n_lbvh && (top_count == nullptr || x - n_lbvh >= __ldg(top_count))) return;   // an unused slot
   float lo[4][3], hi[4][3];
   int link[4];
   int ns = 2;
@@ -1659,14 +1662,16 @@ static int cluster_max_for(int n) {
 
 // The 4-wide traversal tree: one 4-wide node per binary node slot, at the
 // same index (the root is the binary root).
-static rt_status collapse4(rt_scene* s, const BuildScratch& b, const float4* nodes, int n_bin, cudaStream_t st) {
+static rt_status collapse4(rt_scene* s, const BuildScratch& b, const float4* nodes, int n_bin, bool top,
+                           cudaStream_t st) {
   rt_status rs = ensure(s->nodes4, (size_t)n_bin * 128);
   if (rs) return rs;
   s->n_nodes4 = n_bin;
   if (s->n_prims == 1) {
     k_wide_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, (float4*)s->nodes4.p);
   } else {
-    k_collapse4<<<(n_bin + 255) / 256, 256, 0, st>>>(nodes, n_bin, (float4*)s->nodes4.p);
+    k_collapse4<<<(n_bin + 255) / 256, 256, 0, st>>>(nodes, n_bin, (int)s->n_prims - 1, top ? b.top_count : nullptr,
+                                                     (float4*)s->nodes4.p);
   }
   return cuda_error(cudaGetLastError(), "rt_bvh_build: 4-wide tree");
 }
@@ -1697,7 +1702,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     k_layout_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, nodes, b.info);
     k_gather_prims<<<1, 32, 0, st>>>(b.vals0, 1, (const float4*)s->prims_id.p, (float4*)s->prims_leaf.p);
     s->root = 0;
-    if ((rs = collapse4(s, b, nodes, (int)slots, st))) return rs;
+    if ((rs = collapse4(s, b, nodes, (int)slots, false, st))) return rs;
     s->last_build_launches = L + 4;
     s->built = true;
     return cuda_error(cudaGetLastError(), "rt_bvh_build");
@@ -1771,7 +1776,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     L += 5 + kTopMaxLevels;
     s->root = top_base;
   }
-  if ((rs = collapse4(s, b, nodes, (int)slots, st))) return rs;
+  if ((rs = collapse4(s, b, nodes, (int)slots, top, st))) return rs;
   L += 1;
   s->last_build_launches = L;
   s->built = true;
