@@ -117,7 +117,7 @@ __global__ void k_prim_bounds(const float4* __restrict__ prims, int n, float4* _
     cy = Cy = 0.5f * (lo.y + hi.y);
     cz = Cz = 0.5f * (lo.z + hi.z);
   }
-  // warp reduce, then one atomic per warp
+  // warp reduce, then block reduce (blockDim.x <= 256), then one atomic per block
   for (int o = 16; o > 0; o >>= 1) {
     cx = fminf(cx, __shfl_xor_sync(0xffffffffu, cx, o));
     cy = fminf(cy, __shfl_xor_sync(0xffffffffu, cy, o));
@@ -126,13 +126,25 @@ __global__ void k_prim_bounds(const float4* __restrict__ prims, int n, float4* _
     Cy = fmaxf(Cy, __shfl_xor_sync(0xffffffffu, Cy, o));
     Cz = fmaxf(Cz, __shfl_xor_sync(0xffffffffu, Cz, o));
   }
-  if ((threadIdx.x & 31) == 0 && cx <= Cx) {
-    atomicMin(&cb[0], f2o(cx));
-    atomicMin(&cb[1], f2o(cy));
-    atomicMin(&cb[2], f2o(cz));
-    atomicMax(&cb[3], f2o(Cx));
-    atomicMax(&cb[4], f2o(Cy));
-    atomicMax(&cb[5], f2o(Cz));
+  __shared__ float s_b[8][6];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+    s_b[w][0] = cx;
+    s_b[w][1] = cy;
+    s_b[w][2] = cz;
+    s_b[w][3] = Cx;
+    s_b[w][4] = Cy;
+    s_b[w][5] = Cz;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x;
+    float v = s_b[0][k];
+    for (int j = 1; j < nw; ++j) v = k < 3 ? fminf(v, s_b[j][k]) : fmaxf(v, s_b[j][k]);
+    if (k < 3 ? v < INFINITY : v > -INFINITY) {
+      if (k < 3) atomicMin(&cb[k], f2o(v));
+      else atomicMax(&cb[k], f2o(v));
+    }
   }
 }
 
