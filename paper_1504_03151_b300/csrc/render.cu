@@ -305,6 +305,7 @@ __device__ __forceinline__ void count_ray(Counters* ctr, int cls, int depth, uns
 }
 
 constexpr int kWarpPending = 64;   // pending children per warp (shared memory, 12 KB a block)
+constexpr int kWavefrontDepths = 1;   // frames without the radiance cache: depths 0..1 as wavefronts
 
 
 template <bool kCount, bool kPass>
@@ -833,11 +834,14 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   // the diffuse bounce nearly every hit has a child, every depth is wide,
   // and wavefronts are faster at each of them (measured on the 1080p terrain:
   // 2.2 ms a pass against 3.5 ms depth first); the radiance cache never bounces.
+  // Without the cache, depth 1 (tens of thousands of rays) is a wavefront too
+  // and the depth-first kernel takes the tail from depth 2 (measured: 1.37
+  // against 1.38-1.40 ms a step; a wavefront depth 2 as well was slower).
   if (fp.ps.bounce) per_depth = true;
-  int last = per_depth ? D : 0;
+  int last = per_depth ? D : (T < 0 ? std::min(D, kWavefrontDepths) : 0);
   bool cache_in_paths = !per_depth && T >= 1;
   if (per_depth || T == 0) fp.path_depth0 = T >= 0 ? T + 1 : 1;
-  else fp.path_depth0 = 1;
+  else fp.path_depth0 = last + 1;
   if (cache_in_paths && fp.nrc_depth >= 0) fp.prev_hits = nrc_prev_hits(nrc);
   for (int depth = 0; depth <= last; ++depth) {
     // trace(depth) fills the shadow buffer that shadow(depth - 2) reads
