@@ -44,11 +44,11 @@ BYTES_NODE = 128
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "7100f47b85aef08c"
+PROFILED_SHA = "f0396ef885311bac"
 PROFILED_TRAFFIC = {
-    0: (24_632_576 + 124_867_584 + 10_513_152,
-        "k_trace<1,0,0> + k_paths<0,0>: profiles/k_trace_primary_terrain1080p.md, profiles/k_paths_terrain1080p.md"),
-    1: (179_974_400 + 7_628_288, "k_shadow<0>: profiles/k_shadow_terrain1080p.md"),
+    0: (24_626_688 + 122_784_256 + 5_496_064 + 768 + 7_376_384,
+        "k_trace<1,0,0> + k_trace<0,0,0> (depth 1) + k_paths<0,0> (depths 2-5): profiles/launches_terrain1080p_d5.md"),
+    1: (180_145_920 + 4_689_664 + 5_758_464, "k_shadow<0> (depths 0 and 1): profiles/launches_terrain1080p_d5.md"),
 }
 
 
@@ -62,6 +62,8 @@ def profiled_traffic(cls):
     if h.hexdigest()[:16] != PROFILED_SHA:
         return None, "kernel sources changed since the ncu capture"
     return PROFILED_TRAFFIC[cls]
+
+
 BYTES_TRI = 48
 
 
