@@ -310,7 +310,7 @@ __device__ __forceinline__ void count_ray(Counters* ctr, int cls, int depth, uns
 }
 
 constexpr int kWarpPending = 64;   // pending children per warp (shared memory, 12 KB a block)
-constexpr int kWavefrontDepths = 1;   // frames without the radiance cache: depths 0..1 as wavefronts
+constexpr int kWavefrontDepths = 1;   // depths 0..1 run as wavefronts (the cache, if any, lies deeper)
 
 
 template <bool kCount, bool kPass>
@@ -839,11 +839,12 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   // the diffuse bounce nearly every hit has a child, every depth is wide,
   // and wavefronts are faster at each of them (measured on the 1080p terrain:
   // 2.2 ms a pass against 3.5 ms depth first); the radiance cache never bounces.
-  // Without the cache, depth 1 (tens of thousands of rays) is a wavefront too
-  // and the depth-first kernel takes the tail from depth 2 (measured: 1.37
-  // against 1.38-1.40 ms a step; a wavefront depth 2 as well was slower).
+  // Depth 1 (tens of thousands of rays) is a wavefront too and the
+  // depth-first kernel takes the tail from depth 2 (measured: 1.37 against
+  // 1.38-1.40 ms a step; a wavefront depth 2 as well was slower), unless the
+  // cache sits at depth 0 or 1.
   if (fp.ps.bounce) per_depth = true;
-  int last = per_depth ? D : (T < 0 ? std::min(D, kWavefrontDepths) : 0);
+  int last = per_depth ? D : (T < 0 || T > kWavefrontDepths ? std::min(D, kWavefrontDepths) : 0);
   bool cache_in_paths = !per_depth && T >= 1;
   if (per_depth || T == 0) fp.path_depth0 = T >= 0 ? T + 1 : 1;
   else fp.path_depth0 = last + 1;
