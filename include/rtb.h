@@ -274,6 +274,17 @@ rt_status rt_render_stage_times(rt_scene* s, float* ms_total, float* ms_trace, f
 rt_status rt_render_host(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
                          float* out_rgb_host, const rt_render_options* opt, void* stream);
 
+/* rt_render_host for a stream of frames: returns once the frame and its
+ * copy are queued.  The frame renders on `stream` into one of two
+ * scene-owned device images (alternating from call to call; a frame waits
+ * for the copy that last used its image) and is copied to out_host
+ * (H*W*3 float32; pinned memory for an asynchronous copy) on a copy stream
+ * of the scene, so that the copy overlaps the next frame's work.  out_host
+ * is complete, and may be reused, once rt_scene_sync(s, stream) has
+ * returned, which also waits for the copy stream.  Errors as rt_render_ex. */
+rt_status rt_render_host_async(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
+                               float* out_host, const rt_render_options* options, void* stream);
+
 /* The primary rays rt_render traces (device arrays, H*W*3 float each,
  * pixel-major): the same device function generates them. */
 rt_status rt_camera_rays(const rt_camera* cam, int width, int height, float* o_device,
@@ -409,7 +420,8 @@ rt_status rt_batch_render(rt_batch* b, const rt_tune* tune, rt_render_stats* sta
 rt_status rt_batch_autotune(rt_batch* b, rt_tune* best, float* best_ms, void* stream);
 rt_status rt_batch_destroy(rt_batch* b);
 
-/* Waits for `stream` and returns (and clears) the latched kernel error. */
+/* Waits for `stream` (and for the host copies of rt_render_host_async)
+ * and returns (and clears) the latched kernel error. */
 rt_status rt_scene_sync(rt_scene* s, void* stream);
 
 rt_status rt_scene_destroy(rt_scene* s);

@@ -17,7 +17,7 @@ import numpy as np
 __all__ = [
     "RtError", "lib", "rt_abi_version", "rt_last_error", "rt_render_options_default",
     "rt_scene_create", "rt_scene_update", "rt_bvh_build", "rt_bvh_get_info", "rt_bvh_export", "rt_bvh_export_wide",
-    "rt_render", "rt_render_ex", "rt_render_host", "rt_camera_rays", "rt_trace_closest",
+    "rt_render", "rt_render_ex", "rt_render_host", "rt_render_host_async", "rt_camera_rays", "rt_trace_closest",
     "rt_trace_any", "rt_scene_sync", "rt_scene_destroy", "rt_render_stage_times", "Scene",
     "rt_nrc_config_default", "rt_nrc_create", "rt_nrc_destroy", "rt_nrc_get_params", "rt_nrc_set_params",
     "rt_nrc_get_grads", "rt_nrc_infer", "rt_nrc_train_step", "rt_render_nrc",
@@ -163,6 +163,7 @@ def lib():
             "rt_batch_destroy": (I, [P]),
             "rt_scene_set_area_lights": (I, [P, P, S]),
             "rt_render_pass": (I, [P, P, I, I, I, P, P, P, P, P]),
+            "rt_render_host_async": (I, [P, P, I, I, I, P, P, P]),
             "rt_scene_destroy": (I, [P]),
         }
         for name, (res, args) in sigs.items():
@@ -335,6 +336,13 @@ def rt_render_host(scene, camera, width, height, max_depth, out_host, options=No
     cam = make_camera(camera)
     _check(lib().rt_render_host(scene, ctypes.byref(cam), width, height, max_depth, _hptr(out_host),
                                 ctypes.byref(options) if options is not None else None, _stream(stream)))
+
+
+def rt_render_host_async(scene, camera, width, height, max_depth, out_host, options=None, stream=None):
+    """Queues a frame and its copy to the pinned host buffer out_host (complete after rt_scene_sync)."""
+    cam = make_camera(camera)
+    _check(lib().rt_render_host_async(scene, ctypes.byref(cam), width, height, max_depth, _hptr(out_host),
+                                      ctypes.byref(options) if options is not None else None, _stream(stream)))
 
 
 def rt_render_stage_times(scene):

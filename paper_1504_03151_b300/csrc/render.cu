@@ -972,6 +972,42 @@ rt_status rt_render_host(rt_scene* s, const rt_camera* cam, int width, int heigh
   return RT_OK;
 }
 
+static rt_status ensure_copy_stream(rt_scene* s) {
+  if (s->copy_stream) return RT_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+  for (int k = 0; e == cudaSuccess && k < 2; ++k) {
+    e = cudaEventCreateWithFlags(&s->ev_rendered[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_copied[k], cudaEventDisableTiming);
+  }
+  return cuda_error(e, "copy stream");
+}
+
+rt_status rt_render_host_async(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
+                               float* out_host, const rt_render_options* opt, void* stream) {
+  if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_render_host_async: scene is NULL");
+  if (!out_host) return set_error(RT_ERR_INVALID_ARG, "rt_render_host_async: out_rgb_host is NULL");
+  if (width < 1 || height < 1) return set_error(RT_ERR_INVALID_ARG, "rt_render_host_async: bad size");
+  const size_t bytes = (size_t)width * height * 3 * sizeof(float);
+  rt_status rs = ensure_copy_stream(s);
+  if (rs) return rs;
+  const int k = s->stage_next;
+  if ((rs = ensure(s->fb_stage[k], bytes))) return rs;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the image this frame renders into was copied out two calls ago: wait for that copy
+  cudaError_t e = cudaStreamWaitEvent(st, s->ev_copied[k], 0);
+  if (e != cudaSuccess) return cuda_error(e, "rt_render_host_async");
+  rs = render_impl(s, cam, width, height, max_depth, (float*)s->fb_stage[k].p, opt, nullptr, nullptr, nullptr, st);
+  if (rs) return rs;
+  e = cudaEventRecord(s->ev_rendered[k], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, s->ev_rendered[k], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_host, s->fb_stage[k].p, bytes, cudaMemcpyDeviceToHost, s->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_copied[k], s->copy_stream);
+  if (e != cudaSuccess) return cuda_error(e, "rt_render_host_async copy");
+  s->stage_next = k ^ 1;
+  return RT_OK;
+}
+
 // pass k folded into the running mean: accum += (image - accum) / (k + 1)
 __global__ void k_accumulate(float* __restrict__ accum, const float* __restrict__ img, size_t n, int k) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1071,6 +1107,15 @@ rt_status rt_scene_destroy(rt_scene* s) {
   }
   release(s->counters);
   release(s->fb_host_stage);
+  release(s->fb_stage[0]);
+  release(s->fb_stage[1]);
+  if (s->copy_stream) {
+    cudaStreamDestroy(s->copy_stream);
+    for (int k = 0; k < 2; ++k) {
+      cudaEventDestroy(s->ev_rendered[k]);
+      cudaEventDestroy(s->ev_copied[k]);
+    }
+  }
   for (auto e : s->tev) cudaEventDestroy(e);
   if (s->status) cudaFree(s->status);
   delete s;

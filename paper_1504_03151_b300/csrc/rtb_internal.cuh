@@ -138,6 +138,12 @@ struct rt_scene {
   int lbvh_cut = 0;              // > 0: the LBVH nodes over this many primitives still await their refit
   // render
   rtb::Buf rayq[2], shadowq[2], counters, fb_host_stage;
+  // rt_render_host_async: two device images, each copied to the host on the
+  // copy stream while the next frame renders into the other
+  rtb::Buf fb_stage[2];
+  int stage_next = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_rendered[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
   cudaStream_t side = nullptr;   // runs each depth's shadow kernel beside the next depth's trace
   cudaEvent_t ev_traced[RT_MAX_DEPTH + 1], ev_shadowed[RT_MAX_DEPTH + 1];
   int64_t ray_cap = 0, shadow_cap = 0;

@@ -315,6 +315,8 @@ rt_status rt_scene_sync(rt_scene* s, void* stream) {
   if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_scene_sync: scene is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaStreamSynchronize(st);
+  // and the host copies of rt_render_host_async, which follow the stream's frames
+  if (e == cudaSuccess && s->copy_stream) e = cudaStreamSynchronize(s->copy_stream);
   if (e != cudaSuccess) return cuda_error(e, "rt_scene_sync");
   unsigned flags = 0;
   e = cudaMemcpy(&flags, s->status, sizeof(unsigned), cudaMemcpyDeviceToHost);

@@ -410,6 +410,29 @@ def test_scene_update_then_rebuild():
     scene.close()
 
 
+def test_render_host_async_frames_match_sync():
+    """Frames queued back to back through the two device images, each copied
+    to its own pinned buffer; a third frame reuses the first image (it waits
+    for that image's copy).  Every image equals rt_render_host's."""
+    sc = small_terrain(seed=7)
+    W, H, D = sc.width, sc.height, sc.max_depth
+    scene = rtb.Scene(sc).build()
+    opts = rtb.make_options(background=sc.background)
+    cams = [sc.camera, S.camera((10.0, 8.0, 20.0), (0.0, 0.0, 0.0)), S.camera((-5.0, 6.0, 15.0), (0.0, 1.0, 0.0))]
+    refs = []
+    for c in cams:
+        ref = np.zeros(W * H * 3, np.float32)
+        rtb.rt_render_host(scene.handle, c, W, H, D, ref, opts)
+        refs.append(ref)
+    outs = [torch.full((W * H * 3,), float("nan")).pin_memory() for _ in range(3)]
+    for c, o in zip(cams, outs):
+        rtb.rt_render_host_async(scene.handle, c, W, H, D, o, opts)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    for o, ref in zip(outs, refs):
+        np.testing.assert_allclose(o.numpy(), ref, atol=1e-5, rtol=0)   # only atomic ordering differs
+    scene.close()
+
+
 def test_scene_update_with_a_bad_material_is_reported():
     """rt_scene_update does not validate; a material index out of range is
     replaced by material 0 on the device and reported by the next sync."""
