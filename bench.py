@@ -44,7 +44,7 @@ BYTES_NODE = 128
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "2222874de74dbe88"
+PROFILED_SHA = "f700c75a53bb77d8"
 PROFILED_TRAFFIC = {
     0: (24_626_688 + 122_784_256 + 5_496_064 + 768 + 7_376_384,
         "k_trace<1,0,0> + k_trace<0,0,0> (depth 1) + k_paths<0,0> (depths 2-5): profiles/launches_terrain1080p_d5.md"),
