@@ -249,6 +249,18 @@ constexpr int kTsMisc = 216064;  // mbarrier, tmem slot, flags, loss
 constexpr int kTrainSmem = kTsMisc + 64;
 
 // Lane of row m of an M = 64 accumulator: 16 rows in each 32-lane quarter.
+// One CTA's gradient row: the kNP parameter gradients (oracle layout), then
+// the loss, padded to whole float4.
+constexpr int kGPRow = (kNP + 1 + 3) / 4 * 4;
+
+__device__ __forceinline__ void store16(float* dst, const float* v) {   // dst 16-byte aligned
+  float4* d = (float4*)dst;
+  d[0] = make_float4(v[0], v[1], v[2], v[3]);
+  d[1] = make_float4(v[4], v[5], v[6], v[7]);
+  d[2] = make_float4(v[8], v[9], v[10], v[11]);
+  d[3] = make_float4(v[12], v[13], v[14], v[15]);
+}
+
 __device__ __forceinline__ int m64_row_of_lane(int lane) { return (lane & 31) < 16 ? (lane >> 5) * 16 + (lane & 31) : -1; }
 
 __device__ __forceinline__ void store_transposed(uint8_t* tileT, int col, int rows, const float* v) {
@@ -264,7 +276,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, const float4* __restrict__ recs,
                                                                 const float* __restrict__ targets,
                                                                 const unsigned* __restrict__ count, unsigned cap,
-                                                                float* __restrict__ grad, unsigned* status) {
+                                                                float* __restrict__ gpart, unsigned* status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint64_t* mbar = (uint64_t*)(sm + kTsMisc);
   uint32_t* tslot = (uint32_t*)(sm + kTsMisc + 8);
@@ -454,36 +466,39 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
     first = false;
   }
 done:
-  // weight gradients of this CTA: tensor memory -> global (atomics)
-  if (!aborted && !first) {
+  // this CTA's gradients and loss: its own row of gpart (plain stores; the
+  // Adam kernel sums the rows in a fixed order).  A CTA without a tile, or
+  // one whose wait timed out, writes zeros.
+  float* gp = gpart + (size_t)blockIdx.x * kGPRow;
+  const bool have = !aborted && !first;
+  if (have) {
     tc::fence_after_sync();
     int m = m64_row_of_lane(tid);
     float v[16];
     // dW0 (M = 64 x N = 96)
     for (int c = 0; c < 6; ++c) {
       tc::ld16(lane_addr + kTcDW0 + 16 * c, v);
-      if (m >= 0)
-        for (int k = 0; k < 16; ++k) atomicAdd(&grad[off_w(0) + m * 96 + 16 * c + k], v[k]);
+      if (m >= 0) store16(gp + off_w(0) + m * 96 + 16 * c, v);
     }
     for (int l = 1; l <= 3; ++l)
       for (int c = 0; c < 4; ++c) {
         tc::ld16(lane_addr + kTcDW1 + 64 * (l - 1) + 16 * c, v);
-        if (m >= 0)
-          for (int k = 0; k < 16; ++k) atomicAdd(&grad[off_w(l) + m * 64 + 16 * c + k], v[k]);
+        if (m >= 0) store16(gp + off_w(l) + m * 64 + 16 * c, v);
       }
     // dW4^T [64 in][16 out] -> dW4 [3][64]
     tc::ld16(lane_addr + kTcDW4, v);
     if (m >= 0)
-      for (int k = 0; k < 3; ++k) atomicAdd(&grad[off_w(4) + k * 64 + m], v[k]);
+      for (int k = 0; k < 3; ++k) gp[off_w(4) + k * 64 + m] = v[k];
+  } else {
+    for (int i = tid; i < kNW; i += blockDim.x) gp[i] = 0.f;
   }
-  __syncthreads();
-  if (!first) {
-    for (int i = tid; i < 4 * 64; i += blockDim.x) atomicAdd(&grad[off_b(0) + i], db[i]);
-    if (tid < 3) atomicAdd(&grad[off_b(4) + tid], db[256 + tid]);
+  for (int i = tid; i < 4 * 64; i += blockDim.x) gp[off_b(0) + i] = have ? db[i] : 0.f;
+  if (tid < 3) gp[off_b(4) + tid] = have ? db[256 + tid] : 0.f;
+  {
     float ls = warp_sum(loss_acc);
     if (lane == 0) atomicAdd(s_loss, ls);
     __syncthreads();
-    if (tid == 0) atomicAdd(&grad[kNP], *s_loss);
+    if (tid == 0) gp[kNP] = have ? *s_loss : 0.f;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -496,12 +511,17 @@ done:
 // Adam on the FP32 master parameters, then the BF16 copies; clears the
 // gradient for the next step.
 // ---------------------------------------------------------------------------
-__global__ void k_nrc_adam(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                           float lr, float b1, float b2, float eps, float c1, float c2, int apply) {
+// The gradient (and, at kNP, the loss) is the sum of the training CTAs'
+// rows, in CTA order; it stays in g for inspection.
+__global__ void k_nrc_adam(float* __restrict__ w, const float* __restrict__ gpart, int n_part, float* __restrict__ g,
+                           float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2, float eps,
+                           float c1, float c2, int apply) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= kNP) return;
-  if (apply) {
-    float gi = g[i];
+  if (i > kNP) return;
+  float gi = 0.f;
+  for (int c = 0; c < n_part; ++c) gi += gpart[(size_t)c * kGPRow + i];
+  g[i] = gi;
+  if (i < kNP && apply) {
     float mi = b1 * m[i] + (1.f - b1) * gi;
     float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
@@ -551,11 +571,6 @@ void nrc_make_records(const float* pnv, const float* targets, int64_t n, float4*
   k_make_records<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pnv, n, recs, stride);
 }
 
-__global__ void k_zero(float* p, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = 0.f;
-}
-
 }  // namespace rtb
 
 // ---------------------------------------------------------------------------
@@ -567,6 +582,7 @@ struct rt_nrc {
   rt_nrc_config cfg;
   NrcDevice nd;
   Buf params, m, v, grad, packed;
+  Buf gpart;   // the training CTAs' gradient rows (sm_count x kGPRow floats)
   Buf infer_q, train_q, train_target, counters;   // frame queues (render integration)
   int64_t infer_cap = 0, train_cap = 0;
   int64_t step = 0;
@@ -615,14 +631,14 @@ rt_status nrc_train_launch(rt_nrc* r, const float4* recs, const float* targets, 
                            unsigned* status, cudaStream_t st) {
   rt_status rs = nrc_setup_kernels();
   if (rs) return rs;
-  k_zero<<<(kNP + 1 + 255) / 256, 256, 0, st>>>((float*)r->grad.p, kNP + 1);
-  k_nrc_train<<<r->sm_count, kTrainThreads, kTrainSmem, st>>>(r->nd, recs, targets, count, cap, (float*)r->grad.p,
+  if ((rs = ensure(r->gpart, (size_t)r->sm_count * kGPRow * sizeof(float)))) return rs;
+  k_nrc_train<<<r->sm_count, kTrainThreads, kTrainSmem, st>>>(r->nd, recs, targets, count, cap, (float*)r->gpart.p,
                                                                status);
   r->step++;
   float c1 = 1.f - powf(r->cfg.beta1, (float)r->step), c2 = 1.f - powf(r->cfg.beta2, (float)r->step);
-  k_nrc_adam<<<(kNP + 255) / 256, 256, 0, st>>>((float*)r->params.p, (float*)r->grad.p, (float*)r->m.p,
-                                                 (float*)r->v.p, r->cfg.lr, r->cfg.beta1, r->cfg.beta2, r->cfg.eps, c1,
-                                                 c2, 1);
+  k_nrc_adam<<<(kNP + 1 + 255) / 256, 256, 0, st>>>((float*)r->params.p, (const float*)r->gpart.p, r->sm_count,
+                                                     (float*)r->grad.p, (float*)r->m.p, (float*)r->v.p, r->cfg.lr,
+                                                     r->cfg.beta1, r->cfg.beta2, r->cfg.eps, c1, c2, 1);
   rs = nrc_pack(r, st);
   if (rs) return rs;
   return cuda_error(cudaGetLastError(), "nrc train");
@@ -746,6 +762,7 @@ rt_status rt_nrc_destroy(rt_nrc* r) {
   release(r->m);
   release(r->v);
   release(r->grad);
+  release(r->gpart);
   release(r->packed);
   release(r->infer_q);
   release(r->train_q);

@@ -900,7 +900,7 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     rs = nrc_train_launch(nrc, fp.train_q, fp.target, &fp.ctr->train_count, fp.train_cap, s->status, st);
     if (rs) return rs;
     if (timing) timing_end(s, slot, st);
-    launches += 4;
+    launches += 3;   // training, Adam, BF16 repack
   }
   if (timing) timing_end(s, frame_slot, st);
   cudaError_t e = cudaGetLastError();
