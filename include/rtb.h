@@ -100,9 +100,9 @@ enum {
   RT_FLAG_STAGE_TIMING = 1,   /* record per-stage CUDA events (stats.ms_*) */
   RT_FLAG_COUNT_WORK = 2,     /* count node visits / primitive tests (slower kernels) */
   RT_FLAG_NO_GRAPH = 4,       /* launch the kernels directly, no CUDA graph */
-  RT_FLAG_PER_DEPTH_WAVEFRONT = 8, /* queue every depth (default: depth 0 as a wavefront,
-                                      deeper rays depth-first, one thread per depth-1 subtree) */
-  RT_FLAG_DIFFUSE_BOUNCE = 16      /* Monte-Carlo GI (Eq. 8's hemisphere integral): below the
+  RT_FLAG_PER_DEPTH_WAVEFRONT = 8, /* queue every depth (default: depths 0 and 1 as wavefronts,
+                                      deeper rays depth first, one lane per path segment) */
+  RT_FLAG_DIFFUSE_BOUNCE = 16,     /* Monte-Carlo GI (Eq. 8's hemisphere integral): below the
                                       last depth, every non-dielectric hit with reflectivity < 1
                                       and some albedo > 0 also sends one cosine-weighted ray of
                                       weight pi (1 - reflectivity) albedo (f_r = albedo, as in the
@@ -111,6 +111,14 @@ enum {
                                       Only the Lambert lobe is integrated.  Such a frame runs
                                       every depth as a wavefront (as RT_FLAG_PER_DEPTH_WAVEFRONT).
                                       Not with the radiance cache (RT_ERR_UNSUPPORTED). */
+  RT_FLAG_DETERMINISTIC = 32       /* accumulate every pixel in 64-bit fixed point (units of
+                                      2^-32, contributions clamped to +-2^30) with integer
+                                      atomics, whose sum does not depend on the order the rays
+                                      finish in, and convert to float32 at the end of the frame:
+                                      the image is bit-identical from run to run.  Costs a
+                                      scene-owned buffer of 24 bytes a pixel and one conversion
+                                      pass.  Not with the radiance cache or a batch
+                                      (RT_ERR_UNSUPPORTED). */
 };
 
 typedef struct rt_render_options {

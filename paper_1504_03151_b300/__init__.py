@@ -44,6 +44,7 @@ RT_FLAG_COUNT_WORK = 2
 RT_FLAG_NO_GRAPH = 4
 RT_FLAG_PER_DEPTH_WAVEFRONT = 8
 RT_FLAG_DIFFUSE_BOUNCE = 16
+RT_FLAG_DETERMINISTIC = 32
 RT_MAX_DEPTH = 16
 
 

@@ -460,6 +460,8 @@ rt_status rt_batch_create(rt_scene* const* scenes, int32_t n, const rt_camera* c
   rt_render_options_default(&opt);
   if (options) opt = *options;
   if (!opt.use_bvh) return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: batches trace with the BVH (use_bvh)");
+  if (opt.flags & RT_FLAG_DETERMINISTIC)
+    return set_error(RT_ERR_UNSUPPORTED, "rt_batch_create: a batch does not take RT_FLAG_DETERMINISTIC");
   if (!std::isfinite(opt.background[0]) || !std::isfinite(opt.background[1]) || !std::isfinite(opt.background[2]) ||
       !std::isfinite(opt.eps_scale) || opt.eps_scale < 0.f || opt.traversal_cap < 0)
     return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: invalid options");

@@ -62,15 +62,39 @@ struct FrameParams {
   uint32_t seed;
   const unsigned* prev_hits;   // depth-first frames: cache hits of the previous frame (0: take all)
   PassInfo ps;                 // the pass: camera jitter and area-light samples
+  unsigned long long* fb_fixed;   // RT_FLAG_DETERMINISTIC: 3 per pixel, 64-bit fixed point (else NULL)
 };
 
+constexpr float kFixScale = 4294967296.f;   // 2^32 units of radiance
+constexpr float kFixMax = 1073741824.f;     // |contribution| clamp, 2^30: sums stay far inside 64 bits
+
+__device__ __forceinline__ unsigned long long to_fixed(float x) {
+  x = x == x ? fminf(fmaxf(x, -kFixMax), kFixMax) : 0.f;
+  return (unsigned long long)__float2ll_rn(x * kFixScale);   // two's complement: signed sums wrap right
+}
+
 // Adds radiance to a pixel, or to a training target when the ray belongs to
-// the radiance cache's training subset (pixel id < 0 -> slot ~pixel).
+// the radiance cache's training subset (pixel id < 0 -> slot ~pixel).  In a
+// deterministic frame the pixel sums are integers, whose order cannot change
+// them.
 __device__ __forceinline__ void add_fb(const FrameParams& fp, int pixel, f3 c) {
+  if (fp.fb_fixed != nullptr && pixel >= 0) {
+    unsigned long long* q = fp.fb_fixed + 3 * (size_t)pixel;
+    atomicAdd(q, to_fixed(c.x));
+    atomicAdd(q + 1, to_fixed(c.y));
+    atomicAdd(q + 2, to_fixed(c.z));
+    return;
+  }
   float* p = pixel >= 0 ? fp.fb + 3 * (size_t)pixel : fp.target + 3 * (size_t)(~pixel);
   atomicAdd(p, c.x);
   atomicAdd(p + 1, c.y);
   atomicAdd(p + 2, c.z);
+}
+
+// The deterministic frame's image: fixed-point sums -> float32.
+__global__ void k_fixed_to_float(float* __restrict__ out, const unsigned long long* __restrict__ fixed, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)((double)(long long)fixed[i] * (1.0 / 4294967296.0));
 }
 
 
@@ -752,6 +776,9 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     return set_error(RT_ERR_INVALID_ARG, "rt_render: invalid options");
   if (nrc && (opt.flags & RT_FLAG_DIFFUSE_BOUNCE))
     return set_error(RT_ERR_UNSUPPORTED, "rt_render_nrc: the radiance cache does not take RT_FLAG_DIFFUSE_BOUNCE");
+  const bool deterministic = (opt.flags & RT_FLAG_DETERMINISTIC) != 0;
+  if (nrc && deterministic)
+    return set_error(RT_ERR_UNSUPPORTED, "rt_render_nrc: the radiance cache does not take RT_FLAG_DETERMINISTIC");
   bool use_bvh = opt.use_bvh != 0;
   if (use_bvh && !s->built) return set_error(RT_ERR_NOT_BUILT, "rt_render: BVH requested before rt_bvh_build");
   occupancy(s);
@@ -831,7 +858,14 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     s->tcount = 0;
     frame_slot = timing_begin(s, 3, st);
   }
-  cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);
+  const size_t n_out = (size_t)W * H * 3;
+  if (deterministic) {
+    if ((rs = ensure(s->fb_fixed, n_out * sizeof(unsigned long long)))) return rs;
+    fp.fb_fixed = (unsigned long long*)s->fb_fixed.p;
+    cudaMemsetAsync(fp.fb_fixed, 0, n_out * sizeof(unsigned long long), st);   // out is written at the end
+  } else {
+    cudaMemsetAsync(out, 0, n_out * sizeof(float), st);
+  }
   cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
   bool per_depth = (opt.flags & RT_FLAG_PER_DEPTH_WAVEFRONT) != 0;
   // depths 0..last run as wavefronts; the rest run as depth-first paths,
@@ -894,6 +928,10 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     launches += 2;
   }
   cudaStreamWaitEvent(st, s->ev_shadowed[last], 0);
+  if (deterministic) {
+    k_fixed_to_float<<<(unsigned)((n_out + 255) / 256), 256, 0, st>>>(out, fp.fb_fixed, n_out);
+    launches += 1;
+  }
   if (T >= 0 && train) {
     // one Adam step on this frame's targets (complete once both streams joined)
     int slot = timing ? timing_begin(s, 2, st) : -1;
@@ -1107,6 +1145,7 @@ rt_status rt_scene_destroy(rt_scene* s) {
   }
   release(s->counters);
   release(s->fb_host_stage);
+  release(s->fb_fixed);
   release(s->fb_stage[0]);
   release(s->fb_stage[1]);
   if (s->copy_stream) {

@@ -138,6 +138,7 @@ struct rt_scene {
   int lbvh_cut = 0;              // > 0: the LBVH nodes over this many primitives still await their refit
   // render
   rtb::Buf rayq[2], shadowq[2], counters, fb_host_stage;
+  rtb::Buf fb_fixed;             // RT_FLAG_DETERMINISTIC: the frame's 64-bit fixed-point sums
   // rt_render_host_async: two device images, each copied to the host on the
   // copy stream while the next frame renders into the other
   rtb::Buf fb_stage[2];

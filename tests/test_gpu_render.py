@@ -410,6 +410,43 @@ def test_scene_update_then_rebuild():
     scene.close()
 
 
+@pytest.mark.parametrize("flags", [0, rtb.RT_FLAG_PER_DEPTH_WAVEFRONT])
+def test_deterministic_frames_are_bit_identical(flags):
+    """RT_FLAG_DETERMINISTIC: the pixel sums are 64-bit fixed-point integers,
+    so repeated frames agree to the bit (float atomics differ in their last
+    bits from run to run), and they agree with the float frame within the
+    rounding of the accumulation."""
+    sc = S.scene_terrain(seed=7, width=96, height=64, max_depth=5, cells=(16, 12), n_ico=6, ico_level=2)
+    W, H, D = sc.width, sc.height, sc.max_depth
+    scene = rtb.Scene(sc).build()
+    det = rtb.make_options(background=sc.background, flags=flags | rtb.RT_FLAG_DETERMINISTIC)
+    imgs = []
+    for _ in range(3):
+        out = torch.full((W * H * 3,), float("nan"), device="cuda")
+        rtb.rt_render_ex(scene.handle, sc.camera, W, H, D, out, det)
+        imgs.append(out.cpu().numpy())
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    for img in imgs[1:]:
+        assert np.array_equal(img, imgs[0])
+    ref = torch.empty(W * H * 3, device="cuda")
+    rtb.rt_render_ex(scene.handle, sc.camera, W, H, D, ref, rtb.make_options(background=sc.background, flags=flags))
+    np.testing.assert_allclose(imgs[0], ref.cpu().numpy(), atol=1e-5, rtol=0)
+    # parity with the oracle holds as for the float frame
+    g = oracle_render(sc)
+    err = np.abs(imgs[0].reshape(-1, 3).astype(np.float64) - g["rgb"]).max(axis=1)
+    assert not ((err > COLOUR_TOL) & (g["robust"] >= 1.0)).any()
+    # refused with the radiance cache and by a batch
+    nrc = rtb.rt_nrc_create(scene.handle)
+    with pytest.raises(rtb.RtError) as ei:
+        rtb.rt_render_nrc(scene.handle, nrc, sc.camera, W, H, D, ref, train=False, options=det)
+    assert ei.value.status == rtb.RT_ERR_UNSUPPORTED
+    rtb.rt_nrc_destroy(nrc)
+    with pytest.raises(rtb.RtError) as ei:
+        rtb.rt_batch_create([scene.handle], [sc.camera], [W], [H], D, [ref], det)
+    assert ei.value.status == rtb.RT_ERR_UNSUPPORTED
+    scene.close()
+
+
 def test_render_host_async_frames_match_sync():
     """Frames queued back to back through the two device images, each copied
     to its own pinned buffer; a third frame reuses the first image (it waits
