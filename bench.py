@@ -44,11 +44,11 @@ BYTES_NODE = 128
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "f700c75a53bb77d8"
+PROFILED_SHA = "a6b916224dded734"
 PROFILED_TRAFFIC = {
-    0: (24_626_688 + 122_784_256 + 5_496_064 + 768 + 7_376_384,
+    0: (24_692_736 + 122_469_888 + 5_493_760 + 2_560 + 7_366_656,
         "k_trace<1,0,0> + k_trace<0,0,0> (depth 1) + k_paths<0,0> (depths 2-5): profiles/launches_terrain1080p_d5.md"),
-    1: (180_145_920 + 4_689_664 + 5_758_464, "k_shadow<0> (depths 0 and 1): profiles/launches_terrain1080p_d5.md"),
+    1: (180_072_704 + 4_691_200 + 5_760_000, "k_shadow<0> (depths 0 and 1): profiles/launches_terrain1080p_d5.md"),
 }
 
 
