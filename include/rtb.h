@@ -367,6 +367,17 @@ rt_status rt_nrc_destroy(rt_nrc* nrc);
  * resets the Adam moments and step. */
 rt_status rt_nrc_get_params(rt_nrc* nrc, float* host_params, void* stream);
 rt_status rt_nrc_set_params(rt_nrc* nrc, const float* host_params, void* stream);
+/* Writes the cache to a file: its configuration, FP32 parameters, Adam
+ * moments and step (little-endian, behind a magic tag and a format
+ * version).  Syncs the stream.  RT_ERR_INVALID_ARG when the file cannot
+ * be written. */
+rt_status rt_nrc_save(rt_nrc* nrc, const char* path, void* stream);
+/* Restores a cache written by rt_nrc_save into nrc: parameters, Adam
+ * moments, step and configuration (the encoding box stays that of nrc's
+ * scene).  Syncs the stream.  RT_ERR_INVALID_ARG on a missing or truncated
+ * file, another format, or an invalid configuration or non-finite value;
+ * nrc is then unchanged. */
+rt_status rt_nrc_load(rt_nrc* nrc, const char* path, void* stream);
 /* Gradient of the last training step (RT_NRC_PARAMS floats) and its loss. */
 rt_status rt_nrc_get_grads(rt_nrc* nrc, float* host_grads, float* host_loss, void* stream);
 /* exp(MLP(encode(p, n, v))) for n hits given as n x 9 device floats (p, n, v);

@@ -20,7 +20,7 @@ __all__ = [
     "rt_render", "rt_render_ex", "rt_render_host", "rt_render_host_async", "rt_camera_rays", "rt_trace_closest",
     "rt_trace_any", "rt_scene_sync", "rt_scene_destroy", "rt_render_stage_times", "Scene",
     "rt_nrc_config_default", "rt_nrc_create", "rt_nrc_destroy", "rt_nrc_get_params", "rt_nrc_set_params",
-    "rt_nrc_get_grads", "rt_nrc_infer", "rt_nrc_train_step", "rt_render_nrc",
+    "rt_nrc_get_grads", "rt_nrc_infer", "rt_nrc_train_step", "rt_render_nrc", "rt_nrc_save", "rt_nrc_load",
     "rt_tune", "rt_batch_create", "rt_batch_set_cameras", "rt_batch_render", "rt_batch_autotune",
     "rt_batch_destroy", "Batch", "rt_pass", "rt_scene_set_area_lights", "rt_render_pass",
 ]
@@ -165,6 +165,8 @@ def lib():
             "rt_scene_set_area_lights": (I, [P, P, S]),
             "rt_render_pass": (I, [P, P, I, I, I, P, P, P, P, P]),
             "rt_render_host_async": (I, [P, P, I, I, I, P, P, P]),
+            "rt_nrc_save": (I, [P, ctypes.c_char_p, P]),
+            "rt_nrc_load": (I, [P, ctypes.c_char_p, P]),
             "rt_scene_destroy": (I, [P]),
         }
         for name, (res, args) in sigs.items():
@@ -397,6 +399,16 @@ def rt_nrc_create(scene, config=None) -> int:
     h = P()
     _check(lib().rt_nrc_create(scene, ctypes.byref(config) if config is not None else None, ctypes.byref(h)))
     return h.value
+
+
+def rt_nrc_save(nrc, path, stream=None):
+    """Writes the cache (configuration, parameters, Adam state) to `path`."""
+    _check(lib().rt_nrc_save(nrc, os.fsencode(path), _stream(stream)))
+
+
+def rt_nrc_load(nrc, path, stream=None):
+    """Restores a cache written by rt_nrc_save into `nrc`."""
+    _check(lib().rt_nrc_load(nrc, os.fsencode(path), _stream(stream)))
 
 
 def rt_nrc_destroy(nrc):

@@ -244,9 +244,10 @@ constexpr int kTsHT = 114688;    // 4 x 16 KB: H1^T .. H4^T [64][128]
 constexpr int kTsDZ = 180224;    // 16 KB: dZ [128][64] (dZ5: [128][16])
 constexpr int kTsDZT = 196608;   // 16 KB: dZ^T [64][128] (dZ5^T: [16][128])
 constexpr int kTsBias = 212992;  // 272 floats
-constexpr int kTsDB = 214528;    // 272 floats: bias gradients of this CTA
-constexpr int kTsMisc = 216064;  // mbarrier, tmem slot, flags, loss
+constexpr int kTsDB = 214528;    // 4 x 272 floats: bias gradients, one set per warp (summed in warp order)
+constexpr int kTsMisc = 218880;  // mbarrier, tmem slot, flags, loss of each warp
 constexpr int kTrainSmem = kTsMisc + 64;
+static_assert(kTrainSmem <= 227 * 1024, "the training CTA's shared memory exceeds the per-block limit");
 
 // Lane of row m of an M = 64 accumulator: 16 rows in each 32-lane quarter.
 // One CTA's gradient row: the kNP parameter gradients (oracle layout), then
@@ -280,9 +281,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
   extern __shared__ __align__(1024) uint8_t sm[];
   uint64_t* mbar = (uint64_t*)(sm + kTsMisc);
   uint32_t* tslot = (uint32_t*)(sm + kTsMisc + 8);
-  float* s_loss = (float*)(sm + kTsMisc + 16);
+  float* s_loss = (float*)(sm + kTsMisc + 16);   // [4]
   float* bias = (float*)(sm + kTsBias);
   float* db = (float*)(sm + kTsDB);
+  float* db_w = db + (threadIdx.x >> 5) * kPackedBias;   // this warp's set: only its lane 0 adds to it
   int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc::alloc(tc::smem_u32(tslot), kTrainTmemCols);
   const uint16_t* pw = (const uint16_t*)nd.packed;
@@ -296,10 +298,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
   load_tile(sm + kTsT3, pw + kPT3, 64, 64);
   load_tile(sm + kTsT4, pw + kPT4, 64, 16);
   const float* gb = (const float*)(pw + kPackedBf16);
-  for (int i = tid; i < kPackedBias; i += blockDim.x) {
-    bias[i] = gb[i];
-    db[i] = 0.f;
-  }
+  for (int i = tid; i < kPackedBias; i += blockDim.x) bias[i] = gb[i];
+  for (int i = tid; i < 4 * kPackedBias; i += blockDim.x) db[i] = 0.f;
   if (tid == 0) {
     tc::mbar_init(tc::smem_u32(mbar), 1);
     *s_loss = 0.f;
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         float s = warp_sum(g[c]);
-        if (lane == 0) atomicAdd(&db[256 + c], s);
+        if (lane == 0) db_w[256 + c] += s;
       }
       store_chunk(sm + kTsDZ, tid, 0, 16, g);
       store_chunk(sm + kTsDZ, tid, 1, 16, g + 8);
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
 #pragma unroll
       for (int k = 0; k < 64; ++k) {
         float s = warp_sum(g[k]);
-        if (lane == 0) atomicAdd(&db[64 * (l - 1) + k], s);
+        if (lane == 0) db_w[64 * (l - 1) + k] += s;
       }
 #pragma unroll
       for (int c = 0; c < 8; ++c) store_chunk(sm + kTsDZ, tid, c, 64, g + 8 * c);
@@ -492,13 +492,17 @@ done:
   } else {
     for (int i = tid; i < kNW; i += blockDim.x) gp[i] = 0.f;
   }
-  for (int i = tid; i < 4 * 64; i += blockDim.x) gp[off_b(0) + i] = have ? db[i] : 0.f;
-  if (tid < 3) gp[off_b(4) + tid] = have ? db[256 + tid] : 0.f;
+  // the warps' bias gradients and losses, summed in warp order (deterministic)
+  auto db_sum = [&](int i) {
+    return db[i] + db[kPackedBias + i] + db[2 * kPackedBias + i] + db[3 * kPackedBias + i];
+  };
+  for (int i = tid; i < 4 * 64; i += blockDim.x) gp[off_b(0) + i] = have ? db_sum(i) : 0.f;
+  if (tid < 3) gp[off_b(4) + tid] = have ? db_sum(256 + tid) : 0.f;
   {
     float ls = warp_sum(loss_acc);
-    if (lane == 0) atomicAdd(s_loss, ls);
+    if (lane == 0) s_loss[warp] = ls;
     __syncthreads();
-    if (tid == 0) gp[kNP] = have ? *s_loss : 0.f;
+    if (tid == 0) gp[kNP] = have ? ((s_loss[0] + s_loss[1]) + s_loss[2]) + s_loss[3] : 0.f;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -777,6 +781,69 @@ rt_status rt_nrc_get_params(rt_nrc* r, float* host, void* stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaMemcpy(host, r->params.p, kNP * 4, cudaMemcpyDeviceToHost);
   return cuda_error(e, "rt_nrc_get_params");
+}
+
+// File layout of rt_nrc_save: header, then params, m, v (kNP floats each).
+struct NrcFileHeader {
+  char magic[8];          // "RTBNRC" 0 1
+  uint32_t version;       // 1
+  uint32_t n_params;      // kNP
+  rt_nrc_config cfg;
+  int64_t step;
+};
+static const char kNrcMagic[8] = {'R', 'T', 'B', 'N', 'R', 'C', 0, 1};
+
+rt_status rt_nrc_save(rt_nrc* r, const char* path, void* stream) {
+  if (!r || !path) return set_error(RT_ERR_INVALID_ARG, "rt_nrc_save: NULL argument");
+  std::vector<float> buf(3 * (size_t)kNP);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(buf.data(), r->params.p, kNP * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(buf.data() + kNP, r->m.p, kNP * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(buf.data() + 2 * kNP, r->v.p, kNP * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "rt_nrc_save");
+  NrcFileHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kNrcMagic, 8);
+  h.version = 1;
+  h.n_params = kNP;
+  h.cfg = r->cfg;
+  h.step = r->step;
+  FILE* f = fopen(path, "wb");
+  if (!f) return set_error(RT_ERR_INVALID_ARG, std::string("rt_nrc_save: cannot open ") + path);
+  bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return set_error(RT_ERR_INVALID_ARG, std::string("rt_nrc_save: cannot write ") + path);
+  return RT_OK;
+}
+
+rt_status rt_nrc_load(rt_nrc* r, const char* path, void* stream) {
+  if (!r || !path) return set_error(RT_ERR_INVALID_ARG, "rt_nrc_load: NULL argument");
+  FILE* f = fopen(path, "rb");
+  if (!f) return set_error(RT_ERR_INVALID_ARG, std::string("rt_nrc_load: cannot open ") + path);
+  NrcFileHeader h;
+  std::vector<float> buf(3 * (size_t)kNP);
+  bool ok = fread(&h, sizeof(h), 1, f) == 1 && fread(buf.data(), 4, buf.size(), f) == buf.size();
+  char extra;
+  ok = ok && fread(&extra, 1, 1, f) == 0;   // nothing after the arrays
+  fclose(f);
+  if (!ok) return set_error(RT_ERR_INVALID_ARG, "rt_nrc_load: truncated file or trailing bytes");
+  if (memcmp(h.magic, kNrcMagic, 8) != 0 || h.version != 1 || h.n_params != (uint32_t)kNP)
+    return set_error(RT_ERR_INVALID_ARG, "rt_nrc_load: not a radiance-cache file of this format");
+  const rt_nrc_config& c = h.cfg;
+  if (c.train_batch < 1 || c.terminate_depth < 0 || c.terminate_depth > RT_MAX_DEPTH || !std::isfinite(c.lr) ||
+      !std::isfinite(c.beta1) || !std::isfinite(c.beta2) || !std::isfinite(c.eps) || h.step < 0)
+    return set_error(RT_ERR_INVALID_ARG, "rt_nrc_load: invalid configuration");
+  for (float x : buf)
+    if (!std::isfinite(x)) return set_error(RT_ERR_INVALID_ARG, "rt_nrc_load: non-finite value");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(r->params.p, buf.data(), kNP * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(r->m.p, buf.data() + kNP, kNP * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(r->v.p, buf.data() + 2 * kNP, kNP * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "rt_nrc_load");
+  r->cfg = c;
+  r->step = h.step;
+  return nrc_pack(r, st);
 }
 
 rt_status rt_nrc_set_params(rt_nrc* r, const float* host, void* stream) {

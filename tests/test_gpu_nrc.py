@@ -240,3 +240,47 @@ def test_training_frame_image_and_rays(flags):
     assert np.isfinite(p1).all()
     rtb.rt_nrc_destroy(nrc)
     scene.close()
+
+
+def test_nrc_save_and_load(tmp_path):
+    """rt_nrc_save / rt_nrc_load restore parameters, Adam moments and step:
+    a loaded cache infers exactly as the saved one and takes the same next
+    training step.  Damaged or foreign files are refused and leave the
+    cache as it was."""
+    sc, scene = _scene()
+    rng = np.random.default_rng(4)
+    n = 2048
+    pnv = _samples(sc, n, rng)
+    target = (0.3 + 0.2 * np.sin(pnv[:, :3])).astype(np.float32)
+    pd, td = torch.from_numpy(pnv).cuda(), torch.from_numpy(target).cuda()
+    a = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=3))
+    for _ in range(5):
+        rtb.rt_nrc_train_step(a, scene.handle, pd, td, n)
+    path = tmp_path / "cache.rtbnrc"
+    rtb.rt_nrc_save(a, path)
+    b = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=99))   # other weights
+    before = rtb.rt_nrc_get_params(b)
+    raw = path.read_bytes()
+    for bad in (raw[:-4], raw + b"x", b"XXXXXXXX" + raw[8:]):
+        (tmp_path / "bad").write_bytes(bad)
+        with pytest.raises(rtb.RtError) as ei:
+            rtb.rt_nrc_load(b, tmp_path / "bad")
+        assert ei.value.status == rtb.RT_ERR_INVALID_ARG
+    np.testing.assert_array_equal(rtb.rt_nrc_get_params(b), before)
+    with pytest.raises(rtb.RtError):
+        rtb.rt_nrc_load(b, tmp_path / "missing")
+    rtb.rt_nrc_load(b, path)
+    np.testing.assert_array_equal(rtb.rt_nrc_get_params(b), rtb.rt_nrc_get_params(a))
+    oa = torch.empty(n * 3, device="cuda")
+    ob = torch.empty(n * 3, device="cuda")
+    rtb.rt_nrc_infer(a, scene.handle, pd, n, oa)
+    rtb.rt_nrc_infer(b, scene.handle, pd, n, ob)
+    assert torch.equal(oa, ob)
+    # the same next step: the Adam moments and the step count came along
+    rtb.rt_nrc_train_step(a, scene.handle, pd, td, n)
+    rtb.rt_nrc_train_step(b, scene.handle, pd, td, n)
+    np.testing.assert_array_equal(rtb.rt_nrc_get_params(b), rtb.rt_nrc_get_params(a))
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    rtb.rt_nrc_destroy(a)
+    rtb.rt_nrc_destroy(b)
+    scene.close()
