@@ -171,6 +171,23 @@ def cpu_oracle_sample(sc, seconds_hint=15.0):
                             f"{dt:.1f} s)", cores
 
 
+def max_over_ranks(x, dist, device="cpu"):
+    """The largest of the ranks' values of x (the slowest rank's time); x
+    itself on one rank (dist None)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, rays_per_rank, ms):
+    """Whole-job Mrays/s: every rank traces rays_per_rank a step, and the
+    job's step lasts as long as its slowest rank's (ms)."""
+    return world * rays_per_rank / (ms * 1e3)
+
+
 def run_reference(args, rank, world):
     """The reference arm: the FP64 CPU oracle on the host cores."""
     from paper_1504_03151_b300 import scenes as S
@@ -466,12 +483,8 @@ def main():
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * rays / (ms * 1e3)        # Mrays/s over all ranks
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), dist, dev)
+    value = job_throughput(world, rays, ms)        # Mrays/s over all ranks
 
     # end to end through the public API: every step copies the geometry from
     # pinned host memory, builds, renders and copies the image into pinned
@@ -520,12 +533,8 @@ def main():
             rtb.rt_bvh_build(h)
             rtb.rt_render_host_async(h, sc.camera, W, H, D, out_pins[j], opts)
         assert rtb.rt_scene_sync(h) == rtb.RT_OK
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
-        if dist:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-    e2e_value = world * rays / (e2e_ms * 1e3) if e2e_ms else None
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / n_e2e, dist, dev)
+    e2e_value = job_throughput(world, rays, e2e_ms) if e2e_ms else None
 
     # roofline of the dominant kernel class
     pk, pk_kind = peaks()
@@ -565,11 +574,7 @@ def main():
             nrc_step()
             nev[k][1].record(stream)
         torch.cuda.synchronize()
-        nrc_ms = sum(a.elapsed_time(b) for a, b in nev) / args.steps
-        if dist:
-            t = torch.tensor([nrc_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            nrc_ms = float(t.item())
+        nrc_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in nev) / args.steps, dist, dev)
         # the network's kernels alone, against the tensor-core peak: one training
         # step on 65,536 samples and inference on 2^20 queries (random hits in
         # the scene box; algorithmic FLOPs of the unpadded 96-64-64-64-64-3 MLP)
@@ -607,7 +612,7 @@ def main():
         x, r = nrc_out.double(), full.double()
         relmse = float(((x - r) ** 2 / (r ** 2 + 0.01)).mean())
         mse01 = float(((x.clamp(0, 1) - r.clamp(0, 1)) ** 2).mean())
-        nrc_value = world * rays / (nrc_ms * 1e3)
+        nrc_value = job_throughput(world, rays, nrc_ms)
         nrc_line = {
             "metric": "Mrays-equivalent/s (full-depth rays per cached step)", "value": nrc_value,
             "ms_per_step": nrc_ms, "vs_plain": nrc_value / value, "relmse_vs_full_depth": relmse,
