@@ -555,6 +555,19 @@ def test_empty_scene_and_single_primitive():
     compare(gpu_render(tri), oracle_render(tri, mode="brute"))
 
 
+@pytest.mark.parametrize("red_first", [False, True])
+def test_exact_ties_go_to_the_lower_primitive_id_on_gpu(red_first):
+    """Duplicated primitives (a floor and a sphere, each twice, in two
+    colours): the GPU keeps the lower id on the exact tie, as the oracle."""
+    import test_oracle_pins as P
+    sc = P._duplicated_scene(red_first)
+    g = gpu_render(sc)
+    hit = g["prim"] >= 0
+    assert hit.mean() > 0.5
+    assert set(np.unique(g["prim"][hit])) <= {0, 2, 3}
+    compare(g, oracle_render(sc, mode="brute"))
+
+
 def test_degenerate_triangles_never_hit():
     mats = S.material(S.MAT_DIFFUSE, (0.5, 0.5, 0.5))
     li = S.lights([(0, 10, 0)], [(1, 1, 1)])

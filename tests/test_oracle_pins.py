@@ -365,3 +365,37 @@ def test_scene_rejects_bad_input():
                 S.spheres_from([(0, 0, 0)], [1.0], [3])):
         with pytest.raises(ValueError):
             O.OracleScene(bad, notri, mats, li)
+
+
+def _duplicated_scene(red_first):
+    """A floor (2 triangles) and a sphere, each present twice at exactly the
+    same place: once grey (material 0), once red (material 1).  red_first
+    puts the red copies at the lower primitive ids."""
+    mats = np.concatenate([S.material(S.MAT_DIFFUSE, (0.5, 0.5, 0.5), ks=0.0),
+                           S.material(S.MAT_DIFFUSE, (0.9, 0.1, 0.1), ks=0.0)])
+    first, second = (1, 0) if red_first else (0, 1)
+    v0 = [(-5, 0, -5), (-5, 0, -5)]
+    v1 = [(-5, 0, 5), (5, 0, 5)]
+    v2 = [(5, 0, 5), (5, 0, -5)]
+    tris = np.concatenate([S.triangles_from(v0, v1, v2, first), S.triangles_from(v0, v1, v2, second)])
+    sph = S.spheres_from([(0.0, 1.0, 0.0), (0.0, 1.0, 0.0)], [0.8, 0.8], [first, second])
+    return S.Scene("dup", sph, tris, mats, S.lights([(3.0, 8.0, 4.0)], [(1.0, 1.0, 1.0)]),
+                   S.camera((0.0, 4.0, 7.0), (0.0, 0.5, 0.0)), 48, 36, 1)
+
+
+@pytest.mark.parametrize("red_first", [False, True])
+def test_exact_ties_go_to_the_lower_primitive_id(red_first):
+    """Duplicated primitives tie exactly: the hit is the lower id, in brute
+    force and through the BVH, and the colour is that primitive's."""
+    sc = _duplicated_scene(red_first)
+    orc = O.OracleScene.from_scene(sc)
+    # ids: the spheres 0, 1; the first floor 2, 3; its copy 4, 5
+    for mode in ("brute", "bvh"):
+        r = orc.render(sc.camera, sc.width, sc.height, 0, mode=mode)
+        hit = r["prim"] >= 0
+        assert hit.mean() > 0.5
+        assert set(np.unique(r["prim"][hit])) <= {0, 2, 3}
+        assert (r["prim"][hit] != 1).all() and not np.isin(r["prim"][hit], [4, 5]).any()
+        lit = r["rgb"][hit]
+        red = lit[:, 0] > 3 * lit[:, 2] + 1e-9
+        assert (red == red_first)[lit[:, 0] > 1e-6].all()
