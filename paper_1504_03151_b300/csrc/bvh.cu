@@ -22,7 +22,7 @@ constexpr int kSortCoopMaxBlocks = 1024;   // grid of the single-launch sort (co
 constexpr int kSortCoopMaxKeys = 1 << 22;  // larger inputs take the multi-launch sort
 constexpr int kTopBins = 16;        // SAH bins per axis for the top-level rebuild
 constexpr int kTopMaxLevels = 64;   // launches of the level kernel (empty ones return at once)
-constexpr int kTopCache = 4096;     // clusters of one segment held in shared memory (36 B each)
+constexpr int kTopCache = 4096;     // clusters of one segment held in shared memory (40 B each)
 constexpr int kTopWarpSeg = 32;     // segments of at most this many clusters are finished by one warp
 constexpr int kTopForceMedian = 32; // from this level on, split segments at the middle: with at
                                     // most 2^28 clusters every segment is done by level 60
@@ -761,6 +761,7 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
   }
   // centroid bounds: warp reduction, one atomic per warp and axis
   float cmin[3], cmax[3];
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     cmin[a] = mine ? cc[a] : INFINITY;
     cmax[a] = mine ? cc[a] : -INFINITY;
@@ -781,6 +782,7 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
   const float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
   int bin[3];
   const float lo3[3] = {lo.x, lo.y, lo.z}, hi3[3] = {hi.x, hi.y, hi.z};
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     bin[a] = bin_of(cc[a], clo[a], cext[a]);
     if (mine) {
@@ -850,7 +852,7 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
     left = t < m / 2;   // split at the middle, order kept
   } else {
     const int ax = best / (kTopBins - 1), sb = best % (kTopBins - 1);
-    left = bin[ax] <= sb;
+    left = (ax == 0 ? bin[0] : ax == 1 ? bin[1] : bin[2]) <= sb;
   }
   const unsigned bl = __ballot_sync(0xffffffffu, mine && left), br = __ballot_sync(0xffffffffu, mine && !left);
   if (lane == 0) {
@@ -905,6 +907,293 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
   return nleft;
 }
 
+// Split of a segment of more than 256 clusters by the whole block: the same
+// bins, SAH costs, choice and stable partition as split_small.  A segment of
+// up to cache_cap clusters is first read into shared memory, its loads
+// issued eight deep.  After that every thread takes a contiguous chunk of
+// the segment for the bounds and the partition: it counts and bounds its
+// two sides in one pass before a block scan places them.
+__device__ __forceinline__ int split_large(int level, int b, int e, const int* ids_in, int* ids_out,
+                                           const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
+                                           int cache_cap, float4 side_lo[2], float4 side_hi[2]) {
+  __shared__ int s_cb[6];
+  __shared__ int bin_count[3][kTopBins];
+  __shared__ int bin_lo[3][kTopBins][3], bin_hi[3][kTopBins][3];
+  __shared__ float s_cost[3 * (kTopBins - 1)];
+  __shared__ int s_split_axis, s_split_bin;
+  __shared__ int s_wl[8], s_wr[8];
+  __shared__ int s_box[2][6];
+  extern __shared__ float4 s_dyn[];
+  const unsigned FULL = 0xffffffffu;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, m = e - b;
+  float4* c_lo = s_dyn;
+  float4* c_hi = s_dyn + cache_cap;
+  int* c_id = (int*)(s_dyn + 2 * (size_t)cache_cap);
+  int* c_part = c_id + cache_cap;
+  const bool cached = m <= cache_cap;
+  if (t < 6) {
+    s_cb[t] = f2o(t < 3 ? INFINITY : -INFINITY);
+    s_box[0][t] = f2o(t < 3 ? INFINITY : -INFINITY);
+    s_box[1][t] = f2o(t < 3 ? INFINITY : -INFINITY);
+  }
+  if (t < 3 * kTopBins) {
+    int a = t / kTopBins, k = t % kTopBins;
+    bin_count[a][k] = 0;
+    for (int q = 0; q < 3; ++q) {
+      bin_lo[a][k][q] = f2o(INFINITY);
+      bin_hi[a][k][q] = f2o(-INFINITY);
+    }
+  }
+  if (cached) {
+    for (int k0 = t; k0 < m; k0 += 256 * 8) {
+      int id[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + 256 * u;
+        id[u] = k < m ? __ldcg(&ids_in[b + k]) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + 256 * u;
+        if (k < m) {
+          c_id[k] = id[u];
+          c_lo[k] = clu_lo[id[u]];
+          c_hi[k] = clu_hi[id[u]];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // position k (0..m-1) of the segment
+  auto fetch = [&](int k, int& c, float4& lo, float4& hi) {
+    if (cached) {
+      c = c_id[k];
+      lo = c_lo[k];
+      hi = c_hi[k];
+    } else {
+      c = __ldcg(&ids_in[b + k]);
+      lo = clu_lo[c];
+      hi = clu_hi[c];
+    }
+  };
+  // this thread's chunk [k0, k1); an odd length keeps a warp's strided
+  // shared-memory reads free of bank conflicts
+  const int per = ((m + 255) / 256) | 1;
+  const int k0 = min(t * per, m), k1 = min(k0 + per, m);
+  // centroid bounds of the segment
+  {
+    float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int k = k0; k < k1; ++k) {
+      int c;
+      float4 lo, hi;
+      fetch(k, c, lo, hi);
+      const float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
+      for (int a = 0; a < 3; ++a) {
+        v[a] = fminf(v[a], cc[a]);
+        v[a + 3] = fmaxf(v[a + 3], cc[a]);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      for (int q = 0; q < 3; ++q) v[q] = fminf(v[q], __shfl_xor_sync(FULL, v[q], o));
+      for (int q = 3; q < 6; ++q) v[q] = fmaxf(v[q], __shfl_xor_sync(FULL, v[q], o));
+    }
+    if (lane == 0 && v[0] <= v[3]) {
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&s_cb[a], f2o(v[a]));
+        atomicMax(&s_cb[a + 3], f2o(v[a + 3]));
+      }
+    }
+  }
+  __syncthreads();
+  const float clo[3] = {o2f(s_cb[0]), o2f(s_cb[1]), o2f(s_cb[2])};
+  const float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
+  // bin every axis (strided, so that a warp's lanes spread over the bins)
+  for (int k = t; k < m; k += 256) {
+    int c;
+    float4 lo, hi;
+    fetch(k, c, lo, hi);
+    const int b0 = bin_of(0.5f * (lo.x + hi.x), clo[0], cext[0]);
+    const int b1 = bin_of(0.5f * (lo.y + hi.y), clo[1], cext[1]);
+    const int b2 = bin_of(0.5f * (lo.z + hi.z), clo[2], cext[2]);
+    const int n = (int)lo.w;
+    const int ilo[3] = {f2o(lo.x), f2o(lo.y), f2o(lo.z)}, ihi[3] = {f2o(hi.x), f2o(hi.y), f2o(hi.z)};
+    atomicAdd(&bin_count[0][b0], n);
+    atomicAdd(&bin_count[1][b1], n);
+    atomicAdd(&bin_count[2][b2], n);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      atomicMin(&bin_lo[0][b0][q], ilo[q]);
+      atomicMax(&bin_hi[0][b0][q], ihi[q]);
+      atomicMin(&bin_lo[1][b1][q], ilo[q]);
+      atomicMax(&bin_hi[1][b1][q], ihi[q]);
+      atomicMin(&bin_lo[2][b2][q], ilo[q]);
+      atomicMax(&bin_hi[2][b2][q], ihi[q]);
+    }
+  }
+  __syncthreads();
+  // SAH of every split plane (one thread per plane)
+  if (t < 3 * (kTopBins - 1)) {
+    int a = t / (kTopBins - 1), sp = t % (kTopBins - 1);
+    float l0[3] = {INFINITY, INFINITY, INFINITY}, l1[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float r0[3] = {INFINITY, INFINITY, INFINITY}, r1[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int nl = 0, nr = 0;
+    for (int k = 0; k < kTopBins; ++k) {
+      int cnt = bin_count[a][k];
+      if (cnt == 0) continue;
+      bool lft = k <= sp;
+      if (lft) nl += cnt;
+      else nr += cnt;
+      for (int q = 0; q < 3; ++q) {
+        float blo = o2f(bin_lo[a][k][q]), bhi = o2f(bin_hi[a][k][q]);
+        if (lft) {
+          l0[q] = fminf(l0[q], blo);
+          l1[q] = fmaxf(l1[q], bhi);
+        } else {
+          r0[q] = fminf(r0[q], blo);
+          r1[q] = fmaxf(r1[q], bhi);
+        }
+      }
+    }
+    float cost = INFINITY;
+    if (nl > 0 && nr > 0) {
+      float AL = area(make_float4(l0[0], l0[1], l0[2], 0), make_float4(l1[0], l1[1], l1[2], 0));
+      float AR = area(make_float4(r0[0], r0[1], r0[2], 0), make_float4(r1[0], r1[1], r1[2], 0));
+      cost = AL * (float)nl + AR * (float)nr;
+    }
+    s_cost[t] = cost;
+  }
+  __syncthreads();
+  if (t == 0) {
+    int best = -1;
+    float bc = INFINITY;
+    for (int k = 0; k < 3 * (kTopBins - 1); ++k)
+      if (s_cost[k] < bc) {
+        bc = s_cost[k];
+        best = k;
+      }
+    if (best < 0 || level >= kTopForceMedian) {
+      s_split_axis = -1;   // split the segment at its middle
+      s_split_bin = 0;
+    } else {
+      s_split_axis = best / (kTopBins - 1);
+      s_split_bin = best % (kTopBins - 1);
+    }
+  }
+  __syncthreads();
+  const int ax = s_split_axis, sb = s_split_bin;
+  // right side (1) or left (0) of position k; by position: the halves in order
+  bool by_position = ax < 0;
+  const float alo = ax == 0 ? clo[0] : (ax == 1 ? clo[1] : clo[2]);
+  const float aext = ax == 0 ? cext[0] : (ax == 1 ? cext[1] : cext[2]);
+  auto side_of = [&](int k, float4 lo, float4 hi) {
+    if (by_position) return k >= m / 2 ? 1 : 0;
+    const float cl = ax == 0 ? lo.x : (ax == 1 ? lo.y : lo.z);
+    const float ch = ax == 0 ? hi.x : (ax == 1 ? hi.y : hi.z);
+    return bin_of(0.5f * (cl + ch), alo, aext) <= sb ? 0 : 1;
+  };
+  int nleft = 0, before_l = 0, before_r = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    float bx[2][6];
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) bx[sd][q] = q < 3 ? INFINITY : -INFINITY;
+    int nl = 0, nr = 0;
+    for (int k = k0; k < k1; ++k) {
+      int c;
+      float4 lo, hi;
+      fetch(k, c, lo, hi);
+      const int sd = side_of(k, lo, hi);
+      nl += sd == 0;
+      nr += sd;
+      const float v[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const float x = sd ? bx[1][q] : bx[0][q];
+        const float y = q < 3 ? fminf(x, v[q]) : fmaxf(x, v[q]);
+        if (sd) bx[1][q] = y;
+        else bx[0][q] = y;
+      }
+    }
+    // exclusive scan of the two counts over the block
+    int il = nl, ir = nr;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int xl = __shfl_up_sync(FULL, il, o), xr = __shfl_up_sync(FULL, ir, o);
+      if (lane >= o) {
+        il += xl;
+        ir += xr;
+      }
+    }
+    if (lane == 31) {
+      s_wl[w] = il;
+      s_wr[w] = ir;
+    }
+    __syncthreads();
+    int total_l = 0;
+    before_l = il - nl;
+    before_r = ir - nr;
+    for (int q = 0; q < 8; ++q) {
+      if (q < w) {
+        before_l += s_wl[q];
+        before_r += s_wr[q];
+      }
+      total_l += s_wl[q];
+    }
+    __syncthreads();   // s_wl / s_wr are read before a second attempt writes them
+    if (!by_position && (total_l == 0 || total_l == m)) {
+      // not reachable with a finite SAH cost; keep a valid split at the middle
+      by_position = true;
+      continue;
+    }
+    nleft = total_l;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) bx[sd][q] = fminf(bx[sd][q], __shfl_xor_sync(FULL, bx[sd][q], o));
+#pragma unroll
+        for (int q = 3; q < 6; ++q) bx[sd][q] = fmaxf(bx[sd][q], __shfl_xor_sync(FULL, bx[sd][q], o));
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd)
+        if (bx[sd][0] <= bx[sd][3])
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            atomicMin(&s_box[sd][q], f2o(bx[sd][q]));
+            atomicMax(&s_box[sd][q + 3], f2o(bx[sd][q + 3]));
+          }
+    }
+    break;
+  }
+  // stable partition: left side ascending from b, right side from b + nleft.
+  // A cached segment is placed in shared memory first and copied out with
+  // coalesced stores (the chunks' lanes would scatter their stores).
+  {
+    int* dst = cached ? c_part : ids_out + b;
+    int pl = before_l, pr = nleft + before_r;
+    for (int k = k0; k < k1; ++k) {
+      int c;
+      float4 lo, hi;
+      fetch(k, c, lo, hi);
+      if (side_of(k, lo, hi)) dst[pr++] = c;
+      else dst[pl++] = c;
+    }
+  }
+  __syncthreads();
+  if (cached) {
+    for (int k = t; k < m; k += 256) ids_out[b + k] = c_part[k];
+    __syncthreads();
+  }
+  for (int sd = 0; sd < 2; ++sd) {
+    side_lo[sd] = make_float4(o2f(s_box[sd][0]), o2f(s_box[sd][1]), o2f(s_box[sd][2]), 0.f);
+    side_hi[sd] = make_float4(o2f(s_box[sd][3]), o2f(s_box[sd][4]), o2f(s_box[sd][5]), 0.f);
+  }
+  return nleft;
+}
+
 // One block (256 threads) per active segment of this level: binned SAH
 // split (16 bins per axis, cost A_L N_L + A_R N_R with N in primitives),
 // stable partition of the cluster ids, then the two children are emitted:
@@ -917,15 +1206,8 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
                                                const int* __restrict__ clu_link, const float4* __restrict__ clu_lo,
                                                const float4* __restrict__ clu_hi, int* top_count, float4* nodes,
                                                BuildInfo* info, int4* small_seg, int* small_count, int cache_cap) {
-  __shared__ int s_cb[6];
-  __shared__ int bin_count[3][kTopBins];
-  __shared__ int bin_lo[3][kTopBins][3], bin_hi[3][kTopBins][3];
-  __shared__ float s_cost[3 * (kTopBins - 1)];
-  __shared__ int s_split_axis, s_split_bin;
-  __shared__ int s_wcount[8];
-  __shared__ int s_box[2][6];
   int nseg = __ldcg(&seg_count[level]);
-  int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int t = threadIdx.x;
   for (int sidx = blockIdx.x; sidx < nseg; sidx += gridDim.x) {
     int4 sg = __ldcg(&seg_in[sidx]);
     int b = sg.x, e = sg.y, node = sg.w;
@@ -935,241 +1217,12 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
     if (m <= 256) {
       nleft = split_small(level, b, e, ids_in, ids_out, clu_lo, clu_hi, slo, shi);
     } else {
-      // a segment of up to cache_cap clusters is read once into shared memory
-      extern __shared__ float4 s_dyn[];
-      float4* c_lo = s_dyn;
-      float4* c_hi = s_dyn + cache_cap;
-      int* c_id = (int*)(s_dyn + 2 * (size_t)cache_cap);
-      const bool cached = m <= cache_cap;
-      if (cached) {
-        for (int k = t; k < m; k += 256) c_id[k] = __ldcg(&ids_in[b + k]);
-        __syncthreads();
-        for (int k = t; k < m; k += 256) {
-          int c = c_id[k];
-          c_lo[k] = clu_lo[c];
-          c_hi[k] = clu_hi[c];
-        }
-      }
-      auto fetch = [&](int k, int& c, float4& lo, float4& hi) {
-        if (cached) {
-          c = c_id[k - b];
-          lo = c_lo[k - b];
-          hi = c_hi[k - b];
-        } else {
-          c = __ldcg(&ids_in[k]);
-          lo = clu_lo[c];
-          hi = clu_hi[c];
-        }
-      };
-      if (t < 6) {
-        s_cb[t] = f2o(t < 3 ? INFINITY : -INFINITY);
-        s_box[0][t] = f2o(t < 3 ? INFINITY : -INFINITY);
-        s_box[1][t] = f2o(t < 3 ? INFINITY : -INFINITY);
-      }
-      if (t < 3 * kTopBins) {
-        int a = t / kTopBins, k = t % kTopBins;
-        bin_count[a][k] = 0;
-        for (int q = 0; q < 3; ++q) {
-          bin_lo[a][k][q] = f2o(INFINITY);
-          bin_hi[a][k][q] = f2o(-INFINITY);
-        }
-      }
-      __syncthreads();
-      // centroid bounds of the segment
-      float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
-      for (int k = b + t; k < e; k += 256) {
-        int c;
-        float4 lo, hi;
-        fetch(k, c, lo, hi);
-        float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
-        for (int a = 0; a < 3; ++a) {
-          cmin[a] = fminf(cmin[a], cc[a]);
-          cmax[a] = fmaxf(cmax[a], cc[a]);
-        }
-      }
-      for (int a = 0; a < 3; ++a) {
-        if (cmin[a] <= cmax[a]) {
-          atomicMin(&s_cb[a], f2o(cmin[a]));
-          atomicMax(&s_cb[a + 3], f2o(cmax[a]));
-        }
-      }
-      __syncthreads();
-      float clo[3] = {o2f(s_cb[0]), o2f(s_cb[1]), o2f(s_cb[2])};
-      float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
-      // bin every axis
-      for (int k = b + t; k < e; k += 256) {
-        int c;
-        float4 lo, hi;
-        fetch(k, c, lo, hi);
-        float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
-        float lo3[3] = {lo.x, lo.y, lo.z}, hi3[3] = {hi.x, hi.y, hi.z};
-        for (int a = 0; a < 3; ++a) {
-          int bi = bin_of(cc[a], clo[a], cext[a]);
-          atomicAdd(&bin_count[a][bi], (int)lo.w);
-          for (int q = 0; q < 3; ++q) {
-            atomicMin(&bin_lo[a][bi][q], f2o(lo3[q]));
-            atomicMax(&bin_hi[a][bi][q], f2o(hi3[q]));
-          }
-        }
-      }
-      __syncthreads();
-      // SAH of every split plane (one thread per plane)
-      if (t < 3 * (kTopBins - 1)) {
-        int a = t / (kTopBins - 1), sp = t % (kTopBins - 1);
-        float l0[3] = {INFINITY, INFINITY, INFINITY}, l1[3] = {-INFINITY, -INFINITY, -INFINITY};
-        float r0[3] = {INFINITY, INFINITY, INFINITY}, r1[3] = {-INFINITY, -INFINITY, -INFINITY};
-        int nl = 0, nr = 0;
-        for (int k = 0; k < kTopBins; ++k) {
-          int cnt = bin_count[a][k];
-          if (cnt == 0) continue;
-          bool lft = k <= sp;
-          if (lft) nl += cnt;
-          else nr += cnt;
-          for (int q = 0; q < 3; ++q) {
-            float blo = o2f(bin_lo[a][k][q]), bhi = o2f(bin_hi[a][k][q]);
-            if (lft) {
-              l0[q] = fminf(l0[q], blo);
-              l1[q] = fmaxf(l1[q], bhi);
-            } else {
-              r0[q] = fminf(r0[q], blo);
-              r1[q] = fmaxf(r1[q], bhi);
-            }
-          }
-        }
-        float cost = INFINITY;
-        if (nl > 0 && nr > 0) {
-          float AL = area(make_float4(l0[0], l0[1], l0[2], 0), make_float4(l1[0], l1[1], l1[2], 0));
-          float AR = area(make_float4(r0[0], r0[1], r0[2], 0), make_float4(r1[0], r1[1], r1[2], 0));
-          cost = AL * (float)nl + AR * (float)nr;
-        }
-        s_cost[t] = cost;
-      }
-      __syncthreads();
-      if (t == 0) {
-        int best = -1;
-        float bc = INFINITY;
-        for (int k = 0; k < 3 * (kTopBins - 1); ++k)
-          if (s_cost[k] < bc) {
-            bc = s_cost[k];
-            best = k;
-          }
-        if (best < 0 || level >= kTopForceMedian) {
-          s_split_axis = -1;   // split the segment at its middle
-          s_split_bin = 0;
-        } else {
-          s_split_axis = best / (kTopBins - 1);
-          s_split_bin = best % (kTopBins - 1);
-        }
-      }
-      __syncthreads();
-      int ax = s_split_axis, sb = s_split_bin;
-      // stable partition into ids_out[b, e): left side ascending from b,
-      // right side descending from e-1, then the right side is reversed
-      nleft = m / 2;
-      bool by_position = ax < 0;   // sides by position (a split at the middle)
-      if (ax < 0) {
-        for (int k = b + t; k < e; k += 256) {
-          int c;
-          float4 lo, hi;
-          fetch(k, c, lo, hi);
-          ids_out[k] = c;
-        }
-      } else {
-        int run_l = 0, run_r = 0;
-        for (int k0 = b; k0 < e; k0 += 256) {
-          int k = k0 + t;
-          bool valid = k < e;
-          int c = 0;
-          bool left = false;
-          if (valid) {
-            float4 lo, hi;
-            fetch(k, c, lo, hi);
-            float cl = ax == 0 ? lo.x : (ax == 1 ? lo.y : lo.z);
-            float ch = ax == 0 ? hi.x : (ax == 1 ? hi.y : hi.z);
-            left = bin_of(0.5f * (cl + ch), clo[ax], cext[ax]) <= sb;
-          }
-          unsigned bl = __ballot_sync(0xffffffffu, left);
-          unsigned br = __ballot_sync(0xffffffffu, valid && !left);
-          if (lane == 0) s_wcount[w] = __popc(bl) | (__popc(br) << 16);
-          __syncthreads();
-          int before_l = 0, before_r = 0, chunk_l = 0, chunk_r = 0;
-          for (int q = 0; q < 8; ++q) {
-            int v = s_wcount[q];
-            if (q < w) {
-              before_l += v & 0xffff;
-              before_r += v >> 16;
-            }
-            chunk_l += v & 0xffff;
-            chunk_r += v >> 16;
-          }
-          unsigned lt = (1u << lane) - 1u;
-          if (valid && left) ids_out[b + run_l + before_l + __popc(bl & lt)] = c;
-          if (valid && !left) ids_out[e - 1 - (run_r + before_r + __popc(br & lt))] = c;
-          run_l += chunk_l;
-          run_r += chunk_r;
-          __syncthreads();
-        }
-        nleft = run_l;
-        int nr = m - nleft;
-        for (int k = t; k < nr / 2; k += 256) {
-          int x = ids_out[b + nleft + k];
-          ids_out[b + nleft + k] = ids_out[e - 1 - k];
-          ids_out[e - 1 - k] = x;
-        }
-        if (nleft == 0 || nleft == m) {   // not reachable with a finite SAH cost; keep a valid split
-          __syncthreads();
-          for (int k = b + t; k < e; k += 256) {
-            int c;
-            float4 lo, hi;
-            fetch(k, c, lo, hi);
-            ids_out[k] = c;
-          }
-          nleft = m / 2;
-          by_position = true;
-        }
-      }
-      __syncthreads();
-      // boxes of the two sides
-      {
-        float lo[2][3] = {{INFINITY, INFINITY, INFINITY}, {INFINITY, INFINITY, INFINITY}};
-        float hi[2][3] = {{-INFINITY, -INFINITY, -INFINITY}, {-INFINITY, -INFINITY, -INFINITY}};
-        for (int k = b + t; k < e; k += 256) {
-          int c;
-          float4 a, h;
-          fetch(k, c, a, h);
-          int side;
-          if (by_position) {
-            side = k < b + nleft ? 0 : 1;
-          } else {
-            float cl = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
-            float ch = ax == 0 ? h.x : (ax == 1 ? h.y : h.z);
-            side = bin_of(0.5f * (cl + ch), clo[ax], cext[ax]) <= sb ? 0 : 1;
-          }
-          lo[side][0] = fminf(lo[side][0], a.x);
-          lo[side][1] = fminf(lo[side][1], a.y);
-          lo[side][2] = fminf(lo[side][2], a.z);
-          hi[side][0] = fmaxf(hi[side][0], h.x);
-          hi[side][1] = fmaxf(hi[side][1], h.y);
-          hi[side][2] = fmaxf(hi[side][2], h.z);
-        }
-        for (int side = 0; side < 2; ++side)
-          for (int q = 0; q < 3; ++q) {
-            if (lo[side][q] <= hi[side][q]) {
-              atomicMin(&s_box[side][q], f2o(lo[side][q]));
-              atomicMax(&s_box[side][q + 3], f2o(hi[side][q]));
-            }
-          }
-      }
-      __syncthreads();
-      for (int side = 0; side < 2; ++side) {
-        slo[side] = make_float4(o2f(s_box[side][0]), o2f(s_box[side][1]), o2f(s_box[side][2]), 0.f);
-        shi[side] = make_float4(o2f(s_box[side][3]), o2f(s_box[side][4]), o2f(s_box[side][5]), 0.f);
-      }
+      nleft = split_large(level, b, e, ids_in, ids_out, clu_lo, clu_hi, cache_cap, slo, shi);
     }
     if (t < 2) {
       int cb = t == 0 ? b : b + nleft;
       int ce = t == 0 ? b + nleft : e;
-      float4 lo = slo[t], hi = shi[t];
+      float4 lo = t == 0 ? slo[0] : slo[1], hi = t == 0 ? shi[0] : shi[1];
       int link;
       if (ce - cb == 1) {
         int c = ids_out[cb];
@@ -1233,11 +1286,17 @@ __device__ void build_small_subtree(int4 item, int top_base, const int* ids, con
     int best_ax = 0, best_k = -1;
     int rank_ax[3];
     float bl[7], br[7];
+    // the lanes' segments differ, so every test below is written without
+    // short-circuit operators: a branch on them would diverge
+    const unsigned seg_w = (unsigned)(se - sb);
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
+      const float ca = cen[a];
       int rank = 0;
+#pragma unroll
       for (int j = 0; j < 32; ++j) {
-        float cj = __shfl_sync(FULL, cen[a], j);
-        rank += (j >= sb && j < se && (cj < cen[a] || (cj == cen[a] && j < lane))) ? 1 : 0;
+        float cj = __shfl_sync(FULL, ca, j);
+        rank += (int)(((unsigned)(j - sb) < seg_w) & ((cj < ca) | ((cj == ca) & (j < lane))));
       }
       rank_ax[a] = rank;
       s_idx[sb + rank] = lane;
@@ -1263,10 +1322,9 @@ __device__ void build_small_subtree(int4 item, int top_base, const int* ids, con
       for (int o = 1; o < 32; o <<= 1) {
         float oc = __shfl_up_sync(FULL, cost, o);
         int op = __shfl_up_sync(FULL, pos, o);
-        if (lane - o >= sb && (oc < cost || (oc == cost && op < pos))) {
-          cost = oc;
-          pos = op;
-        }
+        const bool take = (lane - o >= sb) & ((oc < cost) | ((oc == cost) & (op < pos)));
+        cost = take ? oc : cost;
+        pos = take ? op : pos;
       }
       const float seg_cost = __shfl_sync(FULL, cost, se - 1);
       const int seg_pos = __shfl_sync(FULL, pos, se - 1);
@@ -1293,7 +1351,7 @@ __device__ void build_small_subtree(int4 item, int top_base, const int* ids, con
       for (int q = 0; q < 7; ++q) bl[q] = br[q] = q < 3 ? -INFINITY : INFINITY;
     }
     // the lanes in the chosen order: left child [sb, best_k], right child [best_k + 1, se)
-    const int dst = act ? sb + rank_ax[best_ax] : lane;
+    const int dst = act ? sb + (best_ax == 0 ? rank_ax[0] : best_ax == 1 ? rank_ax[1] : rank_ax[2]) : lane;
     s_c[dst] = c;
     s_lo[dst] = lo;
     s_hi[dst] = hi;
@@ -1344,7 +1402,10 @@ __device__ void build_small_subtree(int4 item, int top_base, const int* ids, con
   }
 }
 
-// Every small segment of the top-level rebuild, one warp each.
+// Every small segment of the top-level rebuild, one warp each.  Segment i
+// goes to warp i / gridDim of block i % gridDim, so that the segments
+// spread over all SMs (a warp's rounds are latency bound) before any block
+// takes a second one.
 __device__ __forceinline__ void top_small_body(const int* seg_count, const int4* small_seg, int top_base,
                                                const int* clu_a, const int* clu_b, const int* __restrict__ clu_link,
                                                const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
@@ -1354,7 +1415,7 @@ __device__ __forceinline__ void top_small_body(const int* seg_count, const int4*
   const int w = threadIdx.x >> 5;
   const int n_small = __ldcg(&seg_count[kTopMaxLevels + 2]);
   const int warps = (int)(gridDim.x * (blockDim.x >> 5));
-  for (int i = (int)(blockIdx.x * (blockDim.x >> 5)) + w; i < n_small; i += warps) {
+  for (int i = w * (int)gridDim.x + (int)blockIdx.x; i < n_small; i += warps) {
     int4 item = __ldcg(&small_seg[i]);
     // the cluster ids of a level-L segment are in the buffer its parent's split wrote
     const int* ids = (item.w & 1) ? clu_b : clu_a;
@@ -1752,7 +1813,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     int top_grid = std::max(1, 2 * s->sm_count);
     // dynamic shared memory: the cluster cache of one segment
     int cache_cap = kTopCache;
-    const size_t dyn = (size_t)cache_cap * 36;
+    const size_t dyn = (size_t)cache_cap * 40;   // per cached cluster: lo, hi, id, partitioned id
     static int coop_blocks = -1;
     if (coop_blocks < 0) {
       int coop = 0, per_sm = 0;
