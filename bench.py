@@ -44,7 +44,7 @@ BYTES_NODE = 128
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "a6b916224dded734"
+PROFILED_SHA = "20e6f594cce21065"
 PROFILED_TRAFFIC = {
     0: (24_692_736 + 122_469_888 + 5_493_760 + 2_560 + 7_366_656,
         "k_trace<1,0,0> + k_trace<0,0,0> (depth 1) + k_paths<0,0> (depths 2-5): profiles/launches_terrain1080p_d5.md"),

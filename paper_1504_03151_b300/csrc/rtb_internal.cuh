@@ -175,6 +175,7 @@ struct CamBasis;
 // Pinhole camera basis of a frame (host FP32 arithmetic) and its validation.
 CamBasis camera_basis(const rt_camera* c, int W, int H);
 bool finite_cam(const rt_camera* c);
+void preload_frame_kernels(int device);   // loads the frame kernels in a fixed order (once per device)
 
 // ---------------------------------------------------------------------------
 // Device math

@@ -196,6 +196,7 @@ rt_status rt_scene_create(const rt_sphere* spheres, size_t n_spheres, const rt_t
   }
   cudaGetDevice(&s->device);
   cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  preload_frame_kernels(s->device);
   s->n_spheres = (int64_t)n_spheres;
   s->n_tris = (int64_t)n_triangles;
   s->n_prims = s->n_spheres + s->n_tris;
