@@ -722,6 +722,84 @@ __device__ __forceinline__ int bin_of(float c, float lo, float ext) {
   return min(max(bi, 0), kTopBins - 1);
 }
 
+// The cheapest of the 3 x (kTopBins - 1) split planes of a set of bins
+// (SAH A_L N_L + A_R N_R, N in primitives): warp a scans axis a, lane k
+// holding bin k, with prefix and suffix scans of the counts and bounds;
+// the plane index is a * (kTopBins - 1) + (last bin on the left).  Returns
+// the same index in every thread, the lowest on ties, or -1 when no plane
+// has a finite cost.  All threads of the block call it (it synchronises).
+__device__ __forceinline__ int best_plane(const int (*cnt)[kTopBins], const int (*blo)[kTopBins][3],
+                                          const int (*bhi)[kTopBins][3], float* s_bc, int* s_bk) {
+  const unsigned FULL = 0xffffffffu;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (w < 3) {
+    const bool in = lane < kTopBins;
+    int pn = in ? cnt[w][lane] : 0, sn = pn;
+    float pl[3], ph[3], sl[3], sh[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      pl[q] = sl[q] = in ? o2f(blo[w][lane][q]) : INFINITY;
+      ph[q] = sh[q] = in ? o2f(bhi[w][lane][q]) : -INFINITY;
+    }
+#pragma unroll
+    for (int o = 1; o < kTopBins; o <<= 1) {
+      const int xn = __shfl_up_sync(FULL, pn, o), yn = __shfl_down_sync(FULL, sn, o);
+      const bool up = lane >= o, down = lane + o < kTopBins;
+      pn += up ? xn : 0;
+      sn += down ? yn : 0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float xl = __shfl_up_sync(FULL, pl[q], o), xh = __shfl_up_sync(FULL, ph[q], o);
+        const float yl = __shfl_down_sync(FULL, sl[q], o), yh = __shfl_down_sync(FULL, sh[q], o);
+        pl[q] = up ? fminf(pl[q], xl) : pl[q];
+        ph[q] = up ? fmaxf(ph[q], xh) : ph[q];
+        sl[q] = down ? fminf(sl[q], yl) : sl[q];
+        sh[q] = down ? fmaxf(sh[q], yh) : sh[q];
+      }
+    }
+    // the right side of the plane after bin `lane`: the suffix from the next bin
+    const int rn = __shfl_down_sync(FULL, sn, 1);
+    float rl[3], rh[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      rl[q] = __shfl_down_sync(FULL, sl[q], 1);
+      rh[q] = __shfl_down_sync(FULL, sh[q], 1);
+    }
+    float cost = INFINITY;
+    int k = INT_MAX;
+    if (lane < kTopBins - 1) {
+      k = w * (kTopBins - 1) + lane;
+      if (pn > 0 && rn > 0) {
+        const float AL = area(make_float4(pl[0], pl[1], pl[2], 0.f), make_float4(ph[0], ph[1], ph[2], 0.f));
+        const float AR = area(make_float4(rl[0], rl[1], rl[2], 0.f), make_float4(rh[0], rh[1], rh[2], 0.f));
+        cost = AL * (float)pn + AR * (float)rn;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oc = __shfl_xor_sync(FULL, cost, o);
+      const int ok = __shfl_xor_sync(FULL, k, o);
+      const bool take = (oc < cost) | ((oc == cost) & (ok < k));
+      cost = take ? oc : cost;
+      k = take ? ok : k;
+    }
+    if (lane == 0) {
+      s_bc[w] = cost;
+      s_bk[w] = k;
+    }
+  }
+  __syncthreads();
+  float bc = INFINITY;
+  int bk = -1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float c = s_bc[a];
+    bk = c < bc ? s_bk[a] : bk;
+    bc = c < bc ? c : bc;
+  }
+  return bk;
+}
+
 // Split of a segment of at most 256 clusters, one cluster per thread, held
 // in registers from one load: the same bins, SAH costs, choice and stable
 // partition as the general path below, with fewer passes and barriers.
@@ -732,8 +810,8 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
   __shared__ int s_cb[6];
   __shared__ int s_cnt[3][kTopBins];
   __shared__ int s_blo[3][kTopBins][3], s_bhi[3][kTopBins][3];
-  __shared__ float s_cost[3 * (kTopBins - 1)];
-  __shared__ int s_best;
+  __shared__ float s_bc[3];
+  __shared__ int s_bk[3];
   __shared__ int s_wl[8], s_wr[8];
   __shared__ int s_box[2][6];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, m = e - b;
@@ -794,59 +872,9 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
     }
   }
   __syncthreads();
-  if (t < 3 * (kTopBins - 1)) {
-    int a = t / (kTopBins - 1), sp = t % (kTopBins - 1);
-    float l0[3] = {INFINITY, INFINITY, INFINITY}, l1[3] = {-INFINITY, -INFINITY, -INFINITY};
-    float r0[3] = {INFINITY, INFINITY, INFINITY}, r1[3] = {-INFINITY, -INFINITY, -INFINITY};
-    int nl = 0, nr = 0;
-    for (int k = 0; k < kTopBins; ++k) {
-      int cnt = s_cnt[a][k];
-      if (cnt == 0) continue;
-      bool lft = k <= sp;
-      if (lft) nl += cnt;
-      else nr += cnt;
-      for (int q = 0; q < 3; ++q) {
-        float blo = o2f(s_blo[a][k][q]), bhi = o2f(s_bhi[a][k][q]);
-        if (lft) {
-          l0[q] = fminf(l0[q], blo);
-          l1[q] = fmaxf(l1[q], bhi);
-        } else {
-          r0[q] = fminf(r0[q], blo);
-          r1[q] = fmaxf(r1[q], bhi);
-        }
-      }
-    }
-    float cost = INFINITY;
-    if (nl > 0 && nr > 0) {
-      float AL = area(make_float4(l0[0], l0[1], l0[2], 0), make_float4(l1[0], l1[1], l1[2], 0));
-      float AR = area(make_float4(r0[0], r0[1], r0[2], 0), make_float4(r1[0], r1[1], r1[2], 0));
-      cost = AL * (float)nl + AR * (float)nr;
-    }
-    s_cost[t] = cost;
-  }
-  __syncthreads();
-  if (w == 0) {
-    // the cheapest plane, ties to the lower index (as a serial scan would pick)
-    float bc = INFINITY;
-    int bk = -1;
-    for (int k = lane; k < 3 * (kTopBins - 1); k += 32) {
-      if (s_cost[k] < bc) {
-        bc = s_cost[k];
-        bk = k;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      float oc = __shfl_xor_sync(0xffffffffu, bc, o);
-      int ok = __shfl_xor_sync(0xffffffffu, bk, o);
-      if (oc < bc || (oc == bc && ok >= 0 && (bk < 0 || ok < bk))) {
-        bc = oc;
-        bk = ok;
-      }
-    }
-    if (lane == 0) s_best = (bk < 0 || level >= kTopForceMedian) ? -1 : bk;
-  }
-  __syncthreads();
-  const int best = s_best;
+  int best = best_plane(s_cnt, s_blo, s_bhi, s_bc, s_bk);
+  if (level >= kTopForceMedian) best = -1;
+
   bool left;
   if (best < 0) {
     left = t < m / 2;   // split at the middle, order kept
@@ -919,8 +947,8 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
   __shared__ int s_cb[6];
   __shared__ int bin_count[3][kTopBins];
   __shared__ int bin_lo[3][kTopBins][3], bin_hi[3][kTopBins][3];
-  __shared__ float s_cost[3 * (kTopBins - 1)];
-  __shared__ int s_split_axis, s_split_bin;
+  __shared__ float s_bc[3];
+  __shared__ int s_bk[3];
   __shared__ int s_wl[8], s_wr[8];
   __shared__ int s_box[2][6];
   extern __shared__ float4 s_dyn[];
@@ -1031,56 +1059,11 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
     }
   }
   __syncthreads();
-  // SAH of every split plane (one thread per plane)
-  if (t < 3 * (kTopBins - 1)) {
-    int a = t / (kTopBins - 1), sp = t % (kTopBins - 1);
-    float l0[3] = {INFINITY, INFINITY, INFINITY}, l1[3] = {-INFINITY, -INFINITY, -INFINITY};
-    float r0[3] = {INFINITY, INFINITY, INFINITY}, r1[3] = {-INFINITY, -INFINITY, -INFINITY};
-    int nl = 0, nr = 0;
-    for (int k = 0; k < kTopBins; ++k) {
-      int cnt = bin_count[a][k];
-      if (cnt == 0) continue;
-      bool lft = k <= sp;
-      if (lft) nl += cnt;
-      else nr += cnt;
-      for (int q = 0; q < 3; ++q) {
-        float blo = o2f(bin_lo[a][k][q]), bhi = o2f(bin_hi[a][k][q]);
-        if (lft) {
-          l0[q] = fminf(l0[q], blo);
-          l1[q] = fmaxf(l1[q], bhi);
-        } else {
-          r0[q] = fminf(r0[q], blo);
-          r1[q] = fmaxf(r1[q], bhi);
-        }
-      }
-    }
-    float cost = INFINITY;
-    if (nl > 0 && nr > 0) {
-      float AL = area(make_float4(l0[0], l0[1], l0[2], 0), make_float4(l1[0], l1[1], l1[2], 0));
-      float AR = area(make_float4(r0[0], r0[1], r0[2], 0), make_float4(r1[0], r1[1], r1[2], 0));
-      cost = AL * (float)nl + AR * (float)nr;
-    }
-    s_cost[t] = cost;
-  }
-  __syncthreads();
-  if (t == 0) {
-    int best = -1;
-    float bc = INFINITY;
-    for (int k = 0; k < 3 * (kTopBins - 1); ++k)
-      if (s_cost[k] < bc) {
-        bc = s_cost[k];
-        best = k;
-      }
-    if (best < 0 || level >= kTopForceMedian) {
-      s_split_axis = -1;   // split the segment at its middle
-      s_split_bin = 0;
-    } else {
-      s_split_axis = best / (kTopBins - 1);
-      s_split_bin = best % (kTopBins - 1);
-    }
-  }
-  __syncthreads();
-  const int ax = s_split_axis, sb = s_split_bin;
+  // the cheapest split plane; by position (ax < 0) when none has a finite
+  // cost or the level is deep
+  const int best = best_plane(bin_count, bin_lo, bin_hi, s_bc, s_bk);
+  const int ax = (best < 0 || level >= kTopForceMedian) ? -1 : best / (kTopBins - 1);
+  const int sb = ax < 0 ? 0 : best % (kTopBins - 1);
   // right side (1) or left (0) of position k; by position: the halves in order
   bool by_position = ax < 0;
   const float alo = ax == 0 ? clo[0] : (ax == 1 ? clo[1] : clo[2]);
