@@ -218,7 +218,8 @@ rt_status rt_scene_set_area_lights(rt_scene* s, const rt_area_light* lights, siz
 rt_status rt_scene_update(rt_scene* s, const rt_sphere* spheres, const rt_triangle* triangles,
                           void* stream);
 
-/* Builds the BVH on the device: 30-bit Morton codes, radix sort, LBVH
+/* Builds the BVH on the device: 30-bit Morton codes, radix sort (by the
+ * codes' top 24 bits for at most 2^17 primitives, else all 30), LBVH
  * hierarchy, bottom-up boxes, binned-SAH rebuild of the top levels and
  * SAH leaf collapsing.  Stream-ordered; rebuild allowed at any time. */
 rt_status rt_bvh_build(rt_scene* s, void* stream);
@@ -232,7 +233,9 @@ rt_status rt_bvh_get_info(rt_scene* s, rt_bvh_info* info, void* stream);
  * two int32 child links (>= 0: node index; < 0: leaf ~(start << 3 |
  * count - 1) over prim_order positions); two unused words.  prim_order:
  * n_prims int32 (leaf order -> primitive id); morton: n_prims uint32
- * sorted codes.  Any pointer may be NULL. */
+ * sorted codes, in leaf order, with the bits below the sort key cleared (the
+ * low 6 bits for at most 2^17 primitives, none above).  Any pointer may be
+ * NULL. */
 rt_status rt_bvh_export(rt_scene* s, float* nodes, int64_t nodes_capacity, int32_t* prim_order,
                         uint32_t* morton, void* stream);
 

@@ -362,6 +362,9 @@ def test_morton_codes_against_cpu_interleave():
         return out
 
     code = (spread(q[:, 0]) << 2) | (spread(q[:, 1]) << 1) | spread(q[:, 2])
+    # the sort key is the code's top 24 bits for at most 2^17 primitives
+    assert n <= 1 << 17
+    code &= ~np.int64(63)
     got = morton.astype(np.int64)
     exp = code[order]
     # quantisation may differ by one cell where a centroid sits on a cell edge
