@@ -568,12 +568,21 @@ __device__ __forceinline__ ChildInfo child_info(int c, const unsigned* __restric
 
 // The box, SAH costs and collapse decision of internal node `node`, from
 // its two children (both done).
-__device__ __forceinline__ void refit_node(int node, const unsigned* __restrict__ vals,
+// The second of a node's two children to arrive refits it: returns the
+// count before this arrival.  Acquire-release at device scope: the
+// arriving thread's earlier writes (its child's box and costs) are visible
+// to whoever arrives after it, and the second thread sees the first's.
+__device__ __forceinline__ int arrive(int* flag) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(flag) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void refit_node(int node, int l, int r, const unsigned* __restrict__ vals,
                                            const float4* __restrict__ aabb_lo, const float4* __restrict__ aabb_hi,
-                                           const int* __restrict__ lch, const int* __restrict__ rch, int2 rg,
-                                           float4* node_lo, float4* node_hi, float* cost_lbvh) {
-  ChildInfo a = child_info(lch[node], vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
-  ChildInfo b = child_info(rch[node], vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
+                                           int2 rg, float4* node_lo, float4* node_hi, float* cost_lbvh) {
+  ChildInfo a = child_info(l, vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
+  ChildInfo b = child_info(r, vals, aabb_lo, aabb_hi, node_lo, node_hi, cost_lbvh);
   float4 lo = make_float4(fminf(a.lo.x, b.lo.x), fminf(a.lo.y, b.lo.y), fminf(a.lo.z, b.lo.z), 0.f);
   float4 hi = make_float4(fmaxf(a.hi.x, b.hi.x), fmaxf(a.hi.y, b.hi.y), fmaxf(a.hi.z, b.hi.z), 0.f);
   float A = area(lo, hi), Aa = area(a.lo, a.hi), Ab = area(b.lo, b.hi);
@@ -610,13 +619,13 @@ __global__ void k_refit(int n, int cut, const unsigned* __restrict__ vals, const
   // a radix tree has at most n-1 ancestors above a leaf; the bound and the
   // index check only guard against a malformed tree
   for (int it = 0; node >= 0 && node < n - 1 && it < n; ++it) {
+    // the links are read before the flag: this kernel does not change them
     const int2 rg = range[node];
+    const int l = lch[node], r = rch[node], up = parent[node];
     if (rg.y - rg.x + 1 > cut) return;
-    __threadfence();
-    if (atomicAdd(&flags[node], 1) == 0) return;
-    __threadfence();
-    refit_node(node, vals, aabb_lo, aabb_hi, lch, rch, rg, node_lo, node_hi, cost_lbvh);
-    node = parent[node];
+    if (arrive(&flags[node]) == 0) return;
+    refit_node(node, l, r, vals, aabb_lo, aabb_hi, rg, node_lo, node_hi, cost_lbvh);
+    node = up;
   }
 }
 
@@ -640,7 +649,7 @@ __global__ void k_refit_upper(int n, int cut, const unsigned* __restrict__ vals,
   __threadfence();
   int node = i;
   for (int it = 0; it < n; ++it) {
-    refit_node(node, vals, aabb_lo, aabb_hi, lch, rch, rg, node_lo, node_hi, cost_lbvh);
+    refit_node(node, lch[node], rch[node], vals, aabb_lo, aabb_hi, rg, node_lo, node_hi, cost_lbvh);
     node = parent[node];
     if (node < 0 || node >= n - 1) return;
     rg = range[node];
