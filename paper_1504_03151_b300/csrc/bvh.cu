@@ -1286,70 +1286,108 @@ __device__ void build_small_subtree(int4 item, int top_base, const int* ids, con
   // this lane's segment [sb, se) of lanes; lanes without a cluster are finished singletons
   int sb = own ? 0 : lane, se = own ? m : lane + 1;
   int node = item.z, level = item.w;
+  // The subtree has m - 1 inner nodes.  All but its root (allocated by the
+  // level that made the segment) come from one block of consecutive ids,
+  // reserved with one atomic, in breadth-first order.
+  int sub_base = 0, sub_next = 0;
+  if (lane == 0 && m > 2) sub_base = atomicAdd(top_count, m - 2);
+  sub_base = __shfl_sync(FULL, sub_base, 0);
   for (int round = 0; round < 32; ++round) {
     const bool act = se - sb >= 2;
     if (!__any_sync(FULL, act)) break;
     const float cen[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
-    float best = INFINITY;
-    int best_ax = 0, best_k = -1;
-    int rank_ax[3];
-    float bl[7], br[7];
-    // the lanes' segments differ, so every test below is written without
-    // short-circuit operators: a branch on them would diverge
+    // The three axes advance together, so that a lone warp has three
+    // independent shuffle chains in flight.  The lanes' segments differ, so
+    // every test below is written without short-circuit operators: a branch
+    // on them would diverge.
     const unsigned seg_w = (unsigned)(se - sb);
+    int rank[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const bool in = (unsigned)(j - sb) < seg_w;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float cj = __shfl_sync(FULL, cen[a], j);
+        rank[a] += (int)(in & ((cj < cen[a]) | ((cj == cen[a]) & (j < lane))));
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s_idx[32 * a + sb + rank[a]] = lane;
+    __syncwarp();
+    int src[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) src[a] = s_idx[32 * a + lane];
+    __syncwarp();
+    // per axis, boxes and primitive counts of the prefixes and suffixes of
+    // the segment's clusters in that axis' order
+    const float v[7] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, lo.w};
+    float pre[3][7], suf[3][7], right[3][7];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int q = 0; q < 7; ++q) pre[a][q] = suf[a][q] = __shfl_sync(FULL, v[q], src[a]);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const bool up = lane - o >= sb, down = lane + o < se;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+          const float x = __shfl_up_sync(FULL, pre[a][q], o);
+          const float y = __shfl_down_sync(FULL, suf[a][q], o);
+          pre[a][q] = up ? combine7(q, pre[a][q], x) : pre[a][q];
+          suf[a][q] = down ? combine7(q, suf[a][q], y) : suf[a][q];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int q = 0; q < 7; ++q) right[a][q] = __shfl_down_sync(FULL, suf[a][q], 1);   // suffix from the next position
+    // SAH of the split after each position; per axis the cheapest in the
+    // segment, ties to the lower position
+    const bool valid = act & (lane + 1 < se);
+    float cost[3];
+    int pos[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float ca = cen[a];
-      int rank = 0;
+      cost[a] = valid ? box_area7(pre[a]) * pre[a][6] + box_area7(right[a]) * right[a][6] : INFINITY;
+      pos[a] = lane;
+    }
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        float cj = __shfl_sync(FULL, ca, j);
-        rank += (int)(((unsigned)(j - sb) < seg_w) & ((cj < ca) | ((cj == ca) & (j < lane))));
+    for (int o = 1; o < 32; o <<= 1) {
+      const bool up = lane - o >= sb;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float oc = __shfl_up_sync(FULL, cost[a], o);
+        const int op = __shfl_up_sync(FULL, pos[a], o);
+        const bool take = up & ((oc < cost[a]) | ((oc == cost[a]) & (op < pos[a])));
+        cost[a] = take ? oc : cost[a];
+        pos[a] = take ? op : pos[a];
       }
-      rank_ax[a] = rank;
-      s_idx[sb + rank] = lane;
-      __syncwarp();
-      const int src = s_idx[lane];
-      __syncwarp();
-      float v[7] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, lo.w};
-      float pre[7], suf[7];
-      for (int q = 0; q < 7; ++q) pre[q] = suf[q] = __shfl_sync(FULL, v[q], src);
-      for (int o = 1; o < 32; o <<= 1) {
-        for (int q = 0; q < 7; ++q) {
-          float x = __shfl_up_sync(FULL, pre[q], o);
-          float y = __shfl_down_sync(FULL, suf[q], o);
-          if (lane - o >= sb) pre[q] = combine7(q, pre[q], x);
-          if (lane + o < se) suf[q] = combine7(q, suf[q], y);
-        }
-      }
-      float right[7];
-      for (int q = 0; q < 7; ++q) right[q] = __shfl_down_sync(FULL, suf[q], 1);   // suffix from the next position
-      const bool valid = act && lane + 1 < se;
-      float cost = valid ? box_area7(pre) * pre[6] + box_area7(right) * right[6] : INFINITY;
-      int pos = lane;
-      for (int o = 1; o < 32; o <<= 1) {
-        float oc = __shfl_up_sync(FULL, cost, o);
-        int op = __shfl_up_sync(FULL, pos, o);
-        const bool take = (lane - o >= sb) & ((oc < cost) | ((oc == cost) & (op < pos)));
-        cost = take ? oc : cost;
-        pos = take ? op : pos;
-      }
-      const float seg_cost = __shfl_sync(FULL, cost, se - 1);
-      const int seg_pos = __shfl_sync(FULL, pos, se - 1);
-      float cl[7], cr[7];
-      for (int q = 0; q < 7; ++q) {
-        cl[q] = __shfl_sync(FULL, pre[q], seg_pos);
-        cr[q] = __shfl_sync(FULL, right[q], seg_pos);
-      }
-      if (seg_cost < best) {
-        best = seg_cost;
-        best_ax = a;
-        best_k = seg_pos;
-        for (int q = 0; q < 7; ++q) {
-          bl[q] = cl[q];
-          br[q] = cr[q];
-        }
-      }
+    }
+    // the cheapest axis, ties to the lower axis
+    float best = INFINITY;
+    int best_ax = 0, best_k = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float seg_cost = __shfl_sync(FULL, cost[a], se - 1);
+      const int seg_pos = __shfl_sync(FULL, pos[a], se - 1);
+      const bool better = seg_cost < best;
+      best = better ? seg_cost : best;
+      best_ax = better ? a : best_ax;
+      best_k = better ? seg_pos : best_k;
+    }
+    // the two children's boxes: the chosen axis' prefix at best_k and the
+    // suffix after it (the source lane is in this segment, so it chose the
+    // same axis)
+    const int from = best_k < 0 ? lane : best_k;
+    float bl[7], br[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const float p = best_ax == 0 ? pre[0][q] : (best_ax == 1 ? pre[1][q] : pre[2][q]);
+      const float r = best_ax == 0 ? right[0][q] : (best_ax == 1 ? right[1][q] : right[2][q]);
+      bl[q] = __shfl_sync(FULL, p, from);
+      br[q] = __shfl_sync(FULL, r, from);
     }
     if (act && best_k < 0) {
       // no finite cost (not reachable for finite boxes): halves of the x
@@ -1359,7 +1397,7 @@ __device__ void build_small_subtree(int4 item, int top_base, const int* ids, con
       for (int q = 0; q < 7; ++q) bl[q] = br[q] = q < 3 ? -INFINITY : INFINITY;
     }
     // the lanes in the chosen order: left child [sb, best_k], right child [best_k + 1, se)
-    const int dst = act ? sb + (best_ax == 0 ? rank_ax[0] : best_ax == 1 ? rank_ax[1] : rank_ax[2]) : lane;
+    const int dst = act ? sb + (best_ax == 0 ? rank[0] : best_ax == 1 ? rank[1] : rank[2]) : lane;
     s_c[dst] = c;
     s_lo[dst] = lo;
     s_hi[dst] = hi;
@@ -1370,23 +1408,31 @@ __device__ void build_small_subtree(int4 item, int top_base, const int* ids, con
     __syncwarp();
     const int k = act ? best_k : lane;
     const int c_right = __shfl_sync(FULL, c, min(k + 1, 31));
+    const float h_right = __shfl_sync(FULL, hi.w, min(k + 1, 31));   // the right cluster's height
+    // this round's new nodes, numbered in lane order (left before right)
+    // after those of the earlier rounds
+    const bool lead = act && lane == sb;
+    const bool new_l = lead && k + 1 - sb > 1, new_r = lead && se - (k + 1) > 1;
+    const unsigned ml = __ballot_sync(FULL, new_l), mr = __ballot_sync(FULL, new_r);
+    const unsigned below = (1u << lane) - 1u;
+    const int id_l = sub_base + sub_next + __popc(ml & below) + __popc(mr & below);
+    sub_next += __popc(ml) + __popc(mr);
     int cnode_l = -1, cnode_r = -1;
-    if (act && lane == sb) {
-      const int nl = k + 1 - sb, nr = se - (k + 1);
+    if (lead) {
       int link_l, link_r;
-      if (nl == 1) {
+      if (!new_l) {
         link_l = clu_link[c];
         atomicMax(&info->height, level + 1 + __float_as_int(hi.w));
       } else {
-        cnode_l = atomicAdd(top_count, 1);
+        cnode_l = id_l;
         link_l = top_base + cnode_l;
         atomicMax(&info->height, level + 2);
       }
-      if (nr == 1) {
+      if (!new_r) {
         link_r = clu_link[c_right];
-        atomicMax(&info->height, level + 1 + __float_as_int(clu_hi[c_right].w));
+        atomicMax(&info->height, level + 1 + __float_as_int(h_right));
       } else {
-        cnode_r = atomicAdd(top_count, 1);
+        cnode_r = id_l + (new_l ? 1 : 0);
         link_r = top_base + cnode_r;
         atomicMax(&info->height, level + 2);
       }
@@ -1418,7 +1464,7 @@ __device__ __forceinline__ void top_small_body(const int* seg_count, const int4*
                                                const int* clu_a, const int* clu_b, const int* __restrict__ clu_link,
                                                const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
                                                int* top_count, float4* nodes, BuildInfo* info) {
-  __shared__ int s_idx[8][32], s_c[8][32];
+  __shared__ int s_idx[8][3 * 32], s_c[8][32];
   __shared__ float4 s_lo[8][32], s_hi[8][32];
   const int w = threadIdx.x >> 5;
   const int n_small = __ldcg(&seg_count[kTopMaxLevels + 2]);
