@@ -1561,27 +1561,45 @@ __global__ void __launch_bounds__(256) k_collapse4(const float4* __restrict__ bi
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= n_bin) return;
   if (x >= n_lbvh && (top_count == nullptr || x - n_lbvh >= __ldg(top_count))) return;   // an unused slot
+  // Slots are indexed only by constants once the loops unroll, so they stay
+  // in registers; the slot chosen at run time is written through selects.
   float lo[4][3], hi[4][3];
-  int link[4];
+  int link[4] = {kEmptyLink, kEmptyLink, kEmptyLink, kEmptyLink};
   int ns = 2;
   bin_child(bin, x, 0, lo[0], hi[0], link[0]);
   bin_child(bin, x, 1, lo[1], hi[1], link[1]);
-  while (ns < 4) {
+#pragma unroll
+  for (int m = 2; m < 4; ++m) {
+    // the inner child of largest area (the first on ties) is opened
     int best = -1;
     float ba = -1.f;
-    for (int k = 0; k < ns; ++k) {
-      if (link[k] < 0 || link[k] >= n_bin) continue;   // a leaf stays a leaf
-      float a = half_area(lo[k], hi[k]);
-      if (a > ba) {
-        ba = a;
-        best = k;
-      }
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      const bool inner = link[k] >= 0 && link[k] < n_bin;   // a leaf stays a leaf
+      const float a = inner ? half_area(lo[k], hi[k]) : -1.f;
+      const bool take = inner && a > ba;
+      ba = take ? a : ba;
+      best = take ? k : best;
     }
     if (best < 0) break;
-    int c = link[best];
-    bin_child(bin, c, 1, lo[ns], hi[ns], link[ns]);
-    bin_child(bin, c, 0, lo[best], hi[best], link[best]);
-    ++ns;
+    int c = link[0];
+#pragma unroll
+    for (int k = 1; k < m; ++k) c = best == k ? link[k] : c;
+    float l0[3], h0[3];
+    int c0;
+    bin_child(bin, c, 1, lo[m], hi[m], link[m]);
+    bin_child(bin, c, 0, l0, h0, c0);
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      const bool here = best == k;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo[k][a] = here ? l0[a] : lo[k][a];
+        hi[k][a] = here ? h0[a] : hi[k][a];
+      }
+      link[k] = here ? c0 : link[k];
+    }
+    ns = m + 1;
   }
   float r[6][4];
   int out_link[4];
