@@ -46,9 +46,9 @@ PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b3
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
 PROFILED_SHA = "20e6f594cce21065"
 PROFILED_TRAFFIC = {
-    0: (24_692_736 + 122_469_888 + 5_493_760 + 2_560 + 7_366_656,
+    0: (24_637_952 + 122_092_800 + 5_496_576 + 1_024 + 7_396_096,
         "k_trace<1,0,0> + k_trace<0,0,0> (depth 1) + k_paths<0,0> (depths 2-5): profiles/launches_terrain1080p_d5.md"),
-    1: (180_072_704 + 4_691_200 + 5_760_000, "k_shadow<0> (depths 0 and 1): profiles/launches_terrain1080p_d5.md"),
+    1: (179_979_264 + 4_312_064 + 5_756_672, "k_shadow<0> (depths 0 and 1): profiles/launches_terrain1080p_d5.md"),
 }
 
 
