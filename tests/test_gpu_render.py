@@ -26,6 +26,12 @@ def small_terrain(w=96, h=64, depth=5, seed=7):
     return S.scene_terrain(seed=seed, width=w, height=h, max_depth=depth, cells=(16, 12), n_ico=6, ico_level=2)
 
 
+def large_terrain():
+    """222,208 triangles: above 2^17, so the build sorts all 30 bits of the
+    Morton codes (four passes) instead of their top 24."""
+    return S.scene_terrain(seed=3, width=64, height=48, cells=(384, 256))
+
+
 # ---------------------------------------------------------------------------
 # closed forms on the GPU
 # ---------------------------------------------------------------------------
@@ -215,9 +221,10 @@ def _child_box(nodes, node, c):
     return np.array([n[4], n[6], n[10]]), np.array([n[5], n[7], n[11]])
 
 
-@pytest.mark.parametrize("which", ["spheres8", "terrain_small", "terrain"])
+@pytest.mark.parametrize("which", ["spheres8", "terrain_small", "terrain", "terrain_large"])
 def test_bvh_structure_invariants(which):
-    sc = {"spheres8": S.scene_spheres8, "terrain_small": small_terrain, "terrain": S.scene_terrain}[which]()
+    sc = {"spheres8": S.scene_spheres8, "terrain_small": small_terrain, "terrain": S.scene_terrain,
+          "terrain_large": large_terrain}[which]()
     n = sc.n_prims
     scene = rtb.Scene(sc).build()
     info = rtb.rt_bvh_get_info(scene.handle)
@@ -344,8 +351,9 @@ def test_wide_bvh_structure(which):
     assert depth <= info["max_depth"]
 
 
-def test_morton_codes_against_cpu_interleave():
-    sc = S.scene_terrain()
+@pytest.mark.parametrize("which", ["terrain", "terrain_large"])
+def test_morton_codes_against_cpu_interleave(which):
+    sc = S.scene_terrain() if which == "terrain" else large_terrain()
     n = sc.n_prims
     scene = rtb.Scene(sc).build()
     _, order, morton = rtb.rt_bvh_export(scene.handle, n, 2 * n)
@@ -362,9 +370,11 @@ def test_morton_codes_against_cpu_interleave():
         return out
 
     code = (spread(q[:, 0]) << 2) | (spread(q[:, 1]) << 1) | spread(q[:, 2])
-    # the sort key is the code's top 24 bits for at most 2^17 primitives
-    assert n <= 1 << 17
-    code &= ~np.int64(63)
+    # the sort key is the code's top 24 bits for at most 2^17 primitives,
+    # all 30 above
+    assert (n <= 1 << 17) == (which == "terrain")
+    if n <= 1 << 17:
+        code &= ~np.int64(63)
     got = morton.astype(np.int64)
     exp = code[order]
     # quantisation may differ by one cell where a centroid sits on a cell edge
