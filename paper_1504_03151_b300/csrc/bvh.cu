@@ -22,7 +22,7 @@ constexpr int kSortCoopMaxBlocks = 1024;   // grid of the single-launch sort (co
 constexpr int kSortCoopMaxKeys = 1 << 22;  // larger inputs take the multi-launch sort
 constexpr int kTopBins = 16;        // SAH bins per axis for the top-level rebuild
 constexpr int kTopMaxLevels = 64;   // launches of the level kernel (empty ones return at once)
-constexpr int kTopCache = 4096;     // clusters of one segment held in shared memory (40 B each)
+constexpr int kTopCache = 4096;     // clusters of one segment held in shared memory (41 B each)
 constexpr int kTopWarpSeg = 32;     // segments of at most this many clusters are finished by one warp
 constexpr int kTopForceMedian = 32; // from this level on, split segments at the middle: with at
                                     // most 2^28 clusters every segment is done by level 60
@@ -983,6 +983,7 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
   float4* c_hi = s_dyn + cache_cap;
   int* c_id = (int*)(s_dyn + 2 * (size_t)cache_cap);
   int* c_part = c_id + cache_cap;
+  unsigned char* c_side = (unsigned char*)(c_part + cache_cap);   // side of each cached cluster
   const bool cached = m <= cache_cap;
   if (t < 6) {
     s_cb[t] = f2o(t < 3 ? INFINITY : -INFINITY);
@@ -1112,6 +1113,7 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
       float4 lo, hi;
       fetch(k, c, lo, hi);
       const int sd = side_of(k, lo, hi);
+      if (cached) c_side[k] = (unsigned char)sd;
       nl += sd == 0;
       nr += sd;
       const float v[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
@@ -1183,10 +1185,16 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
     int* dst = cached ? c_part : ids_out + b;
     int pl = before_l, pr = nleft + before_r;
     for (int k = k0; k < k1; ++k) {
-      int c;
-      float4 lo, hi;
-      fetch(k, c, lo, hi);
-      if (side_of(k, lo, hi)) dst[pr++] = c;
+      int c, sd;
+      if (cached) {
+        c = c_id[k];
+        sd = c_side[k];
+      } else {
+        float4 lo, hi;
+        fetch(k, c, lo, hi);
+        sd = side_of(k, lo, hi);
+      }
+      if (sd) dst[pr++] = c;
       else dst[pl++] = c;
     }
   }
@@ -1518,13 +1526,6 @@ __global__ void __launch_bounds__(256) k_top_all(int top_base, int* seg_count, i
   top_small_body(seg_count, small_seg, top_base, clu_a, clu_b, clu_link, clu_lo, clu_hi, top_count, nodes, info);
 }
 
-__global__ void k_top_done(const int* __restrict__ top_count, const int* __restrict__ n_clusters, BuildInfo* info,
-                           int top_base) {
-  info->n_top = *top_count;
-  info->n_clusters = *n_clusters;
-  info->root = top_base;
-}
-
 // ---------------------------------------------------------------------------
 // 8. 4-wide traversal tree.  A 4-wide node stands for one internal node of
 //    the binary tree and takes its children; while it has fewer than four,
@@ -1557,8 +1558,16 @@ __device__ __forceinline__ float half_area(const float* lo, const float* hi) {
 // Slots past the LBVH's n_lbvh internal nodes are top nodes; only the first
 // *top_count of them exist (none without a top rebuild: top_count NULL).
 __global__ void __launch_bounds__(256) k_collapse4(const float4* __restrict__ bin, int n_bin, int n_lbvh,
-                                                   const int* __restrict__ top_count, float4* __restrict__ out) {
+                                                   const int* __restrict__ top_count,
+                                                   const int* __restrict__ n_clusters, BuildInfo* info, int top_base,
+                                                   float4* __restrict__ out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x == 0 && top_count) {
+    // the rebuilt top's counts and root, for rt_bvh_get_info
+    info->n_top = *top_count;
+    info->n_clusters = *n_clusters;
+    info->root = top_base;
+  }
   if (x >= n_bin) return;
   if (x >= n_lbvh && (top_count == nullptr || x - n_lbvh >= __ldg(top_count))) return;   // an unused slot
   // Slots are indexed only by constants once the loops unroll, so they stay
@@ -1808,7 +1817,7 @@ static int cluster_max_for(int n) {
 // The 4-wide traversal tree: one 4-wide node per binary node slot, at the
 // same index (the root is the binary root).
 static rt_status collapse4(rt_scene* s, const BuildScratch& b, const float4* nodes, int n_bin, bool top,
-                           cudaStream_t st) {
+                           int top_base, cudaStream_t st) {
   rt_status rs = ensure(s->nodes4, (size_t)n_bin * 128);
   if (rs) return rs;
   s->n_nodes4 = n_bin;
@@ -1816,6 +1825,7 @@ static rt_status collapse4(rt_scene* s, const BuildScratch& b, const float4* nod
     k_wide_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, (float4*)s->nodes4.p);
   } else {
     k_collapse4<<<(n_bin + 255) / 256, 256, 0, st>>>(nodes, n_bin, (int)s->n_prims - 1, top ? b.top_count : nullptr,
+                                                     b.seg_count + kTopMaxLevels + 1, b.info, top_base,
                                                      (float4*)s->nodes4.p);
   }
   return cuda_error(cudaGetLastError(), "rt_bvh_build: 4-wide tree");
@@ -1847,7 +1857,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     k_layout_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, nodes, b.info);
     k_gather_prims<<<1, 32, 0, st>>>(b.vals0, 1, (const float4*)s->prims_id.p, (float4*)s->prims_leaf.p);
     s->root = 0;
-    if ((rs = collapse4(s, b, nodes, (int)slots, false, st))) return rs;
+    if ((rs = collapse4(s, b, nodes, (int)slots, false, 0, st))) return rs;
     s->last_build_launches = L + 4;
     s->built = true;
     return cuda_error(cudaGetLastError(), "rt_bvh_build");
@@ -1888,7 +1898,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     int top_grid = std::max(1, 2 * s->sm_count);
     // dynamic shared memory: the cluster cache of one segment
     int cache_cap = kTopCache;
-    const size_t dyn = (size_t)cache_cap * 40;   // per cached cluster: lo, hi, id, partitioned id
+    const size_t dyn = (size_t)cache_cap * 41;   // per cached cluster: lo, hi, id, partitioned id, side
     static int coop_blocks = -1;
     if (coop_blocks < 0) {
       int coop = 0, per_sm = 0;
@@ -1920,11 +1930,10 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
                                             b.clu_lo, b.clu_hi, b.top_count, nodes, b.info);
       L += 1;
     }
-    k_top_done<<<1, 1, 0, st>>>(b.top_count, n_clusters_dev, b.info, top_base);
-    L += 5 + kTopMaxLevels;
+    L += 4 + kTopMaxLevels;   // k_collapse4 records the top's counts and root
     s->root = top_base;
   }
-  if ((rs = collapse4(s, b, nodes, (int)slots, top, st))) return rs;
+  if ((rs = collapse4(s, b, nodes, (int)slots, top, top ? s->root : 0, st))) return rs;
   L += 1;
   s->last_build_launches = L;
   s->built = true;
