@@ -194,6 +194,30 @@ def test_schlick_normal_incidence_and_snell():
             assert not ok and R == 1.0                                # TIR
 
 
+def test_schlick_oblique_incidence_golden():
+    """Fresnel-Schlick at oblique angles on both sides of the interface:
+    the cosine on the less dense side (cos theta_i from air, cos theta_t from
+    glass or water) and the fifth power, against hand-worked values."""
+    g = json.load(open(os.path.join(GOLDEN, "schlick_oblique.json")))
+    for c in g["cases"]:
+        th = math.radians(c["theta_deg"])
+        d = np.array([math.sin(th), 0.0, -math.cos(th)])
+        ok, R, dt = O.refract(d, [0, 0, 1], c["n1"], c["n2"])
+        assert ok, c["what"]
+        assert R == pytest.approx(c["R"], abs=1e-12), c["what"]
+        # the refracted ray obeys Snell's law at the same angle
+        assert c["n1"] * math.sin(th) == pytest.approx(c["n2"] * math.hypot(dt[0], dt[1]), abs=1e-12)
+        # the pins tell the readings apart: the other cosine, or a fourth
+        # power, would be off by far more than the tolerance
+        r0 = ((c["n1"] - c["n2"]) / (c["n1"] + c["n2"])) ** 2
+        ci = math.cos(th)
+        ct = math.sqrt(1.0 - (c["n1"] / c["n2"] * math.sin(th)) ** 2)
+        other = ct if c["cos_used"] == "incident" else ci
+        assert abs(R - (r0 + (1 - r0) * (1 - other) ** 5)) > 1e-5, c["what"]
+        used = ci if c["cos_used"] == "incident" else ct
+        assert abs(R - (r0 + (1 - r0) * (1 - used) ** 4)) > 1e-5, c["what"]
+
+
 def test_total_internal_reflection_angle():
     crit = math.degrees(math.asin(1 / 1.5))
     assert crit == pytest.approx(41.8103, abs=1e-4)
