@@ -36,7 +36,11 @@ UNIT = "Mrays/s"
 # algorithmic FP32 operations per unit of work (counted from the math)
 OPS_BOX = 14      # ordered slab test of one child box: 6 FFMA + 6 min/max + 1 widening FMUL + 1 compare
 OPS_TRI = 30      # Moller-Trumbore
+# algorithmic bytes per unit of work: a 4-wide node visit reads its 128-B
+# node, a primitive test its 48-B record, and a ray reads its 48-B record
+# and writes a 16-B hit (the per-ray figures, as if no ray shared a load)
 BYTES_NODE = 128
+BYTES_RAY_IO = 48 + 16
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one frame's
 # launches of each kernel class, from one ncu capture of the bench workload
@@ -47,8 +51,10 @@ PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b3
 PROFILED_SHA = "20e6f594cce21065"
 PROFILED_TRAFFIC = {
     0: (24_637_952 + 122_092_800 + 5_496_576 + 1_024 + 7_396_096,
-        "k_trace<1,0,0> + k_trace<0,0,0> (depth 1) + k_paths<0,0> (depths 2-5): profiles/launches_terrain1080p_d5.md"),
-    1: (179_979_264 + 4_312_064 + 5_756_672, "k_shadow<0> (depths 0 and 1): profiles/launches_terrain1080p_d5.md"),
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one frame's k_trace<1,0,0>, k_trace<0,0,0> "
+        "(depth 1) and k_paths<0,0> (depths 2-5) launches"),
+    1: (179_979_264 + 4_312_064 + 5_756_672,
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one frame's two k_shadow<0> launches (depths 0, 1)"),
 }
 
 
@@ -153,9 +159,16 @@ class ClockSampler:
                 "samples": len(inside), "interval_ms": self.INTERVAL_MS}
 
 
-def cpu_oracle_sample(sc, seconds_hint=15.0):
-    """Times the FP64 oracle (brute force, as it stands) on a bounded pixel
-    sample of the frame; returns (Mrays/s, sample description, cores)."""
+def oracle_threads():
+    """The host threads the oracle's OpenMP loop uses (all cores unless OMP_NUM_THREADS says otherwise)."""
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_oracle_sample(sc):
+    """Times the FP64 oracle as it stands: brute force over every primitive
+    on a bounded pixel sample of the frame, and its own median-split BVH
+    (proven equal to brute force) on the full frame.  Returns the cpu_baseline
+    object; its value is the BVH mode's full-frame Mrays/s."""
     import oracle as O
     orc = O.OracleScene.from_scene(sc)
     W, H = sc.width, sc.height
@@ -166,9 +179,16 @@ def cpu_oracle_sample(sc, seconds_hint=15.0):
     dt = time.perf_counter() - t0
     c = r["counts"]
     rays = c["primary"] + c["shadow"] + c["secondary"]
-    cores = os.cpu_count()
-    return rays / dt / 1e6, f"brute force, every {stride}th pixel of the frame ({len(pix)} px, {rays} rays, " \
-                            f"{dt:.1f} s)", cores
+    t0 = time.perf_counter()
+    f = orc.render(sc.camera, W, H, sc.max_depth, mode="bvh")
+    dtf = time.perf_counter() - t0
+    cf = f["counts"]
+    rays_f = cf["primary"] + cf["shadow"] + cf["secondary"]
+    return {"value": rays_f / dtf / 1e6, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"the oracle's BVH mode over the full frame ({W * H} px, {rays_f} rays, {dtf:.1f} s)",
+            "bvh_full_frame_s": dtf,
+            "brute_force": {"value": rays / dt / 1e6, "unit": UNIT,
+                            "sample": f"every {stride}th pixel of the frame ({len(pix)} px, {rays} rays, {dt:.1f} s)"}}
 
 
 def max_over_ranks(x, dist, device="cpu"):
@@ -194,30 +214,44 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     sc = S.scene_terrain()
-    for _ in range(args.warmup):
-        pass   # the oracle has no warm-up state; keep the timed steps bounded instead
     import oracle as O
     orc = O.OracleScene.from_scene(sc)
     W, H = sc.width, sc.height
-    stride = 4099
-    times, rays = [], 0
-    for k in range(args.steps):
-        pix = np.arange(k % stride, W * H, stride)
+    # The oracle's BVH mode (the mode of cpu_baseline's value).  A warm-up
+    # step on every 97th pixel measures its cost a pixel; the timed steps
+    # then take every stride-th pixel (offset by the step), the stride sized
+    # so that all of them together take about two minutes: the full frame
+    # (stride 1) when K is small enough.
+    per_px = 0.0
+    for w in range(max(args.warmup, 1)):
+        pix = np.arange(w % 97, W * H, 97)
         t0 = time.perf_counter()
-        r = orc.render(sc.camera, W, H, sc.max_depth, mode="brute", pixels=pix)
+        orc.render(sc.camera, W, H, sc.max_depth, mode="bvh", pixels=pix)
+        per_px = (time.perf_counter() - t0) / len(pix)
+    budget_s = 120.0 / max(args.steps, 1)
+    stride = max(1, int(np.ceil(per_px * W * H / budget_s)))
+    times, rays, n_px = [], 0, 0
+    for k in range(args.steps):
+        pix = None if stride == 1 else np.arange(k % stride, W * H, stride)
+        t0 = time.perf_counter()
+        r = orc.render(sc.camera, W, H, sc.max_depth, mode="bvh", pixels=pix)
         times.append(time.perf_counter() - t0)
         c = r["counts"]
         rays += c["primary"] + c["shadow"] + c["secondary"]
+        n_px += W * H if pix is None else len(pix)
     total = sum(times)
     value = rays / total / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "terrain 1920x1080, 123904 triangles, depth 5, 4 lights",
-                   "sample": f"each step: every {stride}th pixel (offset by the step index)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"brute force, every {stride}th pixel per step"},
+        "config": {"workload": "terrain 1920x1080, 123904 triangles (fBm 256x192 + 20 L3 icospheres), depth 5, "
+                               "4 point lights, materials 60/25/15",
+                   "sample": f"each step: every {stride}th pixel (offset by the step index), "
+                             f"{n_px / args.steps:.0f} px a step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                         "sample": f"the oracle's BVH mode, every {stride}th pixel a step ({n_px} px, {rays} rays, "
+                                   f"{total:.1f} s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -536,16 +570,49 @@ def main():
         e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / n_e2e, dist, dev)
     e2e_value = job_throughput(world, rays, e2e_ms) if e2e_ms else None
 
-    # roofline of the dominant kernel class
+    # roofline of the two kernel classes (closest hit + shade; any-hit
+    # shadow): FP32-issue fraction of the algorithmic operations and L2
+    # fraction of the algorithmic bytes, over the classes' stage times in the
+    # timed frames (where they overlap each other); beside them the stage
+    # times with every kernel run alone (RT_FLAG_SERIAL_STAGES, untimed steps)
+    ser_trace, ser_shadow = [], []
+    opts_s = rtb.make_options(background=sc.background, flags=rtb.RT_FLAG_STAGE_TIMING | rtb.RT_FLAG_SERIAL_STAGES | mode)
+    for k in range(max(args.steps // 2, 3)):
+        flush.zero_()
+        step(opts_s)
+        _, a, b = rtb.rt_render_stage_times(h)
+        ser_trace.append(a)
+        ser_shadow.append(b)
+    l2_probe = {mb: rtb.rt_probe_l2_read(mb << 20, max(1, (40 << 30) // (mb << 20))) for mb in (16, 32, 64)}
+    l2_peak = max(l2_probe.values())
     pk, pk_kind = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2032.0)
     alu_peak = 148 * 128 * sm_mhz * 1e6 / 1e12       # FP32 lanes x clock: Tops/s (one op per lane per clock)
     tr = sum(trace_ms) / len(trace_ms)
     sh = sum(shadow_ms) / len(shadow_ms)
-    cls, kms = (0, tr) if tr >= sh else (1, sh)
-    ops = work["box_tests"][cls] * OPS_BOX + work["prim_tests"][cls] * OPS_TRI
+    classes = {}
+    for c_, name, kms_, sms_, nrays in ((0, "closest_hit", tr, sum(ser_trace) / len(ser_trace),
+                                         st["primary"] + st["secondary"]),
+                                        (1, "shadow", sh, sum(ser_shadow) / len(ser_shadow), st["shadow"])):
+        ops_ = work["box_tests"][c_] * OPS_BOX + work["prim_tests"][c_] * OPS_TRI
+        byt_ = work["node_visits"][c_] * BYTES_NODE + work["prim_tests"][c_] * BYTES_TRI + nrays * BYTES_RAY_IO
+        tb, tsrc = profiled_traffic(c_)
+        classes[name] = {
+            "kernel_ms": kms_, "kernel_ms_alone": sms_, "rays": nrays, "alg_ops": ops_, "alg_bytes": byt_,
+            "alu_frac": ops_ / (kms_ * 1e-3) / 1e12 / alu_peak,
+            "l2_frac": byt_ / (kms_ * 1e-3) / 1e9 / l2_peak,
+            "alu_frac_alone": ops_ / (sms_ * 1e-3) / 1e12 / alu_peak,
+            "l2_frac_alone": byt_ / (sms_ * 1e-3) / 1e9 / l2_peak,
+            "dram_bytes": tb, "dram_source": tsrc,
+            "dram_over_alg_bytes": tb / byt_ if tb else None,
+        }
+        classes[name]["frac"] = max(classes[name]["alu_frac"], classes[name]["l2_frac"])
+    cls = 0 if tr >= sh else 1
+    cname = "closest_hit" if cls == 0 else "shadow"
+    C = classes[cname]
+    kms, ops, traffic, traffic_src = C["kernel_ms"], C["alg_ops"], C["dram_bytes"], C["dram_source"]
     achieved = ops / (kms * 1e-3) / 1e12
-    traffic, traffic_src = profiled_traffic(cls)
+    l2_bound = C["l2_frac"] > C["alu_frac"]
     launches_per_step = info["build_launches"] + 1 + 2 + st["launches"] + 2
 
     # radiance cache: online training frames, then timed training frames;
@@ -637,8 +704,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sample, cores = cpu_oracle_sample(sc)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = cpu_oracle_sample(sc)
 
     if rank == 0:
         line = {
@@ -651,11 +717,24 @@ def main():
                        "secondary": st["secondary"], "l2": "flushed between steps (256 MB write)",
                        "step": "repack + BVH build + render", "parallelism": f"replicas x{world}",
                        "bvh": {k: info[k] for k in ("n_nodes", "max_depth", "sah_cost", "sah_cost_lbvh")}},
-            "roofline": {"bound": "alu", "kernel": "closest-hit+shade" if cls == 0 else "any-hit shadow",
-                         "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
-                         "traffic": traffic, "traffic_unit": "bytes per frame", "traffic_source": traffic_src,
-                         "peak_source": f"148 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} clock)",
-                         "kernel_ms": kms, "alg_ops": ops},
+            "roofline": {"bound": "l2" if l2_bound else "alu",
+                         "kernel": "closest-hit+shade" if cls == 0 else "any-hit shadow",
+                         "achieved": C["alg_bytes"] / (kms * 1e-3) / 1e9 if l2_bound else achieved,
+                         "peak": l2_peak if l2_bound else alu_peak, "unit": "GB/s" if l2_bound else "Tops/s",
+                         "frac": C["frac"], "traffic": traffic, "traffic_unit": "bytes per frame",
+                         "traffic_source": traffic_src,
+                         "alu": {"achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": C["alu_frac"],
+                                 "peak_source": f"148 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} clock)"},
+                         "l2": {"achieved": C["alg_bytes"] / (kms * 1e-3) / 1e9, "peak": l2_peak, "unit": "GB/s",
+                                "frac": C["l2_frac"],
+                                "peak_source": "rt_probe_l2_read: streaming L1-bypassing reads of an L2-resident "
+                                               "buffer, best of " + ", ".join(f"{m} MB {g:.0f}"
+                                                                              for m, g in l2_probe.items())},
+                         "kernel_ms": kms, "kernel_ms_alone": C["kernel_ms_alone"], "alg_ops": ops,
+                         "alg_bytes": C["alg_bytes"], "dram_over_alg_bytes": C["dram_over_alg_bytes"],
+                         "alg_units": "ops: 14 a child-box test, 30 a triangle test; bytes: 128 a node visit, "
+                                      "48 a primitive test, 64 a ray (48-B record in, 16-B hit out)",
+                         "classes": classes},
             "stage_ms": {"trace": tr, "shadow": sh, "step": ms,
                          "note": "sums of per-kernel times; shadow kernels overlap the next depth's trace"},
             "work": {"node_visits_per_depth": work["node_visits_per_depth"],

@@ -111,6 +111,10 @@ enum {
                                       Only the Lambert lobe is integrated.  Such a frame runs
                                       every depth as a wavefront (as RT_FLAG_PER_DEPTH_WAVEFRONT).
                                       Not with the radiance cache (RT_ERR_UNSUPPORTED). */
+  RT_FLAG_SERIAL_STAGES = 64,      /* run each depth's shadow kernel on the caller's stream after
+                                      that depth's closest-hit kernel, not beside the next depth on
+                                      a side stream: with RT_FLAG_STAGE_TIMING every kernel is then
+                                      timed alone (a measurement mode; frames take longer) */
   RT_FLAG_DETERMINISTIC = 32       /* accumulate every pixel in 64-bit fixed point (units of
                                       2^-32, contributions clamped to +-2^30) with integer
                                       atomics, whose sum does not depend on the order the rays
@@ -128,11 +132,18 @@ typedef struct rt_render_options {
   float eps_scale;            /* origin offset eps = eps_scale * max(1, |p|_inf) */
   int64_t queue_capacity;     /* rays per secondary / shadow queue; 0 = default */
   int64_t traversal_cap;      /* loop steps per ray before RT_ERR_TRAVERSAL_LIMIT; 0 = default */
+  uint32_t* ray_counts;       /* NULL, or a device buffer of H*W*2*(max_depth+1) uint32 that a frame
+                                 rendered with RT_FLAG_COUNT_WORK clears and fills: for pixel p and
+                                 depth d, [p][d][0] = closest-hit rays traced at depth d and
+                                 [p][d][1] = shadow rays cast from its depth-d hits (the per-pixel
+                                 split of rt_render_stats' rays_per_depth and shadow_per_depth).
+                                 The radiance cache's training rays are not counted.  Frames only
+                                 (rt_render_ex, rt_render_pass, rt_render_nrc); a batch ignores it. */
 } rt_render_options;
 
 /* Defaults: use_bvh 1, flags 0, background 0.1, eps_scale 1e-4,
  * queue_capacity max(2*W*H, 65536) closest-hit rays (shadow queue:
- * n_lights x that), traversal_cap 4 * nodes + 64. */
+ * n_lights x that), traversal_cap 4 * nodes + 64, ray_counts NULL. */
 void rt_render_options_default(rt_render_options* opt);
 
 typedef struct rt_render_stats {
@@ -193,7 +204,11 @@ typedef struct rt_pass {
   int32_t reserved; /* 0 */
 } rt_pass;
 
-/* Copies the host arrays to the device and packs them into the device
+/* The scene of the paper's problem statement (Sec. II; Sec. IV.B): the
+ * objects - spheres of Eq. 9, plus triangles - with their materials (the
+ * f_r and L_e of Eq. 6-8) and the point lights that Alg. 1 casts shadow
+ * rays to.
+ * Copies the host arrays to the device and packs them into the device
  * layout.  Spheres and triangles may be empty (not both NULL with n > 0).
  * Validates every value: RT_ERR_INVALID_ARG on NaN/Inf, radius <= 0 or a
  * material index >= n_materials.  Synchronous. */
@@ -218,7 +233,10 @@ rt_status rt_scene_set_area_lights(rt_scene* s, const rt_area_light* lights, siz
 rt_status rt_scene_update(rt_scene* s, const rt_sphere* spheres, const rt_triangle* triangles,
                           void* stream);
 
-/* Builds the BVH on the device: 30-bit Morton codes, radix sort (by the
+/* The acceleration structure, which the paper names only among the
+ * speed-ups of Sec. II (its Alg. 1 tests every object, which use_bvh = 0
+ * keeps); the result is the same nearest hit.
+ * Builds the BVH on the device: 30-bit Morton codes, radix sort (by the
  * codes' top 24 bits for at most 2^17 primitives, else all 30), LBVH
  * hierarchy, bottom-up boxes, binned-SAH rebuild of the top levels and
  * SAH leaf collapsing.  Stream-ordered; rebuild allowed at any time. */
@@ -263,13 +281,24 @@ rt_status rt_render_pass(rt_scene* s, const rt_camera* cam, int width, int heigh
                          const rt_pass* pass, float* accum_rgb_device, const rt_render_options* options,
                          rt_render_stats* stats, void* stream);
 
-/* Renders one frame into out_rgb_device (H*W*3 float32, overwritten). */
+/* One frame of the paper's method (Sec. IV.A; Alg. 1; Eq. 6-12): a camera
+ * ray per pixel, its closest hit (spheres by Eq. 9-12, triangles by
+ * Moller-Trumbore), local shading by Eq. 6-8 with one shadow ray per point
+ * light (Alg. 1), the reflection / refraction recursion (Fig. 3) turned into
+ * an iteration over depths 0..max_depth (Sec. IV.A), and every
+ * contribution added onto its pixel (Sec. IV.A).
+ * Renders into out_rgb_device (H*W*3 float32, overwritten; caller-owned).
+ * RT_ERR_INVALID_ARG on a NULL scene or image, an invalid camera, a size
+ * < 1 or max_depth outside [0, RT_MAX_DEPTH]; RT_ERR_NOT_BUILT before
+ * rt_bvh_build; kernel errors are latched (rt_scene_sync). */
 rt_status rt_render(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
                     float* out_rgb_device, void* stream);
 
-/* rt_render with options (NULL = defaults), optional primary-ray AOVs
- * (device, H*W: hit primitive id / hit distance, inf on a miss) and
- * optional stats (host; filled after a stream sync). */
+/* rt_render (the frame of Sec. IV.A, Alg. 1, Eq. 6-12) with options
+ * (NULL = defaults; use_bvh = 0 is Alg. 1's loop over every object),
+ * optional primary-ray AOVs (device, H*W: hit primitive id / hit distance,
+ * inf on a miss) and optional stats (host; filled after a stream sync, which
+ * also returns the latched kernel errors). */
 rt_status rt_render_ex(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
                        float* out_rgb_device, const rt_render_options* opt, int32_t* aov_prim,
                        float* aov_t, rt_render_stats* stats, void* stream);
@@ -301,13 +330,16 @@ rt_status rt_render_host_async(rt_scene* s, const rt_camera* cam, int width, int
 rt_status rt_camera_rays(const rt_camera* cam, int width, int height, float* o_device,
                          float* d_device, void* stream);
 
-/* Closest hit for n rays (device arrays n*3 float), t in (tmin, inf):
+/* The closest-hit query of the frame (Eq. 9-12 for spheres, Alg. 1's
+ * nearest object) on caller rays.
+ * Closest hit for n rays (device arrays n*3 float), t in (tmin, inf):
  * prim id (or -1) and t (inf on a miss).  use_bvh as in the options. */
 rt_status rt_trace_closest(rt_scene* s, const float* o_device, const float* d_device, int64_t n,
                            float tmin, int use_bvh, int32_t* prim_device, float* t_device,
                            void* stream);
 
-/* Any hit with t in (tmin, tmax[i]) for n rays: occluded[i] = 0/1. */
+/* Alg. 1's shadow test on caller rays: any hit with t in (tmin, tmax[i])
+ * for n rays: occluded[i] = 0/1. */
 rt_status rt_trace_any(rt_scene* s, const float* o_device, const float* d_device,
                        const float* tmax_device, int64_t n, float tmin, int use_bvh,
                        uint8_t* occluded_device, void* stream);
@@ -442,10 +474,34 @@ rt_status rt_batch_render(rt_batch* b, const rt_tune* tune, rt_render_stats* sta
 rt_status rt_batch_autotune(rt_batch* b, rt_tune* best, float* best_ms, void* stream);
 rt_status rt_batch_destroy(rt_batch* b);
 
+/* The one-call form of a batch: renders frame i = (scenes[i], cameras[i],
+ * widths[i] x heights[i]) into out_rgb[i] for i < n, to max_depth, in one
+ * persistent launch, with `tune` (NULL = a default tile and block shape)
+ * and default options.  It creates a batch, renders it, waits for `stream`
+ * and destroys the batch, so it pays the graph capture every call; a
+ * caller that renders the same frames again keeps an rt_batch instead.
+ * Errors as rt_batch_create and rt_batch_render, and the scenes' latched
+ * kernel errors.  Batching has no counterpart in the paper. */
+rt_status rt_render_batch(rt_scene* const* scenes, const rt_camera* cameras, const int32_t* widths,
+                          const int32_t* heights, int32_t n, int32_t max_depth, float* const* out_rgb,
+                          const rt_tune* tune, void* stream);
+
+/* A measurement helper with no counterpart in the paper: the L2 read
+ * bandwidth of the current device in GB/s, the roofline of traversal
+ * kernels whose nodes and primitives fit in L2.  Allocates a device buffer
+ * of `bytes` (64 KB .. 2 GB; below the L2's size to measure L2), reads it
+ * once to bring it into L2, then times `reps` more streaming reads that
+ * bypass L1 (CUDA events on `stream`), frees it and returns the bytes read
+ * per second.  Synchronous. */
+rt_status rt_probe_l2_read(size_t bytes, int reps, float* gbs, void* stream);
+
 /* Waits for `stream` (and for the host copies of rt_render_host_async)
- * and returns (and clears) the latched kernel error. */
+ * and returns (and clears) the latched kernel error.  Host-side plumbing:
+ * no counterpart in the paper. */
 rt_status rt_scene_sync(rt_scene* s, void* stream);
 
+/* Waits for the device and frees everything the scene owns (NULL is a
+ * no-op).  Host-side plumbing: no counterpart in the paper. */
 rt_status rt_scene_destroy(rt_scene* s);
 
 #ifdef __cplusplus

@@ -41,6 +41,8 @@ def lib():
         L.orc_camera_ray.argtypes = [P, I32, I32, I32, I32, P, P]
         L.orc_render.restype = I32
         L.orc_render.argtypes = [P, P, I32, I32, I32, I32, P, I64, P, P, P, P, P, I32]
+        L.orc_render_px.restype = I32
+        L.orc_render_px.argtypes = [P, P, I32, I32, I32, I32, P, I64, P, P, P, P, P, P, P, I32]
         L.orc_closest_hits.restype = I32
         L.orc_closest_hits.argtypes = [P, I64, P, P, D, I32, P, P, P, I32]
         L.orc_any_hits.restype = I32
@@ -146,11 +148,14 @@ class OracleScene:
     def bvh_nodes(self) -> int:
         return lib().orc_bvh_node_count(self._h)
 
-    def render(self, camera, width, height, max_depth, mode="bvh", pixels=None, nthreads=0):
+    def render(self, camera, width, height, max_depth, mode="bvh", pixels=None, nthreads=0, per_pixel=False):
         """Renders (all or the listed) pixels.  mode: 'brute', 'bvh' or 'iterative'.
 
         Returns dict(rgb [n,3] f64, prim [n] i32, t [n] f64, robust [n] f64,
-        counts dict)."""
+        counts dict).  per_pixel: also robust_struct [n] f64 (margins of the
+        decisions that change ray counts) and px_counts [n, max_depth+1, 2]
+        u32 (closest-hit rays traced at each depth, shadow rays cast from
+        each depth's hits), see orc_render_px."""
         m = {"brute": 0, "bvh": 1, "iterative": 2}[mode]
         cam = np.ascontiguousarray(camera)
         if pixels is not None:
@@ -163,13 +168,16 @@ class OracleScene:
         t = np.zeros(n)
         robust = np.zeros(n)
         counts = np.zeros(3 + 3 * (max_depth + 1), np.uint64)
-        rc = lib().orc_render(self._h, _ptr(cam), width, height, max_depth, m, _ptr(pixels),
-                              n if pixels is not None else 0, _ptr(rgb), _ptr(prim), _ptr(t),
-                              _ptr(robust), _ptr(counts), nthreads)
+        rs = np.zeros(n) if per_pixel else None
+        px = np.zeros((n, max_depth + 1, 2), np.uint32) if per_pixel else None
+        rc = lib().orc_render_px(self._h, _ptr(cam), width, height, max_depth, m, _ptr(pixels),
+                                 n if pixels is not None else 0, _ptr(rgb), _ptr(prim), _ptr(t),
+                                 _ptr(robust), _ptr(counts), _ptr(rs), _ptr(px), nthreads)
         if rc != 0:
             raise ValueError("oracle render rejected its arguments")
         per_depth = counts[3:].reshape(max_depth + 1, 3)
-        return {
+        extra = {"robust_struct": rs, "px_counts": px} if per_pixel else {}
+        return {**extra,
             "rgb": rgb, "prim": prim, "t": t, "robust": robust,
             "counts": {"primary": int(counts[0]), "shadow": int(counts[1]),
                        "secondary": int(counts[2]),

@@ -596,6 +596,7 @@ typedef struct {
   int n_children;
   child_t child[2];
   double robust;
+  double robust_struct; /* smallest margin of a decision that changes the ray counts, any weight */
   int n_shadow;
 } shade_t;
 
@@ -607,6 +608,7 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
   shade_t out;
   memset(&out, 0, sizeof out);
   out.robust = ROBUST_CAP;
+  out.robust_struct = ROBUST_CAP;
   const prim_t* p = &s->prims[pi];
   const mat_t* m = &s->mats[p->mat];
   v3 ph = add(r->o, scl(r->d, t));
@@ -625,9 +627,10 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
   double dn = dot(r->d, ng);
   int inside = dn > 0.0;
   v3 n = inside ? scl(ng, -1.0) : ng;
-  if (count_robust) {
+  if (want_robust) {
     double rb = fabs(dn) / Ad;
-    if (rb < out.robust) out.robust = rb;
+    if (count_robust && rb < out.robust) out.robust = rb;
+    if (rb < out.robust_struct) out.robust_struct = rb;
   }
 
   /* L_e of Eq. 7, except on a ray made by a diffuse bounce: the vertex
@@ -659,9 +662,11 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
         v3 f = add(scl(m->albedo, nl), mk(m->ks * spec, m->ks * spec, m->ks * spec));
         v3 contrib = scl(mul(mul(w, L->inten), f), 1.0 - rho);
         int relevant = count_robust && maxc(mul(scl(w, 1.0 - rho), L->inten)) * (2.0 + m->ks) >= 1e-3;
-        if (relevant) {
+        if (want_robust) {
+          /* n.l > 0 decides whether a shadow ray is cast */
           double rb = fabs(nl) / (An + r->ed + (Up + s->K * GAMMA32 * maxabs(L->pos)) / dist_l);
-          if (rb < out.robust) out.robust = rb;
+          if (relevant && rb < out.robust) out.robust = rb;
+          if (rb < out.robust_struct) out.robust_struct = rb;
         }
         if (!(nl > 0.0)) continue;
         /* shadow ray from the offset origin to the light */
@@ -729,11 +734,12 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
         v3 contrib = scl(mul(mul(w, Lrad), f), G * (1.0 - rho));
         double uy = (Up + s->K * 3 * GAMMA32 * maxabs(y)) / dist_c;   /* direction to the sample */
         int relevant = count_robust && maxc(scl(mul(w, Lrad), (1.0 - rho) * fabs(G))) * (2.0 + m->ks) >= 1e-3;
-        if (relevant) {
+        if (want_robust) {
           double rb = fabs(nl) / (An + r->ed + uy);
-          if (rb < out.robust) out.robust = rb;
-          rb = fabs(cos_y) / (uy + s->K * 8 * GAMMA32);
-          if (rb < out.robust) out.robust = rb;
+          double rb2 = fabs(cos_y) / (uy + s->K * 8 * GAMMA32);
+          if (rb2 < rb) rb = rb2;
+          if (relevant && rb < out.robust) out.robust = rb;
+          if (rb < out.robust_struct) out.robust_struct = rb;
         }
         if (!(nl > 0.0) || !(cos_y > 0.0)) continue;
         ray_t sr;
@@ -776,10 +782,11 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
       c->r.ed = 3.0 * An + s->K * 16 * GAMMA32;
       c->w = scl(mul(w, m->albedo), M_PI * (1.0 - rho));
       c->code = ((code << 1) | 1u) | CODE_BOUNCE;
-      if (count_robust) {
+      if (want_robust) {
         /* the basis changes branch where n.z changes sign */
         double rb = fabs(n.z) / (An + s->K * 4 * GAMMA32);
-        if (rb < out.robust) out.robust = rb;
+        if (count_robust && rb < out.robust) out.robust = rb;
+        if (rb < out.robust_struct) out.robust_struct = rb;
       }
     }
   } else {
@@ -787,10 +794,12 @@ static shade_t shade_hit(const orc_scene* s, const ray_t* r, v3 w, int32_t pi, d
     double R, kk;
     v3 dt;
     int has_t = refract_schlick(r->d, n, n1, n2, &R, &dt, &kk);
-    if (count_robust) {
+    if (want_robust) {
+      /* total internal reflection decides whether a refraction ray is spawned */
       double eta = n1 / n2, ci = -dot(r->d, n);
       double rb = fabs(kk) / (2.0 * eta * eta * fabs(ci) * Ad + s->K * 4 * GAMMA32);
-      if (rb < out.robust) out.robust = rb;
+      if (count_robust && rb < out.robust) out.robust = rb;
+      if (rb < out.robust_struct) out.robust_struct = rb;
     }
     if (spawn) {
       child_t* c = &out.child[out.n_children++];
@@ -824,6 +833,8 @@ typedef struct {
   int max_depth, use_bvh;
   uint64_t* counts;     /* 3 + 3 * (max_depth + 1) */
   double robust;
+  int want_struct;      /* track robust_struct (every ray, whatever its weight) */
+  double robust_struct; /* smallest margin of any decision that changes the pixel's ray counts */
 } trace_ctx;
 
 /* The radiance cache's answer for a hit: exp(MLP(encode(p, n, -d))), with
@@ -857,14 +868,16 @@ static v3 trace_rec(trace_ctx* cx, const ray_t* r, int depth, v3 w, int64_t pixe
   cx->counts[depth == 0 ? 0 : 2]++;
   cx->counts[3 + 3 * depth + 0]++;
   int want = maxc(w) * s->l_max >= 1e-3;
-  hit_t h = closest_hit(s, r, 0.0, cx->use_bvh, want);
+  hit_t h = closest_hit(s, r, 0.0, cx->use_bvh, want || cx->want_struct);
   if (want && h.robust < cx->robust) cx->robust = h.robust;
+  if (cx->want_struct && h.robust < cx->robust_struct) cx->robust_struct = h.robust;
   if (prim0) { *prim0 = h.prim; *t0 = h.t; }
   if (h.prim < 0) return mul(w, s->bg);
   cx->counts[3 + 3 * depth + 2]++;
   if (depth == s->nrc_depth) return mul(w, cache_radiance(s, r, h));
   shade_t sh = shade_hit(s, r, w, h.prim, h.t, h.cosn, depth < cx->max_depth, cx->use_bvh, 1, pixel, code);
   if (sh.robust < cx->robust) cx->robust = sh.robust;
+  if (sh.robust_struct < cx->robust_struct) cx->robust_struct = sh.robust_struct;
   cx->counts[1] += (uint64_t)sh.n_shadow;
   cx->counts[3 + 3 * depth + 1] += (uint64_t)sh.n_shadow;
   v3 c = sh.local;
@@ -1123,7 +1136,15 @@ void orc_set_cache(orc_scene* s, int depth, const double* W, const double* B, in
 int orc_render(const orc_scene* s, const void* cam, int W, int H, int max_depth, int mode,
                const int64_t* pixels, int64_t n_pixels, double* rgb, int32_t* prim, double* t,
                double* robust, uint64_t* counts, int nthreads) {
+  return orc_render_px(s, cam, W, H, max_depth, mode, pixels, n_pixels, rgb, prim, t, robust, counts, NULL, NULL,
+                       nthreads);
+}
+
+int orc_render_px(const orc_scene* s, const void* cam, int W, int H, int max_depth, int mode,
+                  const int64_t* pixels, int64_t n_pixels, double* rgb, int32_t* prim, double* t,
+                  double* robust, uint64_t* counts, double* robust_struct, uint32_t* px_counts, int nthreads) {
   if (!s || !cam || W < 1 || H < 1 || max_depth < 0 || max_depth > MAX_DEPTH_LIMIT) return 1;
+  if (robust_struct && mode == 2) return 1;   /* the iterative form tracks no margins */
   int64_t n = pixels ? n_pixels : (int64_t)W * H;
   int nc = 3 + 3 * (max_depth + 1);
   uint64_t* total = (uint64_t*)calloc((size_t)nc, sizeof(uint64_t));
@@ -1149,6 +1170,15 @@ int orc_render(const orc_scene* s, const void* cam, int W, int H, int max_depth,
       trace_ctx cx;
       cx.s = s; cx.max_depth = max_depth; cx.use_bvh = (mode == 1); cx.counts = cnt;
       cx.robust = ROBUST_CAP;
+      cx.want_struct = robust_struct != NULL;
+      cx.robust_struct = ROBUST_CAP;
+      /* per-pixel counts: this pixel's share of the per-depth totals */
+      uint64_t before[2 * (MAX_DEPTH_LIMIT + 1)];
+      if (px_counts)
+        for (int d = 0; d <= max_depth; ++d) {
+          before[2 * d] = cnt[3 + 3 * d];
+          before[2 * d + 1] = cnt[3 + 3 * d + 1];
+        }
       int32_t p0 = -1;
       double t0 = INFINITY;
       v3 c;
@@ -1158,6 +1188,13 @@ int orc_render(const orc_scene* s, const void* cam, int W, int H, int max_depth,
       if (prim) prim[i] = p0;
       if (t) t[i] = p0 >= 0 ? t0 : INFINITY;
       if (robust) robust[i] = cx.robust;
+      if (robust_struct) robust_struct[i] = cx.robust_struct;
+      if (px_counts)
+        for (int d = 0; d <= max_depth; ++d) {
+          px_counts[(size_t)i * 2 * (max_depth + 1) + 2 * d] = (uint32_t)(cnt[3 + 3 * d] - before[2 * d]);
+          px_counts[(size_t)i * 2 * (max_depth + 1) + 2 * d + 1] =
+              (uint32_t)(cnt[3 + 3 * d + 1] - before[2 * d + 1]);
+        }
     }
 #ifdef _OPENMP
 #pragma omp critical

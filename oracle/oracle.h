@@ -91,6 +91,22 @@ int orc_render(const orc_scene* s, const void* cam, int width, int height,
                int64_t n_pixels, double* rgb, int32_t* prim, double* t,
                double* robust, uint64_t* counts, int nthreads);
 
+/* orc_render with two more per-pixel outputs (either may be NULL):
+ *   robust_struct[i]  smallest margin, in the same units as robust, of any
+ *                     decision that changes the pixel's ray counts (which
+ *                     primitive a ray hits, front or back, n.l > 0 for a
+ *                     light, total internal reflection, the bounce basis),
+ *                     taken over every ray whatever its weight; modes 0 and
+ *                     1 only
+ *   px_counts         n x 2 (max_depth + 1) uint32: per depth d, the
+ *                     pixel's closest-hit rays traced at d, then its
+ *                     shadow rays cast from depth-d hits */
+int orc_render_px(const orc_scene* s, const void* cam, int width, int height,
+                  int max_depth, int mode, const int64_t* pixels,
+                  int64_t n_pixels, double* rgb, int32_t* prim, double* t,
+                  double* robust, uint64_t* counts, double* robust_struct,
+                  uint32_t* px_counts, int nthreads);
+
 /* Closest hit for n given FP32 rays (promoted to double), t in (tmin, inf).
  * prim/t as above; robust as above for this single query, with the rays
  * treated as exact (intersection rounding only). */

@@ -18,11 +18,11 @@ __all__ = [
     "RtError", "lib", "rt_abi_version", "rt_last_error", "rt_render_options_default",
     "rt_scene_create", "rt_scene_update", "rt_bvh_build", "rt_bvh_get_info", "rt_bvh_export", "rt_bvh_export_wide",
     "rt_render", "rt_render_ex", "rt_render_host", "rt_render_host_async", "rt_camera_rays", "rt_trace_closest",
-    "rt_trace_any", "rt_scene_sync", "rt_scene_destroy", "rt_render_stage_times", "Scene",
+    "rt_trace_any", "rt_scene_sync", "rt_scene_destroy", "rt_render_stage_times", "rt_probe_l2_read", "Scene",
     "rt_nrc_config_default", "rt_nrc_create", "rt_nrc_destroy", "rt_nrc_get_params", "rt_nrc_set_params",
     "rt_nrc_get_grads", "rt_nrc_infer", "rt_nrc_train_step", "rt_render_nrc", "rt_nrc_save", "rt_nrc_load",
     "rt_tune", "rt_batch_create", "rt_batch_set_cameras", "rt_batch_render", "rt_batch_autotune",
-    "rt_batch_destroy", "Batch", "rt_pass", "rt_scene_set_area_lights", "rt_render_pass",
+    "rt_batch_destroy", "rt_render_batch", "Batch", "rt_pass", "rt_scene_set_area_lights", "rt_render_pass",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,6 +45,7 @@ RT_FLAG_NO_GRAPH = 4
 RT_FLAG_PER_DEPTH_WAVEFRONT = 8
 RT_FLAG_DIFFUSE_BOUNCE = 16
 RT_FLAG_DETERMINISTIC = 32
+RT_FLAG_SERIAL_STAGES = 64
 RT_MAX_DEPTH = 16
 
 
@@ -62,7 +63,7 @@ class rt_camera(ctypes.Structure):
 class rt_render_options(ctypes.Structure):
     _fields_ = [("use_bvh", ctypes.c_int32), ("flags", ctypes.c_int32), ("background", ctypes.c_float * 3),
                 ("eps_scale", ctypes.c_float), ("queue_capacity", ctypes.c_int64),
-                ("traversal_cap", ctypes.c_int64)]
+                ("traversal_cap", ctypes.c_int64), ("ray_counts", ctypes.c_void_p)]
 
 
 class rt_render_stats(ctypes.Structure):
@@ -143,6 +144,7 @@ def lib():
             "rt_render_ex": (I, [P, P, I, I, I, P, P, P, P, P, P]),
             "rt_render_host": (I, [P, P, I, I, I, P, P, P]),
             "rt_render_stage_times": (I, [P, P, P, P]),
+            "rt_probe_l2_read": (I, [S, I, P, P]),
             "rt_camera_rays": (I, [P, I, I, P, P, P]),
             "rt_trace_closest": (I, [P, P, P, I64, F, I, P, P, P]),
             "rt_trace_any": (I, [P, P, P, P, I64, F, I, P, P]),
@@ -162,6 +164,7 @@ def lib():
             "rt_batch_render": (I, [P, P, P, P]),
             "rt_batch_autotune": (I, [P, P, P, P]),
             "rt_batch_destroy": (I, [P]),
+            "rt_render_batch": (I, [P, P, P, P, I, I, P, P, P]),
             "rt_scene_set_area_lights": (I, [P, P, S]),
             "rt_render_pass": (I, [P, P, I, I, I, P, P, P, P, P]),
             "rt_render_host_async": (I, [P, P, I, I, I, P, P, P]),
@@ -238,7 +241,9 @@ def rt_render_options_default() -> rt_render_options:
 
 
 def make_options(use_bvh=True, flags=0, background=(0.1, 0.1, 0.1), eps_scale=1e-4, queue_capacity=0,
-                 traversal_cap=0) -> rt_render_options:
+                 traversal_cap=0, ray_counts=None) -> rt_render_options:
+    """ray_counts: None or a CUDA int32/uint32 tensor of H*W*2*(max_depth+1)
+    entries (per-pixel ray counts; needs RT_FLAG_COUNT_WORK)."""
     o = rt_render_options_default()
     o.use_bvh = int(bool(use_bvh))
     o.flags = int(flags)
@@ -246,6 +251,7 @@ def make_options(use_bvh=True, flags=0, background=(0.1, 0.1, 0.1), eps_scale=1e
     o.eps_scale = float(eps_scale)
     o.queue_capacity = int(queue_capacity)
     o.traversal_cap = int(traversal_cap)
+    o.ray_counts = None if ray_counts is None else _dptr(ray_counts)
     return o
 
 
@@ -346,6 +352,13 @@ def rt_render_host_async(scene, camera, width, height, max_depth, out_host, opti
     cam = make_camera(camera)
     _check(lib().rt_render_host_async(scene, ctypes.byref(cam), width, height, max_depth, _hptr(out_host),
                                       ctypes.byref(options) if options is not None else None, _stream(stream)))
+
+
+def rt_probe_l2_read(nbytes, reps=50, stream=None) -> float:
+    """The L2 read bandwidth (GB/s) over a buffer of nbytes (a measurement helper)."""
+    g = ctypes.c_float()
+    _check(lib().rt_probe_l2_read(int(nbytes), int(reps), ctypes.byref(g), _stream(stream)))
+    return g.value
 
 
 def rt_render_stage_times(scene):
@@ -507,6 +520,18 @@ def rt_batch_autotune(batch, stream=None):
 
 def rt_batch_destroy(batch):
     _check(lib().rt_batch_destroy(batch))
+
+
+def rt_render_batch(scenes, cameras, widths, heights, max_depth, outs, tune=None, stream=None):
+    """The one-call batch: create, render with `tune`, wait, destroy."""
+    n = len(scenes)
+    sc_arr = (ctypes.c_void_p * n)(*[ctypes.c_void_p(h) if isinstance(h, int) else h for h in scenes])
+    cam_arr = (rt_camera * n)(*[make_camera(c) for c in cameras])
+    w_arr = (ctypes.c_int32 * n)(*[int(x) for x in widths])
+    h_arr = (ctypes.c_int32 * n)(*[int(x) for x in heights])
+    o_arr = (ctypes.c_void_p * n)(*[_dptr(o) for o in outs])
+    _check(lib().rt_render_batch(sc_arr, cam_arr, w_arr, h_arr, n, int(max_depth), o_arr,
+                                 ctypes.byref(tune) if tune is not None else None, _stream(stream)))
 
 
 class Batch:

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librtb.so")
-SOURCES = ["scene.cu", "bvh.cu", "render.cu", "nrc.cu", "batch.cu"]
+SOURCES = ["scene.cu", "bvh.cu", "render.cu", "nrc.cu", "batch.cu", "probe.cu"]
 HEADERS = ["rtb_internal.cuh", "nrc_internal.cuh", "tc.cuh", "trace_device.cuh"]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include", "rtb.h")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -24,7 +24,7 @@ def _stale(target, deps):
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [INCLUDE]
-    objs = []
+    objs, cmds = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
@@ -34,7 +34,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose:
                 cmd += ["-Xptxas", "-v"]
                 print(" ".join(cmd), file=sys.stderr)
-            subprocess.run(cmd, check=True)
+            cmds.append(cmd)
+    # the translation units are independent: compile them side by side
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+        for r in list(ex.map(lambda c: subprocess.run(c), cmds)):
+            if r.returncode != 0:
+                raise subprocess.CalledProcessError(r.returncode, r.args)
     if force or _stale(LIB, objs):
         cmd = ["nvcc"] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcudart"]
         subprocess.run(cmd, check=True)

@@ -600,6 +600,21 @@ rt_status rt_batch_autotune(rt_batch* b, rt_tune* best, float* best_ms, void* st
   return RT_OK;
 }
 
+rt_status rt_render_batch(rt_scene* const* scenes, const rt_camera* cameras, const int32_t* widths,
+                          const int32_t* heights, int32_t n, int32_t max_depth, float* const* out_rgb,
+                          const rt_tune* tune, void* stream) {
+  rt_batch* b = nullptr;
+  rt_status rs = rt_batch_create(scenes, n, cameras, widths, heights, max_depth, out_rgb, nullptr, &b);
+  if (rs) return rs;
+  rs = rt_batch_render(b, tune, nullptr, stream);
+  // the batch's tables must outlive its launch
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (!rs && e != cudaSuccess) rs = cuda_error(e, "rt_render_batch");
+  for (int i = 0; !rs && i < n; ++i) rs = rt_scene_sync(scenes[i], stream);
+  rt_batch_destroy(b);
+  return rs;
+}
+
 rt_status rt_batch_destroy(rt_batch* b) {
   if (!b) return RT_OK;
   if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);

@@ -64,7 +64,18 @@ struct FrameParams {
   const unsigned* prev_hits;   // depth-first frames: cache hits of the previous frame (0: take all)
   PassInfo ps;                 // the pass: camera jitter and area-light samples
   unsigned long long* fb_fixed;   // RT_FLAG_DETERMINISTIC: 3 per pixel, 64-bit fixed point (else NULL)
+  unsigned* px_rays;              // counting frames: per pixel and depth, closest-hit and shadow rays (else NULL)
+  int px_stride;                  // 2 (max_depth + 1)
 };
+
+// Per-pixel ray counts (counting instances only): cls 0 = a closest-hit ray
+// traced at `depth`, cls 1 = a shadow ray cast from a depth-`depth` hit.
+// Rays of the radiance cache's training subset (pixel < 0) are not counted.
+template <bool kCount>
+__device__ __forceinline__ void count_px(const FrameParams& fp, int pixel, int depth, int cls) {
+  if (kCount && fp.px_rays != nullptr && pixel >= 0)
+    atomicAdd(&fp.px_rays[(size_t)pixel * fp.px_stride + 2 * depth + cls], 1u);
+}
 
 constexpr float kFixScale = 4294967296.f;   // 2^32 units of radiance
 constexpr float kFixMax = 1073741824.f;     // |contribution| clamp, 2^30: sums stay far inside 64 bits
@@ -180,6 +191,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
       w = xyz(q2);
       code = __float_as_uint(q2.w);
     }
+    if (active) count_px<kCount>(fp, pixel, depth, 0);
     // closest hit
     float t = INFINITY;
     bool fail = false;
@@ -314,6 +326,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FramePara
     if (kCount) wc.vmax = max(wc.vmax, wc.visits - v0);
     if (fail) atomicOr(sc.status, kErrTraversalLimit);
     if (part && h < 0 && !fail) add_fb(fp, __float_as_int(q0.w), xyz(q2));
+    if (part) count_px<kCount>(fp, __float_as_int(q0.w), depth, 1);
   }
   flush_work<kCount>(ctr, 1, depth, wc);
 }
@@ -436,6 +449,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
       unsigned sv0 = wc.visits, st0 = wc.tests, sb0 = wc.boxes;
       int h = traverse<true, kCount>(sc, make_ray(o, d), 0.0f, tm, stack, cap, sfail, wc);
       count_ray<kCount>(ctr, 1, ~depth, wc.visits - sv0, wc.tests - st0, wc.boxes - sb0);
+      count_px<kCount>(fp, pixel, ~depth, 1);
       if (sfail) atomicOr(sc.status, kErrTraversalLimit);
       if (h < 0 && !sfail) add_fb(fp, pixel, w);
     } else if (have) {
@@ -444,6 +458,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
       unsigned v0 = wc.visits, t0 = wc.tests, b0 = wc.boxes;
       int hit = traverse<false, kCount>(sc, make_ray(o, d), 0.0f, t, stack, cap, fail, wc);
       count_ray<kCount>(ctr, 0, depth, wc.visits - v0, wc.tests - t0, wc.boxes - b0);
+      count_px<kCount>(fp, pixel, depth, 0);
       if (fail) atomicOr(sc.status, kErrTraversalLimit);
       bool live = hit >= 0;
       if (!live) add_fb(fp, pixel, w * bg);
@@ -519,6 +534,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
             unsigned sv0 = wc.visits, st0 = wc.tests, sb0 = wc.boxes;
             int h = traverse<true, kCount>(sc, make_ray(os, sd), 0.0f, tmax, stack, cap, sfail, wc);
             count_ray<kCount>(ctr, 1, depth, wc.visits - sv0, wc.tests - st0, wc.boxes - sb0);
+            count_px<kCount>(fp, pixel, depth, 1);
             if (sfail) atomicOr(sc.status, kErrTraversalLimit);
             if (h < 0 && !sfail) add_fb(fp, pixel, contrib);
           }
@@ -899,7 +915,13 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     cudaMemsetAsync(out, 0, n_out * sizeof(float), st);
   }
   cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
+  if (count && opt.ray_counts != nullptr) {
+    fp.px_rays = opt.ray_counts;
+    fp.px_stride = 2 * (D + 1);
+    cudaMemsetAsync(fp.px_rays, 0, (size_t)W * H * fp.px_stride * sizeof(unsigned), st);
+  }
   bool per_depth = (opt.flags & RT_FLAG_PER_DEPTH_WAVEFRONT) != 0;
+  const bool serial = (opt.flags & RT_FLAG_SERIAL_STAGES) != 0;
   // depths 0..last run as wavefronts; the rest run as depth-first paths,
   // which meet the cache at depth T themselves unless it is depth 0.  With
   // the diffuse bounce nearly every hit has a child, every depth is wide,
@@ -926,13 +948,15 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     }
     if (timing) timing_end(s, slot, st);
     // shadow(depth) runs on the side stream, beside trace(depth + 1)
+    // (on the main stream after it when the stages are serialised)
+    cudaStream_t sst = serial ? st : s->side;
     cudaEventRecord(s->ev_traced[depth], st);
-    cudaStreamWaitEvent(s->side, s->ev_traced[depth], 0);
-    slot = timing ? timing_begin(s, 1, s->side) : -1;
-    if (count) k_shadow<true><<<s->shadow_blocks, kTraceThreads, 0, s->side>>>(sc, fp, depth, cap);
-    else k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, s->side>>>(sc, fp, depth, cap);
-    if (timing) timing_end(s, slot, s->side);
-    cudaEventRecord(s->ev_shadowed[depth], s->side);
+    cudaStreamWaitEvent(sst, s->ev_traced[depth], 0);
+    slot = timing ? timing_begin(s, 1, sst) : -1;
+    if (count) k_shadow<true><<<s->shadow_blocks, kTraceThreads, 0, sst>>>(sc, fp, depth, cap);
+    else k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, sst>>>(sc, fp, depth, cap);
+    if (timing) timing_end(s, slot, sst);
+    cudaEventRecord(s->ev_shadowed[depth], sst);
     launches += 2;
   }
   if (T >= 0 && !cache_in_paths) {

@@ -135,6 +135,7 @@ void rt_render_options_default(rt_render_options* o) {
   o->eps_scale = 1e-4f;
   o->queue_capacity = 0;
   o->traversal_cap = 0;
+  o->ray_counts = nullptr;
 }
 
 rt_status rt_scene_create(const rt_sphere* spheres, size_t n_spheres, const rt_triangle* triangles,

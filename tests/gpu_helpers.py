@@ -6,7 +6,14 @@ may legitimately differ):
   * a pixel whose oracle path tree has a decision within reach of FP32
     rounding (oracle robust < 1) may differ; every other pixel must match:
     primary hit id bit-exact, colour within 2e-3 max-abs;
-  * pixels that do differ (id or colour beyond 2e-3) are at most 0.1 %;
+  * with per-pixel ray counts (per_pixel=True on both sides), every pixel
+    none of whose count-deciding choices is within reach of FP32 rounding
+    (oracle robust_struct >= 1, every ray whatever its weight) traces
+    exactly the oracle's closest-hit rays and casts exactly its shadow
+    rays at every depth;
+  * pixels that do differ (id, colour beyond 2e-3, or ray counts) are at
+    most 0.1 %, and the pixels exempted by the rounding model at most
+    FRAGILE_BUDGET;
   * primary hit distances agree to 1e-5 relative where the ids match.
 """
 import numpy as np
@@ -18,9 +25,16 @@ import paper_1504_03151_b300 as rtb
 COLOUR_TOL = 2e-3
 T_REL_TOL = 1e-5
 BUDGET = 1e-3
+# Pixels the rounding model exempts (any decision of the path tree within
+# K = 4 times its modelled FP32 uncertainty): 0.27 % of the 1080p terrain
+# frame, 0.075 % with K = 1.  The exemption is a conservative superset of
+# the pixels that can differ; those that do differ are held to BUDGET.
+FRAGILE_BUDGET = 5e-3
 
 
-def gpu_render(sc, use_bvh=True, flags=0, width=None, height=None, max_depth=None, **opt):
+def gpu_render(sc, use_bvh=True, flags=0, width=None, height=None, max_depth=None, per_pixel=False, **opt):
+    """per_pixel: also the per-pixel ray counts (counting kernels), res["px"]
+    [H*W, max_depth+1, 2] like the oracle's px_counts."""
     W = width or sc.width
     H = height or sc.height
     D = sc.max_depth if max_depth is None else max_depth
@@ -30,7 +44,11 @@ def gpu_render(sc, use_bvh=True, flags=0, width=None, height=None, max_depth=Non
     out = torch.full((H * W * 3,), float("nan"), device="cuda", dtype=torch.float32)
     prim = torch.full((H * W,), -7, device="cuda", dtype=torch.int32)
     t = torch.full((H * W,), float("nan"), device="cuda", dtype=torch.float32)
-    options = rtb.make_options(use_bvh=use_bvh, flags=flags, background=sc.background, **opt)
+    px = None
+    if per_pixel:
+        px = torch.full((H * W * 2 * (D + 1),), -1, device="cuda", dtype=torch.int32)
+        flags |= rtb.RT_FLAG_COUNT_WORK
+    options = rtb.make_options(use_bvh=use_bvh, flags=flags, background=sc.background, ray_counts=px, **opt)
     st = rtb.rt_render_ex(scene.handle, sc.camera, W, H, D, out, options, prim, t, stats=True)
     torch.cuda.synchronize()
     res = {
@@ -39,23 +57,32 @@ def gpu_render(sc, use_bvh=True, flags=0, width=None, height=None, max_depth=Non
         "t": t.double().cpu().numpy(),
         "stats": st,
     }
+    if per_pixel:
+        res["px"] = px.view(H * W, D + 1, 2).cpu().numpy().astype(np.uint32)
     scene.close()
     return res
 
 
-def oracle_render(sc, mode="bvh", width=None, height=None, max_depth=None, pixels=None):
+def oracle_render(sc, mode="bvh", width=None, height=None, max_depth=None, pixels=None, per_pixel=False):
     W = width or sc.width
     H = height or sc.height
     D = sc.max_depth if max_depth is None else max_depth
     orc = O.OracleScene.from_scene(sc)
-    return orc.render(sc.camera, W, H, D, mode=mode, pixels=pixels)
+    return orc.render(sc.camera, W, H, D, mode=mode, pixels=pixels, per_pixel=per_pixel)
 
 
-def compare(gpu, ref, pixels=None, budget=BUDGET):
-    """Returns a report dict; raises AssertionError on a parity failure."""
+def compare(gpu, ref, pixels=None, budget=BUDGET, fragile_budget=None):
+    """Returns a report dict; raises AssertionError on a parity failure.
+    fragile_budget: bound on the exempted pixels (default: the larger of
+    FRAGILE_BUDGET and budget, for images of a few hundred pixels)."""
+    if fragile_budget is None:
+        fragile_budget = max(FRAGILE_BUDGET, budget)
     g_rgb, g_prim, g_t = gpu["rgb"], gpu["prim"], gpu["t"]
+    g_px = gpu.get("px")
     if pixels is not None:
         g_rgb, g_prim, g_t = g_rgb[pixels], g_prim[pixels], g_t[pixels]
+        if g_px is not None:
+            g_px = g_px[pixels]
     robust = ref["robust"] >= 1.0
     err = np.abs(g_rgb - ref["rgb"]).max(axis=1)
     assert np.isfinite(g_rgb).all(), "non-finite GPU colour"
@@ -77,4 +104,24 @@ def compare(gpu, ref, pixels=None, budget=BUDGET):
     assert rep["colour_mismatch_frac"] <= budget, rep
     assert rep["prim_mismatch_frac"] <= budget, rep
     assert rep["max_rel_t_robust"] <= T_REL_TOL, rep
+    assert rep["fragile_frac"] <= fragile_budget, rep
+    if g_px is not None and ref.get("px_counts") is not None:
+        sound = ref["robust_struct"] >= 1.0
+        bad_n = (g_px != ref["px_counts"]).any(axis=(1, 2))
+        rep["struct_fragile_frac"] = float(1 - sound.mean())
+        rep["count_mismatch_frac"] = float(bad_n.mean())
+        # slack of the frame's totals: what the exempted pixels hold on either side
+        rep["count_slack_rays"] = int(np.maximum(g_px[~sound], ref["px_counts"][~sound]).sum())
+        assert not (bad_n & sound).any(), \
+            f"ray counts differ on robust pixels: {np.where(bad_n & sound)[0][:10]} {rep}"
+        assert rep["count_mismatch_frac"] <= budget, rep
+        assert rep["struct_fragile_frac"] <= fragile_budget, rep
     return rep
+
+
+def check_totals(gpu, max_depth):
+    """The per-pixel counts add up to the frame's per-depth totals."""
+    st, px = gpu["stats"], gpu["px"]
+    s = px.astype(np.int64).sum(axis=0)
+    assert list(s[:, 0]) == list(st["rays_per_depth"][:max_depth + 1]), (s[:, 0], st["rays_per_depth"])
+    assert list(s[:, 1]) == list(st["shadow_per_depth"][:max_depth + 1]), (s[:, 1], st["shadow_per_depth"])

@@ -39,6 +39,7 @@ def test_abi_version_and_defaults():
     assert o.use_bvh == 1 and o.flags == 0 and o.queue_capacity == 0
     assert list(o.background) == pytest.approx([0.1, 0.1, 0.1])
     assert o.eps_scale == pytest.approx(1e-4)
+    assert o.ray_counts is None
 
 
 def test_struct_sizes_match_header_layout():
@@ -46,7 +47,7 @@ def test_struct_sizes_match_header_layout():
     assert S.MATERIAL_DTYPE.itemsize == 44 and S.LIGHT_DTYPE.itemsize == 24
     import ctypes
     assert ctypes.sizeof(rtb.rt_camera) == S.CAMERA_DTYPE.itemsize == 40
-    assert ctypes.sizeof(rtb.rt_render_options) == 40
+    assert ctypes.sizeof(rtb.rt_render_options) == 48   # ... traversal_cap, then the ray_counts pointer
     assert ctypes.sizeof(rtb.rt_tune) == 16
     assert ctypes.sizeof(rtb.rt_pass) == 24
 

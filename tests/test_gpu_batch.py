@@ -98,6 +98,17 @@ def test_batch_matches_oracle():
     sc_.close()
 
 
+def test_one_call_render_batch(frames):
+    """rt_render_batch (create, render, wait, destroy in one call) makes the
+    images of the batch handle, background 0.1 (the default options)."""
+    fr = [f for f in frames if tuple(f[1].background) == (0.1, 0.1, 0.1)] or frames[:1]
+    outs = [torch.full((w * h * 3,), float("nan"), device="cuda") for _, _, _, w, h in fr]
+    rtb.rt_render_batch([f[0].handle for f in fr], [f[2] for f in fr], [f[3] for f in fr], [f[4] for f in fr], 3,
+                        outs, rtb.make_tune(8, 4, 128, 0))
+    for img, (scene, sc, cam, w, h) in zip(images(outs, fr), fr):
+        assert_same_image(img, single_frame(scene, cam, w, h, 3, (0.1, 0.1, 0.1)))
+
+
 @pytest.mark.parametrize("tune", [(8, 4, 128, 0), (4, 8, 64, 0), (16, 2, 256, 0), (32, 1, 128, 2), (1, 32, 64, 1)])
 def test_every_tune_gives_the_same_image(frames, tune):
     b, outs = make_batch(frames)

@@ -87,9 +87,14 @@ def test_nrc_inference_matches_oracle():
     # accumulation may round it to neighbouring values: a few outputs move
     # by one such step; every other output agrees to rounding noise.
     q = np.quantile(rel, [0.5, 0.99, 0.999, 1.0])
-    assert q[0] <= 1e-5 and q[1] <= 1e-2 and q[3] <= 5e-2, q
-    ref32 = O.mlp_forward(_oracle_inputs(sc, pnv), W, B, bf16_acts=False)
-    assert (np.abs(g - ref32) / np.maximum(np.abs(ref32), 1e-3)).max() <= 5e-2
+    # against the plain FP64 network (activations not rounded): the BF16
+    # activations of the network's definition are the only difference
+    ref64 = O.mlp_forward(_oracle_inputs(sc, pnv), W, B, bf16_acts=False)
+    rel64 = np.abs(g - ref64) / np.maximum(np.abs(ref64), 1e-3)
+    q64 = np.quantile(rel64, [0.5, 0.99, 0.999, 1.0])
+    print("vs BF16-activation oracle", q, "vs plain FP64 oracle", q64)
+    assert q[0] <= 1e-5 and q[1] <= 1e-2 and q[3] <= 1e-2, q
+    assert q64[3] <= 1e-2, q64
     rtb.rt_nrc_destroy(nrc)
     scene.close()
 
@@ -120,6 +125,26 @@ def test_nrc_gradients_and_adam_match_oracle():
     gb = g[O.N_W:].astype(np.float64)
     assert _cos(gb, dB) >= 0.999
     assert np.linalg.norm(gb - dB) <= 1e-2 * np.linalg.norm(dB)
+    # Against the plain FP64 gradient (no BF16 rounding of activations and
+    # backward signals).  Rounding each per-sample term to BF16 (2^-9
+    # relative) is magnified where the sum over samples cancels, so the
+    # network's own BF16 definition sits measurably off the FP64 gradient;
+    # the oracle measures that gap on these inputs (bf16 vs plain), and the
+    # GPU may be off the FP64 gradient by 1.5 times it plus the 1e-2 bar.
+    l64, dW64, dB64 = O.mlp_loss_grad(_oracle_inputs(sc, pnv), target.astype(np.float64), W, B, bf16_acts=False)
+    assert loss == pytest.approx(l64, rel=1e-2)
+    for off, rows, cols in LAYERS + [(O.N_W, 1, O.N_B)]:
+        a = g[off:off + rows * cols].astype(np.float64)
+        b64 = (dW64[off:off + rows * cols] if off < O.N_W else dB64)
+        bb = (dW[off:off + rows * cols] if off < O.N_W else dB)
+        gap_cos = 1.0 - _cos(bb, b64)
+        gap_rel = np.linalg.norm(bb - b64) / np.linalg.norm(b64)
+        c64 = _cos(a, b64)
+        r64 = np.linalg.norm(a - b64) / np.linalg.norm(b64)
+        print(f"layer at {off}: GPU vs FP64 cos {c64:.6f} rel {r64:.4f}; BF16 oracle vs FP64 cos {1 - gap_cos:.6f} "
+              f"rel {gap_rel:.4f}")
+        assert c64 >= 1.0 - (2.0 * gap_cos + 1e-3), (off, c64, gap_cos)
+        assert r64 <= 1.5 * gap_rel + 1e-2, (off, r64, gap_rel)
     # Adam's first step from zero moments: w - lr * g / (|g| + eps) on the GPU's own gradient
     p1 = rtb.rt_nrc_get_params(nrc)
     exp = p0.astype(np.float64) - 1e-2 * g / (np.abs(g.astype(np.float64)) + 1e-8)
@@ -153,11 +178,12 @@ def _gpu_bbox32(sc):
     return lo32.astype(np.float64), (np.float32(1.0) / (hi32 - lo32)).astype(np.float64)
 
 
-def _render_nrc(scene, nrc, sc, train, flags=0):
+def _render_nrc(scene, nrc, sc, train, flags=0, ray_counts=None):
     W, H = sc.width, sc.height
     out = torch.full((W * H * 3,), float("nan"), device="cuda")
     st = rtb.rt_render_nrc(scene.handle, nrc, sc.camera, W, H, sc.max_depth, out, train=train,
-                           options=rtb.make_options(background=sc.background, flags=flags), stats=True)
+                           options=rtb.make_options(background=sc.background, flags=flags, ray_counts=ray_counts),
+                           stats=True)
     assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
     return out.view(-1, 3).double().cpu().numpy(), st
 
@@ -178,19 +204,22 @@ def test_cached_frame_matches_oracle(flags):
     for _ in range(5):
         rtb.rt_nrc_train_step(nrc, scene.handle, torch.from_numpy(pnv).cuda(), torch.from_numpy(tgt).cuda(), 2048)
     params = rtb.rt_nrc_get_params(nrc)
-    img, st = _render_nrc(scene, nrc, sc, train=False, flags=flags)
+    D = sc.max_depth
+    px = torch.full((sc.width * sc.height * 2 * (D + 1),), -1, device="cuda", dtype=torch.int32)
+    img, st = _render_nrc(scene, nrc, sc, train=False, flags=flags | rtb.RT_FLAG_COUNT_WORK, ray_counts=px)
     orc = O.OracleScene.from_scene(sc)
     lo, inv = _gpu_bbox32(sc)
     orc.set_cache(2, params, lo, inv, bf16=True)
-    ref = orc.render(sc.camera, sc.width, sc.height, sc.max_depth, mode="brute")
-    g = {"rgb": img, "prim": ref["prim"], "t": ref["t"]}   # primary AOVs are checked elsewhere
-    compare(g, ref, budget=5e-3)
+    ref = orc.render(sc.camera, sc.width, sc.height, D, mode="brute", per_pixel=True)
+    g = {"rgb": img, "prim": ref["prim"], "t": ref["t"],   # primary AOVs are checked elsewhere
+         "px": px.view(-1, D + 1, 2).cpu().numpy().astype(np.uint32)}
+    rep = compare(g, ref, budget=5e-3)   # per-pixel ray counts exact outside the exempted pixels
     c = ref["counts"]
     assert st["primary"] == c["primary"]
-    assert abs(st["shadow"] - c["shadow"]) <= 1e-3 * c["shadow"] + 4
-    assert st["rays_per_depth"][:3] == c["rays_per_depth"][:3] or \
-        np.abs(np.array(st["rays_per_depth"][:3]) - np.array(c["rays_per_depth"][:3])).max() <= 4
+    for k in ("shadow", "secondary"):
+        assert abs(st[k] - c[k]) <= rep["count_slack_rays"], (k, st[k], c[k], rep)
     assert sum(st["rays_per_depth"][3:]) == 0            # nothing is traced past the cache
+    assert (g["px"][:, 3:, :] == 0).all()
     rtb.rt_nrc_destroy(nrc)
     scene.close()
 

@@ -11,7 +11,7 @@ import paper_1504_03151_b300 as rtb
 from paper_1504_03151_b300 import build as rtb_build
 from paper_1504_03151_b300 import scenes as S
 
-from gpu_helpers import COLOUR_TOL, compare, gpu_render, oracle_render
+from gpu_helpers import COLOUR_TOL, check_totals, compare, gpu_render, oracle_render
 
 pytestmark = pytest.mark.gpu
 
@@ -70,24 +70,27 @@ def test_camera_rays_match_oracle():
 @pytest.mark.parametrize("use_bvh", [False, True])
 def test_spheres8_parity(use_bvh):
     sc = S.scene_spheres8()
-    ref = oracle_render(sc, mode="brute")
-    g = gpu_render(sc, use_bvh=use_bvh)
+    ref = oracle_render(sc, mode="brute", per_pixel=True)
+    g = gpu_render(sc, use_bvh=use_bvh, per_pixel=True)
     rep = compare(g, ref)
     assert rep["max_err_robust"] < 1e-4, rep
+    check_totals(g, sc.max_depth)
     st = g["stats"]
     c = ref["counts"]
     assert st["primary"] == c["primary"] == 256 * 256
     for k in ("shadow", "secondary"):
-        assert abs(st[k] - c[k]) <= 1e-3 * c[k] + 4, (k, st[k], c[k])
+        assert abs(st[k] - c[k]) <= rep["count_slack_rays"], (k, st[k], c[k], rep)
+    print(rep)
 
 
 def test_terrain_small_parity_all_modes():
     sc = small_terrain()
-    ref = oracle_render(sc, mode="brute")
-    gb = gpu_render(sc, use_bvh=False)
-    gv = gpu_render(sc, use_bvh=True)
+    ref = oracle_render(sc, mode="brute", per_pixel=True)
+    gb = gpu_render(sc, use_bvh=False, per_pixel=True)
+    gv = gpu_render(sc, use_bvh=True, per_pixel=True)
     compare(gb, ref)
     compare(gv, ref)
+    check_totals(gv, sc.max_depth)
     # BVH and brute force on the GPU: same FP32 tests, same answer
     np.testing.assert_array_equal(gb["prim"], gv["prim"])
     np.testing.assert_allclose(gb["rgb"], gv["rgb"], atol=1e-5)
@@ -103,26 +106,34 @@ def test_ragged_sizes(wh):
 
 
 def test_terrain_1080p_full_frame_parity():
+    """The benchmark frame, every pixel: ids, colours and, per pixel and
+    depth, the closest-hit and shadow rays, against the oracle."""
     sc = S.scene_terrain()
-    g = gpu_render(sc)
-    ref = oracle_render(sc, mode="bvh")
+    g = gpu_render(sc, per_pixel=True)
+    ref = oracle_render(sc, mode="bvh", per_pixel=True)
     rep = compare(g, ref)
+    check_totals(g, sc.max_depth)
     st = g["stats"]
     c = ref["counts"]
     assert st["primary"] == 1920 * 1080
+    # outside the exempted pixels the counts match exactly (compare); the
+    # totals differ by at most what the exempted pixels hold
     for k in ("shadow", "secondary"):
-        assert abs(st[k] - c[k]) <= 1e-3 * c[k], (k, st[k], c[k])
-    for d in range(sc.max_depth + 1):
-        assert abs(st["rays_per_depth"][d] - c["rays_per_depth"][d]) <= 1e-3 * c["rays_per_depth"][d] + 16
+        assert abs(st[k] - c[k]) <= rep["count_slack_rays"], (k, st[k], c[k], rep)
     print(rep)
+    # the same frame rendered without counting: identical image
+    g2 = gpu_render(sc)
+    assert np.abs(g2["rgb"] - g["rgb"]).max() <= 1e-5
+    np.testing.assert_array_equal(g2["prim"], g["prim"])
 
 
 def test_depth_zero_and_max_depth():
     sc = S.scene_spheres8(width=64, height=64)
     for D in (0, 1, 16):
-        ref = oracle_render(sc, mode="brute", max_depth=D)
-        g = gpu_render(sc, max_depth=D)
+        ref = oracle_render(sc, mode="brute", max_depth=D, per_pixel=True)
+        g = gpu_render(sc, max_depth=D, per_pixel=True)
         compare(g, ref, budget=2e-3)
+        check_totals(g, D)
         if D == 0:
             assert g["stats"]["secondary"] == 0
 
@@ -578,7 +589,9 @@ def test_exact_ties_go_to_the_lower_primitive_id_on_gpu(red_first):
     hit = g["prim"] >= 0
     assert hit.mean() > 0.5
     assert set(np.unique(g["prim"][hit])) <= {0, 2, 3}
-    compare(g, oracle_render(sc, mode="brute"))
+    # every hit is an exact tie, which the rounding model exempts (55 % of
+    # the pixels); the tie rule itself is what the assertions above check
+    compare(g, oracle_render(sc, mode="brute"), fragile_budget=1.0)
 
 
 def test_degenerate_triangles_never_hit():

@@ -333,6 +333,41 @@ def test_depth_semantics():
     assert r3["counts"]["rays_per_depth"][1] == int(mirror.sum())
 
 
+def test_per_pixel_ray_counts():
+    """The per-pixel counts of the oracle: hand cases and the totals."""
+    # one lit sphere seen from its light's side, depth 0: a hit pixel casts
+    # one shadow ray (n.l > 0 on the whole visible cap), a miss casts none
+    sc = S.single_sphere(width=33, height=33)
+    orc = O.OracleScene.from_scene(sc)
+    r = orc.render(sc.camera, 33, 33, 0, mode="brute", per_pixel=True)
+    px = r["px_counts"]
+    hit = r["prim"] >= 0
+    assert hit.sum() > 50 and (~hit).sum() > 50
+    assert (px[:, 0, 0] == 1).all()
+    np.testing.assert_array_equal(px[:, 0, 1], hit.astype(np.uint32))
+    # a mirror sphere (rho = 1) over nothing, depth 2: every hit pixel sends
+    # one reflection that misses (nothing else is there), and no shadow ray
+    mats = S.material(S.MAT_MIRROR, (0.5, 0.5, 0.5), reflectivity=1.0)
+    sc2 = S.Scene("mirror", S.spheres_from([(0, 0, 0)], [1.0], [0]), np.zeros(0, S.TRIANGLE_DTYPE), mats,
+                  S.lights([(0, 0, 10)], [(1, 1, 1)]), S.camera((0, 0, 5), (0, 0, 0)), 33, 33, 2)
+    r2 = O.OracleScene.from_scene(sc2).render(sc2.camera, 33, 33, 2, mode="brute", per_pixel=True)
+    hit2 = r2["prim"] >= 0
+    np.testing.assert_array_equal(r2["px_counts"][:, 1, 0], hit2.astype(np.uint32))
+    assert (r2["px_counts"][:, :, 1] == 0).all()
+    assert (r2["px_counts"][:, 2, 0] == 0).all()
+    # on the terrain the per-pixel counts add up to the totals, and asking
+    # for them changes no other output
+    st = _small_terrain()
+    orc = O.OracleScene.from_scene(st)
+    a = orc.render(st.camera, 64, 48, st.max_depth, mode="bvh")
+    b = orc.render(st.camera, 64, 48, st.max_depth, mode="bvh", per_pixel=True)
+    np.testing.assert_array_equal(a["rgb"], b["rgb"])
+    np.testing.assert_array_equal(a["robust"], b["robust"])
+    s = b["px_counts"].astype(np.int64).sum(axis=0)
+    assert list(s[:, 0]) == b["counts"]["rays_per_depth"]
+    assert list(s[:, 1]) == b["counts"]["shadow_per_depth"]
+
+
 # ---------------------------------------------------------------------------
 # the oracle's BVH returns the brute-force answer
 # ---------------------------------------------------------------------------

@@ -77,3 +77,25 @@ def test_noalloc_counts_every_kind_of_light():
     assert ei.value.status == rtb.RT_ERR_UNSUPPORTED
     assert "RT_NOALLOC_MAX_LIGHTS" in str(ei.value)
     scene.close()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After a first call (which looks up the array's address), further
+    calls leave the device's free memory unchanged: no cudaMalloc on the
+    way, and no allocation by a library routine either."""
+    sc = S.scene_terrain(seed=7, width=96, height=64, max_depth=5, cells=(16, 12), n_ico=6, ico_level=2)
+    scene = rtb.Scene(sc).build()
+    W, H, D = sc.width, sc.height, sc.max_depth
+    out = torch.empty(W * H * 3, device="cuda")
+    rtb.rt_render_noalloc(scene.handle, sc.camera, W, H, D, out)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rtb.rt_render_noalloc(scene.handle, sc.camera, W, H, D, out)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert np.isfinite(out.cpu().numpy()).all()
+    scene.close()
