@@ -610,8 +610,8 @@ def main():
     cls = 0 if tr >= sh else 1
     cname = "closest_hit" if cls == 0 else "shadow"
     C = classes[cname]
-    kms, ops, traffic, traffic_src = C["kernel_ms"], C["alg_ops"], C["dram_bytes"], C["dram_source"]
-    achieved = ops / (kms * 1e-3) / 1e12
+    cls_ms, ops, traffic, traffic_src = C["kernel_ms"], C["alg_ops"], C["dram_bytes"], C["dram_source"]
+    achieved = ops / (cls_ms * 1e-3) / 1e12
     l2_bound = C["l2_frac"] > C["alu_frac"]
     launches_per_step = info["build_launches"] + 1 + 2 + st["launches"] + 2
 
@@ -719,18 +719,18 @@ def main():
                        "bvh": {k: info[k] for k in ("n_nodes", "max_depth", "sah_cost", "sah_cost_lbvh")}},
             "roofline": {"bound": "l2" if l2_bound else "alu",
                          "kernel": "closest-hit+shade" if cls == 0 else "any-hit shadow",
-                         "achieved": C["alg_bytes"] / (kms * 1e-3) / 1e9 if l2_bound else achieved,
+                         "achieved": C["alg_bytes"] / (cls_ms * 1e-3) / 1e9 if l2_bound else achieved,
                          "peak": l2_peak if l2_bound else alu_peak, "unit": "GB/s" if l2_bound else "Tops/s",
                          "frac": C["frac"], "traffic": traffic, "traffic_unit": "bytes per frame",
                          "traffic_source": traffic_src,
                          "alu": {"achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": C["alu_frac"],
                                  "peak_source": f"148 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({pk_kind} clock)"},
-                         "l2": {"achieved": C["alg_bytes"] / (kms * 1e-3) / 1e9, "peak": l2_peak, "unit": "GB/s",
+                         "l2": {"achieved": C["alg_bytes"] / (cls_ms * 1e-3) / 1e9, "peak": l2_peak, "unit": "GB/s",
                                 "frac": C["l2_frac"],
                                 "peak_source": "rt_probe_l2_read: streaming L1-bypassing reads of an L2-resident "
                                                "buffer, best of " + ", ".join(f"{m} MB {g:.0f}"
                                                                               for m, g in l2_probe.items())},
-                         "kernel_ms": kms, "kernel_ms_alone": C["kernel_ms_alone"], "alg_ops": ops,
+                         "kernel_ms": cls_ms, "kernel_ms_alone": C["kernel_ms_alone"], "alg_ops": ops,
                          "alg_bytes": C["alg_bytes"], "dram_over_alg_bytes": C["dram_over_alg_bytes"],
                          "alg_units": "ops: 14 a child-box test, 30 a triangle test; bytes: 128 a node visit, "
                                       "48 a primitive test, 64 a ray (48-B record in, 16-B hit out)",

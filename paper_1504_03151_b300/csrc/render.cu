@@ -688,6 +688,7 @@ CamBasis camera_basis(const rt_camera* c, int W, int H) {
 
 static int g_blocks_per_sm_trace = 0, g_blocks_per_sm_shadow = 0;
 
+
 using TraceKernel = void (*)(DevScene, FrameParams, int, int);
 using PathsKernel = void (*)(DevScene, FrameParams, int);
 
@@ -937,6 +938,18 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   if (per_depth || T == 0) fp.path_depth0 = T >= 0 ? T + 1 : 1;
   else fp.path_depth0 = last + 1;
   if (cache_in_paths && fp.nrc_depth >= 0) fp.prev_hits = nrc_prev_hits(nrc);
+  // shadow(depth) runs on the side stream, beside trace(depth + 1) (on the
+  // main stream after it when the stages are serialised)
+  auto launch_shadow = [&](int depth) {
+    cudaStream_t sst = serial ? st : s->side;
+    cudaStreamWaitEvent(sst, s->ev_traced[depth], 0);
+    int slot = timing ? timing_begin(s, 1, sst) : -1;
+    if (count) k_shadow<true><<<s->shadow_blocks, kTraceThreads, 0, sst>>>(sc, fp, depth, cap);
+    else k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, sst>>>(sc, fp, depth, cap);
+    if (timing) timing_end(s, slot, sst);
+    cudaEventRecord(s->ev_shadowed[depth], sst);
+    launches += 1;
+  };
   for (int depth = 0; depth <= last; ++depth) {
     // trace(depth) fills the shadow buffer that shadow(depth - 2) reads
     if (depth >= 2) cudaStreamWaitEvent(st, s->ev_shadowed[depth - 2], 0);
@@ -947,18 +960,11 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
       trace_kernel(false, count, pass_k)<<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);
     }
     if (timing) timing_end(s, slot, st);
-    // shadow(depth) runs on the side stream, beside trace(depth + 1)
-    // (on the main stream after it when the stages are serialised)
-    cudaStream_t sst = serial ? st : s->side;
     cudaEventRecord(s->ev_traced[depth], st);
-    cudaStreamWaitEvent(sst, s->ev_traced[depth], 0);
-    slot = timing ? timing_begin(s, 1, sst) : -1;
-    if (count) k_shadow<true><<<s->shadow_blocks, kTraceThreads, 0, sst>>>(sc, fp, depth, cap);
-    else k_shadow<false><<<s->shadow_blocks, kTraceThreads, 0, sst>>>(sc, fp, depth, cap);
-    if (timing) timing_end(s, slot, sst);
-    cudaEventRecord(s->ev_shadowed[depth], sst);
-    launches += 2;
+    launches += 1;
+    launch_shadow(depth);
   }
+  bool run_paths = !per_depth && D >= fp.path_depth0 && (T < 0 || cache_in_paths || train);
   if (T >= 0 && !cache_in_paths) {
     // cache lookups of the depth-T hits, beside the training rays' paths
     int slot = timing ? timing_begin(s, 2, s->side) : -1;
@@ -968,7 +974,6 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     cudaEventRecord(s->ev_shadowed[last], s->side);
     launches += 1;
   }
-  bool run_paths = !per_depth && D >= fp.path_depth0 && (T < 0 || cache_in_paths || train);
   if (run_paths) {
     int slot = timing ? timing_begin(s, 0, st) : -1;
     paths_kernel(count, pass_k)<<<s->paths_blocks, kTraceThreads, 0, st>>>(sc, fp, cap);

