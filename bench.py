@@ -356,37 +356,44 @@ def scaleup_leg(rtb, S, torch, dev, stream, flush, steps, with_nrc):
                     f"{W}x{H}, depth {D}, {len(sc.lights)} lights",
     }
     if with_nrc:
+        # the four views with the cache at depth 2, in one persistent launch
+        # (inference and one training step after it), trained online launch
+        # after launch; judged against the plain full-depth views above
+        full = [o.clone() for o in outs]
         nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=1))
-        cached = torch.empty(W * H * 3, device=dev)
-        for k in range(32):                      # online training, the views in turn
-            rtb.rt_render_nrc(scene.handle, nrc, views[k % 4], W, H, D, cached, train=True, options=opts)
-        nrays = 0
-        nms, rel = [], []
-        for k, v in enumerate(views):
-            nst = rtb.rt_render_nrc(scene.handle, nrc, v, W, H, D, cached, train=True, options=opts, stats=True)
-            nrays += nst["primary"] + nst["shadow"] + nst["secondary"]
+        cached = [torch.empty(W * H * 3, device=dev) for _ in views]
+        bn = rtb.Batch([scene] * 4, views, [W] * 4, [H] * 4, D, cached, opts)
+        for k in range(32):                      # online training
+            bn.render_nrc(nrc, train=True, tune=tune)
+        nst = bn.render_nrc(nrc, train=True, tune=tune, stats=True)
+        nrays = nst["primary"] + nst["shadow"] + nst["secondary"]
+        nms = []
+        for k in range(steps):
             flush.zero_()
             e0, e1 = ev(), ev()
             e0.record(stream)
-            rtb.rt_render_nrc(scene.handle, nrc, v, W, H, D, cached, train=True, options=opts)
+            bn.render_nrc(nrc, train=True, tune=tune)
             e1.record(stream)
             torch.cuda.synchronize()
             nms.append(e0.elapsed_time(e1))
-            x, r = cached.double(), outs[k].double()
-            rel.append(float(((x - r) ** 2 / (r ** 2 + 0.01)).mean()))
-        nrc_ms = sum(nms)
+        rel = [float(((x.double() - r.double()) ** 2 / (r.double() ** 2 + 0.01)).mean()) for x, r in zip(cached, full)]
+        nrc_ms = sum(nms) / len(nms)
         line["radiance_cache"] = {
-            "metric": "Mrays-equivalent/s (full-depth rays per cached frame, 4 views)",
+            "metric": "Mrays-equivalent/s (full-depth rays of the 4 views per cached launch)",
             "value": rays / (nrc_ms * 1e3), "ms_4_views": nrc_ms, "vs_plain_batch": ms / nrc_ms,
-            "relmse_vs_full_depth": rel, "rays_traced_4_views": nrays, "warmup_frames": 32,
+            "relmse_vs_full_depth": rel, "rays_traced_4_views": nrays, "warmup_launches": 32,
+            "cache_hits": nst["hits_per_depth"][2],
+            "launch": "one persistent launch of the 4 views (rt_batch_render_nrc), the cache's inference over "
+                      "their depth-2 hits, one training step (65,536 samples) and Adam",
         }
+        bn.close()
         rtb.rt_nrc_destroy(nrc)
     b.close()
     scene.close()
     return line
 
 
-def passes_leg(rtb, S, torch, dev, stream, flush, steps):
+def passes_leg(rtb, S, torch, dev, stream, flush, steps, with_nrc=True):
     """Progressive passes of the headline terrain with sampled lights (two
     area lights and a glowing sphere besides the 4 point lights), jittered
     camera rays over 4 x 4 strata, depth 5; once with light sampling alone
@@ -416,6 +423,45 @@ def passes_leg(rtb, S, torch, dev, stream, flush, steps):
         out[name] = {"value": rays / (ms * 1e3), "ms_per_pass": ms, "rays_per_pass": rays,
                      "shadow_per_pass": sum(c["shadow"] for c in counted) / len(counted),
                      "secondary_per_pass": sum(c["secondary"] for c in counted) / len(counted)}
+    if with_nrc:
+        # the radiance cache fed by GI paths: passes with the diffuse bounce
+        # whose depth-2 hits read the cache, trained online on the GI paths
+        # a seeded subset traces to full depth; Mrays-equivalent = the
+        # full-depth GI pass's rays / the cached pass's time (with training)
+        opts = rtb.make_options(background=sc.background, flags=rtb.RT_FLAG_DIFFUSE_BOUNCE)
+        nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=1))
+        for k in range(64):
+            rtb.rt_render_nrc_pass(scene.handle, nrc, sc.camera, W, H, D, rtb.make_pass(k, 7, 4, True), acc, True,
+                                   opts)
+        nst = rtb.rt_render_nrc_pass(scene.handle, nrc, sc.camera, W, H, D, rtb.make_pass(64, 7, 4, True), acc, True,
+                                     opts, stats=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            rtb.rt_render_nrc_pass(scene.handle, nrc, sc.camera, W, H, D, rtb.make_pass(65 + k, 7, 4, True), acc,
+                                   True, opts)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(c) for a, c in ev) / steps
+        # judged on the mean of 8 passes against the mean of the same 8 full-depth passes
+        full = torch.empty(W * H * 3, device=dev)
+        cached = torch.empty(W * H * 3, device=dev)
+        for k in range(8):
+            ps = rtb.make_pass(k, 11, 4, True)
+            rtb.rt_render_pass(scene.handle, sc.camera, W, H, D, ps, full, opts)
+            rtb.rt_render_nrc_pass(scene.handle, nrc, sc.camera, W, H, D, ps, cached, False, opts)
+        torch.cuda.synchronize()
+        x, r = cached.double(), full.double()
+        out["gi_cache"] = {
+            "value": out["gi"]["rays_per_pass"] / (ms * 1e3), "ms_per_pass": ms,
+            "vs_gi_plain": out["gi"]["ms_per_pass"] / ms,
+            "relmse_vs_full_depth_8_passes": float(((x - r) ** 2 / (r ** 2 + 0.01)).mean()),
+            "rays_traced_per_pass": nst["primary"] + nst["shadow"] + nst["secondary"],
+            "cache_depth": 2, "warmup_passes": 64,
+            "metric": "Mrays-equivalent/s (rays of the full-depth GI pass per cached GI pass, with training)",
+        }
+        rtb.rt_nrc_destroy(nrc)
     scene.close()
     return out
 
@@ -697,7 +743,7 @@ def main():
         batch_line = batch_leg(rtb, S, torch, dev, stream, flush, max(args.steps // 2, 3))
     passes_line = None
     if world == 1 and not args.no_passes:
-        passes_line = passes_leg(rtb, S, torch, dev, stream, flush, max(args.steps // 2, 3))
+        passes_line = passes_leg(rtb, S, torch, dev, stream, flush, max(args.steps // 2, 3), not args.no_nrc)
     scaleup_line = None
     if world == 1 and not args.no_scaleup:
         scaleup_line = scaleup_leg(rtb, S, torch, dev, stream, flush, 3, not args.no_nrc)

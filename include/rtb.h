@@ -110,7 +110,9 @@ enum {
                                       no emission where it hits: emitters are sampled as lights.
                                       Only the Lambert lobe is integrated.  Such a frame runs
                                       every depth as a wavefront (as RT_FLAG_PER_DEPTH_WAVEFRONT).
-                                      Not with the radiance cache (RT_ERR_UNSUPPORTED). */
+                                      With the radiance cache: frames and passes take it (the
+                                      cache then learns from GI paths); a batch does not
+                                      (RT_ERR_UNSUPPORTED). */
   RT_FLAG_SERIAL_STAGES = 64,      /* run each depth's shadow kernel on the caller's stream after
                                       that depth's closest-hit kernel, not beside the next depth on
                                       a side stream: with RT_FLAG_STAGE_TIMING every kernel is then
@@ -422,15 +424,29 @@ rt_status rt_nrc_infer(rt_nrc* nrc, rt_scene* s, const float* pnv_device, int64_
 /* One training step (gradient + Adam) on n samples: pnv n x 9, target n x 3. */
 rt_status rt_nrc_train_step(rt_nrc* nrc, rt_scene* s, const float* pnv_device, const float* target_device,
                             int64_t n, void* stream);
-/* A frame whose hits at cfg.terminate_depth take their radiance from the
- * cache (no shadow or secondary rays there); when `train` is set, a seeded
- * subset of those hits (about train_batch) is also traced to max_depth with
- * unit weight, the results become training targets and one Adam step runs
- * after the frame.  Options (NULL = defaults) and stats as in rt_render_ex
+/* A frame whose hits at cfg.terminate_depth take the radiance they reflect
+ * from the cache (no shadow or secondary rays there; the hit's own emission
+ * L_e is added as at any hit, unless a diffuse bounce reached it); when
+ * `train` is set, a seeded subset of those hits (about train_batch) is also
+ * traced to max_depth with unit weight, the results become training targets
+ * and one Adam step runs after the frame.  Options (NULL = defaults) and stats as in rt_render_ex
  * (rays actually traced). */
 rt_status rt_render_nrc(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int width, int height, int max_depth,
                         float* out_rgb_device, int train, const rt_render_options* opt, rt_render_stats* stats,
                         void* stream);
+
+/* rt_render_pass with the radiance cache: pass `pass->index` (its light
+ * samples, jitter and, with RT_FLAG_DIFFUSE_BOUNCE, its bounce directions)
+ * rendered as rt_render_nrc renders a frame - hits at the cache's depth take
+ * the radiance they reflect from the cache, a seeded subset is traced on
+ * into training targets when `train` is set, then one training step - and
+ * folded into accum_rgb_device as rt_render_pass does.  With the diffuse
+ * bounce the training targets are Monte-Carlo GI paths (Eq. 8's hemisphere
+ * integral), and the frame runs every depth as a wavefront.  The cache has
+ * no counterpart in the paper; the passes are those of Sec. IV.A. */
+rt_status rt_render_nrc_pass(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int width, int height, int max_depth,
+                             const rt_pass* pass, float* accum_rgb_device, int train,
+                             const rt_render_options* options, rt_render_stats* stats, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched rendering.  The paper renders one scene at a time; this renders
@@ -473,6 +489,21 @@ rt_status rt_batch_render(rt_batch* b, const rt_tune* tune, rt_render_stats* sta
  * valid). */
 rt_status rt_batch_autotune(rt_batch* b, rt_tune* best, float* best_ms, void* stream);
 rt_status rt_batch_destroy(rt_batch* b);
+
+/* The radiance cache (rt_nrc) inside the batch's persistent launch: every
+ * frame's hits at the cache's terminate_depth end their path in the cache
+ * (one inference record each, the network's answer added after the launch);
+ * with train set, a seeded subset of them (about train_batch over the whole
+ * batch) is traced on to max_depth with unit weight into training targets,
+ * and one training step runs after the launch.  Every frame must show the
+ * scene the cache was created for (RT_ERR_INVALID_ARG otherwise); not with
+ * RT_FLAG_DIFFUSE_BOUNCE (RT_ERR_UNSUPPORTED).  Launched directly (no
+ * graph): the batch kernel, the inference kernel, and with train the
+ * training, Adam and repack kernels.  tune: NULL = the batch's autotuned
+ * choice.  stats as rt_batch_render.  The paper has no counterpart: it
+ * neither batches nor caches (Sec. IV.A per frame). */
+rt_status rt_batch_render_nrc(rt_batch* b, rt_nrc* nrc, int train, const rt_tune* tune, rt_render_stats* stats,
+                              void* stream);
 
 /* The one-call form of a batch: renders frame i = (scenes[i], cameras[i],
  * widths[i] x heights[i]) into out_rgb[i] for i < n, to max_depth, in one

@@ -874,7 +874,14 @@ static v3 trace_rec(trace_ctx* cx, const ray_t* r, int depth, v3 w, int64_t pixe
   if (prim0) { *prim0 = h.prim; *t0 = h.t; }
   if (h.prim < 0) return mul(w, s->bg);
   cx->counts[3 + 3 * depth + 2]++;
-  if (depth == s->nrc_depth) return mul(w, cache_radiance(s, r, h));
+  if (depth == s->nrc_depth) {
+    /* the cache stands for the radiance the hit reflects; its own L_e is
+     * added as at any hit (not on a diffuse bounce, whose parent sampled
+     * the emitters) */
+    v3 c = cache_radiance(s, r, h);
+    if (!(code & CODE_BOUNCE)) c = add(c, s->mats[s->prims[h.prim].mat].emis);
+    return mul(w, c);
+  }
   shade_t sh = shade_hit(s, r, w, h.prim, h.t, h.cosn, depth < cx->max_depth, cx->use_bvh, 1, pixel, code);
   if (sh.robust < cx->robust) cx->robust = sh.robust;
   if (sh.robust_struct < cx->robust_struct) cx->robust_struct = sh.robust_struct;
@@ -907,7 +914,12 @@ static v3 trace_iter(trace_ctx* cx, const ray_t* r0, int64_t pixel, int32_t* pri
       if (depth == 0 && prim0) { *prim0 = h.prim; *t0 = h.t; }
       if (h.prim < 0) { pix = add(pix, mul(cur[i].w, s->bg)); continue; }
       cx->counts[3 + 3 * depth + 2]++;
-      if (depth == s->nrc_depth) { pix = add(pix, mul(cur[i].w, cache_radiance(s, &cur[i].r, h))); continue; }
+      if (depth == s->nrc_depth) {
+        v3 c = cache_radiance(s, &cur[i].r, h);
+        if (!(cur[i].code & CODE_BOUNCE)) c = add(c, s->mats[s->prims[h.prim].mat].emis);
+        pix = add(pix, mul(cur[i].w, c));
+        continue;
+      }
       shade_t sh = shade_hit(s, &cur[i].r, cur[i].w, h.prim, h.t, h.cosn, depth < cx->max_depth, 0, 0, pixel,
                              cur[i].code);
       cx->counts[1] += (uint64_t)sh.n_shadow;

@@ -22,7 +22,7 @@ __all__ = [
     "rt_nrc_config_default", "rt_nrc_create", "rt_nrc_destroy", "rt_nrc_get_params", "rt_nrc_set_params",
     "rt_nrc_get_grads", "rt_nrc_infer", "rt_nrc_train_step", "rt_render_nrc", "rt_nrc_save", "rt_nrc_load",
     "rt_tune", "rt_batch_create", "rt_batch_set_cameras", "rt_batch_render", "rt_batch_autotune",
-    "rt_batch_destroy", "rt_render_batch", "Batch", "rt_pass", "rt_scene_set_area_lights", "rt_render_pass",
+    "rt_batch_destroy", "rt_render_batch", "rt_batch_render_nrc", "rt_render_nrc_pass", "Batch", "rt_pass", "rt_scene_set_area_lights", "rt_render_pass",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -165,6 +165,8 @@ def lib():
             "rt_batch_autotune": (I, [P, P, P, P]),
             "rt_batch_destroy": (I, [P]),
             "rt_render_batch": (I, [P, P, P, P, I, I, P, P, P]),
+            "rt_batch_render_nrc": (I, [P, P, I, P, P, P]),
+            "rt_render_nrc_pass": (I, [P, P, P, I, I, I, P, P, I, P, P, P]),
             "rt_scene_set_area_lights": (I, [P, P, S]),
             "rt_render_pass": (I, [P, P, I, I, I, P, P, P, P, P]),
             "rt_render_host_async": (I, [P, P, I, I, I, P, P, P]),
@@ -483,6 +485,17 @@ def rt_render_pass(scene, camera, width, height, max_depth, pass_, accum_rgb, op
     return stats_dict(st, max_depth) if st is not None else None
 
 
+def rt_render_nrc_pass(scene, nrc, camera, width, height, max_depth, pass_, accum_rgb, train=True, options=None,
+                       stats=False, stream=None):
+    """rt_render_pass with the radiance cache (see rt_render_nrc)."""
+    cam = make_camera(camera)
+    st = rt_render_stats() if stats else None
+    _check(lib().rt_render_nrc_pass(scene, nrc, ctypes.byref(cam), width, height, max_depth, ctypes.byref(pass_),
+                                    _dptr(accum_rgb), int(train), ctypes.byref(options) if options is not None else None,
+                                    ctypes.byref(st) if st is not None else None, _stream(stream)))
+    return stats_dict(st, max_depth) if st is not None else None
+
+
 def rt_batch_create(scenes, cameras, widths, heights, max_depth, outs, options=None):
     """scenes: rt_scene handles; cameras: camera tuples or rt_camera; outs: device tensors."""
     n = len(scenes)
@@ -507,6 +520,14 @@ def rt_batch_render(batch, tune=None, stats=False, max_depth=RT_MAX_DEPTH, strea
     st = rt_render_stats() if stats else None
     _check(lib().rt_batch_render(batch, ctypes.byref(tune) if tune is not None else None,
                                  ctypes.byref(st) if st is not None else None, _stream(stream)))
+    return stats_dict(st, max_depth) if st is not None else None
+
+
+def rt_batch_render_nrc(batch, nrc, train=False, tune=None, stats=False, max_depth=RT_MAX_DEPTH, stream=None):
+    """The batch with the radiance cache at its terminate depth (one launch, then inference and training)."""
+    st = rt_render_stats() if stats else None
+    _check(lib().rt_batch_render_nrc(batch, nrc, int(bool(train)), ctypes.byref(tune) if tune is not None else None,
+                                     ctypes.byref(st) if st is not None else None, _stream(stream)))
     return stats_dict(st, max_depth) if st is not None else None
 
 
@@ -546,6 +567,9 @@ class Batch:
 
     def render(self, tune=None, stats=False, stream=None):
         return rt_batch_render(self.handle, tune, stats, self.max_depth, stream)
+
+    def render_nrc(self, nrc, train=False, tune=None, stats=False, stream=None):
+        return rt_batch_render_nrc(self.handle, nrc, train, tune, stats, self.max_depth, stream)
 
     def autotune(self, stream=None):
         return rt_batch_autotune(self.handle, stream)

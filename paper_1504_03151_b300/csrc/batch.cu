@@ -20,6 +20,7 @@
 #include <cstring>
 #include <vector>
 
+#include "nrc_internal.cuh"
 #include "rtb_internal.cuh"
 #include "trace_device.cuh"
 
@@ -51,6 +52,23 @@ struct BatchCounts {
   unsigned shadow[RT_MAX_DEPTH + 1];   // shadow rays cast from depth-d hits
   unsigned hits[RT_MAX_DEPTH + 1];
   unsigned fetch;                      // next tile
+  unsigned infer_count, train_count;   // radiance-cache records of the launch
+  unsigned cache_hits;                 // hits at the cache depth
+};
+
+// The radiance cache in a batch (nrc_depth < 0: off): hits at nrc_depth
+// push an inference record (p, pixel) (n) (-d) (w, frame) and end their
+// path, except a seeded subset (probability train_batch / the previous
+// launch's cache hits), which is traced on with unit weight into a training
+// target (pixel ids < 0 route to target slot ~pixel).
+struct BatchNrc {
+  int depth;
+  float4* infer_q;
+  float4* train_q;
+  float* target;
+  unsigned infer_cap, train_cap, train_batch;
+  const unsigned* prev_hits;
+  uint32_t seed;
 };
 
 struct BatchParams {
@@ -62,10 +80,13 @@ struct BatchParams {
   float bg_r, bg_g, bg_b, eps_scale;
   BatchCounts* cnt;
   PassInfo ps;   // area-light samples and camera jitter: pass 0 of seed 0, no jitter
+  BatchNrc nrc;
 };
 
-__device__ __forceinline__ void add_rgb(float* fb, int pixel, f3 c) {
-  float* p = fb + 3 * (size_t)pixel;
+// Adds radiance to a pixel of the frame, or to a training target of the
+// radiance cache when the path belongs to its training subset (pixel < 0).
+__device__ __forceinline__ void add_rgb(float* fb, float* target, int pixel, f3 c) {
+  float* p = pixel >= 0 ? fb + 3 * (size_t)pixel : target + 3 * (size_t)(~pixel);
   atomicAdd(p, c.x);
   atomicAdd(p + 1, c.y);
   atomicAdd(p + 2, c.z);
@@ -101,7 +122,8 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
   DevScene sc;
   sc.n_prims = 0;
   float* fb = nullptr;
-  int cap = 0;
+  float* const target = bp.nrc.target;
+  int cap = 0, frame = 0;
   WorkCount wc = {0u, 0u, 0u, 0u};
   for (;;) {
     // --- refill lanes without an item: own overflow, then the warp's stack
@@ -149,6 +171,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
         else hi = mid - 1;
       }
       const BatchScene* bs = bp.scenes + lo;
+      frame = lo;
       sc = bs->sc;
       fb = bs->fb;
       cap = bs->cap;
@@ -175,23 +198,58 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
       float tm = tmax_item;
       int h = traverse<true, false, kThreads>(sc, make_ray(o, d), 0.0f, tm, stack, cap, sfail, wc);
       if (sfail) atomicOr(sc.status, kErrTraversalLimit);
-      if (h < 0 && !sfail) add_rgb(fb, pixel, w);
+      if (h < 0 && !sfail) add_rgb(fb, target, pixel, w);
     } else if (have) {
       float t = INFINITY;
       bool fail = false;
       int hit = traverse<false, false, kThreads>(sc, make_ray(o, d), 0.0f, t, stack, cap, fail, wc);
       if (fail) atomicOr(sc.status, kErrTraversalLimit);
       atomicAdd(&s_cnt[0][depth], 1u);
-      if (hit < 0) {
-        add_rgb(fb, pixel, w * bg);
+      bool live = hit >= 0;
+      Surface sf;
+      if (!live) {
+        add_rgb(fb, target, pixel, w * bg);
       } else {
         atomicAdd(&s_cnt[2][depth], 1u);
-        Surface sf = surface_at(sc, hit, o, d, t, bp.eps_scale);
+        sf = surface_at(sc, hit, o, d, t, bp.eps_scale);
         // L_e (not on a diffuse bounce: its parent sampled the emitters)
         const bool via_bounce = kPass && (code & kCodeBounce) != 0u;
-        const uint32_t vcode = kPass ? (code & ~kCodeBounce) : code;
         if (!via_bounce && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f))
-          add_rgb(fb, pixel, w * sf.emission);
+          add_rgb(fb, target, pixel, w * sf.emission);
+        if (depth == bp.nrc.depth) {
+          // the radiance cache: this hit's radiance comes from the network
+          atomicAdd(&bp.cnt->cache_hits, 1u);
+          const unsigned pos = atomicAdd(&bp.cnt->infer_count, 1u);
+          if (pos < bp.nrc.infer_cap) {
+            float4* q = bp.nrc.infer_q + 4 * (size_t)pos;
+            q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float(pixel));
+            q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
+            q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
+            q[3] = make_float4(w.x, w.y, w.z, __int_as_float(frame));
+          } else {
+            atomicOr(sc.status, kErrQueueOverflow);
+          }
+          const unsigned prev = bp.nrc.prev_hits ? *bp.nrc.prev_hits : 0u;
+          const float u = (float)(hash32(bp.nrc.seed ^ hash32((uint32_t)pixel * 0x9E3779B9u ^
+                                                               __float_as_uint(d.x) ^ (uint32_t)frame * 0x85EBCA6Bu)) >>
+                                  8) *
+                          (1.0f / 16777216.0f);
+          const bool sel = bp.nrc.train_batch > 0 && (prev == 0u || (float)bp.nrc.train_batch > u * (float)prev);
+          const unsigned slot = sel ? atomicAdd(&bp.cnt->train_count, 1u) : 0u;
+          if (sel && slot < bp.nrc.train_cap) {
+            float4* q = bp.nrc.train_q + 3 * (size_t)slot;
+            q[0] = make_float4(sf.p.x, sf.p.y, sf.p.z, __int_as_float((int)slot));
+            q[1] = make_float4(sf.n.x, sf.n.y, sf.n.z, 0.f);
+            q[2] = make_float4(-d.x, -d.y, -d.z, 0.f);
+            w = mk3(1.f, 1.f, 1.f);
+            pixel = ~(int)slot;   // traced on, with unit weight, into the training target
+          } else {
+            live = false;          // this path ends in the cache
+          }
+        }
+      }
+      if (live) {
+        const uint32_t vcode = kPass ? (code & ~kCodeBounce) : code;
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
           // point lights, then one sampled point of each area light and emitter
           for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights + sc.n_emitters : 0); ++li) {
@@ -224,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<kThreads>()) k_batc
             bool sfail = false;
             int h = traverse<true, false, kThreads>(sc, make_ray(os, sd), 0.0f, tmax, stack, cap, sfail, wc);
             if (sfail) atomicOr(sc.status, kErrTraversalLimit);
-            if (h < 0 && !sfail) add_rgb(fb, pixel, contrib);
+            if (h < 0 && !sfail) add_rgb(fb, target, pixel, contrib);
           }
         }
         if (depth < bp.max_depth) {
@@ -337,6 +395,7 @@ struct rt_batch {
   rt_render_options opt;
   int device = 0, sm_count = 0;
   Buf table, counts;
+  Buf fbs;                            // device array of the frames' images (the cache's inference adds there)
   BatchScene* host_table = nullptr;   // pinned staging of the device table
   cudaStream_t cap_stream = nullptr;  // graphs are captured here (never the caller's stream)
   struct Graph {
@@ -377,20 +436,19 @@ static rt_status batch_table(rt_batch* b, const rt_tune& tune, unsigned* n_tiles
                     "rt_batch_render: table");
 }
 
-// The launch of one tune: counters, image clears and the kernel, captured
-// on the batch's own stream into a graph (once per tune).
-static rt_status batch_graph(rt_batch* b, const rt_tune& tune, bool pass, unsigned n_tiles, cudaGraphExec_t* exec) {
-  for (auto& g : b->graphs)
-    if (same_tune(g.tune, tune) && g.pass == pass) {
-      *exec = g.exec;
-      return RT_OK;
-    }
-  BatchKernel kern = batch_kernel(tune.block_threads, pass);
+// Blocks of the persistent grid for a tune: as many as fit, or the tune's cap a SM.
+static rt_status batch_grid(const rt_batch* b, const rt_tune& tune, BatchKernel kern, int* grid) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tune.block_threads, 0);
   if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: occupancy");
   if (per_sm < 1) return set_error(RT_ERR_UNSUPPORTED, "rt_batch_render: the kernel does not fit on an SM");
   if (tune.blocks_per_sm > 0) per_sm = std::min(per_sm, tune.blocks_per_sm);
+  *grid = b->sm_count * per_sm;
+  return RT_OK;
+}
+
+// The kernel's parameters for a tune, with the radiance cache off.
+static BatchParams batch_params(const rt_batch* b, const rt_tune& tune, unsigned n_tiles) {
   BatchParams bp;
   bp.scenes = (const BatchScene*)b->table.p;
   bp.n = b->n;
@@ -406,12 +464,38 @@ static rt_status batch_graph(rt_batch* b, const rt_tune& tune, bool pass, unsign
   memset(&bp.ps, 0, sizeof(bp.ps));
   bp.ps.strata = 1;
   bp.ps.bounce = (b->opt.flags & RT_FLAG_DIFFUSE_BOUNCE) != 0;
+  memset(&bp.nrc, 0, sizeof(bp.nrc));
+  bp.nrc.depth = -1;
+  return bp;
+}
+
+// Whether the batch needs the kernel instance with the sampling code.
+static bool batch_pass(const rt_batch* b) {
+  bool pass = (b->opt.flags & RT_FLAG_DIFFUSE_BOUNCE) != 0;
+  for (rt_scene* s : b->scenes) pass = pass || s->n_alights > 0 || s->n_emitters > 0;
+  return pass;
+}
+
+// The launch of one tune: counters, image clears and the kernel, captured
+// on the batch's own stream into a graph (once per tune).
+static rt_status batch_graph(rt_batch* b, const rt_tune& tune, bool pass, unsigned n_tiles, cudaGraphExec_t* exec) {
+  for (auto& g : b->graphs)
+    if (same_tune(g.tune, tune) && g.pass == pass) {
+      *exec = g.exec;
+      return RT_OK;
+    }
+  BatchKernel kern = batch_kernel(tune.block_threads, pass);
+  int grid = 0;
+  rt_status rs = batch_grid(b, tune, kern, &grid);
+  if (rs) return rs;
+  BatchParams bp = batch_params(b, tune, n_tiles);
+  cudaError_t e;
   cudaStream_t cs = b->cap_stream;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_error(e, "rt_batch_render: begin capture");
   cudaMemsetAsync(b->counts.p, 0, sizeof(BatchCounts), cs);
   for (int i = 0; i < b->n; ++i) cudaMemsetAsync(b->outs[i], 0, (size_t)b->W[i] * b->H[i] * 3 * sizeof(float), cs);
-  kern<<<b->sm_count * per_sm, tune.block_threads, 0, cs>>>(bp);
+  kern<<<grid, tune.block_threads, 0, cs>>>(bp);
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
   e = cudaGetLastError();
@@ -435,8 +519,7 @@ static rt_status batch_render(rt_batch* b, const rt_tune& tune, cudaStream_t st)
   unsigned n_tiles = 0;
   rt_status rs = batch_table(b, tune, &n_tiles, st);
   if (rs) return rs;
-  bool pass = (b->opt.flags & RT_FLAG_DIFFUSE_BOUNCE) != 0;
-  for (rt_scene* s : b->scenes) pass = pass || s->n_alights > 0 || s->n_emitters > 0;
+  const bool pass = batch_pass(b);
   cudaGraphExec_t exec = nullptr;
   if ((rs = batch_graph(b, tune, pass, n_tiles, &exec))) return rs;
   // the tile count depends only on the sizes and the tile shape, both fixed per graph
@@ -509,17 +592,15 @@ rt_status rt_batch_set_cameras(rt_batch* b, const rt_camera* cameras) {
   return RT_OK;
 }
 
-rt_status rt_batch_render(rt_batch* b, const rt_tune* tune, rt_render_stats* stats, void* stream) {
-  if (!b) return set_error(RT_ERR_INVALID_ARG, "rt_batch_render: batch is NULL");
+}  // extern "C"
+
+namespace rtb {
+
+// Sums the launch's counters into *stats (syncs `stream`) and returns the
+// scenes' latched errors.
+static rt_status batch_stats(rt_batch* b, rt_render_stats* stats, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  // the staging copy of the previous render may still be in flight
-  cudaError_t e = cudaStreamSynchronize(b->cap_stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render");
-  rt_status rs = batch_render(b, tune ? *tune : b->best, st);
-  if (rs) return rs;
-  if (!stats) return RT_OK;
-  e = cudaStreamSynchronize(st);
+  cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_error(e, "rt_batch_render");
   BatchCounts c;
   e = cudaMemcpy(&c, b->counts.p, sizeof(c), cudaMemcpyDeviceToHost);
@@ -533,12 +614,103 @@ rt_status rt_batch_render(rt_batch* b, const rt_tune* tune, rt_render_stats* sta
     if (d == 0) stats->primary = c.rays[0];
     else stats->secondary += c.rays[d];
   }
-  stats->launches = 1;
   for (int i = 0; i < b->n; ++i) {
-    rs = rt_scene_sync(b->scenes[i], stream);
+    rt_status rs = rt_scene_sync(b->scenes[i], stream);
     if (rs) return rs;
   }
   return RT_OK;
+}
+
+}  // namespace rtb
+
+extern "C" {
+
+rt_status rt_batch_render(rt_batch* b, const rt_tune* tune, rt_render_stats* stats, void* stream) {
+  if (!b) return set_error(RT_ERR_INVALID_ARG, "rt_batch_render: batch is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  // the staging copy of the previous render may still be in flight
+  cudaError_t e = cudaStreamSynchronize(b->cap_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render");
+  rt_status rs = batch_render(b, tune ? *tune : b->best, st);
+  if (rs) return rs;
+  if (!stats) return RT_OK;
+  rs = batch_stats(b, stats, stream);
+  if (!rs) stats->launches = 1;
+  return rs;
+}
+
+rt_status rt_batch_render_nrc(rt_batch* b, rt_nrc* nrc, int train, const rt_tune* tune_in, rt_render_stats* stats,
+                              void* stream) {
+  if (!b || !nrc) return set_error(RT_ERR_INVALID_ARG, "rt_batch_render_nrc: NULL batch or cache");
+  for (int i = 0; i < b->n; ++i)
+    if (b->scenes[i] != nrc_scene(nrc))
+      return set_error(RT_ERR_INVALID_ARG, "rt_batch_render_nrc: every frame must show the scene of the cache");
+  if (b->opt.flags & RT_FLAG_DIFFUSE_BOUNCE)
+    return set_error(RT_ERR_UNSUPPORTED, "rt_batch_render_nrc: the radiance cache does not take RT_FLAG_DIFFUSE_BOUNCE");
+  const rt_tune tune = tune_in ? *tune_in : b->best;
+  if (!valid_tune(tune))
+    return set_error(RT_ERR_INVALID_ARG, "rt_batch_render_nrc: tune needs tile_w * tile_h == 32, block_threads 64, "
+                                         "128 or 256 and blocks_per_sm >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(b->cap_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render_nrc");
+  unsigned n_tiles = 0;
+  rt_status rs = batch_table(b, tune, &n_tiles, st);
+  if (rs) return rs;
+  // inference records: up to two children per dielectric hit above the cache
+  // depth; 2 x the batch's pixels is the frames' ray-queue default
+  int64_t pixels = 0;
+  for (int i = 0; i < b->n; ++i) pixels += (int64_t)b->W[i] * b->H[i];
+  NrcFrame nf;
+  if ((rs = nrc_frame_buffers(nrc, std::min<int64_t>(2 * pixels, 0x7fffffff), train != 0, &nf))) return rs;
+  if (!b->fbs.p) {
+    if ((rs = ensure(b->fbs, sizeof(float*) * b->n))) return rs;
+    e = cudaMemcpy(b->fbs.p, b->outs.data(), sizeof(float*) * b->n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "rt_batch_render_nrc: image table");
+  }
+  const bool pass = batch_pass(b);
+  BatchKernel kern = batch_kernel(tune.block_threads, pass);
+  int grid = 0;
+  if ((rs = batch_grid(b, tune, kern, &grid))) return rs;
+  BatchParams bp = batch_params(b, tune, n_tiles);
+  const int T = nf.depth <= b->max_depth ? nf.depth : -1;
+  bp.nrc.depth = T;
+  bp.nrc.infer_q = nf.infer_q;
+  bp.nrc.train_q = nf.train_q;
+  bp.nrc.target = nf.target;
+  bp.nrc.infer_cap = nf.infer_cap;
+  bp.nrc.train_cap = nf.train_cap;
+  bp.nrc.train_batch = train ? nf.train_batch : 0u;
+  bp.nrc.prev_hits = nrc_prev_hits(nrc);
+  bp.nrc.seed = nf.seed;
+  BatchCounts* cnt = (BatchCounts*)b->counts.p;
+  unsigned* status = b->scenes[0]->status;
+  if (T >= 0 && train) cudaMemsetAsync(nf.target, 0, (size_t)nf.train_cap * 12, st);
+  cudaMemsetAsync(cnt, 0, sizeof(BatchCounts), st);
+  for (int i = 0; i < b->n; ++i) cudaMemsetAsync(b->outs[i], 0, (size_t)b->W[i] * b->H[i] * 3 * sizeof(float), st);
+  kern<<<grid, tune.block_threads, 0, st>>>(bp);
+  int launches = 1;
+  if (T >= 0) {
+    // the cache's answers for every frame's hits at depth T, then one
+    // training step on the launch's targets
+    if ((rs = nrc_infer_launch(nrc, nf.infer_q, &cnt->infer_count, nf.infer_cap, nullptr, nullptr, status, st,
+                               (float* const*)b->fbs.p)))
+      return rs;
+    nrc_keep_hits(nrc, &cnt->cache_hits, st);
+    launches += 1;
+    if (train) {
+      if ((rs = nrc_train_launch(nrc, nf.train_q, nf.target, &cnt->train_count, nf.train_cap, status, st))) return rs;
+      launches += 3;
+    }
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "rt_batch_render_nrc: launch");
+  if (!stats) return RT_OK;
+  rs = batch_stats(b, stats, stream);
+  if (!rs) stats->launches = launches;
+  return rs;
 }
 
 rt_status rt_batch_autotune(rt_batch* b, rt_tune* best, float* best_ms, void* stream) {
@@ -621,6 +793,7 @@ rt_status rt_batch_destroy(rt_batch* b) {
   for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
   release(b->table);
   release(b->counts);
+  release(b->fbs);
   if (b->host_table) cudaFreeHost(b->host_table);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;

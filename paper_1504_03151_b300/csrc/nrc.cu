@@ -117,7 +117,7 @@ __device__ __forceinline__ void fb_add(float* fb, float* target, int pixel, floa
 __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const float4* __restrict__ recs,
                                                             const unsigned* __restrict__ count, unsigned cap,
                                                             float* __restrict__ fb, float* __restrict__ out3,
-                                                            unsigned* status) {
+                                                            unsigned* status, float* const* __restrict__ fbs) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint64_t* mbar = (uint64_t*)(sm + kSmMisc);
   uint32_t* tslot = (uint32_t*)(sm + kSmMisc + 8);
@@ -156,13 +156,14 @@ __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const
     bool valid = row < n;
     float f[96];
     float wr = 0.f, wg = 0.f, wb = 0.f;
-    int pixel = 0;
+    int pixel = 0, frame = 0;
     if (valid) {
       float4 q0 = recs[4 * (size_t)row], q1 = recs[4 * (size_t)row + 1], q2 = recs[4 * (size_t)row + 2],
              q3 = recs[4 * (size_t)row + 3];
       float pnv[9] = {q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z};
       encode81(pnv, lo, ie, f);
       pixel = __float_as_int(q0.w);
+      frame = __float_as_int(q3.w);
       wr = q3.x;
       wg = q3.y;
       wb = q3.z;
@@ -209,7 +210,8 @@ __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const
             out3[3 * (size_t)row + 1] = y1;
             out3[3 * (size_t)row + 2] = y2;
           }
-          if (fb) fb_add(fb, nd.target, pixel, wr * y0, wg * y1, wb * y2);
+          if (fbs) fb_add(fbs[frame], nd.target, pixel, wr * y0, wg * y1, wb * y2);
+          else if (fb) fb_add(fb, nd.target, pixel, wr * y0, wg * y1, wb * y2);
         }
         tc::fence_before_sync();
         __syncthreads();
@@ -583,6 +585,7 @@ void nrc_make_records(const float* pnv, const float* targets, int64_t n, float4*
 using namespace rtb;
 
 struct rt_nrc {
+  const rt_scene* scene = nullptr;   // the scene it was created for (its box normalises the encoding)
   rt_nrc_config cfg;
   NrcDevice nd;
   Buf params, m, v, grad, packed;
@@ -623,11 +626,11 @@ static rt_status nrc_pack(rt_nrc* r, cudaStream_t st) {
 }
 
 rt_status nrc_infer_launch(rt_nrc* r, const float4* recs, const unsigned* count, unsigned cap, float* fb,
-                           float* out3, unsigned* status, cudaStream_t st) {
+                           float* out3, unsigned* status, cudaStream_t st, float* const* fbs) {
   rt_status rs = nrc_setup_kernels();
   if (rs) return rs;
   int blocks = r->infer_blocks;
-  k_nrc_infer<<<blocks, kInferThreads, kInferSmem, st>>>(r->nd, recs, count, cap, fb, out3, status);
+  k_nrc_infer<<<blocks, kInferThreads, kInferSmem, st>>>(r->nd, recs, count, cap, fb, out3, status, fbs);
   return cuda_error(cudaGetLastError(), "nrc infer");
 }
 
@@ -649,6 +652,8 @@ rt_status nrc_train_launch(rt_nrc* r, const float4* recs, const float* targets, 
 }
 
 NrcDevice* nrc_device(rt_nrc* r) { return &r->nd; }
+
+const rt_scene* nrc_scene(const rt_nrc* r) { return r->scene; }
 
 const unsigned* nrc_prev_hits(rt_nrc* r) { return (const unsigned*)r->counters.p + 4; }
 
@@ -706,6 +711,7 @@ rt_status rt_nrc_create(rt_scene* s, const rt_nrc_config* cfg_in, rt_nrc** out) 
       !(cfg.beta2 >= 0.f && cfg.beta2 < 1.f) || !(cfg.eps > 0.f))
     return set_error(RT_ERR_INVALID_ARG, "rt_nrc_create: invalid configuration");
   rt_nrc* r = new rt_nrc();
+  r->scene = s;
   r->cfg = cfg;
   cudaDeviceGetAttribute(&r->sm_count, cudaDevAttrMultiProcessorCount, s->device);
   r->infer_blocks = r->sm_count * 2;

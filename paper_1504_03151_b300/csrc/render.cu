@@ -216,10 +216,16 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
     Surface sf;
     sf.kind = RT_MAT_DIELECTRIC;   // no local term, no children unless a hit sets it
     if (is_hit) sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
+    // L_e, Eq. 7 (not on a diffuse bounce: its parent sampled the emitters)
+    const bool via_bounce = kPass && (code & kCodeBounce) != 0u;
+    const uint32_t vcode = kPass ? (code & ~kCodeBounce) : code;
+    const bool emits =
+        is_hit && !via_bounce && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f);
+    if (emits) add_fb(fp, pixel, w * sf.emission);
     if (depth == fp.nrc_depth) {
-      // radiance cache: every hit here takes the rest of its path from the
-      // cache; a seeded subset is also traced on, with unit weight, into a
-      // training target
+      // radiance cache: every hit here takes the radiance it reflects from
+      // the cache (its own L_e is added above, as at any hit); a seeded
+      // subset is also traced on, with unit weight, into a training target
       bool ok;
       unsigned pos = warp_push(&ctr->infer_count, is_hit, fp.infer_cap, ok, sc.status);
       if (ok) {
@@ -244,11 +250,6 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
       }
       is_hit = sel;
     }
-    // L_e, Eq. 7 (not on a diffuse bounce: its parent sampled the emitters)
-    const bool via_bounce = kPass && (code & kCodeBounce) != 0u;
-    const uint32_t vcode = kPass ? (code & ~kCodeBounce) : code;
-    if (is_hit && !via_bounce && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f))
-      add_fb(fp, pixel, w * sf.emission);
     // Alg. 1: one shadow ray per point light where n.l > 0
     bool local = is_hit && sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f;
     for (int li = 0; li < sc.n_lights; ++li) {
@@ -466,6 +467,9 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
       if (live) {
         atomicAdd(&s_cnt[2][depth], 1u);
         sf = surface_at(sc, hit, o, d, t, fp.eps_scale);
+        // L_e, Eq. 7 (frames with the diffuse bounce run every depth as a
+        // wavefront, so no path here is a bounce and every hit adds its L_e)
+        if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
         if (depth == fp.nrc_depth) {
           // radiance cache (as in k_trace); the selection probability comes
           // from the previous frame's number of cache hits
@@ -497,10 +501,7 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_PATHS_MIN_BLOCKS) k_paths(D
           }
         }
       }
-      // (frames with the diffuse bounce run every depth as a wavefront, so
-      // no path here is a bounce and every hit adds its L_e)
       if (live) {
-        if (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f) add_fb(fp, pixel, w * sf.emission);
         if (sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f) {
           // point lights, then one sampled point of each area light and emitter
           for (int li = 0; li < sc.n_lights + (kPass ? sc.n_alights + sc.n_emitters : 0); ++li) {
@@ -823,8 +824,6 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
   if (!std::isfinite(opt.background[0]) || !std::isfinite(opt.background[1]) || !std::isfinite(opt.background[2]) ||
       !std::isfinite(opt.eps_scale) || opt.eps_scale < 0.f || opt.queue_capacity < 0 || opt.traversal_cap < 0)
     return set_error(RT_ERR_INVALID_ARG, "rt_render: invalid options");
-  if (nrc && (opt.flags & RT_FLAG_DIFFUSE_BOUNCE))
-    return set_error(RT_ERR_UNSUPPORTED, "rt_render_nrc: the radiance cache does not take RT_FLAG_DIFFUSE_BOUNCE");
   const bool deterministic = (opt.flags & RT_FLAG_DETERMINISTIC) != 0;
   if (nrc && deterministic)
     return set_error(RT_ERR_UNSUPPORTED, "rt_render_nrc: the radiance cache does not take RT_FLAG_DETERMINISTIC");
@@ -1114,8 +1113,12 @@ __global__ void k_accumulate(float* __restrict__ accum, const float* __restrict_
   accum[i] = k == 0 ? img[i] : accum[i] + (img[i] - accum[i]) / (float)(k + 1);
 }
 
-rt_status rt_render_pass(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth, const rt_pass* pass,
-                         float* accum, const rt_render_options* opt, rt_render_stats* stats, void* stream) {
+}  // extern "C"
+
+// One pass (with or without the radiance cache) folded into the running mean.
+static rt_status render_pass_impl(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
+                                  const rt_pass* pass, float* accum, const rt_render_options* opt,
+                                  rt_render_stats* stats, void* stream, rt_nrc* nrc, int train) {
   if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_render_pass: scene is NULL");
   if (!pass || !accum) return set_error(RT_ERR_INVALID_ARG, "rt_render_pass: NULL pass or image");
   if (pass->index < 0 || pass->strata < 1 || pass->reserved != 0)
@@ -1125,11 +1128,25 @@ rt_status rt_render_pass(rt_scene* s, const rt_camera* cam, int width, int heigh
   rt_status rs = ensure(s->pass_img, n * sizeof(float));
   if (rs) return rs;
   cudaStream_t st = (cudaStream_t)stream;
-  rs = render_impl(s, cam, width, height, max_depth, (float*)s->pass_img.p, opt, nullptr, nullptr, stats, st,
-                   nullptr, 0, pass);
+  rs = render_impl(s, cam, width, height, max_depth, (float*)s->pass_img.p, opt, nullptr, nullptr, stats, st, nrc,
+                   train, pass);
   if (rs) return rs;
   k_accumulate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(accum, (const float*)s->pass_img.p, n, pass->index);
   return cuda_error(cudaGetLastError(), "rt_render_pass");
+}
+
+extern "C" {
+
+rt_status rt_render_pass(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth, const rt_pass* pass,
+                         float* accum, const rt_render_options* opt, rt_render_stats* stats, void* stream) {
+  return render_pass_impl(s, cam, width, height, max_depth, pass, accum, opt, stats, stream, nullptr, 0);
+}
+
+rt_status rt_render_nrc_pass(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int width, int height, int max_depth,
+                             const rt_pass* pass, float* accum, int train, const rt_render_options* opt,
+                             rt_render_stats* stats, void* stream) {
+  if (!nrc) return set_error(RT_ERR_INVALID_ARG, "rt_render_nrc_pass: cache is NULL");
+  return render_pass_impl(s, cam, width, height, max_depth, pass, accum, opt, stats, stream, nrc, train);
 }
 
 rt_status rt_render_nrc(rt_scene* s, rt_nrc* nrc, const rt_camera* cam, int width, int height, int max_depth,

@@ -207,3 +207,116 @@ def test_batch_argument_errors(frames):
     assert ei.value.status == rtb.RT_ERR_NOT_BUILT
     b2.close()
     raw.close()
+
+
+# ---------------------------------------------------------------------------
+# the radiance cache inside the persistent launch
+# ---------------------------------------------------------------------------
+def _cache_frames():
+    """One terrain (mirror and glass icospheres) seen by three cameras at
+    three sizes, and a radiance cache on it trained a few steps on smooth
+    targets so that its answers vary over the scene."""
+    sc = small_terrain(w=72, h=40, depth=5)
+    scene = rtb.Scene(sc).build()
+    views = [sc.camera, S.camera((10.0, 8.0, 20.0), (0.0, 0.0, 0.0)), S.camera((-12.0, 6.0, -18.0), (0.0, 1.0, 0.0))]
+    sizes = [(72, 40), (40, 72), (33, 17)]
+    nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=21))
+    V = np.concatenate([sc.triangles["v0"], sc.triangles["v1"], sc.triangles["v2"]]).astype(np.float64)
+    rng = np.random.default_rng(8)
+    n = 2048
+    p = rng.uniform(V.min(0), V.max(0), (n, 3))
+    nv = rng.normal(size=(n, 6)).reshape(n, 2, 3)
+    nv /= np.linalg.norm(nv, axis=2, keepdims=True)
+    pnv = np.concatenate([p, nv.reshape(n, 6)], 1).astype(np.float32)
+    tgt = (0.2 + 0.1 * np.cos(pnv[:, :3])).astype(np.float32)
+    for _ in range(5):
+        rtb.rt_nrc_train_step(nrc, scene.handle, torch.from_numpy(pnv).cuda(), torch.from_numpy(tgt).cuda(), n)
+    return sc, scene, views, sizes, nrc
+
+
+def test_batch_cache_matches_cached_frames():
+    """rt_batch_render_nrc without training makes, frame by frame, the image
+    rt_render_nrc makes with the same network: the same hits read the cache
+    at depth 2 and nothing is traced past it."""
+    sc, scene, views, sizes, nrc = _cache_frames()
+    outs = [torch.full((w * h * 3,), float("nan"), device="cuda") for w, h in sizes]
+    b = rtb.Batch([scene] * 3, views, [w for w, _ in sizes], [h for _, h in sizes], 5, outs,
+                  rtb.make_options(background=sc.background))
+    st = b.render_nrc(nrc, train=False, stats=True)
+    assert sum(st["rays_per_depth"][3:]) == 0 and st["hits_per_depth"][2] > 0
+    torch.cuda.synchronize()
+    for o, v, (w, h) in zip(outs, views, sizes):
+        ref = torch.empty(w * h * 3, device="cuda")
+        rtb.rt_render_nrc(scene.handle, nrc, v, w, h, 5, ref, train=False,
+                          options=rtb.make_options(background=sc.background))
+        torch.cuda.synchronize()
+        assert_same_image(o.view(h * w, 3).double().cpu().numpy(), ref.view(h * w, 3).double().cpu().numpy())
+    b.close()
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()
+
+
+def test_batch_cache_matches_oracle():
+    """The batched cached frames against the oracle's cached-frame render
+    (the same BF16 network at depth 2)."""
+    sc, scene, views, sizes, nrc = _cache_frames()
+    import oracle as O
+    outs = [torch.empty(w * h * 3, device="cuda") for w, h in sizes]
+    b = rtb.Batch([scene] * 3, views, [w for w, _ in sizes], [h for _, h in sizes], 5, outs,
+                  rtb.make_options(background=sc.background))
+    b.render_nrc(nrc, train=False)
+    torch.cuda.synchronize()
+    params = rtb.rt_nrc_get_params(nrc)
+    V = np.concatenate([sc.triangles["v0"], sc.triangles["v1"], sc.triangles["v2"]])
+    lo32, hi32 = V.min(0).astype(np.float32), V.max(0).astype(np.float32)
+    orc = O.OracleScene.from_scene(sc)
+    orc.set_cache(2, params, lo32.astype(np.float64), (np.float32(1.0) / (hi32 - lo32)).astype(np.float64), bf16=True)
+    for o, v, (w, h) in zip(outs, views, sizes):
+        ref = orc.render(v, w, h, 5, mode="brute")
+        img = o.view(h * w, 3).double().cpu().numpy()
+        err = np.abs(img - ref["rgb"]).max(axis=1)
+        robust = ref["robust"] >= 1.0
+        # the cache's BF16 answers: the bar of the cached-frame tests
+        assert not ((err > COLOUR_TOL) & robust).any(), np.where((err > COLOUR_TOL) & robust)[0][:10]
+        assert (err > COLOUR_TOL).mean() <= 5e-3
+    b.close()
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()
+
+
+def test_batch_cache_trains_and_checks_its_scene():
+    """With training the launch also traces a subset of the cached hits to
+    full depth (rays past depth 2), the network moves and stays finite, and
+    the image is the inference-only image of the network it started with.
+    A frame of another scene is refused."""
+    sc, scene, views, sizes, nrc = _cache_frames()
+    outs = [torch.empty(w * h * 3, device="cuda") for w, h in sizes]
+    b = rtb.Batch([scene] * 3, views, [w for w, _ in sizes], [h for _, h in sizes], 5, outs,
+                  rtb.make_options(background=sc.background))
+    b.render_nrc(nrc, train=False)
+    torch.cuda.synchronize()
+    a = [o.clone() for o in outs]
+    p0 = rtb.rt_nrc_get_params(nrc)
+    st = b.render_nrc(nrc, train=True, stats=True)
+    assert sum(st["rays_per_depth"][3:]) > 0
+    torch.cuda.synchronize()
+    for x, y in zip(a, outs):
+        np.testing.assert_allclose(x.cpu().numpy(), y.cpu().numpy(), atol=1e-5)
+    p1 = rtb.rt_nrc_get_params(nrc)
+    assert np.isfinite(p1).all() and np.abs(p1 - p0).max() > 0
+    for _ in range(8):
+        b.render_nrc(nrc, train=True)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    assert np.isfinite(rtb.rt_nrc_get_params(nrc)).all()
+    other = rtb.Scene(S.scene_spheres8(width=16, height=16)).build()
+    o2 = torch.empty(16 * 16 * 3, device="cuda")
+    b2 = rtb.Batch([scene, other], views[:1] + [S.scene_spheres8().camera], [72, 16], [40, 16], 5,
+                   [outs[0], o2], rtb.make_options(background=sc.background))
+    with pytest.raises(rtb.RtError) as ei:
+        b2.render_nrc(nrc)
+    assert ei.value.status == rtb.RT_ERR_INVALID_ARG
+    b2.close()
+    other.close()
+    b.close()
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()

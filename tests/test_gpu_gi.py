@@ -138,3 +138,104 @@ def test_full_size_lit_terrain_sampled_parity(flags):
     px = np.sort(np.random.default_rng(21).choice(W * H, 400, replace=False))
     ref = orc.render(sc.camera, W, H, D, mode="bvh", pixels=px)
     check_colour(img[px], ref["rgb"], ref["robust"])
+
+
+# ---------------------------------------------------------------------------
+# the radiance cache fed by Monte-Carlo GI paths
+# ---------------------------------------------------------------------------
+def _scene_box32(sc):
+    """The scene box the library normalises the cache's positions by (FP32)."""
+    pts = [sc.triangles["v0"], sc.triangles["v1"], sc.triangles["v2"]]
+    if len(sc.spheres):
+        c, r = sc.spheres["center"].astype(np.float32), sc.spheres["radius"].astype(np.float32)[:, None]
+        pts += [c - r, c + r]
+    V = np.concatenate([np.asarray(p, np.float32).reshape(-1, 3) for p in pts])
+    lo, hi = V.min(0), V.max(0)
+    return lo.astype(np.float64), (np.float32(1.0) / (hi - lo)).astype(np.float64)
+
+
+def _trained_cache(scene, sc, seed=5):
+    nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=seed))
+    lo, inv = _scene_box32(sc)
+    rng = np.random.default_rng(seed)
+    n = 2048
+    p = lo + rng.uniform(0, 1, (n, 3)) / inv
+    nv = rng.normal(size=(n, 2, 3))
+    nv /= np.linalg.norm(nv, axis=2, keepdims=True)
+    pnv = np.concatenate([p, nv.reshape(n, 6)], 1).astype(np.float32)
+    tgt = (0.2 + 0.1 * np.cos(pnv[:, :3])).astype(np.float32)
+    for _ in range(5):
+        rtb.rt_nrc_train_step(nrc, scene.handle, torch.from_numpy(pnv).cuda(), torch.from_numpy(tgt).cuda(), n)
+    return nrc
+
+
+def test_gi_cached_passes_match_oracle():
+    """Passes with the diffuse bounce and the cache at depth 2 (no
+    training): every depth is a wavefront, bounce rays reaching depth 2 read
+    the cache, and the cached vertices add their own L_e unless a bounce
+    reached them.  Against the oracle's cached GI passes with the same BF16
+    network and the same Philox samples."""
+    sc = S.scene_spheres8_emitters(width=48, height=40, max_depth=4)
+    scene = rtb.Scene(sc).build()
+    nrc = _trained_cache(scene, sc)
+    params = rtb.rt_nrc_get_params(nrc)
+    W, H, D = sc.width, sc.height, sc.max_depth
+    acc = torch.empty(W * H * 3, device="cuda")
+    opts = rtb.make_options(background=sc.background, flags=GI)
+    for k in range(4):
+        rtb.rt_render_nrc_pass(scene.handle, nrc, sc.camera, W, H, D, rtb.make_pass(k, 11, 2, True), acc, train=False,
+                               options=opts)
+    torch.cuda.synchronize()
+    img = acc.view(-1, 3).double().cpu().numpy()
+    orc = O.OracleScene.from_scene(sc)
+    orc.set_diffuse_bounce(True)
+    lo, inv = _scene_box32(sc)
+    orc.set_cache(2, params, lo, inv, bf16=True)
+    ref, robust = None, None
+    for k in range(4):
+        orc.set_pass(11, k, 2, True)
+        r = orc.render(sc.camera, W, H, D, mode="bvh")
+        ref = r["rgb"] if ref is None else ref + (r["rgb"] - ref) / (k + 1)
+        robust = r["robust"] if robust is None else np.minimum(robust, r["robust"])
+    err = np.abs(img - ref).max(axis=1)
+    assert np.isfinite(img).all()
+    # the cache's BF16 answers: the bar of the cached-frame tests
+    assert not ((err > 2e-3) & (robust >= 1)).any(), np.where((err > 2e-3) & (robust >= 1))[0][:10]
+    assert (err > 2e-3).mean() <= 5e-3
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()
+
+
+def test_gi_cache_learns_from_gi_paths():
+    """Online training on GI passes: the targets are the GI paths the tracer
+    traces past the cache's depth; the network moves, stays finite, and the
+    cached passes end up closer to the full-depth GI passes than passes
+    truncated at the cache's depth are."""
+    sc = S.scene_terrain_lit(width=160, height=90, max_depth=5)
+    scene = rtb.Scene(sc).build()
+    W, H, D = sc.width, sc.height, sc.max_depth
+    opts = rtb.make_options(background=sc.background, flags=GI)
+    nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=2))
+    scratch = torch.empty(W * H * 3, device="cuda")
+    p0 = rtb.rt_nrc_get_params(nrc)
+    for k in range(48):
+        st = rtb.rt_render_nrc_pass(scene.handle, nrc, sc.camera, W, H, D, rtb.make_pass(k, 3, 4, True), scratch,
+                                    train=True, options=opts, stats=(k == 0))
+        if k == 0:
+            assert sum(st["rays_per_depth"][3:]) > 0     # training paths go past the cache's depth
+    p1 = rtb.rt_nrc_get_params(nrc)
+    assert np.isfinite(p1).all() and np.abs(p1 - p0).max() > 0
+    n = 16
+    full, trunc, cached = (torch.empty(W * H * 3, device="cuda") for _ in range(3))
+    for k in range(n):                         # other samples than training's (seed 7, not 3)
+        ps = rtb.make_pass(k, 7, 4, True)
+        rtb.rt_render_pass(scene.handle, sc.camera, W, H, D, ps, full, opts)
+        rtb.rt_render_pass(scene.handle, sc.camera, W, H, 2, ps, trunc, opts)
+        rtb.rt_render_nrc_pass(scene.handle, nrc, sc.camera, W, H, D, ps, cached, train=False, options=opts)
+    torch.cuda.synchronize()
+    f, t, c = (x.double().view(-1, 3).cpu().numpy() for x in (full, trunc, cached))
+    rel = lambda x: float(np.mean((x - f) ** 2 / (f ** 2 + 0.01)))
+    print(f"GI relMSE: cache {rel(c):.3e}, truncated {rel(t):.3e}")
+    assert rel(c) < rel(t)
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()

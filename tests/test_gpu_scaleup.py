@@ -60,6 +60,39 @@ def test_scaleup_four_views_sampled_parity():
     scene.close()
 
 
+def test_scaleup_radiance_cache_in_one_launch_sampled_parity():
+    """The four 4K views with the radiance cache at depth 2 of 8, in one
+    persistent launch (rt_batch_render_nrc, the benchmark's scale-up cache
+    leg), against the oracle's cached-frame mode with the same BF16 network
+    on sampled pixels."""
+    sc = S.scene_scaleup()
+    W, H, D = sc.width, sc.height, sc.max_depth
+    scene = rtb.Scene(sc).build()
+    views = S.views_scaleup()
+    outs = [torch.empty(W * H * 3, device="cuda") for _ in views]
+    b = rtb.Batch([scene] * 4, views, [W] * 4, [H] * 4, D, outs, rtb.make_options(background=sc.background))
+    nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=1))
+    for _ in range(3):                        # a few online steps: the network is no longer its initial one
+        b.render_nrc(nrc, train=True)
+    st = b.render_nrc(nrc, train=False, stats=True)
+    assert st["primary"] == 4 * W * H and sum(st["rays_per_depth"][3:]) == 0
+    torch.cuda.synchronize()
+    params = rtb.rt_nrc_get_params(nrc)
+    V = np.concatenate([sc.triangles["v0"], sc.triangles["v1"], sc.triangles["v2"]])
+    lo32, hi32 = V.min(0).astype(np.float32), V.max(0).astype(np.float32)
+    orc = O.OracleScene.from_scene(sc)
+    orc.set_cache(2, params, lo32.astype(np.float64), (np.float32(1.0) / (hi32 - lo32)).astype(np.float64), bf16=True)
+    rng = np.random.default_rng(13)
+    for v, o in zip(views, outs):
+        img = o.view(H * W, 3).double().cpu().numpy()
+        px = np.sort(rng.choice(W * H, 300, replace=False))
+        ref = orc.render(v, W, H, D, mode="bvh", pixels=px)
+        check_sampled(img[px], ref)
+    rtb.rt_nrc_destroy(nrc)
+    b.close()
+    scene.close()
+
+
 def test_sixty_four_scene_batch_sampled_parity():
     scs = S.scene_batch()
     scenes = [rtb.Scene(x).build() for x in scs]

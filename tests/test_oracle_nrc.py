@@ -163,3 +163,37 @@ def test_cached_frame_closed_form():
     assert cached["counts"]["shadow"] == 0
     orc.clear_cache()
     np.testing.assert_array_equal(orc.render(cam, 40, 30, 3, mode="brute")["rgb"], plain["rgb"])
+
+
+def test_cached_vertex_adds_its_own_emission():
+    # The cache stands for the radiance a hit reflects; the hit's own L_e
+    # (Eq. 7) is added as at any other hit.  A constant cache c at depth 1
+    # behind a rho = 1 mirror: where the reflection meets the emitting
+    # sphere the pixel is exactly c + L_e, elsewhere c or the background.
+    from paper_1504_03151_b300 import scenes as S
+    big = 50.0
+    plane = S.triangles_from([(-big, 0, -big), (-big, 0, -big)], [(-big, 0, big), (big, 0, big)],
+                             [(big, 0, big), (big, 0, -big)], 0)
+    sph = S.spheres_from([(0.0, 1.5, -1.0)], [1.0], [1])
+    Le = np.array([0.3, 0.1, 0.05])
+    mats = np.concatenate([S.material(S.MAT_MIRROR, (0.5, 0.5, 0.5), reflectivity=1.0),
+                           S.material(S.MAT_DIFFUSE, (0.8, 0.3, 0.2), emission=tuple(Le))])
+    cam = S.camera((0, 4, 6), (0, 0, -2))
+    orc = O.OracleScene(sph, plane, mats, np.zeros(0, S.LIGHT_DTYPE), background=(0.1, 0.2, 0.3))
+    Le = Le.astype(np.float32).astype(np.float64)   # the scene's values are FP32
+    c = np.array([0.25, 0.5, 2.0])
+    params = np.zeros(O.N_W + O.N_B)
+    params[O.N_W + O.N_B - 3:] = np.log(c)
+    plain = orc.render(cam, 40, 30, 3, mode="brute")
+    orc.set_cache(1, params, lo=np.zeros(3), inv_ext=np.ones(3), bf16=False)
+    cached = orc.render(cam, 40, 30, 3, mode="brute")
+    it = orc.render(cam, 40, 30, 3, mode="iterative")
+    np.testing.assert_allclose(cached["rgb"], it["rgb"], atol=1e-14)
+    on_mirror = plain["prim"] >= 1
+    # with no lights, a reflection that meets the sphere shows exactly its L_e in the plain frame
+    sees_sphere = on_mirror & (np.abs(plain["rgb"] - Le).max(1) < 1e-12)
+    assert sees_sphere.sum() > 20
+    np.testing.assert_allclose(cached["rgb"][sees_sphere], np.tile(c + Le, (sees_sphere.sum(), 1)), atol=1e-14)
+    # the sphere seen directly (depth 0, before the cache) shows its L_e
+    direct = plain["prim"] == 0
+    np.testing.assert_allclose(cached["rgb"][direct], np.tile(Le, (direct.sum(), 1)), atol=1e-14)
