@@ -213,10 +213,11 @@ def test_batch_argument_errors(frames):
 # the radiance cache inside the persistent launch
 # ---------------------------------------------------------------------------
 def _cache_frames():
-    """One terrain (mirror and glass icospheres) seen by three cameras at
-    three sizes, and a radiance cache on it trained a few steps on smooth
-    targets so that its answers vary over the scene."""
-    sc = small_terrain(w=72, h=40, depth=5)
+    """One terrain with 20 icospheres (its mirrors and glass give the first
+    view some 50 hits at depth 2) seen by three cameras at three sizes, and a
+    radiance cache on it trained a few steps on smooth targets so that its
+    answers vary over the scene."""
+    sc = S.scene_terrain(seed=3, width=72, height=40, max_depth=5, cells=(16, 12), n_ico=20, ico_level=1)
     scene = rtb.Scene(sc).build()
     views = [sc.camera, S.camera((10.0, 8.0, 20.0), (0.0, 0.0, 0.0)), S.camera((-12.0, 6.0, -18.0), (0.0, 1.0, 0.0))]
     sizes = [(72, 40), (40, 72), (33, 17)]
