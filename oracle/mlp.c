@@ -113,10 +113,10 @@ double orc_mlp_loss_grad_ex(int64_t n, const double* x, const double* target, co
       const double* Wl = W + w_off(l);
       double* dWl = dW + w_off(l);
       double* dBl = dB + b_off(l);
-      double gr[96];   /* the gradient the weight and input gradients use */
+      double gr[96];   /* the backward signal as stored: what every gradient of this layer uses */
       for (int o = 0; o < DIMS[l + 1]; ++o) gr[o] = bf16 ? orc_round_bf16(g[l + 1][o]) : g[l + 1][o];
       for (int o = 0; o < DIMS[l + 1]; ++o) {
-        dBl[o] += g[l + 1][o];
+        dBl[o] += gr[o];
         for (int k = 0; k < DIMS[l]; ++k) dWl[(int64_t)o * DIMS[l] + k] += gr[o] * a[l][k];
       }
       if (l > 0) {

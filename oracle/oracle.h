@@ -170,10 +170,10 @@ double orc_mlp_loss_grad(int64_t n, const double* x, const double* target,
                          double* dB);
 
 /* As above with bf16 != 0: hidden activations rounded to BF16 after the
- * ReLU, and the gradients w.r.t. pre-activations rounded to BF16 where
- * they enter the weight and input gradients (bias gradients use the
- * unrounded values); the network's activations are BF16 by design, the
- * accumulation stays FP64. */
+ * ReLU, and the gradients w.r.t. pre-activations (the backward signal)
+ * rounded to BF16 as they are stored, so that the weight, bias and input
+ * gradients all use the stored values; the network's activations and
+ * backward signals are BF16 by design, the accumulation stays FP64. */
 void orc_mlp_forward_ex(int64_t n, const double* x, const double* W, const double* B, double* y, int bf16);
 double orc_mlp_loss_grad_ex(int64_t n, const double* x, const double* target, const double* W,
                             const double* B, double* dW, double* dB, int bf16);

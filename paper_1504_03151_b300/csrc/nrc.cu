@@ -226,32 +226,43 @@ done:
 }
 
 // ---------------------------------------------------------------------------
-// training: forward (activations kept), loss gradient, backward; weight
-// gradients accumulate in tensor memory over the CTA's tiles, then go to
-// global memory with atomics.  One CTA per SM (512 tensor-memory columns).
+// training: forward (activations kept), loss gradient, backward; weight and
+// bias gradients accumulate in tensor memory over the CTA's tiles, then go
+// to its own row of the gradient buffer.  One CTA per SM (its 512
+// tensor-memory columns), 128 samples a tile, one sample a thread.
+//
+// Every activation is stored once, row by row (a sample's features in
+// 16-byte chunks, the K-major layout of the forward MMAs).  The
+// weight-gradient MMAs, whose K is the batch, read the same tiles as
+// MN-major operands, so no transposed copy is made.  The activation tiles
+// carry a constant column of ones past their features, so each weight-
+// gradient MMA also sums the backward signal over the batch: the bias
+// gradient of that layer.
 // ---------------------------------------------------------------------------
 constexpr int kTrainThreads = 128;
 constexpr int kTrainTmemCols = 512;
-// tensor-memory columns
+// activation tiles: width (features + the ones column, padded to 8)
+constexpr int kXW = 104;    // X: 96 features, ones at column 96
+constexpr int kHW = 80;     // H1..H4: 64 features, ones at column 64
+// tensor-memory columns (16-aligned)
 constexpr int kTcAcc = 0;      // 64: forward / backward accumulator (M = 128)
-constexpr int kTcDW0 = 64;     // 96: dW0 (M = 64, N = 96)
-constexpr int kTcDW1 = 160;    // 64 each: dW1, dW2, dW3
-constexpr int kTcDW4 = 352;    // 16: dW4^T (M = 64, N = 16)
+constexpr int kTcDW0 = 64;     // 104: dW0 | dB0 (M = 64, N = 104)
+constexpr int kTcDW1 = 176;    // 80 each at 176, 256, 336: dW_l | dB_l (M = 64, N = 80)
+constexpr int kTcDW4 = 416;    // 16: dW4^T (M = 64, N = 16)
 // shared memory (bytes)
 constexpr int kTsW0 = 0, kTsW1 = 12288, kTsW2 = 20480, kTsW3 = 28672, kTsW4 = 36864;   // forward, 38 KB
 constexpr int kTsT1 = 38912, kTsT2 = 47104, kTsT3 = 55296, kTsT4 = 63488;              // backward, 26 KB
-constexpr int kTsA = 65536;      // 24 KB: X (K = 96), then H (K = 64)
-constexpr int kTsXT = 90112;     // 24 KB: X^T [96][128]
-constexpr int kTsHT = 114688;    // 4 x 16 KB: H1^T .. H4^T [64][128]
-constexpr int kTsDZ = 180224;    // 16 KB: dZ [128][64] (dZ5: [128][16])
-constexpr int kTsDZT = 196608;   // 16 KB: dZ^T [64][128] (dZ5^T: [16][128])
-constexpr int kTsBias = 212992;  // 272 floats
-constexpr int kTsDB = 214528;    // 4 x 272 floats: bias gradients, one set per warp (summed in warp order)
-constexpr int kTsMisc = 218880;  // mbarrier, tmem slot, flags, loss of each warp
-constexpr int kTrainSmem = kTsMisc + 64;
+constexpr int kTsX = 65536;                        // X [128][104]: 26 KB
+constexpr int kTsH = kTsX + 128 * kXW * 2;         // H1..H4 [128][80]: 4 x 20 KB
+constexpr int kTsDZ = kTsH + 4 * 128 * kHW * 2;    // dZ [128][64] (dZ5: [128][16]): 16 KB
+constexpr int kTsBias = kTsDZ + 16384;             // 272 floats
+constexpr int kTsDB = kTsBias + 1088;              // dB4 of each warp: 4 x 4 floats
+constexpr int kTsMisc = kTsDB + 64;                // mbarrier, tmem slot, loss of each warp
+// the allocation ends 32 KB past the last tile, so that no operand
+// descriptor can reach past it whatever its strides
+constexpr int kTrainSmem = kTsMisc + 64 + 32768;
 static_assert(kTrainSmem <= 227 * 1024, "the training CTA's shared memory exceeds the per-block limit");
 
-// Lane of row m of an M = 64 accumulator: 16 rows in each 32-lane quarter.
 // One CTA's gradient row: the kNP parameter gradients (oracle layout), then
 // the loss, padded to whole float4.
 constexpr int kGPRow = (kNP + 1 + 3) / 4 * 4;
@@ -264,16 +275,23 @@ __device__ __forceinline__ void store16(float* dst, const float* v) {   // dst 1
   d[3] = make_float4(v[12], v[13], v[14], v[15]);
 }
 
+// Lane of row m of an M = 64 accumulator: 16 rows in each 32-lane quarter.
 __device__ __forceinline__ int m64_row_of_lane(int lane) { return (lane & 31) < 16 ? (lane >> 5) * 16 + (lane & 31) : -1; }
-
-__device__ __forceinline__ void store_transposed(uint8_t* tileT, int col, int rows, const float* v) {
-  // element (k, col) of a [rows][128] K-major tile for k < rows
-  for (int k = 0; k < rows; ++k) *(uint16_t*)(tileT + tc::core_off(k, col, 128)) = bf16_bits(v[k]);
-}
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// The constant columns of a [128][width] activation tile: ones at column
+// `col`, zeros up to the width (chunks from col / 8 on).
+__device__ __forceinline__ void fill_ones(uint8_t* tile, int width, int col) {
+  for (int i = threadIdx.x; i < 128 * (width - col) / 8; i += blockDim.x) {
+    const int r = i / ((width - col) / 8), c = col / 8 + i % ((width - col) / 8);
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (c == col / 8) v[0] = 1.f;
+    store_chunk(tile, r, c, width, v);
+  }
 }
 
 __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, const float4* __restrict__ recs,
@@ -285,8 +303,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
   uint32_t* tslot = (uint32_t*)(sm + kTsMisc + 8);
   float* s_loss = (float*)(sm + kTsMisc + 16);   // [4]
   float* bias = (float*)(sm + kTsBias);
-  float* db = (float*)(sm + kTsDB);
-  float* db_w = db + (threadIdx.x >> 5) * kPackedBias;   // this warp's set: only its lane 0 adds to it
+  float* db4 = (float*)(sm + kTsDB);              // [warp][4]
   int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc::alloc(tc::smem_u32(tslot), kTrainTmemCols);
   const uint16_t* pw = (const uint16_t*)nd.packed;
@@ -299,9 +316,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
   load_tile(sm + kTsT2, pw + kPT2, 64, 64);
   load_tile(sm + kTsT3, pw + kPT3, 64, 64);
   load_tile(sm + kTsT4, pw + kPT4, 64, 16);
+  fill_ones(sm + kTsX, kXW, 96);
+  for (int l = 0; l < 4; ++l) fill_ones(sm + kTsH + l * 128 * kHW * 2, kHW, 64);
   const float* gb = (const float*)(pw + kPackedBf16);
   for (int i = tid; i < kPackedBias; i += blockDim.x) bias[i] = gb[i];
-  for (int i = tid; i < 4 * kPackedBias; i += blockDim.x) db[i] = 0.f;
+  if (tid < 16) db4[tid] = 0.f;
   if (tid == 0) {
     tc::mbar_init(tc::smem_u32(mbar), 1);
     *s_loss = 0.f;
@@ -317,11 +336,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
                           tc::smem_u32(sm + kTsW3), tc::smem_u32(sm + kTsW4)};
   const uint32_t sT[5] = {0u, tc::smem_u32(sm + kTsT1), tc::smem_u32(sm + kTsT2), tc::smem_u32(sm + kTsT3),
                           tc::smem_u32(sm + kTsT4)};
-  const uint32_t sA = tc::smem_u32(sm + kTsA), sXT = tc::smem_u32(sm + kTsXT), sDZ = tc::smem_u32(sm + kTsDZ),
-                 sDZT = tc::smem_u32(sm + kTsDZT);
-  uint32_t sHT[5];
-  sHT[0] = sXT;
-  for (int l = 1; l <= 4; ++l) sHT[l] = tc::smem_u32(sm + kTsHT + (l - 1) * 16384);
+  // the activation entering layer l: X, then H1..H4, and its tile width
+  uint32_t sAct[5];
+  sAct[0] = tc::smem_u32(sm + kTsX);
+  for (int l = 1; l <= 4; ++l) sAct[l] = tc::smem_u32(sm + kTsH + (l - 1) * 128 * kHW * 2);
+  const uint32_t sDZ = tc::smem_u32(sm + kTsDZ);
   unsigned n = min(*count, cap);
   unsigned tiles = (n + 127) / 128;
   float inv_n3 = n > 0 ? 1.0f / (3.0f * (float)n) : 0.f;
@@ -347,32 +366,35 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
     unsigned row = tile * 128 + tid;
     bool valid = row < n;
     uint32_t mask[4][2];   // ReLU masks of the 4 hidden layers (64 bits each)
-    float f[96];
     float tr = 0.f, tg = 0.f, tb = 0.f;
-    if (valid) {
-      float4 q0 = recs[3 * (size_t)row], q1 = recs[3 * (size_t)row + 1], q2 = recs[3 * (size_t)row + 2];
-      float pnv[9] = {q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z};
-      encode81(pnv, lo, ie, f);
-      int slot = __float_as_int(q0.w);
-      tr = targets[3 * (size_t)slot];
-      tg = targets[3 * (size_t)slot + 1];
-      tb = targets[3 * (size_t)slot + 2];
-    } else {
+    {
+      float f[96];
+      if (valid) {
+        float4 q0 = recs[3 * (size_t)row], q1 = recs[3 * (size_t)row + 1], q2 = recs[3 * (size_t)row + 2];
+        float pnv[9] = {q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z};
+        encode81(pnv, lo, ie, f);
+        int slot = __float_as_int(q0.w);
+        tr = targets[3 * (size_t)slot];
+        tg = targets[3 * (size_t)slot + 1];
+        tb = targets[3 * (size_t)slot + 2];
+      } else {
 #pragma unroll
-      for (int k = 0; k < 96; ++k) f[k] = 0.f;
+        for (int k = 0; k < 96; ++k) f[k] = 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 12; ++c) store_chunk(sm + kTsX, tid, c, kXW, f + 8 * c);
     }
-#pragma unroll
-    for (int c = 0; c < 12; ++c) store_chunk(sm + kTsA, tid, c, 96, f + 8 * c);
-    store_transposed(sm + kTsXT, tid, 96, f);
     tc::fence_proxy_async();
     __syncthreads();
-    // forward
+    // forward: Z_{l+1} = Act_l W_l^T (A = the activation tile, K-major)
     float o[16];
     for (int l = 0; l < 5; ++l) {
       int N = l < 4 ? 64 : 16;
       if (tid == 0) {
         tc::fence_after_sync();
-        tc::gemm(tmem + kTcAcc, sA, sW[l], d_in(l), tc::idesc_bf16_f32(128, N), false);
+        const uint32_t sbo_a = (uint32_t)((l == 0 ? kXW : kHW) / 8) * 128u;
+        const uint32_t sbo_b = (uint32_t)(d_in(l) / 8) * 128u;
+        tc::gemm_kk(tmem + kTcAcc, sAct[l], sbo_a, sW[l], sbo_b, d_in(l), tc::idesc_bf16_f32(128, N), false);
         tc::commit(mb);
       }
       RTB_WAIT();
@@ -388,9 +410,9 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
           mask[l][k >> 5] |= (pos ? 1u : 0u) << (k & 31);
           h[k] = pos ? z : 0.f;
         }
+        uint8_t* hl = sm + kTsH + l * 128 * kHW * 2;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) store_chunk(sm + kTsA, tid, c, 64, h + 8 * c);
-        store_transposed(sm + kTsHT + l * 16384, tid, 64, h);
+        for (int c = 0; c < 8; ++c) store_chunk(hl, tid, c, kHW, h + 8 * c);
         tc::fence_before_sync();
         tc::fence_proxy_async();
         __syncthreads();
@@ -399,7 +421,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
         tc::fence_before_sync();
       }
     }
-    // loss gradient at the exp output: dL/dz5 = 2 (y - t) / (y^2 + 0.01) / (3n) * y
+    // loss gradient at the exp output: dL/dz5 = 2 (y - t) / (y^2 + 0.01) / (3n) * y,
+    // stored in BF16; the output bias gradient sums the stored values
     {
       float g[16];
 #pragma unroll
@@ -417,48 +440,45 @@ __global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, co
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        float s = warp_sum(g[c]);
-        if (lane == 0) db_w[256 + c] += s;
+        float s = warp_sum(bf16_float(bf16_bits(g[c])));
+        if (lane == 0) db4[4 * warp + c] += s;
       }
       store_chunk(sm + kTsDZ, tid, 0, 16, g);
       store_chunk(sm + kTsDZ, tid, 1, 16, g + 8);
-      store_transposed(sm + kTsDZT, tid, 16, g);
       tc::fence_proxy_async();
       __syncthreads();
     }
-    // backward: layer 4 -> 0
+    // backward: layer 4 -> 0.  dW_l | dB_l [M = out][N = in + ones] += dZ^T Act_l,
+    // both operands MN-major over the batch; dAct_l = dZ W_l (K-major)
     for (int l = 4; l >= 0; --l) {
       if (tid == 0) {
         tc::fence_after_sync();
         if (l == 4) {
-          // dW4^T [64 in][16 out] += H4^T . dZ5 (K = batch)
-          tc::gemm(tmem + kTcDW4, sHT[4], sDZT, 128, tc::idesc_bf16_f32(64, 16), !first);
-          // dH4 = dZ5 . W4  (A: dZ5 [128][16], B: W4^T [64][16])
+          // dW4^T [64 in][16 out] += H4^T dZ5: A = H4 (M = in), B = dZ5 (N = out)
+          tc::gemm_mn(tmem + kTcDW4, sAct[4], (uint32_t)(kHW / 8) * 128u, sDZ, 2u * 128u, 128,
+                      tc::idesc_bf16_f32_mn(64, 16), !first);
+          // dH4 = dZ5 W4 (A: dZ5 [128][16], B: W4^T [64][16])
           tc::gemm(tmem + kTcAcc, sDZ, sT[4], 16, tc::idesc_bf16_f32(128, 64), false);
         } else {
-          // dW_l [64 out][in] += dZ_{l+1}^T . H_l (K = batch); H_0 = X
-          uint32_t col = l == 0 ? kTcDW0 : kTcDW1 + 64 * (l - 1);
-          tc::gemm(tmem + col, sDZT, sHT[l], 128, tc::idesc_bf16_f32(64, d_in(l)), !first);
+          // dW_l | dB_l += dZ^T [Act_l | 1]: A = dZ (M = out), B = Act_l (N = in + ones)
+          const uint32_t col = l == 0 ? kTcDW0 : kTcDW1 + 80 * (l - 1);
+          const int width = l == 0 ? kXW : kHW;
+          tc::gemm_mn(tmem + col, sDZ, 8u * 128u, sAct[l], (uint32_t)(width / 8) * 128u, 128,
+                      tc::idesc_bf16_f32_mn(64, width), !first);
           if (l > 0) tc::gemm(tmem + kTcAcc, sDZ, sT[l], 64, tc::idesc_bf16_f32(128, 64), false);
         }
         tc::commit(mb);
       }
       RTB_WAIT();
       if (l == 0) break;
-      // dZ_l = dH_l * relu'(z_l)
+      // dZ_l = dH_l * relu'(z_l), stored in BF16 for both of its MMAs
       float g[64];
 #pragma unroll
       for (int c = 0; c < 4; ++c) tc::ld16(lane_addr + kTcAcc + 16 * c, g + 16 * c);
 #pragma unroll
       for (int k = 0; k < 64; ++k) g[k] = ((mask[l - 1][k >> 5] >> (k & 31)) & 1u) ? g[k] : 0.f;
 #pragma unroll
-      for (int k = 0; k < 64; ++k) {
-        float s = warp_sum(g[k]);
-        if (lane == 0) db_w[64 * (l - 1) + k] += s;
-      }
-#pragma unroll
       for (int c = 0; c < 8; ++c) store_chunk(sm + kTsDZ, tid, c, 64, g + 8 * c);
-      store_transposed(sm + kTsDZT, tid, 64, g);
       tc::fence_before_sync();
       tc::fence_proxy_async();
       __syncthreads();
@@ -477,29 +497,31 @@ done:
     tc::fence_after_sync();
     int m = m64_row_of_lane(tid);
     float v[16];
-    // dW0 (M = 64 x N = 96)
-    for (int c = 0; c < 6; ++c) {
+    // dW0 | dB0 (M = 64 x N = 104): columns 0..95 the weights, 96 the bias
+    for (int c = 0; c < 7; ++c) {
       tc::ld16(lane_addr + kTcDW0 + 16 * c, v);
-      if (m >= 0) store16(gp + off_w(0) + m * 96 + 16 * c, v);
+      if (m >= 0) {
+        if (c < 6) store16(gp + off_w(0) + m * 96 + 16 * c, v);
+        else gp[off_b(0) + m] = v[0];
+      }
     }
     for (int l = 1; l <= 3; ++l)
-      for (int c = 0; c < 4; ++c) {
-        tc::ld16(lane_addr + kTcDW1 + 64 * (l - 1) + 16 * c, v);
-        if (m >= 0) store16(gp + off_w(l) + m * 64 + 16 * c, v);
+      for (int c = 0; c < 5; ++c) {
+        tc::ld16(lane_addr + kTcDW1 + 80 * (l - 1) + 16 * c, v);
+        if (m >= 0) {
+          if (c < 4) store16(gp + off_w(l) + m * 64 + 16 * c, v);
+          else gp[off_b(l) + m] = v[0];
+        }
       }
     // dW4^T [64 in][16 out] -> dW4 [3][64]
     tc::ld16(lane_addr + kTcDW4, v);
     if (m >= 0)
       for (int k = 0; k < 3; ++k) gp[off_w(4) + k * 64 + m] = v[k];
   } else {
-    for (int i = tid; i < kNW; i += blockDim.x) gp[i] = 0.f;
+    for (int i = tid; i < kNW + 4 * 64; i += blockDim.x) gp[i] = 0.f;
   }
-  // the warps' bias gradients and losses, summed in warp order (deterministic)
-  auto db_sum = [&](int i) {
-    return db[i] + db[kPackedBias + i] + db[2 * kPackedBias + i] + db[3 * kPackedBias + i];
-  };
-  for (int i = tid; i < 4 * 64; i += blockDim.x) gp[off_b(0) + i] = have ? db_sum(i) : 0.f;
-  if (tid < 3) gp[off_b(4) + tid] = have ? db_sum(256 + tid) : 0.f;
+  // the output bias gradients and the losses of the warps, summed in warp order (deterministic)
+  if (tid < 3) gp[off_b(4) + tid] = have ? ((db4[tid] + db4[4 + tid]) + db4[8 + tid]) + db4[12 + tid] : 0.f;
   {
     float ls = warp_sum(loss_acc);
     if (lane == 0) s_loss[warp] = ls;

