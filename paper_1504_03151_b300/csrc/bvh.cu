@@ -23,6 +23,11 @@ constexpr int kSortCoopMaxKeys = 1 << 22;  // larger inputs take the multi-launc
 constexpr int kTopBins = 16;        // SAH bins per axis for the top-level rebuild
 constexpr int kTopMaxLevels = 64;   // launches of the level kernel (empty ones return at once)
 constexpr int kTopCache = 4096;     // clusters of one segment held in shared memory (41 B each)
+// A segment of more clusters bins an even subsample of about this many to
+// choose its split plane (the partition still takes every cluster).  On the
+// 1080p terrain the root's 3,299 clusters bin 825: the root split went from
+// 27 to 21 us and the tree's SAH cost stayed 28.500.
+constexpr int kTopSample = 1024;
 constexpr int kTopWarpSeg = 32;     // segments of at most this many clusters are finished by one warp
 constexpr int kTopForceMedian = 32; // from this level on, split segments at the middle: with at
                                     // most 2^28 clusters every segment is done by level 60
@@ -1061,8 +1066,11 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
   __syncthreads();
   const float clo[3] = {o2f(s_cb[0]), o2f(s_cb[1]), o2f(s_cb[2])};
   const float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
-  // bin every axis (strided, so that a warp's lanes spread over the bins)
-  for (int k = t; k < m; k += 256) {
+  // bin every axis (strided, so that a warp's lanes spread over the bins);
+  // a segment of more than kTopSample clusters bins an even subsample of
+  // about that many to choose its plane (the partition takes them all)
+  const int sstep = m > kTopSample ? (m + kTopSample - 1) / kTopSample : 1;
+  for (int k = t * sstep; k < m; k += 256 * sstep) {
     int c;
     float4 lo, hi;
     fetch(k, c, lo, hi);
