@@ -85,7 +85,7 @@ def peaks():
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region:
-    the sampler runs every 20 ms and is running (its first sample is in)
+    the sampler runs every 10 ms and is running (its first sample is in)
     before the region starts; samples that arrive while the region runs are
     its record.  A region shorter than one interval is represented by the
     first sample after it (then "samples" is 0)."""
@@ -93,7 +93,7 @@ class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-    INTERVAL_MS = 20
+    INTERVAL_MS = 10
 
     def __init__(self, gpu_index=0):
         self.gpu = gpu_index
