@@ -56,9 +56,13 @@ struct BuildScratch {
   float* cost_lbvh;
   int* cent_bounds;              // 6 ordered ints
   // top-level rebuild
-  int *clu_a, *clu_b;            // cluster ids (ping-pong)
-  int* clu_link;                 // per cluster: its link (internal LBVH node or leaf link)
-  float4 *clu_lo, *clu_hi;       // per cluster box; lo.w = prim count; hi.w = height
+  // The cluster list, in two ping-pong buffers (a, b) that hold per
+  // position a cluster's id and its box (lo.w = primitive count, hi.w =
+  // height).  k_find_clusters fills buffer a with id = position.
+  int *clu_a, *clu_b;
+  int* clu_link;                 // per cluster id: its link (internal LBVH node or leaf link)
+  float4 *clu_lo, *clu_hi;       // buffer a's boxes
+  float4 *clu_lo_b, *clu_hi_b;   // buffer b's boxes
   int4 *seg_a, *seg_b;           // active segments: (begin, end, parent slot, node id)
   int* seg_count;                // [level] segments; [kTopMaxLevels + 1] clusters; [kTopMaxLevels + 2] small segments
   int* top_count;
@@ -67,6 +71,15 @@ struct BuildScratch {
 };
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// One buffer of the top rebuild's cluster list: a split reads a segment's
+// ids and boxes by position, all in one round trip, and writes them in
+// their new order to the other buffer.
+struct CluList {
+  int* id;
+  float4* lo;
+  float4* hi;
+};
 
 // ---------------------------------------------------------------------------
 // ordered-int encoding of floats for atomic min / max
@@ -747,8 +760,11 @@ __device__ __forceinline__ void write_child(float4* nodes, int node, int side, f
   n[12 + side] = __int_as_float(link);
 }
 
-__device__ __forceinline__ int bin_of(float c, float lo, float ext) {
-  int bi = ext > 0.f ? (int)((c - lo) / ext * kTopBins) : 0;
+// Bin of centroid coordinate c over [lo, lo + extent): inv = kTopBins /
+// extent, or 0 for an empty extent (every centroid in bin 0).
+__device__ __forceinline__ float bin_scale(float ext) { return ext > 0.f ? (float)kTopBins / ext : 0.f; }
+__device__ __forceinline__ int bin_of(float c, float lo, float inv) {
+  const int bi = (int)((c - lo) * inv);
   return min(max(bi, 0), kTopBins - 1);
 }
 
@@ -834,9 +850,8 @@ __device__ __forceinline__ int best_plane(const int (*cnt)[kTopBins], const int 
 // in registers from one load: the same bins, SAH costs, choice and stable
 // partition as the general path below, with fewer passes and barriers.
 // Returns the number of clusters on the left side.
-__device__ __forceinline__ int split_small(int level, int b, int e, const int* ids_in, int* ids_out,
-                                           const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
-                                           float4 side_lo[2], float4 side_hi[2]) {
+__device__ __forceinline__ int split_small(int level, int b, int e, CluList in, CluList out, float4 side_lo[2],
+                                           float4 side_hi[2]) {
   __shared__ int s_cb[6];
   __shared__ int s_cnt[3][kTopBins];
   __shared__ int s_blo[3][kTopBins][3], s_bhi[3][kTopBins][3];
@@ -849,9 +864,9 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
   int c = 0;
   float4 lo = make_float4(0, 0, 0, 0), hi = make_float4(0, 0, 0, 0);
   if (mine) {
-    c = __ldcg(&ids_in[b + t]);
-    lo = clu_lo[c];
-    hi = clu_hi[c];
+    c = __ldcg(&in.id[b + t]);
+    lo = __ldcg(&in.lo[b + t]);
+    hi = __ldcg(&in.hi[b + t]);
   }
   float cc[3] = {0.5f * (lo.x + hi.x), 0.5f * (lo.y + hi.y), 0.5f * (lo.z + hi.z)};
   if (t < 6) {
@@ -887,12 +902,13 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
   }
   __syncthreads();
   const float clo[3] = {o2f(s_cb[0]), o2f(s_cb[1]), o2f(s_cb[2])};
-  const float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
+  const float cinv[3] = {bin_scale(o2f(s_cb[3]) - clo[0]), bin_scale(o2f(s_cb[4]) - clo[1]),
+                         bin_scale(o2f(s_cb[5]) - clo[2])};
   int bin[3];
   const float lo3[3] = {lo.x, lo.y, lo.z}, hi3[3] = {hi.x, hi.y, hi.z};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    bin[a] = bin_of(cc[a], clo[a], cext[a]);
+    bin[a] = bin_of(cc[a], clo[a], cinv[a]);
     if (mine) {
       atomicAdd(&s_cnt[a][bin[a]], (int)lo.w);
       for (int q = 0; q < 3; ++q) {
@@ -938,7 +954,9 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
     const unsigned bl2 = __ballot_sync(0xffffffffu, mine && left), br2 = __ballot_sync(0xffffffffu, mine && !left);
     if (mine) {
       int pos = left ? b + before_l + __popc(bl2 & lt) : b + nleft + before_r + __popc(br2 & lt);
-      ids_out[pos] = c;
+      out.id[pos] = c;
+      out.lo[pos] = lo;
+      out.hi[pos] = hi;
     }
   }
   // the two sides' boxes
@@ -971,9 +989,8 @@ __device__ __forceinline__ int split_small(int level, int b, int e, const int* i
 // issued eight deep.  After that every thread takes a contiguous chunk of
 // the segment for the bounds and the partition: it counts and bounds its
 // two sides in one pass before a block scan places them.
-__device__ __forceinline__ int split_large(int level, int b, int e, const int* ids_in, int* ids_out,
-                                           const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
-                                           int cache_cap, float4 side_lo[2], float4 side_hi[2]) {
+__device__ __forceinline__ int split_large(int level, int b, int e, CluList in, CluList out, int cache_cap,
+                                           float4 side_lo[2], float4 side_hi[2]) {
   __shared__ int s_cb[6];
   __shared__ int bin_count[3][kTopBins];
   __shared__ int bin_lo[3][kTopBins][3], bin_hi[3][kTopBins][3];
@@ -987,7 +1004,7 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
   float4* c_lo = s_dyn;
   float4* c_hi = s_dyn + cache_cap;
   int* c_id = (int*)(s_dyn + 2 * (size_t)cache_cap);
-  int* c_part = c_id + cache_cap;
+  int* c_part = c_id + cache_cap;              // cache slot of each position of the partition
   unsigned char* c_side = (unsigned char*)(c_part + cache_cap);   // side of each cached cluster
   const bool cached = m <= cache_cap;
   if (t < 6) {
@@ -1006,18 +1023,23 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
   if (cached) {
     for (int k0 = t; k0 < m; k0 += 256 * 8) {
       int id[8];
+      float4 l[8], h[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int k = k0 + 256 * u;
-        id[u] = k < m ? __ldcg(&ids_in[b + k]) : 0;
+        if (k < m) {
+          id[u] = __ldcg(&in.id[b + k]);
+          l[u] = __ldcg(&in.lo[b + k]);
+          h[u] = __ldcg(&in.hi[b + k]);
+        }
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int k = k0 + 256 * u;
         if (k < m) {
           c_id[k] = id[u];
-          c_lo[k] = clu_lo[id[u]];
-          c_hi[k] = clu_hi[id[u]];
+          c_lo[k] = l[u];
+          c_hi[k] = h[u];
         }
       }
     }
@@ -1030,9 +1052,9 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
       lo = c_lo[k];
       hi = c_hi[k];
     } else {
-      c = __ldcg(&ids_in[b + k]);
-      lo = clu_lo[c];
-      hi = clu_hi[c];
+      c = __ldcg(&in.id[b + k]);
+      lo = __ldcg(&in.lo[b + k]);
+      hi = __ldcg(&in.hi[b + k]);
     }
   };
   // this thread's chunk [k0, k1); an odd length keeps a warp's strided
@@ -1065,18 +1087,26 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
   }
   __syncthreads();
   const float clo[3] = {o2f(s_cb[0]), o2f(s_cb[1]), o2f(s_cb[2])};
-  const float cext[3] = {o2f(s_cb[3]) - clo[0], o2f(s_cb[4]) - clo[1], o2f(s_cb[5]) - clo[2]};
-  // bin every axis (strided, so that a warp's lanes spread over the bins);
-  // a segment of more than kTopSample clusters bins an even subsample of
-  // about that many to choose its plane (the partition takes them all)
+  const float cinv[3] = {bin_scale(o2f(s_cb[3]) - clo[0]), bin_scale(o2f(s_cb[4]) - clo[1]),
+                         bin_scale(o2f(s_cb[5]) - clo[2])};
+  // bin every axis.  A segment of more than kTopSample clusters bins an
+  // even subsample of about that many to choose its plane (the partition
+  // takes them all).  Lane l of every warp takes samples from the l-th
+  // 32nd of the list, so that the lanes of one atomic lie far apart in the
+  // list, which keeps neighbouring (same-bin) clusters out of one
+  // instruction's lanes; the warps interleave within each lane's part.
   const int sstep = m > kTopSample ? (m + kTopSample - 1) / kTopSample : 1;
-  for (int k = t * sstep; k < m; k += 256 * sstep) {
+  const int n_samp = (m + sstep - 1) / sstep, per_lane = (n_samp + 31) / 32;
+  for (int r = w; r < per_lane; r += 8) {
+    const int q = lane * per_lane + r;
+    if (q >= n_samp) break;
+    const int k = q * sstep;
     int c;
     float4 lo, hi;
     fetch(k, c, lo, hi);
-    const int b0 = bin_of(0.5f * (lo.x + hi.x), clo[0], cext[0]);
-    const int b1 = bin_of(0.5f * (lo.y + hi.y), clo[1], cext[1]);
-    const int b2 = bin_of(0.5f * (lo.z + hi.z), clo[2], cext[2]);
+    const int b0 = bin_of(0.5f * (lo.x + hi.x), clo[0], cinv[0]);
+    const int b1 = bin_of(0.5f * (lo.y + hi.y), clo[1], cinv[1]);
+    const int b2 = bin_of(0.5f * (lo.z + hi.z), clo[2], cinv[2]);
     const int n = (int)lo.w;
     const int ilo[3] = {f2o(lo.x), f2o(lo.y), f2o(lo.z)}, ihi[3] = {f2o(hi.x), f2o(hi.y), f2o(hi.z)};
     atomicAdd(&bin_count[0][b0], n);
@@ -1101,12 +1131,12 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
   // right side (1) or left (0) of position k; by position: the halves in order
   bool by_position = ax < 0;
   const float alo = ax == 0 ? clo[0] : (ax == 1 ? clo[1] : clo[2]);
-  const float aext = ax == 0 ? cext[0] : (ax == 1 ? cext[1] : cext[2]);
+  const float ainv = ax == 0 ? cinv[0] : (ax == 1 ? cinv[1] : cinv[2]);
   auto side_of = [&](int k, float4 lo, float4 hi) {
     if (by_position) return k >= m / 2 ? 1 : 0;
     const float cl = ax == 0 ? lo.x : (ax == 1 ? lo.y : lo.z);
     const float ch = ax == 0 ? hi.x : (ax == 1 ? hi.y : hi.z);
-    return bin_of(0.5f * (cl + ch), alo, aext) <= sb ? 0 : 1;
+    return bin_of(0.5f * (cl + ch), alo, ainv) <= sb ? 0 : 1;
   };
   int nleft = 0, before_l = 0, before_r = 0;
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -1187,28 +1217,34 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
     break;
   }
   // stable partition: left side ascending from b, right side from b + nleft.
-  // A cached segment is placed in shared memory first and copied out with
-  // coalesced stores (the chunks' lanes would scatter their stores).
+  // A cached segment is ordered in shared memory first (the cache slot of
+  // every new position) and copied out with coalesced stores (the chunks'
+  // lanes would scatter their stores).
   {
-    int* dst = cached ? c_part : ids_out + b;
     int pl = before_l, pr = nleft + before_r;
     for (int k = k0; k < k1; ++k) {
-      int c, sd;
       if (cached) {
-        c = c_id[k];
-        sd = c_side[k];
+        const int p = c_side[k] ? pr++ : pl++;
+        c_part[p] = k;
       } else {
+        int c;
         float4 lo, hi;
         fetch(k, c, lo, hi);
-        sd = side_of(k, lo, hi);
+        const int p = b + (side_of(k, lo, hi) ? pr++ : pl++);
+        out.id[p] = c;
+        out.lo[p] = lo;
+        out.hi[p] = hi;
       }
-      if (sd) dst[pr++] = c;
-      else dst[pl++] = c;
     }
   }
   __syncthreads();
   if (cached) {
-    for (int k = t; k < m; k += 256) ids_out[b + k] = c_part[k];
+    for (int p = t; p < m; p += 256) {
+      const int k = c_part[p];
+      out.id[b + p] = c_id[k];
+      out.lo[b + p] = c_lo[k];
+      out.hi[b + p] = c_hi[k];
+    }
     __syncthreads();
   }
   for (int sd = 0; sd < 2; ++sd) {
@@ -1223,12 +1259,11 @@ __device__ __forceinline__ int split_large(int level, int b, int e, const int* i
 // stable partition of the cluster ids, then the two children are emitted:
 // a single cluster becomes a direct link, anything larger a new top node
 // (and a segment of the next level).
-// seg_in / ids_in were written by the previous level (possibly by other
-// blocks of the same launch): they are read through L2 (__ldcg).
+// seg_in and the input list were written by the previous level (possibly
+// by other blocks of the same launch): they are read through L2 (__ldcg).
 __device__ __forceinline__ void top_level_body(int level, int top_base, const int* seg_count, const int4* seg_in,
-                                               int4* seg_out, int* seg_count_out, const int* ids_in, int* ids_out,
-                                               const int* __restrict__ clu_link, const float4* __restrict__ clu_lo,
-                                               const float4* __restrict__ clu_hi, int* top_count, float4* nodes,
+                                               int4* seg_out, int* seg_count_out, CluList in, CluList out,
+                                               const int* __restrict__ clu_link, int* top_count, float4* nodes,
                                                BuildInfo* info, int4* small_seg, int* small_count, int cache_cap) {
   int nseg = __ldcg(&seg_count[level]);
   int t = threadIdx.x;
@@ -1239,9 +1274,9 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
     float4 slo[2], shi[2];
     int nleft;
     if (m <= 256) {
-      nleft = split_small(level, b, e, ids_in, ids_out, clu_lo, clu_hi, slo, shi);
+      nleft = split_small(level, b, e, in, out, slo, shi);
     } else {
-      nleft = split_large(level, b, e, ids_in, ids_out, clu_lo, clu_hi, cache_cap, slo, shi);
+      nleft = split_large(level, b, e, in, out, cache_cap, slo, shi);
     }
     if (t < 2) {
       int cb = t == 0 ? b : b + nleft;
@@ -1249,18 +1284,20 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
       float4 lo = t == 0 ? slo[0] : slo[1], hi = t == 0 ? shi[0] : shi[1];
       int link;
       if (ce - cb == 1) {
-        int c = ids_out[cb];
+        const int c = __ldcg(&out.id[cb]);
+        const float h = __ldcg(&out.hi[cb]).w;
         link = clu_link[c];
         // internal nodes on this path: the top levels 0..level, then the cluster's
-        atomicMax(&info->height, level + 1 + __float_as_int(clu_hi[c].w));
+        atomicMax(&info->height, level + 1 + __float_as_int(h));
       } else {
-        int child = atomicAdd(top_count, 1);
+        // the node id and the queue slot, two independent atomics in flight together
+        const bool small = ce - cb <= kTopWarpSeg;
+        const int child = atomicAdd(top_count, 1);
+        const int slot = atomicAdd(small ? small_count : seg_count_out, 1);
         link = top_base + child;
-        if (ce - cb <= kTopWarpSeg) {
-          int slot = atomicAdd(small_count, 1);
+        if (small) {
           small_seg[slot] = make_int4(cb, ce, child, level + 1);
         } else {
-          int slot = atomicAdd(seg_count_out, 1);
           seg_out[slot] = make_int4(cb, ce, node, child);
         }
         atomicMax(&info->height, level + 2);
@@ -1288,17 +1325,16 @@ __device__ __forceinline__ float combine7(int q, float a, float b) {
   return q < 3 ? fminf(a, b) : (q < 6 ? fmaxf(a, b) : a + b);
 }
 
-__device__ void build_small_subtree(int4 item, int top_base, const int* ids, const int* __restrict__ clu_link,
-                                    const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
+__device__ void build_small_subtree(int4 item, int top_base, CluList in, const int* __restrict__ clu_link,
                                     int* top_count, float4* nodes, BuildInfo* info, int* s_idx, int* s_c,
                                     float4* s_lo, float4* s_hi) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int m = item.y - item.x;
   const bool own = lane < m;
-  int c = own ? __ldcg(&ids[item.x + lane]) : 0;
-  float4 lo = own ? clu_lo[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 hi = own ? clu_hi[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+  int c = own ? __ldcg(&in.id[item.x + lane]) : 0;
+  float4 lo = own ? __ldcg(&in.lo[item.x + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 hi = own ? __ldcg(&in.hi[item.x + lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
   // this lane's segment [sb, se) of lanes; lanes without a cluster are finished singletons
   int sb = own ? 0 : lane, se = own ? m : lane + 1;
   int node = item.z, level = item.w;
@@ -1476,10 +1512,9 @@ __device__ void build_small_subtree(int4 item, int top_base, const int* ids, con
 // goes to warp i / gridDim of block i % gridDim, so that the segments
 // spread over all SMs (a warp's rounds are latency bound) before any block
 // takes a second one.
-__device__ __forceinline__ void top_small_body(const int* seg_count, const int4* small_seg, int top_base,
-                                               const int* clu_a, const int* clu_b, const int* __restrict__ clu_link,
-                                               const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
-                                               int* top_count, float4* nodes, BuildInfo* info) {
+__device__ __forceinline__ void top_small_body(const int* seg_count, const int4* small_seg, int top_base, CluList la,
+                                               CluList lb, const int* __restrict__ clu_link, int* top_count,
+                                               float4* nodes, BuildInfo* info) {
   __shared__ int s_idx[8][3 * 32], s_c[8][32];
   __shared__ float4 s_lo[8][32], s_hi[8][32];
   const int w = threadIdx.x >> 5;
@@ -1487,51 +1522,43 @@ __device__ __forceinline__ void top_small_body(const int* seg_count, const int4*
   const int warps = (int)(gridDim.x * (blockDim.x >> 5));
   for (int i = w * (int)gridDim.x + (int)blockIdx.x; i < n_small; i += warps) {
     int4 item = __ldcg(&small_seg[i]);
-    // the cluster ids of a level-L segment are in the buffer its parent's split wrote
-    const int* ids = (item.w & 1) ? clu_b : clu_a;
-    build_small_subtree(item, top_base, ids, clu_link, clu_lo, clu_hi, top_count, nodes, info, s_idx[w], s_c[w],
+    // a level-L segment is in the buffer its parent's split wrote
+    build_small_subtree(item, top_base, (item.w & 1) ? lb : la, clu_link, top_count, nodes, info, s_idx[w], s_c[w],
                         s_lo[w], s_hi[w]);
   }
 }
 
 __global__ void __launch_bounds__(256) k_top_small(const int* seg_count, const int4* small_seg, int top_base,
-                                                   const int* clu_a, const int* clu_b,
-                                                   const int* __restrict__ clu_link,
-                                                   const float4* __restrict__ clu_lo,
-                                                   const float4* __restrict__ clu_hi, int* top_count, float4* nodes,
-                                                   BuildInfo* info) {
-  top_small_body(seg_count, small_seg, top_base, clu_a, clu_b, clu_link, clu_lo, clu_hi, top_count, nodes, info);
+                                                   CluList la, CluList lb, const int* __restrict__ clu_link,
+                                                   int* top_count, float4* nodes, BuildInfo* info) {
+  top_small_body(seg_count, small_seg, top_base, la, lb, clu_link, top_count, nodes, info);
 }
 
 __global__ void __launch_bounds__(256) k_top_level(int level, int top_base, const int* seg_count, const int4* seg_in,
-                                                   int4* seg_out, int* seg_count_out, const int* ids_in, int* ids_out,
-                                                   const int* __restrict__ clu_link,
-                                                   const float4* __restrict__ clu_lo,
-                                                   const float4* __restrict__ clu_hi, int* top_count, float4* nodes,
+                                                   int4* seg_out, int* seg_count_out, CluList in, CluList out,
+                                                   const int* __restrict__ clu_link, int* top_count, float4* nodes,
                                                    BuildInfo* info, int4* small_seg, int* small_count,
                                                    int cache_cap) {
-  top_level_body(level, top_base, seg_count, seg_in, seg_out, seg_count_out, ids_in, ids_out, clu_link, clu_lo, clu_hi,
-                 top_count, nodes, info, small_seg, small_count, cache_cap);
+  top_level_body(level, top_base, seg_count, seg_in, seg_out, seg_count_out, in, out, clu_link, top_count, nodes, info,
+                 small_seg, small_count, cache_cap);
 }
 
 // Every level in one cooperative launch: the blocks meet at a grid-wide
 // barrier between levels and stop at the first level without segments.
-__global__ void __launch_bounds__(256) k_top_all(int top_base, int* seg_count, int4* seg_a, int4* seg_b, int* clu_a,
-                                                 int* clu_b, const int* __restrict__ clu_link,
-                                                 const float4* __restrict__ clu_lo, const float4* __restrict__ clu_hi,
-                                                 int* top_count, float4* nodes, BuildInfo* info, int4* small_seg,
-                                                 int cache_cap) {
+__global__ void __launch_bounds__(256) k_top_all(int top_base, int* seg_count, int4* seg_a, int4* seg_b, CluList la,
+                                                 CluList lb, const int* __restrict__ clu_link, int* top_count,
+                                                 float4* nodes, BuildInfo* info, int4* small_seg, int cache_cap) {
   cg::grid_group grid = cg::this_grid();
   for (int level = 0; level < kTopMaxLevels; ++level) {
     if (__ldcg(&seg_count[level]) == 0) break;   // the same value in every block after the barrier
     bool odd = level & 1;
     top_level_body(level, top_base, seg_count, odd ? seg_b : seg_a, odd ? seg_a : seg_b, seg_count + level + 1,
-                   odd ? clu_b : clu_a, odd ? clu_a : clu_b, clu_link, clu_lo, clu_hi, top_count, nodes, info,
-                   small_seg, seg_count + kTopMaxLevels + 2, cache_cap);
+                   odd ? lb : la, odd ? la : lb, clu_link, top_count, nodes, info, small_seg,
+                   seg_count + kTopMaxLevels + 2, cache_cap);
     grid.sync();
   }
   // the small segments, one warp each, with no more barriers
-  top_small_body(seg_count, small_seg, top_base, clu_a, clu_b, clu_link, clu_lo, clu_hi, top_count, nodes, info);
+  top_small_body(seg_count, small_seg, top_base, la, lb, clu_link, top_count, nodes, info);
 }
 
 // ---------------------------------------------------------------------------
@@ -1765,13 +1792,15 @@ static rt_status carve(rt_scene* s, int n, BuildScratch& b) {
   sz[k++] = N * 4;   // clu_link
   sz[k++] = N * 16;  // clu_lo
   sz[k++] = N * 16;  // clu_hi
+  sz[k++] = N * 16;  // clu_lo_b
+  sz[k++] = N * 16;  // clu_hi_b
   sz[k++] = N * 16;  // seg_a
   sz[k++] = N * 16;  // seg_b
   sz[k++] = (kTopMaxLevels + 3) * 4;   // seg_count: levels, n_clusters, small segments
   sz[k++] = 16;      // top_count
   sz[k++] = N * 16;  // small_seg
   sz[k++] = sizeof(BuildInfo);
-  static_assert(sizeof(sz) / sizeof(sz[0]) >= 34, "scratch region table too small");
+  static_assert(sizeof(sz) / sizeof(sz[0]) >= 36, "scratch region table too small");
   size_t total = 0;
   for (int i = 0; i < k; ++i) total += align_up(sz[i]);
   rt_status st = ensure(s->build_tmp, total);
@@ -1806,6 +1835,8 @@ static rt_status carve(rt_scene* s, int n, BuildScratch& b) {
   b.clu_link = (int*)ptr[q++];
   b.clu_lo = (float4*)ptr[q++];
   b.clu_hi = (float4*)ptr[q++];
+  b.clu_lo_b = (float4*)ptr[q++];
+  b.clu_hi_b = (float4*)ptr[q++];
   b.seg_a = (int4*)ptr[q++];
   b.seg_b = (int4*)ptr[q++];
   b.seg_count = (int*)ptr[q++];
@@ -1917,10 +1948,11 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
       coop_blocks = coop ? std::min(per_sm, 2) * s->sm_count : 0;
     }
     bool launched = false;
+    CluList la{b.clu_a, b.clu_lo, b.clu_hi}, lb{b.clu_b, b.clu_lo_b, b.clu_hi_b};
     if (coop_blocks > 0) {
       int tb_ = top_base;
-      void* args[] = {&tb_, &b.seg_count, &b.seg_a, &b.seg_b, &b.clu_a, &b.clu_b, &b.clu_link,
-                      &b.clu_lo, &b.clu_hi, &b.top_count, &nodes, &b.info, &b.small_seg, &cache_cap};
+      void* args[] = {&tb_, &b.seg_count, &b.seg_a, &b.seg_b, &la, &lb, &b.clu_link,
+                      &b.top_count, &nodes, &b.info, &b.small_seg, &cache_cap};
       launched = cudaLaunchCooperativeKernel((void*)k_top_all, coop_blocks, 256, args, dyn, st) == cudaSuccess;
       if (!launched) cudaGetLastError();
       L += launched ? 1 - kTopMaxLevels : 0;
@@ -1929,13 +1961,12 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
       bool odd = level & 1;
       k_top_level<<<top_grid, 256, dyn, st>>>(level, top_base, b.seg_count, odd ? b.seg_b : b.seg_a,
                                               odd ? b.seg_a : b.seg_b, b.seg_count + level + 1,
-                                              odd ? b.clu_b : b.clu_a, odd ? b.clu_a : b.clu_b, b.clu_link, b.clu_lo,
-                                              b.clu_hi, b.top_count, nodes, b.info, b.small_seg,
-                                              b.seg_count + kTopMaxLevels + 2, cache_cap);
+                                              odd ? lb : la, odd ? la : lb, b.clu_link, b.top_count, nodes, b.info,
+                                              b.small_seg, b.seg_count + kTopMaxLevels + 2, cache_cap);
     }
     if (!launched) {
-      k_top_small<<<top_grid, 256, 0, st>>>(b.seg_count, b.small_seg, top_base, b.clu_a, b.clu_b, b.clu_link,
-                                            b.clu_lo, b.clu_hi, b.top_count, nodes, b.info);
+      k_top_small<<<top_grid, 256, 0, st>>>(b.seg_count, b.small_seg, top_base, la, lb, b.clu_link, b.top_count,
+                                            nodes, b.info);
       L += 1;
     }
     L += 4 + kTopMaxLevels;   // k_collapse4 records the top's counts and root
