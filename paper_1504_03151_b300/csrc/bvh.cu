@@ -1590,20 +1590,21 @@ __device__ __forceinline__ float half_area(const float* lo, const float* hi) {
   return dx * dy + dy * dz + dz * dx;
 }
 
-// Slots past the LBVH's n_lbvh internal nodes are top nodes; only the first
-// *top_count of them exist (none without a top rebuild: top_count NULL).
-__global__ void __launch_bounds__(256) k_collapse4(const float4* __restrict__ bin, int n_bin, int n_lbvh,
-                                                   const int* __restrict__ top_count,
+// Slots x0 .. x1 - 1.  Slots past the LBVH's n_lbvh internal nodes are top
+// nodes; only the first *top_count of them exist (none without a top
+// rebuild: top_count NULL, which a launch over LBVH slots alone passes too).
+__global__ void __launch_bounds__(256) k_collapse4(const float4* __restrict__ bin, int x0, int x1, int n_bin,
+                                                   int n_lbvh, const int* __restrict__ top_count,
                                                    const int* __restrict__ n_clusters, BuildInfo* info, int top_base,
                                                    float4* __restrict__ out) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x == 0 && top_count) {
+  const int x = x0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (x == x0 && top_count) {
     // the rebuilt top's counts and root, for rt_bvh_get_info
     info->n_top = *top_count;
     info->n_clusters = *n_clusters;
     info->root = top_base;
   }
-  if (x >= n_bin) return;
+  if (x >= x1) return;
   if (x >= n_lbvh && (top_count == nullptr || x - n_lbvh >= __ldg(top_count))) return;   // an unused slot
   // Slots are indexed only by constants once the loops unroll, so they stay
   // in registers; the slot chosen at run time is written through selects.
@@ -1854,20 +1855,32 @@ static int cluster_max_for(int n) {
 }
 
 // The 4-wide traversal tree: one 4-wide node per binary node slot, at the
-// same index (the root is the binary root).
-static rt_status collapse4(rt_scene* s, const BuildScratch& b, const float4* nodes, int n_bin, bool top,
-                           int top_base, cudaStream_t st) {
+// same index (the root is the binary root), for slots x0 .. x1 - 1.  The
+// top's counts are recorded by the launch that takes slot n - 1, the first
+// top node, when there is a top (top_base >= 0).
+static rt_status collapse4(rt_scene* s, const BuildScratch& b, const float4* nodes, int n_bin, int top_base,
+                           int x0, int x1, cudaStream_t st) {
   rt_status rs = ensure(s->nodes4, (size_t)n_bin * 128);
   if (rs) return rs;
   s->n_nodes4 = n_bin;
   if (s->n_prims == 1) {
     k_wide_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, (float4*)s->nodes4.p);
-  } else {
-    k_collapse4<<<(n_bin + 255) / 256, 256, 0, st>>>(nodes, n_bin, (int)s->n_prims - 1, top ? b.top_count : nullptr,
-                                                     b.seg_count + kTopMaxLevels + 1, b.info, top_base,
-                                                     (float4*)s->nodes4.p);
+  } else if (x1 > x0) {
+    const int n_lbvh = (int)s->n_prims - 1;
+    const bool counts = top_base >= 0 && x0 <= n_lbvh && n_lbvh < x1;
+    k_collapse4<<<(x1 - x0 + 255) / 256, 256, 0, st>>>(nodes, x0, x1, n_bin, n_lbvh, counts ? b.top_count : nullptr,
+                                                       b.seg_count + kTopMaxLevels + 1, b.info, top_base,
+                                                       (float4*)s->nodes4.p);
   }
   return cuda_error(cudaGetLastError(), "rt_bvh_build: 4-wide tree");
+}
+
+static rt_status ensure_build_side(rt_scene* s) {
+  if (s->build_side) return RT_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&s->build_side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_build_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_build_join, cudaEventDisableTiming);
+  return cuda_error(e, "rt_bvh_build: side stream");
 }
 
 rt_status bvh_build(rt_scene* s, cudaStream_t st) {
@@ -1896,7 +1909,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     k_layout_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, nodes, b.info);
     k_gather_prims<<<1, 32, 0, st>>>(b.vals0, 1, (const float4*)s->prims_id.p, (float4*)s->prims_leaf.p);
     s->root = 0;
-    if ((rs = collapse4(s, b, nodes, (int)slots, false, 0, st))) return rs;
+    if ((rs = collapse4(s, b, nodes, (int)slots, -1, 0, (int)slots, st))) return rs;
     s->last_build_launches = L + 4;
     s->built = true;
     return cuda_error(cudaGetLastError(), "rt_bvh_build");
@@ -1917,13 +1930,28 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
   // the LBVH above the clusters only feeds the plain LBVH's cost, which
   // rt_bvh_get_info computes when asked (upper_refit)
   s->lbvh_cut = top ? cmax : 0;
-  k_layout<<<grid, tb, 0, st>>>(n, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo, b.aabb_hi,
+  // With a top rebuild, the binary layout of the LBVH nodes, the primitives
+  // in leaf order and the 4-wide nodes of the LBVH slots do not depend on
+  // it: they run on the build's second stream beside it, on the SMs that
+  // its few active blocks leave idle.
+  const bool fork = top && ensure_build_side(s) == RT_OK;
+  cudaStream_t sl = fork ? s->build_side : st;
+  if (fork) {
+    cudaEventRecord(s->ev_build_fork, st);
+    cudaStreamWaitEvent(sl, s->ev_build_fork, 0);
+  }
+  k_layout<<<grid, tb, 0, sl>>>(n, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo, b.aabb_hi,
                                 nodes);
-  k_gather_prims<<<(3 * n + 255) / 256, 256, 0, st>>>(b.vals0, n, (const float4*)s->prims_id.p,
+  k_gather_prims<<<(3 * n + 255) / 256, 256, 0, sl>>>(b.vals0, n, (const float4*)s->prims_id.p,
                                                       (float4*)s->prims_leaf.p);
   if (!top) k_info_lbvh<<<1, 1, 0, st>>>(b.node_lo, b.node_hi, b.cost_lbvh, b.info, 0);
   L += top ? 7 : 8;
   s->root = 0;
+  if (fork) {
+    if ((rs = collapse4(s, b, nodes, (int)slots, n - 1, 0, n - 1, sl))) return rs;
+    cudaEventRecord(s->ev_build_join, sl);
+    L += 1;
+  }
   if (top) {
     // top levels: binned SAH over the Morton clusters
     int top_base = n - 1;
@@ -1972,7 +2000,13 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     L += 4 + kTopMaxLevels;   // k_collapse4 records the top's counts and root
     s->root = top_base;
   }
-  if ((rs = collapse4(s, b, nodes, (int)slots, top, top ? s->root : 0, st))) return rs;
+  if (fork) {
+    cudaStreamWaitEvent(st, s->ev_build_join, 0);
+    rs = collapse4(s, b, nodes, (int)slots, s->root, n - 1, (int)slots, st);
+  } else {
+    rs = collapse4(s, b, nodes, (int)slots, top ? s->root : -1, 0, (int)slots, st);
+  }
+  if (rs) return rs;
   L += 1;
   s->last_build_launches = L;
   s->built = true;

@@ -1214,6 +1214,11 @@ rt_status rt_scene_destroy(rt_scene* s) {
   release(s->rayq[1]);
   release(s->shadowq[0]);
   release(s->shadowq[1]);
+  if (s->build_side) {
+    cudaStreamDestroy(s->build_side);
+    cudaEventDestroy(s->ev_build_fork);
+    cudaEventDestroy(s->ev_build_join);
+  }
   if (s->side) {
     cudaStreamDestroy(s->side);
     for (int d = 0; d <= RT_MAX_DEPTH; ++d) {

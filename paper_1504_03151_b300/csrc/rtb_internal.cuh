@@ -136,6 +136,10 @@ struct rt_scene {
   float last_build_ms = 0.f;
   int last_build_launches = 0;
   int lbvh_cut = 0;              // > 0: the LBVH nodes over this many primitives still await their refit
+  // the build's second stream: the parts that do not depend on the top
+  // rebuild run on it beside that rebuild
+  cudaStream_t build_side = nullptr;
+  cudaEvent_t ev_build_fork = nullptr, ev_build_join = nullptr;
   // render
   rtb::Buf rayq[2], shadowq[2], counters, fb_host_stage;
   rtb::Buf fb_fixed;             // RT_FLAG_DETERMINISTIC: the frame's 64-bit fixed-point sums
