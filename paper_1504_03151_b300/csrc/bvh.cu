@@ -187,11 +187,17 @@ __device__ __forceinline__ unsigned quantize10(float c, float lo, float hi) {
   return (unsigned)min(max(q, 0), 1023);
 }
 
+// Also clears the arrays the hierarchy and the refit fill (their arrival
+// flags, and -1 parents), which saves three memsets on the build's path.
 __global__ void k_morton(const float4* __restrict__ lo, const float4* __restrict__ hi, int n,
                          const int* __restrict__ cb, int drop, unsigned* __restrict__ keys,
-                         unsigned* __restrict__ vals) {
+                         unsigned* __restrict__ vals, int* __restrict__ flags, int* __restrict__ parent,
+                         int* __restrict__ leaf_parent) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  flags[i] = 0;
+  parent[i] = -1;
+  leaf_parent[i] = -1;
   float4 a = lo[i], b = hi[i];
   float cx = 0.5f * (a.x + b.x), cy = 0.5f * (a.y + b.y), cz = 0.5f * (a.z + b.z);
   unsigned qx = quantize10(cx, o2f(cb[0]), o2f(cb[3]));
@@ -730,18 +736,6 @@ __global__ void k_find_clusters(int n, int cluster_max, const int* __restrict__ 
   }
 }
 
-__global__ void k_top_init(int* seg_count, int4* seg0, const int* __restrict__ n_clusters, int* top_count,
-                           BuildInfo* info) {
-  // one segment covering every cluster; it becomes top node 0
-  if (threadIdx.x == 0) {
-    seg0[0] = make_int4(0, *n_clusters, -1, 0);
-    seg_count[0] = 1;
-    for (int l = 1; l <= kTopMaxLevels; ++l) seg_count[l] = 0;
-    top_count[0] = 1;
-    info->height = 1;
-  }
-}
-
 __global__ void k_iota(int* __restrict__ a, const int* __restrict__ n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < *n) a[i] = i;
@@ -1265,10 +1259,15 @@ __device__ __forceinline__ void top_level_body(int level, int top_base, const in
                                                int4* seg_out, int* seg_count_out, CluList in, CluList out,
                                                const int* __restrict__ clu_link, int* top_count, float4* nodes,
                                                BuildInfo* info, int4* small_seg, int* small_count, int cache_cap) {
-  int nseg = __ldcg(&seg_count[level]);
+  // level 0 is one segment over every cluster, which becomes top node 0
+  const int nseg = level == 0 ? 1 : __ldcg(&seg_count[level]);
   int t = threadIdx.x;
+  if (level == 0 && blockIdx.x == 0 && t == 0) {
+    top_count[0] = 1;
+    info->height = 1;
+  }
   for (int sidx = blockIdx.x; sidx < nseg; sidx += gridDim.x) {
-    int4 sg = __ldcg(&seg_in[sidx]);
+    const int4 sg = level == 0 ? make_int4(0, __ldcg(&seg_count[kTopMaxLevels + 1]), -1, 0) : __ldcg(&seg_in[sidx]);
     int b = sg.x, e = sg.y, node = sg.w;
     int m = e - b;
     float4 slo[2], shi[2];
@@ -1550,7 +1549,7 @@ __global__ void __launch_bounds__(256) k_top_all(int top_base, int* seg_count, i
                                                  float4* nodes, BuildInfo* info, int4* small_seg, int cache_cap) {
   cg::grid_group grid = cg::this_grid();
   for (int level = 0; level < kTopMaxLevels; ++level) {
-    if (__ldcg(&seg_count[level]) == 0) break;   // the same value in every block after the barrier
+    if (level > 0 && __ldcg(&seg_count[level]) == 0) break;   // the same value in every block after the barrier
     bool odd = level & 1;
     top_level_body(level, top_base, seg_count, odd ? seg_b : seg_a, odd ? seg_a : seg_b, seg_count + level + 1,
                    odd ? lb : la, odd ? la : lb, clu_link, top_count, nodes, info, small_seg,
@@ -1917,11 +1916,8 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
   const int key_bits = morton_key_bits(n);
   const bool odd = sort_passes(key_bits) & 1;
   k_morton<<<grid, tb, 0, st>>>(b.aabb_lo, b.aabb_hi, n, b.cent_bounds, 30 - key_bits, odd ? b.keys1 : b.keys0,
-                                odd ? b.vals1 : b.vals0);
+                                odd ? b.vals1 : b.vals0, b.flags, b.parent, b.leaf_parent);
   L += 1 + radix_sort_pairs(s, b, n, key_bits, st);
-  cudaMemsetAsync(b.flags, 0, (size_t)n * 4, st);
-  cudaMemsetAsync(b.parent, 0xff, (size_t)n * 4, st);
-  cudaMemsetAsync(b.leaf_parent, 0xff, (size_t)n * 4, st);
   k_hierarchy<<<grid, tb, 0, st>>>(b.keys0, n, b.lch, b.rch, b.parent, b.leaf_parent, b.range);
   int cmax = cluster_max_for(n);
   const bool top = n > 2 * cmax;   // the top levels are rebuilt over clusters of <= cmax primitives
@@ -1945,7 +1941,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
   k_gather_prims<<<(3 * n + 255) / 256, 256, 0, sl>>>(b.vals0, n, (const float4*)s->prims_id.p,
                                                       (float4*)s->prims_leaf.p);
   if (!top) k_info_lbvh<<<1, 1, 0, st>>>(b.node_lo, b.node_hi, b.cost_lbvh, b.info, 0);
-  L += top ? 7 : 8;
+  L += top ? 4 : 5;   // k_hierarchy, k_refit, k_layout, k_gather_prims (and k_info_lbvh)
   s->root = 0;
   if (fork) {
     if ((rs = collapse4(s, b, nodes, (int)slots, n - 1, 0, n - 1, sl))) return rs;
@@ -1956,12 +1952,11 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     // top levels: binned SAH over the Morton clusters
     int top_base = n - 1;
     int* n_clusters_dev = b.seg_count + kTopMaxLevels + 1;
+    // every top node the rebuild allocates gets both children written; the
+    // slots past them are never read (k_collapse4 stops at *top_count)
     cudaMemsetAsync(b.seg_count, 0, (kTopMaxLevels + 3) * 4, st);
-    // a zeroed top node is harmless to traverse (links to node 0, empty boxes)
-    cudaMemsetAsync(nodes + 4 * (size_t)top_base, 0, (size_t)(slots - top_base) * 64, st);
     k_find_clusters<<<grid, tb, 0, st>>>(n, cmax, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo,
                                          b.aabb_hi, n_clusters_dev, b.clu_a, b.clu_link, b.clu_lo, b.clu_hi);
-    k_top_init<<<1, 32, 0, st>>>(b.seg_count, b.seg_a, n_clusters_dev, b.top_count, b.info);
     int top_grid = std::max(1, 2 * s->sm_count);
     // dynamic shared memory: the cluster cache of one segment
     int cache_cap = kTopCache;
@@ -1997,7 +1992,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
                                             nodes, b.info);
       L += 1;
     }
-    L += 4 + kTopMaxLevels;   // k_collapse4 records the top's counts and root
+    L += 2 + kTopMaxLevels;   // k_collapse4 records the top's counts and root
     s->root = top_base;
   }
   if (fork) {
