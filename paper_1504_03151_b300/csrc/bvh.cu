@@ -104,11 +104,14 @@ __device__ __forceinline__ float pad_hi(float x) { return x + fabsf(x) * 2.4e-7f
 // ---------------------------------------------------------------------------
 // 1. primitive boxes and the centroid bounds
 // ---------------------------------------------------------------------------
-__global__ void k_init_bounds(int* cb) {
-  int t = threadIdx.x;
+// The centroid bounds' reset value (an empty box).  The kernel that follows
+// the last reader of the bounds in a build (k_hierarchy, or k_layout_single)
+// resets them for the next build; k_init_bounds runs only on fresh scratch.
+__device__ __forceinline__ void reset_bounds(int* cb, int t) {
   if (t < 3) cb[t] = f2o(INFINITY);
   else if (t < 6) cb[t] = f2o(-INFINITY);
 }
+__global__ void k_init_bounds(int* cb) { reset_bounds(cb, threadIdx.x); }
 
 __global__ void k_prim_bounds(const float4* __restrict__ prims, int n, float4* __restrict__ lo_out,
                               float4* __restrict__ hi_out, int* __restrict__ cb) {
@@ -525,9 +528,16 @@ __device__ __forceinline__ int prefix_len(const unsigned* __restrict__ keys, int
   return 32 + __clz((unsigned)i ^ (unsigned)j);
 }
 
+// Block 0 also resets the centroid bounds for the next build (k_morton, the
+// last reader, is done) and clears the top rebuild's counters (seg_n ints).
 __global__ void k_hierarchy(const unsigned* __restrict__ keys, int n, int* __restrict__ lch, int* __restrict__ rch,
-                            int* __restrict__ parent, int* __restrict__ leaf_parent, int2* __restrict__ range) {
+                            int* __restrict__ parent, int* __restrict__ leaf_parent, int2* __restrict__ range,
+                            int* __restrict__ cb, int* __restrict__ seg_count, int seg_n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0) {
+    reset_bounds(cb, threadIdx.x);
+    if (threadIdx.x < seg_n) seg_count[threadIdx.x] = 0;
+  }
   if (i >= n - 1) return;
   int dl = prefix_len(keys, n, i, i - 1), dr = prefix_len(keys, n, i, i + 1);
   int d = dr > dl ? 1 : -1;
@@ -1717,7 +1727,8 @@ __global__ void k_wide_single(const float4* __restrict__ aabb_lo, const float4* 
 
 // one primitive: a root whose second child box is empty
 __global__ void k_layout_single(const float4* __restrict__ aabb_lo, const float4* __restrict__ aabb_hi,
-                                float4* __restrict__ out, BuildInfo* info) {
+                                float4* __restrict__ out, BuildInfo* info, int* __restrict__ cb) {
+  for (int t = 0; t < 6; ++t) reset_bounds(cb, t);
   float4 lo = aabb_lo[0], hi = aabb_hi[0];
   out[0] = make_float4(lo.x, hi.x, lo.y, hi.y);
   out[1] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
@@ -1900,12 +1911,16 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
   float4* nodes = (float4*)s->nodes.p;
   int tb = 256, grid = (n + tb - 1) / tb;
   int L = 0;   // launches (kernels + memsets) of this build
-  k_init_bounds<<<1, 32, 0, st>>>(b.cent_bounds);
+  if (s->bounds_gen != s->build_tmp.gen) {
+    k_init_bounds<<<1, 32, 0, st>>>(b.cent_bounds);   // fresh scratch
+    s->bounds_gen = s->build_tmp.gen;
+    L += 1;
+  }
   k_prim_bounds<<<grid, tb, 0, st>>>((const float4*)s->prims_id.p, n, b.aabb_lo, b.aabb_hi, b.cent_bounds);
-  L += 2;
+  L += 1;
   if (n == 1) {
     cudaMemsetAsync(b.vals0, 0, 4, st);
-    k_layout_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, nodes, b.info);
+    k_layout_single<<<1, 1, 0, st>>>(b.aabb_lo, b.aabb_hi, nodes, b.info, b.cent_bounds);
     k_gather_prims<<<1, 32, 0, st>>>(b.vals0, 1, (const float4*)s->prims_id.p, (float4*)s->prims_leaf.p);
     s->root = 0;
     if ((rs = collapse4(s, b, nodes, (int)slots, -1, 0, (int)slots, st))) return rs;
@@ -1918,7 +1933,9 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
   k_morton<<<grid, tb, 0, st>>>(b.aabb_lo, b.aabb_hi, n, b.cent_bounds, 30 - key_bits, odd ? b.keys1 : b.keys0,
                                 odd ? b.vals1 : b.vals0, b.flags, b.parent, b.leaf_parent);
   L += 1 + radix_sort_pairs(s, b, n, key_bits, st);
-  k_hierarchy<<<grid, tb, 0, st>>>(b.keys0, n, b.lch, b.rch, b.parent, b.leaf_parent, b.range);
+  static_assert(kTopMaxLevels + 3 <= 256, "k_hierarchy's first block clears the top counters");
+  k_hierarchy<<<grid, tb, 0, st>>>(b.keys0, n, b.lch, b.rch, b.parent, b.leaf_parent, b.range, b.cent_bounds,
+                                   b.seg_count, kTopMaxLevels + 3);
   int cmax = cluster_max_for(n);
   const bool top = n > 2 * cmax;   // the top levels are rebuilt over clusters of <= cmax primitives
   k_refit<<<grid, tb, 0, st>>>(n, top ? cmax : n, b.vals0, b.aabb_lo, b.aabb_hi, b.lch, b.rch, b.parent,
@@ -1952,9 +1969,9 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     // top levels: binned SAH over the Morton clusters
     int top_base = n - 1;
     int* n_clusters_dev = b.seg_count + kTopMaxLevels + 1;
-    // every top node the rebuild allocates gets both children written; the
-    // slots past them are never read (k_collapse4 stops at *top_count)
-    cudaMemsetAsync(b.seg_count, 0, (kTopMaxLevels + 3) * 4, st);
+    // (k_hierarchy cleared the counters.)  Every top node the rebuild
+    // allocates gets both children written; the slots past them are never
+    // read (k_collapse4 stops at *top_count).
     k_find_clusters<<<grid, tb, 0, st>>>(n, cmax, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo,
                                          b.aabb_hi, n_clusters_dev, b.clu_a, b.clu_link, b.clu_lo, b.clu_hi);
     int top_grid = std::max(1, 2 * s->sm_count);
@@ -1992,7 +2009,7 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
                                             nodes, b.info);
       L += 1;
     }
-    L += 2 + kTopMaxLevels;   // k_collapse4 records the top's counts and root
+    L += 1 + kTopMaxLevels;   // k_collapse4 records the top's counts and root
     s->root = top_base;
   }
   if (fork) {

@@ -103,6 +103,7 @@ struct DevScene {
 struct Buf {
   void* p = nullptr;
   size_t bytes = 0;
+  unsigned gen = 0;   // bumped by every allocation (the address alone may repeat)
 };
 
 struct GraphCache;
@@ -136,6 +137,7 @@ struct rt_scene {
   float last_build_ms = 0.f;
   int last_build_launches = 0;
   int lbvh_cut = 0;              // > 0: the LBVH nodes over this many primitives still await their refit
+  unsigned bounds_gen = 0;       // build_tmp.gen whose centroid bounds hold their reset value
   // the build's second stream: the parts that do not depend on the top
   // rebuild run on it beside that rebuild
   cudaStream_t build_side = nullptr;

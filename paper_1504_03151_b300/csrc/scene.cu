@@ -36,6 +36,7 @@ rt_status ensure(Buf& b, size_t bytes) {
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e != cudaSuccess) return cuda_error(e, "cudaMalloc");
   b.bytes = bytes;
+  ++b.gen;
   return RT_OK;
 }
 
