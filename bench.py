@@ -661,7 +661,9 @@ def main():
     cls_ms, ops, traffic, traffic_src = C["kernel_ms"], C["alg_ops"], C["dram_bytes"], C["dram_source"]
     achieved = ops / (cls_ms * 1e-3) / 1e12
     l2_bound = C["l2_frac"] > C["alu_frac"]
-    launches_per_step = info["build_launches"] + 1 + 2 + st["launches"] + 2
+    # a step: the geometry copy and k_pack (rt_scene_update), the build's
+    # kernels and memsets, the frame's counter clear and its kernels
+    launches_per_step = 2 + info["build_launches"] + 1 + st["launches"]
 
     # radiance cache: online training frames, then timed training frames;
     # its Mrays-equivalent = rays the full-depth frame traces / cached step time

@@ -1886,9 +1886,10 @@ static rt_status collapse4(rt_scene* s, const BuildScratch& b, const float4* nod
 }
 
 static rt_status ensure_build_side(rt_scene* s) {
-  if (s->build_side) return RT_OK;
-  cudaError_t e = cudaStreamCreateWithFlags(&s->build_side, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_build_fork, cudaEventDisableTiming);
+  if (s->ev_build_join) return RT_OK;
+  rt_status rs = ensure_side_stream(s);
+  if (rs) return rs;
+  cudaError_t e = cudaEventCreateWithFlags(&s->ev_build_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_build_join, cudaEventDisableTiming);
   return cuda_error(e, "rt_bvh_build: side stream");
 }
@@ -1945,26 +1946,21 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
   s->lbvh_cut = top ? cmax : 0;
   // With a top rebuild, the binary layout of the LBVH nodes, the primitives
   // in leaf order and the 4-wide nodes of the LBVH slots do not depend on
-  // it: they run on the build's second stream beside it, on the SMs that
-  // its few active blocks leave idle.
+  // it: they run on the scene's side stream beside it (forked below, once
+  // the clusters are found), on the SMs that its few active blocks leave
+  // idle.  (Forked right after k_refit, to overlap the cluster search too,
+  // the step was 4 us slower.)
   const bool fork = top && ensure_build_side(s) == RT_OK;
-  cudaStream_t sl = fork ? s->build_side : st;
-  if (fork) {
-    cudaEventRecord(s->ev_build_fork, st);
-    cudaStreamWaitEvent(sl, s->ev_build_fork, 0);
-  }
-  k_layout<<<grid, tb, 0, sl>>>(n, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo, b.aabb_hi,
-                                nodes);
-  k_gather_prims<<<(3 * n + 255) / 256, 256, 0, sl>>>(b.vals0, n, (const float4*)s->prims_id.p,
-                                                      (float4*)s->prims_leaf.p);
+  auto layout = [&](cudaStream_t sl) {
+    k_layout<<<grid, tb, 0, sl>>>(n, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo, b.aabb_hi,
+                                  nodes);
+    k_gather_prims<<<(3 * n + 255) / 256, 256, 0, sl>>>(b.vals0, n, (const float4*)s->prims_id.p,
+                                                        (float4*)s->prims_leaf.p);
+  };
+  if (!fork) layout(st);
   if (!top) k_info_lbvh<<<1, 1, 0, st>>>(b.node_lo, b.node_hi, b.cost_lbvh, b.info, 0);
   L += top ? 4 : 5;   // k_hierarchy, k_refit, k_layout, k_gather_prims (and k_info_lbvh)
   s->root = 0;
-  if (fork) {
-    if ((rs = collapse4(s, b, nodes, (int)slots, n - 1, 0, n - 1, sl))) return rs;
-    cudaEventRecord(s->ev_build_join, sl);
-    L += 1;
-  }
   if (top) {
     // top levels: binned SAH over the Morton clusters
     int top_base = n - 1;
@@ -1974,6 +1970,14 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     // read (k_collapse4 stops at *top_count).
     k_find_clusters<<<grid, tb, 0, st>>>(n, cmax, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo,
                                          b.aabb_hi, n_clusters_dev, b.clu_a, b.clu_link, b.clu_lo, b.clu_hi);
+    if (fork) {
+      cudaEventRecord(s->ev_build_fork, st);
+      cudaStreamWaitEvent(s->side, s->ev_build_fork, 0);
+      layout(s->side);
+      if ((rs = collapse4(s, b, nodes, (int)slots, n - 1, 0, n - 1, s->side))) return rs;
+      cudaEventRecord(s->ev_build_join, s->side);
+      L += 1;
+    }
     int top_grid = std::max(1, 2 * s->sm_count);
     // dynamic shared memory: the cluster cache of one segment
     int cache_cap = kTopCache;

@@ -66,6 +66,7 @@ struct FrameParams {
   unsigned long long* fb_fixed;   // RT_FLAG_DETERMINISTIC: 3 per pixel, 64-bit fixed point (else NULL)
   unsigned* px_rays;              // counting frames: per pixel and depth, closest-hit and shadow rays (else NULL)
   int px_stride;                  // 2 (max_depth + 1)
+  int fb_store;                   // 1: the depth-0 kernel stores each pixel's first value (the image is not cleared)
 };
 
 // Per-pixel ray counts (counting instances only): cls 0 = a closest-hit ray
@@ -101,6 +102,15 @@ __device__ __forceinline__ void add_fb(const FrameParams& fp, int pixel, f3 c) {
   atomicAdd(p, c.x);
   atomicAdd(p + 1, c.y);
   atomicAdd(p + 2, c.z);
+}
+
+// The first value of a pixel, stored by the depth-0 kernel (every pixel has
+// exactly one camera ray, traced before any other kernel of the frame adds).
+__device__ __forceinline__ void store_fb(const FrameParams& fp, int pixel, f3 c) {
+  float* p = fp.fb + 3 * (size_t)pixel;
+  p[0] = c.x;
+  p[1] = c.y;
+  p[2] = c.z;
 }
 
 // The deterministic frame's image: fixed-point sums -> float32.
@@ -210,7 +220,8 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
     }
     // shading
     bool is_hit = active && hit >= 0;
-    if (active && hit < 0) add_fb(fp, pixel, w * mk3(fp.bg_r, fp.bg_g, fp.bg_b));
+    const bool first_store = kPrimary && fp.fb_store;
+    if (active && hit < 0 && !first_store) add_fb(fp, pixel, w * mk3(fp.bg_r, fp.bg_g, fp.bg_b));
     unsigned hm = __ballot_sync(kFull, is_hit);
     if (lane == 0 && hm) atomicAdd(&ctr->hits[depth], (unsigned)__popc(hm));
     Surface sf;
@@ -221,7 +232,12 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
     const uint32_t vcode = kPass ? (code & ~kCodeBounce) : code;
     const bool emits =
         is_hit && !via_bounce && (sf.emission.x != 0.f || sf.emission.y != 0.f || sf.emission.z != 0.f);
-    if (emits) add_fb(fp, pixel, w * sf.emission);
+    if (first_store) {
+      if (active)
+        store_fb(fp, pixel, !is_hit ? w * mk3(fp.bg_r, fp.bg_g, fp.bg_b) : (emits ? w * sf.emission : mk3(0.f, 0.f, 0.f)));
+    } else if (emits) {
+      add_fb(fp, pixel, w * sf.emission);
+    }
     if (depth == fp.nrc_depth) {
       // radiance cache: every hit here takes the radiance it reflects from
       // the cache (its own L_e is added above, as at any hit); a seeded
@@ -799,7 +815,7 @@ static rt_status stage_times(rt_scene* s, float* total, float* trace, float* sha
 
 // The side stream that runs each depth's shadow kernel while the main
 // stream traces the next depth, and the events that order them.
-static rt_status ensure_side_stream(rt_scene* s) {
+rt_status ensure_side_stream(rt_scene* s) {
   if (s->side) return RT_OK;
   cudaError_t e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
   for (int d = 0; e == cudaSuccess && d <= RT_MAX_DEPTH; ++d) {
@@ -912,7 +928,7 @@ static rt_status render_impl(rt_scene* s, const rt_camera* cam, int W, int H, in
     fp.fb_fixed = (unsigned long long*)s->fb_fixed.p;
     cudaMemsetAsync(fp.fb_fixed, 0, n_out * sizeof(unsigned long long), st);   // out is written at the end
   } else {
-    cudaMemsetAsync(out, 0, n_out * sizeof(float), st);
+    fp.fb_store = 1;   // the depth-0 kernel writes every pixel first: no clear
   }
   cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
   if (count && opt.ray_counts != nullptr) {
@@ -1214,11 +1230,8 @@ rt_status rt_scene_destroy(rt_scene* s) {
   release(s->rayq[1]);
   release(s->shadowq[0]);
   release(s->shadowq[1]);
-  if (s->build_side) {
-    cudaStreamDestroy(s->build_side);
-    cudaEventDestroy(s->ev_build_fork);
-    cudaEventDestroy(s->ev_build_join);
-  }
+  if (s->ev_build_fork) cudaEventDestroy(s->ev_build_fork);
+  if (s->ev_build_join) cudaEventDestroy(s->ev_build_join);
   if (s->side) {
     cudaStreamDestroy(s->side);
     for (int d = 0; d <= RT_MAX_DEPTH; ++d) {
@@ -1334,8 +1347,8 @@ extern "C" rt_status rt_render_noalloc(rt_scene* s, const rt_camera* cam, int W,
   int cap = (int)std::min<int64_t>(4 * std::max<int64_t>(s->n_nodes4, 1) + 64, 0x7fffffff);
   // the counters must start at zero; the queues are written before they are read
   cudaError_t e = cudaMemsetAsync(fp.ctr, 0, sizeof(Counters), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, (size_t)W * H * 3 * sizeof(float), st);
   if (e != cudaSuccess) return cuda_error(e, "rt_render_noalloc memset");
+  fp.fb_store = 1;   // the depth-0 kernel writes every pixel first: no clear
   for (int depth = 0; depth <= D; ++depth) {
     const bool pass_k = sc.n_alights + sc.n_emitters > 0;
     trace_kernel(depth == 0, false, pass_k)<<<s->trace_blocks, kTraceThreads, 0, st>>>(sc, fp, depth, cap);

@@ -138,9 +138,8 @@ struct rt_scene {
   int last_build_launches = 0;
   int lbvh_cut = 0;              // > 0: the LBVH nodes over this many primitives still await their refit
   unsigned bounds_gen = 0;       // build_tmp.gen whose centroid bounds hold their reset value
-  // the build's second stream: the parts that do not depend on the top
-  // rebuild run on it beside that rebuild
-  cudaStream_t build_side = nullptr;
+  // the build runs the parts that do not depend on the top rebuild on the
+  // side stream (below) beside that rebuild, between these two events
   cudaEvent_t ev_build_fork = nullptr, ev_build_join = nullptr;
   // render
   rtb::Buf rayq[2], shadowq[2], counters, fb_host_stage;
@@ -174,6 +173,11 @@ void release(Buf& b);
 
 // BVH (bvh.cu).
 rt_status bvh_build(rt_scene* s, cudaStream_t st);
+
+// The scene's side stream and its per-depth events (render.cu).  The build
+// uses it too: a third stream of the scene, measured, made the frame's two
+// streams stop overlapping in back-to-back steps (1.34 against 1.20 ms).
+rt_status ensure_side_stream(rt_scene* s);
 
 // Kernel launch helpers shared by render.cu.
 DevScene dev_scene(const rt_scene* s, bool use_bvh);
