@@ -316,14 +316,16 @@ rt_status rt_render_stage_times(rt_scene* s, float* ms_total, float* ms_trace, f
 rt_status rt_render_host(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
                          float* out_rgb_host, const rt_render_options* opt, void* stream);
 
-/* rt_render_host for a stream of frames: returns once the frame and its
- * copy are queued.  The frame renders on `stream` into one of two
- * scene-owned device images (alternating from call to call; a frame waits
- * for the copy that last used its image) and is copied to out_host
- * (H*W*3 float32; pinned memory for an asynchronous copy) on a copy stream
- * of the scene, so that the copy overlaps the next frame's work.  out_host
- * is complete, and may be reused, once rt_scene_sync(s, stream) has
- * returned, which also waits for the copy stream.  Errors as rt_render_ex. */
+/* rt_render_host for a stream of frames: returns once the frame is queued.
+ * The frame renders on `stream` into one of two scene-owned device images
+ * (alternating from call to call; a frame waits for the copy that last used
+ * its image) and is copied to out_host (H*W*3 float32; pinned memory for an
+ * asynchronous copy) on a copy stream of the scene.  The copy is queued by
+ * the next call, after the work already queued on its stream (the next
+ * frame's update and build), so that it runs beside the next frame's
+ * render; or by rt_scene_sync.  out_host is complete, and may be reused,
+ * once rt_scene_sync(s, stream) has returned, which also waits for the copy
+ * stream.  Errors as rt_render_ex. */
 rt_status rt_render_host_async(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
                                float* out_host, const rt_render_options* options, void* stream);
 

@@ -148,6 +148,11 @@ struct rt_scene {
   // copy stream while the next frame renders into the other
   rtb::Buf fb_stage[2];
   int stage_next = 0;
+  // the last frame's copy, queued when the next frame is (or at a sync)
+  int copy_pending = -1;         // its image (fb_stage index), or -1
+  float* copy_dst = nullptr;
+  size_t copy_bytes = 0;
+  cudaEvent_t ev_issue = nullptr;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_rendered[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
   cudaStream_t side = nullptr;   // runs each depth's shadow kernel beside the next depth's trace
@@ -178,6 +183,10 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st);
 // uses it too: a third stream of the scene, measured, made the frame's two
 // streams stop overlapping in back-to-back steps (1.34 against 1.20 ms).
 rt_status ensure_side_stream(rt_scene* s);
+
+// Queues the copy rt_render_host_async left pending, if any, after the
+// frame that rendered it (render.cu).
+rt_status issue_pending_copy(rt_scene* s);
 
 // Kernel launch helpers shared by render.cu.
 DevScene dev_scene(const rt_scene* s, bool use_bvh);

@@ -317,6 +317,8 @@ rt_status rt_scene_update(rt_scene* s, const rt_sphere* spheres, const rt_triang
 rt_status rt_scene_sync(rt_scene* s, void* stream) {
   if (!s) return set_error(RT_ERR_INVALID_ARG, "rt_scene_sync: scene is NULL");
   cudaStream_t st = (cudaStream_t)stream;
+  rt_status rs = issue_pending_copy(s);   // the last rt_render_host_async frame's image
+  if (rs) return rs;
   cudaError_t e = cudaStreamSynchronize(st);
   // and the host copies of rt_render_host_async, which follow the stream's frames
   if (e == cudaSuccess && s->copy_stream) e = cudaStreamSynchronize(s->copy_stream);
