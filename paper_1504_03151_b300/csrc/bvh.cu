@@ -702,14 +702,18 @@ __global__ void k_info_sah_lbvh(const float* __restrict__ cost_lbvh, BuildInfo* 
 // 6. binned-SAH rebuild of the top levels (HLBVH style): the LBVH nodes
 //    with at most `cluster_max` primitives whose parent has more become
 //    clusters; a new top tree is built over the clusters' boxes with 16
-//    bins per axis, level by level (one block per segment).
+//    bins per axis, level by level (one block per segment).  With clusters
+//    of at most kWarpRefitMax primitives, the clusters are found first and
+//    each cluster's subtree is then refitted by one warp in shared memory
+//    (k_refit_clusters) instead of by k_refit's climb through global
+//    atomics; the LBVH nodes above the clusters are never refitted.
 // ---------------------------------------------------------------------------
 __global__ void k_find_clusters(int n, int cluster_max, const int* __restrict__ lch, const int* __restrict__ rch,
                                 const int2* __restrict__ range, const float4* __restrict__ node_lo,
                                 const float4* __restrict__ node_hi, const unsigned* __restrict__ vals,
                                 const float4* __restrict__ aabb_lo, const float4* __restrict__ aabb_hi,
                                 int* __restrict__ clu_count_out, int* __restrict__ clu_ids, int* __restrict__ clu_link,
-                                float4* __restrict__ clu_lo, float4* __restrict__ clu_hi) {
+                                float4* __restrict__ clu_lo, float4* __restrict__ clu_hi, int defer) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   int2 rg = range[i];
@@ -731,18 +735,146 @@ __global__ void k_find_clusters(int n, int cluster_max, const int* __restrict__ 
       int2 r2 = range[c];
       count = r2.y - r2.x + 1;
       if (count > cluster_max) continue;
-      lo = node_lo[c];
-      hi = node_hi[c];
-      int meta = __float_as_int(hi.w);
-      bool collapse = (meta >> 8) & 1;
-      link = collapse ? leaf_link(r2.x, count) : c;
-      height = collapse ? 0 : (meta & 0xff);
+      if (defer) {
+        // k_refit_clusters refits the subtree and completes the entry
+        lo = hi = make_float4(0.f, 0.f, 0.f, 0.f);
+        link = c;
+        height = 0;
+      } else {
+        lo = node_lo[c];
+        hi = node_hi[c];
+        int meta = __float_as_int(hi.w);
+        bool collapse = (meta >> 8) & 1;
+        link = collapse ? leaf_link(r2.x, count) : c;
+        height = collapse ? 0 : (meta & 0xff);
+      }
     }
     int slot = atomicAdd(clu_count_out, 1);
     clu_ids[slot] = slot;
     clu_link[slot] = link;
     clu_lo[slot] = make_float4(lo.x, lo.y, lo.z, (float)count);
     clu_hi[slot] = make_float4(hi.x, hi.y, hi.z, __int_as_float(height));
+  }
+}
+
+// One warp per cluster entry whose link is still a node id (k_find_clusters
+// with `defer`): the same boxes, SAH costs, leaf collapsing and node writes
+// as k_refit, for the subtree under that node, climbed bottom-up inside the
+// warp.  The subtree's leaf boxes and links are loaded into shared memory
+// first (one round trip); then every round, each live item (a leaf, or a
+// node refitted in an earlier round) arrives at its parent through a
+// shared-memory counter, and the second arrival refits the parent.  Then
+// the warp completes the entry as k_find_clusters would have.
+constexpr int kWarpRefitMax = 64;   // cluster size up to which this path is taken
+constexpr int kWarpRefitWarps = 4;  // warps per block
+
+__global__ void __launch_bounds__(32 * kWarpRefitWarps)
+    k_refit_clusters(int n, const unsigned* __restrict__ vals, const float4* __restrict__ aabb_lo,
+                     const float4* __restrict__ aabb_hi, const int* __restrict__ lch, const int* __restrict__ rch,
+                     const int* __restrict__ parent, const int* __restrict__ leaf_parent,
+                     const int2* __restrict__ range, float4* __restrict__ node_lo, float4* __restrict__ node_hi,
+                     float* __restrict__ cost_lbvh, const int* __restrict__ n_clusters, int* __restrict__ clu_link,
+                     float4* __restrict__ clu_lo, float4* __restrict__ clu_hi) {
+  constexpr int M = kWarpRefitMax;
+  // slot q < M: leaf a + q; slot M + q: internal node a + q (lo.w = cost, hi.w = meta bits)
+  __shared__ float4 s_lo[kWarpRefitWarps][2 * M], s_hi[kWarpRefitWarps][2 * M];
+  __shared__ float s_cl[kWarpRefitWarps][M];   // the plain LBVH's cost of internal slot q
+  __shared__ int s_l[kWarpRefitWarps][M], s_r[kWarpRefitWarps][M], s_par[kWarpRefitWarps][M];
+  __shared__ int s_cnt[kWarpRefitWarps][M], s_lpar[kWarpRefitWarps][M], s_flag[kWarpRefitWarps][M];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n_entries = __ldg(n_clusters);
+  const int warps = (int)gridDim.x * kWarpRefitWarps;
+  float4* lo_s = s_lo[w];
+  float4* hi_s = s_hi[w];
+  for (int e = (int)blockIdx.x * kWarpRefitWarps + w; e < n_entries; e += warps) {
+    const int R = clu_link[e];
+    if (R < 0) continue;   // a one-primitive cluster, complete
+    const int2 rg = range[R];
+    const int a = rg.x, m = rg.y - rg.x + 1;   // 2 <= m <= M
+    if (m > M) continue;   // not reachable: the host takes this path only for clusters of <= M
+    __syncwarp();
+    for (int q = lane; q < m; q += 32) {
+      const unsigned pid = vals[a + q];
+      lo_s[q] = aabb_lo[pid];
+      hi_s[q] = aabb_hi[pid];
+      s_lpar[w][q] = leaf_parent[a + q];
+      const int i = a + q;
+      if (i <= n - 2) {
+        s_l[w][q] = lch[i];
+        s_r[w][q] = rch[i];
+        s_par[w][q] = parent[i];
+        const int2 ri = range[i];
+        s_cnt[w][q] = ri.y - ri.x + 1;
+      }
+      s_flag[w][q] = 0;
+    }
+    __syncwarp();
+    // each lane's items: its leaves; an item is a slot (leaf q, or M + q), -1 when done
+    int item[2] = {lane < m ? lane : -1, lane + 32 < m ? lane + 32 : -1};
+    for (int round = 0; round <= 2 * M; ++round) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int it = item[k];
+        if (it < 0) continue;
+        if (it == M + (R - a)) {   // the cluster's root: done
+          item[k] = -1;
+          continue;
+        }
+        const int p = it < M ? s_lpar[w][it] : s_par[w][it - M];
+        const int pq = p - a;
+        if (pq < 0 || pq >= m) {   // not reachable in a well-formed tree
+          item[k] = -1;
+          continue;
+        }
+        if (atomicAdd(&s_flag[w][pq], 1) == 0) {   // the sibling refits the parent
+          item[k] = -1;
+          continue;
+        }
+        // both children are ready: refit p (as refit_node, from shared memory)
+        const int cl_ = s_l[w][pq], cr_ = s_r[w][pq];
+        const int sl = cl_ < 0 ? (~cl_) - a : M + (cl_ - a), sr = cr_ < 0 ? (~cr_) - a : M + (cr_ - a);
+        const float4 al = lo_s[sl], ah = hi_s[sl], bl = lo_s[sr], bh = hi_s[sr];
+        const bool la = sl < M, lb = sr < M;
+        const float ca = la ? kCostIsect : al.w, cb = lb ? kCostIsect : bl.w;
+        const float cla = la ? kCostIsect : s_cl[w][sl - M], clb = lb ? kCostIsect : s_cl[w][sr - M];
+        const int ha = la ? 0 : (__float_as_int(ah.w) & 0xff), hb = lb ? 0 : (__float_as_int(bh.w) & 0xff);
+        float4 lo = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.f);
+        float4 hi = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.f);
+        const float A = area(lo, hi), Aa = area(al, ah), Ab = area(bl, bh);
+        float ci, cl;
+        if (A > 0.f) {
+          ci = kCostTrav + (Aa * ca + Ab * cb) / A;
+          cl = kCostTrav + (Aa * cla + Ab * clb) / A;
+        } else {
+          ci = kCostTrav + ca + cb;
+          cl = kCostTrav + cla + clb;
+        }
+        const int count = s_cnt[w][pq];
+        const float leaf_cost = kCostIsect * (float)count;
+        const int collapse = (count <= kMaxLeaf && leaf_cost <= ci) ? 1 : 0;
+        const int height = collapse ? 0 : 1 + max(ha, hb);
+        lo.w = collapse ? leaf_cost : ci;
+        hi.w = __int_as_float(height | (collapse << 8));
+        lo_s[M + pq] = lo;
+        hi_s[M + pq] = hi;
+        s_cl[w][pq] = cl;
+        node_lo[p] = lo;
+        node_hi[p] = hi;
+        cost_lbvh[p] = cl;
+        item[k] = M + pq;
+      }
+      __syncwarp();
+      if (!__any_sync(FULL, (item[0] >= 0) | (item[1] >= 0))) break;
+    }
+    if (lane == 0) {
+      const float4 lo = lo_s[M + (R - a)], hi = hi_s[M + (R - a)];
+      const int meta = __float_as_int(hi.w);
+      const bool collapse = (meta >> 8) & 1;
+      clu_link[e] = collapse ? leaf_link(a, m) : R;
+      clu_lo[e] = make_float4(lo.x, lo.y, lo.z, (float)m);
+      clu_hi[e] = make_float4(hi.x, hi.y, hi.z, __int_as_float(collapse ? 0 : (meta & 0xff)));
+    }
   }
 }
 
@@ -1939,8 +2071,12 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
                                    b.seg_count, kTopMaxLevels + 3);
   int cmax = cluster_max_for(n);
   const bool top = n > 2 * cmax;   // the top levels are rebuilt over clusters of <= cmax primitives
-  k_refit<<<grid, tb, 0, st>>>(n, top ? cmax : n, b.vals0, b.aabb_lo, b.aabb_hi, b.lch, b.rch, b.parent,
-                               b.leaf_parent, b.range, b.node_lo, b.node_hi, b.cost_lbvh, b.flags);
+  // clusters of at most kWarpRefitMax primitives are refitted one warp each
+  // after they are found (k_refit_clusters); otherwise k_refit climbs first
+  const bool warp_refit = top && cmax <= kWarpRefitMax;
+  if (!warp_refit)
+    k_refit<<<grid, tb, 0, st>>>(n, top ? cmax : n, b.vals0, b.aabb_lo, b.aabb_hi, b.lch, b.rch, b.parent,
+                                 b.leaf_parent, b.range, b.node_lo, b.node_hi, b.cost_lbvh, b.flags);
   // the LBVH above the clusters only feeds the plain LBVH's cost, which
   // rt_bvh_get_info computes when asked (upper_refit)
   s->lbvh_cut = top ? cmax : 0;
@@ -1969,7 +2105,13 @@ rt_status bvh_build(rt_scene* s, cudaStream_t st) {
     // allocates gets both children written; the slots past them are never
     // read (k_collapse4 stops at *top_count).
     k_find_clusters<<<grid, tb, 0, st>>>(n, cmax, b.lch, b.rch, b.range, b.node_lo, b.node_hi, b.vals0, b.aabb_lo,
-                                         b.aabb_hi, n_clusters_dev, b.clu_a, b.clu_link, b.clu_lo, b.clu_hi);
+                                         b.aabb_hi, n_clusters_dev, b.clu_a, b.clu_link, b.clu_lo, b.clu_hi,
+                                         warp_refit ? 1 : 0);
+    if (warp_refit) {
+      k_refit_clusters<<<8 * s->sm_count, 32 * kWarpRefitWarps, 0, st>>>(
+          n, b.vals0, b.aabb_lo, b.aabb_hi, b.lch, b.rch, b.parent, b.leaf_parent, b.range, b.node_lo, b.node_hi,
+          b.cost_lbvh, n_clusters_dev, b.clu_link, b.clu_lo, b.clu_hi);
+    }
     if (fork) {
       cudaEventRecord(s->ev_build_fork, st);
       cudaStreamWaitEvent(s->side, s->ev_build_fork, 0);
