@@ -283,6 +283,33 @@ def test_bvh_structure_invariants(which):
     assert info["sah_cost"] <= info["sah_cost_lbvh"] * 1.001 or which == "spheres8"
 
 
+def test_rebuilds_sort_the_same():
+    """The single-launch sort's digit counts are made by the Morton kernel
+    and by each pass's scatter, and cleared after use: every rebuild of a
+    scene (24-bit keys, and 30-bit keys above 2^17 primitives) sorts the
+    same, and an update that changes the geometry sorts its new codes."""
+    for sc in (S.scene_terrain(), large_terrain()):
+        n = sc.n_prims
+        scene = rtb.Scene(sc).build()
+        first = rtb.rt_bvh_export(scene.handle, n, 2 * n)
+        for _ in range(3):
+            rtb.rt_bvh_build(scene.handle)
+            _, order, morton = rtb.rt_bvh_export(scene.handle, n, 2 * n)
+            assert np.array_equal(order, first[1]) and np.array_equal(morton, first[2])
+        tris = sc.triangles.copy()
+        for k in ("v0", "v1", "v2"):
+            tris[k][:, 1] *= 0.5                     # flatten: new codes
+        rtb.rt_scene_update(scene.handle, sc.spheres, tris)
+        rtb.rt_bvh_build(scene.handle)
+        _, order, morton = rtb.rt_bvh_export(scene.handle, n, 2 * n)
+        assert np.array_equal(np.sort(order), np.arange(n))
+        assert (np.diff(morton.astype(np.int64)) >= 0).all()
+        eq = np.diff(morton.astype(np.int64)) == 0
+        assert (np.diff(order)[eq] > 0).all()
+        assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+        scene.close()
+
+
 def _prim_boxes(sc):
     n = sc.n_prims
     lo, hi = np.zeros((n, 3)), np.zeros((n, 3))
