@@ -48,15 +48,15 @@ BYTES_RAY_IO = 48 + 16
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "119b45fff075d3e8"
+PROFILED_SHA = "06c2780849874b25"
 PROFILED_TRAFFIC = {
-    0: (24_656_384 + 123_875_072 + 5_517_312 + 1_024 + 7_845_120 + 112_851_712,
+    0: (10_055_424 + 133_894_400 + 5_491_968 + 0 + 8_006_912 + 107_245_568,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's k_trace<1,0,0>, k_trace<0,0,0> "
         "(depth 1) and k_paths<0,0> (depths 2-5) launches, one capture per kernel (-k, -c 2 / -c 1); "
-        "L2 bytes (lts__t_bytes.sum) 706,708,640"),
-    1: (179_920_640 + 8_221_696 + 5_800_448,
+        "L2 bytes (lts__t_bytes.sum) 674,188,384"),
+    1: (179_861_504 + 7_645_696 + 5_799_424 + 0,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's two k_shadow<0> launches "
-        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 797,715,328"),
+        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 796,925,472"),
 }
 
 
