@@ -300,7 +300,14 @@ rt_status rt_render(rt_scene* s, const rt_camera* cam, int width, int height, in
  * (NULL = defaults; use_bvh = 0 is Alg. 1's loop over every object),
  * optional primary-ray AOVs (device, H*W: hit primitive id / hit distance,
  * inf on a miss) and optional stats (host; filled after a stream sync, which
- * also returns the latched kernel errors). */
+ * also returns the latched kernel errors).
+ *
+ * CUDA graphs: once a scene has been built and rendered at a given size,
+ * depth and options, rt_scene_update from device arrays, rt_bvh_build and
+ * rt_render / rt_render_ex without stats allocate nothing and never wait
+ * for the host, so a frame's calls can be captured into a CUDA graph
+ * (stream capture on `stream`) and replayed.  A replay repeats the captured
+ * camera and sizes, and reads the geometry arrays anew. */
 rt_status rt_render_ex(rt_scene* s, const rt_camera* cam, int width, int height, int max_depth,
                        float* out_rgb_device, const rt_render_options* opt, int32_t* aov_prim,
                        float* aov_t, rt_render_stats* stats, void* stream);
