@@ -2026,7 +2026,86 @@ static rt_status ensure_build_side(rt_scene* s) {
   return cuda_error(e, "rt_bvh_build: side stream");
 }
 
+static rt_status bvh_build_launch(rt_scene* s, cudaStream_t st);
+
+// The buffers a build's launches name, by their allocation generations.
+static void build_key(const rt_scene* s, unsigned key[6]) {
+  key[0] = (unsigned)s->n_prims;
+  key[1] = s->build_tmp.gen;
+  key[2] = s->nodes.gen;
+  key[3] = s->nodes4.gen;
+  key[4] = s->prims_id.gen;
+  key[5] = s->prims_leaf.gen;
+}
+
+// A build: its ~20 launches (kernels, memsets, the side stream's fork and
+// join) depend only on the scene's size and buffers.  A build that found
+// the buffers unchanged by the build before it captures its launches into
+// a CUDA graph, and later builds with the same buffers replay that graph
+// on their stream (one launch instead of twenty).  A build called on a
+// stream that is being captured launches directly, into the caller's graph.
 rt_status bvh_build(rt_scene* s, cudaStream_t st) {
+  if (s->n_prims < 2) return bvh_build_launch(s, st);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return bvh_build_launch(s, st);
+  }
+  unsigned key[6];
+  build_key(s, key);
+  const bool same = memcmp(key, s->build_key, sizeof(key)) == 0;
+  if (s->build_exec && same) {
+    cudaError_t e = cudaGraphLaunch(s->build_exec, st);
+    if (e != cudaSuccess) return cuda_error(e, "rt_bvh_build: graph launch");
+    s->root = s->build_root;
+    s->lbvh_cut = s->build_lbvh_cut;
+    s->n_nodes_total = s->build_nodes_total;
+    s->n_nodes4 = s->build_nodes4;
+    s->last_build_launches = s->build_launches;
+    s->built = true;
+    return RT_OK;
+  }
+  if (s->build_exec) {
+    cudaGraphExecDestroy(s->build_exec);
+    s->build_exec = nullptr;
+  }
+  rt_status rs = bvh_build_launch(s, st);
+  if (rs) return rs;
+  unsigned after[6];
+  build_key(s, after);
+  if (memcmp(after, key, sizeof(key)) != 0 || s->build_cap_failed) {
+    memcpy(s->build_key, after, sizeof(after));   // buffers were (re)allocated: capture next time
+    return RT_OK;
+  }
+  // nothing was allocated: the same launches, captured for the next builds
+  cudaError_t e = cudaSuccess;
+  if (!s->build_cap) e = cudaStreamCreateWithFlags(&s->build_cap, cudaStreamNonBlocking);
+  cudaGraph_t graph = nullptr;
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(s->build_cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rs = bvh_build_launch(s, s->build_cap);
+    e = cudaStreamEndCapture(s->build_cap, &graph);
+    if (rs != RT_OK && e == cudaSuccess) e = cudaErrorUnknown;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&s->build_exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    // no graph then: every build launches directly
+    cudaGetLastError();
+    s->build_exec = nullptr;
+    s->build_cap_failed = true;
+    return RT_OK;
+  }
+  memcpy(s->build_key, key, sizeof(key));
+  s->build_root = s->root;
+  s->build_lbvh_cut = s->lbvh_cut;
+  s->build_nodes_total = s->n_nodes_total;
+  s->build_nodes4 = s->n_nodes4;
+  s->build_launches = s->last_build_launches;
+  return RT_OK;
+}
+
+static rt_status bvh_build_launch(rt_scene* s, cudaStream_t st) {
   int n = (int)s->n_prims;
   if (n == 0) {
     s->root = -1;

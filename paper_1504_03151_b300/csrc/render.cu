@@ -1259,6 +1259,8 @@ rt_status rt_scene_destroy(rt_scene* s) {
   release(s->rayq[1]);
   release(s->shadowq[0]);
   release(s->shadowq[1]);
+  if (s->build_exec) cudaGraphExecDestroy(s->build_exec);
+  if (s->build_cap) cudaStreamDestroy(s->build_cap);
   if (s->ev_build_fork) cudaEventDestroy(s->ev_build_fork);
   if (s->ev_build_join) cudaEventDestroy(s->ev_build_join);
   if (s->side) {

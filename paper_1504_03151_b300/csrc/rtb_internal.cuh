@@ -138,6 +138,14 @@ struct rt_scene {
   int last_build_launches = 0;
   int lbvh_cut = 0;              // > 0: the LBVH nodes over this many primitives still await their refit
   unsigned bounds_gen = 0;       // build_tmp.gen whose centroid bounds hold their reset value
+  // the build's launches captured into a CUDA graph, replayed by the builds
+  // that find the same buffers (bvh.cu)
+  cudaGraphExec_t build_exec = nullptr;
+  cudaStream_t build_cap = nullptr;   // the stream the build is captured on
+  unsigned build_key[6] = {0, 0, 0, 0, 0, 0};
+  bool build_cap_failed = false;
+  int build_root = 0, build_lbvh_cut = 0, build_launches = 0;
+  int64_t build_nodes_total = 0, build_nodes4 = 0;
   // the build runs the parts that do not depend on the top rebuild on the
   // side stream (below) beside that rebuild, between these two events
   cudaEvent_t ev_build_fork = nullptr, ev_build_join = nullptr;
