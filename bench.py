@@ -48,7 +48,7 @@ BYTES_RAY_IO = 48 + 16
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "06c2780849874b25"
+PROFILED_SHA = "71b39b7f28311edf"
 PROFILED_TRAFFIC = {
     0: (10_055_424 + 133_894_400 + 5_491_968 + 0 + 8_006_912 + 107_245_568,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's k_trace<1,0,0>, k_trace<0,0,0> "
