@@ -25,9 +25,10 @@ constexpr int kTopMaxLevels = 64;   // launches of the level kernel (empty ones 
 constexpr int kTopCache = 4096;     // clusters of one segment held in shared memory (41 B each)
 // A segment of more clusters bins an even subsample of about this many to
 // choose its split plane (the partition still takes every cluster).  On the
-// 1080p terrain the root's 3,299 clusters bin 550 (the two next levels' 1,650
-// and 825 bin 550 and 413): the build is 6 us shorter than with all of
-// them, and the tree's SAH cost 28.48 against 28.50 (256: 28.61).
+// 1080p terrain the root's 3,299 clusters bin every 7th (472), the next
+// levels' 1,650 and 825 every 4th and every 2nd (413 each): the build is
+// 6 us shorter than with a subsample of 1024, and the tree's SAH cost 28.48
+// against 28.50 (with 256: 28.61).
 constexpr int kTopSample = 512;
 constexpr int kTopWarpSeg = 32;     // segments of at most this many clusters are finished by one warp
 constexpr int kTopForceMedian = 32; // from this level on, split segments at the middle: with at
