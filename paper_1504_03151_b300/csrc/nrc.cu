@@ -32,14 +32,20 @@ __host__ __device__ constexpr int off_b(int l) { return kNW + 64 * l; }
 __host__ __device__ constexpr int d_in(int l) { return l == 0 ? 96 : 64; }
 __host__ __device__ constexpr int d_out(int l) { return l == 4 ? 3 : 64; }
 
-// Packed BF16 copies (row-major) read by the kernels, then FP32 biases.
-// forward W_l as [out][in] (W4 padded to 16 rows), backward W_l^T as
-// [in][out] (W4^T padded to 16 columns).
-constexpr int kPW0 = 0, kPW1 = 6144, kPW2 = 10240, kPW3 = 14336, kPW4 = 18432;   // W4: 16 x 64
-constexpr int kPT1 = 19456, kPT2 = 23552, kPT3 = 27648, kPT4 = 31744;             // T4: 64 x 16
-constexpr int kPackedBf16 = 32768;                                                 // 64 KB
+// The packed copy the kernels read: the BF16 weights as the shared-memory
+// image of the forward operands (W_l as [out][in] in the K-major core-matrix
+// layout of tc::core_off; W4 padded to 16 rows of zeros), so that one bulk
+// copy stages them, then the FP32 biases (b0..b3, b4 padded to 16).  The
+// backward pass reads the same tiles as MN-major operands: W_l^T needs no
+// copy of its own.
+constexpr int kImgW0 = 0, kImgW1 = 12288, kImgW2 = 20480, kImgW3 = 28672, kImgW4 = 36864;   // bytes
+constexpr int kImgBytes = 38912;
 constexpr int kPackedBias = 4 * 64 + 16;
-constexpr size_t kPackedBytes = kPackedBf16 * 2 + kPackedBias * 4;
+constexpr int kPackedBytes = kImgBytes + kPackedBias * 4;   // 40,000
+__host__ __device__ constexpr int img_off(int l) {
+  return l == 0 ? kImgW0 : l == 1 ? kImgW1 : l == 2 ? kImgW2 : l == 3 ? kImgW3 : kImgW4;
+}
+static_assert(kImgBytes % 16 == 0 && kPackedBytes % 16 == 0, "bulk copies move whole 16-byte units");
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float bf16_float(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
@@ -83,15 +89,40 @@ __device__ __forceinline__ void store_chunk(uint8_t* tile, int r, int c, int K, 
   *(uint4*)(tile + tc::core_off(r, 8 * c, K)) = q;
 }
 
-// Copies a row-major [R][K] bf16 matrix from global memory into a K-major
-// canonical tile (16-byte chunks).
-__device__ __forceinline__ void load_tile(uint8_t* tile, const uint16_t* __restrict__ g, int R, int K) {
-  int chunks = R * (K / 8);
-  for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
-    int r = i / (K / 8), c = i % (K / 8);
-    uint4 q = *(const uint4*)(g + (size_t)r * K + 8 * c);
-    *(uint4*)(tile + tc::core_off(r, 8 * c, K)) = q;
+// The same 96 features for row t of a K-major [128][96] tile, each 16-byte
+// chunk stored as soon as its 8 features exist (fewer live registers than
+// encoding the whole row first).  A row past the batch is zero.
+__device__ __forceinline__ void encode_store(const float* pnv, const float* lo, const float* inv_ext, bool valid,
+                                             uint8_t* tile, int t) {
+  float f[96];
+  float xh[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    xh[j] = (pnv[j] - lo[j]) * inv_ext[j];
+    f[j] = valid ? xh[j] : 0.f;
+    f[3 + j] = valid ? pnv[3 + j] : 0.f;
+    f[6 + j] = valid ? pnv[6 + j] : 0.f;
   }
+  store_chunk(tile, t, 0, 96, f);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float sc = (float)(1 << k);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float sn, cs;
+      sincospif(sc * xh[j], &sn, &cs);
+      f[9 + 6 * k + j] = valid ? sn : 0.f;
+      f[9 + 6 * k + 3 + j] = valid ? cs : 0.f;
+    }
+    const int have = 9 + 6 * (k + 1);   // features formed so far
+#pragma unroll
+    for (int c = 1; c < 10; ++c)
+      if (8 * c + 8 <= have && 8 * c + 8 > have - 6) store_chunk(tile, t, c, 96, f + 8 * c);
+  }
+#pragma unroll
+  for (int k = kFeatures; k < 96; ++k) f[k] = 0.f;
+  store_chunk(tile, t, 10, 96, f + 80);
+  store_chunk(tile, t, 11, 96, f + 88);
 }
 
 // ---------------------------------------------------------------------------
@@ -101,8 +132,8 @@ __device__ __forceinline__ void load_tile(uint8_t* tile, const uint16_t* __restr
 constexpr int kInferThreads = 128;
 constexpr int kInferTmemCols = 64;
 // dynamic shared memory (bytes), 1 KB aligned sections
-constexpr int kSmW0 = 0, kSmW1 = 12288, kSmW2 = 20480, kSmW3 = 28672, kSmW4 = 36864;   // 2 KB
-constexpr int kSmBias = 38912;                                                         // 272 floats
+constexpr int kSmW0 = kImgW0, kSmW1 = kImgW1, kSmW2 = kImgW2, kSmW3 = kImgW3, kSmW4 = kImgW4;
+constexpr int kSmBias = kImgBytes;   // 272 floats: the packed copy lands here whole
 constexpr int kSmA = 40960;                                                            // 24 KB
 constexpr int kSmMisc = 65536;                                                         // mbarrier, tmem slot, flags
 constexpr int kInferSmem = kSmMisc + 64;
@@ -124,23 +155,22 @@ __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const
   int* abort_flag = (int*)(sm + kSmMisc + 16);
   float* bias = (float*)(sm + kSmBias);
   int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t wbar = tc::smem_u32(sm + kSmMisc + 24);
   if (warp == 0) tc::alloc(tc::smem_u32(tslot), kInferTmemCols);
-  const uint16_t* pw = (const uint16_t*)nd.packed;
-  load_tile(sm + kSmW0, pw + kPW0, 64, 96);
-  load_tile(sm + kSmW1, pw + kPW1, 64, 64);
-  load_tile(sm + kSmW2, pw + kPW2, 64, 64);
-  load_tile(sm + kSmW3, pw + kPW3, 64, 64);
-  load_tile(sm + kSmW4, pw + kPW4, 16, 64);
-  const float* gb = (const float*)(pw + kPackedBf16);
-  for (int i = tid; i < kPackedBias; i += blockDim.x) bias[i] = gb[i];
   if (tid == 0) {
     tc::mbar_init(tc::smem_u32(mbar), 1);
+    tc::mbar_init(wbar, 1);
     *abort_flag = 0;
+    tc::fence_mbar_init();
+    // the weights' shared-memory image and the biases: one bulk copy
+    tc::mbar_expect_tx(wbar, kPackedBytes);
+    tc::bulk_g2s(tc::smem_u32(sm), nd.packed, kPackedBytes, wbar);
   }
-  tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  const bool w_ok = !__syncthreads_or(!tc::mbar_wait(wbar, 0));
+  if (!w_ok && tid == 0) atomicOr(status, kErrNrcTimeout);
   uint32_t tmem = *tslot;
   uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
   uint32_t mb = tc::smem_u32(mbar);
@@ -148,7 +178,7 @@ __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const
   const uint32_t sW[5] = {tc::smem_u32(sm + kSmW0), tc::smem_u32(sm + kSmW1), tc::smem_u32(sm + kSmW2),
                           tc::smem_u32(sm + kSmW3), tc::smem_u32(sm + kSmW4)};
   unsigned n = min(*count, cap);
-  unsigned tiles = (n + 127) / 128;
+  unsigned tiles = w_ok ? (n + 127) / 128 : 0u;
   uint32_t phase = 0;
   float lo[3] = {nd.lo[0], nd.lo[1], nd.lo[2]}, ie[3] = {nd.inv_ext[0], nd.inv_ext[1], nd.inv_ext[2]};
   for (unsigned tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -229,39 +259,64 @@ done:
 // training: forward (activations kept), loss gradient, backward; weight and
 // bias gradients accumulate in tensor memory over the CTA's tiles, then go
 // to its own row of the gradient buffer.  One CTA per SM (its 512
-// tensor-memory columns), 128 samples a tile, one sample a thread.
+// tensor-memory columns) keeps two tiles of 128 samples in flight: warpgroup
+// s (warps 4s..4s+3, one sample a thread) runs the epilogues of the tiles of
+// slot s, and one lane of warp 8 issues every MMA, alternating between the
+// slots stage by stage in a fixed order.  One slot's epilogue runs while the
+// other slot's MMAs do, and the accumulated gradient does not depend on
+// timing.
 //
 // Every activation is stored once, row by row (a sample's features in
 // 16-byte chunks, the K-major layout of the forward MMAs).  The
 // weight-gradient MMAs, whose K is the batch, read the same tiles as
-// MN-major operands, so no transposed copy is made.  The activation tiles
-// carry a constant column of ones past their features, so each weight-
-// gradient MMA also sums the backward signal over the batch: the bias
-// gradient of that layer.
+// MN-major operands, and the backward MMAs read the forward weight tiles as
+// MN-major W^T, so no transposed copy is made.  The backward signal dZ_l
+// is written over H_l once dW_l has been formed from H_l.  The bias
+// gradients are MMAs of dZ^T against a tile of ones.
 // ---------------------------------------------------------------------------
-constexpr int kTrainThreads = 128;
+constexpr int kTrainWarps = 9;   // two epilogue warpgroups, then the MMA warp
+constexpr int kTrainThreads = 32 * kTrainWarps;
 constexpr int kTrainTmemCols = 512;
-// activation tiles: width (features + the ones column, padded to 8)
-constexpr int kXW = 104;    // X: 96 features, ones at column 96
-constexpr int kHW = 80;     // H1..H4: 64 features, ones at column 64
 // tensor-memory columns (16-aligned)
-constexpr int kTcAcc = 0;      // 64: forward / backward accumulator (M = 128)
-constexpr int kTcDW0 = 64;     // 104: dW0 | dB0 (M = 64, N = 104)
-constexpr int kTcDW1 = 176;    // 80 each at 176, 256, 336: dW_l | dB_l (M = 64, N = 80)
-constexpr int kTcDW4 = 416;    // 16: dW4^T (M = 64, N = 16)
-// shared memory (bytes)
-constexpr int kTsW0 = 0, kTsW1 = 12288, kTsW2 = 20480, kTsW3 = 28672, kTsW4 = 36864;   // forward, 38 KB
-constexpr int kTsT1 = 38912, kTsT2 = 47104, kTsT3 = 55296, kTsT4 = 63488;              // backward, 26 KB
-constexpr int kTsX = 65536;                        // X [128][104]: 26 KB
-constexpr int kTsH = kTsX + 128 * kXW * 2;         // H1..H4 [128][80]: 4 x 20 KB
-constexpr int kTsDZ = kTsH + 4 * 128 * kHW * 2;    // dZ [128][64] (dZ5: [128][16]): 16 KB
-constexpr int kTsBias = kTsDZ + 16384;             // 272 floats
-constexpr int kTsDB = kTsBias + 1088;              // dB4 of each warp: 4 x 4 floats
-constexpr int kTsMisc = kTsDB + 64;                // mbarrier, tmem slot, loss of each warp
-// the allocation ends 32 KB past the last tile, so that no operand
-// descriptor can reach past it whatever its strides
-constexpr int kTrainSmem = kTsMisc + 64 + 32768;
+constexpr int kTcAcc = 0;      // 64 a slot, at 64 s: forward / backward accumulator (M = 128)
+constexpr int kTcDW0 = 128;    // 96: dW0 (M = 64 out, N = 96 in)
+constexpr int kTcDW1 = 224;    // 64 each at 224, 288, 352: dW1..dW3
+constexpr int kTcDW4 = 416;    // 16: dW4^T (M = 64 in, N = 16 out)
+constexpr int kTcDB = 432;     // 16 each at 432 + 16 l: dB0..dB3 (M = 64 out; every column the same sum)
+static_assert(kTcDB + 4 * 16 <= kTrainTmemCols, "the training accumulators exceed the tensor memory");
+__host__ __device__ constexpr int tc_dw(int l) { return l == 0 ? kTcDW0 : kTcDW1 + 64 * (l - 1); }
+// shared memory (bytes): the weight image, a ones tile, control words, then two slots
+constexpr int kTsOnes = kImgBytes;         // [16][128] ones, K-major: 4 KB
+constexpr int kTsMisc = kTsOnes + 4096;    // mbarriers, tensor-memory slot, abort flag, per-warp sums
+constexpr int kTsSlot0 = kTsMisc + 256;
+constexpr int kTsX = 0;                    // within a slot: X [128][96]
+constexpr int kTsH = 24576;                // H1..H4 [128][64], 16 KB each (then dZ1..dZ4)
+constexpr int kTsZ5 = kTsH + 4 * 16384;    // dZ5 [128][16]
+constexpr int kTsSlotBytes = kTsZ5 + 4096;
+constexpr int kTrainSmem = kTsSlot0 + 2 * kTsSlotBytes;
 static_assert(kTrainSmem <= 227 * 1024, "the training CTA's shared memory exceeds the per-block limit");
+static_assert(kTsSlot0 % 16 == 0 && kTsSlotBytes % 16 == 0, "operand tiles start on 16-byte boundaries");
+
+// Bytes an operand read spans from its start address (one past the last
+// byte), for the two unswizzled layouts the MMAs below use: K-major (8-row
+// groups `sbo` apart, K = 16 steps 256 B apart) and MN-major (K = 16 steps
+// 2 k_pitch apart, 8-element chunks along M or N 128 B apart).  Each
+// operand's span must fit its tile: no MMA reads past it.
+__host__ __device__ constexpr int span_kmajor(int rows, int K, int sbo) {
+  return (rows / 8 - 1) * sbo + (K / 16 - 1) * 256 + 256;
+}
+__host__ __device__ constexpr int span_mnmajor(int mn, int K, int k_pitch) {
+  return (K / 16 - 1) * 2 * k_pitch + k_pitch + (mn / 8 - 1) * 128 + 128;
+}
+static_assert(span_kmajor(128, 96, 1536) <= 24576 && span_kmajor(128, 64, 1024) <= 16384 &&
+                  span_kmajor(128, 16, 256) <= 4096, "forward A operands (X, H_l, dZ5)");
+static_assert(span_kmajor(64, 96, 1536) <= kImgW1 - kImgW0 && span_kmajor(64, 64, 1024) <= kImgW2 - kImgW1 &&
+                  span_kmajor(16, 64, 1024) <= kImgBytes - kImgW4, "forward B operands (W_l)");
+static_assert(span_mnmajor(64, 64, 1024) <= kImgW2 - kImgW1 && span_mnmajor(64, 16, 1024) <= kImgBytes - kImgW4,
+              "backward B operands (W_l^T)");
+static_assert(span_mnmajor(64, 128, 1024) <= 16384 && span_mnmajor(16, 128, 256) <= 4096 &&
+                  span_mnmajor(96, 128, 1536) <= 24576 && span_kmajor(16, 128, 2048) <= 4096,
+              "weight- and bias-gradient operands (H_l, dZ_l, dZ5, X, ones)");
 
 // One CTA's gradient row: the kNP parameter gradients (oracle layout), then
 // the loss, padded to whole float4.
@@ -275,311 +330,423 @@ __device__ __forceinline__ void store16(float* dst, const float* v) {   // dst 1
   d[3] = make_float4(v[12], v[13], v[14], v[15]);
 }
 
-// Lane of row m of an M = 64 accumulator: 16 rows in each 32-lane quarter.
-__device__ __forceinline__ int m64_row_of_lane(int lane) { return (lane & 31) < 16 ? (lane >> 5) * 16 + (lane & 31) : -1; }
-
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// The constant columns of a [128][width] activation tile: ones at column
-// `col`, zeros up to the width (chunks from col / 8 on).
-__device__ __forceinline__ void fill_ones(uint8_t* tile, int width, int col) {
-  for (int i = threadIdx.x; i < 128 * (width - col) / 8; i += blockDim.x) {
-    const int r = i / ((width - col) / 8), c = col / 8 + i % ((width - col) / 8);
-    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (c == col / 8) v[0] = 1.f;
-    store_chunk(tile, r, c, width, v);
+// Waits for an mbarrier phase; gives up at ~2^20 polls or once another
+// thread of the CTA has raised the abort flag.
+__device__ __forceinline__ bool train_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+  for (int i = 0; i < (1 << 20); ++i) {
+    if (tc::mbar_try_wait(mbar, parity)) return true;
+    if ((i & 31) == 31) {
+      if (*abort_flag) return false;
+      if (i > 4096) __nanosleep(32);
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Shared-memory addresses of one slot's tiles.
+struct TrainSlot {
+  uint32_t x, h[5], z5;   // h[1..4]
+};
+
+// The MMAs of one stage of one slot (issued by one thread): stages 0..4
+// are the forward layers, 5..9 the backward layers 4..0.  `first` starts
+// the gradient accumulators (the CTA's first tile).
+__device__ __noinline__ void train_issue(uint32_t tmem, const uint32_t* w, uint32_t ones, const TrainSlot& t,
+                                            int s, int stage, bool first) {
+  const uint32_t acc = tmem + kTcAcc + 64u * s;
+  const uint32_t ac = first ? 0u : 1u;
+  if (stage == 0) {
+    tc::gemm_kk(acc, t.x, 1536u, w[0], 1536u, 96, tc::idesc_bf16_f32(128, 64), false);
+  } else if (stage < 4) {
+    tc::gemm_kk(acc, t.h[stage], 1024u, w[stage], 1024u, 64, tc::idesc_bf16_f32(128, 64), false);
+  } else if (stage == 4) {
+    tc::gemm_kk(acc, t.h[4], 1024u, w[4], 1024u, 64, tc::idesc_bf16_f32(128, 16), false);
+  } else if (stage == 5) {
+    // dW4^T [64 in][16 out] += H4^T dZ5 (both MN-major over the batch)
+    tc::gemm_mn(tmem + kTcDW4, t.h[4], 1024u, t.z5, 256u, 128, tc::idesc_bf16_f32_mn(64, 16), !first);
+    // dH4 = dZ5 W4: A = dZ5 (K-major, K = 16), B = W4 read as W4^T (MN-major)
+    tc::mma(acc, tc::smem_desc(t.z5, 128u, 256u), tc::smem_desc(w[4], 1024u, 128u), tc::idesc_bf16_f32_bmn(128, 64),
+            0u);
+  } else {
+    const int l = 9 - stage;   // 3, 2, 1, 0
+    const uint32_t dz = t.h[l + 1];
+    // dW_l [out][in] += dZ_{l+1}^T H_l, and dB_l += dZ_{l+1}^T 1
+    if (l == 0)
+      tc::gemm_mn(tmem + kTcDW0, dz, 1024u, t.x, 1536u, 128, tc::idesc_bf16_f32_mn(64, 96), !first);
+    else
+      tc::gemm_mn(tmem + tc_dw(l), dz, 1024u, t.h[l], 1024u, 128, tc::idesc_bf16_f32_mn(64, 64), !first);
+    for (int j = 0; j < 8; ++j)
+      tc::mma(tmem + kTcDB + 16u * l, tc::smem_desc(dz + 2048u * j, 1024u, 128u),
+              tc::smem_desc(ones + 256u * j, 128u, 2048u), tc::idesc_bf16_f32_amn(64, 16), (ac || j > 0) ? 1u : 0u);
+    // dH_l = dZ_{l+1} W_l: A = dZ (K-major), B = W_l read as W_l^T (MN-major)
+    if (l > 0)
+      for (int j = 0; j < 4; ++j)
+        tc::mma(acc, tc::smem_desc(dz + 256u * j, 128u, 1024u), tc::smem_desc(w[l] + 2048u * j, 1024u, 128u),
+                tc::idesc_bf16_f32_bmn(128, 64), j > 0 ? 1u : 0u);
   }
 }
 
-__global__ void __launch_bounds__(kTrainThreads, 1) k_nrc_train(NrcDevice nd, const float4* __restrict__ recs,
-                                                                const float* __restrict__ targets,
-                                                                const unsigned* __restrict__ count, unsigned cap,
-                                                                float* __restrict__ gpart, unsigned* status) {
+// A training sample's inputs: position, normal and direction, and its target.
+__device__ __forceinline__ void train_fetch(const float4* __restrict__ recs, const float* __restrict__ pnv,
+                                            const float* __restrict__ targets, unsigned row, bool valid, float* q,
+                                            float* t3) {
+  if (!valid) return;
+  int slot;
+  if (pnv) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) q[j] = pnv[9 * (size_t)row + j];
+    slot = (int)row;
+  } else {
+    const float4 a = recs[3 * (size_t)row], b = recs[3 * (size_t)row + 1], c = recs[3 * (size_t)row + 2];
+    q[0] = a.x, q[1] = a.y, q[2] = a.z, q[3] = b.x, q[4] = b.y, q[5] = b.z, q[6] = c.x, q[7] = c.y, q[8] = c.z;
+    slot = __float_as_int(a.w);
+  }
+  t3[0] = targets[3 * (size_t)slot];
+  t3[1] = targets[3 * (size_t)slot + 1];
+  t3[2] = targets[3 * (size_t)slot + 2];
+}
+
+__global__ void __launch_bounds__(kTrainThreads, 1)
+    k_nrc_train(NrcDevice nd, const float4* __restrict__ recs, const float* __restrict__ pnv,
+                const float* __restrict__ targets, const unsigned* __restrict__ count, unsigned cap,
+                float* __restrict__ gpart, unsigned* status) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint64_t* mbar = (uint64_t*)(sm + kTsMisc);
-  uint32_t* tslot = (uint32_t*)(sm + kTsMisc + 8);
-  float* s_loss = (float*)(sm + kTsMisc + 16);   // [4]
-  float* bias = (float*)(sm + kTsBias);
-  float* db4 = (float*)(sm + kTsDB);              // [warp][4]
-  int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t full0 = tc::smem_u32(sm + kTsMisc), ready0 = full0 + 16, wbar = full0 + 32;
+  uint32_t* tslot = (uint32_t*)(sm + kTsMisc + 40);
+  volatile int* abort_flag = (volatile int*)(sm + kTsMisc + 44);
+  float* s_loss = (float*)(sm + kTsMisc + 48);   // [8 warps]
+  float* db4 = (float*)(sm + kTsMisc + 80);      // [8 warps][4]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc::alloc(tc::smem_u32(tslot), kTrainTmemCols);
-  const uint16_t* pw = (const uint16_t*)nd.packed;
-  load_tile(sm + kTsW0, pw + kPW0, 64, 96);
-  load_tile(sm + kTsW1, pw + kPW1, 64, 64);
-  load_tile(sm + kTsW2, pw + kPW2, 64, 64);
-  load_tile(sm + kTsW3, pw + kPW3, 64, 64);
-  load_tile(sm + kTsW4, pw + kPW4, 16, 64);
-  load_tile(sm + kTsT1, pw + kPT1, 64, 64);
-  load_tile(sm + kTsT2, pw + kPT2, 64, 64);
-  load_tile(sm + kTsT3, pw + kPT3, 64, 64);
-  load_tile(sm + kTsT4, pw + kPT4, 64, 16);
-  fill_ones(sm + kTsX, kXW, 96);
-  for (int l = 0; l < 4; ++l) fill_ones(sm + kTsH + l * 128 * kHW * 2, kHW, 64);
-  const float* gb = (const float*)(pw + kPackedBf16);
-  for (int i = tid; i < kPackedBias; i += blockDim.x) bias[i] = gb[i];
-  if (tid < 16) db4[tid] = 0.f;
-  if (tid == 0) {
-    tc::mbar_init(tc::smem_u32(mbar), 1);
-    *s_loss = 0.f;
+  if (tid == 32) {
+    for (int s = 0; s < 2; ++s) {
+      tc::mbar_init(full0 + 8 * s, 1);
+      tc::mbar_init(ready0 + 8 * s, 128);
+    }
+    tc::mbar_init(wbar, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+    // the forward weights' shared-memory image: one bulk copy
+    tc::mbar_expect_tx(wbar, kImgBytes);
+    tc::bulk_g2s(tc::smem_u32(sm), nd.packed, kImgBytes, wbar);
+  }
+  {
+    // the ones tile (BF16 1.0 everywhere) and the per-warp sums
+    uint4* o = (uint4*)(sm + kTsOnes);
+    for (int i = tid; i < 4096 / 16; i += blockDim.x) o[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    if (tid < 32) db4[tid] = 0.f;
+    if (tid < 8) s_loss[tid] = 0.f;
   }
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  uint32_t tmem = *tslot;
-  uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-  uint32_t mb = tc::smem_u32(mbar);
-  const uint32_t sW[5] = {tc::smem_u32(sm + kTsW0), tc::smem_u32(sm + kTsW1), tc::smem_u32(sm + kTsW2),
-                          tc::smem_u32(sm + kTsW3), tc::smem_u32(sm + kTsW4)};
-  const uint32_t sT[5] = {0u, tc::smem_u32(sm + kTsT1), tc::smem_u32(sm + kTsT2), tc::smem_u32(sm + kTsT3),
-                          tc::smem_u32(sm + kTsT4)};
-  // the activation entering layer l: X, then H1..H4, and its tile width
-  uint32_t sAct[5];
-  sAct[0] = tc::smem_u32(sm + kTsX);
-  for (int l = 1; l <= 4; ++l) sAct[l] = tc::smem_u32(sm + kTsH + (l - 1) * 128 * kHW * 2);
-  const uint32_t sDZ = tc::smem_u32(sm + kTsDZ);
-  unsigned n = min(*count, cap);
-  unsigned tiles = (n + 127) / 128;
-  float inv_n3 = n > 0 ? 1.0f / (3.0f * (float)n) : 0.f;
-  uint32_t phase = 0;
-  bool first = true;
-  float loss_acc = 0.f;
+  const bool w_ok = !__syncthreads_or(!tc::mbar_wait(wbar, 0));
+  if (!w_ok && tid == 0) atomicOr(status, kErrNrcTimeout);
+  const uint32_t tmem = *tslot;
+  const unsigned n = count ? min(*count, cap) : cap;
+  const unsigned tiles = w_ok ? (n + 127) / 128 : 0u;
+  const float* gbias = (const float*)((const uint8_t*)nd.packed + kImgBytes);
   bool aborted = false;
-  float lo[3] = {nd.lo[0], nd.lo[1], nd.lo[2]}, ie[3] = {nd.inv_ext[0], nd.inv_ext[1], nd.inv_ext[2]};
 
-#define RTB_WAIT()                                   \
-  {                                                  \
-    bool ok_ = tc::mbar_wait(mb, phase);             \
-    phase ^= 1;                                      \
-    if (__syncthreads_or(!ok_)) {                    \
-      if (tid == 0) atomicOr(status, kErrNrcTimeout); \
-      aborted = true;                                \
-      goto done;                                     \
-    }                                                \
-    tc::fence_after_sync();                          \
-  }
-
-  for (unsigned tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    unsigned row = tile * 128 + tid;
-    bool valid = row < n;
-    uint32_t mask[4][2];   // ReLU masks of the 4 hidden layers (64 bits each)
-    float tr = 0.f, tg = 0.f, tb = 0.f;
-    {
-      float f[96];
-      if (valid) {
-        float4 q0 = recs[3 * (size_t)row], q1 = recs[3 * (size_t)row + 1], q2 = recs[3 * (size_t)row + 2];
-        float pnv[9] = {q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z};
-        encode81(pnv, lo, ie, f);
-        int slot = __float_as_int(q0.w);
-        tr = targets[3 * (size_t)slot];
-        tg = targets[3 * (size_t)slot + 1];
-        tb = targets[3 * (size_t)slot + 2];
-      } else {
-#pragma unroll
-        for (int k = 0; k < 96; ++k) f[k] = 0.f;
+  if (warp == 8) {
+    // ---- the MMA issuer: stage by stage, slot 0 then slot 1 ----
+    if (lane == 0 && tiles > 0) {
+      const uint32_t w[5] = {tc::smem_u32(sm + kImgW0), tc::smem_u32(sm + kImgW1), tc::smem_u32(sm + kImgW2),
+                             tc::smem_u32(sm + kImgW3), tc::smem_u32(sm + kImgW4)};
+      TrainSlot ts[2];
+      for (int s = 0; s < 2; ++s) {
+        const uint32_t b = tc::smem_u32(sm + kTsSlot0 + s * kTsSlotBytes);
+        ts[s].x = b + kTsX;
+        ts[s].h[0] = 0u;
+        for (int l = 1; l <= 4; ++l) ts[s].h[l] = b + kTsH + 16384u * (l - 1);
+        ts[s].z5 = b + kTsZ5;
       }
-#pragma unroll
-      for (int c = 0; c < 12; ++c) store_chunk(sm + kTsX, tid, c, kXW, f + 8 * c);
+      const uint32_t ones = tc::smem_u32(sm + kTsOnes);
+      uint32_t rph[2] = {0u, 0u};
+      for (unsigned k = 0; !aborted && blockIdx.x + k * gridDim.x < tiles; k += 2) {
+        const bool has1 = blockIdx.x + (k + 1) * gridDim.x < tiles;
+        for (int stage = 0; stage < 10 && !aborted; ++stage)
+          for (int s = 0; s < (has1 ? 2 : 1); ++s) {
+            if (!train_wait(ready0 + 8 * s, rph[s], abort_flag)) {
+              aborted = true;
+              break;
+            }
+            rph[s] ^= 1u;
+            tc::fence_after_sync();
+            train_issue(tmem, w, ones, ts[s], s, stage, k == 0 && s == 0);
+            tc::commit(full0 + 8 * s);
+          }
+      }
+      if (aborted) {
+        *abort_flag = 1;
+        atomicOr(status, kErrNrcTimeout);
+      }
     }
-    tc::fence_proxy_async();
-    __syncthreads();
-    // forward: Z_{l+1} = Act_l W_l^T (A = the activation tile, K-major)
-    float o[16];
-    for (int l = 0; l < 5; ++l) {
-      int N = l < 4 ? 64 : 16;
-      if (tid == 0) {
-        tc::fence_after_sync();
-        const uint32_t sbo_a = (uint32_t)((l == 0 ? kXW : kHW) / 8) * 128u;
-        const uint32_t sbo_b = (uint32_t)(d_in(l) / 8) * 128u;
-        tc::gemm_kk(tmem + kTcAcc, sAct[l], sbo_a, sW[l], sbo_b, d_in(l), tc::idesc_bf16_f32(128, N), false);
-        tc::commit(mb);
+    __syncwarp();
+  } else {
+    // ---- the epilogues of slot s ----
+    const int s = warp >> 2, t = tid & 127, wq = warp & 3;
+    const uint32_t full = full0 + 8 * s, ready = ready0 + 8 * s;
+    const uint32_t acc = tmem + ((uint32_t)(wq * 32) << 16) + kTcAcc + 64u * s;   // this warp's lane quarter
+    uint8_t* slot = sm + kTsSlot0 + s * kTsSlotBytes;
+    const float lo[3] = {nd.lo[0], nd.lo[1], nd.lo[2]}, ie[3] = {nd.inv_ext[0], nd.inv_ext[1], nd.inv_ext[2]};
+    uint32_t fph = 0u;
+    float loss_acc = 0.f;
+    float q[9] = {}, tq[3] = {};
+    unsigned tile = blockIdx.x + (unsigned)s * gridDim.x;
+    train_fetch(recs, pnv, targets, tile * 128 + t, tile < tiles && tile * 128 + t < n, q, tq);
+    for (; tile < tiles; tile += 2 * gridDim.x) {
+      const unsigned row = tile * 128 + t;
+      const bool valid = row < n;
+      const float tr = tq[0], tg = tq[1], tb = tq[2];
+      encode_store(q, lo, ie, valid, slot + kTsX, t);
+      // the next tile of this slot: its inputs load while this one runs
+      {
+        const unsigned nt = tile + 2 * gridDim.x;
+        train_fetch(recs, pnv, targets, nt * 128 + t, nt < tiles && nt * 128 + t < n, q, tq);
       }
-      RTB_WAIT();
-      if (l < 4) {
-        float h[64];
+      tc::fence_proxy_async();
+      mbar_arrive(ready);
+      // forward epilogues: H_{l+1} = relu(Z_{l+1} + b_l), its ReLU mask kept
+      uint32_t mask[4][2];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tc::ld16(lane_addr + kTcAcc + 16 * c, h + 16 * c);
-        mask[l][0] = mask[l][1] = 0u;
+      for (int l = 0; l < 4; ++l) {
+        if (!train_wait(full, fph, abort_flag)) aborted = true;
+        fph ^= 1u;
+        tc::fence_after_sync();
+        uint8_t* hl = slot + kTsH + 16384 * l;
 #pragma unroll
-        for (int k = 0; k < 64; ++k) {
-          float z = h[k] + bias[64 * l + k];
-          bool pos = valid && z > 0.f;
-          mask[l][k >> 5] |= (pos ? 1u : 0u) << (k & 31);
-          h[k] = pos ? z : 0.f;
+        for (int half = 0; half < 2; ++half) {
+          float h[32];
+          tc::ld32(acc + 32 * half, h);
+          const float4* b4 = (const float4*)(gbias + 64 * l + 32 * half);
+          uint32_t mk = 0u;
+#pragma unroll
+          for (int k4 = 0; k4 < 8; ++k4) {
+            const float4 b = __ldg(b4 + k4);
+            const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int k = 4 * k4 + e;
+              const float z = h[k] + bb[e];
+              const bool pos = valid && z > 0.f;
+              mk |= (pos ? 1u : 0u) << k;
+              h[k] = pos ? z : 0.f;
+            }
+          }
+          // kept as an opaque word: otherwise the compiler carries the 64 ReLU
+          // predicates of every layer to the backward pass in registers
+          asm volatile("mov.b32 %0, %1;" : "=r"(mask[l][half]) : "r"(mk));
+#pragma unroll
+          for (int c = 0; c < 4; ++c) store_chunk(hl, t, 4 * half + c, 64, h + 8 * c);
         }
-        uint8_t* hl = sm + kTsH + l * 128 * kHW * 2;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) store_chunk(hl, tid, c, kHW, h + 8 * c);
         tc::fence_before_sync();
         tc::fence_proxy_async();
-        __syncthreads();
-      } else {
-        tc::ld16(lane_addr + kTcAcc, o);
-        tc::fence_before_sync();
+        mbar_arrive(ready);
       }
-    }
-    // loss gradient at the exp output: dL/dz5 = 2 (y - t) / (y^2 + 0.01) / (3n) * y,
-    // stored in BF16; the output bias gradient sums the stored values
-    {
-      float g[16];
+      // loss gradient at the exp output: dL/dz5 = 2 (y - t) / (y^2 + 0.01) / (3n) * y,
+      // stored in BF16; the output bias gradient sums the stored values
+      {
+        if (!train_wait(full, fph, abort_flag)) aborted = true;
+        fph ^= 1u;
+        tc::fence_after_sync();
+        float o[16];
+        tc::ld16(acc, o);
+        tc::fence_before_sync();
+        const float inv_n3 = 1.0f / (3.0f * (float)n);
+        float g[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) g[k] = 0.f;
-      if (valid) {
-        float t3[3] = {tr, tg, tb};
+        for (int k = 0; k < 16; ++k) g[k] = 0.f;
+        if (valid) {
+          const float t3[3] = {tr, tg, tb};
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float y = expf(o[c] + __ldg(gbias + 256 + c));
+            const float den = y * y + 0.01f;
+            const float dy = y - t3[c];
+            loss_acc += dy * dy / den * inv_n3;
+            g[c] = 2.f * dy / den * inv_n3 * y;
+          }
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          float y = expf(o[c] + bias[256 + c]);
-          float den = y * y + 0.01f;
-          float dy = y - t3[c];
-          loss_acc += dy * dy / den * inv_n3;
-          g[c] = 2.f * dy / den * inv_n3 * y;
+          const float sum = warp_sum(bf16_float(bf16_bits(g[c])));
+          if (lane == 0) db4[4 * warp + c] += sum;
         }
+        store_chunk(slot + kTsZ5, t, 0, 16, g);
+        store_chunk(slot + kTsZ5, t, 1, 16, g + 8);
+        tc::fence_proxy_async();
+        mbar_arrive(ready);
       }
+      // backward epilogues: dZ_l = dH_l * relu'(z_l), stored over H_l
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float s = warp_sum(bf16_float(bf16_bits(g[c])));
-        if (lane == 0) db4[4 * warp + c] += s;
-      }
-      store_chunk(sm + kTsDZ, tid, 0, 16, g);
-      store_chunk(sm + kTsDZ, tid, 1, 16, g + 8);
-      tc::fence_proxy_async();
-      __syncthreads();
-    }
-    // backward: layer 4 -> 0.  dW_l | dB_l [M = out][N = in + ones] += dZ^T Act_l,
-    // both operands MN-major over the batch; dAct_l = dZ W_l (K-major)
-    for (int l = 4; l >= 0; --l) {
-      if (tid == 0) {
+      for (int l = 4; l >= 1; --l) {
+        if (!train_wait(full, fph, abort_flag)) aborted = true;
+        fph ^= 1u;
         tc::fence_after_sync();
-        if (l == 4) {
-          // dW4^T [64 in][16 out] += H4^T dZ5: A = H4 (M = in), B = dZ5 (N = out)
-          tc::gemm_mn(tmem + kTcDW4, sAct[4], (uint32_t)(kHW / 8) * 128u, sDZ, 2u * 128u, 128,
-                      tc::idesc_bf16_f32_mn(64, 16), !first);
-          // dH4 = dZ5 W4 (A: dZ5 [128][16], B: W4^T [64][16])
-          tc::gemm(tmem + kTcAcc, sDZ, sT[4], 16, tc::idesc_bf16_f32(128, 64), false);
-        } else {
-          // dW_l | dB_l += dZ^T [Act_l | 1]: A = dZ (M = out), B = Act_l (N = in + ones)
-          const uint32_t col = l == 0 ? kTcDW0 : kTcDW1 + 80 * (l - 1);
-          const int width = l == 0 ? kXW : kHW;
-          tc::gemm_mn(tmem + col, sDZ, 8u * 128u, sAct[l], (uint32_t)(width / 8) * 128u, 128,
-                      tc::idesc_bf16_f32_mn(64, width), !first);
-          if (l > 0) tc::gemm(tmem + kTcAcc, sDZ, sT[l], 64, tc::idesc_bf16_f32(128, 64), false);
+        uint8_t* hl = slot + kTsH + 16384 * (l - 1);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float g[32];
+          tc::ld32(acc + 32 * half, g);
+          const uint32_t mk = mask[l - 1][half];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) g[k] = ((mk >> k) & 1u) ? g[k] : 0.f;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) store_chunk(hl, t, 4 * half + c, 64, g + 8 * c);
         }
-        tc::commit(mb);
+        tc::fence_before_sync();
+        tc::fence_proxy_async();
+        mbar_arrive(ready);
       }
-      RTB_WAIT();
-      if (l == 0) break;
-      // dZ_l = dH_l * relu'(z_l), stored in BF16 for both of its MMAs
-      float g[64];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) tc::ld16(lane_addr + kTcAcc + 16 * c, g + 16 * c);
-#pragma unroll
-      for (int k = 0; k < 64; ++k) g[k] = ((mask[l - 1][k >> 5] >> (k & 31)) & 1u) ? g[k] : 0.f;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) store_chunk(sm + kTsDZ, tid, c, 64, g + 8 * c);
-      tc::fence_before_sync();
-      tc::fence_proxy_async();
-      __syncthreads();
+      // the tile's last MMAs (dW0, dB0) read X and dZ1: done before the next tile overwrites them
+      if (!train_wait(full, fph, abort_flag)) aborted = true;
+      fph ^= 1u;
+      tc::fence_after_sync();
+      if (aborted) break;
     }
-    tc::fence_before_sync();
-    __syncthreads();
-    first = false;
+    if (aborted) {
+      *abort_flag = 1;
+      atomicOr(status, kErrNrcTimeout);
+    }
+    const float ls = warp_sum(loss_acc);
+    if (lane == 0) s_loss[warp] = ls;
   }
-done:
+  tc::fence_before_sync();
+  aborted = __syncthreads_or(aborted) != 0;
+  tc::fence_after_sync();
+
   // this CTA's gradients and loss: its own row of gpart (plain stores; the
   // Adam kernel sums the rows in a fixed order).  A CTA without a tile, or
   // one whose wait timed out, writes zeros.
   float* gp = gpart + (size_t)blockIdx.x * kGPRow;
-  const bool have = !aborted && !first;
-  if (have) {
-    tc::fence_after_sync();
-    int m = m64_row_of_lane(tid);
-    float v[16];
-    // dW0 | dB0 (M = 64 x N = 104): columns 0..95 the weights, 96 the bias
-    for (int c = 0; c < 7; ++c) {
-      tc::ld16(lane_addr + kTcDW0 + 16 * c, v);
-      if (m >= 0) {
-        if (c < 6) store16(gp + off_w(0) + m * 96 + 16 * c, v);
-        else gp[off_b(0) + m] = v[0];
-      }
-    }
-    for (int l = 1; l <= 3; ++l)
-      for (int c = 0; c < 5; ++c) {
-        tc::ld16(lane_addr + kTcDW1 + 80 * (l - 1) + 16 * c, v);
-        if (m >= 0) {
-          if (c < 4) store16(gp + off_w(l) + m * 64 + 16 * c, v);
-          else gp[off_b(l) + m] = v[0];
+  const bool have = !aborted && tiles > blockIdx.x;
+  if (have && warp < 8) {
+    // accumulator row m of an M = 64 MMA: lane (m / 16) * 32 + m % 16
+    const int wq = warp & 3, m = wq * 16 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(wq * 32) << 16);
+    const bool mine = lane < 16;
+    float v[32];
+    if (warp < 4) {
+      for (int c = 0; c < 3; ++c) {   // dW0: 96 columns
+        tc::ld32(lane_base + kTcDW0 + 32 * c, v);
+        if (mine) {
+          store16(gp + off_w(0) + m * 96 + 32 * c, v);
+          store16(gp + off_w(0) + m * 96 + 32 * c + 16, v + 16);
         }
       }
-    // dW4^T [64 in][16 out] -> dW4 [3][64]
-    tc::ld16(lane_addr + kTcDW4, v);
-    if (m >= 0)
-      for (int k = 0; k < 3; ++k) gp[off_w(4) + k * 64 + m] = v[k];
-  } else {
+      for (int c = 0; c < 2; ++c) {   // dW1
+        tc::ld32(lane_base + tc_dw(1) + 32 * c, v);
+        if (mine) {
+          store16(gp + off_w(1) + m * 64 + 32 * c, v);
+          store16(gp + off_w(1) + m * 64 + 32 * c + 16, v + 16);
+        }
+      }
+      tc::ld16(lane_base + kTcDB, v);
+      if (mine) gp[off_b(0) + m] = v[0];
+      tc::ld16(lane_base + kTcDB + 16, v);
+      if (mine) gp[off_b(1) + m] = v[0];
+    } else {
+      for (int l = 2; l <= 3; ++l)
+        for (int c = 0; c < 2; ++c) {
+          tc::ld32(lane_base + tc_dw(l) + 32 * c, v);
+          if (mine) {
+            store16(gp + off_w(l) + m * 64 + 32 * c, v);
+            store16(gp + off_w(l) + m * 64 + 32 * c + 16, v + 16);
+          }
+        }
+      tc::ld16(lane_base + kTcDB + 32, v);
+      if (mine) gp[off_b(2) + m] = v[0];
+      tc::ld16(lane_base + kTcDB + 48, v);
+      if (mine) gp[off_b(3) + m] = v[0];
+      // dW4^T [64 in][16 out] -> dW4 [3][64]
+      tc::ld16(lane_base + kTcDW4, v);
+      if (mine)
+        for (int k = 0; k < 3; ++k) gp[off_w(4) + k * 64 + m] = v[k];
+    }
+  } else if (!have) {
     for (int i = tid; i < kNW + 4 * 64; i += blockDim.x) gp[i] = 0.f;
   }
   // the output bias gradients and the losses of the warps, summed in warp order (deterministic)
-  if (tid < 3) gp[off_b(4) + tid] = have ? ((db4[tid] + db4[4 + tid]) + db4[8 + tid]) + db4[12 + tid] : 0.f;
-  {
-    float ls = warp_sum(loss_acc);
-    if (lane == 0) s_loss[warp] = ls;
-    __syncthreads();
-    if (tid == 0) gp[kNP] = have ? ((s_loss[0] + s_loss[1]) + s_loss[2]) + s_loss[3] : 0.f;
+  if (tid < 3) {
+    float b = 0.f;
+    for (int w8 = 0; w8 < 8; ++w8) b += db4[4 * w8 + tid];
+    gp[off_b(4) + tid] = have ? b : 0.f;
+  }
+  if (tid == 0) {
+    float l8 = 0.f;
+    for (int w8 = 0; w8 < 8; ++w8) l8 += s_loss[w8];
+    gp[kNP] = have ? l8 : 0.f;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   if (warp == 0) tc::dealloc(tmem, kTrainTmemCols);
-#undef RTB_WAIT
 }
 
 // ---------------------------------------------------------------------------
-// Adam on the FP32 master parameters, then the BF16 copies; clears the
-// gradient for the next step.
+// Adam on the FP32 master parameters; each updated parameter also goes to
+// its place in the packed BF16 image (or the FP32 biases).
 // ---------------------------------------------------------------------------
-// The gradient (and, at kNP, the loss) is the sum of the training CTAs'
-// rows, in CTA order; it stays in g for inspection.
-__global__ void k_nrc_adam(float* __restrict__ w, const float* __restrict__ gpart, int n_part, float* __restrict__ g,
-                           float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2, float eps,
-                           float c1, float c2, int apply) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > kNP) return;
-  float gi = 0.f;
-  for (int c = 0; c < n_part; ++c) gi += gpart[(size_t)c * kGPRow + i];
-  g[i] = gi;
-  if (i < kNP && apply) {
-    float mi = b1 * m[i] + (1.f - b1) * gi;
-    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+// Writes parameter i (oracle layout) into the packed copy.
+__device__ __forceinline__ void pack_param(uint8_t* __restrict__ packed, int i, float x) {
+  if (i < kNW) {
+    const int l = i < off_w(1) ? 0 : min(1 + (i - off_w(1)) / 4096, 4);
+    const int rel = i - off_w(l), o = rel / d_in(l), c = rel % d_in(l);
+    *(uint16_t*)(packed + img_off(l) + tc::core_off(o, c, d_in(l))) = bf16_bits(x);
+  } else {
+    ((float*)(packed + kImgBytes))[i - kNW] = x;   // b0..b3 (64 each), then b4 (3)
   }
 }
 
-__global__ void k_nrc_pack(const float* __restrict__ w, uint16_t* __restrict__ packed) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float* pb = (float*)(packed + kPackedBf16);
-  if (i < kPackedBf16) {
-    float x = 0.f;
-    if (i < kPW4) {   // W0..W3 [out][in]
-      x = w[i];
-    } else if (i < kPT1) {   // W4 padded to 16 rows
-      int r = (i - kPW4) / 64, c = (i - kPW4) % 64;
-      x = r < 3 ? w[off_w(4) + r * 64 + c] : 0.f;
-    } else if (i < kPT4) {   // W1^T .. W3^T [in][out]
-      int l = 1 + (i - kPT1) / 4096, j = (i - kPT1) % 4096;
-      int in = j / 64, out = j % 64;
-      x = w[off_w(l) + out * 64 + in];
-    } else {   // W4^T [64 in][16 out]
-      int in = (i - kPT4) / 16, out = (i - kPT4) % 16;
-      x = out < 3 ? w[off_w(4) + out * 64 + in] : 0.f;
-    }
-    packed[i] = bf16_bits(x);
-  } else if (i < kPackedBf16 + kPackedBias) {
-    int j = i - kPackedBf16;
-    pb[j] = j < 256 ? w[kNW + j] : (j < 259 ? w[kNW + j] : 0.f);
+// Every parameter into a zeroed packed copy (creation, loading).
+__global__ void k_nrc_pack(const float* __restrict__ w, uint8_t* __restrict__ packed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kNP) pack_param(packed, i, w[i]);
+}
+
+// The gradient (and, at kNP, the loss) is the sum of the training CTAs'
+// rows; it stays in g for inspection.  A block takes 32 parameters and
+// its 8 warps every 8th row each; the partial sums are added in warp
+// order, so the sum does not depend on timing.
+constexpr int kAdamParams = 32;
+__global__ void __launch_bounds__(256) k_nrc_adam(float* __restrict__ w, const float* __restrict__ gpart, int n_part,
+                                                  float* __restrict__ g, float* __restrict__ m,
+                                                  float* __restrict__ v, float lr, float b1, float b2, float eps,
+                                                  float c1, float c2, int apply, uint8_t* __restrict__ packed) {
+  __shared__ float part[8][kAdamParams];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int i = blockIdx.x * kAdamParams + lane;
+  float s = 0.f;
+  if (i <= kNP) {
+#pragma unroll 4
+    for (int c = grp; c < n_part; c += 8) s += gpart[(size_t)c * kGPRow + i];
+  }
+  part[grp][lane] = s;
+  __syncthreads();
+  if (grp != 0 || i > kNP) return;
+  float gi = part[0][lane];
+#pragma unroll
+  for (int r = 1; r < 8; ++r) gi += part[r][lane];
+  g[i] = gi;
+  if (i < kNP && apply) {
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    pack_param(packed, i, wi);
   }
 }
 
@@ -642,8 +809,9 @@ static rt_status nrc_setup_kernels() {
 }
 
 static rt_status nrc_pack(rt_nrc* r, cudaStream_t st) {
-  int n = kPackedBf16 + kPackedBias;
-  k_nrc_pack<<<(n + 255) / 256, 256, 0, st>>>((const float*)r->params.p, (uint16_t*)r->packed.p);
+  cudaError_t e = cudaMemsetAsync(r->packed.p, 0, kPackedBytes, st);
+  if (e != cudaSuccess) return cuda_error(e, "nrc pack");
+  k_nrc_pack<<<(kNP + 255) / 256, 256, 0, st>>>((const float*)r->params.p, (uint8_t*)r->packed.p);
   return cuda_error(cudaGetLastError(), "nrc pack");
 }
 
@@ -657,19 +825,17 @@ rt_status nrc_infer_launch(rt_nrc* r, const float4* recs, const unsigned* count,
 }
 
 rt_status nrc_train_launch(rt_nrc* r, const float4* recs, const float* targets, const unsigned* count, unsigned cap,
-                           unsigned* status, cudaStream_t st) {
+                           unsigned* status, cudaStream_t st, const float* pnv) {
   rt_status rs = nrc_setup_kernels();
   if (rs) return rs;
   if ((rs = ensure(r->gpart, (size_t)r->sm_count * kGPRow * sizeof(float)))) return rs;
-  k_nrc_train<<<r->sm_count, kTrainThreads, kTrainSmem, st>>>(r->nd, recs, targets, count, cap, (float*)r->gpart.p,
-                                                               status);
+  k_nrc_train<<<r->sm_count, kTrainThreads, kTrainSmem, st>>>(r->nd, recs, pnv, targets, count, cap,
+                                                               (float*)r->gpart.p, status);
   r->step++;
   float c1 = 1.f - powf(r->cfg.beta1, (float)r->step), c2 = 1.f - powf(r->cfg.beta2, (float)r->step);
-  k_nrc_adam<<<(kNP + 1 + 255) / 256, 256, 0, st>>>((float*)r->params.p, (const float*)r->gpart.p, r->sm_count,
-                                                     (float*)r->grad.p, (float*)r->m.p, (float*)r->v.p, r->cfg.lr,
-                                                     r->cfg.beta1, r->cfg.beta2, r->cfg.eps, c1, c2, 1);
-  rs = nrc_pack(r, st);
-  if (rs) return rs;
+  k_nrc_adam<<<(kNP + 1 + kAdamParams - 1) / kAdamParams, 256, 0, st>>>(
+      (float*)r->params.p, (const float*)r->gpart.p, r->sm_count, (float*)r->grad.p, (float*)r->m.p, (float*)r->v.p,
+      r->cfg.lr, r->cfg.beta1, r->cfg.beta2, r->cfg.eps, c1, c2, 1, (uint8_t*)r->packed.p);
   return cuda_error(cudaGetLastError(), "nrc train");
 }
 
@@ -917,14 +1083,7 @@ rt_status rt_nrc_train_step(rt_nrc* r, rt_scene* s, const float* pnv_dev, const 
                             void* stream) {
   if (!r || !s || n <= 0 || n > (1 << 26) || !pnv_dev || !target_dev)
     return set_error(RT_ERR_INVALID_ARG, "rt_nrc_train_step: bad argument");
-  cudaStream_t st = (cudaStream_t)stream;
-  rt_status rs;
-  if ((rs = ensure(r->train_q, (size_t)n * 48)) || (rs = ensure(r->counters, 64))) return rs;
-  cudaError_t e = cudaMemcpyAsync((unsigned*)r->counters.p + 1, &n, 4, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_error(e, "rt_nrc_train_step");
-  nrc_make_records(pnv_dev, target_dev, n, (float4*)r->train_q.p, 3, st);
-  return nrc_train_launch(r, (const float4*)r->train_q.p, target_dev, (const unsigned*)r->counters.p + 1,
-                          (unsigned)n, s->status, st);
+  return nrc_train_launch(r, nullptr, target_dev, nullptr, (unsigned)n, s->status, (cudaStream_t)stream, pnv_dev);
 }
 
 }  // extern "C"

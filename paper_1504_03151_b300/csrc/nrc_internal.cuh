@@ -16,7 +16,7 @@ constexpr unsigned kErrNrcTimeout = 8u;                // a tensor-core wait tim
 
 // What the cache kernels read, by value.
 struct NrcDevice {
-  const void* packed;     // BF16 weights (forward + transposed) then FP32 biases
+  const void* packed;     // BF16 forward weights (shared-memory image) then FP32 biases
   float* target;          // training targets of the current frame (3 per slot)
   float lo[3], inv_ext[3];
 };
@@ -25,8 +25,11 @@ struct NrcDevice {
 // fbs set, to fbs[frame] with the frame index in the record's last word).
 rt_status nrc_infer_launch(rt_nrc* r, const float4* recs, const unsigned* count, unsigned cap, float* fb, float* out3,
                            unsigned* status, cudaStream_t st, float* const* fbs = nullptr);
+// Training on `count` (at most cap; all cap when count is null) stride-3
+// records whose slot indexes targets, or, with pnv set, on the first cap
+// rows of pnv (n x 9) and targets (n x 3); then the Adam step.
 rt_status nrc_train_launch(rt_nrc* r, const float4* recs, const float* targets, const unsigned* count, unsigned cap,
-                           unsigned* status, cudaStream_t st);
+                           unsigned* status, cudaStream_t st, const float* pnv = nullptr);
 // Records from caller arrays: pnv n x 9 -> stride-4 (inference, weight 1)
 // or stride-3 (training, slot = index) float4 records.
 void nrc_make_records(const float* pnv, const float* targets, int64_t n, float4* recs, int stride, cudaStream_t st);

@@ -161,6 +161,42 @@ def test_nrc_gradients_and_adam_match_oracle():
     scene.close()
 
 
+def test_nrc_gradients_many_tiles_per_sm():
+    # More tiles than two per SM (the training kernel keeps two in flight on
+    # each SM and accumulates every tile of a CTA into one gradient row), a
+    # ragged last tile; the same step on two caches of one seed gives the
+    # same gradient bit for bit.
+    sc, scene = _scene()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 128 * (2 * sms + sms // 2) + 77
+    rng = np.random.default_rng(11)
+    pnv = _samples(sc, n, rng)
+    target = rng.uniform(0.05, 1.5, (n, 3)).astype(np.float32)
+    pd, td = torch.from_numpy(pnv).cuda(), torch.from_numpy(target).cuda()
+    grads = []
+    for _ in range(2):
+        nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=5))
+        p0 = rtb.rt_nrc_get_params(nrc)
+        rtb.rt_nrc_train_step(nrc, scene.handle, pd, td, n)
+        assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+        grads.append(rtb.rt_nrc_get_grads(nrc))
+        rtb.rt_nrc_destroy(nrc)
+    (g, loss), (g2, loss2) = grads
+    assert np.array_equal(g, g2) and loss == loss2
+    W, B = _split(p0)
+    ref_loss, dW, dB = O.mlp_loss_grad(_oracle_inputs(sc, pnv), target.astype(np.float64), W, B, bf16_acts=True)
+    assert loss == pytest.approx(ref_loss, rel=1e-2)
+    for off, rows, cols in LAYERS:
+        a = g[off:off + rows * cols].astype(np.float64)
+        b = dW[off:off + rows * cols]
+        assert _cos(a, b) >= 0.999, (off, _cos(a, b))
+        assert np.linalg.norm(a - b) <= 1e-2 * np.linalg.norm(b) + 1e-12, (off, np.linalg.norm(a - b), np.linalg.norm(b))
+    gb = g[O.N_W:].astype(np.float64)
+    assert _cos(gb, dB) >= 0.999
+    assert np.linalg.norm(gb - dB) <= 1e-2 * np.linalg.norm(dB)
+    scene.close()
+
+
 def test_nrc_training_reduces_loss():
     sc, scene = _scene()
     nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=9))
