@@ -16,9 +16,13 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "nrc_internal.cuh"
 #include "rtb_internal.cuh"
 #include "tc.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rtb {
 
@@ -256,6 +260,26 @@ done:
 }
 
 // ---------------------------------------------------------------------------
+// the packed copy
+// ---------------------------------------------------------------------------
+// Writes parameter i (oracle layout) into the packed copy.
+__device__ __forceinline__ void pack_param(uint8_t* __restrict__ packed, int i, float x) {
+  if (i < kNW) {
+    const int l = i < off_w(1) ? 0 : min(1 + (i - off_w(1)) / 4096, 4);
+    const int rel = i - off_w(l), o = rel / d_in(l), c = rel % d_in(l);
+    *(uint16_t*)(packed + img_off(l) + tc::core_off(o, c, d_in(l))) = bf16_bits(x);
+  } else {
+    ((float*)(packed + kImgBytes))[i - kNW] = x;   // b0..b3 (64 each), then b4 (3)
+  }
+}
+
+// Every parameter into a zeroed packed copy (creation, loading).
+__global__ void k_nrc_pack(const float* __restrict__ w, uint8_t* __restrict__ packed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kNP) pack_param(packed, i, w[i]);
+}
+
+// ---------------------------------------------------------------------------
 // training: forward (activations kept), loss gradient, backward; weight and
 // bias gradients accumulate in tensor memory over the CTA's tiles, then go
 // to its own row of the gradient buffer.  One CTA per SM (its 512
@@ -272,7 +296,8 @@ done:
 // MN-major operands, and the backward MMAs read the forward weight tiles as
 // MN-major W^T, so no transposed copy is made.  The backward signal dZ_l
 // is written over H_l once dW_l has been formed from H_l.  The bias
-// gradients are MMAs of dZ^T against a tile of ones.
+// gradients are MMAs of dZ^T against a block of ones (one K = 16 step's
+// operand, read again at every step).
 // ---------------------------------------------------------------------------
 constexpr int kTrainWarps = 9;   // two epilogue warpgroups, then the MMA warp
 constexpr int kTrainThreads = 32 * kTrainWarps;
@@ -285,9 +310,11 @@ constexpr int kTcDW4 = 416;    // 16: dW4^T (M = 64 in, N = 16 out)
 constexpr int kTcDB = 432;     // 16 each at 432 + 16 l: dB0..dB3 (M = 64 out; every column the same sum)
 static_assert(kTcDB + 4 * 16 <= kTrainTmemCols, "the training accumulators exceed the tensor memory");
 __host__ __device__ constexpr int tc_dw(int l) { return l == 0 ? kTcDW0 : kTcDW1 + 64 * (l - 1); }
-// shared memory (bytes): the weight image, a ones tile, control words, then two slots
-constexpr int kTsOnes = kImgBytes;         // [16][128] ones, K-major: 4 KB
-constexpr int kTsMisc = kTsOnes + 4096;    // mbarriers, tensor-memory slot, abort flag, per-warp sums
+// shared memory (bytes): the weight image and the FP32 biases (one bulk
+// copy of the packed buffer), a block of ones, control words, then two slots
+constexpr int kTsBias = kImgBytes;         // 272 floats
+constexpr int kTsOnes = kTsBias + kPackedBias * 4;   // [16][16] ones, K-major: 512 B
+constexpr int kTsMisc = kTsOnes + 512;     // mbarriers, tensor-memory slot, abort flag, per-warp sums
 constexpr int kTsSlot0 = kTsMisc + 256;
 constexpr int kTsX = 0;                    // within a slot: X [128][96]
 constexpr int kTsH = 24576;                // H1..H4 [128][64], 16 KB each (then dZ1..dZ4)
@@ -315,7 +342,7 @@ static_assert(span_kmajor(64, 96, 1536) <= kImgW1 - kImgW0 && span_kmajor(64, 64
 static_assert(span_mnmajor(64, 64, 1024) <= kImgW2 - kImgW1 && span_mnmajor(64, 16, 1024) <= kImgBytes - kImgW4,
               "backward B operands (W_l^T)");
 static_assert(span_mnmajor(64, 128, 1024) <= 16384 && span_mnmajor(16, 128, 256) <= 4096 &&
-                  span_mnmajor(96, 128, 1536) <= 24576 && span_kmajor(16, 128, 2048) <= 4096,
+                  span_mnmajor(96, 128, 1536) <= 24576 && span_kmajor(16, 16, 256) <= 512,
               "weight- and bias-gradient operands (H_l, dZ_l, dZ5, X, ones)");
 
 // One CTA's gradient row: the kNP parameter gradients (oracle layout), then
@@ -335,15 +362,13 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Waits for an mbarrier phase; gives up at ~2^20 polls or once another
+// Waits for an mbarrier phase; gives up after ~2^14 suspended polls or once another
 // thread of the CTA has raised the abort flag.
 __device__ __forceinline__ bool train_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
-  for (int i = 0; i < (1 << 20); ++i) {
-    if (tc::mbar_try_wait(mbar, parity)) return true;
-    if ((i & 31) == 31) {
-      if (*abort_flag) return false;
-      if (i > 4096) __nanosleep(32);
-    }
+  // each poll suspends the thread for up to ~1 us; 2^14 of them bound the wait
+  for (int i = 0; i < (1 << 14); ++i) {
+    if (tc::mbar_try_wait_hint(mbar, parity, 1000u)) return true;
+    if (*abort_flag) return false;
   }
   return false;
 }
@@ -352,46 +377,71 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
-// Shared-memory addresses of one slot's tiles.
-struct TrainSlot {
-  uint32_t x, h[5], z5;   // h[1..4]
-};
+// Issues NK back-to-back MMAs: step j reads A at a + j a_step and B at
+// b + j b_step (bytes; the descriptors' start-address fields advance by
+// step / 16, far from overflowing below 256 KB).
+template <int NK>
+__device__ __forceinline__ void mma_k(uint32_t d, uint64_t a, uint32_t a_step, uint64_t b, uint32_t b_step,
+                                      uint32_t idesc, bool accumulate) {
+#pragma unroll
+  for (int j = 0; j < NK; ++j)
+    tc::mma(d, a + (uint64_t)((a_step >> 4) * j), b + (uint64_t)((b_step >> 4) * j), idesc,
+            (accumulate || j > 0) ? 1u : 0u);
+}
+// K-major operand (8-row groups sbo apart) and MN-major operand (8-row K
+// groups k_pitch apart, 8-element chunks 128 B apart) descriptors.
+__device__ __forceinline__ uint64_t kdesc(uint32_t a, uint32_t sbo) { return tc::smem_desc(a, 128u, sbo); }
+__device__ __forceinline__ uint64_t mndesc(uint32_t a, uint32_t k_pitch) { return tc::smem_desc(a, k_pitch, 128u); }
 
-// The MMAs of one stage of one slot (issued by one thread): stages 0..4
-// are the forward layers, 5..9 the backward layers 4..0.  `first` starts
-// the gradient accumulators (the CTA's first tile).
-__device__ __noinline__ void train_issue(uint32_t tmem, const uint32_t* w, uint32_t ones, const TrainSlot& t,
-                                            int s, int stage, bool first) {
+// The MMAs of one stage of slot s (issued by one thread): stages 0..4 are
+// the forward layers, 5..9 the backward layers 4..0.  `first` starts the
+// gradient accumulators (the CTA's first tile).  sbase is the shared-memory
+// address of the weight image (the start of the CTA's shared memory).
+__device__ __noinline__ void train_issue(uint32_t sbase, uint32_t tmem, int s, int stage, bool first) {
   const uint32_t acc = tmem + kTcAcc + 64u * s;
-  const uint32_t ac = first ? 0u : 1u;
-  if (stage == 0) {
-    tc::gemm_kk(acc, t.x, 1536u, w[0], 1536u, 96, tc::idesc_bf16_f32(128, 64), false);
-  } else if (stage < 4) {
-    tc::gemm_kk(acc, t.h[stage], 1024u, w[stage], 1024u, 64, tc::idesc_bf16_f32(128, 64), false);
-  } else if (stage == 4) {
-    tc::gemm_kk(acc, t.h[4], 1024u, w[4], 1024u, 64, tc::idesc_bf16_f32(128, 16), false);
-  } else if (stage == 5) {
-    // dW4^T [64 in][16 out] += H4^T dZ5 (both MN-major over the batch)
-    tc::gemm_mn(tmem + kTcDW4, t.h[4], 1024u, t.z5, 256u, 128, tc::idesc_bf16_f32_mn(64, 16), !first);
-    // dH4 = dZ5 W4: A = dZ5 (K-major, K = 16), B = W4 read as W4^T (MN-major)
-    tc::mma(acc, tc::smem_desc(t.z5, 128u, 256u), tc::smem_desc(w[4], 1024u, 128u), tc::idesc_bf16_f32_bmn(128, 64),
-            0u);
-  } else {
-    const int l = 9 - stage;   // 3, 2, 1, 0
-    const uint32_t dz = t.h[l + 1];
-    // dW_l [out][in] += dZ_{l+1}^T H_l, and dB_l += dZ_{l+1}^T 1
-    if (l == 0)
-      tc::gemm_mn(tmem + kTcDW0, dz, 1024u, t.x, 1536u, 128, tc::idesc_bf16_f32_mn(64, 96), !first);
-    else
-      tc::gemm_mn(tmem + tc_dw(l), dz, 1024u, t.h[l], 1024u, 128, tc::idesc_bf16_f32_mn(64, 64), !first);
-    for (int j = 0; j < 8; ++j)
-      tc::mma(tmem + kTcDB + 16u * l, tc::smem_desc(dz + 2048u * j, 1024u, 128u),
-              tc::smem_desc(ones + 256u * j, 128u, 2048u), tc::idesc_bf16_f32_amn(64, 16), (ac || j > 0) ? 1u : 0u);
-    // dH_l = dZ_{l+1} W_l: A = dZ (K-major), B = W_l read as W_l^T (MN-major)
-    if (l > 0)
-      for (int j = 0; j < 4; ++j)
-        tc::mma(acc, tc::smem_desc(dz + 256u * j, 128u, 1024u), tc::smem_desc(w[l] + 2048u * j, 1024u, 128u),
-                tc::idesc_bf16_f32_bmn(128, 64), j > 0 ? 1u : 0u);
+  const uint32_t slot = sbase + kTsSlot0 + (uint32_t)s * kTsSlotBytes;
+  const uint32_t X = slot + kTsX, Z5 = slot + kTsZ5, ones = sbase + kTsOnes;
+  const uint32_t f128_64 = tc::idesc_bf16_f32(128, 64);
+  switch (stage) {
+    case 0:
+      mma_k<6>(acc, kdesc(X, 1536u), 256u, kdesc(sbase + kImgW0, 1536u), 256u, f128_64, false);
+      break;
+    case 1:
+    case 2:
+    case 3:
+      mma_k<4>(acc, kdesc(slot + kTsH + 16384u * (stage - 1), 1024u), 256u, kdesc(sbase + img_off(stage), 1024u),
+               256u, f128_64, false);
+      break;
+    case 4:
+      mma_k<4>(acc, kdesc(slot + kTsH + 3 * 16384u, 1024u), 256u, kdesc(sbase + kImgW4, 1024u), 256u,
+               tc::idesc_bf16_f32(128, 16), false);
+      break;
+    case 5: {
+      // dW4^T [64 in][16 out] += H4^T dZ5 (both MN-major over the batch)
+      mma_k<8>(tmem + kTcDW4, mndesc(slot + kTsH + 3 * 16384u, 1024u), 2048u, mndesc(Z5, 256u), 512u,
+               tc::idesc_bf16_f32_mn(64, 16), !first);
+      // dH4 = dZ5 W4: A = dZ5 (K-major, K = 16), B = W4 read as W4^T (MN-major)
+      tc::mma(acc, kdesc(Z5, 256u), mndesc(sbase + kImgW4, 1024u), tc::idesc_bf16_f32_bmn(128, 64), 0u);
+      break;
+    }
+    default: {
+      const int l = 9 - stage;   // 3, 2, 1, 0
+      const uint32_t dz = slot + kTsH + 16384u * l;   // dZ_{l+1}, over H_{l+1}
+      // dW_l [out][in] += dZ_{l+1}^T H_l, and dB_l += dZ_{l+1}^T 1
+      if (l == 0)
+        mma_k<8>(tmem + kTcDW0, mndesc(dz, 1024u), 2048u, mndesc(X, 1536u), 3072u, tc::idesc_bf16_f32_mn(64, 96),
+                 !first);
+      else
+        mma_k<8>(tmem + tc_dw(l), mndesc(dz, 1024u), 2048u, mndesc(slot + kTsH + 16384u * (l - 1), 1024u), 2048u,
+                 tc::idesc_bf16_f32_mn(64, 64), !first);
+      mma_k<8>(tmem + kTcDB + 16u * l, mndesc(dz, 1024u), 2048u, kdesc(ones, 256u), 0u,
+               tc::idesc_bf16_f32_amn(64, 16), !first);
+      // dH_l = dZ_{l+1} W_l: A = dZ (K-major), B = W_l read as W_l^T (MN-major)
+      if (l > 0)
+        mma_k<4>(acc, kdesc(dz, 1024u), 256u, mndesc(sbase + img_off(l), 1024u), 2048u,
+                 tc::idesc_bf16_f32_bmn(128, 64), false);
+      break;
+    }
   }
 }
 
@@ -415,10 +465,62 @@ __device__ __forceinline__ void train_fetch(const float4* __restrict__ recs, con
   t3[2] = targets[3 * (size_t)slot + 2];
 }
 
+// The Adam step that follows the gradient in the same launch.
+struct AdamStep {
+  float *w, *g, *m, *v;   // FP32 masters, summed gradient (and loss at kNP), moments
+  uint8_t* packed;        // the packed copy the kernels read
+  float lr, b1, b2, eps, c1, c2;
+  int apply;
+};
+
+__device__ __forceinline__ void adam_update(const AdamStep& a, int i, float gi) {
+  a.g[i] = gi;
+  if (i < kNP && a.apply) {
+    const float mi = a.b1 * a.m[i] + (1.f - a.b1) * gi;
+    const float vi = a.b2 * a.v[i] + (1.f - a.b2) * gi * gi;
+    a.m[i] = mi;
+    a.v[i] = vi;
+    const float wi = a.w[i] - a.lr * (mi / a.c1) / (sqrtf(vi / a.c2) + a.eps);
+    a.w[i] = wi;
+    pack_param(a.packed, i, wi);
+  }
+}
+
+// After every CTA has written its gradient row: this CTA's slice of the
+// parameters (and the loss, the last entry) is summed over the rows and
+// stepped.  Threads 0..255: parameter t % 128 of a 128-wide chunk, rows of
+// parity t / 128 in row order, then the two halves in order (the sum does
+// not depend on timing).
+__device__ void adam_slice(const float* __restrict__ gpart, int rows, const AdamStep& a, float* part) {
+  const int tid = threadIdx.x, G = (int)gridDim.x;
+  const int per = (kNP + 1 + G - 1) / G, beg = min(kNP + 1, (int)blockIdx.x * per), end = min(kNP + 1, beg + per);
+  for (int p0 = beg; p0 < end; p0 += 128) {
+    const int i = p0 + (tid & 127), h = tid >> 7;
+    float sum = 0.f;
+    if (tid < 256) {
+      constexpr int kBatch = 40;   // loads in flight a thread
+      for (int c0 = h; c0 < rows; c0 += 2 * kBatch) {
+        float r[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+          const int c = c0 + 2 * k;
+          r[k] = (c < rows && i < end) ? __ldcg(&gpart[(size_t)c * kGPRow + i]) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) sum += r[k];
+      }
+      part[tid] = sum;
+    }
+    __syncthreads();
+    if (tid < 128 && i < end) adam_update(a, i, part[tid] + part[128 + tid]);
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(kTrainThreads, 1)
     k_nrc_train(NrcDevice nd, const float4* __restrict__ recs, const float* __restrict__ pnv,
                 const float* __restrict__ targets, const unsigned* __restrict__ count, unsigned cap,
-                float* __restrict__ gpart, unsigned* status) {
+                float* __restrict__ gpart, unsigned* status, AdamStep adam) {
   extern __shared__ __align__(1024) uint8_t sm[];
   const uint32_t full0 = tc::smem_u32(sm + kTsMisc), ready0 = full0 + 16, wbar = full0 + 32;
   uint32_t* tslot = (uint32_t*)(sm + kTsMisc + 40);
@@ -430,19 +532,19 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
   if (tid == 32) {
     for (int s = 0; s < 2; ++s) {
       tc::mbar_init(full0 + 8 * s, 1);
-      tc::mbar_init(ready0 + 8 * s, 128);
+      tc::mbar_init(ready0 + 8 * s, 4);   // one arrival a warp
     }
     tc::mbar_init(wbar, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
-    // the forward weights' shared-memory image: one bulk copy
-    tc::mbar_expect_tx(wbar, kImgBytes);
-    tc::bulk_g2s(tc::smem_u32(sm), nd.packed, kImgBytes, wbar);
+    // the forward weights' shared-memory image and the biases: one bulk copy
+    tc::mbar_expect_tx(wbar, kPackedBytes);
+    tc::bulk_g2s(tc::smem_u32(sm), nd.packed, kPackedBytes, wbar);
   }
   {
-    // the ones tile (BF16 1.0 everywhere) and the per-warp sums
+    // the block of ones (BF16 1.0) and the per-warp sums
     uint4* o = (uint4*)(sm + kTsOnes);
-    for (int i = tid; i < 4096 / 16; i += blockDim.x) o[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    for (int i = tid; i < 512 / 16; i += blockDim.x) o[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
     if (tid < 32) db4[tid] = 0.f;
     if (tid < 8) s_loss[tid] = 0.f;
   }
@@ -455,23 +557,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
   const uint32_t tmem = *tslot;
   const unsigned n = count ? min(*count, cap) : cap;
   const unsigned tiles = w_ok ? (n + 127) / 128 : 0u;
-  const float* gbias = (const float*)((const uint8_t*)nd.packed + kImgBytes);
+  const float* bias = (const float*)(sm + kTsBias);
   bool aborted = false;
 
   if (warp == 8) {
     // ---- the MMA issuer: stage by stage, slot 0 then slot 1 ----
     if (lane == 0 && tiles > 0) {
-      const uint32_t w[5] = {tc::smem_u32(sm + kImgW0), tc::smem_u32(sm + kImgW1), tc::smem_u32(sm + kImgW2),
-                             tc::smem_u32(sm + kImgW3), tc::smem_u32(sm + kImgW4)};
-      TrainSlot ts[2];
-      for (int s = 0; s < 2; ++s) {
-        const uint32_t b = tc::smem_u32(sm + kTsSlot0 + s * kTsSlotBytes);
-        ts[s].x = b + kTsX;
-        ts[s].h[0] = 0u;
-        for (int l = 1; l <= 4; ++l) ts[s].h[l] = b + kTsH + 16384u * (l - 1);
-        ts[s].z5 = b + kTsZ5;
-      }
-      const uint32_t ones = tc::smem_u32(sm + kTsOnes);
+      const uint32_t sbase = tc::smem_u32(sm);
       uint32_t rph[2] = {0u, 0u};
       for (unsigned k = 0; !aborted && blockIdx.x + k * gridDim.x < tiles; k += 2) {
         const bool has1 = blockIdx.x + (k + 1) * gridDim.x < tiles;
@@ -483,7 +575,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
             }
             rph[s] ^= 1u;
             tc::fence_after_sync();
-            train_issue(tmem, w, ones, ts[s], s, stage, k == 0 && s == 0);
+            train_issue(sbase, tmem, s, stage, k == 0 && s == 0);
             tc::commit(full0 + 8 * s);
           }
       }
@@ -516,7 +608,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
         train_fetch(recs, pnv, targets, nt * 128 + t, nt < tiles && nt * 128 + t < n, q, tq);
       }
       tc::fence_proxy_async();
-      mbar_arrive(ready);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ready);
       // forward epilogues: H_{l+1} = relu(Z_{l+1} + b_l), its ReLU mask kept
       uint32_t mask[4][2];
 #pragma unroll
@@ -529,11 +622,11 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
         for (int half = 0; half < 2; ++half) {
           float h[32];
           tc::ld32(acc + 32 * half, h);
-          const float4* b4 = (const float4*)(gbias + 64 * l + 32 * half);
+          const float4* b4 = (const float4*)(bias + 64 * l + 32 * half);
           uint32_t mk = 0u;
 #pragma unroll
           for (int k4 = 0; k4 < 8; ++k4) {
-            const float4 b = __ldg(b4 + k4);
+            const float4 b = b4[k4];
             const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -552,7 +645,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
         }
         tc::fence_before_sync();
         tc::fence_proxy_async();
-        mbar_arrive(ready);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ready);
       }
       // loss gradient at the exp output: dL/dz5 = 2 (y - t) / (y^2 + 0.01) / (3n) * y,
       // stored in BF16; the output bias gradient sums the stored values
@@ -571,7 +665,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
           const float t3[3] = {tr, tg, tb};
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const float y = expf(o[c] + __ldg(gbias + 256 + c));
+            const float y = expf(o[c] + bias[256 + c]);
             const float den = y * y + 0.01f;
             const float dy = y - t3[c];
             loss_acc += dy * dy / den * inv_n3;
@@ -586,7 +680,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
         store_chunk(slot + kTsZ5, t, 0, 16, g);
         store_chunk(slot + kTsZ5, t, 1, 16, g + 8);
         tc::fence_proxy_async();
-        mbar_arrive(ready);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ready);
       }
       // backward epilogues: dZ_l = dH_l * relu'(z_l), stored over H_l
 #pragma unroll
@@ -607,7 +702,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
         }
         tc::fence_before_sync();
         tc::fence_proxy_async();
-        mbar_arrive(ready);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ready);
       }
       // the tile's last MMAs (dW0, dB0) read X and dZ1: done before the next tile overwrites them
       if (!train_wait(full, fph, abort_flag)) aborted = true;
@@ -692,62 +788,9 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   if (warp == 0) tc::dealloc(tmem, kTrainTmemCols);
-}
-
-// ---------------------------------------------------------------------------
-// Adam on the FP32 master parameters; each updated parameter also goes to
-// its place in the packed BF16 image (or the FP32 biases).
-// ---------------------------------------------------------------------------
-// Writes parameter i (oracle layout) into the packed copy.
-__device__ __forceinline__ void pack_param(uint8_t* __restrict__ packed, int i, float x) {
-  if (i < kNW) {
-    const int l = i < off_w(1) ? 0 : min(1 + (i - off_w(1)) / 4096, 4);
-    const int rel = i - off_w(l), o = rel / d_in(l), c = rel % d_in(l);
-    *(uint16_t*)(packed + img_off(l) + tc::core_off(o, c, d_in(l))) = bf16_bits(x);
-  } else {
-    ((float*)(packed + kImgBytes))[i - kNW] = x;   // b0..b3 (64 each), then b4 (3)
-  }
-}
-
-// Every parameter into a zeroed packed copy (creation, loading).
-__global__ void k_nrc_pack(const float* __restrict__ w, uint8_t* __restrict__ packed) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < kNP) pack_param(packed, i, w[i]);
-}
-
-// The gradient (and, at kNP, the loss) is the sum of the training CTAs'
-// rows; it stays in g for inspection.  A block takes 32 parameters and
-// its 8 warps every 8th row each; the partial sums are added in warp
-// order, so the sum does not depend on timing.
-constexpr int kAdamParams = 32;
-__global__ void __launch_bounds__(256) k_nrc_adam(float* __restrict__ w, const float* __restrict__ gpart, int n_part,
-                                                  float* __restrict__ g, float* __restrict__ m,
-                                                  float* __restrict__ v, float lr, float b1, float b2, float eps,
-                                                  float c1, float c2, int apply, uint8_t* __restrict__ packed) {
-  __shared__ float part[8][kAdamParams];
-  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  const int i = blockIdx.x * kAdamParams + lane;
-  float s = 0.f;
-  if (i <= kNP) {
-#pragma unroll 4
-    for (int c = grp; c < n_part; c += 8) s += gpart[(size_t)c * kGPRow + i];
-  }
-  part[grp][lane] = s;
-  __syncthreads();
-  if (grp != 0 || i > kNP) return;
-  float gi = part[0][lane];
-#pragma unroll
-  for (int r = 1; r < 8; ++r) gi += part[r][lane];
-  g[i] = gi;
-  if (i < kNP && apply) {
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    w[i] = wi;
-    pack_param(packed, i, wi);
-  }
+  // every CTA's row written (a cooperative launch: all CTAs are resident)
+  cg::this_grid().sync();
+  adam_slice(gpart, (int)gridDim.x, adam, (float*)(sm + kTsSlot0));
 }
 
 __global__ void k_make_records(const float* __restrict__ pnv, int64_t n, float4* __restrict__ recs, int stride) {
@@ -829,13 +872,25 @@ rt_status nrc_train_launch(rt_nrc* r, const float4* recs, const float* targets, 
   rt_status rs = nrc_setup_kernels();
   if (rs) return rs;
   if ((rs = ensure(r->gpart, (size_t)r->sm_count * kGPRow * sizeof(float)))) return rs;
-  k_nrc_train<<<r->sm_count, kTrainThreads, kTrainSmem, st>>>(r->nd, recs, pnv, targets, count, cap,
-                                                               (float*)r->gpart.p, status);
   r->step++;
-  float c1 = 1.f - powf(r->cfg.beta1, (float)r->step), c2 = 1.f - powf(r->cfg.beta2, (float)r->step);
-  k_nrc_adam<<<(kNP + 1 + kAdamParams - 1) / kAdamParams, 256, 0, st>>>(
-      (float*)r->params.p, (const float*)r->gpart.p, r->sm_count, (float*)r->grad.p, (float*)r->m.p, (float*)r->v.p,
-      r->cfg.lr, r->cfg.beta1, r->cfg.beta2, r->cfg.eps, c1, c2, 1, (uint8_t*)r->packed.p);
+  AdamStep ad;
+  ad.w = (float*)r->params.p;
+  ad.g = (float*)r->grad.p;
+  ad.m = (float*)r->m.p;
+  ad.v = (float*)r->v.p;
+  ad.packed = (uint8_t*)r->packed.p;
+  ad.lr = r->cfg.lr;
+  ad.b1 = r->cfg.beta1;
+  ad.b2 = r->cfg.beta2;
+  ad.eps = r->cfg.eps;
+  ad.c1 = 1.f - powf(r->cfg.beta1, (float)r->step);
+  ad.c2 = 1.f - powf(r->cfg.beta2, (float)r->step);
+  ad.apply = 1;
+  float* gp = (float*)r->gpart.p;
+  void* args[] = {(void*)&r->nd, (void*)&recs, (void*)&pnv, (void*)&targets, (void*)&count, (void*)&cap,
+                  (void*)&gp, (void*)&status, (void*)&ad};
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_nrc_train, r->sm_count, kTrainThreads, args, kTrainSmem, st);
+  if (e != cudaSuccess) return cuda_error(e, "nrc train (cooperative launch)");
   return cuda_error(cudaGetLastError(), "nrc train");
 }
 

@@ -69,6 +69,21 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t mbar, uint32_t parity
   return ok;
 }
 
+// The same test, but a thread whose phase has not completed is suspended
+// until it completes or about `hint_ns` nanoseconds pass, instead of
+// spinning on the issue slots its neighbours need.
+__device__ __forceinline__ uint32_t mbar_try_wait_hint(uint32_t mbar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, %3;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok;
+}
+
 // Waits for the given phase parity of an mbarrier, at most ~2^20 polls.
 // Returns false on time-out (the caller reports it and cleans up).
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
