@@ -150,6 +150,7 @@ __device__ __forceinline__ void fb_add(float* fb, float* target, int pixel, floa
 }
 
 __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const float4* __restrict__ recs,
+                                                            const float* __restrict__ pnv,
                                                             const unsigned* __restrict__ count, unsigned cap,
                                                             float* __restrict__ fb, float* __restrict__ out3,
                                                             unsigned* status, float* const* __restrict__ fbs) {
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const
   uint32_t sA = tc::smem_u32(sm + kSmA);
   const uint32_t sW[5] = {tc::smem_u32(sm + kSmW0), tc::smem_u32(sm + kSmW1), tc::smem_u32(sm + kSmW2),
                           tc::smem_u32(sm + kSmW3), tc::smem_u32(sm + kSmW4)};
-  unsigned n = min(*count, cap);
+  unsigned n = count ? min(*count, cap) : cap;
   unsigned tiles = w_ok ? (n + 127) / 128 : 0u;
   uint32_t phase = 0;
   float lo[3] = {nd.lo[0], nd.lo[1], nd.lo[2]}, ie[3] = {nd.inv_ext[0], nd.inv_ext[1], nd.inv_ext[2]};
@@ -191,7 +192,14 @@ __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const
     float f[96];
     float wr = 0.f, wg = 0.f, wb = 0.f;
     int pixel = 0, frame = 0;
-    if (valid) {
+    if (valid && pnv) {
+      // caller arrays: p, n, v of query `row`, weight 1 (outputs to out3 only)
+      float q[9];
+#pragma unroll
+      for (int j = 0; j < 9; ++j) q[j] = pnv[9 * (size_t)row + j];
+      encode81(q, lo, ie, f);
+      wr = wg = wb = 1.f;
+    } else if (valid) {
       float4 q0 = recs[4 * (size_t)row], q1 = recs[4 * (size_t)row + 1], q2 = recs[4 * (size_t)row + 2],
              q3 = recs[4 * (size_t)row + 3];
       float pnv[9] = {q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z};
@@ -793,21 +801,6 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
   adam_slice(gpart, (int)gridDim.x, adam, (float*)(sm + kTsSlot0));
 }
 
-__global__ void k_make_records(const float* __restrict__ pnv, int64_t n, float4* __restrict__ recs, int stride) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float* q = pnv + 9 * i;
-  float4* r = recs + stride * i;
-  r[0] = make_float4(q[0], q[1], q[2], __int_as_float((int)i));
-  r[1] = make_float4(q[3], q[4], q[5], 0.f);
-  r[2] = make_float4(q[6], q[7], q[8], 0.f);
-  if (stride == 4) r[3] = make_float4(1.f, 1.f, 1.f, 0.f);
-}
-
-void nrc_make_records(const float* pnv, const float* targets, int64_t n, float4* recs, int stride, cudaStream_t st) {
-  (void)targets;
-  k_make_records<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pnv, n, recs, stride);
-}
 
 }  // namespace rtb
 
@@ -844,6 +837,8 @@ static bool g_smem_attr_set = false;
 static rt_status nrc_setup_kernels() {
   if (g_smem_attr_set) return RT_OK;
   cudaError_t e = cudaFuncSetAttribute(k_nrc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem);
+  if (e == cudaSuccess)   // the whole on-chip memory as shared memory: three inference CTAs an SM
+    e = cudaFuncSetAttribute(k_nrc_infer, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_nrc_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem);
   if (e != cudaSuccess) return cuda_error(e, "nrc kernel attributes");
@@ -859,11 +854,11 @@ static rt_status nrc_pack(rt_nrc* r, cudaStream_t st) {
 }
 
 rt_status nrc_infer_launch(rt_nrc* r, const float4* recs, const unsigned* count, unsigned cap, float* fb,
-                           float* out3, unsigned* status, cudaStream_t st, float* const* fbs) {
+                           float* out3, unsigned* status, cudaStream_t st, float* const* fbs, const float* pnv) {
   rt_status rs = nrc_setup_kernels();
   if (rs) return rs;
   int blocks = r->infer_blocks;
-  k_nrc_infer<<<blocks, kInferThreads, kInferSmem, st>>>(r->nd, recs, count, cap, fb, out3, status, fbs);
+  k_nrc_infer<<<blocks, kInferThreads, kInferSmem, st>>>(r->nd, recs, pnv, count, cap, fb, out3, status, fbs);
   return cuda_error(cudaGetLastError(), "nrc infer");
 }
 
@@ -957,7 +952,7 @@ rt_status rt_nrc_create(rt_scene* s, const rt_nrc_config* cfg_in, rt_nrc** out) 
   r->scene = s;
   r->cfg = cfg;
   cudaDeviceGetAttribute(&r->sm_count, cudaDevAttrMultiProcessorCount, s->device);
-  r->infer_blocks = r->sm_count * 2;
+  r->infer_blocks = r->sm_count * 3;   // 64 KB of shared memory and 64 tensor-memory columns each: three an SM
   for (int j = 0; j < 3; ++j) {
     float lo = s->bbox_lo[j], hi = s->bbox_hi[j];
     if (!(hi > lo)) hi = lo + 1.f;
@@ -1122,14 +1117,8 @@ rt_status rt_nrc_infer(rt_nrc* r, rt_scene* s, const float* pnv_dev, int64_t n, 
   if (!r || !s || (n > 0 && (!pnv_dev || !out_dev)) || n < 0 || n > (1 << 26))
     return set_error(RT_ERR_INVALID_ARG, "rt_nrc_infer: bad argument");
   if (n == 0) return RT_OK;
-  cudaStream_t st = (cudaStream_t)stream;
-  rt_status rs;
-  if ((rs = ensure(r->infer_q, (size_t)n * 64)) || (rs = ensure(r->counters, 64))) return rs;
-  cudaError_t e = cudaMemcpyAsync(r->counters.p, &n, 4, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_error(e, "rt_nrc_infer");
-  nrc_make_records(pnv_dev, nullptr, n, (float4*)r->infer_q.p, 4, st);
-  return nrc_infer_launch(r, (const float4*)r->infer_q.p, (const unsigned*)r->counters.p, (unsigned)n, nullptr,
-                          out_dev, s->status, st);
+  return nrc_infer_launch(r, nullptr, nullptr, (unsigned)n, nullptr, out_dev, s->status, (cudaStream_t)stream,
+                          nullptr, pnv_dev);
 }
 
 // One training step on n given samples (p, n, v) with targets (n x 3):

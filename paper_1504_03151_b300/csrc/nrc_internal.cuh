@@ -23,16 +23,14 @@ struct NrcDevice {
 
 // Inference over `count` records, adding weight x radiance to fb (or, with
 // fbs set, to fbs[frame] with the frame index in the record's last word).
+// With pnv set, the first cap rows of pnv (n x 9) instead of records, weight 1, outputs to out3.
 rt_status nrc_infer_launch(rt_nrc* r, const float4* recs, const unsigned* count, unsigned cap, float* fb, float* out3,
-                           unsigned* status, cudaStream_t st, float* const* fbs = nullptr);
+                           unsigned* status, cudaStream_t st, float* const* fbs = nullptr, const float* pnv = nullptr);
 // Training on `count` (at most cap; all cap when count is null) stride-3
 // records whose slot indexes targets, or, with pnv set, on the first cap
 // rows of pnv (n x 9) and targets (n x 3); then the Adam step.
 rt_status nrc_train_launch(rt_nrc* r, const float4* recs, const float* targets, const unsigned* count, unsigned cap,
                            unsigned* status, cudaStream_t st, const float* pnv = nullptr);
-// Records from caller arrays: pnv n x 9 -> stride-4 (inference, weight 1)
-// or stride-3 (training, slot = index) float4 records.
-void nrc_make_records(const float* pnv, const float* targets, int64_t n, float4* recs, int stride, cudaStream_t st);
 NrcDevice* nrc_device(rt_nrc* r);
 const rt_scene* nrc_scene(const rt_nrc* r);   // the scene whose box normalises the encoding
 
