@@ -161,6 +161,9 @@ __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const
   float* bias = (float*)(sm + kSmBias);
   int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t wbar = tc::smem_u32(sm + kSmMisc + 24);
+  // a CTA without a tile returns before staging anything
+  const unsigned n = count ? min(*count, cap) : cap;
+  if (blockIdx.x >= (n + 127) / 128) return;
   if (warp == 0) tc::alloc(tc::smem_u32(tslot), kInferTmemCols);
   if (tid == 0) {
     tc::mbar_init(tc::smem_u32(mbar), 1);
@@ -182,7 +185,6 @@ __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const
   uint32_t sA = tc::smem_u32(sm + kSmA);
   const uint32_t sW[5] = {tc::smem_u32(sm + kSmW0), tc::smem_u32(sm + kSmW1), tc::smem_u32(sm + kSmW2),
                           tc::smem_u32(sm + kSmW3), tc::smem_u32(sm + kSmW4)};
-  unsigned n = count ? min(*count, cap) : cap;
   unsigned tiles = w_ok ? (n + 127) / 128 : 0u;
   uint32_t phase = 0;
   float lo[3] = {nd.lo[0], nd.lo[1], nd.lo[2]}, ie[3] = {nd.inv_ext[0], nd.inv_ext[1], nd.inv_ext[2]};
