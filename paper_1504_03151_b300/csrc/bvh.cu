@@ -499,7 +499,7 @@ static int radix_sort_pairs(rt_scene* s, BuildScratch& b, int n, int bits, cudaS
     int coop = 0, per_sm = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_coop, 256, 0);
-    coop_blocks = coop ? std::min(std::min(per_sm, 2) * s->sm_count, kSortCoopMaxBlocks) : 0;
+    coop_blocks = coop ? std::min(std::min(per_sm, 1) * s->sm_count, kSortCoopMaxBlocks) : 0;   // one an SM
   }
   if (coop_blocks > 0 && n <= kSortCoopMaxKeys) {
     void* args[] = {&k_in, &v_in, &k_out, &v_out, &n, &passes, &b.hist, &b.partials};
@@ -2212,7 +2212,7 @@ static rt_status bvh_build_launch(rt_scene* s, cudaStream_t st) {
       cudaFuncSetAttribute(k_top_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
       cudaFuncSetAttribute(k_top_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_top_all, 256, dyn);
-      coop_blocks = coop ? std::min(per_sm, 2) * s->sm_count : 0;
+      coop_blocks = coop ? std::min(per_sm, 1) * s->sm_count : 0;   // one an SM: cheaper grid barriers
     }
     bool launched = false;
     CluList la{b.clu_a, b.clu_lo, b.clu_hi}, lb{b.clu_b, b.clu_lo_b, b.clu_hi_b};
