@@ -188,35 +188,39 @@ __global__ void __launch_bounds__(kInferThreads) k_nrc_infer(NrcDevice nd, const
   unsigned tiles = w_ok ? (n + 127) / 128 : 0u;
   uint32_t phase = 0;
   float lo[3] = {nd.lo[0], nd.lo[1], nd.lo[2]}, ie[3] = {nd.inv_ext[0], nd.inv_ext[1], nd.inv_ext[2]};
+  // a query's inputs: position, normal, direction (q[0..8]), frame (q[9]);
+  // path weight and pixel (w)
+  auto fetch = [&](unsigned tl, float* q, float4& w) {
+    const unsigned row = tl * 128 + tid;
+    if (tl >= tiles || row >= n) return;
+    if (pnv) {
+      // caller arrays: p, n, v of query `row`, weight 1 (outputs to out3 only)
+#pragma unroll
+      for (int j = 0; j < 9; ++j) q[j] = pnv[9 * (size_t)row + j];
+      w = make_float4(1.f, 1.f, 1.f, 0.f);
+    } else {
+      const float4 q0 = recs[4 * (size_t)row], q1 = recs[4 * (size_t)row + 1], q2 = recs[4 * (size_t)row + 2],
+                   q3 = recs[4 * (size_t)row + 3];
+      q[0] = q0.x, q[1] = q0.y, q[2] = q0.z, q[3] = q1.x, q[4] = q1.y, q[5] = q1.z, q[6] = q2.x, q[7] = q2.y;
+      q[8] = q2.z;
+      q[9] = q3.w;
+      w = make_float4(q3.x, q3.y, q3.z, q0.w);
+    }
+  };
+  float nq[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float4 nw = make_float4(0.f, 0.f, 0.f, 0.f);
+  fetch(blockIdx.x, nq, nw);
   for (unsigned tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     unsigned row = tile * 128 + tid;
     bool valid = row < n;
-    float f[96];
-    float wr = 0.f, wg = 0.f, wb = 0.f;
-    int pixel = 0, frame = 0;
-    if (valid && pnv) {
-      // caller arrays: p, n, v of query `row`, weight 1 (outputs to out3 only)
-      float q[9];
+    float q[10];
 #pragma unroll
-      for (int j = 0; j < 9; ++j) q[j] = pnv[9 * (size_t)row + j];
-      encode81(q, lo, ie, f);
-      wr = wg = wb = 1.f;
-    } else if (valid) {
-      float4 q0 = recs[4 * (size_t)row], q1 = recs[4 * (size_t)row + 1], q2 = recs[4 * (size_t)row + 2],
-             q3 = recs[4 * (size_t)row + 3];
-      float pnv[9] = {q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z};
-      encode81(pnv, lo, ie, f);
-      pixel = __float_as_int(q0.w);
-      frame = __float_as_int(q3.w);
-      wr = q3.x;
-      wg = q3.y;
-      wb = q3.z;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 96; ++k) f[k] = 0.f;
-    }
-#pragma unroll
-    for (int c = 0; c < 12; ++c) store_chunk(sm + kSmA, tid, c, 96, f + 8 * c);
+    for (int j = 0; j < 10; ++j) q[j] = nq[j];
+    const float wr = nw.x, wg = nw.y, wb = nw.z;
+    const int pixel = __float_as_int(nw.w), frame = __float_as_int(q[9]);
+    // the next tile's inputs load while this one runs
+    fetch(tile + gridDim.x, nq, nw);
+    encode_store(q, lo, ie, valid, sm + kSmA, tid);
     tc::fence_proxy_async();
     __syncthreads();
     for (int l = 0; l < 5; ++l) {
