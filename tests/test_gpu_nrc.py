@@ -197,6 +197,34 @@ def test_nrc_gradients_many_tiles_per_sm():
     scene.close()
 
 
+@pytest.mark.parametrize("tiles_per_sm", [0, 1, 3])
+@pytest.mark.parametrize("extra", [1, 128, 129])
+def test_nrc_gradients_edge_batches(tiles_per_sm, extra):
+    # Batches around the kernel's boundaries: a single sample, whole tiles,
+    # one past a tile, and CTAs whose two slots hold an odd number of tiles
+    # (the second slot idle in the last round).
+    sc, scene = _scene()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 128 * sms * tiles_per_sm + extra
+    rng = np.random.default_rng(100 + n)
+    pnv = _samples(sc, n, rng)
+    target = rng.uniform(0.05, 1.5, (n, 3)).astype(np.float32)
+    nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=6))
+    p0 = rtb.rt_nrc_get_params(nrc)
+    rtb.rt_nrc_train_step(nrc, scene.handle, torch.from_numpy(pnv).cuda(), torch.from_numpy(target).cuda(), n)
+    assert rtb.rt_scene_sync(scene.handle) == rtb.RT_OK
+    g, loss = rtb.rt_nrc_get_grads(nrc)
+    W, B = _split(p0)
+    ref_loss, dW, dB = O.mlp_loss_grad(_oracle_inputs(sc, pnv), target.astype(np.float64), W, B, bf16_acts=True)
+    assert np.isfinite(g).all()
+    assert loss == pytest.approx(ref_loss, rel=1e-2)
+    ref = np.concatenate([dW, dB])
+    assert _cos(g.astype(np.float64), ref) >= 0.999
+    assert np.linalg.norm(g.astype(np.float64) - ref) <= 1e-2 * np.linalg.norm(ref)
+    rtb.rt_nrc_destroy(nrc)
+    scene.close()
+
+
 def test_nrc_training_reduces_loss():
     sc, scene = _scene()
     nrc = rtb.rt_nrc_create(scene.handle, rtb.rt_nrc_config_default(seed=9))
