@@ -268,14 +268,46 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
     }
     // Alg. 1: one shadow ray per point light where n.l > 0
     bool local = is_hit && sf.kind != RT_MAT_DIELECTRIC && (1.f - sf.rho) > 0.f;
-    for (int li = 0; li < sc.n_lights; ++li) {
-      f3 contrib = mk3(0, 0, 0), os = mk3(0, 0, 0), sd = mk3(0, 0, 1);
-      float tmax = 0.f;
-      bool valid = local && light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib,
-                                       os, sd, tmax);
-      bool ok;
-      unsigned pos = warp_push(&ctr->shadow[depth], valid, fp.shadow_cap, ok, sc.status);
-      if (ok) store_ray(fp.shadowq[depth & 1], pos, os, pixel, sd, tmax, contrib);
+    if (sc.n_lights <= 32) {
+      // the warp's rays of every light in one reservation: which lights each
+      // lane's hit faces, one atomic for their total, then the records light
+      // by light (the same order as one push a light)
+      uint32_t faces = 0u;
+      unsigned total = 0u;
+      for (int li = 0; li < sc.n_lights; ++li) {
+        const bool f = local && light_faces(sf, __ldg(&sc.lights[2 * li]));
+        faces |= (f ? 1u : 0u) << li;
+        total += (unsigned)__popc(__ballot_sync(kFull, f));
+      }
+      unsigned base = 0u;
+      if (total) {
+        if ((threadIdx.x & 31) == 0) base = atomicAdd(&ctr->shadow[depth], total);
+        base = __shfl_sync(kFull, base, 0);
+      }
+      const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+      for (int li = 0; li < sc.n_lights && total; ++li) {
+        const bool f = (faces >> li) & 1u;
+        const unsigned mask = __ballot_sync(kFull, f);
+        if (f) {
+          f3 contrib = mk3(0, 0, 0), os = mk3(0, 0, 0), sd = mk3(0, 0, 1);
+          float tmax = 0.f;
+          light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib, os, sd, tmax);
+          const unsigned pos = base + (unsigned)__popc(mask & lt);
+          if (pos < fp.shadow_cap) store_ray(fp.shadowq[depth & 1], pos, os, pixel, sd, tmax, contrib);
+          else atomicOr(sc.status, kErrQueueOverflow);
+        }
+        base += (unsigned)__popc(mask);
+      }
+    } else {
+      for (int li = 0; li < sc.n_lights; ++li) {
+        f3 contrib = mk3(0, 0, 0), os = mk3(0, 0, 0), sd = mk3(0, 0, 1);
+        float tmax = 0.f;
+        bool valid = local && light_term(sf, d, w, __ldg(&sc.lights[2 * li]), __ldg(&sc.lights[2 * li + 1]), contrib,
+                                         os, sd, tmax);
+        bool ok;
+        unsigned pos = warp_push(&ctr->shadow[depth], valid, fp.shadow_cap, ok, sc.status);
+        if (ok) store_ray(fp.shadowq[depth & 1], pos, os, pixel, sd, tmax, contrib);
+      }
     }
     // area lights, then emissive primitives: one sampled point of each per pass
     for (int li = 0; kPass && li < sc.n_alights + sc.n_emitters; ++li) {

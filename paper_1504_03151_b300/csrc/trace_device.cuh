@@ -455,6 +455,13 @@ __device__ __forceinline__ float spec_pow(float rv, float shin) { return __powf(
 // Alg. 1 for one point light (Eq. 8 with point lights): the term the light
 // adds if nothing blocks it, and the shadow ray that decides; false where
 // n.l <= 0 (no shadow ray is cast).
+// Whether point light L0 lies on the lit side of the hit (n.l > 0): the
+// test light_term makes, computed the same way.
+__device__ __forceinline__ bool light_faces(const Surface& sf, float4 L0) {
+  const f3 l = normalize(xyz(L0) - sf.p);
+  return dot(sf.n, l) > 0.f;
+}
+
 __device__ __forceinline__ bool light_term(const Surface& sf, f3 d, f3 w, float4 L0, float4 L1, f3& contrib, f3& o_s,
                                            f3& d_s, float& tmax) {
   f3 lp = xyz(L0);
