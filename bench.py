@@ -48,15 +48,15 @@ BYTES_RAY_IO = 48 + 16
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "71b39b7f28311edf"
+PROFILED_SHA = "254d92a4540827f7"
 PROFILED_TRAFFIC = {
-    0: (10_055_424 + 133_894_400 + 5_491_968 + 0 + 8_006_912 + 107_245_568,
+    0: (10_076_416 + 134_113_536 + 5_792_256 + 768 + 7_799_552 + 110_930_688,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's k_trace<1,0,0>, k_trace<0,0,0> "
         "(depth 1) and k_paths<0,0> (depths 2-5) launches, one capture per kernel (-k, -c 2 / -c 1); "
-        "L2 bytes (lts__t_bytes.sum) 674,188,384"),
-    1: (179_861_504 + 7_645_696 + 5_799_424 + 0,
+        "L2 bytes (lts__t_bytes.sum) 679,261,920"),
+    1: (179_856_896 + 7_685_376 + 5_771_264 + 0,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's two k_shadow<0> launches "
-        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 796,925,472"),
+        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 740,827,008"),
 }
 
 
