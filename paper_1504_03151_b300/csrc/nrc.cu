@@ -58,29 +58,6 @@ __device__ __forceinline__ float bf16_float(uint16_t b) { return __bfloat162floa
 // encoding: 3 normalised position values, normal (3), view direction (3),
 // sin and cos of 2^k pi x_hat_j for k = 0..11 -> 81 values, zero-padded to 96
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void encode81(const float* pnv, const float* lo, const float* inv_ext, float* f) {
-  float xh[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    xh[j] = (pnv[j] - lo[j]) * inv_ext[j];
-    f[j] = xh[j];
-    f[3 + j] = pnv[3 + j];
-    f[6 + j] = pnv[6 + j];
-  }
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    float sc = (float)(1 << k);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float s, c;
-      sincospif(sc * xh[j], &s, &c);
-      f[9 + 6 * k + j] = s;
-      f[9 + 6 * k + 3 + j] = c;
-    }
-  }
-#pragma unroll
-  for (int k = 81; k < 96; ++k) f[k] = 0.f;
-}
 
 // Writes 8 consecutive features (columns 8c..8c+7) of row r as one 16-byte
 // chunk of a K-major canonical tile.
@@ -93,9 +70,10 @@ __device__ __forceinline__ void store_chunk(uint8_t* tile, int r, int c, int K, 
   *(uint4*)(tile + tc::core_off(r, 8 * c, K)) = q;
 }
 
-// The same 96 features for row t of a K-major [128][96] tile, each 16-byte
-// chunk stored as soon as its 8 features exist (fewer live registers than
-// encoding the whole row first).  A row past the batch is zero.
+// The 96 features of one sample (p, n, v) as row t of a K-major [128][96]
+// tile, each 16-byte chunk stored as soon as its 8 features exist (fewer
+// live registers than encoding the whole row first).  A row past the batch
+// is zero.
 __device__ __forceinline__ void encode_store(const float* pnv, const float* lo, const float* inv_ext, bool valid,
                                              uint8_t* tile, int t) {
   float f[96];

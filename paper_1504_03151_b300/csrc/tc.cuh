@@ -122,39 +122,19 @@ __device__ __forceinline__ void gemm(uint32_t tmem_d, uint32_t saddr_a, uint32_t
   }
 }
 
-// The same GEMM over K-major tiles whose row pitch differs from K: sbo_a /
-// sbo_b are the byte distances between 8-row groups of A and B (a tile of
-// W columns has W / 8 x 128 B; only the first K columns are read).
-__device__ __forceinline__ void gemm_kk(uint32_t tmem_d, uint32_t saddr_a, uint32_t sbo_a, uint32_t saddr_b,
-                                        uint32_t sbo_b, int K, uint32_t idesc, bool accumulate) {
-  for (int j = 0; j < K / 16; ++j) {
-    uint64_t a = smem_desc(saddr_a + 256u * j, 128u, sbo_a);
-    uint64_t b = smem_desc(saddr_b + 256u * j, 128u, sbo_b);
-    mma(tmem_d, a, b, idesc, (accumulate || j > 0) ? 1u : 0u);
-  }
-}
-
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both
 // operands MN-major (bits 15 and 16: A and B transposed), shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N) {
   return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
 }
 
-// D = A B^T (+ D) with both operands MN-major, unswizzled: a core matrix is
-// 8 rows along K of 16 contiguous bytes (8 elements) along M (or N); core
-// matrices are 128 B apart along M / N (the stride byte offset) and
-// k_pitch bytes apart along K (the leading byte offset).  A row-major tile
-// stored K-major for another product - rows = this product's K, 16-byte
-// chunks of its M or N elements - is such an operand, with k_pitch its
-// 8-row-group distance.  K (a multiple of 16) is the tile's row count.
-__device__ __forceinline__ void gemm_mn(uint32_t tmem_d, uint32_t saddr_a, uint32_t k_pitch_a, uint32_t saddr_b,
-                                        uint32_t k_pitch_b, int K, uint32_t idesc, bool accumulate) {
-  for (int j = 0; j < K / 16; ++j) {
-    uint64_t a = smem_desc(saddr_a + 2u * k_pitch_a * j, k_pitch_a, 128u);
-    uint64_t b = smem_desc(saddr_b + 2u * k_pitch_b * j, k_pitch_b, 128u);
-    mma(tmem_d, a, b, idesc, (accumulate || j > 0) ? 1u : 0u);
-  }
-}
+// An MN-major, unswizzled operand: a core matrix is 8 rows along K of 16
+// contiguous bytes (8 elements) along M (or N); core matrices are 128 B
+// apart along M / N (the stride byte offset) and k_pitch bytes apart along
+// K (the leading byte offset), and a K = 16 step advances 2 k_pitch.  A
+// row-major tile stored K-major for another product - rows = this
+// product's K, 16-byte chunks of its M or N elements - is such an operand,
+// with k_pitch its 8-row-group distance.
 
 // Instruction descriptor of kind::f16 (BF16, FP32 D) with only A
 // MN-major (bit 15), or only B MN-major (bit 16).
