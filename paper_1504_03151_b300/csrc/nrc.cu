@@ -73,9 +73,11 @@ __device__ __forceinline__ void store_chunk(uint8_t* tile, int r, int c, int K, 
 // The 96 features of one sample (p, n, v) as row t of a K-major [128][96]
 // tile, each 16-byte chunk stored as soon as its 8 features exist (fewer
 // live registers than encoding the whole row first).  A row past the batch
-// is zero.
+// is zero.  With ones81 the first padding column (feature 81) of a sample
+// is 1: the layer-0 weight-gradient MMA then also sums the backward signal
+// over the batch (dB0), against a weight column the packed copy keeps 0.
 __device__ __forceinline__ void encode_store(const float* pnv, const float* lo, const float* inv_ext, bool valid,
-                                             uint8_t* tile, int t) {
+                                             uint8_t* tile, int t, bool ones81 = false) {
   float f[96];
   float xh[3];
 #pragma unroll
@@ -103,6 +105,7 @@ __device__ __forceinline__ void encode_store(const float* pnv, const float* lo, 
   }
 #pragma unroll
   for (int k = kFeatures; k < 96; ++k) f[k] = 0.f;
+  if (ones81 && valid) f[kFeatures] = 1.f;
   store_chunk(tile, t, 10, 96, f + 80);
   store_chunk(tile, t, 11, 96, f + 88);
 }
@@ -259,7 +262,8 @@ __device__ __forceinline__ void pack_param(uint8_t* __restrict__ packed, int i, 
   if (i < kNW) {
     const int l = i < off_w(1) ? 0 : min(1 + (i - off_w(1)) / 4096, 4);
     const int rel = i - off_w(l), o = rel / d_in(l), c = rel % d_in(l);
-    *(uint16_t*)(packed + img_off(l) + tc::core_off(o, c, d_in(l))) = bf16_bits(x);
+    // the padding features' weights stay 0: the training encoding puts a 1 in feature 81
+    *(uint16_t*)(packed + img_off(l) + tc::core_off(o, c, d_in(l))) = (l == 0 && c >= kFeatures) ? 0 : bf16_bits(x);
   } else {
     ((float*)(packed + kImgBytes))[i - kNW] = x;   // b0..b3 (64 each), then b4 (3)
   }
@@ -299,7 +303,7 @@ constexpr int kTcAcc = 0;      // 64 a slot, at 64 s: forward / backward accumul
 constexpr int kTcDW0 = 128;    // 96: dW0 (M = 64 out, N = 96 in)
 constexpr int kTcDW1 = 224;    // 64 each at 224, 288, 352: dW1..dW3
 constexpr int kTcDW4 = 416;    // 16: dW4^T (M = 64 in, N = 16 out)
-constexpr int kTcDB = 432;     // 16 each at 432 + 16 l: dB0..dB3 (M = 64 out; every column the same sum)
+constexpr int kTcDB = 432;     // 16 each at 432 + 16 l: dB1..dB3 (M = 64 out; every column the same sum); dB0 is in dW0
 static_assert(kTcDB + 4 * 16 <= kTrainTmemCols, "the training accumulators exceed the tensor memory");
 __host__ __device__ constexpr int tc_dw(int l) { return l == 0 ? kTcDW0 : kTcDW1 + 64 * (l - 1); }
 // shared memory (bytes): the weight image and the FP32 biases (one bulk
@@ -419,15 +423,16 @@ __device__ __noinline__ void train_issue(uint32_t sbase, uint32_t tmem, int s, i
     default: {
       const int l = 9 - stage;   // 3, 2, 1, 0
       const uint32_t dz = slot + kTsH + 16384u * l;   // dZ_{l+1}, over H_{l+1}
-      // dW_l [out][in] += dZ_{l+1}^T H_l, and dB_l += dZ_{l+1}^T 1
+      // dW_l [out][in] += dZ_{l+1}^T H_l, and dB_l += dZ_{l+1}^T 1 (layer 0: in dW0)
       if (l == 0)
         mma_k<8>(tmem + kTcDW0, mndesc(dz, 1024u), 2048u, mndesc(X, 1536u), 3072u, tc::idesc_bf16_f32_mn(64, 96),
                  !first);
       else
         mma_k<8>(tmem + tc_dw(l), mndesc(dz, 1024u), 2048u, mndesc(slot + kTsH + 16384u * (l - 1), 1024u), 2048u,
                  tc::idesc_bf16_f32_mn(64, 64), !first);
-      mma_k<8>(tmem + kTcDB + 16u * l, mndesc(dz, 1024u), 2048u, kdesc(ones, 256u), 0u,
-               tc::idesc_bf16_f32_amn(64, 16), !first);
+      if (l > 0)   // dB0 is column 81 of dW0 (the ones column of X)
+        mma_k<8>(tmem + kTcDB + 16u * l, mndesc(dz, 1024u), 2048u, kdesc(ones, 256u), 0u,
+                 tc::idesc_bf16_f32_amn(64, 16), !first);
       // dH_l = dZ_{l+1} W_l: A = dZ (K-major), B = W_l read as W_l^T (MN-major)
       if (l > 0)
         mma_k<4>(acc, kdesc(dz, 1024u), 256u, mndesc(sbase + img_off(l), 1024u), 2048u,
@@ -593,7 +598,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
       const unsigned row = tile * 128 + t;
       const bool valid = row < n;
       const float tr = tq[0], tg = tq[1], tb = tq[2];
-      encode_store(q, lo, ie, valid, slot + kTsX, t);
+      encode_store(q, lo, ie, valid, slot + kTsX, t, true);
       // the next tile of this slot: its inputs load while this one runs
       {
         const unsigned nt = tile + 2 * gridDim.x;
@@ -726,8 +731,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
     const bool mine = lane < 16;
     float v[32];
     if (warp < 4) {
-      for (int c = 0; c < 3; ++c) {   // dW0: 96 columns
+      for (int c = 0; c < 3; ++c) {   // dW0: 96 columns; column 81 is dB0, 81..95 are padding
         tc::ld32(lane_base + kTcDW0 + 32 * c, v);
+        if (c == 2) {
+          if (mine) gp[off_b(0) + m] = v[kFeatures - 64];
+#pragma unroll
+          for (int k = kFeatures - 64; k < 32; ++k) v[k] = 0.f;
+        }
         if (mine) {
           store16(gp + off_w(0) + m * 96 + 32 * c, v);
           store16(gp + off_w(0) + m * 96 + 32 * c + 16, v + 16);
@@ -740,8 +750,6 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
           store16(gp + off_w(1) + m * 64 + 32 * c + 16, v + 16);
         }
       }
-      tc::ld16(lane_base + kTcDB, v);
-      if (mine) gp[off_b(0) + m] = v[0];
       tc::ld16(lane_base + kTcDB + 16, v);
       if (mine) gp[off_b(1) + m] = v[0];
     } else {
