@@ -223,6 +223,12 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
   int deep[kStackSize - kStackShared > 0 ? kStackSize - kStackShared : 1];   // entries below the shared part
   // rows of the near planes: lo when the direction is positive, else hi
   const int sx = r.idir.x < 0.f, sy = r.idir.y < 0.f, sz = r.idir.z < 0.f;
+  // Speculative walk (Aila and Laine 2009): a lane that reaches a leaf
+  // keeps it for later and walks on through inner nodes until every lane of
+  // the warp holds a leaf, so that the warp's lanes test leaves together
+  // instead of one after another.  Any order of the leaves gives the same
+  // result (closest hits tie to the lower primitive id).
+  int leaf = kSentinelLink;
   for (;;) {
     // inner nodes
     while (node >= 0) {
@@ -239,20 +245,32 @@ __device__ int traverse(const DevScene& sc, const RayInv& r, float tmin, float& 
         fail = true;
         return kAny ? -1 : best;
       }
+      if (node < 0 && node != kSentinelLink && leaf == kSentinelLink) {
+        leaf = node;
+        node = pop_stack<kStride>(stack, deep, sp);
+      }
+      if (!__any_sync(__activemask(), leaf == kSentinelLink)) break;
     }
-    if (node == kSentinelLink) break;
-    // leaves
-    while (node < 0 && node != kSentinelLink) {
-      int ls = leaf_start(node), lc = leaf_count(node);
+    // leaves: the kept one first, then any the walk stands at
+    while (leaf != kSentinelLink || (node < 0 && node != kSentinelLink)) {
+      int cur;
+      if (leaf != kSentinelLink) {
+        cur = leaf;
+        leaf = kSentinelLink;
+      } else {
+        cur = node;
+        node = pop_stack<kStride>(stack, deep, sp);
+      }
+      int ls = leaf_start(cur), lc = leaf_count(cur);
       if (ls + lc > sc.n_prims) {
         atomicOr(sc.status, kErrBadTree);
         fail = true;
         return -1;
       }
       if (leaf_hits<kAny, kCount>(sc.prims, ls, lc, r, tmin, tbest, best, best_id, wc)) return best;
-      node = pop_stack<kStride>(stack, deep, sp);
+      if (node >= 0) break;
     }
-    if (node == kSentinelLink) break;
+    if (node == kSentinelLink && leaf == kSentinelLink) break;
   }
   return best;
 }
