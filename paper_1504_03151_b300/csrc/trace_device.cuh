@@ -294,6 +294,11 @@ __device__ int traverse_warp(const DevScene& sc, const RayInv& r, bool part, flo
   int steps = 0;
   int deep[kStackSize - kStackShared > 0 ? kStackSize - kStackShared : 1];
   const int sx = r.idir.x < 0.f, sy = r.idir.y < 0.f, sz = r.idir.z < 0.f;
+  // Speculative, as traverse(): a lane at a leaf keeps it and takes inner
+  // steps with the others until every lane still walking holds a leaf; the
+  // leaf phase ends early when no lane keeps a leaf and some lane has inner
+  // nodes again.
+  int leaf = kSentinelLink;
   for (;;) {
     while (__any_sync(kFull, node >= 0)) {
       if (node >= 0) {
@@ -301,23 +306,39 @@ __device__ int traverse_warp(const DevScene& sc, const RayInv& r, bool part, flo
           fail = true;
           if (kAny) best = -1;
           node = kSentinelLink;
+          leaf = kSentinelLink;
         } else if (node >= sc.n_nodes) {
           atomicOr(sc.status, kErrBadTree);
           fail = true;
           best = -1;
           node = kSentinelLink;
+          leaf = kSentinelLink;
         } else if (!visit_inner<kCount, kStride, kAny>(sc.nodes, node, r, sx, sy, sz, tmin, tbest, stack, deep, sp,
                                                          wc)) {
           fail = true;
           if (kAny) best = -1;
           node = kSentinelLink;
+          leaf = kSentinelLink;
         }
       }
+      if (node < 0 && node != kSentinelLink && leaf == kSentinelLink) {
+        leaf = node;
+        node = pop_stack<kStride>(stack, deep, sp);
+      }
+      if (!__any_sync(kFull, leaf == kSentinelLink && node >= 0)) break;
     }
-    if (!__any_sync(kFull, node != kSentinelLink)) break;
-    while (__any_sync(kFull, node < 0 && node != kSentinelLink)) {
-      if (node < 0 && node != kSentinelLink) {
-        int ls = leaf_start(node), lc = leaf_count(node);
+    if (!__any_sync(kFull, node != kSentinelLink || leaf != kSentinelLink)) break;
+    while (__any_sync(kFull, leaf != kSentinelLink || (node < 0 && node != kSentinelLink))) {
+      if (leaf != kSentinelLink || (node < 0 && node != kSentinelLink)) {
+        int cur;
+        if (leaf != kSentinelLink) {
+          cur = leaf;
+          leaf = kSentinelLink;
+        } else {
+          cur = node;
+          node = pop_stack<kStride>(stack, deep, sp);
+        }
+        int ls = leaf_start(cur), lc = leaf_count(cur);
         if (ls + lc > sc.n_prims) {
           atomicOr(sc.status, kErrBadTree);
           fail = true;
@@ -325,10 +346,9 @@ __device__ int traverse_warp(const DevScene& sc, const RayInv& r, bool part, flo
           node = kSentinelLink;
         } else if (leaf_hits<kAny, kCount>(sc.prims, ls, lc, r, tmin, tbest, best, best_id, wc)) {
           node = kSentinelLink;   // any hit: done
-        } else {
-          node = pop_stack<kStride>(stack, deep, sp);
         }
       }
+      if (__any_sync(kFull, node >= 0) && !__any_sync(kFull, leaf != kSentinelLink)) break;
     }
   }
   return best;
