@@ -48,15 +48,15 @@ BYTES_RAY_IO = 48 + 16
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "254d92a4540827f7"
+PROFILED_SHA = "a24fb277326e5246"
 PROFILED_TRAFFIC = {
-    0: (10_076_416 + 134_113_536 + 5_792_256 + 768 + 7_799_552 + 110_930_688,
+    0: (10_259_712 + 133_959_424 + 5_944_064 + 256 + 7_923_712 + 112_245_760,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's k_trace<1,0,0>, k_trace<0,0,0> "
         "(depth 1) and k_paths<0,0> (depths 2-5) launches, one capture per kernel (-k, -c 2 / -c 1); "
-        "L2 bytes (lts__t_bytes.sum) 679,261,920"),
-    1: (179_856_896 + 7_685_376 + 5_771_264 + 0,
+        "L2 bytes (lts__t_bytes.sum) 693,712,448"),
+    1: (179_823_360 + 7_431_168 + 5_786_112 + 0,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's two k_shadow<0> launches "
-        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 740,827,008"),
+        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 721,167,776"),
 }
 
 
