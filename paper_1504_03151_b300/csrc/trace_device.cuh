@@ -295,9 +295,7 @@ __device__ int traverse_warp(const DevScene& sc, const RayInv& r, bool part, flo
   int deep[kStackSize - kStackShared > 0 ? kStackSize - kStackShared : 1];
   const int sx = r.idir.x < 0.f, sy = r.idir.y < 0.f, sz = r.idir.z < 0.f;
   // Speculative, as traverse(): a lane at a leaf keeps it and takes inner
-  // steps with the others until every lane still walking holds a leaf; the
-  // leaf phase ends early when no lane keeps a leaf and some lane has inner
-  // nodes again.
+  // steps with the others until every lane still walking holds a leaf.
   int leaf = kSentinelLink;
   for (;;) {
     while (__any_sync(kFull, node >= 0)) {
@@ -348,7 +346,6 @@ __device__ int traverse_warp(const DevScene& sc, const RayInv& r, bool part, flo
           node = kSentinelLink;   // any hit: done
         }
       }
-      if (__any_sync(kFull, node >= 0) && !__any_sync(kFull, leaf != kSentinelLink)) break;
     }
   }
   return best;
