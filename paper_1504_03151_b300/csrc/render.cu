@@ -345,8 +345,10 @@ __global__ void __launch_bounds__(kTraceThreads, RTB_TRACE_MIN_BLOCKS) k_trace(D
 // ---------------------------------------------------------------------------
 // shadow rays: any hit on (0, tmax); unblocked -> add the light's term
 // ---------------------------------------------------------------------------
+// Eight blocks an SM: the speculative walk would take 69 registers and leave
+// room for seven; at 63 it spills nothing.
 template <bool kCount>
-__global__ void __launch_bounds__(kTraceThreads) k_shadow(DevScene sc, FrameParams fp, int depth, int cap) {
+__global__ void __launch_bounds__(kTraceThreads, 8) k_shadow(DevScene sc, FrameParams fp, int depth, int cap) {
   __shared__ int s_stack[kStackShared * kTraceThreads];
   int* stack = s_stack + threadIdx.x;
   int lane = threadIdx.x & 31;
