@@ -48,15 +48,15 @@ BYTES_RAY_IO = 48 + 16
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "f3be55174209a7a4"
+PROFILED_SHA = "031d6b167d2443f7"
 PROFILED_TRAFFIC = {
-    0: (10_149_120 + 133_846_528 + 5_935_360 + 512 + 7_931_136 + 109_280_256,
+    0: (10_213_888 + 133_712_896 + 5_952_768 + 256 + 7_934_976 + 111_130_624,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's k_trace<1,0,0>, k_trace<0,0,0> "
         "(depth 1) and k_paths<0,0> (depths 2-5) launches, one capture per kernel (-k, -c 2 / -c 1); "
-        "L2 bytes (lts__t_bytes.sum) 686,684,704"),
-    1: (179_866_112 + 7_817_216 + 5_787_648 + 0,
+        "L2 bytes (lts__t_bytes.sum) 691,205,344"),
+    1: (179_851_776 + 7_432_704 + 5_811_712 + 0,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's two k_shadow<0> launches "
-        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 721,503,104"),
+        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 727,997,280"),
 }
 
 
