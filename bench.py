@@ -671,7 +671,7 @@ def main():
     if n_e2e and graph is not None:
         side = torch.cuda.Stream(dev)
         imgs = [out, torch.empty_like(out)]
-        stage = [torch.empty_like(tri_dev) for _ in range(2)]
+        stage = [tri_dev.clone() for _ in range(2)]    # valid geometry from the first read on
 
         def frame(j):
             rtb.rt_scene_update(h, None, stage[j])

@@ -566,6 +566,80 @@ def test_step_captured_in_a_cuda_graph():
     scene.close()
 
 
+def test_frames_with_host_copies_replayed_from_two_graphs():
+    """The end-to-end frame loop the benchmark times: graph j repacks from
+    upload buffer j, builds, and renders into image j while a side branch
+    copies the previous image to pinned host memory and uploads the next
+    geometry into buffer 1 - j.  Every host image equals the frame rendered
+    directly from the same geometry."""
+    from cuda.bindings import runtime as cudart
+
+    def copy_async(dst, src, st):
+        n = src.numel() * src.element_size()
+        err, = cudart.cudaMemcpyAsync(dst.data_ptr(), src.data_ptr(), n, cudart.cudaMemcpyKind.cudaMemcpyDefault,
+                                      st.cuda_stream)
+        assert err == cudart.cudaError_t.cudaSuccess
+
+    sc = small_terrain(seed=7)
+    W, H, D = sc.width, sc.height, sc.max_depth
+    scene = rtb.Scene(sc).build()
+    h = scene.handle
+    opts = rtb.make_options(background=sc.background)
+    geo = []
+    for k in range(4):                                   # four frames of different geometry
+        t = sc.triangles.copy()
+        for v in ("v0", "v1", "v2"):
+            t[v][:, 1] *= 1.0 - 0.15 * k
+        geo.append(torch.from_numpy(t.view(np.uint8).reshape(-1).copy()).pin_memory())
+    host_in = torch.empty_like(geo[0]).pin_memory()      # the pinned input the side branch uploads
+    imgs = [torch.empty(W * H * 3, device="cuda") for _ in range(2)]
+    stage = [geo[0].cuda() for _ in range(2)]             # valid geometry from the first read on
+    host_out = [torch.empty(W * H * 3).pin_memory() for _ in range(2)]
+    side = torch.cuda.Stream()
+
+    def frame(j):
+        rtb.rt_scene_update(h, sc.spheres, stage[j])
+        rtb.rt_bvh_build(h)
+        cur = torch.cuda.current_stream()
+        side.wait_stream(cur)
+        copy_async(host_out[1 - j], imgs[1 - j], side)
+        copy_async(stage[1 - j], host_in, side)
+        rtb.rt_render_ex(h, sc.camera, W, H, D, imgs[j], opts)
+        cur.wait_stream(side)
+
+    host_in.copy_(geo[0])
+    for j in (0, 1):
+        frame(j)
+    torch.cuda.synchronize()
+    graphs = [torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()]
+    for j in range(2):
+        with torch.cuda.graph(graphs[j]):
+            frame(j)
+    torch.cuda.synchronize()
+    copy_async(stage[0], geo[0], torch.cuda.current_stream())
+    got = []
+    for k in range(4):
+        host_in.copy_(geo[(k + 1) % 4])                  # the next frame's geometry, read by this replay
+        graphs[k % 2].replay()
+        torch.cuda.synchronize()
+        if k > 0:
+            got.append(host_out[(k - 1) % 2].clone())   # the previous frame's image
+    last = 3 % 2
+    copy_async(host_out[last], imgs[last], torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    got.append(host_out[last].clone())
+    ref = torch.empty(W * H * 3, device="cuda")
+    for k in range(4):
+        rtb.rt_scene_update(h, sc.spheres, geo[k].cuda())
+        rtb.rt_bvh_build(h)
+        rtb.rt_render_ex(h, sc.camera, W, H, D, ref, opts)
+        torch.cuda.synchronize()
+        assert (got[k] - ref.cpu()).abs().max().item() < 1e-5, k   # only atomic ordering differs
+    assert (got[0] - got[3]).abs().max().item() > 1e-2               # the frames differ
+    assert rtb.rt_scene_sync(h) == rtb.RT_OK
+    scene.close()
+
+
 def test_scene_update_with_a_bad_material_is_reported():
     """rt_scene_update does not validate; a material index out of range is
     replaced by material 0 on the device and reported by the next sync."""
