@@ -48,15 +48,15 @@ BYTES_RAY_IO = 48 + 16
 # they were taken on: any change to those files reports null instead.
 PROFILED_SOURCES = ["paper_1504_03151_b300/csrc/render.cu", "paper_1504_03151_b300/csrc/trace_device.cuh",
                     "paper_1504_03151_b300/csrc/rtb_internal.cuh"]
-PROFILED_SHA = "031d6b167d2443f7"
+PROFILED_SHA = "ccd6cbd2e027b63a"
 PROFILED_TRAFFIC = {
-    0: (10_213_888 + 133_712_896 + 5_952_768 + 256 + 7_934_976 + 111_130_624,
+    0: (8_801_792 + 128_627_968 + 5_335_552 + 0 + 7_919_360 + 112_625_920,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's k_trace<1,0,0>, k_trace<0,0,0> "
         "(depth 1) and k_paths<0,0> (depths 2-5) launches, one capture per kernel (-k, -c 2 / -c 1); "
-        "L2 bytes (lts__t_bytes.sum) 691,205,344"),
-    1: (179_851_776 + 7_432_704 + 5_811_712 + 0,
+        "L2 bytes (lts__t_bytes.sum) 619,376,672"),
+    1: (179_826_176 + 7_308_032 + 5_791_488 + 0,
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the first frame's two k_shadow<0> launches "
-        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 727,997,280"),
+        "(depths 0, 1), -k k_shadow -c 2; L2 bytes (lts__t_bytes.sum) 722,356,544"),
 }
 
 

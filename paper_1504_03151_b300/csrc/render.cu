@@ -141,8 +141,11 @@ __device__ __forceinline__ void flush_work(Counters* ctr, int cls, int depth, Wo
 // ---------------------------------------------------------------------------
 // closest hit + shade (+ primary ray generation at depth 0)
 // ---------------------------------------------------------------------------
+// Five blocks an SM: with six the closest-hit kernel fits 80 registers and
+// spills; the five-block cap (102) holds it without spills, and the wider
+// issue of the unspilled code outweighs the sixth block's warps.
 #ifndef RTB_TRACE_MIN_BLOCKS
-#define RTB_TRACE_MIN_BLOCKS 6
+#define RTB_TRACE_MIN_BLOCKS 5
 #endif
 #ifndef RTB_PATHS_MIN_BLOCKS
 #define RTB_PATHS_MIN_BLOCKS 5
